@@ -1,0 +1,148 @@
+/*
+ * libsn -- B300 (sm_103a) split-step solver of the generalized
+ * Schroedinger-Newton system.
+ *
+ * The system (Sec. II, Eqs. 1-2) is
+ *     i dpsi/dt = A lap(psi) + B phi psi + G(|psi|^2) psi,
+ *     lap(phi) + C phi = D |psi|^2,
+ * with B = 1 and the local nonlinearity G(|psi|^2) = g |psi|^2.  The potential
+ * is solved spectrally (Sec. III) with the Newton + Yukawa multiplier that the
+ * modified Poisson equation of the non-minimal matter-curvature coupling gives
+ * for constant coefficients (Eq. 9; Eq. 14 is its alpha -> 0 limit):
+ *     phi_k = K(k) rho_k,  K(k) = -4 pi G [1/k^2 + alpha_Y / (k^2 + 1/lambda_Y^2)],
+ *     K(0) = 0 (the mean density is removed).
+ * Time stepping is the symmetric split-step Fourier method (Sec. III):
+ *     S(h) = Kin(h/2) Nl(h) Kin(h/2),
+ *     Kin(tau) = F^-1 exp(i A k^2 tau) F,
+ *     Nl(h) psi = exp(-i (phi + V_ext + g |psi|^2) h) psi.
+ *
+ * Conventions for every call:
+ *   - ndim is 2 or 3; arrays are C-ordered with the slowest axis first
+ *     ((ny, nx) or (nz, ny, nx)); n[] and L[] are given in that order.
+ *   - each n[a] is a power of two in [8, 1024]; L[a] > 0 is the box length.
+ *   - psi is interleaved (re, im): complex64 (two floats) for SN_C64 grids,
+ *     complex128 (two doubles) for SN_C128 grids.  Node-centred coordinates
+ *     x_j = -L/2 + j L / n.
+ *   - the library owns all device memory of a grid; callers own every host
+ *     buffer and every device buffer they pass in.  set/get calls copy.
+ *   - every call returns an sn_status; no exception crosses the boundary.
+ *     Work is queued on the grid's CUDA stream; a failure inside a kernel
+ *     surfaces at the next call that synchronises (sn_get_state,
+ *     sn_observables, or sn_sync).
+ *   - a grid may be used by one host thread at a time.
+ */
+#ifndef SN_H_
+#define SN_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sn_grid_s* sn_grid; /* opaque handle */
+
+typedef enum {
+  SN_OK = 0,
+  SN_EINVAL = -1,      /* invalid argument; nothing was queued */
+  SN_ENOMEM = -2,      /* device allocation failed */
+  SN_ECUDA = -3,       /* a CUDA call or kernel failed; see sn_last_error */
+  SN_ETIMEOUT = -4,    /* a bounded device wait expired */
+  SN_ENONFINITE = -5,  /* the state holds NaN or Inf */
+  SN_ENOTSUP = -6      /* valid request this build does not support */
+} sn_status;
+
+typedef enum {
+  SN_C64 = 0,  /* complex64 state; fused FP32 passes */
+  SN_C128 = 1  /* complex128 state; plain FP64 step */
+} sn_dtype;
+
+/* Parameters of Eqs. 1-2 as used by the step (Sec. II; Eq. 9 / Eq. 14). */
+typedef struct {
+  double coeff_lap;  /* A of Eq. 1; -0.5 for i psi_t = -(1/2) lap psi + ...   */
+  double G;          /* K(k) = -4 pi G (1/k^2 + alpha_Y / (k^2 + 1/lambda_Y^2)) */
+  double alpha_Y;    /* Yukawa strength; 0 gives the pure Newton kernel         */
+  double lambda_Y;   /* Yukawa range (> 0 when alpha_Y != 0)                    */
+  double g_local;    /* local term g |psi|^2                                     */
+  int zero_k0;       /* must be 1: the whole multiplier is zero at k = 0         */
+  const double* v_ext; /* optional real external potential (C order, ncells
+                          doubles), NULL for none; copied by sn_set_kernel       */
+  int v_ext_on_device; /* 1 if v_ext is a device pointer, 0 if host             */
+} sn_kernel;
+
+/* Observables at the current integer step (FP64, computed on the device).
+ *   mass = dV sum |psi|^2
+ *   e_kin = -A (dV/N) sum_k k^2 |F psi|^2
+ *   e_pot = (1/2) dV sum phi rho + dV sum V_ext rho
+ *   e_nl = (g/2) dV sum rho^2,  e_total = e_kin + e_pot + e_nl
+ *   centroid[a] = (L_a / 2 pi) arg(sum rho exp(2 pi i x_a / L_a))
+ *   momentum[a] = (dV/N) sum_k k_a |F psi|^2 (Nyquist k_a counted as 0)
+ * Axis entries are in array order; entries beyond ndim are 0. */
+typedef struct {
+  double mass, e_kin, e_pot, e_nl, e_total;
+  double centroid[3], momentum[3];
+  long long step;
+} sn_obs;
+
+/* Create a grid (Sec. II: psi on a periodic box of ndim dimensions).
+ * out: receives the handle.  n, L: ndim entries each, slowest axis first.
+ * dtype: SN_C64 or SN_C128.  cuda_stream: a cudaStream_t the caller keeps
+ * alive for the grid's lifetime, or NULL for a library-created stream.
+ * psi starts at zero and the kernel at {A=-0.5, G=1, alpha_Y=0, g=0}.
+ * Errors: SN_EINVAL for bad arguments, SN_ENOMEM, SN_ECUDA. */
+sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, int dtype,
+                         void* cuda_stream);
+
+/* Set the parameters of Eqs. 1-2 (see sn_kernel).  Copies v_ext.  Errors:
+ * SN_EINVAL for non-finite values, lambda_Y <= 0 with alpha_Y != 0, or
+ * zero_k0 != 1. */
+sn_status sn_set_kernel(sn_grid g, const sn_kernel* k);
+
+/* Copy a state in: psi holds ncells complex values of the grid's dtype,
+ * host memory (on_device = 0; the call returns after the copy) or device
+ * memory (on_device = 1; ordered on the grid's stream).  Resets the step
+ * counter to 0. */
+sn_status sn_set_state(sn_grid g, const void* psi, int on_device);
+
+/* Copy the state out (same layout as sn_set_state).  Host copies block until
+ * done.  The state is always at an integer step. */
+sn_status sn_get_state(sn_grid g, void* psi_out, int on_device);
+
+/* Advance nsteps symmetric split steps of size dt (Sec. III).  Consecutive
+ * steps are merged (Kin(h/2) Kin(h/2) = Kin(h)); the call opens and closes
+ * the merge, so psi is at an integer step on return.  nsteps = 0 is a no-op.
+ * dt may be negative (time reversal).  Asynchronous on the grid's stream.
+ * Errors: SN_EINVAL (non-finite dt, nsteps < 0), SN_ECUDA. */
+sn_status sn_step(sn_grid g, double dt, int nsteps);
+
+/* Compute the observables of the current state (blocks until done).
+ * Errors: SN_ENONFINITE if any sum is NaN or Inf, SN_ECUDA. */
+sn_status sn_observables(sn_grid g, sn_obs* out);
+
+/* Wait for the grid's queued work; returns SN_ECUDA if a kernel failed. */
+sn_status sn_sync(sn_grid g);
+
+/* Number of kernels this grid has launched since creation. */
+long long sn_launch_count(sn_grid g);
+
+/* Run sn_step(g, dt, nsteps) with a CUDA event pair around every kernel and
+ * report, per kernel kind k (0 <= k < nkinds, kinds as listed by
+ * sn_kind_name), the summed device time in ms, the launch count and the
+ * algorithmic HBM bytes those launches move.  Blocks until done.  The step
+ * itself is identical to sn_step. */
+sn_status sn_profile_step(sn_grid g, double dt, int nsteps, double* ms, long long* launches,
+                          double* bytes, int nkinds);
+
+/* Name of kernel kind k, or NULL past the last kind. */
+const char* sn_kind_name(int k);
+
+/* Free the grid and its device memory (waits for its queued work). */
+void sn_destroy_grid(sn_grid g);
+
+/* Last error message of this grid, or of the calling thread's last failed
+ * sn_create_grid when g is NULL.  Never NULL. */
+const char* sn_last_error(sn_grid g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SN_H_ */

@@ -1,0 +1,747 @@
+// C-ABI of libsn: grid state, FP64-built tables, the step schedule and the
+// observables.  The numerical kernels live in passes_f32.cu (fused FP32 step)
+// and plain_f64.cu (plain FP64 step and observables).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sn.h"
+#include "sn_internal.h"
+
+using namespace sn;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+thread_local std::string g_tls_error = "";
+
+const char* const kKindNames[K_NUM_KINDS] = {
+    "psi_pass", "psi_pass_nphase", "psi_pass_density", "rho_fwd", "rho_green", "rho_inv",
+    "f64_fft", "f64_elementwise", "observables"};
+
+int log2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// FP32 tables carry each factor as a pair of floats, hi = fl(x), lo = fl(x - hi):
+// hi + lo holds x to ~1e-15, so the kinetic factors and twiddles stay unitary
+// far below the FP32 rounding of the products (no systematic mass drift).
+void split_hilo(const std::vector<double2>& v, std::vector<float2>& out) {
+  const size_t n = v.size();
+  out.resize(2 * n);
+  for (size_t i = 0; i < n; ++i) {
+    const float hr = (float)v[i].x, hi = (float)v[i].y;
+    out[i] = make_float2(hr, hi);
+    out[n + i] = make_float2((float)(v[i].x - (double)hr), (float)(v[i].y - (double)hi));
+  }
+}
+
+// Twiddle table of the two-stage Stockham plan for length N (see sn_fft.cuh):
+// [r*R0 + j] = exp(-2 pi i j r / N) (forward second stage, r < R1, j < R0) and
+// [N + r*R1 + j] = exp(+2 pi i j r / N) (inverse second stage, r < R0, j < R1).
+void plan_radices(int N, int* R0, int* R1) {
+  if (N <= 16) { *R0 = N; *R1 = 1; return; }
+  switch (N) {
+    case 32: *R0 = 2; break;
+    case 64: *R0 = 4; break;
+    case 128: *R0 = 8; break;
+    case 256: *R0 = 16; break;
+    case 512: *R0 = 16; break;
+    default: *R0 = 32; break;
+  }
+  *R1 = N / *R0;
+}
+
+std::vector<double2> twiddles_f64(int N) {
+  int R0, R1;
+  plan_radices(N, &R0, &R1);
+  std::vector<double2> tw;
+  if (R1 == 1) return tw;
+  tw.resize(2 * N);
+  for (int r = 0; r < R1; ++r)
+    for (int j = 0; j < R0; ++j) {
+      const double a = -2.0 * kPi * (double)((long long)j * r % N) / N;
+      tw[r * R0 + j] = make_double2(std::cos(a), std::sin(a));
+    }
+  for (int r = 0; r < R0; ++r)
+    for (int j = 0; j < R1; ++j) {
+      const double a = 2.0 * kPi * (double)((long long)j * r % N) / N;
+      tw[N + r * R1 + j] = make_double2(std::cos(a), std::sin(a));
+    }
+  return tw;
+}
+
+double wavenumber(int j, int n, double L) {
+  return 2.0 * kPi / L * (double)(j < n / 2 ? j : j - n);
+}
+
+struct Launch {
+  int kind;
+  double bytes;
+  cudaEvent_t e0, e1;
+};
+
+}  // namespace
+
+struct sn_grid_s {
+  int ndim = 0;
+  int n[3] = {1, 1, 1};
+  double L[3] = {1, 1, 1};
+  int dtype = SN_C64;
+  long long cells = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  long long step = 0;
+  long long launches = 0;
+  std::string err;
+
+  void* psi = nullptr;         // float2* or double2*
+  float2* rhohat = nullptr;    // C64: half spectrum
+  double2* w64a = nullptr;     // FP64 scratch (psi copy / work)
+  double2* w64b = nullptr;
+  double* partials = nullptr;  // observables partials [kObsBlocks][Q_NUM]
+  double* obs_out = nullptr;   // [Q_NUM]
+
+  // per-length twiddles, indexed by log2 N
+  float2* tw32[11] = {};
+  double2* tw64[11] = {};
+  // per-axis tables
+  float* k2_32[3] = {};
+  double* k2_64[3] = {};
+  double* kax_64[3] = {};
+  float* zero32 = nullptr;  // a single 0 (k^2 of a missing middle axis)
+  // kinetic multipliers [axis][half=0/full=1]: n entries (FP64) or 2n (FP32 hi, lo)
+  float2* mult32[3][2] = {};
+  double2* mult64[3][2] = {};
+  double mult_dt = std::nan("");
+  double mult_A = std::nan("");
+
+  sn_kernel kp{};
+  float* vext32 = nullptr;
+  double* vext64 = nullptr;
+  bool has_vext = false;
+
+  // profiling
+  bool profiling = false;
+  std::vector<Launch> prof;
+
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+sn_status fail(sn_grid g, sn_status st, const std::string& msg) {
+  if (g) g->err = msg;
+  else g_tls_error = msg;
+  return st;
+}
+
+sn_status cuda_fail(sn_grid g, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(g, e == cudaErrorMemoryAllocation ? SN_ENOMEM : SN_ECUDA, m);
+}
+
+template <typename T>
+cudaError_t dalloc(sn_grid g, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  g->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t upload(sn_grid g, T** p, const std::vector<T>& host) {
+  cudaError_t e = dalloc(g, p, host.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*p, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+bool is_pow2_in_range(int n) { return n >= 8 && n <= 1024 && (n & (n - 1)) == 0; }
+
+// Launch bookkeeping: counts, and an event pair per launch while profiling.
+struct LaunchScope {
+  sn_grid g;
+  Launch rec;
+  LaunchScope(sn_grid g_, int kind, double bytes) : g(g_) {
+    rec.kind = kind;
+    rec.bytes = bytes;
+    rec.e0 = rec.e1 = nullptr;
+    if (g->profiling) {
+      cudaEventCreate(&rec.e0);
+      cudaEventCreate(&rec.e1);
+      cudaEventRecord(rec.e0, g->stream);
+    }
+  }
+  void done() {
+    g->launches += 1;
+    if (g->profiling) {
+      cudaEventRecord(rec.e1, g->stream);
+      g->prof.push_back(rec);
+    }
+  }
+};
+
+#define SN_LAUNCH(g, kind, bytes, call)                          \
+  do {                                                           \
+    LaunchScope _ls((g), (kind), (double)(bytes));               \
+    cudaError_t _e = (call);                                     \
+    _ls.done();                                                  \
+    if (_e != cudaSuccess) return cuda_fail((g), _e, #call);     \
+  } while (0)
+
+// ---- tables -----------------------------------------------------------------
+
+sn_status ensure_mult_tables(sn_grid g, double dt) {
+  const double A = g->kp.coeff_lap;
+  if (dt == g->mult_dt && A == g->mult_A) return SN_OK;
+  // the previous tables may still be read by queued kernels
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamSynchronize");
+  for (int a = 0; a < g->ndim; ++a) {
+    const int n = g->n[a];
+    for (int f = 0; f < 2; ++f) {
+      const double tau = f ? dt : 0.5 * dt;
+      std::vector<double2> m64(n);
+      for (int j = 0; j < n; ++j) {
+        const double k = wavenumber(j, n, g->L[a]);
+        const double th = A * k * k * tau;
+        m64[j] = make_double2(std::cos(th) / n, std::sin(th) / n);
+      }
+      if (g->dtype == SN_C64) {
+        std::vector<float2> m32;
+        split_hilo(m64, m32);
+        e = cudaMemcpy(g->mult32[a][f], m32.data(), m32.size() * sizeof(float2),
+                       cudaMemcpyHostToDevice);
+      } else {
+        e = cudaMemcpy(g->mult64[a][f], m64.data(), n * sizeof(double2), cudaMemcpyHostToDevice);
+      }
+      if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemcpy(mult)");
+    }
+  }
+  g->mult_dt = dt;
+  g->mult_A = A;
+  return SN_OK;
+}
+
+sn_status ensure_f64_scratch(sn_grid g) {
+  if (g->w64a) return SN_OK;
+  cudaError_t e = dalloc(g, &g->w64a, (size_t)g->cells);
+  if (e == cudaSuccess) e = dalloc(g, &g->w64b, (size_t)g->cells);
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaMalloc(fp64 scratch)");
+  return SN_OK;
+}
+
+// ---- geometry of a pass along array axis a ----------------------------------
+
+struct LineGeom {
+  long long outer, inner;
+  bool strided;
+};
+LineGeom psi_geom(sn_grid g, int a) {
+  long long outer = 1, inner = 1;
+  for (int b = 0; b < a; ++b) outer *= g->n[b];
+  for (int b = a + 1; b < g->ndim; ++b) inner *= g->n[b];
+  return {outer, inner, a != g->ndim - 1};
+}
+
+double kernel_cN(sn_grid g, double scale) { return -4.0 * kPi * g->kp.G * scale; }
+
+// ---- fused FP32 step ----------------------------------------------------------
+
+sn_status psi_pass(sn_grid g, int a, int variant, int full, double dt) {
+  const LineGeom lg = psi_geom(g, a);
+  PsiPassArgs pa{};
+  pa.psi = reinterpret_cast<float2*>(g->psi);
+  pa.outer = lg.outer;
+  pa.inner = lg.inner;
+  pa.mult = g->mult32[a][full];
+  pa.tw = g->tw32[log2i(g->n[a])];
+  pa.rh_in = g->rhohat;
+  pa.vext = g->has_vext ? g->vext32 : nullptr;
+  pa.h = (float)dt;
+  pa.gh = (float)(g->kp.g_local * dt);
+  pa.rh_out = g->rhohat;
+  const double P = g->n[a] / 2 + 1, lines = (double)g->cells / g->n[a];
+  double bytes = 16.0 * g->cells;
+  int kind = K_PSI;
+  if (variant == PSI_NPHASE) {
+    bytes += 8.0 * P * lines;  // C2R reads the half spectrum along this axis
+    if (g->has_vext) bytes += 4.0 * g->cells;
+    kind = K_PSI_NPHASE;
+  } else if (variant == PSI_DENSITY) {
+    bytes += 8.0 * P * lines;
+    kind = K_PSI_DENSITY;
+  }
+  SN_LAUNCH(g, kind, bytes, launch_psi_pass_f32(g->n[a], lg.strided, variant, pa, g->stream));
+  return SN_OK;
+}
+
+// Half-spectrum passes after the density of axis h: forward along the middle
+// axis (3D), Green's multiply along the remaining axis, inverse along the middle.
+sn_status rho_passes(sn_grid g, int h, double dt) {
+  const int d = g->ndim;
+  const long long P = g->n[h] / 2 + 1;
+  int rest[2], nr = 0;
+  for (int b = 0; b < d; ++b)
+    if (b != h) rest[nr++] = b;
+  // rho-hat dims (P, n[rest[0]], [n[rest[1]]])
+  const double bytes = 16.0 * (double)P * ((double)g->cells / g->n[h]);
+  const double mu2 = (g->kp.alpha_Y != 0.0) ? 1.0 / (g->kp.lambda_Y * g->kp.lambda_Y) : 1.0;
+  const double cN = kernel_cN(g, dt / (double)g->cells);
+  const double cY = cN * g->kp.alpha_Y;
+  RhoPassArgs ra{};
+  ra.data = g->rhohat;
+  ra.tw = nullptr;
+  ra.cN = (float)cN;
+  ra.cY = (float)cY;
+  ra.mu2 = (float)mu2;
+  if (d == 2) {
+    const int c = rest[0];
+    ra.outer = P;
+    ra.inner = 1;
+    ra.tw = g->tw32[log2i(g->n[c])];
+    ra.k2p = g->k2_32[h];
+    ra.k2m = g->zero32;
+    ra.k2l = g->k2_32[c];
+    ra.mid_n = 1;
+    SN_LAUNCH(g, K_RHO_GREEN, bytes, launch_rho_pass_f32(g->n[c], false, RHO_GREEN, ra, g->stream));
+    return SN_OK;
+  }
+  // 3D: y (array axis 1) is always the middle axis of the rho-hat passes
+  const int r1 = rest[0], r2 = rest[1];
+  const int y = 1;
+  const int third = (r1 == y) ? r2 : r1;
+  auto geom = [&](int axis, RhoPassArgs& x) -> bool {
+    // along rho-hat axis 2 (last, contiguous) or rho-hat axis 1 (strided)
+    if (axis == r2) {
+      x.outer = P * g->n[r1];
+      x.inner = 1;
+      x.mid_n = g->n[r1];
+      x.k2m = g->k2_32[r1];
+      return false;
+    }
+    x.outer = P;
+    x.inner = g->n[r2];
+    x.mid_n = 1;
+    x.k2m = g->k2_32[r2];
+    return true;
+  };
+  {
+    RhoPassArgs x = ra;
+    const bool st = geom(y, x);
+    x.tw = g->tw32[log2i(g->n[y])];
+    SN_LAUNCH(g, K_RHO_FWD, bytes, launch_rho_pass_f32(g->n[y], st, RHO_FWD, x, g->stream));
+  }
+  {
+    RhoPassArgs x = ra;
+    const bool st = geom(third, x);
+    x.tw = g->tw32[log2i(g->n[third])];
+    x.k2p = g->k2_32[h];
+    x.k2l = g->k2_32[third];
+    SN_LAUNCH(g, K_RHO_GREEN, bytes, launch_rho_pass_f32(g->n[third], st, RHO_GREEN, x, g->stream));
+  }
+  {
+    RhoPassArgs x = ra;
+    const bool st = geom(y, x);
+    x.tw = g->tw32[log2i(g->n[y])];
+    SN_LAUNCH(g, K_RHO_INV, bytes, launch_rho_pass_f32(g->n[y], st, RHO_INV, x, g->stream));
+  }
+  return SN_OK;
+}
+
+sn_status step_f32(sn_grid g, double dt, int nsteps) {
+  const int d = g->ndim;
+  int prev_h = -1;
+  for (int r = 0; r <= nsteps; ++r) {
+    const bool odd = (r & 1) != 0;
+    const int full = (r == 0 || r == nsteps) ? 0 : 1;
+    int order[3];
+    for (int i = 0; i < d; ++i) order[i] = odd ? d - 1 - i : i;
+    for (int i = 0; i < d; ++i) {
+      int variant = PSI_PLAIN;
+      if (i == 0 && r > 0) variant = PSI_NPHASE;
+      if (i == d - 1 && r < nsteps) variant = PSI_DENSITY;
+      sn_status st = psi_pass(g, order[i], variant, full, dt);
+      if (st != SN_OK) return st;
+    }
+    if (r < nsteps) {
+      prev_h = order[d - 1];
+      sn_status st = rho_passes(g, prev_h, dt);
+      if (st != SN_OK) return st;
+    }
+  }
+  return SN_OK;
+}
+
+// ---- plain FP64 step ----------------------------------------------------------
+
+sn_status fftn_f64(sn_grid g, double2* buf, int sign) {
+  for (int a = g->ndim - 1; a >= 0; --a) {
+    const LineGeom lg = psi_geom(g, a);
+    SN_LAUNCH(g, K_F64_FFT, 32.0 * g->cells,
+              launch_fft_f64(g->n[a], lg.strided, sign, buf, lg.outer, lg.inner,
+                             g->tw64[log2i(g->n[a])], g->stream));
+  }
+  return SN_OK;
+}
+
+sn_status kinetic_f64(sn_grid g, int full) {
+  double2* psi = reinterpret_cast<double2*>(g->psi);
+  sn_status st = fftn_f64(g, psi, -1);
+  if (st != SN_OK) return st;
+  const double2* m[3] = {g->mult64[0][full], g->mult64[1][full], g->mult64[2][full]};
+  SN_LAUNCH(g, K_F64_EW, 32.0 * g->cells, launch_mult_kinetic_f64(psi, g->n, g->ndim, m, g->stream));
+  return fftn_f64(g, psi, +1);
+}
+
+sn_status step_f64(sn_grid g, double dt, int nsteps) {
+  sn_status st = ensure_f64_scratch(g);
+  if (st != SN_OK) return st;
+  double2* psi = reinterpret_cast<double2*>(g->psi);
+  double2* w = g->w64b;
+  const double mu2 = (g->kp.alpha_Y != 0.0) ? 1.0 / (g->kp.lambda_Y * g->kp.lambda_Y) : 1.0;
+  const double cN = kernel_cN(g, dt / (double)g->cells);
+  const double* k2[3] = {g->k2_64[0], g->k2_64[1], g->k2_64[2]};
+  for (int s = 0; s < nsteps; ++s) {
+    if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
+    SN_LAUNCH(g, K_F64_EW, 32.0 * g->cells, launch_density_f64(psi, w, g->cells, g->stream));
+    if ((st = fftn_f64(g, w, -1)) != SN_OK) return st;
+    SN_LAUNCH(g, K_F64_EW, 32.0 * g->cells,
+              launch_green_f64(w, g->n, g->ndim, k2, cN, cN * g->kp.alpha_Y, mu2, g->stream));
+    if ((st = fftn_f64(g, w, +1)) != SN_OK) return st;
+    SN_LAUNCH(g, K_F64_EW, (48.0 + (g->has_vext ? 8.0 : 0.0)) * g->cells,
+              launch_phase_f64(psi, w, g->has_vext ? g->vext64 : nullptr, dt,
+                               g->kp.g_local * dt, g->cells, g->stream));
+    if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
+  }
+  return SN_OK;
+}
+
+sn_status do_step(sn_grid g, double dt, int nsteps) {
+  if (!std::isfinite(dt)) return fail(g, SN_EINVAL, "sn_step: dt must be finite");
+  if (nsteps < 0) return fail(g, SN_EINVAL, "sn_step: nsteps must be >= 0");
+  if (nsteps == 0) return SN_OK;
+  sn_status st = ensure_mult_tables(g, dt);
+  if (st != SN_OK) return st;
+  st = (g->dtype == SN_C64) ? step_f32(g, dt, nsteps) : step_f64(g, dt, nsteps);
+  if (st == SN_OK) g->step += nsteps;
+  return st;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" {
+
+sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, int dtype,
+                         void* cuda_stream) {
+  if (!out) return fail(nullptr, SN_EINVAL, "sn_create_grid: out is NULL");
+  *out = nullptr;
+  if (ndim != 2 && ndim != 3) return fail(nullptr, SN_EINVAL, "sn_create_grid: ndim must be 2 or 3");
+  if (!n || !L) return fail(nullptr, SN_EINVAL, "sn_create_grid: n or L is NULL");
+  if (dtype != SN_C64 && dtype != SN_C128)
+    return fail(nullptr, SN_EINVAL, "sn_create_grid: dtype must be SN_C64 or SN_C128");
+  for (int a = 0; a < ndim; ++a) {
+    if (!is_pow2_in_range(n[a])) {
+      if (n[a] > 1024 && (n[a] & (n[a] - 1)) == 0)
+        return fail(nullptr, SN_ENOTSUP, "sn_create_grid: n > 1024 is not supported");
+      return fail(nullptr, SN_EINVAL, "sn_create_grid: each n must be a power of two in [8, 1024]");
+    }
+    if (!(L[a] > 0.0) || !std::isfinite(L[a]))
+      return fail(nullptr, SN_EINVAL, "sn_create_grid: each L must be finite and > 0");
+  }
+  sn_grid g = new sn_grid_s();
+  g->ndim = ndim;
+  g->dtype = dtype;
+  g->cells = 1;
+  for (int a = 0; a < ndim; ++a) {
+    g->n[a] = n[a];
+    g->L[a] = L[a];
+    g->cells *= n[a];
+  }
+  g->kp.coeff_lap = -0.5;
+  g->kp.G = 1.0;
+  g->kp.alpha_Y = 0.0;
+  g->kp.lambda_Y = 1.0;
+  g->kp.g_local = 0.0;
+  g->kp.zero_k0 = 1;
+  g->kp.v_ext = nullptr;
+
+  auto bail = [&](sn_status st) {
+    g_tls_error = g->err;
+    sn_destroy_grid(g);
+    return st;
+  };
+  cudaError_t e;
+  if (cuda_stream) {
+    g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(g, e, "cudaStreamCreate"));
+    g->own_stream = true;
+  }
+  const size_t esz = dtype == SN_C64 ? sizeof(float2) : sizeof(double2);
+  void* p = nullptr;
+  e = cudaMalloc(&p, (size_t)g->cells * esz);
+  if (e != cudaSuccess) return bail(cuda_fail(g, e, "cudaMalloc(psi)"));
+  g->allocs.push_back(p);
+  g->psi = p;
+  e = cudaMemset(g->psi, 0, (size_t)g->cells * esz);
+  if (e != cudaSuccess) return bail(cuda_fail(g, e, "cudaMemset(psi)"));
+  if (dtype == SN_C64) {
+    // half spectrum along the largest possible half axis
+    size_t hs = 0;
+    for (int a = 0; a < ndim; ++a)
+      hs = std::max(hs, (size_t)(n[a] / 2 + 1) * (size_t)(g->cells / n[a]));
+    if ((e = dalloc(g, &g->rhohat, hs)) != cudaSuccess) return bail(cuda_fail(g, e, "cudaMalloc(rhohat)"));
+  }
+  if ((e = dalloc(g, &g->partials, (size_t)kObsBlocks * Q_NUM)) != cudaSuccess)
+    return bail(cuda_fail(g, e, "cudaMalloc(partials)"));
+  if ((e = dalloc(g, &g->obs_out, (size_t)Q_NUM)) != cudaSuccess)
+    return bail(cuda_fail(g, e, "cudaMalloc(obs)"));
+  for (int a = 0; a < ndim; ++a) {
+    const int L2 = log2i(n[a]);
+    if (!g->tw32[L2] && !g->tw64[L2]) {
+      std::vector<double2> tw = twiddles_f64(n[a]);
+      if (tw.empty()) tw.push_back(make_double2(1.0, 0.0));
+      if ((e = upload(g, &g->tw64[L2], tw)) != cudaSuccess) return bail(cuda_fail(g, e, "upload(tw64)"));
+      std::vector<float2> tw32;
+      split_hilo(tw, tw32);
+      if ((e = upload(g, &g->tw32[L2], tw32)) != cudaSuccess)
+        return bail(cuda_fail(g, e, "upload(tw32)"));
+    }
+    std::vector<double> k2(n[a]), kk(n[a]);
+    std::vector<float> k2f(n[a]);
+    for (int j = 0; j < n[a]; ++j) {
+      kk[j] = wavenumber(j, n[a], L[a]);
+      k2[j] = kk[j] * kk[j];
+      k2f[j] = (float)k2[j];
+    }
+    if ((e = upload(g, &g->k2_64[a], k2)) != cudaSuccess) return bail(cuda_fail(g, e, "upload(k2)"));
+    if ((e = upload(g, &g->kax_64[a], kk)) != cudaSuccess) return bail(cuda_fail(g, e, "upload(k)"));
+    if ((e = upload(g, &g->k2_32[a], k2f)) != cudaSuccess) return bail(cuda_fail(g, e, "upload(k2f)"));
+    for (int f = 0; f < 2; ++f) {
+      if (dtype == SN_C64) e = dalloc(g, &g->mult32[a][f], 2 * (size_t)n[a]);
+      else e = dalloc(g, &g->mult64[a][f], (size_t)n[a]);
+      if (e != cudaSuccess) return bail(cuda_fail(g, e, "cudaMalloc(mult)"));
+    }
+  }
+  if ((e = upload(g, &g->zero32, std::vector<float>(1, 0.f))) != cudaSuccess)
+    return bail(cuda_fail(g, e, "upload(zero)"));
+  *out = g;
+  return SN_OK;
+}
+
+sn_status sn_set_kernel(sn_grid g, const sn_kernel* k) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_set_kernel: grid is NULL");
+  if (!k) return fail(g, SN_EINVAL, "sn_set_kernel: kernel is NULL");
+  if (!std::isfinite(k->coeff_lap) || !std::isfinite(k->G) || !std::isfinite(k->alpha_Y) ||
+      !std::isfinite(k->lambda_Y) || !std::isfinite(k->g_local))
+    return fail(g, SN_EINVAL, "sn_set_kernel: parameters must be finite");
+  if (k->alpha_Y != 0.0 && !(k->lambda_Y > 0.0))
+    return fail(g, SN_EINVAL, "sn_set_kernel: lambda_Y must be > 0 when alpha_Y != 0");
+  if (k->zero_k0 != 1) return fail(g, SN_EINVAL, "sn_set_kernel: zero_k0 must be 1");
+  cudaError_t e = cudaStreamSynchronize(g->stream);  // queued steps still read the old vext
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamSynchronize");
+  if (k->v_ext) {
+    std::vector<double> v((size_t)g->cells);
+    e = cudaMemcpy(v.data(), k->v_ext, v.size() * sizeof(double),
+                   k->v_ext_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemcpy(v_ext)");
+    for (double x : v)
+      if (!std::isfinite(x)) return fail(g, SN_EINVAL, "sn_set_kernel: v_ext must be finite");
+    if (g->dtype == SN_C64) {
+      std::vector<float> vf(v.begin(), v.end());
+      if (!g->vext32 && (e = dalloc(g, &g->vext32, vf.size())) != cudaSuccess)
+        return cuda_fail(g, e, "cudaMalloc(vext)");
+      e = cudaMemcpy(g->vext32, vf.data(), vf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && !g->vext64) e = dalloc(g, &g->vext64, v.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->vext64, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemcpy(vext)");
+    g->has_vext = true;
+  } else {
+    g->has_vext = false;
+  }
+  const double oldA = g->kp.coeff_lap;
+  g->kp = *k;
+  g->kp.v_ext = nullptr;
+  if (oldA != k->coeff_lap) g->mult_dt = std::nan("");
+  return SN_OK;
+}
+
+sn_status sn_set_state(sn_grid g, const void* psi, int on_device) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_set_state: grid is NULL");
+  if (!psi) return fail(g, SN_EINVAL, "sn_set_state: psi is NULL");
+  const size_t bytes = (size_t)g->cells * (g->dtype == SN_C64 ? sizeof(float2) : sizeof(double2));
+  cudaError_t e = cudaMemcpyAsync(g->psi, psi, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  g->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return cuda_fail(g, e, "sn_set_state copy");
+  g->step = 0;
+  return SN_OK;
+}
+
+sn_status sn_get_state(sn_grid g, void* psi_out, int on_device) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_get_state: grid is NULL");
+  if (!psi_out) return fail(g, SN_EINVAL, "sn_get_state: psi_out is NULL");
+  const size_t bytes = (size_t)g->cells * (g->dtype == SN_C64 ? sizeof(float2) : sizeof(double2));
+  cudaError_t e = cudaMemcpyAsync(psi_out, g->psi, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  g->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return cuda_fail(g, e, "sn_get_state copy");
+  return SN_OK;
+}
+
+sn_status sn_step(sn_grid g, double dt, int nsteps) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_step: grid is NULL");
+  return do_step(g, dt, nsteps);
+}
+
+sn_status sn_sync(sn_grid g) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_sync: grid is NULL");
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return cuda_fail(g, e, "sn_sync");
+  return SN_OK;
+}
+
+sn_status sn_observables(sn_grid g, sn_obs* out) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_observables: grid is NULL");
+  if (!out) return fail(g, SN_EINVAL, "sn_observables: out is NULL");
+  sn_status st = ensure_f64_scratch(g);
+  if (st != SN_OK) return st;
+  const int d = g->ndim;
+  double2* psi64;
+  if (g->dtype == SN_C64) {
+    psi64 = g->w64a;
+    SN_LAUNCH(g, K_OBS, 24.0 * g->cells,
+              launch_widen_f32_to_f64(reinterpret_cast<const float2*>(g->psi), psi64, g->cells,
+                                      g->stream));
+  } else {
+    psi64 = reinterpret_cast<double2*>(g->psi);
+  }
+  cudaError_t e = cudaMemsetAsync(g->partials, 0, sizeof(double) * kObsBlocks * Q_NUM, g->stream);
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemsetAsync");
+  SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
+            launch_obs_space(psi64, g->has_vext ? g->vext64 : nullptr, g->n, d, g->partials,
+                             g->stream));
+  double2* w = g->w64b;
+  for (int a = 0; a < d; ++a) {
+    e = cudaMemcpyAsync(w, psi64, sizeof(double2) * g->cells, cudaMemcpyDeviceToDevice, g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemcpyAsync");
+    const LineGeom lg = psi_geom(g, a);
+    SN_LAUNCH(g, K_OBS, 32.0 * g->cells,
+              launch_fft_f64(g->n[a], lg.strided, -1, w, lg.outer, lg.inner,
+                             g->tw64[log2i(g->n[a])], g->stream));
+    SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
+              launch_obs_kaxis(w, g->n, d, a, g->kax_64[a], g->partials, g->stream));
+  }
+  SN_LAUNCH(g, K_OBS, 32.0 * g->cells, launch_density_f64(psi64, w, g->cells, g->stream));
+  for (int a = d - 1; a >= 0; --a) {
+    const LineGeom lg = psi_geom(g, a);
+    SN_LAUNCH(g, K_OBS, 32.0 * g->cells,
+              launch_fft_f64(g->n[a], lg.strided, -1, w, lg.outer, lg.inner,
+                             g->tw64[log2i(g->n[a])], g->stream));
+  }
+  const double mu2 = (g->kp.alpha_Y != 0.0) ? 1.0 / (g->kp.lambda_Y * g->kp.lambda_Y) : 1.0;
+  const double cN = kernel_cN(g, 1.0);
+  const double* k2[3] = {g->k2_64[0], g->k2_64[1], g->k2_64[2]};
+  SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
+            launch_obs_green(w, g->n, d, k2, cN, cN * g->kp.alpha_Y, mu2, g->partials, g->stream));
+  SN_LAUNCH(g, K_OBS, 0.0, launch_obs_finish(g->partials, Q_NUM, g->obs_out, g->stream));
+  double q[Q_NUM];
+  e = cudaMemcpyAsync(q, g->obs_out, sizeof(q), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return cuda_fail(g, e, "sn_observables");
+
+  double dV = 1.0;
+  for (int a = 0; a < d; ++a) dV *= g->L[a] / g->n[a];
+  const double N = (double)g->cells;
+  std::memset(out, 0, sizeof(*out));
+  out->mass = dV * q[Q_MASS];
+  double ek = 0.0;
+  for (int a = 0; a < d; ++a) {
+    ek += q[Q_EKIN0 + 2 * a] / g->n[a];
+    out->momentum[a] = dV * q[Q_P0 + 2 * a] / g->n[a];
+    const int a3 = d == 3 ? a : a + 1;
+    out->centroid[a] = g->L[a] / (2.0 * kPi) * std::atan2(q[Q_SX0 + 2 * a3], q[Q_CX0 + 2 * a3]);
+  }
+  out->e_kin = -g->kp.coeff_lap * dV * ek;
+  out->e_pot = 0.5 * dV / N * q[Q_EPOT] + dV * q[Q_VEXT];
+  out->e_nl = 0.5 * g->kp.g_local * dV * q[Q_RHO2];
+  out->e_total = out->e_kin + out->e_pot + out->e_nl;
+  out->step = g->step;
+  for (int i = 0; i < Q_NUM; ++i)
+    if (!std::isfinite(q[i])) return fail(g, SN_ENONFINITE, "sn_observables: state is not finite");
+  return SN_OK;
+}
+
+long long sn_launch_count(sn_grid g) { return g ? g->launches : 0; }
+
+sn_status sn_profile_step(sn_grid g, double dt, int nsteps, double* ms, long long* launches,
+                          double* bytes, int nkinds) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_profile_step: grid is NULL");
+  if (!ms || !launches || !bytes || nkinds < 0)
+    return fail(g, SN_EINVAL, "sn_profile_step: output arrays are NULL");
+  for (int k = 0; k < nkinds; ++k) { ms[k] = 0.0; launches[k] = 0; bytes[k] = 0.0; }
+  // tables first, so that no synchronisation lands between timed launches
+  if (std::isfinite(dt)) {
+    sn_status st0 = ensure_mult_tables(g, dt);
+    if (st0 != SN_OK) return st0;
+  }
+  g->profiling = true;
+  g->prof.clear();
+  sn_status st = do_step(g, dt, nsteps);
+  g->profiling = false;
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  for (const Launch& L : g->prof) {
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, L.e0, L.e1);
+    if (L.kind < nkinds) {
+      ms[L.kind] += t;
+      launches[L.kind] += 1;
+      bytes[L.kind] += L.bytes;
+    }
+    cudaEventDestroy(L.e0);
+    cudaEventDestroy(L.e1);
+  }
+  g->prof.clear();
+  if (st != SN_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(g, e, "sn_profile_step");
+  return SN_OK;
+}
+
+const char* sn_kind_name(int k) {
+  if (k < 0 || k >= K_NUM_KINDS) return nullptr;
+  return kKindNames[k];
+}
+
+void sn_destroy_grid(sn_grid g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (void* p : g->allocs) cudaFree(p);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+}
+
+const char* sn_last_error(sn_grid g) {
+  if (!g) return g_tls_error.c_str();
+  return g->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,278 @@
+// Line-FFT engine shared by every pass kernel of the split-step solver.
+//
+// The symmetric split-step Fourier method (Sec. III) spends its time in DFTs
+// along one grid axis at a time: the kinetic propagator of Eq. 1 factors
+// exactly into one 1D multiplier per axis, and the spectral solve of Eq. 2 is
+// a DFT along every axis.  This header holds the in-register Stockham
+// transform that every pass kernel runs on a batch of lines.
+//
+// Layout contract ("pattern P"): a line of N complex values is owned by
+// T = N / E threads; thread t keeps elements t + T*m (m = 0..E-1) in
+// registers v[m].  Every transform reads pattern P and leaves its result in
+// pattern P with the natural frequency / space index, so a forward transform,
+// a pointwise multiplier and an inverse transform chain without reordering.
+// N = R0 * R1 (at most two Stockham stages); the data crosses shared memory
+// once per transform, between the two stages.  Stage twiddles come from a
+// host-built FP64 table rounded once to the working precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace snfft {
+
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> cscale(cx<R> a, R s) { return {a.re * s, a.im * s}; }
+template <typename R>
+__device__ __forceinline__ cx<R> cconj(cx<R> a) { return {a.re, -a.im}; }
+template <typename R>
+__device__ __forceinline__ R cnorm2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+
+// a * (SIGN * i)
+template <typename R, int SIGN>
+__device__ __forceinline__ cx<R> mul_si(cx<R> a) {
+  if constexpr (SIGN < 0) return {a.im, -a.re};
+  else return {-a.im, a.re};
+}
+
+// a * exp(SIGN * i * theta) with (c, s) = (cos theta, sin theta) given in FP64.
+// In FP32 the constant is carried as a hi + lo pair of floats, so the factor is
+// unimodular to ~1e-15: a single rounded float pair has |w|^2 - 1 of order
+// 1e-8 with a fixed sign (e.g. 2 fl(sqrt(1/2))^2 = 1 - 3.4e-8), which would
+// shrink the norm by the same amount on every butterfly.  Only the products
+// are rounded, and those errors are unbiased.
+template <typename R, int SIGN>
+__device__ __forceinline__ cx<R> rot(cx<R> a, double c, double s) {
+  if constexpr (sizeof(R) == sizeof(float)) {
+    const double ss = SIGN < 0 ? -s : s;
+    const float ch = (float)c, sh = (float)ss;
+    const float cl = (float)(c - (double)ch), sl = (float)(ss - (double)sh);
+    const float ur = a.re * cl - a.im * sl;
+    const float ui = a.re * sl + a.im * cl;
+    return {fmaf(a.re, ch, fmaf(-a.im, sh, ur)), fmaf(a.re, sh, fmaf(a.im, ch, ui))};
+  } else {
+    const R cc = (R)c;
+    const R ss = (R)(SIGN < 0 ? -s : s);
+    return {a.re * cc - a.im * ss, a.re * ss + a.im * cc};
+  }
+}
+
+// a * (wh + wl): product with a factor stored as a hi + lo pair (FP32 path).
+__device__ __forceinline__ cx<float> cmul_hl(cx<float> a, cx<float> wh, cx<float> wl) {
+  const float ur = a.re * wl.re - a.im * wl.im;
+  const float ui = a.re * wl.im + a.im * wl.re;
+  return {fmaf(a.re, wh.re, fmaf(-a.im, wh.im, ur)), fmaf(a.re, wh.im, fmaf(a.im, wh.re, ui))};
+}
+
+// Multiply by table entry idx: FP32 tables hold hi parts at [0, n) and lo parts
+// at [n, 2n); FP64 tables hold the value only.
+template <typename R>
+__device__ __forceinline__ cx<R> tmul(cx<R> a, const cx<R>* tab, int idx, int n) {
+  if constexpr (sizeof(R) == sizeof(float)) {
+    return cmul_hl(a, tab[idx], tab[n + idx]);
+  } else {
+    (void)n;
+    return cmul(a, tab[idx]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small DFTs in registers:  X[q] = sum_r x[r] exp(SIGN 2 pi i r q / RAD)
+// ---------------------------------------------------------------------------
+
+template <typename R, int SIGN>
+__device__ __forceinline__ void dft2(cx<R>* a) {
+  cx<R> t = a[0];
+  a[0] = t + a[1];
+  a[1] = t - a[1];
+}
+
+template <typename R, int SIGN>
+__device__ __forceinline__ void dft4(cx<R>& x0, cx<R>& x1, cx<R>& x2, cx<R>& x3) {
+  const cx<R> t0 = x0 + x2, t1 = x0 - x2, t2 = x1 + x3;
+  const cx<R> t3 = mul_si<R, SIGN>(x1 - x3);
+  x0 = t0 + t2;
+  x2 = t0 - t2;
+  x1 = t1 + t3;
+  x3 = t1 - t3;
+}
+
+constexpr double kC8 = 0.70710678118654752440;   // cos(pi/4)
+constexpr double kC16 = 0.92387953251128675613;  // cos(pi/8)
+constexpr double kS16 = 0.38268343236508977173;  // sin(pi/8)
+
+template <typename R, int SIGN>
+__device__ __forceinline__ void dft8(cx<R>* a) {
+  // radix-2 decimation in time over two 4-point DFTs
+  cx<R> e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  cx<R> o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4<R, SIGN>(e0, e1, e2, e3);
+  dft4<R, SIGN>(o0, o1, o2, o3);
+  o1 = rot<R, SIGN>(o1, kC8, kC8);
+  o2 = mul_si<R, SIGN>(o2);
+  o3 = rot<R, SIGN>(o3, -kC8, kC8);
+  a[0] = e0 + o0; a[4] = e0 - o0;
+  a[1] = e1 + o1; a[5] = e1 - o1;
+  a[2] = e2 + o2; a[6] = e2 - o2;
+  a[3] = e3 + o3; a[7] = e3 - o3;
+}
+
+template <typename R, int SIGN>
+__device__ __forceinline__ void dft16(cx<R>* a) {
+  // 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2
+  cx<R> b[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    cx<R> x0 = a[n2], x1 = a[n2 + 4], x2 = a[n2 + 8], x3 = a[n2 + 12];
+    dft4<R, SIGN>(x0, x1, x2, x3);
+    b[4 * n2 + 0] = x0; b[4 * n2 + 1] = x1; b[4 * n2 + 2] = x2; b[4 * n2 + 3] = x3;
+  }
+  // twiddles W16^(n2 k1)
+  b[5] = rot<R, SIGN>(b[5], kC16, kS16);     // n2=1,k1=1 -> 1
+  b[6] = rot<R, SIGN>(b[6], kC8, kC8);       // 1,2 -> 2
+  b[7] = rot<R, SIGN>(b[7], kS16, kC16);     // 1,3 -> 3
+  b[9] = rot<R, SIGN>(b[9], kC8, kC8);       // 2,1 -> 2
+  b[10] = mul_si<R, SIGN>(b[10]);            // 2,2 -> 4
+  b[11] = rot<R, SIGN>(b[11], -kC8, kC8);    // 2,3 -> 6
+  b[13] = rot<R, SIGN>(b[13], kS16, kC16);   // 3,1 -> 3
+  b[14] = rot<R, SIGN>(b[14], -kC8, kC8);    // 3,2 -> 6
+  b[15] = rot<R, SIGN>(b[15], -kC16, -kS16); // 3,3 -> 9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    cx<R> x0 = b[k1], x1 = b[4 + k1], x2 = b[8 + k1], x3 = b[12 + k1];
+    dft4<R, SIGN>(x0, x1, x2, x3);
+    a[k1] = x0; a[k1 + 4] = x1; a[k1 + 8] = x2; a[k1 + 12] = x3;
+  }
+}
+
+template <typename R, int SIGN>
+__device__ __forceinline__ void dft32(cx<R>* a) {
+  // radix-2 decimation in time over two 16-point DFTs; W32^k = exp(SIGN i pi k / 16)
+  constexpr double C[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613,
+                           0.83146961230254523708, 0.70710678118654752440,
+                           0.55557023301960222474, 0.38268343236508977173,
+                           0.19509032201612826785, 0.0};  // cos(k pi / 16), k = 0..8
+  cx<R> e[16], o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) { e[i] = a[2 * i]; o[i] = a[2 * i + 1]; }
+  dft16<R, SIGN>(e);
+  dft16<R, SIGN>(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    // cos(k pi/16), sin(k pi/16) from the first-octant table
+    const double c = (k <= 8) ? C[k] : -C[16 - k];
+    const double s = (k <= 8) ? C[8 - k] : C[k - 8];
+    cx<R> w = (k == 0) ? o[k] : rot<R, SIGN>(o[k], c, s);
+    a[k] = e[k] + w;
+    a[k + 16] = e[k] - w;
+  }
+}
+
+template <typename R, int SIGN, int RAD>
+__device__ __forceinline__ void dft(cx<R>* a) {
+  if constexpr (RAD == 1) {
+  } else if constexpr (RAD == 2) {
+    dft2<R, SIGN>(a);
+  } else if constexpr (RAD == 4) {
+    dft4<R, SIGN>(a[0], a[1], a[2], a[3]);
+  } else if constexpr (RAD == 8) {
+    dft8<R, SIGN>(a);
+  } else if constexpr (RAD == 16) {
+    dft16<R, SIGN>(a);
+  } else {
+    static_assert(RAD == 32, "unsupported radix");
+    dft32<R, SIGN>(a);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-length plan: E elements per thread, T threads per line, radices R0, R1
+// ---------------------------------------------------------------------------
+
+template <int N>
+struct Plan {
+  static_assert(N >= 8 && N <= 1024 && (N & (N - 1)) == 0, "N must be a power of two in [8,1024]");
+  static constexpr int E = N <= 16 ? N : (N <= 256 ? 16 : 32);
+  static constexpr int T = N / E;
+  static constexpr int R0 = N <= 16 ? N : (N == 32 ? 2 : N == 64 ? 4 : N == 128 ? 8 : N == 256 ? 16 : N == 512 ? 16 : 32);
+  static constexpr int R1 = N / R0;
+  static constexpr int STAGES = (R1 == 1) ? 1 : 2;
+  // padded shared-memory line: one pad slot per 16 elements, odd line stride
+  static constexpr int LS = N + N / 16 + 1;
+  // twiddle table entries: forward second stage (N) + inverse second stage (N)
+  static constexpr int TWN = STAGES == 2 ? 2 * N : 0;
+  // entries held per table in shared memory: FP32 keeps hi and lo parts
+  template <typename R>
+  static constexpr int tw_words() { return sizeof(R) == sizeof(float) ? 2 * TWN : TWN; }
+};
+
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+
+// Twiddle table of length N: entry [r*R0 + j] = exp(-2 pi i j r / N) for the
+// forward second stage (r < R1, j < R0), followed by entry
+// [N + r*R1 + j] = exp(+2 pi i j r / N) for the inverse second stage
+// (r < R0, j < R1).  The FP32 table appends the lo parts of all 2N entries.
+
+// In-place transform of one line held in pattern P.  Every thread of the CTA
+// must call it (it contains __syncthreads); `active` masks the arithmetic and
+// shared-memory traffic of threads whose line is idle in this transform.
+template <typename R, int N, int SIGN>
+__device__ __forceinline__ void line_transform(cx<R> (&v)[Plan<N>::E], cx<R>* line_buf,
+                                               const cx<R>* tw_sm, int t, bool active) {
+  using P = Plan<N>;
+  constexpr int E = P::E, T = P::T;
+  if constexpr (P::STAGES == 1) {
+    if (active) dft<R, SIGN, E>(v);
+    return;
+  } else {
+    constexpr int RA = SIGN < 0 ? P::R0 : P::R1;  // first stage radix (Ns = 1)
+    constexpr int RB = SIGN < 0 ? P::R1 : P::R0;  // second stage radix (Ns = RA)
+    constexpr int UA = E / RA, UB = E / RB;
+    __syncthreads();  // previous readers of line_buf are done
+    if (active) {
+#pragma unroll
+      for (int u = 0; u < UA; ++u) {
+        cx<R> a[RA];
+#pragma unroll
+        for (int r = 0; r < RA; ++r) a[r] = v[u + r * UA];
+        dft<R, SIGN, RA>(a);
+        const int j = t + T * u;
+#pragma unroll
+        for (int q = 0; q < RA; ++q) line_buf[pidx(j * RA + q)] = a[q];
+      }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = line_buf[pidx(t + T * m)];
+      const cx<R>* tw = tw_sm + (SIGN < 0 ? 0 : N);
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = t + T * u;
+        const int jm = j & (RA - 1);
+        cx<R> a[RB];
+        a[0] = v[u];
+#pragma unroll
+        for (int r = 1; r < RB; ++r) a[r] = tmul(v[u + r * UB], tw, r * RA + jm, P::TWN);
+        dft<R, SIGN, RB>(a);
+#pragma unroll
+        for (int q = 0; q < RB; ++q) v[u + q * UB] = a[q];
+      }
+    }
+  }
+}
+
+}  // namespace snfft

@@ -1,0 +1,89 @@
+// Host-side internals of libsn: pass argument blocks, launchers, grid state.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sn.h"
+
+namespace sn {
+
+constexpr int kLinesPerCta = 16;  // lines per CTA in the fused FP32 passes
+
+// Kinds of kernel launch, for per-kind timing and launch counts.
+enum PassKind {
+  K_PSI = 0,        // psi pass: FFT . m . IFFT along one axis
+  K_PSI_NPHASE,     // psi pass with the C2R potential + nonlinear phase prologue
+  K_PSI_DENSITY,    // psi pass with the |psi|^2 R2C epilogue
+  K_RHO_FWD,        // half-spectrum forward FFT along one axis
+  K_RHO_GREEN,      // half-spectrum FFT . K(k) . IFFT along one axis
+  K_RHO_INV,        // half-spectrum inverse FFT along one axis
+  K_F64_FFT,        // plain FP64 step: one axis FFT
+  K_F64_EW,         // plain FP64 step: one elementwise kernel
+  K_OBS,            // observables kernels
+  K_NUM_KINDS
+};
+
+struct PsiPassArgs {
+  float2* psi;
+  long long outer, inner;  // lines = outer * inner; element stride inner (strided) or 1
+  const float2* mult;      // 2N entries: hi then lo parts of exp(i A k^2 tau) / N
+  const float2* tw;        // twiddle table of this N (hi parts, then lo parts)
+  const float2* rh_in;     // NPHASE: half spectrum [N/2+1][lines]
+  const float* vext;       // NPHASE: optional V_ext in psi layout (NULL for none)
+  float h;                 // NPHASE: step h (multiplies V_ext)
+  float gh;                // NPHASE: g * h
+  float2* rh_out;          // DENSITY: half spectrum [N/2+1][lines]
+};
+
+struct RhoPassArgs {
+  float2* data;
+  long long outer, inner;
+  const float2* tw;
+  const float* k2p;  // GREEN: k^2 of the half axis, indexed by plane
+  const float* k2m;  // GREEN: k^2 of the middle axis (or a single 0)
+  const float* k2l;  // GREEN: k^2 of the line axis
+  long long mid_n;   // GREEN, contiguous lines: outer = plane * mid_n + mid
+  float cN, cY, mu2; // GREEN: K = cN/k2 + cY/(k2 + mu2), zero at k2 = 0
+};
+
+enum PsiVariant { PSI_PLAIN = 0, PSI_NPHASE = 1, PSI_DENSITY = 2 };
+enum RhoOp { RHO_FWD = 0, RHO_GREEN = 1, RHO_INV = 2 };
+
+cudaError_t launch_psi_pass_f32(int N, bool strided, int variant, const PsiPassArgs& a,
+                                cudaStream_t s);
+cudaError_t launch_rho_pass_f32(int N, bool strided, int op, const RhoPassArgs& a,
+                                cudaStream_t s);
+
+// ---- plain FP64 path -------------------------------------------------------
+cudaError_t launch_fft_f64(int N, bool strided, int sign, double2* data, long long outer,
+                           long long inner, const double2* tw, cudaStream_t s);
+cudaError_t launch_mult_kinetic_f64(double2* psi, const int* n, int ndim, const double2* const* m,
+                                    cudaStream_t s);
+cudaError_t launch_density_f64(const double2* psi, double2* w, long long cells, cudaStream_t s);
+cudaError_t launch_green_f64(double2* w, const int* n, int ndim, const double* const* k2,
+                             double cN, double cY, double mu2, cudaStream_t s);
+cudaError_t launch_phase_f64(double2* psi, const double2* w, const double* vext, double h,
+                             double gh, long long cells, cudaStream_t s);
+cudaError_t launch_widen_f32_to_f64(const float2* in, double2* out, long long cells,
+                                    cudaStream_t s);
+
+// ---- observables (FP64) ----------------------------------------------------
+enum ObsQ {
+  Q_MASS = 0, Q_RHO2, Q_VEXT, Q_CX0, Q_SX0, Q_CX1, Q_SX1, Q_CX2, Q_SX2,
+  Q_EKIN0, Q_P0, Q_EKIN1, Q_P1, Q_EKIN2, Q_P2, Q_EPOT, Q_NUM
+};
+constexpr int kObsBlocks = 592;  // 4 x 148 SMs
+cudaError_t launch_obs_space(const double2* psi, const double* vext, const int* n, int ndim,
+                             double* partials, cudaStream_t s);
+cudaError_t launch_obs_kaxis(const double2* fa, const int* n, int ndim, int axis,
+                             const double* kax, double* partials, cudaStream_t s);
+cudaError_t launch_obs_green(const double2* rhohat, const int* n, int ndim,
+                             const double* const* k2, double cN, double cY, double mu2,
+                             double* partials, cudaStream_t s);
+cudaError_t launch_obs_finish(const double* partials, int nq, double* out, cudaStream_t s);
+
+}  // namespace sn

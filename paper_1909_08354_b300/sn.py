@@ -1,0 +1,261 @@
+"""ctypes binding of libsn (include/sn.h), argument marshalling only.
+
+Every function here has the name of the C entry point it calls and forwards
+to it; the numerical work happens in the CUDA library.  Arrays may be numpy
+arrays or CPU torch tensors (host memory, pinned or not) or CUDA torch tensors
+(device memory).  Loading fails loudly if libsn.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsn.so")
+
+SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+SN_C64, SN_C128 = 0, 1
+_STATUS = {0: "SN_OK", -1: "SN_EINVAL", -2: "SN_ENOMEM", -3: "SN_ECUDA", -4: "SN_ETIMEOUT",
+           -5: "SN_ENONFINITE", -6: "SN_ENOTSUP"}
+
+
+class SnKernel(ctypes.Structure):
+    _fields_ = [("coeff_lap", ctypes.c_double), ("G", ctypes.c_double),
+                ("alpha_Y", ctypes.c_double), ("lambda_Y", ctypes.c_double),
+                ("g_local", ctypes.c_double), ("zero_k0", ctypes.c_int),
+                ("v_ext", ctypes.c_void_p), ("v_ext_on_device", ctypes.c_int)]
+
+
+class SnObs(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("e_kin", ctypes.c_double),
+                ("e_pot", ctypes.c_double), ("e_nl", ctypes.c_double),
+                ("e_total", ctypes.c_double), ("centroid", ctypes.c_double * 3),
+                ("momentum", ctypes.c_double * 3), ("step", ctypes.c_longlong)]
+
+
+class SNError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/sn.h
+_SIGNATURES = [
+    ("sn_create_grid", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_int, ctypes.c_void_p]),
+    ("sn_set_kernel", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SnKernel)]),
+    ("sn_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("sn_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("sn_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
+    ("sn_observables", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SnObs)]),
+    ("sn_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("sn_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("sn_profile_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    ("sn_kind_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("sn_destroy_grid", None, [ctypes.c_void_p]),
+    ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+]
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsn.so once; raise if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run `python -m paper_1909_08354_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(g, status: int):
+    if status != SN_OK:
+        msg = lib().sn_last_error(g).decode(errors="replace")
+        raise SNError(status, msg)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _array_ptr(x, dtype: int, count: int, writable: bool = False):
+    """(pointer, on_device, keepalive) for a psi buffer of `count` complex values."""
+    want = np.complex64 if dtype == SN_C64 else np.complex128
+    if _is_torch(x):
+        import torch
+        tdt = torch.complex64 if dtype == SN_C64 else torch.complex128
+        if x.dtype != tdt or not x.is_contiguous() or x.numel() != count:
+            raise ValueError(f"expected a contiguous {tdt} tensor of {count} elements")
+        return x.data_ptr(), 1 if x.is_cuda else 0, x
+    a = x if writable else np.ascontiguousarray(x, dtype=want)
+    if a.dtype != want or not a.flags["C_CONTIGUOUS"] or a.size != count:
+        raise ValueError(f"expected a C-contiguous {np.dtype(want)} array of {count} elements")
+    return a.ctypes.data, 0, a
+
+
+# ----------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ----------------------------------------------------------------------------
+
+def sn_create_grid(n: Sequence[int], L: Sequence[float], dtype: int = SN_C64, stream=None):
+    """Create a grid; returns the opaque handle (an int).  `stream` is a
+    cudaStream_t as an int (e.g. torch.cuda.current_stream().cuda_stream) or None."""
+    nd = len(n)
+    h = ctypes.c_void_p()
+    na = (ctypes.c_int * nd)(*[int(v) for v in n])
+    La = (ctypes.c_double * nd)(*[float(v) for v in L])
+    st = lib().sn_create_grid(ctypes.byref(h), nd, na, La, int(dtype),
+                              ctypes.c_void_p(stream) if stream else None)
+    _check(None, st)
+    return h.value
+
+
+def sn_set_kernel(g, coeff_lap=-0.5, G=1.0, alpha_Y=0.0, lambda_Y=1.0, g_local=0.0,
+                  v_ext=None, zero_k0=1):
+    keep = None
+    k = SnKernel(coeff_lap, G, alpha_Y, lambda_Y, g_local, zero_k0, None, 0)
+    if v_ext is not None:
+        if _is_torch(v_ext):
+            import torch
+            keep = v_ext.to(torch.float64).contiguous()
+            k.v_ext = keep.data_ptr()
+            k.v_ext_on_device = 1 if keep.is_cuda else 0
+        else:
+            keep = np.ascontiguousarray(v_ext, dtype=np.float64)
+            k.v_ext = keep.ctypes.data
+    _check(g, lib().sn_set_kernel(g, ctypes.byref(k)))
+    del keep
+
+
+def sn_set_state(g, psi, dtype: int, count: int):
+    p, dev, keep = _array_ptr(psi, dtype, count)
+    _check(g, lib().sn_set_state(g, p, dev))
+    del keep
+
+
+def sn_get_state(g, out, dtype: int, count: int):
+    p, dev, keep = _array_ptr(out, dtype, count, writable=True)
+    _check(g, lib().sn_get_state(g, p, dev))
+    return out
+
+
+def sn_step(g, dt: float, nsteps: int):
+    _check(g, lib().sn_step(g, float(dt), int(nsteps)))
+
+
+def sn_observables(g) -> dict:
+    o = SnObs()
+    _check(g, lib().sn_observables(g, ctypes.byref(o)))
+    return dict(mass=o.mass, e_kin=o.e_kin, e_pot=o.e_pot, e_nl=o.e_nl, e_total=o.e_total,
+                centroid=list(o.centroid), momentum=list(o.momentum), step=o.step)
+
+
+def sn_sync(g):
+    _check(g, lib().sn_sync(g))
+
+
+def sn_launch_count(g) -> int:
+    return int(lib().sn_launch_count(g))
+
+
+def sn_kind_names():
+    names = []
+    while True:
+        s = lib().sn_kind_name(len(names))
+        if s is None:
+            return names
+        names.append(s.decode())
+
+
+def sn_profile_step(g, dt: float, nsteps: int) -> dict:
+    names = sn_kind_names()
+    k = len(names)
+    ms = (ctypes.c_double * k)()
+    ln = (ctypes.c_longlong * k)()
+    by = (ctypes.c_double * k)()
+    _check(g, lib().sn_profile_step(g, float(dt), int(nsteps), ms, ln, by, k))
+    return {names[i]: dict(ms=ms[i], launches=int(ln[i]), bytes=by[i]) for i in range(k)}
+
+
+def sn_destroy_grid(g):
+    if g:
+        lib().sn_destroy_grid(g)
+
+
+def sn_last_error(g=None) -> str:
+    return lib().sn_last_error(g).decode(errors="replace")
+
+
+# ----------------------------------------------------------------------------
+# Convenience object over the same calls
+# ----------------------------------------------------------------------------
+
+class Grid:
+    """Owns one sn_grid handle."""
+
+    def __init__(self, n: Sequence[int], L: Sequence[float], dtype: str = "c64", stream=None):
+        self.n = tuple(int(v) for v in n)
+        self.L = tuple(float(v) for v in L)
+        self.dtype = SN_C64 if dtype in ("c64", "complex64", SN_C64) else SN_C128
+        self.cells = int(np.prod(self.n))
+        self.h = sn_create_grid(self.n, self.L, self.dtype, stream)
+
+    @property
+    def np_dtype(self):
+        return np.complex64 if self.dtype == SN_C64 else np.complex128
+
+    def set_kernel(self, **kw):
+        sn_set_kernel(self.h, **kw)
+
+    def set_state(self, psi):
+        sn_set_state(self.h, psi, self.dtype, self.cells)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.n, dtype=self.np_dtype)
+        return sn_get_state(self.h, out, self.dtype, self.cells)
+
+    def step(self, dt: float, nsteps: int = 1):
+        sn_step(self.h, dt, nsteps)
+
+    def observables(self) -> dict:
+        return sn_observables(self.h)
+
+    def sync(self):
+        sn_sync(self.h)
+
+    def launch_count(self) -> int:
+        return sn_launch_count(self.h)
+
+    def profile_step(self, dt: float, nsteps: int) -> dict:
+        return sn_profile_step(self.h, dt, nsteps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sn_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

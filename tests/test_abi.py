@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every entry point of include/sn.h (CPU only).
+
+No compute call is made here: without a GPU only argument validation (which
+returns before any CUDA call) can run.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1909_08354_b300 import sn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sn.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sn_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["sn_create_grid", "sn_set_kernel", "sn_set_state", "sn_get_state", "sn_step",
+                     "sn_observables", "sn_destroy_grid", "sn_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(sn.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_symbol():
+    wrapped = {name for name, _, _ in sn._SIGNATURES}
+    assert set(declared_functions()) <= wrapped
+
+
+@pytest.mark.parametrize("n,L", [((8, 12), (1.0, 1.0)), ((4, 8), (1.0, 1.0)),
+                                 ((8, 8, 8, 8), (1.0,) * 4), ((16, 16), (1.0, -1.0)),
+                                 ((16, 16), (1.0, float("nan"))), ((8,), (1.0,))])
+def test_invalid_grids_are_rejected_before_any_cuda_call(n, L):
+    with pytest.raises(sn.SNError) as e:
+        sn.sn_create_grid(n, L)
+    assert e.value.status == sn.SN_EINVAL
+    assert "sn_create_grid" in sn.sn_last_error(None)
+
+
+def test_oversized_axis_is_not_supported():
+    with pytest.raises(sn.SNError) as e:
+        sn.sn_create_grid((2048, 8), (1.0, 1.0))
+    assert e.value.status == sn.SN_ENOTSUP
+
+
+def test_null_handles_are_rejected():
+    L = sn.lib()
+    assert L.sn_step(None, 0.1, 1) == sn.SN_EINVAL
+    assert L.sn_set_state(None, None, 0) == sn.SN_EINVAL
+    assert L.sn_observables(None, None) == sn.SN_EINVAL
+    assert L.sn_launch_count(None) == 0
+    L.sn_destroy_grid(None)
+    assert sn.sn_kind_names()[0] == "psi_pass"

@@ -1,0 +1,252 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle, element by element.
+
+Bars (per symmetric split step, Sec. III, from the same input state):
+  * complex128 grids (plain FP64 step): rel-L2 <= 1e-12;
+  * complex64 grids (fused FP32 passes): rel-L2 <= 1e-6.
+k merged steps are held to k times the per-step bar.  Observables are FP64
+reductions and are held to 1e-10 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from paper_1909_08354_b300 import sn
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = {"c64": 1e-6, "c128": 1e-12}
+
+
+def kernel_kw(kp):
+    return dict(coeff_lap=kp.coeff_lap, G=kp.G, alpha_Y=kp.alpha_Y, lambda_Y=kp.lambda_Y,
+                g_local=kp.g_local)
+
+
+def gpu_run(psi, L, kw, dtype, dt, nsteps, calls=1, v_ext=None):
+    g = sn.Grid(psi.shape, L, dtype)
+    try:
+        g.set_kernel(**kw, v_ext=v_ext)
+        g.set_state(np.ascontiguousarray(psi, dtype=g.np_dtype))
+        for _ in range(calls):
+            g.step(dt, nsteps)
+        return g.get_state()
+    finally:
+        g.close()
+
+
+def oracle_run(psi, L, kw, dt, nsteps, v_ext=None):
+    return O.evolve(psi.astype(np.complex128), dt, nsteps, L, v_ext=v_ext, **kw)
+
+
+SHAPES_2D = [(8, 8), (8, 16), (32, 8), (64, 128), (128, 128), (256, 32), (16, 512), (1024, 16)]
+SHAPES_3D = [(8, 8, 8), (8, 16, 32), (32, 16, 8), (16, 32, 64), (64, 64, 64), (32, 8, 256),
+             (16, 128, 16)]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("shape", SHAPES_2D + SHAPES_3D)
+def test_one_step_matches_oracle(shape, dtype):
+    w = W.random_small(shape, seed=sum(shape) + len(shape))
+    psi = w.psi0().astype(np.complex64 if dtype == "c64" else np.complex128)
+    kw = kernel_kw(w.kernel)
+    dt = 0.02
+    out = gpu_run(psi, w.L, kw, dtype, dt, 1)
+    ref = oracle_run(psi, w.L, kw, dt, 1)
+    err = O.rel_l2(out, ref)
+    assert err <= STEP_TOL[dtype], err
+    # the potential and the local term are not negligible in this case
+    free = oracle_run(psi, w.L, dict(kw, G=0.0, g_local=0.0), dt, 1)
+    assert O.rel_l2(free, ref) > 1e3 * STEP_TOL["c64"]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("shape", [(32, 64), (128, 16), (8, 32, 16), (32, 32, 32), (16, 8, 64)])
+def test_merged_steps_match_oracle(shape, dtype):
+    """sn_step(h, 5) merges the interior half steps; both axis orders occur."""
+    w = W.random_small(shape, seed=77 + sum(shape))
+    psi = w.psi0().astype(np.complex64 if dtype == "c64" else np.complex128)
+    kw = kernel_kw(w.kernel)
+    out = gpu_run(psi, w.L, kw, dtype, 0.03, 5)
+    ref = oracle_run(psi, w.L, kw, 0.03, 5)
+    assert O.rel_l2(out, ref) <= 5 * STEP_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_external_potential(dtype):
+    w = W.random_small((16, 32, 8), seed=5)
+    psi = w.psi0().astype(np.complex64 if dtype == "c64" else np.complex128)
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(w.n)
+    kw = kernel_kw(w.kernel)
+    out = gpu_run(psi, w.L, kw, dtype, 0.05, 3, v_ext=v)
+    ref = oracle_run(psi, w.L, kw, 0.05, 3, v_ext=v)
+    assert O.rel_l2(out, ref) <= 3 * STEP_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("shape", [(64, 32), (16, 32, 8)])
+def test_observables_match_oracle(shape, dtype):
+    w = W.random_small(shape, seed=11)
+    psi = w.psi0().astype(np.complex64 if dtype == "c64" else np.complex128)
+    kw = kernel_kw(w.kernel)
+    v = np.random.default_rng(1).standard_normal(w.n) * 0.1
+    g = sn.Grid(shape, w.L, dtype)
+    g.set_kernel(**kw, v_ext=v)
+    g.set_state(psi)
+    got = g.observables()
+    g.close()
+    ref = O.observables(psi.astype(np.complex128), w.L, v_ext=v, **kw)
+    for key in ["mass", "e_kin", "e_pot", "e_nl", "e_total"]:
+        assert abs(got[key] - ref[key]) <= 1e-10 * max(1.0, abs(ref[key])), key
+    for a in range(len(shape)):
+        assert abs(got["centroid"][a] - ref["centroid"][a]) <= 1e-10 * w.L[a]
+        assert abs(got["momentum"][a] - ref["momentum"][a]) <= 1e-10 * max(1.0, ref["mass"])
+
+
+@pytest.mark.parametrize("dtype,tol", [("c64", 2e-6), ("c128", 1e-13)])
+def test_time_reversal(dtype, tol):
+    w = W.random_small((32, 16, 64), seed=21)
+    psi = w.psi0().astype(np.complex64 if dtype == "c64" else np.complex128)
+    g = sn.Grid(w.n, w.L, dtype)
+    g.set_kernel(**kernel_kw(w.kernel))
+    g.set_state(psi)
+    g.step(0.04, 3)
+    g.step(-0.04, 3)
+    back = g.get_state()
+    g.close()
+    assert O.rel_l2(back, psi) <= tol
+
+
+def test_zero_steps_and_zero_dt():
+    w = W.random_small((16, 16, 16), seed=2)
+    psi = w.psi0().astype(np.complex64)
+    g = sn.Grid(w.n, w.L, "c64")
+    g.set_kernel(**kernel_kw(w.kernel))
+    g.set_state(psi)
+    n0 = g.launch_count()
+    g.step(0.1, 0)
+    assert g.launch_count() == n0
+    assert np.array_equal(g.get_state(), psi)
+    g.step(0.0, 2)
+    assert O.rel_l2(g.get_state(), psi) <= 1e-6
+    g.close()
+
+
+def test_launch_count_per_step():
+    g = sn.Grid((32, 32, 32), (10.0,) * 3, "c64")
+    g.step(0.01, 10)
+    # 6 passes per merged step plus the 3 closing psi passes
+    assert g.launch_count() == 6 * 10 + 3
+    g.close()
+    g = sn.Grid((32, 32), (10.0,) * 2, "c64")
+    g.step(0.01, 10)
+    assert g.launch_count() == 3 * 10 + 2
+    g.close()
+
+
+def test_device_pointers_and_torch_stream():
+    torch = pytest.importorskip("torch")
+    w = W.random_small((32, 64), seed=9)
+    psi = w.psi0().astype(np.complex64)
+    s = torch.cuda.Stream()
+    g = sn.Grid(w.n, w.L, "c64", stream=s.cuda_stream)
+    g.set_kernel(**kernel_kw(w.kernel))
+    dev = torch.from_numpy(psi).cuda()
+    torch.cuda.synchronize()
+    g.set_state(dev)
+    g.step(0.02, 3)
+    out = torch.empty_like(dev)
+    g.get_state(out)
+    g.sync()
+    host = gpu_run(psi, w.L, kernel_kw(w.kernel), "c64", 0.02, 3)
+    assert np.array_equal(out.cpu().numpy(), host)
+    g.close()
+
+
+def test_nonfinite_state_is_reported():
+    g = sn.Grid((16, 16), (5.0, 5.0), "c64")
+    psi = np.ones((16, 16), np.complex64)
+    psi[3, 4] = np.nan
+    g.set_state(psi)
+    g.step(0.01, 1)
+    with pytest.raises(sn.SNError) as e:
+        g.observables()
+    assert e.value.status == sn.SN_ENONFINITE
+    g.close()
+
+
+def test_bad_arguments_on_a_live_grid():
+    g = sn.Grid((16, 16), (5.0, 5.0), "c64")
+    with pytest.raises(sn.SNError) as e:
+        g.step(float("nan"), 1)
+    assert e.value.status == sn.SN_EINVAL
+    with pytest.raises(sn.SNError):
+        g.step(0.1, -1)
+    with pytest.raises(sn.SNError):
+        g.set_kernel(alpha_Y=0.5, lambda_Y=0.0)
+    with pytest.raises(sn.SNError):
+        g.set_kernel(zero_k0=0)
+    g.close()
+
+
+# ----------------------------------------------------------------------------
+# The workloads at their own sizes
+# ----------------------------------------------------------------------------
+
+def test_centred_gaussian_2d_128_c128_200_steps():
+    """2D Newtonian collapse, 128^2, L=20, h=1e-3, 200 steps with observables every step."""
+    w = W.centred_gaussian_2d()
+    psi = w.psi0()
+    kw = kernel_kw(w.kernel)
+    g = sn.Grid(w.n, w.L, "c128")
+    g.set_kernel(**kw)
+    g.set_state(psi)
+    masses, energies = [], []
+    for _ in range(w.nsteps):
+        g.step(w.dt, 1)
+        o = g.observables()
+        masses.append(o["mass"])
+        energies.append(o["e_total"])
+    out = g.get_state()
+    g.close()
+    ref = oracle_run(psi, w.L, kw, w.dt, w.nsteps)
+    assert O.rel_l2(out, ref) <= 1e-10
+    m0 = O.observables(psi, w.L, **kw)["mass"]
+    assert max(abs(m / m0 - 1) for m in masses) <= 1e-12
+    ref_obs = O.observables(ref, w.L, **kw)
+    assert abs(energies[-1] - ref_obs["e_total"]) <= 1e-10 * abs(ref_obs["e_total"])
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_head_on_collision_3d_128_one_step(dtype):
+    w = W.head_on_collision_3d()
+    psi = w.psi0().astype(np.complex64 if dtype == "c64" else np.complex128)
+    kw = kernel_kw(w.kernel)
+    out = gpu_run(psi, w.L, kw, dtype, w.dt, 1)
+    ref = oracle_run(psi, w.L, kw, w.dt, 1)
+    assert O.rel_l2(out, ref) <= STEP_TOL[dtype]
+
+
+def test_nbody_3d_256_c64_one_step_vs_oracle():
+    """The benchmarked workload at full size (256^3, complex64), one step, same launch path."""
+    w = W.nbody_3d()
+    psi = w.psi0().astype(np.complex64)
+    kw = kernel_kw(w.kernel)
+    out = gpu_run(psi, w.L, kw, "c64", w.dt, 1)
+    ref = oracle_run(psi, w.L, kw, w.dt, 1)
+    assert O.rel_l2(out, ref) <= STEP_TOL["c64"]
+
+
+@pytest.mark.parametrize("alpha_Y", [0.0, 0.1, 0.5])
+def test_nbody_3d_256_mass_drift_1000_steps(alpha_Y):
+    w = W.nbody_3d(alpha_Y=alpha_Y)
+    g = sn.Grid(w.n, w.L, "c64")
+    g.set_kernel(**kernel_kw(w.kernel))
+    g.set_state(w.psi0().astype(np.complex64))
+    m0 = g.observables()["mass"]
+    g.step(w.dt, w.nsteps)
+    o = g.observables()
+    g.close()
+    assert abs(o["mass"] / m0 - 1) <= 1e-5
+    assert o["step"] == w.nsteps
