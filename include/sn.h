@@ -134,6 +134,39 @@ sn_status sn_profile_step(sn_grid g, double dt, int nsteps, double* ms, long lon
 /* Name of kernel kind k, or NULL past the last kind. */
 const char* sn_kind_name(int k);
 
+/* Largest ny and nx accepted by sn_step_2d_noalloc. */
+#define SN_NOALLOC_MAX_N 512
+
+/* Allocation-free variant of the fused FP32 step for 2D complex64 grids.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code whose device memory is owned in full by
+ * another allocator (a framework's caching pool, a fixed arena), or code that
+ * runs where an allocation's latency or possible failure is not acceptable.
+ *
+ * psi: device pointer to ny*nx complex64 values (interleaved re, im, C order,
+ * x fastest), advanced in place by nsteps merged split steps of size dt with
+ * the same passes and tables as sn_step on an SN_C64 grid (the results agree
+ * to FP32 rounding).  Ly, Lx: box lengths.  k: as for sn_set_kernel, with
+ * v_ext == NULL.  cuda_stream: the stream to queue on (NULL: legacy default).
+ *
+ * No device memory is allocated or freed: the working memory (the potential's
+ * half spectrum and the per-call tables, about 1.1 MB) is one file-scope
+ * static device array of fixed size, which every GPU that loads the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  All calls share the
+ * array, so calls whose work overlaps on the GPU (e.g. on two streams) race
+ * and give wrong results; serialise them.  Each call rewrites the tables it
+ * uses, and the half spectrum is always written before it is read.  The table
+ * upload copies from host memory on cuda_stream and waits for the stream's
+ * earlier work; the steps themselves are queued asynchronously.
+ *
+ * Errors (message in sn_last_error(NULL)): SN_ENOTSUP if ny or nx exceeds
+ * SN_NOALLOC_MAX_N or v_ext is given; SN_EINVAL for other bad arguments;
+ * SN_ECUDA if a CUDA call fails. */
+sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, double Lx,
+                             const sn_kernel* k, double dt, int nsteps, void* cuda_stream);
+
 /* Free the grid and its device memory (waits for its queued work). */
 void sn_destroy_grid(sn_grid g);
 

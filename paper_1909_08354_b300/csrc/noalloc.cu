@@ -1,0 +1,227 @@
+// sn_step_2d_noalloc: the fused FP32 split step for 2D complex64 grids that
+// allocates no device memory.
+//
+// Some callers cannot call cudaMalloc: code whose device memory is owned in
+// full by another allocator (a framework's caching pool, a fixed arena handed
+// out at start-up), or code running where an allocation's latency or its
+// possible failure is not acceptable (a real-time loop, a plugin or callback
+// that must not grow the process's footprint).  This entry point serves them:
+// the caller passes psi in device memory, and every piece of working memory
+// the step needs (the potential's half spectrum and the FP64-built tables) lives
+// in one file-scope static __device__ array of fixed size.  Every GPU that
+// loads the library holds that array until the process exits.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "sn.h"
+#include "sn_internal.h"
+
+using namespace sn;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxN = SN_NOALLOC_MAX_N;  // per axis
+
+// Carving of the scratch array, in float2 units, each region 256-byte aligned.
+constexpr size_t align32(size_t words) { return (words + 31) / 32 * 32; }
+constexpr size_t kRhoWords = align32((size_t)(kMaxN / 2 + 1) * kMaxN);  // half spectrum
+constexpr size_t kTwWords = align32(4 * (size_t)kMaxN);    // twiddles (hi, lo) of one axis
+constexpr size_t kMultWords = align32(2 * (size_t)kMaxN);  // one kinetic table (hi, lo)
+constexpr size_t kK2Words = align32((size_t)kMaxN / 2 + 1);  // k^2 floats of one axis
+constexpr size_t kOffTw = kRhoWords;
+constexpr size_t kOffMult = kOffTw + 2 * kTwWords;
+constexpr size_t kOffK2 = kOffMult + 4 * kMultWords;
+constexpr size_t kOffZero = kOffK2 + 2 * kK2Words;
+constexpr size_t kScratchWords = kOffZero + 32;
+
+static __device__ __align__(256) float2 sn_noalloc_scratch[kScratchWords];
+
+constexpr int kMaxDevices = 64;
+float2* g_scratch_ptr[kMaxDevices] = {};  // device address of the array, per device
+
+sn_status fail(sn_status st, const char* m) {
+  set_thread_error(m);
+  return st;
+}
+
+sn_status cuda_fail(cudaError_t e, const char* what) {
+  char m[256];
+  std::snprintf(m, sizeof(m), "sn_step_2d_noalloc: %s: %s", what, cudaGetErrorString(e));
+  return fail(SN_ECUDA, m);
+}
+
+double wavenumber(int j, int n, double L) { return 2.0 * kPi / L * (double)(j < n / 2 ? j : j - n); }
+
+// hi = fl(x), lo = fl(x - hi) for n complex values: hi parts to out[0, n), lo parts to out[n, 2n)
+void split_hilo(const double2* v, int n, float2* out) {
+  for (int i = 0; i < n; ++i) {
+    const float hr = (float)v[i].x, hi = (float)v[i].y;
+    out[i] = make_float2(hr, hi);
+    out[n + i] = make_float2((float)(v[i].x - (double)hr), (float)(v[i].y - (double)hi));
+  }
+}
+
+// Stage twiddles of the two-stage plan for length N (N <= 512): 2N entries, none for N <= 16.
+int twiddles(int N, double2* tw) {
+  if (N <= 16) return 0;
+  const int R0 = N == 32 ? 2 : N == 64 ? 4 : N == 128 ? 8 : 16;
+  const int R1 = N / R0;
+  for (int r = 0; r < R1; ++r)
+    for (int j = 0; j < R0; ++j) {
+      const double a = -2.0 * kPi * (double)((long long)j * r % N) / N;
+      tw[r * R0 + j] = make_double2(std::cos(a), std::sin(a));
+    }
+  for (int r = 0; r < R0; ++r)
+    for (int j = 0; j < R1; ++j) {
+      const double a = 2.0 * kPi * (double)((long long)j * r % N) / N;
+      tw[N + r * R1 + j] = make_double2(std::cos(a), std::sin(a));
+    }
+  return 2 * N;
+}
+
+// Once per device, with that device current: the device address of the array.
+sn_status scratch_for_current_device(float2** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(SN_ENOTSUP, "sn_step_2d_noalloc: device index too large");
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, sn_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    g_scratch_ptr[dev] = reinterpret_cast<float2*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return SN_OK;
+}
+
+}  // namespace
+
+extern "C" sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, double Lx,
+                                        const sn_kernel* k, double dt, int nsteps,
+                                        void* cuda_stream) {
+  if (!psi) return fail(SN_EINVAL, "sn_step_2d_noalloc: psi is NULL");
+  if (!k) return fail(SN_EINVAL, "sn_step_2d_noalloc: kernel is NULL");
+  const int n[2] = {ny, nx};
+  const double L[2] = {Ly, Lx};
+  for (int a = 0; a < 2; ++a) {
+    if (n[a] < 8 || (n[a] & (n[a] - 1)) != 0)
+      return fail(SN_EINVAL, "sn_step_2d_noalloc: ny and nx must be powers of two >= 8");
+    if (n[a] > kMaxN)
+      return fail(SN_ENOTSUP,
+                  "sn_step_2d_noalloc: ny and nx must be <= SN_NOALLOC_MAX_N (the static scratch "
+                  "array holds the half spectrum of a 512 x 512 grid)");
+    if (!(L[a] > 0.0) || !std::isfinite(L[a]))
+      return fail(SN_EINVAL, "sn_step_2d_noalloc: Ly and Lx must be finite and > 0");
+  }
+  if (!std::isfinite(dt)) return fail(SN_EINVAL, "sn_step_2d_noalloc: dt must be finite");
+  if (nsteps < 0) return fail(SN_EINVAL, "sn_step_2d_noalloc: nsteps must be >= 0");
+  if (!std::isfinite(k->coeff_lap) || !std::isfinite(k->G) || !std::isfinite(k->alpha_Y) ||
+      !std::isfinite(k->lambda_Y) || !std::isfinite(k->g_local))
+    return fail(SN_EINVAL, "sn_step_2d_noalloc: kernel parameters must be finite");
+  if (k->alpha_Y != 0.0 && !(k->lambda_Y > 0.0))
+    return fail(SN_EINVAL, "sn_step_2d_noalloc: lambda_Y must be > 0 when alpha_Y != 0");
+  if (k->zero_k0 != 1) return fail(SN_EINVAL, "sn_step_2d_noalloc: zero_k0 must be 1");
+  if (k->v_ext) return fail(SN_ENOTSUP, "sn_step_2d_noalloc: v_ext is not supported");
+  if (nsteps == 0) return SN_OK;
+
+  float2* s = nullptr;
+  sn_status st = scratch_for_current_device(&s);
+  if (st != SN_OK) return st;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  float2* rhohat = s;
+  float2* tw[2] = {s + kOffTw, s + kOffTw + kTwWords};
+  float2* mult[2][2] = {{s + kOffMult, s + kOffMult + kMultWords},
+                        {s + kOffMult + 2 * kMultWords, s + kOffMult + 3 * kMultWords}};
+  float* k2[2] = {reinterpret_cast<float*>(s + kOffK2),
+                  reinterpret_cast<float*>(s + kOffK2 + kK2Words)};
+  float* zero = reinterpret_cast<float*>(s + kOffZero);
+
+  // Tables for this call (the array keeps whatever an earlier call left).  They
+  // are built on the stack; copies from pageable host memory are staged before
+  // cudaMemcpyAsync returns, so the stack buffers may go out of scope.
+  cudaError_t e = cudaSuccess;
+  double2 t64[2 * kMaxN];
+  float2 t32[4 * kMaxN];
+  float kf[kMaxN];
+  for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
+    const int ntw = twiddles(n[a], t64);
+    if (ntw > 0) {
+      split_hilo(t64, ntw, t32);
+      e = cudaMemcpyAsync(tw[a], t32, 2 * ntw * sizeof(float2), cudaMemcpyHostToDevice, stream);
+    }
+    for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
+      const double tau = f ? dt : 0.5 * dt;
+      for (int j = 0; j < n[a]; ++j) {
+        const double kk = wavenumber(j, n[a], L[a]);
+        const double th = k->coeff_lap * kk * kk * tau;
+        t64[j] = make_double2(std::cos(th) / n[a], std::sin(th) / n[a]);
+      }
+      split_hilo(t64, n[a], t32);
+      e = cudaMemcpyAsync(mult[a][f], t32, 2 * n[a] * sizeof(float2), cudaMemcpyHostToDevice, stream);
+    }
+    if (e == cudaSuccess) {
+      for (int j = 0; j < n[a]; ++j) {
+        const double kk = wavenumber(j, n[a], L[a]);
+        kf[j] = (float)(kk * kk);
+      }
+      e = cudaMemcpyAsync(k2[a], kf, n[a] * sizeof(float), cudaMemcpyHostToDevice, stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(zero, 0, sizeof(float), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "table upload");
+
+  const long long cells = (long long)ny * nx;
+  const double mu2 = (k->alpha_Y != 0.0) ? 1.0 / (k->lambda_Y * k->lambda_Y) : 1.0;
+  const double cN = -4.0 * kPi * k->G * dt / (double)cells;
+  float2* p = reinterpret_cast<float2*>(psi);
+  // Merged Strang steps: round r applies the kinetic factor along both axes
+  // (half step in the first and last round), with the nonlinear phase in the
+  // first pass of every round after the first and the density in the last
+  // pass of every round before the last; the axis order flips every round.
+  for (int r = 0; r <= nsteps; ++r) {
+    const bool odd = (r & 1) != 0;
+    const int full = (r == 0 || r == nsteps) ? 0 : 1;
+    const int order[2] = {odd ? 1 : 0, odd ? 0 : 1};
+    for (int i = 0; i < 2; ++i) {
+      const int a = order[i];
+      int variant = PSI_PLAIN;
+      if (i == 0 && r > 0) variant = PSI_NPHASE;
+      if (i == 1 && r < nsteps) variant = PSI_DENSITY;
+      PsiPassArgs pa{};
+      pa.psi = p;
+      pa.outer = a == 0 ? 1 : ny;
+      pa.inner = a == 0 ? nx : 1;
+      pa.mult = mult[a][full];
+      pa.tw = tw[a];
+      pa.rh_in = rhohat;
+      pa.vext = nullptr;
+      pa.h = (float)dt;
+      pa.gh = (float)(k->g_local * dt);
+      pa.rh_out = rhohat;
+      e = launch_psi_pass_f32(n[a], a == 0, variant, pa, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "psi pass launch");
+    }
+    if (r < nsteps) {
+      const int h = order[1], c = order[0];
+      RhoPassArgs ra{};
+      ra.data = rhohat;
+      ra.outer = n[h] / 2 + 1;
+      ra.inner = 1;
+      ra.tw = tw[c];
+      ra.k2p = k2[h];
+      ra.k2m = zero;
+      ra.k2l = k2[c];
+      ra.mid_n = 1;
+      ra.cN = (float)cN;
+      ra.cY = (float)(cN * k->alpha_Y);
+      ra.mu2 = (float)mu2;
+      e = launch_rho_pass_f32(n[c], false, RHO_GREEN, ra, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "green pass launch");
+    }
+  }
+  return SN_OK;
+}

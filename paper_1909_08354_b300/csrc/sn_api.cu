@@ -90,6 +90,8 @@ struct Launch {
 
 }  // namespace
 
+void sn::set_thread_error(const char* msg) { g_tls_error = msg; }
+
 struct sn_grid_s {
   int ndim = 0;
   int n[3] = {1, 1, 1};

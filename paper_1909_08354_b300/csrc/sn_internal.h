@@ -50,6 +50,9 @@ struct RhoPassArgs {
   float cN, cY, mu2; // GREEN: K = cN/k2 + cY/(k2 + mu2), zero at k2 = 0
 };
 
+// Message returned by sn_last_error(NULL) on this thread.
+void set_thread_error(const char* msg);
+
 enum PsiVariant { PSI_PLAIN = 0, PSI_NPHASE = 1, PSI_DENSITY = 2 };
 enum RhoOp { RHO_FWD = 0, RHO_GREEN = 1, RHO_INV = 2 };
 

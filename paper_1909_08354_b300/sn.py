@@ -61,6 +61,10 @@ _SIGNATURES = [
                                        ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     ("sn_kind_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("sn_step_2d_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(SnKernel), ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_void_p]),
     ("sn_destroy_grid", None, [ctypes.c_void_p]),
     ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -188,6 +192,21 @@ def sn_profile_step(g, dt: float, nsteps: int) -> dict:
     by = (ctypes.c_double * k)()
     _check(g, lib().sn_profile_step(g, float(dt), int(nsteps), ms, ln, by, k))
     return {names[i]: dict(ms=ms[i], launches=int(ln[i]), bytes=by[i]) for i in range(k)}
+
+
+def sn_step_2d_noalloc(psi, L, dt: float, nsteps: int, coeff_lap=-0.5, G=1.0, alpha_Y=0.0,
+                       lambda_Y=1.0, g_local=0.0, stream=None):
+    """In-place steps of a 2D complex64 CUDA tensor psi (ny, nx) without device
+    allocation (see sn_step_2d_noalloc in include/sn.h)."""
+    import torch
+    if not (_is_torch(psi) and psi.is_cuda and psi.dtype == torch.complex64 and psi.dim() == 2
+            and psi.is_contiguous()):
+        raise ValueError("psi must be a contiguous 2D complex64 CUDA tensor")
+    k = SnKernel(coeff_lap, G, alpha_Y, lambda_Y, g_local, 1, None, 0)
+    st = lib().sn_step_2d_noalloc(psi.data_ptr(), psi.shape[0], psi.shape[1], float(L[0]),
+                                  float(L[1]), ctypes.byref(k), float(dt), int(nsteps),
+                                  ctypes.c_void_p(stream) if stream else None)
+    _check(None, st)
 
 
 def sn_destroy_grid(g):
