@@ -36,12 +36,15 @@ import workloads as W  # noqa: E402
 METRIC = "cell-steps/s at 256^3: fast forms vs plain FP64 GPU step at <=1e-6 rel-L2/step"
 UNIT = "cell-steps/s"
 BYTES_PER_CELL_STEP = 80.0  # algorithmic HBM bytes of the fused 3D complex64 step
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch from the ncu capture
+# summarised in profiles/fused_step_nbody_256.md; set to None when the kernel changes
+NCU_TRAFFIC = {"psi_pass_nphase": 201.93e6 + 78.38e6}
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=256)
@@ -217,7 +220,7 @@ def main():
     mass_drift = abs(g.observables()["mass"] / m0 - 1.0)
 
     # ---- per-kernel timing (CUDA events around every launch, same steps)
-    prof = g.profile_step(w.dt, args.steps)
+    prof = g.profile_step(w.dt, min(args.steps, 200))
     kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
     dom = max(kinds, key=lambda k: kinds[k]["ms"])
     peak, peak_src = measured_peaks()
@@ -286,7 +289,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "working set 202 MB > 126 MB L2; no flush"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom),
                          "peak_source": peak_src,
                          "step_achieved": step_gbs, "step_frac": step_gbs / peak,
                          "bytes_per_cell_step": BYTES_PER_CELL_STEP},

@@ -13,6 +13,12 @@
 // C2R axis of the next P1.  The half spectrum is stored with the half axis
 // slowest, [k_h][line], so both the R2C store of P3 and the C2R load of P1 are
 // coalesced over 16 neighbouring lines.
+//
+// The kernels are persistent: a CTA loads its tables once and walks tiles of
+// 16 lines with a stride of gridDim.x.  While it transforms one tile, the next
+// tile's psi is already in flight into registers and (P1) the next tile's half
+// spectrum into shared memory through cp.async, so the HBM stream does not
+// wait for the arithmetic.
 #include "sn_fft.cuh"
 #include "sn_internal.h"
 
@@ -24,12 +30,16 @@ namespace {
 constexpr int LPB = kLinesPerCta;
 constexpr int TSTR = LPB + 1;  // padded row of the [k][line] staging tile
 
-// CTAs per SM the register allocation must allow: 1024 resident threads for
-// lines up to 256 points (memory-level parallelism for the HBM stream).
+template <int N>
+constexpr int cta_threads() {
+  return LPB * Plan<N>::T;
+}
+
+// Resident CTAs per SM the register allocation is sized for: 512 threads per
+// SM, i.e. up to 128 registers, room for the prefetched tile.
 template <int N>
 constexpr int min_ctas() {
-  constexpr int threads = LPB * Plan<N>::T;
-  constexpr int want = 1024 / threads;
+  constexpr int want = 512 / cta_threads<N>();
   return want < 1 ? 1 : (want > 16 ? 16 : want);
 }
 
@@ -39,10 +49,79 @@ __device__ __forceinline__ cx<float> ldc(const float2* p) {
 }
 __device__ __forceinline__ void stc(float2* p, cx<float> v) { *p = make_float2(v.re, v.im); }
 
-// shared memory: twiddles (hi, lo), kinetic factors (hi, lo), line buffers
-template <int N>
+// 8-byte asynchronous global->shared copy; src_bytes = 0 writes zeros without reading.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = pred ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+// Tiles of 16 lines: contiguous lines (stride 1) are 16 consecutive `outer`
+// indices; strided lines are 16 consecutive `inner` indices of one `outer`.
+template <bool STRIDED>
+struct Tiles {
+  long long outer, inner, tiles_i, count;
+  __device__ Tiles(long long o, long long i) : outer(o), inner(i) {
+    tiles_i = STRIDED ? (i + LPB - 1) / LPB : 1;
+    count = STRIDED ? o * tiles_i : (o + LPB - 1) / LPB;
+  }
+  // first line id, number of valid lines, element offset of line l, and its (o, i)
+  __device__ void at(long long tau, int l, int N, long long& line0, int& nvalid, size_t& base,
+                     long long& o, long long& i) const {
+    if (STRIDED) {
+      o = tau / tiles_i;
+      const long long i0 = (tau - o * tiles_i) * LPB;
+      nvalid = (int)min((long long)LPB, inner - i0);
+      line0 = o * inner + i0;
+      i = i0 + l;
+      base = (size_t)o * N * inner + i;
+    } else {
+      const long long o0 = tau * LPB;
+      nvalid = (int)min((long long)LPB, outer - o0);
+      line0 = o0;
+      o = o0 + l;
+      i = 0;
+      base = (size_t)o * N;
+    }
+  }
+};
+
+template <int E, int T>
+__device__ __forceinline__ void load_line(cx<float> (&v)[E], const float2* p, unsigned ustride,
+                                          int t, bool valid) {
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    cx<float> z = {0.f, 0.f};
+    if (valid) z = ldc(p + (unsigned)(t + T * m) * ustride);
+    v[m] = z;
+  }
+}
+
+template <int E, int T>
+__device__ __forceinline__ void store_line(const cx<float> (&v)[E], float2* p, unsigned ustride,
+                                           int t, bool valid) {
+  asm volatile("" : "+l"(p));  // recompute the store addresses instead of keeping them live
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) stc(p + (unsigned)(t + T * m) * ustride, v[m]);
+  }
+}
+
+// shared memory: twiddles (hi, lo), kinetic factors (hi, lo), line buffers,
+// and for P1 two staging tiles of the half spectrum
+template <int N, int VARIANT>
 constexpr size_t psi_smem_bytes() {
-  return (size_t)(2 * Plan<N>::TWN + 2 * N + LPB * Plan<N>::LS) * sizeof(cx<float>);
+  return (size_t)(2 * Plan<N>::TWN + 2 * N + LPB * Plan<N>::LS +
+                  (VARIANT == PSI_NPHASE ? 2 * (N / 2 + 1) * TSTR : 0)) *
+         sizeof(cx<float>);
 }
 template <int N>
 constexpr size_t rho_smem_bytes() {
@@ -50,193 +129,216 @@ constexpr size_t rho_smem_bytes() {
 }
 
 template <int N, bool STRIDED, int VARIANT>
-__global__ void __launch_bounds__(LPB * Plan<N>::T, min_ctas<N>())
+__global__ void __launch_bounds__(cta_threads<N>(), min_ctas<N>())
 psi_pass_kernel(PsiPassArgs a) {
   using P = Plan<N>;
   constexpr int E = P::E, T = P::T, NT = LPB * T, LS = P::LS, H = N / 2 + 1;
   constexpr bool NPHASE = VARIANT == PSI_NPHASE;
   constexpr bool DENSITY = VARIANT == PSI_DENSITY;
+  constexpr bool PF = E <= 16;  // register prefetch of the next tile (lines up to 256)
+  constexpr bool WL = !STRIDED && T <= 32;  // a contiguous line lives in one warp
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw_sm = reinterpret_cast<cx<float>*>(smem_raw);
   cx<float>* mult_sm = tw_sm + 2 * P::TWN;
   cx<float>* lines = mult_sm + 2 * N;
+  cx<float>* rstage = lines + LPB * LS;  // P1: two [H][TSTR] tiles
 
   const int tid = threadIdx.x;
   const int l = STRIDED ? (tid % LPB) : (tid / T);
   const int t = STRIDED ? (tid / LPB) : (tid % T);
-
-  long long line0;  // line id of CTA line 0 (lines are numbered o * inner + i)
-  int nvalid;
-  size_t base, stride;
-  if constexpr (STRIDED) {
-    const long long o = blockIdx.y, i0 = (long long)blockIdx.x * LPB;
-    nvalid = (int)min((long long)LPB, a.inner - i0);
-    line0 = o * a.inner + i0;
-    base = (size_t)o * N * a.inner + i0 + l;
-    stride = a.inner;
-  } else {
-    const long long o0 = (long long)blockIdx.x * LPB;
-    nvalid = (int)min((long long)LPB, a.outer - o0);
-    line0 = o0;
-    base = (size_t)(o0 + l) * N;
-    stride = 1;
-  }
-  const bool valid = l < nvalid;
+  const Tiles<STRIDED> tiles(a.outer, a.inner);
   const size_t nlines = (size_t)(a.outer * a.inner);
-  // element m of my line sits at pl + (t + T m) * stride; offsets fit in 32 bits
-  // (a grid holds at most 2^30 cells)
-  float2* pl = a.psi + base;
-  const unsigned ustride = (unsigned)stride;
+  // element m of a line sits at base + (t + T m) * stride; offsets fit in 32
+  // bits (a grid holds at most 2^30 cells)
+  const unsigned ustride = STRIDED ? (unsigned)a.inner : 1u;
 
   for (int k = tid; k < 2 * P::TWN; k += NT) tw_sm[k] = ldc(a.tw + k);
   for (int k = tid; k < 2 * N; k += NT) mult_sm[k] = ldc(a.mult + k);
 
-  cx<float> v[E];
-  float vph[E];
-  (void)vph;
-
-  if constexpr (NPHASE) {
-    // ---- potential: C2R inverse FFT of the half spectrum of lines (l, l + 8)
-    cx<float>* tile = lines;
+  // P1: stage the [k][line] half-spectrum tile of tile tau into shared memory
+  auto stage_rho = [&](cx<float>* dst, long long tau) {
+    long long line0, o, i;
+    int nvalid;
+    size_t base;
+    tiles.at(tau, 0, N, line0, nvalid, base, o, i);
     for (int idx = tid; idx < H * LPB; idx += NT) {
       const int ll = idx % LPB, k = idx / LPB;
-      cx<float> z = {0.f, 0.f};
-      if (ll < nvalid) z = ldc(a.rh_in + (size_t)k * nlines + line0 + ll);
-      tile[k * TSTR + ll] = z;
+      const bool ok = ll < nvalid;
+      cp_async8(dst + k * TSTR + ll, a.rh_in + (ok ? (size_t)k * nlines + line0 + ll : 0), ok);
     }
-    __syncthreads();
-    const bool pa = l < LPB / 2;
-    if (pa) {
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int k = t + T * m;
-        cx<float> A, B;
-        if (k <= N / 2) {
-          A = tile[k * TSTR + l];
-          B = tile[k * TSTR + l + LPB / 2];
-          if (k == 0 || k == N / 2) { A.im = 0.f; B.im = 0.f; }
-        } else {
-          A = cconj(tile[(N - k) * TSTR + l]);
-          B = cconj(tile[(N - k) * TSTR + l + LPB / 2]);
-        }
-        v[m] = {A.re - B.im, A.im + B.re};  // A + i B
-      }
-    }
-    __syncthreads();  // tile consumed before the line buffers are reused
-    line_transform<float, N, +1>(v, lines + l * LS, tw_sm, t, pa);
-    __syncthreads();
-    if (pa) {
-      float* up = reinterpret_cast<float*>(lines + (l + LPB / 2) * LS);
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        vph[m] = v[m].re;
-        up[t + T * m] = v[m].im;
-      }
-    }
-    __syncthreads();
-    if (!pa) {
-      const float* up = reinterpret_cast<const float*>(lines + l * LS);
-#pragma unroll
-      for (int m = 0; m < E; ++m) vph[m] = up[t + T * m];
-    }
-  }
-  __syncthreads();  // tables visible; V exchange buffers read
+  };
 
-  // ---- load psi (pattern P), nonlinear phase
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    cx<float> z = {0.f, 0.f};
-    if (valid) z = ldc(pl + (unsigned)(t + T * m) * ustride);
-    v[m] = z;
+  cx<float> vn[E];
+  long long tau = blockIdx.x;
+  if (tau < tiles.count) {
+    long long line0, o, i;
+    int nvalid;
+    size_t base;
+    tiles.at(tau, l, N, line0, nvalid, base, o, i);
+    if constexpr (PF) load_line<E, T>(vn, a.psi + base, ustride, t, l < nvalid);
+    if constexpr (NPHASE) stage_rho(rstage, tau);
   }
-  if constexpr (NPHASE) {
-    const float* vx = a.vext != nullptr ? a.vext + base : nullptr;
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      float th = vph[m] + a.gh * cnorm2(v[m]);
-      if (vx != nullptr && valid) th += vx[(unsigned)(t + T * m) * ustride] * a.h;
-      float s, c;
-      sincosf(th, &s, &c);
-      // one Newton step towards |(c, s)| = 1 removes the modulus error of the pair
-      const float f = fmaf(-0.5f, fmaf(c, c, fmaf(s, s, -1.f)), 1.f);
-      c *= f;
-      s *= f;
-      v[m] = {v[m].re * c + v[m].im * s, v[m].im * c - v[m].re * s};  // v * exp(-i th)
-    }
-  }
+  if constexpr (NPHASE) cp_async_commit();
+  __syncthreads();  // tables
 
-  // ---- kinetic factor along this axis
-  line_transform<float, N, -1>(v, lines + l * LS, tw_sm, t, true);
-#pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = cmul_hl(v[m], mult_sm[t + T * m], mult_sm[N + t + T * m]);
-  line_transform<float, N, +1>(v, lines + l * LS, tw_sm, t, true);
+  for (int it = 0; tau < tiles.count; ++it, tau += gridDim.x) {
+    long long line0, o, i;
+    int nvalid;
+    size_t base;
+    tiles.at(tau, l, N, line0, nvalid, base, o, i);
+    const bool valid = l < nvalid;
+    const long long taun = tau + gridDim.x;
+    cx<float> v[E];
+    float vph[E];
+    (void)vph;
 
-  asm volatile("" : "+l"(pl));  // recompute store addresses instead of keeping 16 live
-  if (valid) {
+    if constexpr (NPHASE) {
+      // ---- potential: C2R inverse FFT of the half spectrum of lines (l, l + 8)
+      const cx<float>* tile = rstage + (it & 1) * (H * TSTR);
+      if (taun < tiles.count) stage_rho(rstage + ((it + 1) & 1) * (H * TSTR), taun);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      const bool pa = l < LPB / 2;
+      if (pa) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) stc(pl + (unsigned)(t + T * m) * ustride, v[m]);
-  }
-
-  if constexpr (DENSITY) {
-    // ---- rho = |psi|^2, R2C along this axis, two real lines per complex FFT
-    float rho[E];
-#pragma unroll
-    for (int m = 0; m < E; ++m) rho[m] = valid ? cnorm2(v[m]) : 0.f;
-    const bool pa = l < LPB / 2;
-    __syncthreads();
-    if (!pa) {
-      float* b = reinterpret_cast<float*>(lines + l * LS);
-#pragma unroll
-      for (int m = 0; m < E; ++m) b[t + T * m] = rho[m];
-    }
-    __syncthreads();
-    if (pa) {
-      const float* b = reinterpret_cast<const float*>(lines + (l + LPB / 2) * LS);
-#pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = {rho[m], b[t + T * m]};
-    }
-    line_transform<float, N, -1>(v, lines + l * LS, tw_sm, t, pa);
-    __syncthreads();
-    if (pa) {
-#pragma unroll
-      for (int q = 0; q < E; ++q) lines[l * LS + pidx(t + T * q)] = v[q];
-    }
-    __syncthreads();
-    constexpr int NH = (H + T - 1) / T;
-    cx<float> hs[NH];
-    const cx<float>* zb = lines + (l % (LPB / 2)) * LS;
-#pragma unroll
-    for (int i = 0; i < NH; ++i) {
-      const int k = t + T * i;
-      hs[i] = {0.f, 0.f};
-      if (k < H) {
-        const cx<float> zk = zb[pidx(k)];
-        const cx<float> zn = cconj(zb[pidx((N - k) & (N - 1))]);
-        if (pa) {
-          hs[i] = cscale(zk + zn, 0.5f);
-        } else {
-          const cx<float> d = zk - zn;
-          hs[i] = {0.5f * d.im, -0.5f * d.re};  // (zk - conj z_{N-k}) / (2i)
+        for (int m = 0; m < E; ++m) {
+          const int k = t + T * m;
+          cx<float> A, B;
+          if (k <= N / 2) {
+            A = tile[k * TSTR + l];
+            B = tile[k * TSTR + l + LPB / 2];
+            if (k == 0 || k == N / 2) { A.im = 0.f; B.im = 0.f; }
+          } else {
+            A = cconj(tile[(N - k) * TSTR + l]);
+            B = cconj(tile[(N - k) * TSTR + l + LPB / 2]);
+          }
+          v[m] = {A.re - B.im, A.im + B.re};  // A + i B
         }
       }
-    }
-    __syncthreads();
-    cx<float>* tile = lines;
+      line_transform<float, N, +1, WL>(v, lines + l * LS, tw_sm, t, pa);
+      __syncthreads();
+      if (pa) {
+        float* up = reinterpret_cast<float*>(lines + (l + LPB / 2) * LS);
 #pragma unroll
-    for (int i = 0; i < NH; ++i) {
-      const int k = t + T * i;
-      if (k < H) tile[k * TSTR + l] = hs[i];
+        for (int m = 0; m < E; ++m) {
+          vph[m] = v[m].re;
+          up[t + T * m] = v[m].im;
+        }
+      }
+      __syncthreads();
+      if (!pa) {
+        const float* up = reinterpret_cast<const float*>(lines + l * LS);
+#pragma unroll
+        for (int m = 0; m < E; ++m) vph[m] = up[t + T * m];
+      }
     }
-    __syncthreads();
-    for (int idx = tid; idx < H * LPB; idx += NT) {
-      const int ll = idx % LPB, k = idx / LPB;
-      if (ll < nvalid) stc(a.rh_out + (size_t)k * nlines + line0 + ll, tile[k * TSTR + ll]);
+
+    // ---- this tile's psi (loaded one iteration ago); start the next tile's load
+    if constexpr (PF) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = vn[m];
+      if (taun < tiles.count) {
+        long long line0n, on, in;
+        int nvalidn;
+        size_t basen;
+        tiles.at(taun, l, N, line0n, nvalidn, basen, on, in);
+        load_line<E, T>(vn, a.psi + basen, ustride, t, l < nvalidn);
+      }
+    } else {
+      load_line<E, T>(v, a.psi + base, ustride, t, valid);
     }
+
+    if constexpr (NPHASE) {
+      const float* vx = a.vext != nullptr ? a.vext + base : nullptr;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        float th = vph[m] + a.gh * cnorm2(v[m]);
+        if (vx != nullptr && valid) th += vx[(unsigned)(t + T * m) * ustride] * a.h;
+        // reduce to [-pi, pi] (two-part 2 pi), then the SFU sine and cosine
+        const float kq = rintf(th * 0.159154943091895336f);
+        float r = fmaf(-kq, 6.28318548202514648f, th);
+        r = fmaf(-kq, -1.74845553e-7f, r);
+        float s, c;
+        __sincosf(r, &s, &c);
+        // one Newton step towards |(c, s)| = 1 removes the modulus error of the pair
+        const float f = fmaf(-0.5f, fmaf(c, c, fmaf(s, s, -1.f)), 1.f);
+        c *= f;
+        s *= f;
+        v[m] = {v[m].re * c + v[m].im * s, v[m].im * c - v[m].re * s};  // v * exp(-i th)
+      }
+    }
+
+    // ---- kinetic factor along this axis
+    line_transform<float, N, -1, WL>(v, lines + l * LS, tw_sm, t, true);
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = cmul_hl(v[m], mult_sm[t + T * m], mult_sm[N + t + T * m]);
+    line_transform<float, N, +1, WL>(v, lines + l * LS, tw_sm, t, true);
+    store_line<E, T>(v, a.psi + base, ustride, t, valid);
+
+    if constexpr (DENSITY) {
+      // ---- rho = |psi|^2, R2C along this axis, two real lines per complex FFT
+      float rho[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) rho[m] = valid ? cnorm2(v[m]) : 0.f;
+      const bool pa = l < LPB / 2;
+      __syncthreads();
+      if (!pa) {
+        float* b = reinterpret_cast<float*>(lines + l * LS);
+#pragma unroll
+        for (int m = 0; m < E; ++m) b[t + T * m] = rho[m];
+      }
+      __syncthreads();
+      if (pa) {
+        const float* b = reinterpret_cast<const float*>(lines + (l + LPB / 2) * LS);
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = {rho[m], b[t + T * m]};
+      }
+      line_transform<float, N, -1, WL>(v, lines + l * LS, tw_sm, t, pa);
+      __syncthreads();
+      if (pa) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) lines[l * LS + pidx(t + T * q)] = v[q];
+      }
+      __syncthreads();
+      constexpr int NH = (H + T - 1) / T;
+      cx<float> hs[NH];
+      const cx<float>* zb = lines + (l % (LPB / 2)) * LS;
+#pragma unroll
+      for (int q = 0; q < NH; ++q) {
+        const int k = t + T * q;
+        hs[q] = {0.f, 0.f};
+        if (k < H) {
+          const cx<float> zk = zb[pidx(k)];
+          const cx<float> zn = cconj(zb[pidx((N - k) & (N - 1))]);
+          if (pa) {
+            hs[q] = cscale(zk + zn, 0.5f);
+          } else {
+            const cx<float> d = zk - zn;
+            hs[q] = {0.5f * d.im, -0.5f * d.re};  // (zk - conj z_{N-k}) / (2i)
+          }
+        }
+      }
+      __syncthreads();
+      cx<float>* tile = lines;
+#pragma unroll
+      for (int q = 0; q < NH; ++q) {
+        const int k = t + T * q;
+        if (k < H) tile[k * TSTR + l] = hs[q];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < H * LPB; idx += NT) {
+        const int ll = idx % LPB, k = idx / LPB;
+        if (ll < nvalid) stc(a.rh_out + (size_t)k * nlines + line0 + ll, tile[k * TSTR + ll]);
+      }
+    }
+    __syncthreads();  // line buffers and the staging tile are reused next iteration
   }
+  if constexpr (NPHASE) cp_async_wait<0>();
 }
 
 template <int N, bool STRIDED, int OP>
-__global__ void __launch_bounds__(LPB * Plan<N>::T, min_ctas<N>())
+__global__ void __launch_bounds__(cta_threads<N>(), min_ctas<N>())
 rho_pass_kernel(RhoPassArgs a) {
   using P = Plan<N>;
   constexpr int E = P::E, T = P::T, NT = LPB * T, LS = P::LS;
@@ -247,71 +349,103 @@ rho_pass_kernel(RhoPassArgs a) {
   const int tid = threadIdx.x;
   const int l = STRIDED ? (tid % LPB) : (tid / T);
   const int t = STRIDED ? (tid / LPB) : (tid % T);
-  long long o, i;
-  int nvalid;
-  size_t base, stride;
-  if constexpr (STRIDED) {
-    o = blockIdx.y;
-    const long long i0 = (long long)blockIdx.x * LPB;
-    i = i0 + l;
-    nvalid = (int)min((long long)LPB, a.inner - i0);
-    base = (size_t)o * N * a.inner + i;
-    stride = a.inner;
-  } else {
-    const long long o0 = (long long)blockIdx.x * LPB;
-    o = o0 + l;
-    i = 0;
-    nvalid = (int)min((long long)LPB, a.outer - o0);
-    base = (size_t)o * N;
-    stride = 1;
-  }
-  const bool valid = l < nvalid;
-  float2* pl = a.data + base;
-  const unsigned ustride = (unsigned)stride;
+  const Tiles<STRIDED> tiles(a.outer, a.inner);
+  const unsigned ustride = STRIDED ? (unsigned)a.inner : 1u;
+  constexpr bool PF = E <= 16;  // register prefetch of the next tile (lines up to 256)
+  constexpr bool WL = !STRIDED && T <= 32;  // a contiguous line lives in one warp
   for (int k = tid; k < 2 * P::TWN; k += NT) tw_sm[k] = ldc(a.tw + k);
+
+  cx<float> vn[E];
+  long long tau = blockIdx.x;
+  if (PF && tau < tiles.count) {
+    long long line0, o, i;
+    int nvalid;
+    size_t base;
+    tiles.at(tau, l, N, line0, nvalid, base, o, i);
+    load_line<E, T>(vn, a.data + base, ustride, t, l < nvalid);
+  }
   __syncthreads();
 
-  cx<float> v[E];
+  for (; tau < tiles.count; tau += gridDim.x) {
+    long long line0, o, i;
+    int nvalid;
+    size_t base;
+    tiles.at(tau, l, N, line0, nvalid, base, o, i);
+    const bool valid = l < nvalid;
+    cx<float> v[E];
+    if constexpr (PF) {
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    cx<float> z = {0.f, 0.f};
-    if (valid) z = ldc(pl + (unsigned)(t + T * m) * ustride);
-    v[m] = z;
-  }
-  if constexpr (OP == RHO_INV) {
-    line_transform<float, N, +1>(v, lines + l * LS, tw_sm, t, true);
-  } else {
-    line_transform<float, N, -1>(v, lines + l * LS, tw_sm, t, true);
-  }
-  if constexpr (OP == RHO_GREEN) {
-    long long plane, mid;
-    if constexpr (STRIDED) {
-      plane = o;
-      mid = i;
+      for (int m = 0; m < E; ++m) v[m] = vn[m];
+      const long long taun = tau + gridDim.x;
+      if (taun < tiles.count) {
+        long long line0n, on, in;
+        int nvalidn;
+        size_t basen;
+        tiles.at(taun, l, N, line0n, nvalidn, basen, on, in);
+        load_line<E, T>(vn, a.data + basen, ustride, t, l < nvalidn);
+      }
     } else {
-      plane = o / a.mid_n;
-      mid = o - plane * a.mid_n;
+      load_line<E, T>(v, a.data + base, ustride, t, valid);
     }
-    float k2pm = 0.f;
-    if (valid) k2pm = a.k2p[plane] + a.k2m[mid];
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const float k2 = k2pm + a.k2l[t + T * m];
-      const float K = (k2 > 0.f) ? (a.cN / k2 + a.cY / (k2 + a.mu2)) : 0.f;
-      v[m] = cscale(v[m], K);
+    if constexpr (OP == RHO_INV) {
+      line_transform<float, N, +1, WL>(v, lines + l * LS, tw_sm, t, true);
+    } else {
+      line_transform<float, N, -1, WL>(v, lines + l * LS, tw_sm, t, true);
     }
-    line_transform<float, N, +1>(v, lines + l * LS, tw_sm, t, true);
-  }
-  asm volatile("" : "+l"(pl));
-  if (valid) {
+    if constexpr (OP == RHO_GREEN) {
+      long long plane, mid;
+      if constexpr (STRIDED) {
+        plane = o;
+        mid = i;
+      } else {
+        plane = o / a.mid_n;
+        mid = o - plane * a.mid_n;
+      }
+      float k2pm = 0.f;
+      if (valid) k2pm = a.k2p[plane] + a.k2m[mid];
 #pragma unroll
-    for (int m = 0; m < E; ++m) stc(pl + (unsigned)(t + T * m) * ustride, v[m]);
+      for (int m = 0; m < E; ++m) {
+        // K = cN/k2 + cY/(k2 + mu2) over one division; K's relative error of a few
+        // ulp moves the phase V h by far less than the FP32 rounding of psi
+        const float k2 = k2pm + a.k2l[t + T * m];
+        const float den = k2 * (k2 + a.mu2);
+        const float K = (k2 > 0.f) ? __fdividef(fmaf(a.cN, k2 + a.mu2, a.cY * k2), den) : 0.f;
+        v[m] = cscale(v[m], K);
+      }
+      line_transform<float, N, +1, WL>(v, lines + l * LS, tw_sm, t, true);
+    }
+    store_line<E, T>(v, a.data + base, ustride, t, valid);
   }
+}
+
+// Persistent grid: as many CTAs as fit on the device at once, capped by the
+// number of tiles.
+template <typename K>
+unsigned persistent_ctas(K kern, int threads, size_t smem, long long ntiles) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const long long cap = (long long)per_sm * sms;
+  return (unsigned)(ntiles < cap ? ntiles : cap);
+}
+
+template <bool STRIDED>
+long long host_tiles(long long outer, long long inner) {
+  return STRIDED ? outer * ((inner + LPB - 1) / LPB) : (outer + LPB - 1) / LPB;
 }
 
 template <int N, bool STRIDED, int VARIANT>
 cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
-  constexpr size_t smem = psi_smem_bytes<N>();
+  constexpr size_t smem = psi_smem_bytes<N, VARIANT>();
+  constexpr int threads = cta_threads<N>();
   auto kern = psi_pass_kernel<N, STRIDED, VARIANT>;
   static bool attr = false;
   if (!attr) {
@@ -319,17 +453,15 @@ cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 block(LPB * Plan<N>::T);
-  dim3 grid;
-  if (STRIDED) grid = dim3((unsigned)((a.inner + LPB - 1) / LPB), (unsigned)a.outer);
-  else grid = dim3((unsigned)((a.outer + LPB - 1) / LPB));
-  kern<<<grid, block, smem, s>>>(a);
+  const long long ntiles = host_tiles<STRIDED>(a.outer, a.inner);
+  kern<<<persistent_ctas(kern, threads, smem, ntiles), threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int N, bool STRIDED, int OP>
 cudaError_t launch_rho_t(const RhoPassArgs& a, cudaStream_t s) {
   constexpr size_t smem = rho_smem_bytes<N>();
+  constexpr int threads = cta_threads<N>();
   auto kern = rho_pass_kernel<N, STRIDED, OP>;
   static bool attr = false;
   if (!attr) {
@@ -337,11 +469,8 @@ cudaError_t launch_rho_t(const RhoPassArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 block(LPB * Plan<N>::T);
-  dim3 grid;
-  if (STRIDED) grid = dim3((unsigned)((a.inner + LPB - 1) / LPB), (unsigned)a.outer);
-  else grid = dim3((unsigned)((a.outer + LPB - 1) / LPB));
-  kern<<<grid, block, smem, s>>>(a);
+  const long long ntiles = host_tiles<STRIDED>(a.outer, a.inner);
+  kern<<<persistent_ctas(kern, threads, smem, ntiles), threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

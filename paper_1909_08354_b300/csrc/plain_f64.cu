@@ -188,9 +188,11 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NQ], double* pa
   }
 }
 
-__global__ void obs_space_kernel(const double2* psi, const double* vext, Dims d, int ndim,
+// cs_a[j] = (cos, sin)(2 pi x_j / L_a) per axis, padded axes hold a single (1, 0)
+__global__ void obs_space_kernel(const double2* psi, const double* vext, Dims d,
+                                 const double2* cs0, const double2* cs1, const double2* cs2,
                                  double* partials) {
-  // Q_MASS, Q_RHO2, Q_VEXT, then (cos, sin) of 2 pi x_a / L_a per axis a (array order)
+  // Q_MASS, Q_RHO2, Q_VEXT, then (cos, sin) sums per axis (padded 3D order)
   constexpr int NQ = 9;
   double acc[NQ];
 #pragma unroll
@@ -203,18 +205,14 @@ __global__ void obs_space_kernel(const double2* psi, const double* vext, Dims d,
     acc[0] += rho;
     acc[1] += rho * rho;
     if (vext != nullptr) acc[2] += rho * vext[c];
-    // x_j = -L/2 + j L/n  ->  2 pi x_j / L = pi (2 j / n - 1)
-    const long long idx[3] = {i0, i1, i2};
-    const long long nn[3] = {d.n0, d.n1, d.n2};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double s, co;
-      sincospi(2.0 * (double)idx[a] / (double)nn[a] - 1.0, &s, &co);
-      acc[3 + 2 * a] += rho * co;
-      acc[4 + 2 * a] += rho * s;
-    }
+    const double2 a0 = cs0[i0], a1 = cs1[i1], a2 = cs2[i2];
+    acc[3] += rho * a0.x;
+    acc[4] += rho * a0.y;
+    acc[5] += rho * a1.x;
+    acc[6] += rho * a1.y;
+    acc[7] += rho * a2.x;
+    acc[8] += rho * a2.y;
   }
-  (void)ndim;
   block_reduce_store<NQ>(acc, partials, 0);
 }
 
@@ -314,8 +312,13 @@ cudaError_t launch_widen_f32_to_f64(const float2* in, double2* out, long long ce
 }
 
 cudaError_t launch_obs_space(const double2* psi, const double* vext, const int* n, int ndim,
-                             double* partials, cudaStream_t s) {
-  obs_space_kernel<<<kObsBlocks, kEwThreads, 0, s>>>(psi, vext, dims_of(n, ndim), ndim, partials);
+                             const double2* const* cs, const double2* cs_one, double* partials,
+                             cudaStream_t s) {
+  const double2* c0 = ndim == 3 ? cs[0] : cs_one;
+  const double2* c1 = ndim == 3 ? cs[1] : cs[0];
+  const double2* c2 = ndim == 3 ? cs[2] : cs[1];
+  obs_space_kernel<<<kObsBlocks, kEwThreads, 0, s>>>(psi, vext, dims_of(n, ndim), c0, c1, c2,
+                                                     partials);
   return cudaGetLastError();
 }
 

@@ -118,6 +118,8 @@ struct sn_grid_s {
   float* k2_32[3] = {};
   double* k2_64[3] = {};
   double* kax_64[3] = {};
+  double2* cs_64[3] = {};    // (cos, sin)(2 pi x_j / L) per axis, for the centroids
+  double2* cs_one = nullptr; // {(1, 0)} for the padded axis of a 2D grid
   float* zero32 = nullptr;  // a single 0 (k^2 of a missing middle axis)
   // kinetic multipliers [axis][half=0/full=1]: n entries (FP64) or 2n (FP32 hi, lo)
   float2* mult32[3][2] = {};
@@ -533,6 +535,13 @@ sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, 
     }
     if ((e = upload(g, &g->k2_64[a], k2)) != cudaSuccess) return bail(cuda_fail(g, e, "upload(k2)"));
     if ((e = upload(g, &g->kax_64[a], kk)) != cudaSuccess) return bail(cuda_fail(g, e, "upload(k)"));
+    std::vector<double2> cs(n[a]);
+    for (int j = 0; j < n[a]; ++j) {
+      // x_j = -L/2 + j L/n, so 2 pi x_j / L = pi (2 j / n - 1)
+      const double ph = kPi * (2.0 * j / n[a] - 1.0);
+      cs[j] = make_double2(std::cos(ph), std::sin(ph));
+    }
+    if ((e = upload(g, &g->cs_64[a], cs)) != cudaSuccess) return bail(cuda_fail(g, e, "upload(cs)"));
     if ((e = upload(g, &g->k2_32[a], k2f)) != cudaSuccess) return bail(cuda_fail(g, e, "upload(k2f)"));
     for (int f = 0; f < 2; ++f) {
       if (dtype == SN_C64) e = dalloc(g, &g->mult32[a][f], 2 * (size_t)n[a]);
@@ -542,6 +551,8 @@ sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, 
   }
   if ((e = upload(g, &g->zero32, std::vector<float>(1, 0.f))) != cudaSuccess)
     return bail(cuda_fail(g, e, "upload(zero)"));
+  if ((e = upload(g, &g->cs_one, std::vector<double2>(1, make_double2(1.0, 0.0)))) != cudaSuccess)
+    return bail(cuda_fail(g, e, "upload(cs_one)"));
   *out = g;
   return SN_OK;
 }
@@ -640,8 +651,8 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
   cudaError_t e = cudaMemsetAsync(g->partials, 0, sizeof(double) * kObsBlocks * Q_NUM, g->stream);
   if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemsetAsync");
   SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
-            launch_obs_space(psi64, g->has_vext ? g->vext64 : nullptr, g->n, d, g->partials,
-                             g->stream));
+            launch_obs_space(psi64, g->has_vext ? g->vext64 : nullptr, g->n, d, g->cs_64,
+                             g->cs_one, g->partials, g->stream));
   double2* w = g->w64b;
   for (int a = 0; a < d; ++a) {
     e = cudaMemcpyAsync(w, psi64, sizeof(double2) * g->cells, cudaMemcpyDeviceToDevice, g->stream);

@@ -229,7 +229,9 @@ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 // In-place transform of one line held in pattern P.  Every thread of the CTA
 // must call it (it contains __syncthreads); `active` masks the arithmetic and
 // shared-memory traffic of threads whose line is idle in this transform.
-template <typename R, int N, int SIGN>
+// WARP_LOCAL: every line is held by threads of a single warp, so the
+// exchange needs only a warp barrier (all 32 lanes must still call).
+template <typename R, int N, int SIGN, bool WARP_LOCAL = false>
 __device__ __forceinline__ void line_transform(cx<R> (&v)[Plan<N>::E], cx<R>* line_buf,
                                                const cx<R>* tw_sm, int t, bool active) {
   using P = Plan<N>;
@@ -241,7 +243,7 @@ __device__ __forceinline__ void line_transform(cx<R> (&v)[Plan<N>::E], cx<R>* li
     constexpr int RA = SIGN < 0 ? P::R0 : P::R1;  // first stage radix (Ns = 1)
     constexpr int RB = SIGN < 0 ? P::R1 : P::R0;  // second stage radix (Ns = RA)
     constexpr int UA = E / RA, UB = E / RB;
-    __syncthreads();  // previous readers of line_buf are done
+    if (WARP_LOCAL) __syncwarp(); else __syncthreads();  // previous readers of line_buf are done
     if (active) {
 #pragma unroll
       for (int u = 0; u < UA; ++u) {
@@ -254,7 +256,7 @@ __device__ __forceinline__ void line_transform(cx<R> (&v)[Plan<N>::E], cx<R>* li
         for (int q = 0; q < RA; ++q) line_buf[pidx(j * RA + q)] = a[q];
       }
     }
-    __syncthreads();
+    if (WARP_LOCAL) __syncwarp(); else __syncthreads();
     if (active) {
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = line_buf[pidx(t + T * m)];

@@ -80,8 +80,10 @@ enum ObsQ {
   Q_EKIN0, Q_P0, Q_EKIN1, Q_P1, Q_EKIN2, Q_P2, Q_EPOT, Q_NUM
 };
 constexpr int kObsBlocks = 592;  // 4 x 148 SMs
+// cs[a][j] = (cos, sin)(2 pi x_j / L_a) for the ndim axes; cs_one = {(1, 0)}
 cudaError_t launch_obs_space(const double2* psi, const double* vext, const int* n, int ndim,
-                             double* partials, cudaStream_t s);
+                             const double2* const* cs, const double2* cs_one, double* partials,
+                             cudaStream_t s);
 cudaError_t launch_obs_kaxis(const double2* fa, const int* n, int ndim, int axis,
                              const double* kax, double* partials, cudaStream_t s);
 cudaError_t launch_obs_green(const double2* rhohat, const int* n, int ndim,
