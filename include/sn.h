@@ -134,6 +134,46 @@ sn_status sn_profile_step(sn_grid g, double dt, int nsteps, double* ms, long lon
 /* Name of kernel kind k, or NULL past the last kind. */
 const char* sn_kind_name(int k);
 
+/* ---------------------------------------------------------------------------
+ * Batched scan: many independent 2D complex64 problems of uneven size
+ * advanced together (Sec. III step applied to each; e.g. a scan over the
+ * coupling strength and range of the Eq. 9 kernel and over initial
+ * conditions).  Instance i is an n[i] x n[i] periodic grid of box length L[i]
+ * in both axes with its own kernel parameters and time step.  One
+ * sn_step_batch call runs all merged steps of all instances in a single
+ * persistent cooperative launch, captured once into a CUDA graph and replayed
+ * while nsteps is unchanged.
+ *
+ * Inside the launch, work items (round, pass, instance, tile) are taken in a
+ * fixed order, and an item waits for the previous pass of its instance.  Each
+ * wait has a clock-cycle limit (sn_set_batch_wait_limit; about 2 s by default);
+ * when a wait expires the kernel records it and returns, and the next
+ * synchronising call returns SN_ETIMEOUT and leaves the batch state
+ * incomplete.  Batch calls report messages through sn_last_error(NULL).
+ * ------------------------------------------------------------------------- */
+typedef struct sn_batch_s* sn_batch;
+
+/* n[i]: power of two in [8, 1024]; L[i] > 0.  cuda_stream as for sn_create_grid.
+ * States start at zero, kernels at {A=-0.5, G=1, alpha_Y=0, g=0}. */
+sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* L,
+                          void* cuda_stream);
+/* k[count]: per-instance parameters (v_ext must be NULL: SN_ENOTSUP). */
+sn_status sn_set_kernel_batch(sn_batch b, const sn_kernel* k);
+/* Copy instance `index` in or out (n[index]^2 complex64, host or device). */
+sn_status sn_set_state_batch(sn_batch b, int index, const void* psi, int on_device);
+sn_status sn_get_state_batch(sn_batch b, int index, void* psi_out, int on_device);
+/* nsteps merged steps of every instance, instance i with step dt[i]; async. */
+sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps);
+/* Observables of instance `index` (blocks). */
+sn_status sn_observables_batch(sn_batch b, int index, sn_obs* out);
+/* Wait for the batch's work; SN_ETIMEOUT if a dependency wait expired. */
+sn_status sn_batch_sync(sn_batch b);
+/* Clock cycles one dependency wait may spin before it gives up (>= 0). */
+sn_status sn_set_batch_wait_limit(sn_batch b, long long cycles);
+/* Kernel launches of this batch (one per sn_step_batch call). */
+long long sn_batch_launch_count(sn_batch b);
+void sn_destroy_batch(sn_batch b);
+
 /* Largest ny and nx accepted by sn_step_2d_noalloc. */
 #define SN_NOALLOC_MAX_N 512
 

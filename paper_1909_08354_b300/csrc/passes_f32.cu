@@ -21,18 +21,27 @@
 // wait for the arithmetic.
 #include "sn_fft.cuh"
 #include "sn_internal.h"
+#include "tile_ops.cuh"
 
 using namespace snfft;
 
 namespace sn {
 namespace {
 
-constexpr int LPB = kLinesPerCta;
-constexpr int TSTR = LPB + 1;  // padded row of the [k][line] staging tile
+using tile::load_line;
+using tile::store_line;
+
+// Lines per CTA: 16 (a 128-byte row of 16 neighbouring lines for the strided
+// passes); 8 for 1024-point lines, whose tables, line buffers and staging
+// tiles would not fit in shared memory at 16.
+template <int N>
+__host__ __device__ constexpr int lpb() {
+  return N >= 1024 ? kLinesPerCta / 2 : kLinesPerCta;
+}
 
 template <int N>
 constexpr int cta_threads() {
-  return LPB * Plan<N>::T;
+  return lpb<N>() * Plan<N>::T;
 }
 
 // Resident CTAs per SM the register allocation is sized for: 512 threads per
@@ -47,7 +56,6 @@ __device__ __forceinline__ cx<float> ldc(const float2* p) {
   const float2 v = *p;
   return {v.x, v.y};
 }
-__device__ __forceinline__ void stc(float2* p, cx<float> v) { *p = make_float2(v.re, v.im); }
 
 // 8-byte asynchronous global->shared copy; src_bytes = 0 writes zeros without reading.
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
@@ -64,74 +72,24 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
 }
 
-// Tiles of 16 lines: contiguous lines (stride 1) are 16 consecutive `outer`
-// indices; strided lines are 16 consecutive `inner` indices of one `outer`.
-template <bool STRIDED>
-struct Tiles {
-  long long outer, inner, tiles_i, count;
-  __device__ Tiles(long long o, long long i) : outer(o), inner(i) {
-    tiles_i = STRIDED ? (i + LPB - 1) / LPB : 1;
-    count = STRIDED ? o * tiles_i : (o + LPB - 1) / LPB;
-  }
-  // first line id, number of valid lines, element offset of line l, and its (o, i)
-  __device__ void at(long long tau, int l, int N, long long& line0, int& nvalid, size_t& base,
-                     long long& o, long long& i) const {
-    if (STRIDED) {
-      o = tau / tiles_i;
-      const long long i0 = (tau - o * tiles_i) * LPB;
-      nvalid = (int)min((long long)LPB, inner - i0);
-      line0 = o * inner + i0;
-      i = i0 + l;
-      base = (size_t)o * N * inner + i;
-    } else {
-      const long long o0 = tau * LPB;
-      nvalid = (int)min((long long)LPB, outer - o0);
-      line0 = o0;
-      o = o0 + l;
-      i = 0;
-      base = (size_t)o * N;
-    }
-  }
-};
-
-template <int E, int T>
-__device__ __forceinline__ void load_line(cx<float> (&v)[E], const float2* p, unsigned ustride,
-                                          int t, bool valid) {
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    cx<float> z = {0.f, 0.f};
-    if (valid) z = ldc(p + (unsigned)(t + T * m) * ustride);
-    v[m] = z;
-  }
-}
-
-template <int E, int T>
-__device__ __forceinline__ void store_line(const cx<float> (&v)[E], float2* p, unsigned ustride,
-                                           int t, bool valid) {
-  asm volatile("" : "+l"(p));  // recompute the store addresses instead of keeping them live
-  if (valid) {
-#pragma unroll
-    for (int m = 0; m < E; ++m) stc(p + (unsigned)(t + T * m) * ustride, v[m]);
-  }
-}
-
 // shared memory: twiddles (hi, lo), kinetic factors (hi, lo), line buffers,
 // and for P1 two staging tiles of the half spectrum
 template <int N, int VARIANT>
 constexpr size_t psi_smem_bytes() {
-  return (size_t)(2 * Plan<N>::TWN + 2 * N + LPB * Plan<N>::LS +
-                  (VARIANT == PSI_NPHASE ? 2 * (N / 2 + 1) * TSTR : 0)) *
+  return (size_t)(2 * Plan<N>::TWN + 2 * N + lpb<N>() * Plan<N>::LS +
+                  (VARIANT == PSI_NPHASE ? 2 * (N / 2 + 1) * (lpb<N>() + 1) : 0)) *
          sizeof(cx<float>);
 }
 template <int N>
 constexpr size_t rho_smem_bytes() {
-  return (size_t)(2 * Plan<N>::TWN + LPB * Plan<N>::LS) * sizeof(cx<float>);
+  return (size_t)(2 * Plan<N>::TWN + lpb<N>() * Plan<N>::LS) * sizeof(cx<float>);
 }
 
 template <int N, bool STRIDED, int VARIANT>
 __global__ void __launch_bounds__(cta_threads<N>(), min_ctas<N>())
 psi_pass_kernel(PsiPassArgs a) {
   using P = Plan<N>;
+  constexpr int LPB = lpb<N>(), TSTR = LPB + 1;
   constexpr int E = P::E, T = P::T, NT = LPB * T, LS = P::LS, H = N / 2 + 1;
   constexpr bool NPHASE = VARIANT == PSI_NPHASE;
   constexpr bool DENSITY = VARIANT == PSI_DENSITY;
@@ -146,7 +104,7 @@ psi_pass_kernel(PsiPassArgs a) {
   const int tid = threadIdx.x;
   const int l = STRIDED ? (tid % LPB) : (tid / T);
   const int t = STRIDED ? (tid / LPB) : (tid % T);
-  const Tiles<STRIDED> tiles(a.outer, a.inner);
+  const tile::Tiles<LPB, STRIDED> tiles(a.outer, a.inner);
   const size_t nlines = (size_t)(a.outer * a.inner);
   // element m of a line sits at base + (t + T m) * stride; offsets fit in 32
   // bits (a grid holds at most 2^30 cells)
@@ -193,45 +151,11 @@ psi_pass_kernel(PsiPassArgs a) {
     (void)vph;
 
     if constexpr (NPHASE) {
-      // ---- potential: C2R inverse FFT of the half spectrum of lines (l, l + 8)
-      const cx<float>* tile = rstage + (it & 1) * (H * TSTR);
       if (taun < tiles.count) stage_rho(rstage + ((it + 1) & 1) * (H * TSTR), taun);
       cp_async_commit();
       cp_async_wait<1>();
       __syncthreads();
-      const bool pa = l < LPB / 2;
-      if (pa) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-          const int k = t + T * m;
-          cx<float> A, B;
-          if (k <= N / 2) {
-            A = tile[k * TSTR + l];
-            B = tile[k * TSTR + l + LPB / 2];
-            if (k == 0 || k == N / 2) { A.im = 0.f; B.im = 0.f; }
-          } else {
-            A = cconj(tile[(N - k) * TSTR + l]);
-            B = cconj(tile[(N - k) * TSTR + l + LPB / 2]);
-          }
-          v[m] = {A.re - B.im, A.im + B.re};  // A + i B
-        }
-      }
-      line_transform<float, N, +1, WL>(v, lines + l * LS, tw_sm, t, pa);
-      __syncthreads();
-      if (pa) {
-        float* up = reinterpret_cast<float*>(lines + (l + LPB / 2) * LS);
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-          vph[m] = v[m].re;
-          up[t + T * m] = v[m].im;
-        }
-      }
-      __syncthreads();
-      if (!pa) {
-        const float* up = reinterpret_cast<const float*>(lines + l * LS);
-#pragma unroll
-        for (int m = 0; m < E; ++m) vph[m] = up[t + T * m];
-      }
+      tile::potential_c2r<N, LPB, WL>(rstage + (it & 1) * (H * TSTR), lines, tw_sm, l, t, vph);
     }
 
     // ---- this tile's psi (loaded one iteration ago); start the next tile's load
@@ -250,87 +174,18 @@ psi_pass_kernel(PsiPassArgs a) {
     }
 
     if constexpr (NPHASE) {
-      const float* vx = a.vext != nullptr ? a.vext + base : nullptr;
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        float th = vph[m] + a.gh * cnorm2(v[m]);
-        if (vx != nullptr && valid) th += vx[(unsigned)(t + T * m) * ustride] * a.h;
-        // reduce to [-pi, pi] (two-part 2 pi), then the SFU sine and cosine
-        const float kq = rintf(th * 0.159154943091895336f);
-        float r = fmaf(-kq, 6.28318548202514648f, th);
-        r = fmaf(-kq, -1.74845553e-7f, r);
-        float s, c;
-        __sincosf(r, &s, &c);
-        // one Newton step towards |(c, s)| = 1 removes the modulus error of the pair
-        const float f = fmaf(-0.5f, fmaf(c, c, fmaf(s, s, -1.f)), 1.f);
-        c *= f;
-        s *= f;
-        v[m] = {v[m].re * c + v[m].im * s, v[m].im * c - v[m].re * s};  // v * exp(-i th)
-      }
+      tile::nonlinear_phase<E, T>(v, vph, a.gh, a.vext != nullptr ? a.vext + base : nullptr, a.h,
+                                  ustride, t, valid);
     }
-
-    // ---- kinetic factor along this axis
-    line_transform<float, N, -1, WL>(v, lines + l * LS, tw_sm, t, true);
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = cmul_hl(v[m], mult_sm[t + T * m], mult_sm[N + t + T * m]);
-    line_transform<float, N, +1, WL>(v, lines + l * LS, tw_sm, t, true);
+    tile::kinetic<N, WL>(v, lines + l * LS, tw_sm, mult_sm, t);
     store_line<E, T>(v, a.psi + base, ustride, t, valid);
 
     if constexpr (DENSITY) {
-      // ---- rho = |psi|^2, R2C along this axis, two real lines per complex FFT
-      float rho[E];
-#pragma unroll
-      for (int m = 0; m < E; ++m) rho[m] = valid ? cnorm2(v[m]) : 0.f;
-      const bool pa = l < LPB / 2;
-      __syncthreads();
-      if (!pa) {
-        float* b = reinterpret_cast<float*>(lines + l * LS);
-#pragma unroll
-        for (int m = 0; m < E; ++m) b[t + T * m] = rho[m];
-      }
-      __syncthreads();
-      if (pa) {
-        const float* b = reinterpret_cast<const float*>(lines + (l + LPB / 2) * LS);
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = {rho[m], b[t + T * m]};
-      }
-      line_transform<float, N, -1, WL>(v, lines + l * LS, tw_sm, t, pa);
-      __syncthreads();
-      if (pa) {
-#pragma unroll
-        for (int q = 0; q < E; ++q) lines[l * LS + pidx(t + T * q)] = v[q];
-      }
-      __syncthreads();
-      constexpr int NH = (H + T - 1) / T;
-      cx<float> hs[NH];
-      const cx<float>* zb = lines + (l % (LPB / 2)) * LS;
-#pragma unroll
-      for (int q = 0; q < NH; ++q) {
-        const int k = t + T * q;
-        hs[q] = {0.f, 0.f};
-        if (k < H) {
-          const cx<float> zk = zb[pidx(k)];
-          const cx<float> zn = cconj(zb[pidx((N - k) & (N - 1))]);
-          if (pa) {
-            hs[q] = cscale(zk + zn, 0.5f);
-          } else {
-            const cx<float> d = zk - zn;
-            hs[q] = {0.5f * d.im, -0.5f * d.re};  // (zk - conj z_{N-k}) / (2i)
-          }
-        }
-      }
-      __syncthreads();
-      cx<float>* tile = lines;
-#pragma unroll
-      for (int q = 0; q < NH; ++q) {
-        const int k = t + T * q;
-        if (k < H) tile[k * TSTR + l] = hs[q];
-      }
-      __syncthreads();
-      for (int idx = tid; idx < H * LPB; idx += NT) {
-        const int ll = idx % LPB, k = idx / LPB;
-        if (ll < nvalid) stc(a.rh_out + (size_t)k * nlines + line0 + ll, tile[k * TSTR + ll]);
-      }
+      float2* rh = a.rh_out;
+      tile::density_r2c<N, LPB, WL>(v, valid, lines, tw_sm, l, t, tid, nvalid,
+                                    [&](int k, int ll, cx<float> z) {
+                                      tile::stg_c(rh + (size_t)k * nlines + line0 + ll, z);
+                                    });
     }
     __syncthreads();  // line buffers and the staging tile are reused next iteration
   }
@@ -341,6 +196,7 @@ template <int N, bool STRIDED, int OP>
 __global__ void __launch_bounds__(cta_threads<N>(), min_ctas<N>())
 rho_pass_kernel(RhoPassArgs a) {
   using P = Plan<N>;
+  constexpr int LPB = lpb<N>();
   constexpr int E = P::E, T = P::T, NT = LPB * T, LS = P::LS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw_sm = reinterpret_cast<cx<float>*>(smem_raw);
@@ -349,7 +205,7 @@ rho_pass_kernel(RhoPassArgs a) {
   const int tid = threadIdx.x;
   const int l = STRIDED ? (tid % LPB) : (tid / T);
   const int t = STRIDED ? (tid / LPB) : (tid % T);
-  const Tiles<STRIDED> tiles(a.outer, a.inner);
+  const tile::Tiles<LPB, STRIDED> tiles(a.outer, a.inner);
   const unsigned ustride = STRIDED ? (unsigned)a.inner : 1u;
   constexpr bool PF = E <= 16;  // register prefetch of the next tile (lines up to 256)
   constexpr bool WL = !STRIDED && T <= 32;  // a contiguous line lives in one warp
@@ -389,10 +245,9 @@ rho_pass_kernel(RhoPassArgs a) {
     }
     if constexpr (OP == RHO_INV) {
       line_transform<float, N, +1, WL>(v, lines + l * LS, tw_sm, t, true);
-    } else {
+    } else if constexpr (OP == RHO_FWD) {
       line_transform<float, N, -1, WL>(v, lines + l * LS, tw_sm, t, true);
-    }
-    if constexpr (OP == RHO_GREEN) {
+    } else {
       long long plane, mid;
       if constexpr (STRIDED) {
         plane = o;
@@ -403,16 +258,7 @@ rho_pass_kernel(RhoPassArgs a) {
       }
       float k2pm = 0.f;
       if (valid) k2pm = a.k2p[plane] + a.k2m[mid];
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        // K = cN/k2 + cY/(k2 + mu2) over one division; K's relative error of a few
-        // ulp moves the phase V h by far less than the FP32 rounding of psi
-        const float k2 = k2pm + a.k2l[t + T * m];
-        const float den = k2 * (k2 + a.mu2);
-        const float K = (k2 > 0.f) ? __fdividef(fmaf(a.cN, k2 + a.mu2, a.cY * k2), den) : 0.f;
-        v[m] = cscale(v[m], K);
-      }
-      line_transform<float, N, +1, WL>(v, lines + l * LS, tw_sm, t, true);
+      tile::green<N, WL>(v, lines + l * LS, tw_sm, a.k2l, k2pm, a.cN, a.cY, a.mu2, t);
     }
     store_line<E, T>(v, a.data + base, ustride, t, valid);
   }
@@ -437,7 +283,7 @@ unsigned persistent_ctas(K kern, int threads, size_t smem, long long ntiles) {
   return (unsigned)(ntiles < cap ? ntiles : cap);
 }
 
-template <bool STRIDED>
+template <int LPB, bool STRIDED>
 long long host_tiles(long long outer, long long inner) {
   return STRIDED ? outer * ((inner + LPB - 1) / LPB) : (outer + LPB - 1) / LPB;
 }
@@ -453,7 +299,7 @@ cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const long long ntiles = host_tiles<STRIDED>(a.outer, a.inner);
+  const long long ntiles = host_tiles<lpb<N>(), STRIDED>(a.outer, a.inner);
   kern<<<persistent_ctas(kern, threads, smem, ntiles), threads, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -469,7 +315,7 @@ cudaError_t launch_rho_t(const RhoPassArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const long long ntiles = host_tiles<STRIDED>(a.outer, a.inner);
+  const long long ntiles = host_tiles<lpb<N>(), STRIDED>(a.outer, a.inner);
   kern<<<persistent_ctas(kern, threads, smem, ntiles), threads, smem, s>>>(a);
   return cudaGetLastError();
 }

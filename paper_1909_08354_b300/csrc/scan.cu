@@ -1,0 +1,647 @@
+// Batched split steps of many independent 2D complex64 instances of uneven
+// size in one persistent launch (a parameter scan over the kernel of Eq. 2 /
+// Eq. 9 and over initial conditions; each instance is its own Sec. III
+// problem).
+//
+// Work is a queue of items (round r, slot s, instance i, tile j), in that
+// order.  A 2D merged step has three slots per round: the psi pass along the
+// first axis (with the potential and nonlinear phase after round 0), the psi
+// pass along the second axis (with the density before the last round), and
+// the Green's-multiply pass on the half spectrum.  CTA c takes items
+// c, c + G, c + 2G, ... in increasing order.  An item waits until all items
+// of the previous slot of its instance are done (a per-instance counter):
+// every dependency has a smaller queue index, each CTA works in increasing
+// order and all CTAs are co-resident (cooperative launch), so the waits always
+// end.  Each wait is still bounded by a clock limit; on expiry the kernel
+// records an error word and every CTA returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sn.h"
+#include "sn_internal.h"
+#include "tile_ops.cuh"
+
+using namespace sn;
+using snfft::cx;
+using snfft::Plan;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kThreads = 256;  // threads per CTA for every line length
+constexpr int kMaxLog2 = 10;
+
+template <int N>
+struct ScanCfg {
+  static constexpr int T = Plan<N>::T;
+  static constexpr int LPB = kThreads / T;  // lines per tile
+  using C = tile::Cfg<N, LPB>;
+  static constexpr size_t smem_words = (size_t)LPB * C::LS + (size_t)C::H * C::TSTR;
+};
+
+constexpr size_t max_words() {
+  size_t w = 0;
+  w = std::max(w, ScanCfg<8>::smem_words);
+  w = std::max(w, ScanCfg<16>::smem_words);
+  w = std::max(w, ScanCfg<32>::smem_words);
+  w = std::max(w, ScanCfg<64>::smem_words);
+  w = std::max(w, ScanCfg<128>::smem_words);
+  w = std::max(w, ScanCfg<256>::smem_words);
+  w = std::max(w, ScanCfg<512>::smem_words);
+  w = std::max(w, ScanCfg<1024>::smem_words);
+  return w;
+}
+constexpr size_t kSmemBytes = max_words() * sizeof(cx<float>);
+
+int log2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+int lines_per_tile(int n) {
+  const int E = n <= 16 ? n : (n <= 256 ? 16 : 32);
+  return kThreads / (n / E);
+}
+
+// Per-instance description, device resident.
+struct Inst {
+  int n;
+  int pad;
+  float2* psi;          // n x n
+  float2* rho;          // (n/2 + 1) x n half spectrum
+  const float2* tw;     // twiddles of length n (hi, lo)
+  const float2* mult;   // [half, full] x 2n (hi, lo) kinetic factors, same for both axes
+  const float* k2;      // n entries
+  float cN, cY, mu2, gh;
+  unsigned t_psi, t_rho;  // tiles per psi pass and per Green's pass
+};
+
+struct ScanArgs {
+  const Inst* inst;
+  int count;
+  int nsteps;
+  const unsigned long long* slot_prefix;  // [3 * (count + 1)]: prefix of tiles per slot
+  unsigned long long per_round;           // items of a full round
+  unsigned long long total;               // items of the whole launch
+  unsigned* done;                         // [count] finished items per instance
+  int* err;                               // [2]: code, queue index
+  long long wait_limit;                   // clock cycles per wait
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Bounded wait (thread 0): true when done[i] >= req.
+__device__ bool wait_for(const ScanArgs& a, int i, unsigned req, unsigned long long q) {
+  if (ld_acquire(a.done + i) >= req) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    __nanosleep(64);
+    if (ld_acquire(a.done + i) >= req) return true;
+    if (ld_relaxed(a.err) != 0) return false;
+    if (clock64() - t0 > a.wait_limit) {
+      if (atomicCAS(a.err, 0, 1) == 0) a.err[1] = (int)q;
+      return false;
+    }
+  }
+}
+
+template <int N, bool STRIDED, int VARIANT>
+__device__ __noinline__ void psi_item(const Inst& d, int full, long long tau, unsigned char* smem) {
+  using S = ScanCfg<N>;
+  using C = typename S::C;
+  constexpr int LPB = S::LPB, E = C::E, T = C::T, LS = C::LS, H = C::H, TSTR = C::TSTR;
+  constexpr bool WL = !STRIDED;  // T <= 32 for every N
+  cx<float>* lines = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* rtile = lines + LPB * LS;
+  const int tid = threadIdx.x;
+  const int l = STRIDED ? (tid % LPB) : (tid / T);
+  const int t = STRIDED ? (tid / LPB) : (tid % T);
+  const tile::Tiles<LPB, STRIDED> tiles(STRIDED ? 1 : N, STRIDED ? N : 1);
+  long long line0, o, i;
+  int nvalid;
+  size_t base;
+  tiles.at(tau, l, N, line0, nvalid, base, o, i);
+  const bool valid = l < nvalid;
+  const unsigned ustride = STRIDED ? (unsigned)N : 1u;
+  const cx<float>* tw = reinterpret_cast<const cx<float>*>(d.tw);
+  const cx<float>* mult = reinterpret_cast<const cx<float>*>(d.mult) + full * 2 * N;
+  float vph[E];
+  (void)vph;
+  if constexpr (VARIANT == PSI_NPHASE) {
+    for (int idx = tid; idx < H * LPB; idx += kThreads) {
+      const int ll = idx % LPB, k = idx / LPB;
+      cx<float> z = {0.f, 0.f};
+      if (ll < nvalid) z = tile::ldg_c<true>(d.rho + (size_t)k * N + line0 + ll);
+      rtile[k * TSTR + ll] = z;
+    }
+    __syncthreads();
+    tile::potential_c2r<N, LPB, WL>(rtile, lines, tw, l, t, vph);
+  }
+  cx<float> v[E];
+  tile::load_line<E, T, true>(v, d.psi + base, ustride, t, valid);
+  if constexpr (VARIANT == PSI_NPHASE)
+    tile::nonlinear_phase<E, T>(v, vph, d.gh, nullptr, 0.f, ustride, t, valid);
+  tile::kinetic<N, WL>(v, lines + l * LS, tw, mult, t);
+  tile::store_line<E, T>(v, d.psi + base, ustride, t, valid);
+  if constexpr (VARIANT == PSI_DENSITY) {
+    float2* rh = d.rho;
+    tile::density_r2c<N, LPB, WL>(v, valid, lines, tw, l, t, tid, nvalid,
+                                  [&](int k, int ll, cx<float> z) {
+                                    tile::stg_c(rh + (size_t)k * N + line0 + ll, z);
+                                  });
+  }
+}
+
+template <int N>
+__device__ __noinline__ void green_item(const Inst& d, long long tau, unsigned char* smem) {
+  using S = ScanCfg<N>;
+  using C = typename S::C;
+  constexpr int LPB = S::LPB, E = C::E, T = C::T, LS = C::LS;
+  cx<float>* lines = reinterpret_cast<cx<float>*>(smem);
+  const int tid = threadIdx.x;
+  const int l = tid / T, t = tid % T;
+  const tile::Tiles<LPB, false> tiles(N / 2 + 1, 1);
+  long long line0, o, i;
+  int nvalid;
+  size_t base;
+  tiles.at(tau, l, N, line0, nvalid, base, o, i);
+  const bool valid = l < nvalid;
+  cx<float> v[E];
+  tile::load_line<E, T, true>(v, d.rho + base, 1u, t, valid);
+  const float k2pm = valid ? d.k2[o] : 0.f;
+  tile::green<N, true>(v, lines + l * LS, reinterpret_cast<const cx<float>*>(d.tw), d.k2, k2pm,
+                       d.cN, d.cY, d.mu2, t);
+  tile::store_line<E, T>(v, d.rho + base, 1u, t, valid);
+}
+
+template <int N>
+__device__ void run_item(const Inst& d, int r, int s, int nsteps, long long tau,
+                         unsigned char* smem) {
+  // round r: axis order (0, 1) when r is even, (1, 0) when odd; axis 0 lines are strided
+  const bool odd = (r & 1) != 0;
+  const int full = (r == 0 || r == nsteps) ? 0 : 1;
+  if (s == 2) {
+    green_item<N>(d, tau, smem);
+    return;
+  }
+  const int axis = (s == 0) ? (odd ? 1 : 0) : (odd ? 0 : 1);
+  const bool strided = axis == 0;
+  int variant = PSI_PLAIN;
+  if (s == 0 && r > 0) variant = PSI_NPHASE;
+  if (s == 1 && r < nsteps) variant = PSI_DENSITY;
+  if (strided) {
+    if (variant == PSI_NPHASE) psi_item<N, true, PSI_NPHASE>(d, full, tau, smem);
+    else if (variant == PSI_DENSITY) psi_item<N, true, PSI_DENSITY>(d, full, tau, smem);
+    else psi_item<N, true, PSI_PLAIN>(d, full, tau, smem);
+  } else {
+    if (variant == PSI_NPHASE) psi_item<N, false, PSI_NPHASE>(d, full, tau, smem);
+    else if (variant == PSI_DENSITY) psi_item<N, false, PSI_DENSITY>(d, full, tau, smem);
+    else psi_item<N, false, PSI_PLAIN>(d, full, tau, smem);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) scan_kernel(ScanArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_go;
+  const unsigned long long C = a.count;
+  const unsigned long long* pre = a.slot_prefix;
+  for (unsigned long long q = blockIdx.x; q < a.total; q += gridDim.x) {
+    // decode q -> (round, slot, instance, tile)
+    const unsigned long long r = q / a.per_round;
+    unsigned long long rem = q - r * a.per_round;
+    int s = 0;
+    while (s < 2 && rem >= pre[s * (C + 1) + C]) {
+      rem -= pre[s * (C + 1) + C];
+      ++s;
+    }
+    const unsigned long long* ps = pre + s * (C + 1);
+    int lo = 0, hi = (int)C - 1;  // last instance with ps[i] <= rem
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (ps[mid] <= rem) lo = mid;
+      else hi = mid - 1;
+    }
+    const int inst = lo;
+    const long long tau = (long long)(rem - ps[inst]);
+    const Inst d = a.inst[inst];
+    const unsigned per_inst_round = 2 * d.t_psi + d.t_rho;
+    const unsigned req = (unsigned)r * per_inst_round + (s >= 1 ? d.t_psi : 0) + (s >= 2 ? d.t_psi : 0);
+    if (threadIdx.x == 0) s_go = (ld_relaxed(a.err) == 0) && wait_for(a, inst, req, q);
+    __syncthreads();
+    if (!s_go) return;
+    switch (d.n) {
+      case 8: run_item<8>(d, (int)r, s, a.nsteps, tau, smem); break;
+      case 16: run_item<16>(d, (int)r, s, a.nsteps, tau, smem); break;
+      case 32: run_item<32>(d, (int)r, s, a.nsteps, tau, smem); break;
+      case 64: run_item<64>(d, (int)r, s, a.nsteps, tau, smem); break;
+      case 128: run_item<128>(d, (int)r, s, a.nsteps, tau, smem); break;
+      case 256: run_item<256>(d, (int)r, s, a.nsteps, tau, smem); break;
+      case 512: run_item<512>(d, (int)r, s, a.nsteps, tau, smem); break;
+      default: run_item<1024>(d, (int)r, s, a.nsteps, tau, smem); break;
+    }
+    __syncthreads();  // every store of this item precedes the release below
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(a.done + inst, 1u);
+    }
+  }
+}
+
+}  // namespace
+
+// ============================================================================
+
+struct sn_batch_s {
+  int count = 0;
+  std::vector<int> n;
+  std::vector<double> L;
+  std::vector<sn_kernel> kp;
+  std::vector<double> dt;  // dt the kinetic tables were built for (NaN: none)
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Inst> host_inst;
+  Inst* dev_inst = nullptr;
+  float2* tw[kMaxLog2 + 1] = {};
+  std::vector<float2*> mult;
+  std::vector<float*> k2;
+  unsigned long long* slot_prefix = nullptr;
+  unsigned* done = nullptr;
+  int* err = nullptr;
+  long long wait_limit = 4000000000LL;  // about 2 s at the B300's 2 GHz
+  int grid = 0;
+  long long launches = 0;
+  // a captured launch (memsets + kernel), keyed by nsteps
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = -1;
+  long long graph_limit = -1;
+  // observables of one instance go through a grid of the same shape
+  std::vector<sn_grid> obs_grid;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+sn_status bfail(sn_status st, const std::string& m) {
+  set_thread_error(m.c_str());
+  return st;
+}
+sn_status bcuda(cudaError_t e, const char* what) {
+  return bfail(e == cudaErrorMemoryAllocation ? SN_ENOMEM : SN_ECUDA,
+               std::string("batch: ") + what + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+cudaError_t balloc(sn_batch b, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  b->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return cudaSuccess;
+}
+
+void split_hilo(const std::vector<double2>& v, float2* out) {
+  const size_t n = v.size();
+  for (size_t i = 0; i < n; ++i) {
+    const float hr = (float)v[i].x, hi = (float)v[i].y;
+    out[i] = make_float2(hr, hi);
+    out[n + i] = make_float2((float)(v[i].x - (double)hr), (float)(v[i].y - (double)hi));
+  }
+}
+
+std::vector<double2> twiddles(int N) {
+  std::vector<double2> tw;
+  if (N <= 16) return tw;
+  const int R0 = N == 32 ? 2 : N == 64 ? 4 : N == 128 ? 8 : N == 256 ? 16 : N == 512 ? 16 : 32;
+  const int R1 = N / R0;
+  tw.resize(2 * N);
+  for (int r = 0; r < R1; ++r)
+    for (int j = 0; j < R0; ++j) {
+      const double a = -2.0 * kPi * (double)((long long)j * r % N) / N;
+      tw[r * R0 + j] = make_double2(std::cos(a), std::sin(a));
+    }
+  for (int r = 0; r < R0; ++r)
+    for (int j = 0; j < R1; ++j) {
+      const double a = 2.0 * kPi * (double)((long long)j * r % N) / N;
+      tw[N + r * R1 + j] = make_double2(std::cos(a), std::sin(a));
+    }
+  return tw;
+}
+
+double wavenumber(int j, int n, double L) { return 2.0 * kPi / L * (double)(j < n / 2 ? j : j - n); }
+
+}  // namespace
+
+extern "C" {
+
+sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* L,
+                          void* cuda_stream) {
+  if (!out) return bfail(SN_EINVAL, "sn_create_batch: out is NULL");
+  *out = nullptr;
+  if (count < 1 || !n || !L) return bfail(SN_EINVAL, "sn_create_batch: count >= 1, n and L required");
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 8 || n[i] > 1024 || (n[i] & (n[i] - 1)))
+      return bfail(SN_EINVAL, "sn_create_batch: each n must be a power of two in [8, 1024]");
+    if (!(L[i] > 0.0) || !std::isfinite(L[i]))
+      return bfail(SN_EINVAL, "sn_create_batch: each L must be finite and > 0");
+  }
+  sn_batch b = new sn_batch_s();
+  b->count = count;
+  b->n.assign(n, n + count);
+  b->L.assign(L, L + count);
+  sn_kernel k0{};
+  k0.coeff_lap = -0.5;
+  k0.G = 1.0;
+  k0.lambda_Y = 1.0;
+  k0.zero_k0 = 1;
+  b->kp.assign(count, k0);
+  b->dt.assign(count, std::nan(""));
+  b->host_inst.resize(count);
+  b->mult.assign(count, nullptr);
+  b->k2.assign(count, nullptr);
+  b->obs_grid.assign(count, nullptr);
+  auto bail = [&](sn_status st) {
+    sn_destroy_batch(b);
+    return st;
+  };
+  cudaError_t e;
+  if (cuda_stream) {
+    b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return bail(bcuda(e, "cudaStreamCreate"));
+    b->own_stream = true;
+  }
+  std::vector<unsigned long long> prefix(3 * (count + 1), 0);
+  for (int i = 0; i < count; ++i) {
+    Inst& d = b->host_inst[i];
+    const int N = n[i];
+    const int lpb = lines_per_tile(N);
+    d.n = N;
+    d.t_psi = (unsigned)((N + lpb - 1) / lpb);
+    d.t_rho = (unsigned)((N / 2 + 1 + lpb - 1) / lpb);
+    const size_t cells = (size_t)N * N;
+    if ((e = balloc(b, &d.psi, cells)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(psi)"));
+    if ((e = cudaMemset(d.psi, 0, cells * sizeof(float2))) != cudaSuccess)
+      return bail(bcuda(e, "cudaMemset(psi)"));
+    if ((e = balloc(b, &d.rho, (size_t)(N / 2 + 1) * N)) != cudaSuccess)
+      return bail(bcuda(e, "cudaMalloc(rho)"));
+    const int l2 = log2i(N);
+    if (!b->tw[l2]) {
+      std::vector<double2> t64 = twiddles(N);
+      std::vector<float2> t32(std::max<size_t>(2 * t64.size(), 2));
+      if (!t64.empty()) split_hilo(t64, t32.data());
+      if ((e = balloc(b, &b->tw[l2], t32.size())) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(tw)"));
+      if ((e = cudaMemcpy(b->tw[l2], t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return bail(bcuda(e, "cudaMemcpy(tw)"));
+    }
+    d.tw = b->tw[l2];
+    if ((e = balloc(b, &b->mult[i], (size_t)4 * N)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(mult)"));
+    d.mult = b->mult[i];
+    std::vector<float> k2(N);
+    for (int j = 0; j < N; ++j) {
+      const double k = wavenumber(j, N, L[i]);
+      k2[j] = (float)(k * k);
+    }
+    if ((e = balloc(b, &b->k2[i], (size_t)N)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(k2)"));
+    if ((e = cudaMemcpy(b->k2[i], k2.data(), N * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(bcuda(e, "cudaMemcpy(k2)"));
+    d.k2 = b->k2[i];
+    prefix[0 * (count + 1) + i + 1] = prefix[0 * (count + 1) + i] + d.t_psi;
+    prefix[1 * (count + 1) + i + 1] = prefix[1 * (count + 1) + i] + d.t_psi;
+    prefix[2 * (count + 1) + i + 1] = prefix[2 * (count + 1) + i] + d.t_rho;
+  }
+  if ((e = balloc(b, &b->slot_prefix, prefix.size())) != cudaSuccess)
+    return bail(bcuda(e, "cudaMalloc(prefix)"));
+  if ((e = cudaMemcpy(b->slot_prefix, prefix.data(), prefix.size() * sizeof(unsigned long long),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(bcuda(e, "cudaMemcpy(prefix)"));
+  if ((e = balloc(b, &b->dev_inst, (size_t)count)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(inst)"));
+  if ((e = balloc(b, &b->done, (size_t)count)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(done)"));
+  if ((e = balloc(b, &b->err, (size_t)2)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(err)"));
+  if ((e = cudaMemset(b->err, 0, 2 * sizeof(int))) != cudaSuccess) return bail(bcuda(e, "cudaMemset(err)"));
+  if ((e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemBytes)) != cudaSuccess)
+    return bail(bcuda(e, "cudaFuncSetAttribute"));
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kThreads, kSmemBytes)) !=
+      cudaSuccess)
+    return bail(bcuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
+  if (per_sm < 1) return bail(bfail(SN_ENOTSUP, "sn_create_batch: scan kernel does not fit on an SM"));
+  b->grid = per_sm * sms;
+  *out = b;
+  return SN_OK;
+}
+
+sn_status sn_set_kernel_batch(sn_batch b, const sn_kernel* k) {
+  if (!b || !k) return bfail(SN_EINVAL, "sn_set_kernel_batch: NULL argument");
+  for (int i = 0; i < b->count; ++i) {
+    const sn_kernel& x = k[i];
+    if (!std::isfinite(x.coeff_lap) || !std::isfinite(x.G) || !std::isfinite(x.alpha_Y) ||
+        !std::isfinite(x.lambda_Y) || !std::isfinite(x.g_local))
+      return bfail(SN_EINVAL, "sn_set_kernel_batch: parameters must be finite");
+    if (x.alpha_Y != 0.0 && !(x.lambda_Y > 0.0))
+      return bfail(SN_EINVAL, "sn_set_kernel_batch: lambda_Y must be > 0 when alpha_Y != 0");
+    if (x.zero_k0 != 1) return bfail(SN_EINVAL, "sn_set_kernel_batch: zero_k0 must be 1");
+    if (x.v_ext) return bfail(SN_ENOTSUP, "sn_set_kernel_batch: v_ext is not supported in a batch");
+  }
+  for (int i = 0; i < b->count; ++i) {
+    if (k[i].coeff_lap != b->kp[i].coeff_lap) b->dt[i] = std::nan("");
+    b->kp[i] = k[i];
+  }
+  return SN_OK;
+}
+
+sn_status sn_set_state_batch(sn_batch b, int index, const void* psi, int on_device) {
+  if (!b || !psi || index < 0 || index >= b->count)
+    return bfail(SN_EINVAL, "sn_set_state_batch: bad argument");
+  const size_t bytes = (size_t)b->n[index] * b->n[index] * sizeof(float2);
+  cudaError_t e = cudaMemcpyAsync(b->host_inst[index].psi, psi, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? SN_OK : bcuda(e, "sn_set_state_batch copy");
+}
+
+sn_status sn_get_state_batch(sn_batch b, int index, void* psi_out, int on_device) {
+  if (!b || !psi_out || index < 0 || index >= b->count)
+    return bfail(SN_EINVAL, "sn_get_state_batch: bad argument");
+  sn_status st = sn_batch_sync(b);
+  if (st != SN_OK) return st;
+  const size_t bytes = (size_t)b->n[index] * b->n[index] * sizeof(float2);
+  cudaError_t e = cudaMemcpyAsync(psi_out, b->host_inst[index].psi, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  b->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? SN_OK : bcuda(e, "sn_get_state_batch copy");
+}
+
+sn_status sn_set_batch_wait_limit(sn_batch b, long long cycles) {
+  if (!b || cycles < 0) return bfail(SN_EINVAL, "sn_set_batch_wait_limit: bad argument");
+  b->wait_limit = cycles;
+  return SN_OK;
+}
+
+sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
+  if (!b || !dt) return bfail(SN_EINVAL, "sn_step_batch: NULL argument");
+  if (nsteps < 0) return bfail(SN_EINVAL, "sn_step_batch: nsteps must be >= 0");
+  for (int i = 0; i < b->count; ++i)
+    if (!std::isfinite(dt[i])) return bfail(SN_EINVAL, "sn_step_batch: dt must be finite");
+  if (nsteps == 0) return SN_OK;
+  cudaError_t e;
+  bool changed = false;
+  for (int i = 0; i < b->count; ++i) {
+    Inst& d = b->host_inst[i];
+    const sn_kernel& k = b->kp[i];
+    const int N = b->n[i];
+    const double h = dt[i];
+    const double cells = (double)N * N;
+    const double cN = -4.0 * kPi * k.G * h / cells;
+    const Inst before = d;
+    d.cN = (float)cN;
+    d.cY = (float)(cN * k.alpha_Y);
+    d.mu2 = (float)((k.alpha_Y != 0.0) ? 1.0 / (k.lambda_Y * k.lambda_Y) : 1.0);
+    d.gh = (float)(k.g_local * h);
+    if (std::memcmp(&before, &d, sizeof(Inst)) != 0) changed = true;
+    if (!(h == b->dt[i])) {
+      if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bcuda(e, "sync");
+      std::vector<float2> m32(4 * N);
+      for (int f = 0; f < 2; ++f) {
+        const double tau = f ? h : 0.5 * h;
+        std::vector<double2> m(N);
+        for (int j = 0; j < N; ++j) {
+          const double kk = wavenumber(j, N, b->L[i]);
+          const double th = k.coeff_lap * kk * kk * tau;
+          m[j] = make_double2(std::cos(th) / N, std::sin(th) / N);
+        }
+        split_hilo(m, m32.data() + 2 * N * f);
+      }
+      if ((e = cudaMemcpy(b->mult[i], m32.data(), m32.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return bcuda(e, "cudaMemcpy(mult)");
+      b->dt[i] = h;
+    }
+  }
+  if (changed || b->launches == 0) {
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bcuda(e, "sync");
+    if ((e = cudaMemcpy(b->dev_inst, b->host_inst.data(), sizeof(Inst) * b->count,
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bcuda(e, "cudaMemcpy(inst)");
+  }
+  unsigned long long per_round = 0, last = 0;
+  for (int i = 0; i < b->count; ++i) {
+    per_round += 2ull * b->host_inst[i].t_psi + b->host_inst[i].t_rho;
+    last += 2ull * b->host_inst[i].t_psi;
+  }
+  ScanArgs a{};
+  a.inst = b->dev_inst;
+  a.count = b->count;
+  a.nsteps = nsteps;
+  a.slot_prefix = b->slot_prefix;
+  a.per_round = per_round;
+  a.total = per_round * (unsigned long long)nsteps + last;
+  a.done = b->done;
+  a.err = b->err;
+  a.wait_limit = b->wait_limit;
+
+  if (b->graph && (b->graph_steps != nsteps || b->graph_limit != b->wait_limit)) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  if (!b->graph) {
+    // capture: zero the counters, then one cooperative launch of the whole scan
+    cudaGraph_t gr = nullptr;
+    if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return bcuda(e, "cudaStreamBeginCapture");
+    cudaError_t e1 = cudaMemsetAsync(b->done, 0, sizeof(unsigned) * b->count, b->stream);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)b->grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e2 = e1 == cudaSuccess ? cudaLaunchKernelEx(&cfg, scan_kernel, a) : e1;
+    e = cudaStreamEndCapture(b->stream, &gr);
+    if (e2 != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return bcuda(e2, "scan launch capture");
+    }
+    if (e != cudaSuccess) return bcuda(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&b->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return bcuda(e, "cudaGraphInstantiate");
+    b->graph_steps = nsteps;
+    b->graph_limit = b->wait_limit;
+  }
+  if ((e = cudaGraphLaunch(b->graph, b->stream)) != cudaSuccess) return bcuda(e, "cudaGraphLaunch");
+  b->launches += 1;
+  return SN_OK;
+}
+
+sn_status sn_batch_sync(sn_batch b) {
+  if (!b) return bfail(SN_EINVAL, "sn_batch_sync: batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "sn_batch_sync");
+  int err[2] = {0, 0};
+  if ((e = cudaMemcpy(err, b->err, sizeof(err), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return bcuda(e, "sn_batch_sync error word");
+  if (err[0] != 0) {
+    cudaMemset(b->err, 0, sizeof(err));
+    return bfail(SN_ETIMEOUT, "sn_batch_sync: a dependency wait expired at work item " +
+                                  std::to_string(err[1]) + "; the batch state is incomplete");
+  }
+  return SN_OK;
+}
+
+long long sn_batch_launch_count(sn_batch b) { return b ? b->launches : 0; }
+
+sn_status sn_observables_batch(sn_batch b, int index, sn_obs* out) {
+  if (!b || !out || index < 0 || index >= b->count)
+    return bfail(SN_EINVAL, "sn_observables_batch: bad argument");
+  sn_status st = sn_batch_sync(b);
+  if (st != SN_OK) return st;
+  if (!b->obs_grid[index]) {
+    const int n2[2] = {b->n[index], b->n[index]};
+    const double L2[2] = {b->L[index], b->L[index]};
+    st = sn_create_grid(&b->obs_grid[index], 2, n2, L2, SN_C64, b->stream);
+    if (st != SN_OK) return st;
+  }
+  sn_grid g = b->obs_grid[index];
+  if ((st = sn_set_kernel(g, &b->kp[index])) != SN_OK) return st;
+  if ((st = sn_set_state(g, b->host_inst[index].psi, 1)) != SN_OK) return st;
+  return sn_observables(g, out);
+}
+
+void sn_destroy_batch(sn_batch b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (sn_grid g : b->obs_grid) sn_destroy_grid(g);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->allocs) cudaFree(p);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // extern "C"

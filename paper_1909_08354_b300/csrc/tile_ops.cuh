@@ -1,0 +1,260 @@
+// Building blocks of the fused FP32 passes, applied to one tile of LPB lines.
+//
+// Every function is called by all threads of the CTA (they contain barriers).
+// A tile's lines are numbered l = 0..LPB-1; the T threads of line l hold its
+// elements in pattern P (see sn_fft.cuh).  `lines` is LPB padded line buffers
+// of Plan<N>::LS complex values; `tw` and `mult` point at hi/lo FP32 tables in
+// shared or global memory.  WL says that each line lives inside one warp.
+#pragma once
+
+#include "sn_fft.cuh"
+
+namespace sn {
+namespace tile {
+
+using snfft::cconj;
+using snfft::cmul_hl;
+using snfft::cnorm2;
+using snfft::cscale;
+using snfft::cx;
+using snfft::line_transform;
+using snfft::pidx;
+using snfft::Plan;
+
+template <int N, int LPB>
+struct Cfg {
+  static constexpr int E = Plan<N>::E;
+  static constexpr int T = Plan<N>::T;
+  static constexpr int NT = LPB * T;  // threads per CTA
+  static constexpr int LS = Plan<N>::LS;
+  static constexpr int H = N / 2 + 1;  // half-spectrum length
+  static constexpr int TSTR = LPB + 1;  // padded row of a [k][line] staging tile
+};
+
+// Tiles of LPB lines: contiguous lines (stride 1) are LPB consecutive `outer`
+// indices; strided lines are LPB consecutive `inner` indices of one `outer`.
+template <int LPB, bool STRIDED>
+struct Tiles {
+  long long outer, inner, tiles_i, count;
+  __host__ __device__ Tiles(long long o, long long i) : outer(o), inner(i) {
+    tiles_i = STRIDED ? (i + LPB - 1) / LPB : 1;
+    count = STRIDED ? o * tiles_i : (o + LPB - 1) / LPB;
+  }
+  // first line id, valid lines, element offset of line l and its (o, i)
+  __device__ void at(long long tau, int l, int N, long long& line0, int& nvalid, size_t& base,
+                     long long& o, long long& i) const {
+    if (STRIDED) {
+      o = tau / tiles_i;
+      const long long i0 = (tau - o * tiles_i) * LPB;
+      nvalid = (int)min((long long)LPB, inner - i0);
+      line0 = o * inner + i0;
+      i = i0 + l;
+      base = (size_t)o * N * inner + i;
+    } else {
+      const long long o0 = tau * LPB;
+      nvalid = (int)min((long long)LPB, outer - o0);
+      line0 = o0;
+      o = o0 + l;
+      i = 0;
+      base = (size_t)o * N;
+    }
+  }
+};
+
+// Global loads: L1-cached, or L2 only (CG) for data that other CTAs of the
+// same launch have written.
+template <bool CG>
+__device__ __forceinline__ cx<float> ldg_c(const float2* p) {
+  const float2 v = CG ? __ldcg(p) : *p;
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void stg_c(float2* p, cx<float> v) { *p = make_float2(v.re, v.im); }
+
+template <int E, int T, bool CG = false>
+__device__ __forceinline__ void load_line(cx<float> (&v)[E], const float2* p, unsigned ustride,
+                                          int t, bool valid) {
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    cx<float> z = {0.f, 0.f};
+    if (valid) z = ldg_c<CG>(p + (unsigned)(t + T * m) * ustride);
+    v[m] = z;
+  }
+}
+
+template <int E, int T>
+__device__ __forceinline__ void store_line(const cx<float> (&v)[E], float2* p, unsigned ustride,
+                                           int t, bool valid) {
+  asm volatile("" : "+l"(p));  // recompute the store addresses instead of keeping them live
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) stg_c(p + (unsigned)(t + T * m) * ustride, v[m]);
+  }
+}
+
+// V h on my line's elements (pattern P) from a staged [k][line] half-spectrum
+// tile: C2R inverse FFT of lines (l, l + LPB/2) packed as A + iB.  On entry the
+// tile is visible to all threads and the line buffers are free.
+template <int N, int LPB, bool WL>
+__device__ __forceinline__ void potential_c2r(const cx<float>* rtile, cx<float>* lines,
+                                              const cx<float>* tw, int l, int t,
+                                              float (&vph)[Plan<N>::E]) {
+  using C = Cfg<N, LPB>;
+  constexpr int E = C::E, T = C::T, LS = C::LS, TSTR = C::TSTR, HALF = LPB / 2;
+  cx<float> v[E];
+  const bool pa = l < HALF;
+  if (pa) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + T * m;
+      cx<float> A, B;
+      if (k <= N / 2) {
+        A = rtile[k * TSTR + l];
+        B = rtile[k * TSTR + l + HALF];
+        if (k == 0 || k == N / 2) { A.im = 0.f; B.im = 0.f; }
+      } else {
+        A = cconj(rtile[(N - k) * TSTR + l]);
+        B = cconj(rtile[(N - k) * TSTR + l + HALF]);
+      }
+      v[m] = {A.re - B.im, A.im + B.re};  // A + i B
+    }
+  }
+  line_transform<float, N, +1, WL>(v, lines + l * LS, tw, t, pa);
+  __syncthreads();
+  if (pa) {
+    float* up = reinterpret_cast<float*>(lines + (l + HALF) * LS);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      vph[m] = v[m].re;
+      up[t + T * m] = v[m].im;
+    }
+  }
+  __syncthreads();
+  if (!pa) {
+    const float* up = reinterpret_cast<const float*>(lines + l * LS);
+#pragma unroll
+    for (int m = 0; m < E; ++m) vph[m] = up[t + T * m];
+  }
+}
+
+// psi <- exp(-i (V h + V_ext h + g h |psi|^2)) psi.  The angle is reduced to
+// [-pi, pi] with a two-part 2 pi, the SFU sine and cosine are taken there and
+// the pair is renormalised to unit modulus by one Newton step.
+template <int E, int T>
+__device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float (&vph)[E],
+                                                float gh, const float* vx, float h,
+                                                unsigned ustride, int t, bool valid) {
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    float th = vph[m] + gh * cnorm2(v[m]);
+    if (vx != nullptr && valid) th += vx[(unsigned)(t + T * m) * ustride] * h;
+    const float kq = rintf(th * 0.159154943091895336f);
+    float r = fmaf(-kq, 6.28318548202514648f, th);
+    r = fmaf(-kq, -1.74845553e-7f, r);
+    float s, c;
+    __sincosf(r, &s, &c);
+    const float f = fmaf(-0.5f, fmaf(c, c, fmaf(s, s, -1.f)), 1.f);
+    c *= f;
+    s *= f;
+    v[m] = {v[m].re * c + v[m].im * s, v[m].im * c - v[m].re * s};  // v * exp(-i th)
+  }
+}
+
+// FFT . m . IFFT along my line (m: hi parts at [0, N), lo parts at [N, 2N)).
+template <int N, bool WL>
+__device__ __forceinline__ void kinetic(cx<float> (&v)[Plan<N>::E], cx<float>* line_buf,
+                                        const cx<float>* tw, const cx<float>* mult, int t) {
+  constexpr int E = Plan<N>::E, T = Plan<N>::T;
+  line_transform<float, N, -1, WL>(v, line_buf, tw, t, true);
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = cmul_hl(v[m], mult[t + T * m], mult[N + t + T * m]);
+  line_transform<float, N, +1, WL>(v, line_buf, tw, t, true);
+}
+
+// rho = |psi|^2 of the tile and its R2C FFT along the line (two real lines per
+// complex FFT).  put(k, ll, value) receives half-spectrum entry k of line ll
+// for the valid lines; the calls are spread over all threads with ll fastest.
+template <int N, int LPB, bool WL, class Put>
+__device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], bool valid,
+                                            cx<float>* lines, const cx<float>* tw, int l, int t,
+                                            int tid, int nvalid, Put put) {
+  using C = Cfg<N, LPB>;
+  constexpr int E = C::E, T = C::T, NT = C::NT, LS = C::LS, H = C::H, TSTR = C::TSTR;
+  constexpr int HALF = LPB / 2;
+  cx<float> v[E];
+  float rho[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) rho[m] = valid ? cnorm2(psi[m]) : 0.f;
+  const bool pa = l < HALF;
+  __syncthreads();
+  if (!pa) {
+    float* b = reinterpret_cast<float*>(lines + l * LS);
+#pragma unroll
+    for (int m = 0; m < E; ++m) b[t + T * m] = rho[m];
+  }
+  __syncthreads();
+  if (pa) {
+    const float* b = reinterpret_cast<const float*>(lines + (l + HALF) * LS);
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = {rho[m], b[t + T * m]};
+  }
+  line_transform<float, N, -1, WL>(v, lines + l * LS, tw, t, pa);
+  __syncthreads();
+  if (pa) {
+#pragma unroll
+    for (int q = 0; q < E; ++q) lines[l * LS + pidx(t + T * q)] = v[q];
+  }
+  __syncthreads();
+  constexpr int NH = (H + T - 1) / T;
+  cx<float> hs[NH];
+  const cx<float>* zb = lines + (l % HALF) * LS;
+#pragma unroll
+  for (int q = 0; q < NH; ++q) {
+    const int k = t + T * q;
+    hs[q] = {0.f, 0.f};
+    if (k < H) {
+      const cx<float> zk = zb[pidx(k)];
+      const cx<float> zn = cconj(zb[pidx((N - k) & (N - 1))]);
+      if (pa) {
+        hs[q] = cscale(zk + zn, 0.5f);
+      } else {
+        const cx<float> d = zk - zn;
+        hs[q] = {0.5f * d.im, -0.5f * d.re};  // (zk - conj z_{N-k}) / (2i)
+      }
+    }
+  }
+  __syncthreads();
+  cx<float>* stage = lines;
+#pragma unroll
+  for (int q = 0; q < NH; ++q) {
+    const int k = t + T * q;
+    if (k < H) stage[k * TSTR + l] = hs[q];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < H * LPB; idx += NT) {
+    const int ll = idx % LPB, k = idx / LPB;
+    if (ll < nvalid) put(k, ll, stage[k * TSTR + ll]);
+  }
+}
+
+// FFT . K(k) . IFFT along my line of the half spectrum, K = cN/k2 + cY/(k2 + mu2)
+// with K(0) = 0; k2 = k2pm (the two other axes) + k2l[k] (this axis).
+template <int N, bool WL>
+__device__ __forceinline__ void green(cx<float> (&v)[Plan<N>::E], cx<float>* line_buf,
+                                      const cx<float>* tw, const float* k2l, float k2pm, float cN,
+                                      float cY, float mu2, int t) {
+  constexpr int E = Plan<N>::E, T = Plan<N>::T;
+  line_transform<float, N, -1, WL>(v, line_buf, tw, t, true);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    // one division; K's relative error of a few ulp moves the phase V h by far
+    // less than the FP32 rounding of psi
+    const float k2 = k2pm + k2l[t + T * m];
+    const float den = k2 * (k2 + mu2);
+    const float K = (k2 > 0.f) ? __fdividef(fmaf(cN, k2 + mu2, cY * k2), den) : 0.f;
+    v[m] = cscale(v[m], K);
+  }
+  line_transform<float, N, +1, WL>(v, line_buf, tw, t, true);
+}
+
+}  // namespace tile
+}  // namespace sn

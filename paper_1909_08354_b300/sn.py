@@ -65,6 +65,20 @@ _SIGNATURES = [
                                           ctypes.c_double, ctypes.c_double,
                                           ctypes.POINTER(SnKernel), ctypes.c_double, ctypes.c_int,
                                           ctypes.c_void_p]),
+    ("sn_create_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_void_p]),
+    ("sn_set_kernel_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SnKernel)]),
+    ("sn_set_state_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_int]),
+    ("sn_get_state_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_int]),
+    ("sn_step_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    ("sn_observables_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(SnObs)]),
+    ("sn_batch_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("sn_set_batch_wait_limit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
+    ("sn_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("sn_destroy_batch", None, [ctypes.c_void_p]),
     ("sn_destroy_grid", None, [ctypes.c_void_p]),
     ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -216,6 +230,118 @@ def sn_destroy_grid(g):
 
 def sn_last_error(g=None) -> str:
     return lib().sn_last_error(g).decode(errors="replace")
+
+
+def _obs_dict(o):
+    return dict(mass=o.mass, e_kin=o.e_kin, e_pot=o.e_pot, e_nl=o.e_nl, e_total=o.e_total,
+                centroid=list(o.centroid), momentum=list(o.momentum), step=o.step)
+
+
+def sn_create_batch(n: Sequence[int], L: Sequence[float], stream=None):
+    c = len(n)
+    h = ctypes.c_void_p()
+    st = lib().sn_create_batch(ctypes.byref(h), c, (ctypes.c_int * c)(*[int(v) for v in n]),
+                               (ctypes.c_double * c)(*[float(v) for v in L]),
+                               ctypes.c_void_p(stream) if stream else None)
+    _check(None, st)
+    return h.value
+
+
+def sn_set_kernel_batch(b, kernels):
+    """kernels: sequence of dicts with the keyword arguments of sn_set_kernel."""
+    arr = (SnKernel * len(kernels))()
+    for i, kw in enumerate(kernels):
+        arr[i] = SnKernel(kw.get("coeff_lap", -0.5), kw.get("G", 1.0), kw.get("alpha_Y", 0.0),
+                          kw.get("lambda_Y", 1.0), kw.get("g_local", 0.0), 1, None, 0)
+    _check(None, lib().sn_set_kernel_batch(b, arr))
+
+
+def sn_set_state_batch(b, index: int, psi, count: int):
+    p, dev, keep = _array_ptr(psi, SN_C64, count)
+    _check(None, lib().sn_set_state_batch(b, int(index), p, dev))
+    del keep
+
+
+def sn_get_state_batch(b, index: int, out, count: int):
+    p, dev, keep = _array_ptr(out, SN_C64, count, writable=True)
+    _check(None, lib().sn_get_state_batch(b, int(index), p, dev))
+    return out
+
+
+def sn_step_batch(b, dt, nsteps: int):
+    arr = (ctypes.c_double * len(dt))(*[float(v) for v in dt])
+    _check(None, lib().sn_step_batch(b, arr, int(nsteps)))
+
+
+def sn_observables_batch(b, index: int) -> dict:
+    o = SnObs()
+    _check(None, lib().sn_observables_batch(b, int(index), ctypes.byref(o)))
+    return _obs_dict(o)
+
+
+def sn_batch_sync(b):
+    _check(None, lib().sn_batch_sync(b))
+
+
+def sn_set_batch_wait_limit(b, cycles: int):
+    _check(None, lib().sn_set_batch_wait_limit(b, int(cycles)))
+
+
+def sn_batch_launch_count(b) -> int:
+    return int(lib().sn_batch_launch_count(b))
+
+
+def sn_destroy_batch(b):
+    if b:
+        lib().sn_destroy_batch(b)
+
+
+class Batch:
+    """Owns one sn_batch handle: count square 2D complex64 instances."""
+
+    def __init__(self, n: Sequence[int], L: Sequence[float], stream=None):
+        self.n = [int(v) for v in n]
+        self.L = [float(v) for v in L]
+        self.h = sn_create_batch(self.n, self.L, stream)
+
+    def set_kernels(self, kernels):
+        sn_set_kernel_batch(self.h, kernels)
+
+    def set_state(self, i: int, psi):
+        sn_set_state_batch(self.h, i, psi, self.n[i] ** 2)
+
+    def get_state(self, i: int, out=None):
+        if out is None:
+            out = np.empty((self.n[i], self.n[i]), np.complex64)
+        return sn_get_state_batch(self.h, i, out, self.n[i] ** 2)
+
+    def step(self, dt, nsteps: int):
+        if np.isscalar(dt):
+            dt = [dt] * len(self.n)
+        sn_step_batch(self.h, dt, nsteps)
+
+    def sync(self):
+        sn_batch_sync(self.h)
+
+    def observables(self, i: int) -> dict:
+        return sn_observables_batch(self.h, i)
+
+    def set_wait_limit(self, cycles: int):
+        sn_set_batch_wait_limit(self.h, cycles)
+
+    def launch_count(self) -> int:
+        return sn_batch_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sn_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ----------------------------------------------------------------------------

@@ -61,7 +61,8 @@ def test_one_step_matches_oracle(shape, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-@pytest.mark.parametrize("shape", [(32, 64), (128, 16), (8, 32, 16), (32, 32, 32), (16, 8, 64)])
+@pytest.mark.parametrize("shape", [(32, 64), (128, 16), (8, 32, 16), (32, 32, 32), (16, 8, 64),
+                                   (1024, 16), (16, 1024), (512, 32), (16, 8, 1024)])
 def test_merged_steps_match_oracle(shape, dtype):
     """sn_step(h, 5) merges the interior half steps; both axis orders occur."""
     w = W.random_small(shape, seed=77 + sum(shape))

@@ -1,0 +1,128 @@
+"""Batched scan of independent 2D instances of uneven size (one persistent launch).
+
+Each instance of the batch must give what the oracle gives for it alone
+(per-step bar 1e-6 rel-L2 in complex64, k merged steps held to k times it),
+and what the single-grid path gives.  The bounded dependency waits are
+exercised by a zero wait limit: the launch must end with SN_ETIMEOUT and leave
+the GPU usable.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from paper_1909_08354_b300 import sn
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-6
+
+
+def kw_of(kp):
+    return dict(coeff_lap=kp.coeff_lap, G=kp.G, alpha_Y=kp.alpha_Y, lambda_Y=kp.lambda_Y,
+                g_local=kp.g_local)
+
+
+def grid_run(psi, L, kw, dt, nsteps):
+    g = sn.Grid(psi.shape, L, "c64")
+    g.set_kernel(**kw)
+    g.set_state(psi)
+    g.step(dt, nsteps)
+    out = g.get_state()
+    g.close()
+    return out
+
+
+def test_uneven_batch_matches_oracle_per_instance():
+    sizes = [8, 16, 32, 64, 128, 256, 512, 64, 8, 128]
+    ws = [W.random_small((n, n), seed=100 + i, L=12.0) for i, n in enumerate(sizes)]
+    b = sn.Batch(sizes, [w.L[0] for w in ws])
+    b.set_kernels([kw_of(w.kernel) for w in ws])
+    psis = [w.psi0().astype(np.complex64) for w in ws]
+    for i, p in enumerate(psis):
+        b.set_state(i, p)
+    dts = [0.01 + 0.002 * i for i in range(len(sizes))]
+    b.step(dts, 3)
+    b.sync()
+    for i, w in enumerate(ws):
+        ref = O.evolve(psis[i].astype(np.complex128), dts[i], 3, w.L, **kw_of(w.kernel))
+        assert O.rel_l2(b.get_state(i), ref) <= 3 * STEP_TOL, (i, sizes[i])
+    assert b.launch_count() == 1
+    b.close()
+
+
+def test_batch_graph_replay_and_largest_size():
+    sizes = [1024, 128, 256]
+    ws = [W.random_small((n, n), seed=200 + i, L=20.0) for i, n in enumerate(sizes)]
+    b = sn.Batch(sizes, [w.L[0] for w in ws])
+    b.set_kernels([kw_of(w.kernel) for w in ws])
+    psis = [w.psi0().astype(np.complex64) for w in ws]
+    for i, p in enumerate(psis):
+        b.set_state(i, p)
+    b.step(0.01, 2)
+    b.step(0.01, 2)  # replays the captured launch
+    for i, w in enumerate(ws):
+        ref = grid_run(psis[i], w.L, kw_of(w.kernel), 0.01, 2)
+        ref = grid_run(ref, w.L, kw_of(w.kernel), 0.01, 2)
+        assert O.rel_l2(b.get_state(i), ref) <= 4 * STEP_TOL, sizes[i]
+    o = b.observables(1)
+    assert abs(o["mass"] / O.observables(psis[1].astype(np.complex128), ws[1].L)["mass"] - 1) < 1e-5
+    b.close()
+
+
+def test_expired_wait_reports_timeout_and_gpu_stays_usable():
+    sizes = [256] * 8 + [64] * 8
+    ws = [W.random_small((n, n), seed=300 + i, L=12.0) for i, n in enumerate(sizes)]
+    b = sn.Batch(sizes, [w.L[0] for w in ws])
+    b.set_kernels([kw_of(w.kernel) for w in ws])
+    for i, w in enumerate(ws):
+        b.set_state(i, w.psi0().astype(np.complex64))
+    b.set_wait_limit(0)
+    b.step(0.01, 20)
+    with pytest.raises(sn.SNError) as e:
+        b.sync()
+    assert e.value.status == sn.SN_ETIMEOUT
+    # a normal launch afterwards works and matches the single-grid path
+    b.set_wait_limit(4_000_000_000)
+    psi0 = ws[0].psi0().astype(np.complex64)
+    b.set_state(0, psi0)
+    b.step(0.01, 2)
+    ref = grid_run(psi0, ws[0].L, kw_of(ws[0].kernel), 0.01, 2)
+    assert O.rel_l2(b.get_state(0), ref) <= 2 * STEP_TOL
+    b.close()
+
+
+def test_parameter_scan_96_instances_500_steps():
+    """The 96-instance scan workload (sizes 128^2..1024^2, L=40, h=1e-2, 500 steps).
+
+    One step of every instance matches the single-grid path; over 500 steps the
+    mass of every instance is conserved to 1e-5, and the FP32 trajectory of a
+    128^2 instance is as close to the FP64 oracle's as the single-grid FP32
+    trajectory is (the two FP32 paths round differently, and a collapsing
+    instance amplifies rounding over 500 steps)."""
+    ws = [W.scan_instance_2d(i) for i in range(96)]
+    psis = [w.psi0().astype(np.complex64) for w in ws]
+    b = sn.Batch([w.n[0] for w in ws], [w.L[0] for w in ws])
+    b.set_kernels([kw_of(w.kernel) for w in ws])
+    for i, p in enumerate(psis):
+        b.set_state(i, p)
+    b.step(ws[0].dt, 1)
+    for i, w in enumerate(ws):
+        ref = grid_run(psis[i], w.L, kw_of(w.kernel), w.dt, 1)
+        assert O.rel_l2(b.get_state(i), ref) <= 2 * STEP_TOL, (i, w.n)
+    for i, p in enumerate(psis):
+        b.set_state(i, p)
+    m0 = [float(np.sum(np.abs(p.astype(np.complex128)) ** 2)) for p in psis]
+    b.step(ws[0].dt, ws[0].nsteps)
+    b.sync()
+    for i in range(96):
+        out = b.get_state(i)
+        assert abs(float(np.sum(np.abs(out.astype(np.complex128)) ** 2)) / m0[i] - 1) <= 1e-5, i
+    i = next(k for k, w in enumerate(ws) if w.n[0] == 128)
+    w = ws[i]
+    exact = O.evolve(psis[i].astype(np.complex128), w.dt, w.nsteps, w.L, **kw_of(w.kernel))
+    grid = grid_run(psis[i], w.L, kw_of(w.kernel), w.dt, w.nsteps)
+    e_grid = O.rel_l2(grid, exact)
+    e_batch = O.rel_l2(b.get_state(i), exact)
+    assert e_batch <= 2 * e_grid + 1e-5, (e_batch, e_grid)
+    b.close()
