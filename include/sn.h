@@ -174,6 +174,47 @@ sn_status sn_set_batch_wait_limit(sn_batch b, long long cycles);
 long long sn_batch_launch_count(sn_batch b);
 void sn_destroy_batch(sn_batch b);
 
+/* ---------------------------------------------------------------------------
+ * Fourier-neural-operator surrogate of the solver: predicts the 2D state 50
+ * steps ahead from the state and the kernel parameters given as constant
+ * input channels; the plain split step is its fallback and judge.
+ *   v0 = P a + pb;  z_l = Spec_l(v_l) + W_l v_l + b_l,  v_{l+1} = gelu(z_l)
+ *   (no gelu after the last layer);  Spec(v) keeps the modes
+ *   ky in {0..m-1} u {s-m..s-1}, kx in {0..m-1}:
+ *   Spec(v) = (1/s^2) sum w_kx Re(U e^{+i th}), U = R V per mode, V = sum v e^{-i th}
+ *   out = a[0:2] + Q2 gelu(Q1 v_L + q1b) + q2b
+ * Parameters are one flat FP32 vector in the order P, pb, then per layer R
+ * ([2m][m][C][C][re,im]), W, b, then Q1, q1b, Q2, q2b.  Every contraction runs
+ * on the tensor cores with BF16 operands and FP32 accumulation.  All array
+ * arguments are device pointers, planar [B][channels][s][s] FP32.
+ * ------------------------------------------------------------------------- */
+typedef struct sn_fno_s* sn_fno;
+sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int layers, int proj,
+                        int batch_max, void* cuda_stream);
+long long sn_fno_param_count(sn_fno f);
+/* Copy parameters in (resets the Adam moments) or out; host or device. */
+sn_status sn_fno_set_params(sn_fno f, const float* p, int on_device);
+sn_status sn_fno_get_params(sn_fno f, float* p, int on_device);
+/* Gradients of the last sn_fno_backward (same layout as the parameters). */
+sn_status sn_fno_get_grads(sn_fno f, float* g, int on_device);
+/* out[B][2][s][s] from in[B][c_in][s][s]; keeps the activations for backward. */
+sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B);
+/* loss = mean_b ||out_b - target_b|| / ||target_b|| of the last forward (host
+ * double); stores dloss/dout for sn_fno_backward.  Blocks. */
+sn_status sn_fno_loss(sn_fno f, const float* target, int B, double* loss);
+/* Gradients of that loss with respect to every parameter (overwritten). */
+sn_status sn_fno_backward(sn_fno f);
+/* One Adam step with step count t >= 1 (bias-corrected moments). */
+sn_status sn_fno_adam(sn_fno f, double lr, double beta1, double beta2, double eps, int t);
+sn_status sn_fno_sync(sn_fno f);
+void sn_fno_destroy(sn_fno f);
+/* Test hook: the BF16 tensor-core GEMM C[z] = alpha A[z] B[z] + beta C[z] on
+ * device pointers with element strides (see the FNO), synchronous. */
+sn_status sn_test_gemm_bf16(const float* A, long long sAz, long long sAm, long long sAk,
+                            const float* B, long long sBz, long long sBk, long long sBn, float* C,
+                            long long sCz, long long sCm, long long sCn, int M, int N, int K, int Z,
+                            float alpha, float beta);
+
 /* Largest ny and nx accepted by sn_step_2d_noalloc. */
 #define SN_NOALLOC_MAX_N 512
 

@@ -1,0 +1,563 @@
+// Fourier-neural-operator surrogate of the split-step solver: forward,
+// backward, loss and Adam, every contraction on the BF16 tensor-core GEMM
+// (FP32 accumulation) and every pointwise op in its own small kernel.
+//
+// Network (channels C, grid s x s, kept modes ky in {0..m-1} u {s-m..s-1},
+// kx in {0..m-1}, Nm = 2m * m modes):
+//   v0 = P a + pb
+//   z_l = Spec_l(v_l) + W_l v_l + b_l,  v_{l+1} = gelu(z_l) (identity after the last layer)
+//   Spec(v) = (1/s^2) sum w_kx Re(U e^{+i th}), U = R V (per mode), V = sum v e^{-i th}
+//   h = gelu(Q1 v_L + q1b),  out = a[0:2] + Q2 h + q2b
+// The truncated DFTs are separable real GEMMs: along x with an s x 2m
+// cos/sin matrix, along y per plane with a 4m x s block matrix.  Mode mixing
+// is a batch of Nm complex C x C GEMMs written as four real ones.
+// Activations are planar [B][C][s][s] FP32; modes are [B][C][re|im][Nm].
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sn.h"
+#include "sn_internal.h"
+
+using namespace sn;
+
+namespace {
+constexpr double kPi = 3.14159265358979323846;
+typedef long long ll;
+}  // namespace
+
+struct sn_fno_s {
+  int s = 0, ci = 0, C = 0, m = 0, L = 0, J = 0, Bmax = 0;
+  ll P = 0, Nm = 0, nparams = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
+  ll off_P = 0, off_pb = 0, off_Q1 = 0, off_q1b = 0, off_Q2 = 0, off_q2b = 0;
+  std::vector<ll> off_R, off_W, off_b;
+  float *ExF = nullptr, *ExFw = nullptr, *EyA = nullptr, *EyB = nullptr;
+  float *EyIre = nullptr, *EyIim = nullptr, *WxI = nullptr, *WxI1 = nullptr;
+  float *a = nullptr, *A1 = nullptr, *Uh = nullptr, *B1 = nullptr, *g1 = nullptr, *h = nullptr;
+  float *out = nullptr, *dout = nullptr, *dv = nullptr, *dv2 = nullptr, *dz = nullptr, *dh = nullptr;
+  float *GU = nullptr, *GV = nullptr, *work = nullptr;
+  std::vector<float*> v, z, Vh;
+  double* norms = nullptr;  // per sample (||out - t||^2, ||t||^2)
+  int lastB = 0;
+  ll work_floats = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+sn_status ffail(sn_status st, const std::string& m) {
+  set_thread_error(m.c_str());
+  return st;
+}
+sn_status fcuda(cudaError_t e, const char* what) {
+  return ffail(e == cudaErrorMemoryAllocation ? SN_ENOMEM : SN_ECUDA,
+               std::string("fno: ") + what + ": " + cudaGetErrorString(e));
+}
+#define FCHK(call)                                  \
+  do {                                              \
+    cudaError_t _e = (call);                        \
+    if (_e != cudaSuccess) return fcuda(_e, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t falloc(sn_fno f, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  f->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return cudaSuccess;
+}
+
+// ---- pointwise kernels --------------------------------------------------------
+
+__device__ __forceinline__ float gelu(float x) {
+  return 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) +
+         x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+
+inline unsigned blocks_for(ll n) {
+  const ll b = (n + 255) / 256;
+  return (unsigned)(b < 8192 ? b : 8192);
+}
+
+// z[b][c][p] += bias[c]; v = gelu(z) (act) or z
+__global__ void bias_act_kernel(float* z, const float* bias, float* v, ll C, ll P, ll n, int act) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
+    const ll c = (i / P) % C;
+    const float x = z[i] + bias[c];
+    z[i] = x;
+    if (v != nullptr) v[i] = act ? gelu(x) : x;
+  }
+}
+
+__global__ void gelu_bwd_kernel(const float* dv, const float* z, float* dz, ll n) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x)
+    dz[i] = dv[i] * gelu_grad(z[i]);
+}
+
+// out[b][k][p] = a[b][k][p] + q2b[k], k in {0, 1}
+__global__ void out_init_kernel(const float* a, const float* q2b, float* out, ll ci, ll P, ll n) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
+    const ll b = i / (2 * P), r = i - b * 2 * P, k = r / P;
+    out[i] = a[b * ci * P + r] + q2b[k];
+  }
+}
+
+// out[c] (+)= sum_b sum_p X[b][c][p]; one block per channel, fixed order
+__global__ void channel_sum_kernel(const float* X, ll B, ll C, ll P, float* out) {
+  const ll c = blockIdx.x;
+  double s = 0.0;
+  for (ll b = 0; b < B; ++b)
+    for (ll p = threadIdx.x; p < P; p += blockDim.x) s += X[(b * C + c) * P + p];
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = (float)red[0];
+}
+
+// per sample b: norms[2b] = ||out_b - t_b||^2, norms[2b+1] = ||t_b||^2 (one block per sample)
+__global__ void loss_norms_kernel(const float* out, const float* t, ll n_per, double* norms) {
+  const ll b = blockIdx.x;
+  double d2 = 0.0, t2 = 0.0;
+  for (ll i = threadIdx.x; i < n_per; i += blockDim.x) {
+    const double o = out[b * n_per + i], tt = t[b * n_per + i];
+    d2 += (o - tt) * (o - tt);
+    t2 += tt * tt;
+  }
+  __shared__ double r1[256], r2[256];
+  r1[threadIdx.x] = d2;
+  r2[threadIdx.x] = t2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+      r2[threadIdx.x] += r2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    norms[2 * b] = r1[0];
+    norms[2 * b + 1] = r2[0];
+  }
+}
+
+// dout = (out - t) / (B ||out_b - t_b|| ||t_b||)
+__global__ void loss_grad_kernel(const float* out, const float* t, const double* norms, ll n_per,
+                                 ll B, float* dout) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < B * n_per;
+       i += (ll)gridDim.x * blockDim.x) {
+    const ll b = i / n_per;
+    const double den = (double)B * sqrt(norms[2 * b]) * sqrt(norms[2 * b + 1]);
+    dout[i] = den > 0.0 ? (float)((out[i] - t[i]) / den) : 0.f;
+  }
+}
+
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, ll n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// ---- GEMM plumbing --------------------------------------------------------------
+
+cudaError_t gemm(sn_fno f, int M, int N, int K, int Z, const float* A, ll sAz, ll sAm, ll sAk,
+                 const float* B, ll sBz, ll sBk, ll sBn, float* C, ll sCz, ll sCm, ll sCn,
+                 float alpha = 1.f, float beta = 0.f) {
+  GemmArgs g{};
+  g.A = A; g.sAz = sAz; g.sAm = sAm; g.sAk = sAk;
+  g.B = B; g.sBz = sBz; g.sBk = sBk; g.sBn = sBn;
+  g.C = C; g.sCz = sCz; g.sCm = sCm; g.sCn = sCn; g.sCsp = 0;
+  g.M = M; g.N = N; g.K = K; g.Z = Z; g.kchunk = 0;
+  g.alpha = alpha; g.beta = beta;
+  return gemm_bf16(g, f->stream);
+}
+
+// dW (M x N, row-major) = sum_b dY[b] (M x P) X[b]^T (X[b] is N x P), split over K
+cudaError_t weight_grad(sn_fno f, const float* dY, const float* X, int B, int M, int N, float* dW) {
+  const int kchunk = 8192;
+  const int nsplit = (int)((f->P + kchunk - 1) / kchunk);
+  GemmArgs g{};
+  g.A = dY; g.sAz = (ll)M * f->P; g.sAm = f->P; g.sAk = 1;
+  g.B = X; g.sBz = (ll)N * f->P; g.sBk = 1; g.sBn = f->P;
+  g.C = f->work; g.sCz = (ll)nsplit * M * N; g.sCm = N; g.sCn = 1; g.sCsp = (ll)M * N;
+  g.M = M; g.N = N; g.K = (int)f->P; g.Z = B; g.kchunk = kchunk;
+  g.alpha = 1.f; g.beta = 0.f;
+  cudaError_t e = gemm_bf16(g, f->stream);
+  if (e != cudaSuccess) return e;
+  return reduce_sum(f->work, (ll)B * nsplit, (ll)M * N, (ll)M * N, dW, 0.f, f->stream);
+}
+
+// modes V[B][C][2][Nm] = truncated forward DFT of planes X[B][C][s][s]; Ex: s x 2m
+cudaError_t dft_forward(sn_fno f, const float* X, int B, int Cn, const float* Ex, float* V) {
+  const int s = f->s, m = f->m;
+  const ll planes = (ll)B * Cn;
+  // along x: A1 (planes*s x 2m) = X (planes*s x s) Ex (s x 2m)
+  cudaError_t e = gemm(f, (int)(planes * s), 2 * m, s, 1, X, 0, s, 1, Ex, 0, 2 * m, 1, f->A1, 0,
+                       2 * m, 1);
+  if (e != cudaSuccess) return e;
+  // along y, per plane: V (4m x m) = EyA (4m x s) A1re (s x m) + EyB (4m x s) A1im (s x m)
+  e = gemm(f, 4 * m, m, s, (int)planes, f->EyA, 0, s, 1, f->A1, (ll)s * 2 * m, 2 * m, 1, V,
+           2 * f->Nm, m, 1);
+  if (e != cudaSuccess) return e;
+  return gemm(f, 4 * m, m, s, (int)planes, f->EyB, 0, s, 1, f->A1 + m, (ll)s * 2 * m, 2 * m, 1, V,
+              2 * f->Nm, m, 1, 1.f, 1.f);
+}
+
+// planes Y[B][C][s][s] (=, or += with beta) from modes U[B][C][2][Nm]; Wx: 2m x s
+cudaError_t dft_inverse(sn_fno f, const float* U, int B, int Cn, const float* Wx, float* Y,
+                        float beta) {
+  const int s = f->s, m = f->m;
+  const ll planes = (ll)B * Cn;
+  // along y, per plane: B1re (s x m) = EyIre (s x 4m) U (4m x m); B1im likewise; B1 is [y][re|im][q]
+  cudaError_t e = gemm(f, s, m, 4 * m, (int)planes, f->EyIre, 0, 4 * m, 1, U, 2 * f->Nm, m, 1,
+                       f->B1, (ll)s * 2 * m, 2 * m, 1);
+  if (e != cudaSuccess) return e;
+  e = gemm(f, s, m, 4 * m, (int)planes, f->EyIim, 0, 4 * m, 1, U, 2 * f->Nm, m, 1, f->B1 + m,
+           (ll)s * 2 * m, 2 * m, 1);
+  if (e != cudaSuccess) return e;
+  // along x: Y (planes*s x s) = B1 (planes*s x 2m) Wx (2m x s)
+  return gemm(f, (int)(planes * s), s, 2 * m, 1, f->B1, 0, 2 * m, 1, Wx, 0, s, 1, Y, 0, s, 1, 1.f,
+              beta);
+}
+
+// U[b][o] = sum_i R[mode][i][o] V[b][i] per mode (complex), four real GEMMs
+cudaError_t mode_mix(sn_fno f, const float* V, const float* R, int B, float* U) {
+  const int C = f->C;
+  const ll Nm = f->Nm, bs = (ll)C * 2 * Nm, is = 2 * Nm, Rz = 2LL * C * C;
+  const float* Vre = V;
+  const float* Vim = V + Nm;
+  float* Ure = U;
+  float* Uim = U + Nm;
+  cudaError_t e;
+  // Ure = Vre Rre - Vim Rim ; Uim = Vre Rim + Vim Rre
+  if ((e = gemm(f, B, C, C, (int)Nm, Vre, 1, bs, is, R, Rz, 2 * C, 2, Ure, 1, bs, is)) != cudaSuccess) return e;
+  if ((e = gemm(f, B, C, C, (int)Nm, Vim, 1, bs, is, R + 1, Rz, 2 * C, 2, Ure, 1, bs, is, -1.f, 1.f)) != cudaSuccess) return e;
+  if ((e = gemm(f, B, C, C, (int)Nm, Vre, 1, bs, is, R + 1, Rz, 2 * C, 2, Uim, 1, bs, is)) != cudaSuccess) return e;
+  return gemm(f, B, C, C, (int)Nm, Vim, 1, bs, is, R, Rz, 2 * C, 2, Uim, 1, bs, is, 1.f, 1.f);
+}
+
+// backward of mode_mix: GR[mode][i][o] = sum_b conj(V_i) GU_o ; GV[b][i] = sum_o conj(R_io) GU_o
+cudaError_t mode_mix_bwd(sn_fno f, const float* V, const float* R, const float* GU, int B, float* GR,
+                         float* GV) {
+  const int C = f->C;
+  const ll Nm = f->Nm, bs = (ll)C * 2 * Nm, is = 2 * Nm, Rz = 2LL * C * C;
+  cudaError_t e;
+  // GRre = Vre^T GUre + Vim^T GUim ; GRim = Vre^T GUim - Vim^T GUre   (A: (i, b), B: (b, o))
+  if ((e = gemm(f, C, C, B, (int)Nm, V, 1, is, bs, GU, 1, bs, is, GR, Rz, 2 * C, 2)) != cudaSuccess) return e;
+  if ((e = gemm(f, C, C, B, (int)Nm, V + Nm, 1, is, bs, GU + Nm, 1, bs, is, GR, Rz, 2 * C, 2, 1.f, 1.f)) != cudaSuccess) return e;
+  if ((e = gemm(f, C, C, B, (int)Nm, V, 1, is, bs, GU + Nm, 1, bs, is, GR + 1, Rz, 2 * C, 2)) != cudaSuccess) return e;
+  if ((e = gemm(f, C, C, B, (int)Nm, V + Nm, 1, is, bs, GU, 1, bs, is, GR + 1, Rz, 2 * C, 2, -1.f, 1.f)) != cudaSuccess) return e;
+  // GVre = GUre Rre^T + GUim Rim^T ; GVim = GUim Rre^T - GUre Rim^T   (A: (b, o), B: (o, i))
+  if ((e = gemm(f, B, C, C, (int)Nm, GU, 1, bs, is, R, Rz, 2, 2 * C, GV, 1, bs, is)) != cudaSuccess) return e;
+  if ((e = gemm(f, B, C, C, (int)Nm, GU + Nm, 1, bs, is, R + 1, Rz, 2, 2 * C, GV, 1, bs, is, 1.f, 1.f)) != cudaSuccess) return e;
+  if ((e = gemm(f, B, C, C, (int)Nm, GU + Nm, 1, bs, is, R, Rz, 2, 2 * C, GV + Nm, 1, bs, is)) != cudaSuccess) return e;
+  return gemm(f, B, C, C, (int)Nm, GU, 1, bs, is, R + 1, Rz, 2, 2 * C, GV + Nm, 1, bs, is, -1.f, 1.f);
+}
+
+std::vector<float> dft_matrix(int kind, int s, int m) {
+  // ky list: 0..m-1, s-m..s-1 ; kx: 0..m-1
+  std::vector<int> ky(2 * m);
+  for (int p = 0; p < m; ++p) { ky[p] = p; ky[m + p] = s - m + p; }
+  const double tw = 2.0 * kPi / s;
+  const double wscale = 1.0 / ((double)s * s);
+  std::vector<float> M;
+  auto ang = [&](long long a, long long b) { return tw * (double)((a * b) % s); };
+  if (kind == 0 || kind == 1) {  // Ex (s x 2m): [cos | -sin] (kind 1: times w_q / s^2)
+    M.assign((size_t)s * 2 * m, 0.f);
+    for (int x = 0; x < s; ++x)
+      for (int q = 0; q < m; ++q) {
+        const double w = kind == 1 ? (q == 0 ? 1.0 : 2.0) * wscale : 1.0;
+        M[(size_t)x * 2 * m + q] = (float)(w * std::cos(ang(x, q)));
+        M[(size_t)x * 2 * m + m + q] = (float)(-w * std::sin(ang(x, q)));
+      }
+  } else if (kind == 2 || kind == 3) {  // EyA / EyB (4m x s)
+    M.assign((size_t)4 * m * s, 0.f);
+    for (int p = 0; p < 2 * m; ++p)
+      for (int y = 0; y < s; ++y) {
+        const double c = std::cos(ang(ky[p], y)), sn = std::sin(ang(ky[p], y));
+        M[(size_t)p * s + y] = (float)(kind == 2 ? c : sn);
+        M[(size_t)(2 * m + p) * s + y] = (float)(kind == 2 ? -sn : c);
+      }
+  } else if (kind == 4 || kind == 5) {  // EyIre / EyIim (s x 4m)
+    M.assign((size_t)s * 4 * m, 0.f);
+    for (int y = 0; y < s; ++y)
+      for (int p = 0; p < 2 * m; ++p) {
+        const double c = std::cos(ang(ky[p], y)), sn = std::sin(ang(ky[p], y));
+        M[(size_t)y * 4 * m + p] = (float)(kind == 4 ? c : sn);
+        M[(size_t)y * 4 * m + 2 * m + p] = (float)(kind == 4 ? -sn : c);
+      }
+  } else {  // WxI (kind 6: w_q / s^2) / WxI1 (kind 7: 1), 2m x s: rows q -> w cos, rows m+q -> -w sin
+    M.assign((size_t)2 * m * s, 0.f);
+    for (int q = 0; q < m; ++q)
+      for (int x = 0; x < s; ++x) {
+        const double w = kind == 6 ? (q == 0 ? 1.0 : 2.0) * wscale : 1.0;
+        M[(size_t)q * s + x] = (float)(w * std::cos(ang(q, x)));
+        M[(size_t)(m + q) * s + x] = (float)(-w * std::sin(ang(q, x)));
+      }
+  }
+  return M;
+}
+
+}  // namespace
+
+extern "C" {
+
+sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int layers, int proj,
+                        int batch_max, void* cuda_stream) {
+  if (!out) return ffail(SN_EINVAL, "sn_fno_create: out is NULL");
+  *out = nullptr;
+  if (s < 8 || c_in < 2 || width < 1 || modes < 1 || 2 * modes > s || layers < 1 || proj < 1 ||
+      batch_max < 1)
+    return ffail(SN_EINVAL, "sn_fno_create: need s >= 8, c_in >= 2, 1 <= 2 modes <= s, layers, "
+                            "width, proj, batch_max >= 1");
+  sn_fno f = new sn_fno_s();
+  f->s = s; f->ci = c_in; f->C = width; f->m = modes; f->L = layers; f->J = proj; f->Bmax = batch_max;
+  f->P = (ll)s * s;
+  f->Nm = 2LL * modes * modes;
+  auto bail = [&](sn_status st) { sn_fno_destroy(f); return st; };
+  cudaError_t e;
+  if (cuda_stream) {
+    f->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return bail(fcuda(e, "cudaStreamCreate"));
+    f->own_stream = true;
+  }
+  // parameter layout (the oracle's order)
+  ll off = 0;
+  const ll C = width, Nm = f->Nm;
+  f->off_P = off; off += C * c_in;
+  f->off_pb = off; off += C;
+  for (int l = 0; l < layers; ++l) {
+    f->off_R.push_back(off); off += Nm * C * C * 2;
+    f->off_W.push_back(off); off += C * C;
+    f->off_b.push_back(off); off += C;
+  }
+  f->off_Q1 = off; off += (ll)proj * C;
+  f->off_q1b = off; off += proj;
+  f->off_Q2 = off; off += 2LL * proj;
+  f->off_q2b = off; off += 2;
+  f->nparams = off;
+  const ll B = batch_max, P = f->P;
+  if ((e = falloc(f, &f->params, off)) != cudaSuccess || (e = falloc(f, &f->grads, off)) != cudaSuccess ||
+      (e = falloc(f, &f->am, off)) != cudaSuccess || (e = falloc(f, &f->av, off)) != cudaSuccess)
+    return bail(fcuda(e, "cudaMalloc(params)"));
+  cudaMemset(f->params, 0, off * sizeof(float));
+  cudaMemset(f->am, 0, off * sizeof(float));
+  cudaMemset(f->av, 0, off * sizeof(float));
+  const int kinds[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+  float** mats[8] = {&f->ExF, &f->ExFw, &f->EyA, &f->EyB, &f->EyIre, &f->EyIim, &f->WxI, &f->WxI1};
+  for (int k = 0; k < 8; ++k) {
+    std::vector<float> M = dft_matrix(kinds[k], s, modes);
+    if ((e = falloc(f, mats[k], M.size())) != cudaSuccess) return bail(fcuda(e, "cudaMalloc(dft)"));
+    if ((e = cudaMemcpy(*mats[k], M.data(), M.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return bail(fcuda(e, "cudaMemcpy(dft)"));
+  }
+  const ll plane = B * C * P;
+  f->v.assign(layers + 1, nullptr);
+  f->z.assign(layers, nullptr);
+  f->Vh.assign(layers, nullptr);
+  bool ok = true;
+  ok = ok && falloc(f, &f->a, B * c_in * P) == cudaSuccess;
+  for (int l = 0; l <= layers; ++l) ok = ok && falloc(f, &f->v[l], plane) == cudaSuccess;
+  for (int l = 0; l < layers; ++l) {
+    ok = ok && falloc(f, &f->z[l], plane) == cudaSuccess;
+    ok = ok && falloc(f, &f->Vh[l], B * C * 2 * Nm) == cudaSuccess;
+  }
+  ok = ok && falloc(f, &f->A1, B * C * s * 2LL * modes) == cudaSuccess;
+  ok = ok && falloc(f, &f->B1, B * C * s * 2LL * modes) == cudaSuccess;
+  ok = ok && falloc(f, &f->Uh, B * C * 2 * Nm) == cudaSuccess;
+  ok = ok && falloc(f, &f->GU, B * C * 2 * Nm) == cudaSuccess;
+  ok = ok && falloc(f, &f->GV, B * C * 2 * Nm) == cudaSuccess;
+  ok = ok && falloc(f, &f->g1, B * proj * P) == cudaSuccess;
+  ok = ok && falloc(f, &f->h, B * proj * P) == cudaSuccess;
+  ok = ok && falloc(f, &f->dh, B * proj * P) == cudaSuccess;
+  ok = ok && falloc(f, &f->out, B * 2 * P) == cudaSuccess;
+  ok = ok && falloc(f, &f->dout, B * 2 * P) == cudaSuccess;
+  ok = ok && falloc(f, &f->dv, plane) == cudaSuccess;
+  ok = ok && falloc(f, &f->dv2, plane) == cudaSuccess;
+  ok = ok && falloc(f, &f->dz, plane) == cudaSuccess;
+  ok = ok && falloc(f, &f->norms, 2 * B) == cudaSuccess;
+  const ll nsplit = (P + 8191) / 8192;
+  const ll mn = std::max<ll>((ll)proj * C, std::max<ll>(C * C, C * (ll)c_in));
+  f->work_floats = B * nsplit * std::max<ll>(mn, 2LL * proj);
+  ok = ok && falloc(f, &f->work, f->work_floats) == cudaSuccess;
+  if (!ok) return bail(ffail(SN_ENOMEM, "sn_fno_create: device allocation failed"));
+  *out = f;
+  return SN_OK;
+}
+
+long long sn_fno_param_count(sn_fno f) { return f ? f->nparams : 0; }
+
+sn_status sn_fno_set_params(sn_fno f, const float* p, int on_device) {
+  if (!f || !p) return ffail(SN_EINVAL, "sn_fno_set_params: NULL argument");
+  FCHK(cudaMemcpyAsync(f->params, p, f->nparams * sizeof(float),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, f->stream));
+  FCHK(cudaMemsetAsync(f->am, 0, f->nparams * sizeof(float), f->stream));
+  FCHK(cudaMemsetAsync(f->av, 0, f->nparams * sizeof(float), f->stream));
+  FCHK(cudaStreamSynchronize(f->stream));
+  return SN_OK;
+}
+
+sn_status sn_fno_get_params(sn_fno f, float* p, int on_device) {
+  if (!f || !p) return ffail(SN_EINVAL, "sn_fno_get_params: NULL argument");
+  FCHK(cudaMemcpyAsync(p, f->params, f->nparams * sizeof(float),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, f->stream));
+  FCHK(cudaStreamSynchronize(f->stream));
+  return SN_OK;
+}
+
+sn_status sn_fno_get_grads(sn_fno f, float* g, int on_device) {
+  if (!f || !g) return ffail(SN_EINVAL, "sn_fno_get_grads: NULL argument");
+  FCHK(cudaMemcpyAsync(g, f->grads, f->nparams * sizeof(float),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, f->stream));
+  FCHK(cudaStreamSynchronize(f->stream));
+  return SN_OK;
+}
+
+sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
+  if (!f || !in || !out) return ffail(SN_EINVAL, "sn_fno_forward: NULL argument");
+  if (B < 1 || B > f->Bmax) return ffail(SN_EINVAL, "sn_fno_forward: batch must be in [1, batch_max]");
+  const ll P = f->P, C = f->C, ci = f->ci, J = f->J;
+  cudaStream_t st = f->stream;
+  float* prm = f->params;
+  FCHK(cudaMemcpyAsync(f->a, in, (size_t)B * ci * P * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  // lift
+  FCHK(gemm(f, (int)C, (int)P, (int)ci, B, prm + f->off_P, 0, ci, 1, f->a, ci * P, P, 1, f->v[0], C * P, P, 1));
+  bias_act_kernel<<<blocks_for(B * C * P), 256, 0, st>>>(f->v[0], prm + f->off_pb, nullptr, C, P, B * C * P, 0);
+  FCHK(cudaGetLastError());
+  for (int l = 0; l < f->L; ++l) {
+    FCHK(dft_forward(f, f->v[l], B, (int)C, f->ExF, f->Vh[l]));
+    FCHK(mode_mix(f, f->Vh[l], prm + f->off_R[l], B, f->Uh));
+    FCHK(dft_inverse(f, f->Uh, B, (int)C, f->WxI, f->z[l], 0.f));
+    FCHK(gemm(f, (int)C, (int)P, (int)C, B, prm + f->off_W[l], 0, C, 1, f->v[l], C * P, P, 1, f->z[l], C * P, P, 1, 1.f, 1.f));
+    bias_act_kernel<<<blocks_for(B * C * P), 256, 0, st>>>(f->z[l], prm + f->off_b[l], f->v[l + 1], C, P, B * C * P,
+                                                          l < f->L - 1 ? 1 : 0);
+    FCHK(cudaGetLastError());
+  }
+  // projection
+  FCHK(gemm(f, (int)J, (int)P, (int)C, B, prm + f->off_Q1, 0, C, 1, f->v[f->L], C * P, P, 1, f->g1, J * P, P, 1));
+  bias_act_kernel<<<blocks_for(B * J * P), 256, 0, st>>>(f->g1, prm + f->off_q1b, f->h, J, P, B * J * P, 1);
+  out_init_kernel<<<blocks_for(B * 2 * P), 256, 0, st>>>(f->a, prm + f->off_q2b, f->out, ci, P, B * 2 * P);
+  FCHK(cudaGetLastError());
+  FCHK(gemm(f, 2, (int)P, (int)J, B, prm + f->off_Q2, 0, J, 1, f->h, J * P, P, 1, f->out, 2 * P, P, 1, 1.f, 1.f));
+  if (out != f->out)
+    FCHK(cudaMemcpyAsync(out, f->out, (size_t)B * 2 * P * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  f->lastB = B;
+  return SN_OK;
+}
+
+sn_status sn_fno_loss(sn_fno f, const float* target, int B, double* loss) {
+  if (!f || !target || !loss) return ffail(SN_EINVAL, "sn_fno_loss: NULL argument");
+  if (B != f->lastB) return ffail(SN_EINVAL, "sn_fno_loss: batch differs from the last forward");
+  const ll n_per = 2 * f->P;
+  loss_norms_kernel<<<B, 256, 0, f->stream>>>(f->out, target, n_per, f->norms);
+  loss_grad_kernel<<<blocks_for(B * n_per), 256, 0, f->stream>>>(f->out, target, f->norms, n_per, B, f->dout);
+  FCHK(cudaGetLastError());
+  std::vector<double> nr(2 * B);
+  FCHK(cudaMemcpyAsync(nr.data(), f->norms, nr.size() * sizeof(double), cudaMemcpyDeviceToHost, f->stream));
+  FCHK(cudaStreamSynchronize(f->stream));
+  double s = 0.0;
+  for (int b = 0; b < B; ++b) s += std::sqrt(nr[2 * b]) / std::sqrt(nr[2 * b + 1]);
+  *loss = s / B;
+  return SN_OK;
+}
+
+sn_status sn_fno_backward(sn_fno f) {
+  if (!f || f->lastB < 1) return ffail(SN_EINVAL, "sn_fno_backward: no forward to differentiate");
+  const int B = f->lastB;
+  const ll P = f->P, C = f->C, ci = f->ci, J = f->J;
+  cudaStream_t st = f->stream;
+  float* prm = f->params;
+  float* gr = f->grads;
+  // projection
+  FCHK(weight_grad(f, f->dout, f->h, B, 2, (int)J, gr + f->off_Q2));
+  channel_sum_kernel<<<2, 256, 0, st>>>(f->dout, B, 2, P, gr + f->off_q2b);
+  FCHK(gemm(f, (int)J, (int)P, 2, B, prm + f->off_Q2, 0, 1, J, f->dout, 2 * P, P, 1, f->dh, J * P, P, 1));
+  gelu_bwd_kernel<<<blocks_for(B * J * P), 256, 0, st>>>(f->dh, f->g1, f->dh, B * J * P);
+  FCHK(cudaGetLastError());
+  FCHK(weight_grad(f, f->dh, f->v[f->L], B, (int)J, (int)C, gr + f->off_Q1));
+  channel_sum_kernel<<<(unsigned)J, 256, 0, st>>>(f->dh, B, J, P, gr + f->off_q1b);
+  FCHK(gemm(f, (int)C, (int)P, (int)J, B, prm + f->off_Q1, 0, 1, C, f->dh, J * P, P, 1, f->dv, C * P, P, 1));
+  for (int l = f->L - 1; l >= 0; --l) {
+    const float* dz = f->dv;
+    if (l < f->L - 1) {
+      gelu_bwd_kernel<<<blocks_for(B * C * P), 256, 0, st>>>(f->dv, f->z[l], f->dz, B * C * P);
+      FCHK(cudaGetLastError());
+      dz = f->dz;
+    }
+    FCHK(weight_grad(f, dz, f->v[l], B, (int)C, (int)C, gr + f->off_W[l]));
+    channel_sum_kernel<<<(unsigned)C, 256, 0, st>>>(dz, B, C, P, gr + f->off_b[l]);
+    FCHK(gemm(f, (int)C, (int)P, (int)C, B, prm + f->off_W[l], 0, 1, C, dz, C * P, P, 1, f->dv2, C * P, P, 1));
+    // spectral branch
+    FCHK(dft_forward(f, dz, B, (int)C, f->ExFw, f->GU));
+    FCHK(mode_mix_bwd(f, f->Vh[l], prm + f->off_R[l], f->GU, B, gr + f->off_R[l], f->GV));
+    FCHK(dft_inverse(f, f->GV, B, (int)C, f->WxI1, f->dv2, 1.f));
+    std::swap(f->dv, f->dv2);
+  }
+  FCHK(weight_grad(f, f->dv, f->a, B, (int)C, (int)ci, gr + f->off_P));
+  channel_sum_kernel<<<(unsigned)C, 256, 0, st>>>(f->dv, B, C, P, gr + f->off_pb);
+  FCHK(cudaGetLastError());
+  return SN_OK;
+}
+
+sn_status sn_fno_adam(sn_fno f, double lr, double beta1, double beta2, double eps, int t) {
+  if (!f || t < 1) return ffail(SN_EINVAL, "sn_fno_adam: bad argument");
+  const float c1 = (float)(1.0 - std::pow(beta1, t)), c2 = (float)(1.0 - std::pow(beta2, t));
+  adam_kernel<<<blocks_for(f->nparams), 256, 0, f->stream>>>(f->params, f->grads, f->am, f->av,
+                                                               f->nparams, (float)lr, (float)beta1,
+                                                               (float)beta2, (float)eps, c1, c2);
+  FCHK(cudaGetLastError());
+  return SN_OK;
+}
+
+sn_status sn_fno_sync(sn_fno f) {
+  if (!f) return ffail(SN_EINVAL, "sn_fno_sync: NULL");
+  FCHK(cudaStreamSynchronize(f->stream));
+  return SN_OK;
+}
+
+void sn_fno_destroy(sn_fno f) {
+  if (!f) return;
+  if (f->stream) cudaStreamSynchronize(f->stream);
+  for (void* p : f->allocs) cudaFree(p);
+  if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
+  delete f;
+}
+
+sn_status sn_test_gemm_bf16(const float* A, long long sAz, long long sAm, long long sAk,
+                            const float* B, long long sBz, long long sBk, long long sBn, float* C,
+                            long long sCz, long long sCm, long long sCn, int M, int N, int K, int Z,
+                            float alpha, float beta) {
+  GemmArgs g{};
+  g.A = A; g.sAz = sAz; g.sAm = sAm; g.sAk = sAk;
+  g.B = B; g.sBz = sBz; g.sBk = sBk; g.sBn = sBn;
+  g.C = C; g.sCz = sCz; g.sCm = sCm; g.sCn = sCn;
+  g.M = M; g.N = N; g.K = K; g.Z = Z; g.alpha = alpha; g.beta = beta;
+  cudaError_t e = gemm_bf16(g, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? SN_OK : fcuda(e, "sn_test_gemm_bf16");
+}
+
+}  // extern "C"

@@ -91,4 +91,24 @@ cudaError_t launch_obs_green(const double2* rhohat, const int* n, int ndim,
                              double* partials, cudaStream_t s);
 cudaError_t launch_obs_finish(const double* partials, int nq, double* out, cudaStream_t s);
 
+// ---- BF16 tensor-core GEMM (FNO surrogate) -------------------------------
+// C[z] = alpha * A[z] B[z] + beta * C[z]; element (m,k) of A[z] at
+// A + z sAz + m sAm + k sAk, (k,n) of B at B + z sBz + k sBk + n sBn, (m,n) of C
+// at C + z sCz + m sCm + n sCn.  kchunk > 0 splits K: partial sums of chunk sp
+// go to C + z sCz + sp sCsp (beta must be 0).
+struct GemmArgs {
+  const float* A;
+  long long sAz, sAm, sAk;
+  const float* B;
+  long long sBz, sBk, sBn;
+  float* C;
+  long long sCz, sCm, sCn, sCsp;
+  int M, N, K, Z, kchunk;
+  float alpha, beta;
+};
+cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);
+// out[i] = sum_{j<count} part[j*stride + i] (+ beta * out[i]) for i < n
+cudaError_t reduce_sum(const float* part, long long count, long long stride, long long n, float* out,
+                       float beta, cudaStream_t s);
+
 }  // namespace sn

@@ -79,6 +79,25 @@ _SIGNATURES = [
     ("sn_set_batch_wait_limit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     ("sn_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("sn_destroy_batch", None, [ctypes.c_void_p]),
+    ("sn_fno_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_void_p]),
+    ("sn_fno_param_count", ctypes.c_longlong, [ctypes.c_void_p]),
+    ("sn_fno_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("sn_fno_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("sn_fno_get_grads", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("sn_fno_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("sn_fno_loss", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double)]),
+    ("sn_fno_backward", ctypes.c_int, [ctypes.c_void_p]),
+    ("sn_fno_adam", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+    ("sn_fno_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("sn_fno_destroy", None, [ctypes.c_void_p]),
+    ("sn_test_gemm_bf16", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_longlong] * 3
+                                        + [ctypes.c_void_p] + [ctypes.c_longlong] * 3
+                                        + [ctypes.c_void_p] + [ctypes.c_longlong] * 3
+                                        + [ctypes.c_int] * 4 + [ctypes.c_float] * 2),
     ("sn_destroy_grid", None, [ctypes.c_void_p]),
     ("sn_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -294,6 +313,83 @@ def sn_batch_launch_count(b) -> int:
 def sn_destroy_batch(b):
     if b:
         lib().sn_destroy_batch(b)
+
+
+class Fno:
+    """Owns one sn_fno handle (the surrogate network); arrays are CUDA torch tensors."""
+
+    def __init__(self, s=256, c_in=5, width=64, modes=24, layers=4, proj=128, batch_max=8,
+                 stream=None):
+        self.s, self.c_in, self.width, self.modes, self.layers, self.proj = s, c_in, width, modes, layers, proj
+        self.batch_max = batch_max
+        h = ctypes.c_void_p()
+        _check(None, lib().sn_fno_create(ctypes.byref(h), s, c_in, width, modes, layers, proj,
+                                         batch_max, ctypes.c_void_p(stream) if stream else None))
+        self.h = h.value
+        self.nparams = int(lib().sn_fno_param_count(self.h))
+
+    @staticmethod
+    def _dev(t, n):
+        import torch
+        if not (_is_torch(t) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                and t.numel() >= n):
+            raise ValueError("expected a contiguous float32 CUDA tensor")
+        return t.data_ptr()
+
+    def set_params(self, p):
+        if _is_torch(p):
+            _check(None, lib().sn_fno_set_params(self.h, self._dev(p, self.nparams), 1))
+        else:
+            a = np.ascontiguousarray(p, dtype=np.float32)
+            _check(None, lib().sn_fno_set_params(self.h, a.ctypes.data, 0))
+
+    def get_params(self):
+        out = np.empty(self.nparams, np.float32)
+        _check(None, lib().sn_fno_get_params(self.h, out.ctypes.data, 0))
+        return out
+
+    def get_grads(self):
+        out = np.empty(self.nparams, np.float32)
+        _check(None, lib().sn_fno_get_grads(self.h, out.ctypes.data, 0))
+        return out
+
+    def forward(self, x, out):
+        B = x.shape[0]
+        _check(None, lib().sn_fno_forward(self.h, self._dev(x, B * self.c_in * self.s ** 2),
+                                          self._dev(out, B * 2 * self.s ** 2), B))
+        return out
+
+    def loss(self, target, B):
+        v = ctypes.c_double()
+        _check(None, lib().sn_fno_loss(self.h, self._dev(target, B * 2 * self.s ** 2), B,
+                                       ctypes.byref(v)))
+        return v.value
+
+    def backward(self):
+        _check(None, lib().sn_fno_backward(self.h))
+
+    def adam(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(None, lib().sn_fno_adam(self.h, lr, beta1, beta2, eps, t))
+
+    def sync(self):
+        _check(None, lib().sn_fno_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sn_fno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sn_test_gemm_bf16(A, sA, B, sB, C, sC, M, N, K, Z, alpha=1.0, beta=0.0):
+    """Test hook: strided batched BF16 GEMM on CUDA float32 tensors; s* = (sz, s_row, s_col)."""
+    _check(None, lib().sn_test_gemm_bf16(A.data_ptr(), *sA, B.data_ptr(), *sB, C.data_ptr(), *sC,
+                                         M, N, K, Z, alpha, beta))
 
 
 class Batch:

@@ -1,0 +1,107 @@
+"""FNO surrogate kernels (BF16 tensor-core GEMMs, FP32 accumulation) against the FP64 oracle.
+
+* The GEMM is compared with an FP64 product of the same BF16-rounded operands,
+  so only the FP32 accumulation differs (bar 1e-5 relative).
+* The network's forward output and every parameter group's gradient are
+  compared with the FP64 oracle.  BF16 operands carry 8 significant bits
+  (relative rounding 2^-9 = 2e-3), so a chain of contractions lands at a
+  few 1e-3 to 1e-2; the bars are 2e-2 (forward) and 5e-2 (gradients, which
+  pass through twice as many contractions).
+* Training with the project's own forward, backward and Adam kernels
+  reduces the loss.
+"""
+import numpy as np
+import pytest
+
+import oracle.fno_oracle as F
+from paper_1909_08354_b300 import sn
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def bf16_round(x):
+    """Round float32 values to the nearest BF16 (ties to even), returned as float64."""
+    u = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K,Z", [(70, 45, 37, 3), (64, 128, 256, 2), (5, 300, 16, 4)])
+def test_gemm_bf16_strided(M, N, K, Z):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((Z, K, M)).astype(np.float32)      # stored transposed
+    B = rng.standard_normal((Z, N, K)).astype(np.float32)      # stored transposed
+    C0 = rng.standard_normal((Z, M, N)).astype(np.float32)
+    ref = np.einsum("zkm,znk->zmn", bf16_round(A), bf16_round(B)) * 0.5 + C0
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.from_numpy(C0).cuda()
+    sn.sn_test_gemm_bf16(dA, (K * M, 1, M), dB, (N * K, 1, K), dC, (M * N, N, 1), M, N, K, Z,
+                         alpha=0.5, beta=1.0)
+    got = dC.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max() * np.sqrt(K)
+
+
+SMALL = F.FnoShape(s=32, c_in=5, width=8, modes=4, layers=2, proj=8)
+
+
+def small_problem(seed=5):
+    p = F.init_params(SMALL, seed)
+    for l in range(SMALL.layers):
+        p[f"R{l}"] = p[f"R{l}"] * 30.0
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((2, SMALL.c_in, SMALL.s, SMALL.s))
+    t = a[:, :2] + 0.3 * rng.standard_normal((2, 2, SMALL.s, SMALL.s))
+    return p, a, t
+
+
+def make_net(sh, batch):
+    return sn.Fno(s=sh.s, c_in=sh.c_in, width=sh.width, modes=sh.modes, layers=sh.layers,
+                  proj=sh.proj, batch_max=batch)
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def test_forward_and_gradients_match_oracle():
+    p, a, t = small_problem()
+    out_ref, cache = F.forward(p, a, SMALL)
+    loss_ref, dout = F.rel_l2_loss(out_ref, t)
+    g_ref = F.backward(p, cache, dout, SMALL)
+    net = make_net(SMALL, 2)
+    net.set_params(F.flatten(SMALL, p).astype(np.float32))
+    x = torch.from_numpy(a.astype(np.float32)).cuda()
+    y = torch.empty((2, 2, SMALL.s, SMALL.s), dtype=torch.float32, device="cuda")
+    net.forward(x, y)
+    loss = net.loss(torch.from_numpy(t.astype(np.float32)).cuda(), 2)
+    assert rel(y.cpu().numpy(), out_ref) <= 2e-2
+    assert abs(loss - loss_ref) <= 2e-2 * loss_ref
+    net.backward()
+    g = F.unflatten(SMALL, net.get_grads().astype(np.float64))
+    for name in g_ref:
+        assert rel(g[name], g_ref[name]) <= 5e-2, name
+    net.close()
+
+
+def test_training_reduces_loss():
+    sh = F.FnoShape(s=32, c_in=3, width=16, modes=6, layers=2, proj=16)
+    rng = np.random.default_rng(0)
+    # band-limited inputs (modes below the kept ones), so the map is representable
+    spec = np.zeros((8, sh.c_in, sh.s, sh.s), complex)
+    spec[:, :, :4, :4] = rng.standard_normal((8, sh.c_in, 4, 4)) + 1j * rng.standard_normal((8, sh.c_in, 4, 4))
+    a = (np.fft.ifft2(spec).real * sh.s).astype(np.float32)
+    # target: the (re, im) channels translated by 3 cells in x, a shift operator
+    t = np.roll(a[:, :2], 3, axis=-1).astype(np.float32)
+    net = make_net(sh, 8)
+    net.set_params(F.flatten(sh, F.init_params(sh, 1)).astype(np.float32))
+    x, tt = torch.from_numpy(a).cuda(), torch.from_numpy(t).cuda()
+    y = torch.empty((8, 2, sh.s, sh.s), dtype=torch.float32, device="cuda")
+    losses = []
+    for it in range(1, 201):
+        net.forward(x, y)
+        losses.append(net.loss(tt, 8))
+        net.backward()
+        net.adam(2e-3, it)
+    assert losses[-1] < 0.3 * losses[0], (losses[0], losses[-1])
+    net.close()
