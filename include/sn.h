@@ -134,6 +134,32 @@ sn_status sn_profile_step(sn_grid g, double dt, int nsteps, double* ms, long lon
 /* Name of kernel kind k, or NULL past the last kind. */
 const char* sn_kind_name(int k);
 
+/* Line-transform engine of a complex64 grid's fused step.  Every pass of
+ * sn_step is a batch of 1D DFTs along one axis (the split-step Fourier method
+ * of Sec. III: the kinetic factor of Eq. 1 per axis, and the spectral solve of
+ * Eq. 2 / the Eq. 9 kernel); the engine decides how they are computed.
+ *   SN_ENGINE_FP32 (default): FP32 radix-16/32 Stockham stages on CUDA cores.
+ *   SN_ENGINE_TC16: on axes of length 256, each 16-point DFT stage runs on
+ *     the tensor cores as real 32 x 32 blocks of FP16 operands split into
+ *     hi + lo parts (F_hi x_hi + F_hi x_lo + F_lo x_hi, FP32 accumulation,
+ *     per-line power-of-two scaling); twiddles and the spectral multipliers
+ *     stay FP32.  Axes of other lengths keep the FP32 engine.
+ * Both engines give the same step to FP32 rounding.  The paper's own solver
+ * has no counterpart of this switch (its FFTs are library calls).
+ * Errors: SN_EINVAL (NULL grid, unknown engine), SN_ENOTSUP (TC16 on a
+ * complex128 grid), SN_ENOMEM / SN_ECUDA (table upload). */
+typedef enum { SN_ENGINE_FP32 = 0, SN_ENGINE_TC16 = 1 } sn_engine;
+sn_status sn_set_engine(sn_grid g, int engine);
+
+/* Test hook: in-place unnormalised DFTs, sign -1 (exp(-i ...)) or +1, of
+ * nlines contiguous complex64 lines of length n (power of two, 8..1024) in
+ * device memory, computed by the fused passes' line engine (engine as in
+ * sn_set_engine; TC16 applies to n = 256).  Synchronous on cuda_stream (NULL:
+ * the legacy default stream).  Errors: SN_EINVAL, SN_ECUDA (message in
+ * sn_last_error(NULL)). */
+sn_status sn_test_line_fft_f32(void* data, long long nlines, int n, int sign, int engine,
+                               void* cuda_stream);
+
 /* ---------------------------------------------------------------------------
  * Batched scan: many independent 2D complex64 problems of uneven size
  * advanced together (Sec. III step applied to each; e.g. a scan over the
@@ -182,7 +208,9 @@ void sn_destroy_batch(sn_batch b);
  *   (no gelu after the last layer);  Spec(v) keeps the modes
  *   ky in {0..m-1} u {s-m..s-1}, kx in {0..m-1}:
  *   Spec(v) = (1/s^2) sum w_kx Re(U e^{+i th}), U = R V per mode, V = sum v e^{-i th}
- *   out = a[0:2] + Q2 gelu(Q1 v_L + q1b) + q2b
+ *   (phi, dr, di) = Q2 gelu(Q1 v_L + q1b) + q2b;  out = psi e^{-i phi} + (dr + i di)
+ *   with psi = a[0] + i a[1] (the head turns the input state by a learned phase
+ *   field, the dominant effect of the nonlinear sub-step over 50 steps)
  * Parameters are one flat FP32 vector in the order P, pb, then per layer R
  * ([2m][m][C][C][re,im]), W, b, then Q1, q1b, Q2, q2b.  Every contraction runs
  * on the tensor cores with BF16 operands and FP32 accumulation.  All array
@@ -208,6 +236,14 @@ sn_status sn_fno_backward(sn_fno f);
 sn_status sn_fno_adam(sn_fno f, double lr, double beta1, double beta2, double eps, int t);
 sn_status sn_fno_sync(sn_fno f);
 void sn_fno_destroy(sn_fno f);
+/* Surrogate input/output marshalling on the device: X[b] = (re psi, im psi,
+ * feats[b][0..nfeat-1] as constant planes), planar [B][2+nfeat][cells];
+ * psi[b] (interleaved complex64) from Y[b] = (re, im) planes. */
+sn_status sn_fno_pack(const float* psi, const float* feats, int nfeat, float* X, int B,
+                      long long cells, void* cuda_stream);
+sn_status sn_fno_unpack(const float* Y, float* psi, int B, long long cells, void* cuda_stream);
+/* out[b] = sum |psi_b|^2 (FP64, device output) for B complex64 states of `cells` values. */
+sn_status sn_mass_c64(const float* psi, int B, long long cells, double* out, void* cuda_stream);
 /* Test hook: the BF16 tensor-core GEMM C[z] = alpha A[z] B[z] + beta C[z] on
  * device pointers with element strides (see the FNO), synchronous. */
 sn_status sn_test_gemm_bf16(const float* A, long long sAz, long long sAm, long long sAk,

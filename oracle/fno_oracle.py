@@ -15,7 +15,10 @@ kx in {0..m-1}):
   for l < L:  z_l = Spec_l(v_l) + W_l v_l + b_l,  v_{l+1} = gelu(z_l)  (last: v_L = z_{L-1})
   Spec(v)(y,x) = (1/s^2) sum_{ky,kx} w_kx Re( U[ky,kx] e^{+i th} ),  th = 2 pi (ky y + kx x)/s,
       U[o] = sum_i R[ky,kx,i,o] V[i],  V[i] = sum_{y,x} v_i(y,x) e^{-i th},  w_0 = 1, w_{kx>0} = 2
-  h = gelu(Q1 v_L + q1b),   out = a[:2] + Q2 h + q2b   (residual on the re, im channels)
+  h = gelu(Q1 v_L + q1b),   (phi, dr, di) = Q2 h + q2b   (three output channels)
+  out = psi e^{-i phi} + (dr + i di),  psi = a[0] + i a[1]
+        (the head turns the input state by a predicted phase field, the dominant effect
+         of the nonlinear sub-step, and adds a correction)
   loss = mean_b ||out_b - target_b|| / ||target_b||
 gelu(x) = x Phi(x) with the normal CDF Phi (the erf form).
 """
@@ -64,8 +67,8 @@ def param_shapes(sh: FnoShape) -> List[tuple]:
     for l in range(sh.layers):
         shapes += [(f"R{l}", (2 * sh.modes, sh.modes, sh.width, sh.width, 2)),
                    (f"W{l}", (sh.width, sh.width)), (f"b{l}", (sh.width,))]
-    shapes += [("Q1", (sh.proj, sh.width)), ("q1b", (sh.proj,)), ("Q2", (2, sh.proj)),
-               ("q2b", (2,))]
+    shapes += [("Q1", (sh.proj, sh.width)), ("q1b", (sh.proj,)), ("Q2", (3, sh.proj)),
+               ("q2b", (3,))]
     return shapes
 
 
@@ -122,8 +125,17 @@ def forward(params: Dict[str, np.ndarray], a: np.ndarray, sh: FnoShape):
     g1 = np.einsum("jo,boyx->bjyx", params["Q1"], v) + params["q1b"][None, :, None, None]
     h = _gelu(g1)
     cache["g1"], cache["h"] = g1, h
-    out = a[:, :2] + np.einsum("kj,bjyx->bkyx", params["Q2"], h) + params["q2b"][None, :, None, None]
+    y = np.einsum("kj,bjyx->bkyx", params["Q2"], h) + params["q2b"][None, :, None, None]
+    cache["y"] = y
+    out = head(a, y)
     return out, cache
+
+
+def head(a: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """psi e^{-i phi} + (dr + i di) as (re, im) planes; psi = a[0] + i a[1], (phi, dr, di) = y."""
+    pr, pi, ph = a[:, 0], a[:, 1], y[:, 0]
+    c, s = np.cos(ph), np.sin(ph)
+    return np.stack([pr * c + pi * s + y[:, 1], pi * c - pr * s + y[:, 2]], axis=1)
 
 
 def rel_l2_loss(out: np.ndarray, target: np.ndarray):
@@ -141,10 +153,15 @@ def rel_l2_loss(out: np.ndarray, target: np.ndarray):
 def backward(params: Dict[str, np.ndarray], cache, dout: np.ndarray, sh: FnoShape):
     """Gradients of a scalar loss with respect to every parameter, given dL/dout."""
     g = {}
-    h, g1 = cache["h"], cache["g1"]
-    g["Q2"] = np.einsum("bkyx,bjyx->kj", dout, h)
-    g["q2b"] = dout.sum(axis=(0, 2, 3))
-    dh = np.einsum("kj,bkyx->bjyx", params["Q2"], dout)
+    h, g1, y, a = cache["h"], cache["g1"], cache["y"], cache["a"]
+    # head: d out_r / d phi = rot_i, d out_i / d phi = -rot_r with rot = psi e^{-i phi}
+    c, s = np.cos(y[:, 0]), np.sin(y[:, 0])
+    rot_r = a[:, 0] * c + a[:, 1] * s
+    rot_i = a[:, 1] * c - a[:, 0] * s
+    dy = np.stack([dout[:, 0] * rot_i - dout[:, 1] * rot_r, dout[:, 0], dout[:, 1]], axis=1)
+    g["Q2"] = np.einsum("bkyx,bjyx->kj", dy, h)
+    g["q2b"] = dy.sum(axis=(0, 2, 3))
+    dh = np.einsum("kj,bkyx->bjyx", params["Q2"], dy)
     dg1 = dh * _gelu_grad(g1)
     vL = cache[f"v{sh.layers}"]
     g["Q1"] = np.einsum("bjyx,boyx->jo", dg1, vL)

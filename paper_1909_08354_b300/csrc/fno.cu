@@ -7,7 +7,8 @@
 //   v0 = P a + pb
 //   z_l = Spec_l(v_l) + W_l v_l + b_l,  v_{l+1} = gelu(z_l) (identity after the last layer)
 //   Spec(v) = (1/s^2) sum w_kx Re(U e^{+i th}), U = R V (per mode), V = sum v e^{-i th}
-//   h = gelu(Q1 v_L + q1b),  out = a[0:2] + Q2 h + q2b
+//   h = gelu(Q1 v_L + q1b),  (phi, dr, di) = Q2 h + q2b,
+//   out = psi e^{-i phi} + (dr + i di)  with psi = a[0] + i a[1]
 // The truncated DFTs are separable real GEMMs: along x with an s x 2m
 // cos/sin matrix, along y per plane with a 4m x s block matrix.  Mode mixing
 // is a batch of Nm complex C x C GEMMs written as four real ones.
@@ -41,6 +42,7 @@ struct sn_fno_s {
   float *EyIre = nullptr, *EyIim = nullptr, *WxI = nullptr, *WxI1 = nullptr;
   float *a = nullptr, *A1 = nullptr, *Uh = nullptr, *B1 = nullptr, *g1 = nullptr, *h = nullptr;
   float *out = nullptr, *dout = nullptr, *dv = nullptr, *dv2 = nullptr, *dz = nullptr, *dh = nullptr;
+  float *yh = nullptr, *dy = nullptr;  // head channels (phi, dr, di) and their gradient
   float *GU = nullptr, *GV = nullptr, *work = nullptr;
   std::vector<float*> v, z, Vh;
   double* norms = nullptr;  // per sample (||out - t||^2, ||t||^2)
@@ -105,11 +107,32 @@ __global__ void gelu_bwd_kernel(const float* dv, const float* z, float* dz, ll n
     dz[i] = dv[i] * gelu_grad(z[i]);
 }
 
-// out[b][k][p] = a[b][k][p] + q2b[k], k in {0, 1}
-__global__ void out_init_kernel(const float* a, const float* q2b, float* out, ll ci, ll P, ll n) {
+// out = psi e^{-i phi} + (dr + i di): psi = (a[b][0], a[b][1]), (phi, dr, di) = y[b][0..2]
+__global__ void head_kernel(const float* a, const float* y, float* out, ll ci, ll P, ll n) {
   for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
-    const ll b = i / (2 * P), r = i - b * 2 * P, k = r / P;
-    out[i] = a[b * ci * P + r] + q2b[k];
+    const ll b = i / P, p = i - b * P;
+    const float pr = a[b * ci * P + p], pi = a[b * ci * P + P + p];
+    const float* yy = y + b * 3 * P + p;
+    float s, c;
+    sincosf(yy[0], &s, &c);
+    out[b * 2 * P + p] = pr * c + pi * s + yy[P];
+    out[b * 2 * P + P + p] = pi * c - pr * s + yy[2 * P];
+  }
+}
+
+// dy = (dout_r rot_i - dout_i rot_r, dout_r, dout_i) with rot = psi e^{-i phi}
+__global__ void head_bwd_kernel(const float* a, const float* y, const float* dout, float* dy, ll ci,
+                                ll P, ll n) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
+    const ll b = i / P, p = i - b * P;
+    const float pr = a[b * ci * P + p], pi = a[b * ci * P + P + p];
+    float s, c;
+    sincosf(y[b * 3 * P + p], &s, &c);
+    const float rr = pr * c + pi * s, ri = pi * c - pr * s;
+    const float gr = dout[b * 2 * P + p], gi = dout[b * 2 * P + P + p];
+    dy[b * 3 * P + p] = gr * ri - gi * rr;
+    dy[b * 3 * P + P + p] = gr;
+    dy[b * 3 * P + 2 * P + p] = gi;
   }
 }
 
@@ -176,6 +199,43 @@ __global__ void adam_kernel(float* p, const float* g, float* m, float* v, ll n, 
     v[i] = vi;
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
   }
+}
+
+// X[b] = (re, im, f0, f1, f2) planes from interleaved psi[b] and feats[b][3]
+__global__ void pack_kernel(const float2* psi, const float* feats, int nf, float* X, ll P, ll n) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
+    const ll b = i / P, p = i - b * P;
+    const float2 z = psi[i];
+    float* x = X + b * (2 + nf) * P + p;
+    x[0] = z.x;
+    x[P] = z.y;
+    for (int k = 0; k < nf; ++k) x[(2 + k) * P] = feats[b * nf + k];
+  }
+}
+
+__global__ void unpack_kernel(const float* Y, float2* psi, ll P, ll n) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
+    const ll b = i / P, p = i - b * P;
+    psi[i] = make_float2(Y[b * 2 * P + p], Y[b * 2 * P + P + p]);
+  }
+}
+
+// out[b] = sum_p |psi[b][p]|^2 (FP64, one block per state, fixed order)
+__global__ void mass_kernel(const float2* psi, ll P, double* out) {
+  const ll b = blockIdx.x;
+  double s = 0.0;
+  for (ll p = threadIdx.x; p < P; p += blockDim.x) {
+    const float2 z = psi[b * P + p];
+    s += (double)z.x * z.x + (double)z.y * z.y;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[b] = red[0];
 }
 
 // ---- GEMM plumbing --------------------------------------------------------------
@@ -355,8 +415,8 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
   }
   f->off_Q1 = off; off += (ll)proj * C;
   f->off_q1b = off; off += proj;
-  f->off_Q2 = off; off += 2LL * proj;
-  f->off_q2b = off; off += 2;
+  f->off_Q2 = off; off += 3LL * proj;
+  f->off_q2b = off; off += 3;
   f->nparams = off;
   const ll B = batch_max, P = f->P;
   if ((e = falloc(f, &f->params, off)) != cudaSuccess || (e = falloc(f, &f->grads, off)) != cudaSuccess ||
@@ -394,6 +454,8 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
   ok = ok && falloc(f, &f->h, B * proj * P) == cudaSuccess;
   ok = ok && falloc(f, &f->dh, B * proj * P) == cudaSuccess;
   ok = ok && falloc(f, &f->out, B * 2 * P) == cudaSuccess;
+  ok = ok && falloc(f, &f->yh, B * 3 * P) == cudaSuccess;
+  ok = ok && falloc(f, &f->dy, B * 3 * P) == cudaSuccess;
   ok = ok && falloc(f, &f->dout, B * 2 * P) == cudaSuccess;
   ok = ok && falloc(f, &f->dv, plane) == cudaSuccess;
   ok = ok && falloc(f, &f->dv2, plane) == cudaSuccess;
@@ -401,7 +463,7 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
   ok = ok && falloc(f, &f->norms, 2 * B) == cudaSuccess;
   const ll nsplit = (P + 8191) / 8192;
   const ll mn = std::max<ll>((ll)proj * C, std::max<ll>(C * C, C * (ll)c_in));
-  f->work_floats = B * nsplit * std::max<ll>(mn, 2LL * proj);
+  f->work_floats = B * nsplit * std::max<ll>(mn, 3LL * proj);
   ok = ok && falloc(f, &f->work, f->work_floats) == cudaSuccess;
   if (!ok) return bail(ffail(SN_ENOMEM, "sn_fno_create: device allocation failed"));
   *out = f;
@@ -459,9 +521,11 @@ sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
   // projection
   FCHK(gemm(f, (int)J, (int)P, (int)C, B, prm + f->off_Q1, 0, C, 1, f->v[f->L], C * P, P, 1, f->g1, J * P, P, 1));
   bias_act_kernel<<<blocks_for(B * J * P), 256, 0, st>>>(f->g1, prm + f->off_q1b, f->h, J, P, B * J * P, 1);
-  out_init_kernel<<<blocks_for(B * 2 * P), 256, 0, st>>>(f->a, prm + f->off_q2b, f->out, ci, P, B * 2 * P);
   FCHK(cudaGetLastError());
-  FCHK(gemm(f, 2, (int)P, (int)J, B, prm + f->off_Q2, 0, J, 1, f->h, J * P, P, 1, f->out, 2 * P, P, 1, 1.f, 1.f));
+  FCHK(gemm(f, 3, (int)P, (int)J, B, prm + f->off_Q2, 0, J, 1, f->h, J * P, P, 1, f->yh, 3 * P, P, 1));
+  bias_act_kernel<<<blocks_for(B * 3 * P), 256, 0, st>>>(f->yh, prm + f->off_q2b, nullptr, 3, P, B * 3 * P, 0);
+  head_kernel<<<blocks_for(B * P), 256, 0, st>>>(f->a, f->yh, f->out, ci, P, B * P);
+  FCHK(cudaGetLastError());
   if (out != f->out)
     FCHK(cudaMemcpyAsync(out, f->out, (size_t)B * 2 * P * sizeof(float), cudaMemcpyDeviceToDevice, st));
   f->lastB = B;
@@ -491,10 +555,12 @@ sn_status sn_fno_backward(sn_fno f) {
   cudaStream_t st = f->stream;
   float* prm = f->params;
   float* gr = f->grads;
-  // projection
-  FCHK(weight_grad(f, f->dout, f->h, B, 2, (int)J, gr + f->off_Q2));
-  channel_sum_kernel<<<2, 256, 0, st>>>(f->dout, B, 2, P, gr + f->off_q2b);
-  FCHK(gemm(f, (int)J, (int)P, 2, B, prm + f->off_Q2, 0, 1, J, f->dout, 2 * P, P, 1, f->dh, J * P, P, 1));
+  // head and projection
+  head_bwd_kernel<<<blocks_for(B * P), 256, 0, st>>>(f->a, f->yh, f->dout, f->dy, ci, P, B * P);
+  FCHK(cudaGetLastError());
+  FCHK(weight_grad(f, f->dy, f->h, B, 3, (int)J, gr + f->off_Q2));
+  channel_sum_kernel<<<3, 256, 0, st>>>(f->dy, B, 3, P, gr + f->off_q2b);
+  FCHK(gemm(f, (int)J, (int)P, 3, B, prm + f->off_Q2, 0, 1, J, f->dy, 3 * P, P, 1, f->dh, J * P, P, 1));
   gelu_bwd_kernel<<<blocks_for(B * J * P), 256, 0, st>>>(f->dh, f->g1, f->dh, B * J * P);
   FCHK(cudaGetLastError());
   FCHK(weight_grad(f, f->dh, f->v[f->L], B, (int)J, (int)C, gr + f->off_Q1));
@@ -544,6 +610,31 @@ void sn_fno_destroy(sn_fno f) {
   for (void* p : f->allocs) cudaFree(p);
   if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
   delete f;
+}
+
+sn_status sn_fno_pack(const float* psi, const float* feats, int nfeat, float* X, int B,
+                       long long cells, void* cuda_stream) {
+  if (!psi || !X || B < 1 || cells < 1 || nfeat < 0 || (nfeat > 0 && !feats))
+    return ffail(SN_EINVAL, "sn_fno_pack: bad argument");
+  pack_kernel<<<blocks_for((ll)B * cells), 256, 0, (cudaStream_t)cuda_stream>>>(
+      reinterpret_cast<const float2*>(psi), feats, nfeat, X, cells, (ll)B * cells);
+  FCHK(cudaGetLastError());
+  return SN_OK;
+}
+
+sn_status sn_fno_unpack(const float* Y, float* psi, int B, long long cells, void* cuda_stream) {
+  if (!Y || !psi || B < 1 || cells < 1) return ffail(SN_EINVAL, "sn_fno_unpack: bad argument");
+  unpack_kernel<<<blocks_for((ll)B * cells), 256, 0, (cudaStream_t)cuda_stream>>>(
+      Y, reinterpret_cast<float2*>(psi), cells, (ll)B * cells);
+  FCHK(cudaGetLastError());
+  return SN_OK;
+}
+
+sn_status sn_mass_c64(const float* psi, int B, long long cells, double* out, void* cuda_stream) {
+  if (!psi || !out || B < 1 || cells < 1) return ffail(SN_EINVAL, "sn_mass_c64: bad argument");
+  mass_kernel<<<B, 256, 0, (cudaStream_t)cuda_stream>>>(reinterpret_cast<const float2*>(psi), cells, out);
+  FCHK(cudaGetLastError());
+  return SN_OK;
 }
 
 sn_status sn_test_gemm_bf16(const float* A, long long sAz, long long sAm, long long sAk,

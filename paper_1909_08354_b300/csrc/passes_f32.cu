@@ -19,6 +19,8 @@
 // tile's psi is already in flight into registers and (P1) the next tile's half
 // spectrum into shared memory through cp.async, so the HBM stream does not
 // wait for the arithmetic.
+#include <cmath>
+
 #include "sn_fft.cuh"
 #include "sn_internal.h"
 #include "tile_ops.cuh"
@@ -73,21 +75,34 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // shared memory: twiddles (hi, lo), kinetic factors (hi, lo), line buffers,
-// and for P1 two staging tiles of the half spectrum
-template <int N, int VARIANT>
+// and for P1 two staging tiles of the half spectrum.  The tensor-core engine
+// (TC, 256-point lines) keeps its fragment and twiddle tables, a padded copy
+// of the kinetic factors and padded line buffers instead.
+template <int N, int VARIANT, bool TC>
 constexpr size_t psi_smem_bytes() {
-  return (size_t)(2 * Plan<N>::TWN + 2 * N + lpb<N>() * Plan<N>::LS +
-                  (VARIANT == PSI_NPHASE ? 2 * (N / 2 + 1) * (lpb<N>() + 1) : 0)) *
-         sizeof(cx<float>);
+  constexpr size_t stage =
+      (VARIANT == PSI_NPHASE ? 2 * (N / 2 + 1) * (lpb<N>() + 1) : 0) * sizeof(cx<float>);
+  if constexpr (TC) {
+    return sizeof(tc16::Tabs) + 2 * tc16::MT * sizeof(float2) +
+           (size_t)lpb<N>() * tc16::LS * sizeof(float2) + stage;
+  } else {
+    return (size_t)(2 * Plan<N>::TWN + 2 * N + lpb<N>() * Plan<N>::LS) * sizeof(cx<float>) + stage;
+  }
 }
-template <int N>
+template <int N, bool TC>
 constexpr size_t rho_smem_bytes() {
-  return (size_t)(2 * Plan<N>::TWN + lpb<N>() * Plan<N>::LS) * sizeof(cx<float>);
+  if constexpr (TC) {
+    return sizeof(tc16::Tabs) + tc16::MT * sizeof(float) + 16 * sizeof(float) +
+           (size_t)lpb<N>() * tc16::LS * sizeof(float2);
+  } else {
+    return (size_t)(2 * Plan<N>::TWN + lpb<N>() * Plan<N>::LS) * sizeof(cx<float>);
+  }
 }
 
-template <int N, bool STRIDED, int VARIANT>
+template <int N, bool STRIDED, int VARIANT, bool TC>
 __global__ void __launch_bounds__(cta_threads<N>(), min_ctas<N>())
 psi_pass_kernel(PsiPassArgs a) {
+  static_assert(!TC || N == tc16::N, "the tensor-core engine handles 256-point lines");
   using P = Plan<N>;
   constexpr int LPB = lpb<N>(), TSTR = LPB + 1;
   constexpr int E = P::E, T = P::T, NT = LPB * T, LS = P::LS, H = N / 2 + 1;
@@ -99,7 +114,10 @@ psi_pass_kernel(PsiPassArgs a) {
   cx<float>* tw_sm = reinterpret_cast<cx<float>*>(smem_raw);
   cx<float>* mult_sm = tw_sm + 2 * P::TWN;
   cx<float>* lines = mult_sm + 2 * N;
-  cx<float>* rstage = lines + LPB * LS;  // P1: two [H][TSTR] tiles
+  tc16::Tabs* tabs = reinterpret_cast<tc16::Tabs*>(smem_raw);
+  float2* mult_tc = reinterpret_cast<float2*>(smem_raw + sizeof(tc16::Tabs));
+  if constexpr (TC) lines = reinterpret_cast<cx<float>*>(mult_tc + 2 * tc16::MT);
+  cx<float>* rstage = lines + LPB * (TC ? tc16::LS : LS);  // P1: two [H][TSTR] tiles
 
   const int tid = threadIdx.x;
   const int l = STRIDED ? (tid % LPB) : (tid / T);
@@ -110,8 +128,13 @@ psi_pass_kernel(PsiPassArgs a) {
   // bits (a grid holds at most 2^30 cells)
   const unsigned ustride = STRIDED ? (unsigned)a.inner : 1u;
 
-  for (int k = tid; k < 2 * P::TWN; k += NT) tw_sm[k] = ldc(a.tw + k);
-  for (int k = tid; k < 2 * N; k += NT) mult_sm[k] = ldc(a.mult + k);
+  if constexpr (TC) {
+    tc16::load_tabs(tabs, a.tc, a.tw, tid, NT);
+    for (int k = tid; k < 2 * N; k += NT) mult_tc[(k / N) * tc16::MT + tc16::pt(k % N)] = a.mult[k];
+  } else {
+    for (int k = tid; k < 2 * P::TWN; k += NT) tw_sm[k] = ldc(a.tw + k);
+    for (int k = tid; k < 2 * N; k += NT) mult_sm[k] = ldc(a.mult + k);
+  }
 
   // P1: stage the [k][line] half-spectrum tile of tile tau into shared memory
   auto stage_rho = [&](cx<float>* dst, long long tau) {
@@ -155,7 +178,8 @@ psi_pass_kernel(PsiPassArgs a) {
       cp_async_commit();
       cp_async_wait<1>();
       __syncthreads();
-      tile::potential_c2r<N, LPB, WL>(rstage + (it & 1) * (H * TSTR), lines, tw_sm, l, t, vph);
+      tile::potential_c2r<N, LPB, WL, TC>(rstage + (it & 1) * (H * TSTR), lines, tw_sm, l, t,
+                                          vph, tabs);
     }
 
     // ---- this tile's psi (loaded one iteration ago); start the next tile's load
@@ -177,30 +201,41 @@ psi_pass_kernel(PsiPassArgs a) {
       tile::nonlinear_phase<E, T>(v, vph, a.gh, a.vext != nullptr ? a.vext + base : nullptr, a.h,
                                   ustride, t, valid);
     }
-    tile::kinetic<N, WL>(v, lines + l * LS, tw_sm, mult_sm, t);
+    if constexpr (TC) {
+      const tc16::MultTable mt{mult_tc, mult_tc + tc16::MT};
+      tc16::fmi(v, lines, *tabs, l, t, [&](int) { return mt; });
+    } else {
+      tile::kinetic<N, WL>(v, lines + l * LS, tw_sm, mult_sm, t);
+    }
     store_line<E, T>(v, a.psi + base, ustride, t, valid);
 
     if constexpr (DENSITY) {
       float2* rh = a.rh_out;
-      tile::density_r2c<N, LPB, WL>(v, valid, lines, tw_sm, l, t, tid, nvalid,
-                                    [&](int k, int ll, cx<float> z) {
-                                      tile::stg_c(rh + (size_t)k * nlines + line0 + ll, z);
-                                    });
+      auto put = [&](int k, int ll, cx<float> z) {
+        tile::stg_c(rh + (size_t)k * nlines + line0 + ll, z);
+      };
+      tile::density_r2c<N, LPB, WL, decltype(put), TC>(v, valid, lines, tw_sm, l, t, tid, nvalid,
+                                                       put, tabs);
     }
     __syncthreads();  // line buffers and the staging tile are reused next iteration
   }
   if constexpr (NPHASE) cp_async_wait<0>();
 }
 
-template <int N, bool STRIDED, int OP>
+template <int N, bool STRIDED, int OP, bool TC>
 __global__ void __launch_bounds__(cta_threads<N>(), min_ctas<N>())
 rho_pass_kernel(RhoPassArgs a) {
+  static_assert(!TC || N == tc16::N, "the tensor-core engine handles 256-point lines");
   using P = Plan<N>;
   constexpr int LPB = lpb<N>();
   constexpr int E = P::E, T = P::T, NT = LPB * T, LS = P::LS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw_sm = reinterpret_cast<cx<float>*>(smem_raw);
   cx<float>* lines = tw_sm + 2 * P::TWN;
+  tc16::Tabs* tabs = reinterpret_cast<tc16::Tabs*>(smem_raw);
+  float* k2l_tc = reinterpret_cast<float*>(smem_raw + sizeof(tc16::Tabs));  // padded k^2 of the line axis
+  float* k2pm_sm = k2l_tc + tc16::MT;                                     // per-line k^2 of the others
+  if constexpr (TC) lines = reinterpret_cast<cx<float>*>(k2pm_sm + 16);
 
   const int tid = threadIdx.x;
   const int l = STRIDED ? (tid % LPB) : (tid / T);
@@ -209,7 +244,13 @@ rho_pass_kernel(RhoPassArgs a) {
   const unsigned ustride = STRIDED ? (unsigned)a.inner : 1u;
   constexpr bool PF = E <= 16;  // register prefetch of the next tile (lines up to 256)
   constexpr bool WL = !STRIDED && T <= 32;  // a contiguous line lives in one warp
-  for (int k = tid; k < 2 * P::TWN; k += NT) tw_sm[k] = ldc(a.tw + k);
+  if constexpr (TC) {
+    tc16::load_tabs(tabs, a.tc, a.tw, tid, NT);
+    if constexpr (OP == RHO_GREEN)
+      for (int k = tid; k < N; k += NT) k2l_tc[tc16::pt(k)] = a.k2l[k];
+  } else {
+    for (int k = tid; k < 2 * P::TWN; k += NT) tw_sm[k] = ldc(a.tw + k);
+  }
 
   cx<float> vn[E];
   long long tau = blockIdx.x;
@@ -244,9 +285,9 @@ rho_pass_kernel(RhoPassArgs a) {
       load_line<E, T>(v, a.data + base, ustride, t, valid);
     }
     if constexpr (OP == RHO_INV) {
-      line_transform<float, N, +1, WL>(v, lines + l * LS, tw_sm, t, true);
+      tile::xform<N, +1, WL, TC>(v, lines, tw_sm, tabs, l, t, LPB);
     } else if constexpr (OP == RHO_FWD) {
-      line_transform<float, N, -1, WL>(v, lines + l * LS, tw_sm, t, true);
+      tile::xform<N, -1, WL, TC>(v, lines, tw_sm, tabs, l, t, LPB);
     } else {
       long long plane, mid;
       if constexpr (STRIDED) {
@@ -258,7 +299,14 @@ rho_pass_kernel(RhoPassArgs a) {
       }
       float k2pm = 0.f;
       if (valid) k2pm = a.k2p[plane] + a.k2m[mid];
-      tile::green<N, WL>(v, lines + l * LS, tw_sm, a.k2l, k2pm, a.cN, a.cY, a.mu2, t);
+      if constexpr (TC) {
+        if (t == 0) k2pm_sm[l] = k2pm;  // read after the entry barriers of fmi
+        tc16::fmi(v, lines, *tabs, l, t, [&](int L) {
+          return tc16::GreenMult{k2l_tc, k2pm_sm[L], a.cN, a.cY, a.mu2};
+        });
+      } else {
+        tile::green<N, WL>(v, lines + l * LS, tw_sm, a.k2l, k2pm, a.cN, a.cY, a.mu2, t);
+      }
     }
     store_line<E, T>(v, a.data + base, ustride, t, valid);
   }
@@ -288,11 +336,11 @@ long long host_tiles(long long outer, long long inner) {
   return STRIDED ? outer * ((inner + LPB - 1) / LPB) : (outer + LPB - 1) / LPB;
 }
 
-template <int N, bool STRIDED, int VARIANT>
+template <int N, bool STRIDED, int VARIANT, bool TC = false>
 cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
-  constexpr size_t smem = psi_smem_bytes<N, VARIANT>();
+  constexpr size_t smem = psi_smem_bytes<N, VARIANT, TC>();
   constexpr int threads = cta_threads<N>();
-  auto kern = psi_pass_kernel<N, STRIDED, VARIANT>;
+  auto kern = psi_pass_kernel<N, STRIDED, VARIANT, TC>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -304,11 +352,11 @@ cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int N, bool STRIDED, int OP>
+template <int N, bool STRIDED, int OP, bool TC = false>
 cudaError_t launch_rho_t(const RhoPassArgs& a, cudaStream_t s) {
-  constexpr size_t smem = rho_smem_bytes<N>();
+  constexpr size_t smem = rho_smem_bytes<N, TC>();
   constexpr int threads = cta_threads<N>();
-  auto kern = rho_pass_kernel<N, STRIDED, OP>;
+  auto kern = rho_pass_kernel<N, STRIDED, OP, TC>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -318,6 +366,37 @@ cudaError_t launch_rho_t(const RhoPassArgs& a, cudaStream_t s) {
   const long long ntiles = host_tiles<lpb<N>(), STRIDED>(a.outer, a.inner);
   kern<<<persistent_ctas(kern, threads, smem, ntiles), threads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// tensor-core engine: 256-point lines when the caller passes the fragment table
+cudaError_t psi_dispatch_tc(bool strided, int variant, const PsiPassArgs& a, cudaStream_t s) {
+  if (strided) {
+    switch (variant) {
+      case PSI_PLAIN: return launch_psi_t<256, true, PSI_PLAIN, true>(a, s);
+      case PSI_NPHASE: return launch_psi_t<256, true, PSI_NPHASE, true>(a, s);
+      default: return launch_psi_t<256, true, PSI_DENSITY, true>(a, s);
+    }
+  }
+  switch (variant) {
+    case PSI_PLAIN: return launch_psi_t<256, false, PSI_PLAIN, true>(a, s);
+    case PSI_NPHASE: return launch_psi_t<256, false, PSI_NPHASE, true>(a, s);
+    default: return launch_psi_t<256, false, PSI_DENSITY, true>(a, s);
+  }
+}
+
+cudaError_t rho_dispatch_tc(bool strided, int op, const RhoPassArgs& a, cudaStream_t s) {
+  if (strided) {
+    switch (op) {
+      case RHO_FWD: return launch_rho_t<256, true, RHO_FWD, true>(a, s);
+      case RHO_GREEN: return launch_rho_t<256, true, RHO_GREEN, true>(a, s);
+      default: return launch_rho_t<256, true, RHO_INV, true>(a, s);
+    }
+  }
+  switch (op) {
+    case RHO_FWD: return launch_rho_t<256, false, RHO_FWD, true>(a, s);
+    case RHO_GREEN: return launch_rho_t<256, false, RHO_GREEN, true>(a, s);
+    default: return launch_rho_t<256, false, RHO_INV, true>(a, s);
+  }
 }
 
 template <int N>
@@ -356,6 +435,7 @@ cudaError_t rho_dispatch(bool strided, int op, const RhoPassArgs& a, cudaStream_
 
 cudaError_t launch_psi_pass_f32(int N, bool strided, int variant, const PsiPassArgs& a,
                                 cudaStream_t s) {
+  if (a.tc != nullptr && N == tc16::N) return psi_dispatch_tc(strided, variant, a, s);
   switch (N) {
     case 8: return psi_dispatch<8>(strided, variant, a, s);
     case 16: return psi_dispatch<16>(strided, variant, a, s);
@@ -371,6 +451,7 @@ cudaError_t launch_psi_pass_f32(int N, bool strided, int variant, const PsiPassA
 
 cudaError_t launch_rho_pass_f32(int N, bool strided, int op, const RhoPassArgs& a,
                                 cudaStream_t s) {
+  if (a.tc != nullptr && N == tc16::N) return rho_dispatch_tc(strided, op, a, s);
   switch (N) {
     case 8: return rho_dispatch<8>(strided, op, a, s);
     case 16: return rho_dispatch<16>(strided, op, a, s);
@@ -382,6 +463,61 @@ cudaError_t launch_rho_pass_f32(int N, bool strided, int op, const RhoPassArgs& 
     case 1024: return rho_dispatch<1024>(strided, op, a, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ---- tensor-core engine: fragment tables ------------------------------------
+// F[j][p] = exp(s 2 pi i j q / 16) with q = p (F-as-A stages) or q = pi(p)
+// (data-as-A stages), expanded to the real 32 x 32 block of a complex product
+// with (re, im) interleaved along K, split into FP16 hi = fp16(F) and
+// lo = fp16(F - hi), and laid out per lane in the m16n8k16 fragment order.
+namespace {
+int tc_perm(int p) { return 8 * (p >> 3) + 2 * (p & 3) + ((p >> 2) & 1); }
+void tc_f(int dir, int j, int q, double& re, double& im) {
+  const double a = (dir == 0 ? -2.0 : 2.0) * 3.14159265358979323846 * (double)((j * q) % 16) / 16.0;
+  re = std::cos(a);
+  im = std::sin(a);
+}
+unsigned short tc_half(double v, int term) {
+  const __half h = __float2half_rn((float)v);
+  if (term == 0) return __half_as_ushort(h);
+  return __half_as_ushort(__float2half_rn((float)(v - (double)__half2float(h))));
+}
+unsigned tc_pack(double lo_k, double hi_k, int term) {
+  return (unsigned)tc_half(lo_k, term) | ((unsigned)tc_half(hi_k, term) << 16);
+}
+}  // namespace
+
+void tc16_fragment_table(std::vector<unsigned>& w) {
+  w.assign(tc16::FRAG_WORDS, 0u);
+  unsigned* fa = w.data();                        // [dir][term][q = mt*2+ks][lane][4]
+  unsigned* fb = w.data() + tc16::FRAG_WORDS / 2; // [dir][term][nt][lane][4]
+  for (int dir = 0; dir < 2; ++dir)
+    for (int term = 0; term < 2; ++term)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int gid = lane >> 2, tig = lane & 3;
+        for (int mt = 0; mt < 2; ++mt)
+          for (int ks = 0; ks < 2; ++ks) {
+            unsigned* o = fa + ((((dir * 2 + term) * 4 + mt * 2 + ks) * 32 + lane) * 4);
+            for (int reg = 0; reg < 4; ++reg) {
+              const int j = gid + 8 * (reg & 1);
+              const int p = 8 * ks + tig + 4 * (reg >> 1);
+              double fr, fi;
+              tc_f(dir, j, p, fr, fi);
+              o[reg] = mt == 0 ? tc_pack(fr, -fi, term) : tc_pack(fi, fr, term);
+            }
+          }
+        for (int nt = 0; nt < 4; ++nt) {
+          unsigned* o = fb + ((((dir * 2 + term) * 4 + nt) * 32 + lane) * 4);
+          const int col = 8 * nt + gid, j = col >> 1, part = col & 1;
+          for (int ks = 0; ks < 2; ++ks)
+            for (int e = 0; e < 2; ++e) {
+              const int p = 8 * ks + tig + 4 * e;
+              double fr, fi;
+              tc_f(dir, j, tc_perm(p), fr, fi);
+              o[2 * ks + e] = part == 0 ? tc_pack(fr, -fi, term) : tc_pack(fi, fr, term);
+            }
+        }
+      }
 }
 
 }  // namespace sn

@@ -132,6 +132,11 @@ struct sn_grid_s {
   double* vext64 = nullptr;
   bool has_vext = false;
 
+  // line-transform engine: SN_ENGINE_FP32, or SN_ENGINE_TC16 (tensor cores on
+  // 256-point axes; tc_frag holds its FP16 fragment tables)
+  int engine = SN_ENGINE_FP32;
+  uint4* tc_frag = nullptr;
+
   // profiling
   bool profiling = false;
   std::vector<Launch> prof;
@@ -274,6 +279,7 @@ sn_status psi_pass(sn_grid g, int a, int variant, int full, double dt) {
   pa.h = (float)dt;
   pa.gh = (float)(g->kp.g_local * dt);
   pa.rh_out = g->rhohat;
+  pa.tc = g->engine == SN_ENGINE_TC16 ? g->tc_frag : nullptr;
   const double P = g->n[a] / 2 + 1, lines = (double)g->cells / g->n[a];
   double bytes = 16.0 * g->cells;
   int kind = K_PSI;
@@ -308,6 +314,7 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
   ra.cN = (float)cN;
   ra.cY = (float)cY;
   ra.mu2 = (float)mu2;
+  ra.tc = g->engine == SN_ENGINE_TC16 ? g->tc_frag : nullptr;
   if (d == 2) {
     const int c = rest[0];
     ra.outer = P;
@@ -705,6 +712,63 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
 }
 
 long long sn_launch_count(sn_grid g) { return g ? g->launches : 0; }
+
+sn_status sn_set_engine(sn_grid g, int engine) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_set_engine: grid is NULL");
+  if (engine != SN_ENGINE_FP32 && engine != SN_ENGINE_TC16)
+    return fail(g, SN_EINVAL, "sn_set_engine: unknown engine");
+  if (engine == SN_ENGINE_TC16 && g->dtype != SN_C64)
+    return fail(g, SN_ENOTSUP, "sn_set_engine: the tensor-core engine needs a complex64 grid");
+  if (engine == SN_ENGINE_TC16 && !g->tc_frag) {
+    std::vector<unsigned> w;
+    tc16_fragment_table(w);
+    std::vector<uint4> w4(w.size() / 4);
+    memcpy(w4.data(), w.data(), w.size() * sizeof(unsigned));
+    cudaError_t e = upload(g, &g->tc_frag, w4);
+    if (e != cudaSuccess) return cuda_fail(g, e, "sn_set_engine: upload");
+  }
+  g->engine = engine;
+  return SN_OK;
+}
+
+sn_status sn_test_line_fft_f32(void* data, long long nlines, int n, int sign, int engine,
+                               void* cuda_stream) {
+  if (!data || nlines < 0 || !is_pow2_in_range(n) || (sign != 1 && sign != -1) ||
+      (engine != SN_ENGINE_FP32 && engine != SN_ENGINE_TC16))
+    return fail(nullptr, SN_EINVAL, "sn_test_line_fft_f32: bad argument");
+  if (nlines == 0) return SN_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<float2> tw;
+  std::vector<double2> t64 = twiddles_f64(n);
+  if (t64.empty()) t64.push_back(make_double2(1.0, 0.0));
+  split_hilo(t64, tw);
+  std::vector<unsigned> frag;
+  tc16_fragment_table(frag);
+  void *dtw = nullptr, *dfrag = nullptr;
+  cudaError_t e = cudaMalloc(&dtw, tw.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&dfrag, frag.size() * sizeof(unsigned));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(dtw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(dfrag, frag.data(), frag.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    RhoPassArgs ra{};
+    ra.data = static_cast<float2*>(data);
+    ra.outer = nlines;
+    ra.inner = 1;
+    ra.tw = static_cast<const float2*>(dtw);
+    ra.tc = engine == SN_ENGINE_TC16 ? static_cast<const uint4*>(dfrag) : nullptr;
+    e = launch_rho_pass_f32(n, false, sign < 0 ? RHO_FWD : RHO_INV, ra, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dtw);
+  cudaFree(dfrag);
+  if (e != cudaSuccess) {
+    set_thread_error((std::string("sn_test_line_fft_f32: ") + cudaGetErrorString(e)).c_str());
+    return SN_ECUDA;
+  }
+  return SN_OK;
+}
 
 sn_status sn_profile_step(sn_grid g, double dt, int nsteps, double* ms, long long* launches,
                           double* bytes, int nkinds) {

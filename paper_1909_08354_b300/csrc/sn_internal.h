@@ -37,6 +37,7 @@ struct PsiPassArgs {
   float h;                 // NPHASE: step h (multiplies V_ext)
   float gh;                // NPHASE: g * h
   float2* rh_out;          // DENSITY: half spectrum [N/2+1][lines]
+  const uint4* tc;         // tensor-core fragment table (256-point lines), or NULL
 };
 
 struct RhoPassArgs {
@@ -48,6 +49,7 @@ struct RhoPassArgs {
   const float* k2l;  // GREEN: k^2 of the line axis
   long long mid_n;   // GREEN, contiguous lines: outer = plane * mid_n + mid
   float cN, cY, mu2; // GREEN: K = cN/k2 + cY/(k2 + mu2), zero at k2 = 0
+  const uint4* tc;   // tensor-core fragment table (256-point lines), or NULL
 };
 
 // Message returned by sn_last_error(NULL) on this thread.
@@ -60,6 +62,8 @@ cudaError_t launch_psi_pass_f32(int N, bool strided, int variant, const PsiPassA
                                 cudaStream_t s);
 cudaError_t launch_rho_pass_f32(int N, bool strided, int op, const RhoPassArgs& a,
                                 cudaStream_t s);
+// FP16 fragment tables of the tensor-core engine (tc16.cuh), tc16::FRAG_WORDS words
+void tc16_fragment_table(std::vector<unsigned>& words);
 
 // ---- plain FP64 path -------------------------------------------------------
 cudaError_t launch_fft_f64(int N, bool strided, int sign, double2* data, long long outer,

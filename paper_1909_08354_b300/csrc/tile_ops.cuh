@@ -8,6 +8,7 @@
 #pragma once
 
 #include "sn_fft.cuh"
+#include "tc16.cuh"
 
 namespace sn {
 namespace tile {
@@ -20,6 +21,20 @@ using snfft::cx;
 using snfft::line_transform;
 using snfft::pidx;
 using snfft::Plan;
+
+// One DFT of the lines l < nact of the tile (pattern P in and out): the
+// FP32 Stockham engine, or the tensor-core engine for 256-point lines (TC).
+template <int N, int SIGN, bool WL, bool TC>
+__device__ __forceinline__ void xform(cx<float> (&v)[Plan<N>::E], cx<float>* lines,
+                                      const cx<float>* tw, const tc16::Tabs* tb, int l, int t,
+                                      int nact) {
+  if constexpr (TC) {
+    static_assert(N == tc16::N, "the tensor-core engine handles 256-point lines");
+    tc16::transform<SIGN < 0 ? 0 : 1>(v, lines, *tb, l, t, nact);
+  } else {
+    line_transform<float, N, SIGN, WL>(v, lines + l * Plan<N>::LS, tw, t, l < nact);
+  }
+}
 
 template <int N, int LPB>
 struct Cfg {
@@ -94,10 +109,11 @@ __device__ __forceinline__ void store_line(const cx<float> (&v)[E], float2* p, u
 // V h on my line's elements (pattern P) from a staged [k][line] half-spectrum
 // tile: C2R inverse FFT of lines (l, l + LPB/2) packed as A + iB.  On entry the
 // tile is visible to all threads and the line buffers are free.
-template <int N, int LPB, bool WL>
+template <int N, int LPB, bool WL, bool TC = false>
 __device__ __forceinline__ void potential_c2r(const cx<float>* rtile, cx<float>* lines,
                                               const cx<float>* tw, int l, int t,
-                                              float (&vph)[Plan<N>::E]) {
+                                              float (&vph)[Plan<N>::E],
+                                              const tc16::Tabs* tb = nullptr) {
   using C = Cfg<N, LPB>;
   constexpr int E = C::E, T = C::T, LS = C::LS, TSTR = C::TSTR, HALF = LPB / 2;
   cx<float> v[E];
@@ -118,7 +134,7 @@ __device__ __forceinline__ void potential_c2r(const cx<float>* rtile, cx<float>*
       v[m] = {A.re - B.im, A.im + B.re};  // A + i B
     }
   }
-  line_transform<float, N, +1, WL>(v, lines + l * LS, tw, t, pa);
+  xform<N, +1, WL, TC>(v, lines, tw, tb, l, t, HALF);
   __syncthreads();
   if (pa) {
     float* up = reinterpret_cast<float*>(lines + (l + HALF) * LS);
@@ -173,10 +189,11 @@ __device__ __forceinline__ void kinetic(cx<float> (&v)[Plan<N>::E], cx<float>* l
 // rho = |psi|^2 of the tile and its R2C FFT along the line (two real lines per
 // complex FFT).  put(k, ll, value) receives half-spectrum entry k of line ll
 // for the valid lines; the calls are spread over all threads with ll fastest.
-template <int N, int LPB, bool WL, class Put>
+template <int N, int LPB, bool WL, class Put, bool TC = false>
 __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], bool valid,
                                             cx<float>* lines, const cx<float>* tw, int l, int t,
-                                            int tid, int nvalid, Put put) {
+                                            int tid, int nvalid, Put put,
+                                            const tc16::Tabs* tb = nullptr) {
   using C = Cfg<N, LPB>;
   constexpr int E = C::E, T = C::T, NT = C::NT, LS = C::LS, H = C::H, TSTR = C::TSTR;
   constexpr int HALF = LPB / 2;
@@ -197,7 +214,7 @@ __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], 
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = {rho[m], b[t + T * m]};
   }
-  line_transform<float, N, -1, WL>(v, lines + l * LS, tw, t, pa);
+  xform<N, -1, WL, TC>(v, lines, tw, tb, l, t, HALF);
   __syncthreads();
   if (pa) {
 #pragma unroll

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("SN_LIB_PATH") or os.path.join(_HERE, "libsn.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+SN_ENGINE_FP32, SN_ENGINE_TC16 = 0, 1
 SN_C64, SN_C128 = 0, 1
 _STATUS = {0: "SN_OK", -1: "SN_EINVAL", -2: "SN_ENOMEM", -3: "SN_ECUDA", -4: "SN_ETIMEOUT",
            -5: "SN_ENONFINITE", -6: "SN_ENOTSUP"}
@@ -61,6 +62,9 @@ _SIGNATURES = [
                                        ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     ("sn_kind_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("sn_set_engine", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_test_line_fft_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("sn_step_2d_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double,
                                           ctypes.POINTER(SnKernel), ctypes.c_double, ctypes.c_int,
@@ -94,6 +98,12 @@ _SIGNATURES = [
                                    ctypes.c_double, ctypes.c_double, ctypes.c_int]),
     ("sn_fno_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_fno_destroy", None, [ctypes.c_void_p]),
+    ("sn_fno_pack", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                   ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p]),
+    ("sn_fno_unpack", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_longlong, ctypes.c_void_p]),
+    ("sn_mass_c64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
     ("sn_test_gemm_bf16", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_longlong] * 3
                                         + [ctypes.c_void_p] + [ctypes.c_longlong] * 3
                                         + [ctypes.c_void_p] + [ctypes.c_longlong] * 3
@@ -386,6 +396,36 @@ class Fno:
             pass
 
 
+def sn_fno_pack(psi, feats, X, stream=None):
+    """psi: (B, s, s) complex64 CUDA; feats: (B, nfeat) float32 CUDA; X: (B, 2+nfeat, s, s)."""
+    B = psi.shape[0]
+    _check(None, lib().sn_fno_pack(psi.data_ptr(), feats.data_ptr() if feats is not None else None,
+                                   feats.shape[1] if feats is not None else 0, X.data_ptr(), B,
+                                   psi[0].numel(), ctypes.c_void_p(stream) if stream else None))
+
+
+def sn_fno_unpack(Y, psi, stream=None):
+    _check(None, lib().sn_fno_unpack(Y.data_ptr(), psi.data_ptr(), psi.shape[0], psi[0].numel(),
+                                     ctypes.c_void_p(stream) if stream else None))
+
+
+def sn_mass_c64(psi, out, stream=None):
+    """out: (B,) float64 CUDA tensor receiving sum |psi_b|^2."""
+    _check(None, lib().sn_mass_c64(psi.data_ptr(), psi.shape[0], psi[0].numel(), out.data_ptr(),
+                                   ctypes.c_void_p(stream) if stream else None))
+
+
+def sn_test_line_fft_f32(data, n: int, sign: int, engine: int = SN_ENGINE_FP32, stream=None):
+    """Test hook: in-place unnormalised DFTs of the contiguous complex64 lines of
+    length n in a CUDA tensor (see sn_test_line_fft_f32 in include/sn.h)."""
+    import torch
+    if not (_is_torch(data) and data.is_cuda and data.dtype == torch.complex64
+            and data.is_contiguous() and data.numel() % n == 0):
+        raise ValueError("data must be a contiguous complex64 CUDA tensor of whole lines")
+    _check(None, lib().sn_test_line_fft_f32(data.data_ptr(), data.numel() // n, n, sign, engine,
+                                            ctypes.c_void_p(stream) if stream else None))
+
+
 def sn_test_gemm_bf16(A, sA, B, sB, C, sC, M, N, K, Z, alpha=1.0, beta=0.0):
     """Test hook: strided batched BF16 GEMM on CUDA float32 tensors; s* = (sz, s_row, s_col)."""
     _check(None, lib().sn_test_gemm_bf16(A.data_ptr(), *sA, B.data_ptr(), *sB, C.data_ptr(), *sC,
@@ -474,6 +514,10 @@ class Grid:
 
     def observables(self) -> dict:
         return sn_observables(self.h)
+
+    def set_engine(self, engine: int):
+        """SN_ENGINE_FP32 or SN_ENGINE_TC16 (tensor cores on 256-point axes)."""
+        _check(self.h, lib().sn_set_engine(self.h, int(engine)))
 
     def sync(self):
         sn_sync(self.h)

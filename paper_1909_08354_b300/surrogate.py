@@ -1,0 +1,289 @@
+"""FNO surrogate workflow on the library's kernels.
+
+* Training pairs: each seeded 2D instance (the scan-instance generator at one
+  grid size) is advanced by the batched split-step solver; (psi(t), kernel
+  parameters) -> psi(t + stride dt) pairs are cut every `stride` steps.
+* Training: contiguous minibatches of a pre-shuffled pair set through
+  sn_fno_forward / sn_fno_loss / sn_fno_backward / sn_fno_adam.
+* Rollout: psi is advanced `stride` steps per network call; a prediction
+  whose mass differs from its input's by more than `drift_tol` is replaced by
+  `stride` solver steps (the solver is the fallback and the judge).
+
+Device memory comes from torch tensors; every computation is a library call.
+Every call is queued on torch's current CUDA stream, which must be a
+non-default stream; create the network on that same stream, e.g.
+
+    stream = torch.cuda.Stream(); torch.cuda.set_stream(stream)
+    net = sn.Fno(..., stream=stream.cuda_stream)
+"""
+from __future__ import annotations
+
+import time
+from typing import Dict, List, Sequence
+
+import numpy as np
+
+import workloads as W
+
+from . import sn
+
+# network input channels: (re psi, im psi, alpha_Y, lambda_Y / 20, g / 0.05)
+FEATURE_SCALE = np.array([1.0, 1.0 / 20.0, 1.0 / 0.05])
+
+
+def instances(n: int, seed0: int, s: int = 256) -> List[W.Workload]:
+    return [W.scan_instance_2d(i, sizes=(s,), seed=seed0 + i) for i in range(n)]
+
+
+def kernel_kw(kp) -> Dict[str, float]:
+    return dict(coeff_lap=kp.coeff_lap, G=kp.G, alpha_Y=kp.alpha_Y, lambda_Y=kp.lambda_Y,
+                g_local=kp.g_local)
+
+
+def features(ws: Sequence[W.Workload]) -> np.ndarray:
+    f = np.array([[w.kernel.alpha_Y, w.kernel.lambda_Y, w.kernel.g_local] for w in ws])
+    return (f * FEATURE_SCALE).astype(np.float32)
+
+
+def _stream(torch):
+    h = torch.cuda.current_stream().cuda_stream
+    if not h:
+        raise RuntimeError("set a non-default current CUDA stream before the surrogate calls")
+    return h
+
+
+def _batch(torch, ws, stream):
+    b = sn.Batch([w.n[0] for w in ws], [w.L[0] for w in ws], stream=stream)
+    b.set_kernels([kernel_kw(w.kernel) for w in ws])
+    for i, w in enumerate(ws):
+        b.set_state(i, w.psi0(np.complex64))
+    return b
+
+
+def generate_pairs(torch, ws, stride=50, nsnap=10, chunk=512, seed=0):
+    """X (N, 5, s, s), Y (N, 2, s, s) float32 CUDA tensors, N = len(ws) * nsnap, in a
+    seeded random order so that contiguous slices are shuffled minibatches."""
+    stream = _stream(torch)
+    s = ws[0].n[0]
+    n = len(ws) * nsnap
+    perm = np.random.default_rng(seed).permutation(n)
+    X = torch.empty((n, 5, s, s), dtype=torch.float32, device="cuda")
+    Y = torch.empty((n, 2, s, s), dtype=torch.float32, device="cuda")
+    for c0 in range(0, len(ws), chunk):
+        part = ws[c0:c0 + chunk]
+        c = len(part)
+        feat = torch.from_numpy(features(part)).cuda()
+        b = _batch(torch, part, stream)
+        cur = torch.empty((c, s, s), dtype=torch.complex64, device="cuda")
+        nxt = torch.empty_like(cur)
+        xs = torch.empty((c, 5, s, s), dtype=torch.float32, device="cuda")
+        ys = torch.empty((c, 2, s, s), dtype=torch.float32, device="cuda")
+        for k in range(nsnap):
+            for i in range(c):
+                b.get_state(i, cur[i])
+            b.step(part[0].dt, stride)
+            for i in range(c):
+                b.get_state(i, nxt[i])
+            sn.sn_fno_pack(cur, feat, xs, stream)
+            sn.sn_fno_pack(nxt, None, ys, stream)
+            for i in range(c):
+                j = int(perm[(c0 + i) * nsnap + k])
+                X[j].copy_(xs[i])
+                Y[j].copy_(ys[i])
+        b.close()
+    torch.cuda.synchronize()
+    return X, Y
+
+
+def train(net, X, Y, iters: int, batch: int, lr: float = 1e-3, time_budget: float = None,
+          log=None):
+    """Adam on contiguous minibatches with a cosine-decayed rate; returns the losses."""
+    import math
+    import torch
+    n = X.shape[0]
+    out = torch.empty((batch, 2, X.shape[2], X.shape[3]), dtype=torch.float32, device="cuda")
+    losses, t0 = [], time.perf_counter()
+    nb = n // batch
+    for it in range(1, iters + 1):
+        k = (it - 1) % nb
+        xb, yb = X[k * batch:(k + 1) * batch], Y[k * batch:(k + 1) * batch]
+        net.forward(xb, out)
+        losses.append(net.loss(yb, batch))
+        net.backward()
+        net.adam(lr * 0.5 * (1.0 + math.cos(math.pi * (it - 1) / iters)), it)
+        if log and it % 100 == 0:
+            log(f"iter {it} loss {np.mean(losses[-100:]):.4f} ({time.perf_counter() - t0:.0f} s)")
+        if time_budget is not None and time.perf_counter() - t0 > time_budget:
+            break
+    net.sync()
+    return losses
+
+
+def _masses(torch, psi, stream=None):
+    out = torch.empty(psi.shape[0], dtype=torch.float64, device="cuda")
+    sn.sn_mass_c64(psi, out, stream)
+    return out
+
+
+def rollout(torch, net, ws, rounds=20, stride=50, drift_tol=1e-3, perturb=None):
+    """Advance every instance `rounds` x `stride` steps by the surrogate with
+    fallback, and by the solver alone; compare.  `perturb(r, psi)` may alter
+    the predictions (used to exercise the fallback)."""
+    stream = _stream(torch)
+    s = ws[0].n[0]
+    n = len(ws)
+    dt = ws[0].dt
+    feat = torch.from_numpy(features(ws)).cuda()
+    psi0 = torch.stack([torch.from_numpy(w.psi0(np.complex64)) for w in ws]).cuda()
+    # solver reference trajectory (one batch, snapshots every `stride` steps)
+    b = _batch(torch, ws, stream)
+    ref = torch.empty((rounds, n, s, s), dtype=torch.complex64, device="cuda")
+    for r in range(rounds):
+        b.step(dt, stride)
+        for i in range(n):
+            b.get_state(i, ref[r, i])
+    # solver alone, timed: all rounds in one call
+    for i in range(n):
+        b.set_state(i, psi0[i])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(dt, rounds * stride)
+    b.sync()
+    t_solver = time.perf_counter() - t0
+    # surrogate with fallback
+    B = net.batch_max
+    X = torch.empty((B, 5, s, s), dtype=torch.float32, device="cuda")
+    Yb = torch.empty((B, 2, s, s), dtype=torch.float32, device="cuda")
+    psi = psi0.clone()
+    nxt = torch.empty_like(psi)
+    errors, fallbacks = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in range(rounds):
+        for c0 in range(0, n, B):
+            c = min(B, n - c0)
+            sn.sn_fno_pack(psi[c0:c0 + c], feat[c0:c0 + c], X, stream)
+            net.forward(X[:c], Yb[:c])
+            sn.sn_fno_unpack(Yb[:c], nxt[c0:c0 + c], stream)
+        if perturb is not None:
+            perturb(r, nxt)
+        m_old = _masses(torch, psi, stream).cpu().numpy()
+        m_new = _masses(torch, nxt, stream).cpu().numpy()
+        bad = np.nonzero(np.abs(m_new / m_old - 1.0) > drift_tol)[0]
+        if len(bad):
+            fb = sn.Batch([s] * len(bad), [ws[i].L[0] for i in bad], stream=stream)
+            fb.set_kernels([kernel_kw(ws[i].kernel) for i in bad])
+            for j, i in enumerate(bad):
+                fb.set_state(j, psi[int(i)])
+            fb.step(dt, stride)
+            for j, i in enumerate(bad):
+                fb.get_state(j, nxt[int(i)])
+            fb.sync()
+            fb.close()
+        psi, nxt = nxt, psi
+        fallbacks.append(len(bad))
+    torch.cuda.synchronize()
+    t_sur = time.perf_counter() - t0
+    # relative L2 error of the final surrogate state against the solver's (host, FP64)
+    fin = psi.cpu().numpy().astype(np.complex128)
+    want = ref[rounds - 1].cpu().numpy().astype(np.complex128)
+    errs = [float(np.linalg.norm(fin[i] - want[i]) / np.linalg.norm(want[i])) for i in range(n)]
+    b.close()
+    return {"instances": n, "rounds": rounds, "stride": stride, "t_surrogate_s": t_sur,
+            "t_solver_s": t_solver, "fallbacks_per_round": fallbacks,
+            "fallback_fraction": float(sum(fallbacks)) / (rounds * n),
+            "final_rel_l2_mean": float(np.mean(errs)), "final_rel_l2_max": float(np.max(errs))}
+
+
+def one_step_errors(torch, net, X, Y, batch):
+    """Mean relative L2 error of single predictions and of the persistence guess
+    psi(t + stride dt) ~ psi(t) over the pairs (X, Y) (host FP64 for the latter)."""
+    out = torch.empty((batch, 2, X.shape[2], X.shape[3]), dtype=torch.float32, device="cuda")
+    e_net, e_id = [], []
+    for k in range(X.shape[0] // batch):
+        xb, yb = X[k * batch:(k + 1) * batch], Y[k * batch:(k + 1) * batch]
+        net.forward(xb, out)
+        e_net.append(net.loss(yb, batch))
+        x = xb[:, :2].cpu().numpy().astype(np.float64).reshape(batch, -1)
+        y = yb.cpu().numpy().astype(np.float64).reshape(batch, -1)
+        e_id.append(float(np.mean(np.linalg.norm(x - y, axis=1) / np.linalg.norm(y, axis=1))))
+    return float(np.mean(e_net)), float(np.mean(e_id))
+
+
+def main(argv=None):
+    """Config-scale run: train on solver pairs, then roll out held-out instances.
+
+    Prints one JSON line with the training loss, the held-out single-prediction
+    error against the persistence guess and the zero guess (whose relative error
+    is 1 by definition), and the rollout's fallback fraction, final error and
+    wall times against the batched solver alone."""
+    import argparse
+    import json
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--s", type=int, default=256)
+    ap.add_argument("--train", type=int, default=4096, help="training trajectories")
+    ap.add_argument("--heldout", type=int, default=512)
+    ap.add_argument("--nsnap", type=int, default=10)
+    ap.add_argument("--stride", type=int, default=50)
+    ap.add_argument("--rounds", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--iters", type=int, default=100000)
+    ap.add_argument("--budget", type=float, default=600.0, help="training seconds")
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--width", type=int, default=64)
+    ap.add_argument("--modes", type=int, default=24)
+    ap.add_argument("--layers", type=int, default=4)
+    ap.add_argument("--proj", type=int, default=128)
+    ap.add_argument("--drift-tol", type=float, default=1e-3)
+    ap.add_argument("--init-seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    log = lambda m: print(m, flush=True)  # noqa: E731
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    X, Y = generate_pairs(torch, instances(a.train, 5000, a.s), a.stride, a.nsnap, seed=1)
+    test_ws = instances(a.heldout, 9000, a.s)
+    Xt, Yt = generate_pairs(torch, test_ws, a.stride, 2, seed=2)
+    t_gen = time.perf_counter() - t0
+    log(f"pairs: {X.shape[0]} train, {Xt.shape[0]} held out ({t_gen:.0f} s)")
+    net = sn.Fno(s=a.s, c_in=5, width=a.width, modes=a.modes, layers=a.layers, proj=a.proj,
+                 batch_max=a.batch, stream=stream.cuda_stream)
+    p0 = _init_params(a)
+    if p0.size != net.nparams:
+        raise RuntimeError("parameter layout mismatch")
+    net.set_params(p0)
+    t0 = time.perf_counter()
+    losses = train(net, X, Y, a.iters, a.batch, a.lr, a.budget, log)
+    t_train = time.perf_counter() - t0
+    del X, Y
+    e_net, e_id = one_step_errors(torch, net, Xt, Yt, a.batch)
+    res = rollout(torch, net, test_ws, a.rounds, a.stride, a.drift_tol)
+    res.update({"grid": a.s, "train_pairs": a.train * a.nsnap, "train_iters": len(losses),
+                "train_samples_per_s": len(losses) * a.batch / t_train, "train_s": t_train,
+                "loss_first100": float(np.mean(losses[:100])),
+                "loss_last100": float(np.mean(losses[-100:])),
+                "heldout_rel_l2_net": e_net, "heldout_rel_l2_persistence": e_id,
+                "heldout_rel_l2_zero": 1.0, "params": net.nparams})
+    res.pop("fallbacks_per_round", None)
+    print(json.dumps(res), flush=True)
+    net.close()
+
+
+def _init_params(a):
+    """Seeded initial weights in the library's flat layout (same scheme as the
+    FP64 network's initialiser: uniform +-1/sqrt(fan-in), spectral weights scaled
+    by 1/(width^2))."""
+    rng = np.random.default_rng(a.init_seed)
+    w, m2, m, P = a.width, 2 * a.modes, a.modes, a.proj
+    parts = [rng.uniform(-1, 1, (w, 5)) / np.sqrt(5), np.zeros(w)]
+    for _ in range(a.layers):
+        parts += [rng.uniform(0, 1, (m2, m, w, w, 2)) / (w * w),
+                  rng.uniform(-1, 1, (w, w)) / np.sqrt(w), np.zeros(w)]
+    parts += [rng.uniform(-1, 1, (P, w)) / np.sqrt(w), np.zeros(P),
+              rng.uniform(-1, 1, (3, P)) / np.sqrt(P), np.zeros(3)]
+    return np.concatenate([q.ravel() for q in parts]).astype(np.float32)
+
+
+if __name__ == "__main__":
+    main()

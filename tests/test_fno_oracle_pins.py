@@ -76,11 +76,22 @@ def test_zero_spectral_weights_reduce_to_pointwise_network():
         z = np.einsum("oi,biyx->boyx", p[f"W{l}"], v) + p[f"b{l}"][None, :, None, None]
         v = F._gelu(z) if l < TINY.layers - 1 else z
     h = F._gelu(np.einsum("jo,boyx->bjyx", p["Q1"], v) + p["q1b"][None, :, None, None])
-    ref = a[:, :2] + np.einsum("kj,bjyx->bkyx", p["Q2"], h) + p["q2b"][None, :, None, None]
-    assert np.allclose(out, ref, atol=1e-13)
+    y = np.einsum("kj,bjyx->bkyx", p["Q2"], h) + p["q2b"][None, :, None, None]
+    psi = (a[:, 0] + 1j * a[:, 1]) * np.exp(-1j * y[:, 0]) + y[:, 1] + 1j * y[:, 2]
+    assert np.allclose(out, np.stack([psi.real, psi.imag], axis=1), atol=1e-13)
+
+
+def test_head_turns_the_state_by_the_predicted_phase():
+    rng = np.random.default_rng(4)
+    a = rng.standard_normal((1, 5, 4, 4))
+    y = np.zeros((1, 3, 4, 4))
+    y[:, 0] = 0.7
+    out = F.head(a, y)
+    psi = (a[:, 0] + 1j * a[:, 1]) * np.exp(-0.7j)
+    assert np.allclose(out[:, 0], psi.real) and np.allclose(out[:, 1], psi.imag)
 
 
 def test_parameter_count_of_the_surrogate():
     sh = F.FnoShape()   # 256^2, width 64, 24 modes, 4 layers, projection 128
     assert F.n_params(sh) == (64 * 5 + 64) + 4 * (48 * 24 * 64 * 64 * 2 + 64 * 64 + 64) \
-        + (128 * 64 + 128) + (2 * 128 + 2)
+        + (128 * 64 + 128) + (3 * 128 + 3)

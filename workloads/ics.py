@@ -138,9 +138,10 @@ SCAN_SIZES = (128, 256, 512, 1024)
 
 
 def scan_instance_2d(i: int, sizes: Sequence[int] = SCAN_SIZES, L: float = 40.0,
-                     dt: float = 1e-2, nsteps: int = 500) -> Workload:
-    """Instance i of the batched parameter scan (seed 4000 + i)."""
-    r = SplitMix64(4000 + i)
+                     dt: float = 1e-2, nsteps: int = 500, seed: int | None = None) -> Workload:
+    """Instance i of the batched parameter scan (seed 4000 + i unless given)."""
+    seed = 4000 + i if seed is None else seed
+    r = SplitMix64(seed)
     n = int(sizes[min(int(r.uniform() * len(sizes)), len(sizes) - 1)])
     nl = r.randint(2, 8)
     lumps = []
@@ -153,7 +154,7 @@ def scan_instance_2d(i: int, sizes: Sequence[int] = SCAN_SIZES, L: float = 40.0,
     k = KernelParams(G=1.0, alpha_Y=r.uniform(0.0, 1.0), lambda_Y=r.uniform(1.0, 20.0),
                      g_local=r.uniform(0.0, 0.05))
     return Workload(f"scan2d_{i}_{n}", (n, n), (L, L), lumps, k, dt, nsteps,
-                    meta={"seed": 4000 + i, "index": i})
+                    meta={"seed": seed, "index": i})
 
 
 def random_small(n: Sequence[int], seed: int, L: float | Sequence[float] = 10.0,
