@@ -15,6 +15,19 @@
 // no value overflows FP16 and small values stay clear of its subnormals; the
 // scale is exact and is removed at the end.
 //
+// The tensor cores' FP32 accumulation truncates, which shrinks every stage's
+// result by a few 1e-8 on average, and F_hi + F_lo is unitary only to ~2e-8;
+// both would drain the mass of psi step after step.  Each 256-point transform
+// and every 16-point stage are unitary up to a known factor (Parseval), so the
+// shrink is measured per line (squared norms summed in FP32 on the scaled
+// values) and taken back where it can be: a factor 1 + c with c below an ulp
+// does nothing to a value already rounded to FP32, so it is folded into the lo
+// part of the next FP16 split, lo = fp16(fma(y, c, y - hi)).  Stage A's
+// measured shrink is taken back at stage B's input together with the same
+// amount predicted for stage B; the forward transform's measured remainder is
+// taken back at the inverse transform's input.  What is left is a random
+// per-line factor of order 1e-7 instead of a bias.
+//
 // Two operand roles are used.  "F-as-A": the DFT matrix is the A operand and
 // the data the B operand (columns along N); "data-as-A": the data is the A
 // operand (columns along M) and the transposed DFT matrix the B operand.  With
@@ -79,6 +92,16 @@ __device__ __forceinline__ void split(float re, float im, unsigned& hi, unsigned
   lo = h2u(__floats2half2_rn(re - hf.x, im - hf.y));
 }
 
+// the same split of x (1 + c) for a small c: the correction goes into the lo
+// part before any rounding of x (1 + c) itself, so it survives even when it
+// is far below an ulp of x
+__device__ __forceinline__ void split_c(float re, float im, float c, unsigned& hi, unsigned& lo) {
+  const __half2 h = __floats2half2_rn(re, im);
+  const float2 hf = __half22float2(h);
+  hi = h2u(h);
+  lo = h2u(__floats2half2_rn(fmaf(re, c, re - hf.x), fmaf(im, c, im - hf.y)));
+}
+
 // power-of-two scale s with (largest component) * s < 2^14, and 1 / s, from
 // the bit pattern of the warp's largest |component|
 __device__ __forceinline__ void line_scale(float mx, float& s, float& inv) {
@@ -86,6 +109,41 @@ __device__ __forceinline__ void line_scale(float mx, float& s, float& inv) {
   e = e < 14u ? 14u : (e > 254u ? 254u : e);
   s = __uint_as_float((267u - e) << 23);
   inv = __uint_as_float((e - 13u) << 23);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// eps = sqrt(target / got) - 1 of two squared norms, formed without the
+// cancellation of 1 + eps, so that fma(y, eps, y) applies it exactly before
+// the single rounding of the result (a factor 1 + eps with |eps| below an ulp
+// would round back to 1 and leave the value unchanged)
+__device__ __forceinline__ float parseval_eps(float target, float got) {
+  if (!(got > 0.f)) return 0.f;
+  return __fdiv_rn(target - got, got + __fsqrt_rn(target * got));
+}
+
+// squared norm of F-as-A accumulators (all lanes: the warp total)
+__device__ __forceinline__ float norm_fa(const float (&acc)[2][2][4]) {
+  float n = 0.f;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) n = fmaf(acc[mt][nt][r], acc[mt][nt][r], n);
+  return warp_sum(n);
+}
+__device__ __forceinline__ float norm_da(const float (&acc)[4][4]) {
+  float n = 0.f;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) n = fmaf(acc[nt][r], acc[nt][r], n);
+  return warp_sum(n);
 }
 
 __device__ __forceinline__ float amax(float m, cx<float> z) {
@@ -105,6 +163,8 @@ __device__ __forceinline__ void stage_fa(const uint4 (*fh)[32], const uint4 (*fl
     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.f;
+  // the small hi x lo terms first, then the two hi x hi blocks: only those two
+  // additions to a full-size accumulator are truncated at FP32 precision
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
@@ -114,8 +174,13 @@ __device__ __forceinline__ void stage_fa(const uint4 (*fh)[32], const uint4 (*fl
       for (int nt = 0; nt < 2; ++nt) {
         mma(acc[mt][nt], al, bh[nt][ks][0], bh[nt][ks][1]);
         mma(acc[mt][nt], ah, bl[nt][ks][0], bl[nt][ks][1]);
-        mma(acc[mt][nt], ah, bh[nt][ks][0], bh[nt][ks][1]);
       }
+    }
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const uint4 ah = fh[mt * 2 + ks][lane];
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) mma(acc[mt][nt], ah, bh[nt][ks][0], bh[nt][ks][1]);
     }
   }
 }
@@ -132,19 +197,20 @@ __device__ __forceinline__ void stage_da(const uint4* fh, const uint4* fl, const
     const uint4 bh = fh[nt * 32 + lane], bl = fl[nt * 32 + lane];
     mma(acc[nt], al[0], bh.x, bh.y);
     mma(acc[nt], ah[0], bl.x, bl.y);
-    mma(acc[nt], ah[0], bh.x, bh.y);
     mma(acc[nt], al[1], bh.z, bh.w);
     mma(acc[nt], ah[1], bl.z, bl.w);
+    mma(acc[nt], ah[0], bh.x, bh.y);
     mma(acc[nt], ah[1], bh.z, bh.w);
   }
 }
 
-// twiddle the F-as-A accumulators and repack them as data-as-A fragments.
+// twiddle the F-as-A accumulators and repack them as data-as-A fragments,
+// scaled by 1 + c.
 // Element (row gid + 8 (r >> 1), column 8 ks + 2 tig + (r & 1)) is multiplied
 // by tw[column * TWS + row] (the table is symmetric in its two indices).
 __device__ __forceinline__ void twiddle_pack(const float (&acc)[2][2][4], const float2* twh,
-                                             const float2* twl, uint4 (&ah)[2], uint4 (&al)[2],
-                                             int gid, int tig) {
+                                             const float2* twl, float c, uint4 (&ah)[2],
+                                             uint4 (&al)[2], int gid, int tig) {
 #pragma unroll
   for (int ks = 0; ks < 2; ++ks) {
     unsigned h[4], l[4];
@@ -155,7 +221,7 @@ __device__ __forceinline__ void twiddle_pack(const float (&acc)[2][2][4], const 
       const cx<float> y = cmul_hl({acc[0][ks][r], acc[1][ks][r]}, {wh.x, wh.y}, {wl.x, wl.y});
       // fragment register: r 0 -> a0, 2 -> a1, 1 -> a2, 3 -> a3
       const int q = (r >> 1) | ((r & 1) << 1);
-      split(y.re, y.im, h[q], l[q]);
+      split_c(y.re, y.im, c, h[q], l[q]);
     }
     ah[ks] = make_uint4(h[0], h[1], h[2], h[3]);
     al[ks] = make_uint4(l[0], l[1], l[2], l[3]);
@@ -180,21 +246,28 @@ __device__ __forceinline__ void line_fft(cx<float>* line, const Tabs& tb, int la
   float s, inv;
   line_scale(mx, s, inv);
   unsigned bh[2][2][2], bl[2][2][2];
+  float nin = 0.f;
 #pragma unroll
   for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-      for (int e = 0; e < 2; ++e)
-        split(x[nt][2 * ks + e].re * s, x[nt][2 * ks + e].im * s, bh[nt][ks][e], bl[nt][ks][e]);
+      for (int e = 0; e < 2; ++e) {
+        const float re = x[nt][2 * ks + e].re * s, im = x[nt][2 * ks + e].im * s;
+        nin = fmaf(re, re, fmaf(im, im, nin));
+        split(re, im, bh[nt][ks][e], bl[nt][ks][e]);
+      }
   float acc[2][2][4];
   stage_fa(tb.fa[DIR][0], tb.fa[DIR][1], bh, bl, acc, lane);
+  // stage A's shrink from Parseval (16 |x s|^2), taken back at stage B's
+  // input together with the same amount predicted for stage B
+  const float ea = parseval_eps(16.f * warp_sum(nin), norm_fa(acc));
   uint4 ah[2], al[2];
-  twiddle_pack(acc, tb.tw[DIR][0], tb.tw[DIR][1], ah, al, gid, tig);
+  twiddle_pack(acc, tb.tw[DIR][0], tb.tw[DIR][1], 2.f * ea, ah, al, gid, tig);
   float acc2[4][4];
   stage_da(tb.fb[DIR][0][0], tb.fb[DIR][1][0], ah, al, acc2, lane);
   __syncwarp();
-  const float o = 16.f * inv;  // undo the scale and the 1/16 folded into the twiddles
+  const float o = 16.f * inv;  // undo the scale and the 1/16 folded into the twiddles (exact)
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
@@ -230,7 +303,7 @@ __device__ __forceinline__ void line_fmi(cx<float>* line, const Tabs& tb, const 
                                          int lane) {
   const int gid = lane >> 2, tig = lane & 3;
   unsigned bh[2][2][2], bl[2][2][2];
-  float s1, inv1;
+  float s1, inv1, nin1 = 0.f;
   {
     cx<float> x[2][4];
     float mx = 0.f;
@@ -249,18 +322,25 @@ __device__ __forceinline__ void line_fmi(cx<float>* line, const Tabs& tb, const 
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-        for (int e = 0; e < 2; ++e)
-          split(x[nt][2 * ks + e].re * s1, x[nt][2 * ks + e].im * s1, bh[nt][ks][e],
-                bl[nt][ks][e]);
+        for (int e = 0; e < 2; ++e) {
+          const float re = x[nt][2 * ks + e].re * s1, im = x[nt][2 * ks + e].im * s1;
+          nin1 = fmaf(re, re, fmaf(im, im, nin1));
+          split(re, im, bh[nt][ks][e], bl[nt][ks][e]);
+        }
+    nin1 = warp_sum(nin1);
   }
   float acc[2][2][4];
   uint4 ah[2], al[2];
   float acc2[4][4];
   stage_fa(tb.fa[0][0], tb.fa[0][1], bh, bl, acc, lane);
-  twiddle_pack(acc, tb.tw[0][0], tb.tw[0][1], ah, al, gid, tig);
+  float ea = parseval_eps(16.f * nin1, norm_fa(acc));
+  twiddle_pack(acc, tb.tw[0][0], tb.tw[0][1], 2.f * ea, ah, al, gid, tig);
   stage_da(tb.fb[0][0][0], tb.fb[0][1][0], ah, al, acc2, lane);
+  // what is left of the forward transform's shrink (Parseval: |DFT(x s)/16|^2 =
+  // |x s|^2) is taken back at the inverse's input split
+  const float ez = parseval_eps(nin1, norm_da(acc2));
   // spectrum entry k1 + 16 k2 with k1 = gid + 8 h, k2 = 4 nt + tig
-  float s2, inv2;
+  float s2, inv2, nin2 = 0.f;
   {
     cx<float> z[4][2];
     float mx = 0.f;
@@ -278,14 +358,19 @@ __device__ __forceinline__ void line_fmi(cx<float>* line, const Tabs& tb, const 
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-        for (int e = 0; e < 2; ++e)
-          split(z[2 * ks + e][h].re * s2, z[2 * ks + e][h].im * s2, bh[h][ks][e], bl[h][ks][e]);
+        for (int e = 0; e < 2; ++e) {
+          const float re = z[2 * ks + e][h].re * s2, im = z[2 * ks + e][h].im * s2;
+          nin2 = fmaf(re, re, fmaf(im, im, nin2));
+          split_c(re, im, ez, bh[h][ks][e], bl[h][ks][e]);
+        }
+    nin2 = warp_sum(nin2) * (1.f + 2.f * ez);
   }
   stage_fa(tb.fa[1][0], tb.fa[1][1], bh, bl, acc, lane);
-  twiddle_pack(acc, tb.tw[1][0], tb.tw[1][1], ah, al, gid, tig);
+  ea = parseval_eps(16.f * nin2, norm_fa(acc));
+  twiddle_pack(acc, tb.tw[1][0], tb.tw[1][1], 2.f * ea, ah, al, gid, tig);
   stage_da(tb.fb[1][0][0], tb.fb[1][1][0], ah, al, acc2, lane);
   __syncwarp();
-  const float o = 256.f * inv1 * inv2;
+  const float o = 256.f * inv1 * inv2;  // exact power of two
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
