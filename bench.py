@@ -38,7 +38,7 @@ UNIT = "cell-steps/s"
 BYTES_PER_CELL_STEP = 80.0  # algorithmic HBM bytes of the fused 3D complex64 step
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch from the ncu capture
 # summarised in profiles/fused_step_nbody_256.md; set to None when the kernel changes
-NCU_TRAFFIC = {"psi_pass_nphase": 201.93e6 + 78.38e6}
+NCU_TRAFFIC = {"psi_pass_nphase": 201.92e6 + 79.63e6}
 
 
 def parse():
@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-scan", action="store_true")
+    p.add_argument("--no-tc", action="store_true")
+    p.add_argument("--engine", choices=["fp32", "tc16"], default="fp32",
+                   help="line engine of the timed grid (tc16: tensor cores on 256-point axes)")
+    p.add_argument("--no-fno", action="store_true")
     return p.parse_args()
 
 
@@ -202,6 +206,79 @@ def run_scan(sn, torch, stream, peak):
             "speedup_vs_plain_fp64": t64 / t_batch}
 
 
+def run_tc16(sn, torch, stream, w, kw, psi0, peak, ref1, steps=200):
+    """The same workload on the tensor-core line engine (split-FP16 radix-16 stages)."""
+    g = sn.Grid(w.n, w.L, "c64", stream=stream.cuda_stream)
+    g.set_engine(sn.SN_ENGINE_TC16)
+    g.set_kernel(**kw)
+    g.set_state(psi0)
+    rel = None
+    if ref1 is not None:
+        g.step(w.dt, 1)
+        out1 = g.get_state()
+        rel = float(np.linalg.norm((out1 - ref1).ravel()) / np.linalg.norm(ref1.ravel()))
+        g.set_state(psi0)
+    m0 = g.observables()["mass"]
+    g.step(w.dt, 5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(w.dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    drift = g.observables()["mass"] / m0 - 1.0
+    prof = g.profile_step(w.dt, 50)
+    kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    dk = kinds[dom]
+    achieved = dk["bytes"] / (dk["ms"] / 1e3) / 1e9
+    g.close()
+    return {"engine": "SN_ENGINE_TC16 (mma.sync m16n8k16, FP16 hi/lo split, FP32 accumulation)",
+            "value": w.cells * steps / t, "unit": UNIT, "ms_per_step": 1e3 * t / steps,
+            "steps": steps, "rel_l2_vs_fp64_one_step": rel,
+            "mass_drift_205_steps": drift,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak},
+            "passes": {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / v["launches"],
+                           "GBps": v["bytes"] / (v["ms"] / 1e3) / 1e9} for k, v in kinds.items()}}
+
+
+def run_fno(sn, torch, stream, iters=10):
+    """Training throughput of the FNO surrogate at its full size (256^2, width 64,
+    24x24 modes, 4 layers, projection 128, batch 16): forward + loss + backward + Adam."""
+    s, c_in, B = 256, 5, 16
+    net = sn.Fno(s=s, c_in=c_in, width=64, modes=24, layers=4, proj=128, batch_max=B,
+                 stream=stream.cuda_stream)
+    rng = np.random.default_rng(0)
+    net.set_params(rng.uniform(-0.02, 0.02, net.nparams).astype(np.float32))
+    x = torch.randn(B, c_in, s, s, device="cuda")
+    y = torch.empty(B, 2, s, s, device="cuda")
+    tgt = torch.randn(B, 2, s, s, device="cuda")
+    for it in range(1, 4):
+        net.forward(x, y); net.loss(tgt, B); net.backward(); net.adam(1e-4, it)
+    net.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(iters):
+        net.forward(x, y)
+    e1.record(stream)
+    net.sync()
+    t_fwd = e0.elapsed_time(e1) / 1e3 / iters
+    t0 = time.perf_counter()
+    for it in range(4, 4 + iters):
+        net.forward(x, y); net.loss(tgt, B); net.backward(); net.adam(1e-4, it)
+    net.sync()
+    t_train = (time.perf_counter() - t0) / iters
+    n = net.nparams
+    net.close()
+    return {"network": "FNO 256^2, width 64, 24x24 modes, 4 spectral layers, projection 128, "
+                       "phase head", "params": n, "batch": B,
+            "forward_samples_per_s": B / t_fwd, "train_samples_per_s": B / t_train,
+            "train_step_ms": 1e3 * t_train,
+            "gemm": "mma.sync m16n8k16 BF16, FP32 accumulation"}
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -270,6 +347,8 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     g = sn.Grid(w.n, w.L, "c64", stream=stream.cuda_stream)
+    if args.engine == "tc16":
+        g.set_engine(sn.SN_ENGINE_TC16)
     g.set_kernel(**kw)
     g.set_state(psi0)
     m0 = g.observables()["mass"]
@@ -318,6 +397,7 @@ def main():
 
     # ---- the plain FP64 GPU step (denominator of the metric) and accuracy gate
     fp64 = None
+    ref1 = None
     if not args.no_fp64:
         g64 = sn.Grid(w.n, w.L, "c128", stream=stream.cuda_stream)
         g64.set_kernel(**kw)
@@ -343,9 +423,17 @@ def main():
         g64.close()
     g.close()
 
+    tc = None
+    if not args.no_tc and args.n == 256 and args.engine == "fp32":
+        tc = run_tc16(sn, torch, stream, w, kw, psi0, peak, ref1)
+
     scan = None
     if not args.no_scan:
         scan = run_scan(sn, torch, stream, peak)
+
+    fno = None
+    if not args.no_fno:
+        fno = run_fno(sn, torch, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -363,9 +451,10 @@ def main():
                                    f"16 lumps seed 3000, alpha_Y={args.alpha}, lambda_Y=10, "
                                    f"dt=1e-2",
                        "parallelism": "replicas" if world > 1 else "single",
+                       "engine": args.engine,
                        "l2": "working set 202 MB > 126 MB L2; no flush"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom),
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom) if args.engine == "fp32" else None,
                          "peak_source": peak_src,
                          "step_achieved": step_gbs, "step_frac": step_gbs / peak,
                          "bytes_per_cell_step": BYTES_PER_CELL_STEP},
@@ -378,7 +467,9 @@ def main():
             "fp64_plain_gpu": fp64,
             "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu,
+            "tensor_core_engine": tc,
             "batched_scan": scan,
+            "fno_surrogate": fno,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
