@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-scan", action="store_true")
+    p.add_argument("--scan-count", type=int, default=96, help="instances of the batched scan")
+    p.add_argument("--scan-steps", type=int, default=500, help="steps of the batched scan")
     p.add_argument("--no-tc", action="store_true")
     p.add_argument("--engine", choices=["fp32", "tc16"], default="fp32",
                    help="line engine of the timed grid (tc16: tensor cores on 256-point axes)")
@@ -135,13 +137,12 @@ def cpu_baseline_step(n: int, alpha: float):
     return w.cells / (time.perf_counter() - t0), time.perf_counter() - t0
 
 
-def run_scan(sn, torch, stream, peak):
+def run_scan(sn, torch, stream, peak, count=96, steps=500):
     """The batched parameter scan: 96 2D instances (128^2..1024^2), 500 steps, one launch.
     With several ranks the instances are partitioned by cost (n^2 log n) and each
     rank advances its share in one launch; the time is the slowest rank's."""
     from paper_1909_08354_b300 import dist as D
-    all_ws = [W.scan_instance_2d(i) for i in range(96)]
-    steps = all_ws[0].nsteps
+    all_ws = [W.scan_instance_2d(i, nsteps=steps) for i in range(count)]
     if D.world() > 1:
         mine = D.partition_by_cost([D.scan_cost(w.n[0]) for w in all_ws], D.world())[D.rank()]
         ws = [all_ws[i] for i in mine]
@@ -223,8 +224,9 @@ def run_scan(sn, torch, stream, peak):
         g.close()
     value = cells * steps / t_batch
     gbs = 48.0 * cells * steps / t_batch / 1e9
-    return {"workload": "96 2D instances, n in {128,256,512,1024} (seed 4000+i), L=40, complex64, "
-                        "alpha_Y~U[0,1], lambda_Y~U[1,20], g~U[0,0.05], dt=1e-2, 500 steps",
+    return {"workload": f"{count} 2D instances, n in {{128,256,512,1024}} (seed 4000+i), L=40, "
+                        f"complex64, alpha_Y~U[0,1], lambda_Y~U[1,20], g~U[0,0.05], dt=1e-2, "
+                        f"{steps} steps",
             "cells": cells, "steps": steps, "value": value, "unit": "cell-steps/s",
             "ms_total": 1e3 * t_batch, "launches": 1,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
@@ -454,7 +456,7 @@ def main():
 
     scan = None
     if not args.no_scan:
-        scan = run_scan(sn, torch, stream, peak)
+        scan = run_scan(sn, torch, stream, peak, args.scan_count, args.scan_steps)
 
     fno = None
     if not args.no_fno and world == 1:

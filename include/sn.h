@@ -171,7 +171,8 @@ sn_status sn_test_line_fft_f32(void* data, long long nlines, int n, int sign, in
  * while nsteps is unchanged.
  *
  * Inside the launch, work items (round, pass, instance, tile) are taken in a
- * fixed order, and an item waits for the previous pass of its instance.  Each
+ * fixed order (within a pass, larger instances first), and an item waits for
+ * the previous pass of its instance.  Each
  * wait has a clock-cycle limit (sn_set_batch_wait_limit; about 2 s by default);
  * when a wait expires the kernel records it and returns, and the next
  * synchronising call returns SN_ETIMEOUT and leaves the batch state

@@ -29,7 +29,7 @@ constexpr int kMaxN = SN_NOALLOC_MAX_N;  // per axis
 constexpr size_t align32(size_t words) { return (words + 31) / 32 * 32; }
 constexpr size_t kRhoWords = align32((size_t)(kMaxN / 2 + 1) * kMaxN);  // half spectrum
 constexpr size_t kTwWords = align32(4 * (size_t)kMaxN);    // twiddles (hi, lo) of one axis
-constexpr size_t kMultWords = align32(2 * (size_t)kMaxN);  // one kinetic table (hi, lo)
+constexpr size_t kMultWords = align32(2 * (size_t)kMaxN);  // one kinetic table (a float4 of shears per k)
 constexpr size_t kK2Words = align32((size_t)kMaxN / 2 + 1);  // k^2 floats of one axis
 constexpr size_t kOffTw = kRhoWords;
 constexpr size_t kOffMult = kOffTw + 2 * kTwWords;
@@ -154,14 +154,9 @@ extern "C" sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, d
       e = cudaMemcpyAsync(tw[a], t32, 2 * ntw * sizeof(float2), cudaMemcpyHostToDevice, stream);
     }
     for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
-      const double tau = f ? dt : 0.5 * dt;
-      for (int j = 0; j < n[a]; ++j) {
-        const double kk = wavenumber(j, n[a], L[a]);
-        const double th = k->coeff_lap * kk * kk * tau;
-        t64[j] = make_double2(std::cos(th) / n[a], std::sin(th) / n[a]);
-      }
-      split_hilo(t64, n[a], t32);
-      e = cudaMemcpyAsync(mult[a][f], t32, 2 * n[a] * sizeof(float2), cudaMemcpyHostToDevice, stream);
+      float* l32 = reinterpret_cast<float*>(t32);
+      sn::kinetic_lift_table(n[a], L[a], k->coeff_lap, f ? dt : 0.5 * dt, l32);
+      e = cudaMemcpyAsync(mult[a][f], l32, 4 * n[a] * sizeof(float), cudaMemcpyHostToDevice, stream);
     }
     if (e == cudaSuccess) {
       for (int j = 0; j < n[a]; ++j) {
@@ -195,7 +190,7 @@ extern "C" sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, d
       pa.psi = p;
       pa.outer = a == 0 ? 1 : ny;
       pa.inner = a == 0 ? nx : 1;
-      pa.mult = mult[a][full];
+      pa.lift = reinterpret_cast<const float4*>(mult[a][full]);
       pa.tw = tw[a];
       pa.rh_in = rhohat;
       pa.vext = nullptr;

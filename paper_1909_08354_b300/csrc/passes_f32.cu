@@ -74,7 +74,7 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
 }
 
-// shared memory: twiddles (hi, lo), kinetic factors (hi, lo), line buffers,
+// shared memory: twiddles (hi, lo), kinetic factors (shears), line buffers,
 // and for P1 two staging tiles of the half spectrum.  The tensor-core engine
 // (TC, 256-point lines) keeps its fragment and twiddle tables, a padded copy
 // of the kinetic factors and padded line buffers instead.
@@ -133,7 +133,7 @@ psi_pass_kernel(PsiPassArgs a) {
     for (int k = tid; k < 2 * N; k += NT) mult_tc[(k / N) * tc16::MT + tc16::pt(k % N)] = a.mult[k];
   } else {
     for (int k = tid; k < 2 * P::TWN; k += NT) tw_sm[k] = ldc(a.tw + k);
-    for (int k = tid; k < 2 * N; k += NT) mult_sm[k] = ldc(a.mult + k);
+    for (int k = tid; k < N; k += NT) reinterpret_cast<float4*>(mult_sm)[k] = a.lift[k];
   }
 
   // P1: stage the [k][line] half-spectrum tile of tile tau into shared memory
@@ -205,7 +205,7 @@ psi_pass_kernel(PsiPassArgs a) {
       const tc16::MultTable mt{mult_tc, mult_tc + tc16::MT};
       tc16::fmi(v, lines, *tabs, l, t, [&](int) { return mt; });
     } else {
-      tile::kinetic<N, WL>(v, lines + l * LS, tw_sm, mult_sm, t);
+      tile::kinetic<N, WL>(v, lines + l * LS, tw_sm, reinterpret_cast<const float4*>(mult_sm), t);
     }
     store_line<E, T>(v, a.psi + base, ustride, t, valid);
 

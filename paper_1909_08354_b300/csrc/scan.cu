@@ -4,7 +4,7 @@
 // problem).
 //
 // Work is a queue of items (round r, slot s, instance i, tile j), in that
-// order.  A 2D merged step has three slots per round: the psi pass along the
+// order, with the instances of a slot ordered by decreasing n.  A 2D merged step has three slots per round: the psi pass along the
 // first axis (with the potential and nonlinear phase after round 0), the psi
 // pass along the second axis (with the density before the last round), and
 // the Green's-multiply pass on the half spectrum.  CTA c takes items
@@ -76,7 +76,7 @@ struct Inst {
   float2* psi;          // n x n
   float2* rho;          // (n/2 + 1) x n half spectrum
   const float2* tw;     // twiddles of length n (hi, lo)
-  const float2* mult;   // [half, full] x 2n (hi, lo) kinetic factors, same for both axes
+  const float2* mult;   // [half, full] x n kinetic factors as shears (float4), same for both axes
   const float* k2;      // n entries
   float cN, cY, mu2, gh;
   unsigned t_psi, t_rho;  // tiles per psi pass and per Green's pass
@@ -139,7 +139,7 @@ __device__ __noinline__ void psi_item(const Inst& d, int full, long long tau, un
   const bool valid = l < nvalid;
   const unsigned ustride = STRIDED ? (unsigned)N : 1u;
   const cx<float>* tw = reinterpret_cast<const cx<float>*>(d.tw);
-  const cx<float>* mult = reinterpret_cast<const cx<float>*>(d.mult) + full * 2 * N;
+  const float4* lift = reinterpret_cast<const float4*>(d.mult) + full * N;
   float vph[E];
   (void)vph;
   if constexpr (VARIANT == PSI_NPHASE) {
@@ -156,7 +156,7 @@ __device__ __noinline__ void psi_item(const Inst& d, int full, long long tau, un
   tile::load_line<E, T, true>(v, d.psi + base, ustride, t, valid);
   if constexpr (VARIANT == PSI_NPHASE)
     tile::nonlinear_phase<E, T>(v, vph, d.gh, nullptr, 0.f, ustride, t, valid);
-  tile::kinetic<N, WL>(v, lines + l * LS, tw, mult, t);
+  tile::kinetic<N, WL>(v, lines + l * LS, tw, lift, t);
   tile::store_line<E, T>(v, d.psi + base, ustride, t, valid);
   if constexpr (VARIANT == PSI_DENSITY) {
     float2* rh = d.rho;
@@ -275,6 +275,10 @@ struct sn_batch_s {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<Inst> host_inst;
+  // queue position -> instance: largest n first, so that neighbouring work
+  // items (taken by CTAs at the same time) run the same item function and
+  // share the instruction cache
+  std::vector<int> order;
   Inst* dev_inst = nullptr;
   float2* tw[kMaxLog2 + 1] = {};
   std::vector<float2*> mult;
@@ -387,6 +391,9 @@ sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* 
       return bail(bcuda(e, "cudaStreamCreate"));
     b->own_stream = true;
   }
+  b->order.resize(count);
+  for (int i = 0; i < count; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return n[x] > n[y]; });
   std::vector<unsigned long long> prefix(3 * (count + 1), 0);
   for (int i = 0; i < count; ++i) {
     Inst& d = b->host_inst[i];
@@ -423,9 +430,12 @@ sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* 
     if ((e = cudaMemcpy(b->k2[i], k2.data(), N * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(bcuda(e, "cudaMemcpy(k2)"));
     d.k2 = b->k2[i];
-    prefix[0 * (count + 1) + i + 1] = prefix[0 * (count + 1) + i] + d.t_psi;
-    prefix[1 * (count + 1) + i + 1] = prefix[1 * (count + 1) + i] + d.t_psi;
-    prefix[2 * (count + 1) + i + 1] = prefix[2 * (count + 1) + i] + d.t_rho;
+  }
+  for (int p = 0; p < count; ++p) {
+    const Inst& d = b->host_inst[b->order[p]];
+    prefix[0 * (count + 1) + p + 1] = prefix[0 * (count + 1) + p] + d.t_psi;
+    prefix[1 * (count + 1) + p + 1] = prefix[1 * (count + 1) + p] + d.t_psi;
+    prefix[2 * (count + 1) + p + 1] = prefix[2 * (count + 1) + p] + d.t_rho;
   }
   if ((e = balloc(b, &b->slot_prefix, prefix.size())) != cudaSuccess)
     return bail(bcuda(e, "cudaMalloc(prefix)"));
@@ -523,18 +533,10 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
     if (std::memcmp(&before, &d, sizeof(Inst)) != 0) changed = true;
     if (!(h == b->dt[i])) {
       if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bcuda(e, "sync");
-      std::vector<float2> m32(4 * N);
-      for (int f = 0; f < 2; ++f) {
-        const double tau = f ? h : 0.5 * h;
-        std::vector<double2> m(N);
-        for (int j = 0; j < N; ++j) {
-          const double kk = wavenumber(j, N, b->L[i]);
-          const double th = k.coeff_lap * kk * kk * tau;
-          m[j] = make_double2(std::cos(th) / N, std::sin(th) / N);
-        }
-        split_hilo(m, m32.data() + 2 * N * f);
-      }
-      if ((e = cudaMemcpy(b->mult[i], m32.data(), m32.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
+      std::vector<float> m32(8 * (size_t)N);
+      for (int f = 0; f < 2; ++f)
+        kinetic_lift_table(N, b->L[i], k.coeff_lap, f ? h : 0.5 * h, m32.data() + 4 * N * f);
+      if ((e = cudaMemcpy(b->mult[i], m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
           cudaSuccess)
         return bcuda(e, "cudaMemcpy(mult)");
       b->dt[i] = h;
@@ -542,7 +544,9 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
   }
   if (changed || b->launches == 0) {
     if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bcuda(e, "sync");
-    if ((e = cudaMemcpy(b->dev_inst, b->host_inst.data(), sizeof(Inst) * b->count,
+    std::vector<Inst> queued(b->count);
+    for (int p = 0; p < b->count; ++p) queued[p] = b->host_inst[b->order[p]];
+    if ((e = cudaMemcpy(b->dev_inst, queued.data(), sizeof(Inst) * b->count,
                         cudaMemcpyHostToDevice)) != cudaSuccess)
       return bcuda(e, "cudaMemcpy(inst)");
   }

@@ -92,6 +92,21 @@ struct Launch {
 
 void sn::set_thread_error(const char* msg) { g_tls_error = msg; }
 
+void sn::kinetic_lift_table(int n, double L, double A, double tau, float* out4) {
+  for (int j = 0; j < n; ++j) {
+    const double k = wavenumber(j, n, L);
+    // theta reduced to (-pi, pi], then to [-pi/2, pi/2] with the sign in the scale
+    double th = std::remainder(A * k * k * tau, 2.0 * kPi);
+    double sc = 1.0 / n;
+    if (th > 0.5 * kPi) { th -= kPi; sc = -sc; }
+    if (th < -0.5 * kPi) { th += kPi; sc = -sc; }
+    out4[4 * j + 0] = (float)std::tan(0.5 * th);
+    out4[4 * j + 1] = (float)std::sin(th);
+    out4[4 * j + 2] = (float)sc;
+    out4[4 * j + 3] = 0.f;
+  }
+}
+
 struct sn_grid_s {
   int ndim = 0;
   int n[3] = {1, 1, 1};
@@ -123,6 +138,7 @@ struct sn_grid_s {
   float* zero32 = nullptr;  // a single 0 (k^2 of a missing middle axis)
   // kinetic multipliers [axis][half=0/full=1]: n entries (FP64) or 2n (FP32 hi, lo)
   float2* mult32[3][2] = {};
+  float4* lift32[3][2] = {};  // the same factors as three shears (FP32 engine)
   double2* mult64[3][2] = {};
   double mult_dt = std::nan("");
   double mult_A = std::nan("");
@@ -230,6 +246,11 @@ sn_status ensure_mult_tables(sn_grid g, double dt) {
         split_hilo(m64, m32);
         e = cudaMemcpy(g->mult32[a][f], m32.data(), m32.size() * sizeof(float2),
                        cudaMemcpyHostToDevice);
+        std::vector<float> l32(4 * (size_t)n);
+        sn::kinetic_lift_table(n, g->L[a], A, tau, l32.data());
+        if (e == cudaSuccess)
+          e = cudaMemcpy(g->lift32[a][f], l32.data(), l32.size() * sizeof(float),
+                         cudaMemcpyHostToDevice);
       } else {
         e = cudaMemcpy(g->mult64[a][f], m64.data(), n * sizeof(double2), cudaMemcpyHostToDevice);
       }
@@ -273,6 +294,7 @@ sn_status psi_pass(sn_grid g, int a, int variant, int full, double dt) {
   pa.outer = lg.outer;
   pa.inner = lg.inner;
   pa.mult = g->mult32[a][full];
+  pa.lift = g->lift32[a][full];
   pa.tw = g->tw32[log2i(g->n[a])];
   pa.rh_in = g->rhohat;
   pa.vext = g->has_vext ? g->vext32 : nullptr;
@@ -552,6 +574,7 @@ sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, 
     if ((e = upload(g, &g->k2_32[a], k2f)) != cudaSuccess) return bail(cuda_fail(g, e, "upload(k2f)"));
     for (int f = 0; f < 2; ++f) {
       if (dtype == SN_C64) e = dalloc(g, &g->mult32[a][f], 2 * (size_t)n[a]);
+      if (dtype == SN_C64 && e == cudaSuccess) e = dalloc(g, &g->lift32[a][f], (size_t)n[a]);
       else e = dalloc(g, &g->mult64[a][f], (size_t)n[a]);
       if (e != cudaSuccess) return bail(cuda_fail(g, e, "cudaMalloc(mult)"));
     }

@@ -30,6 +30,20 @@ template <typename R>
 __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
 template <typename R>
 __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+
+// FP32 complex addition and subtraction as one packed FP32x2 instruction each
+// (sm_100 and later): the butterflies are mostly additions, and the passes
+// are bound by instruction issue.  a - b is fma(b, -1, a), rounded once like
+// a subtraction.
+__device__ __forceinline__ cx<float> operator+(cx<float> a, cx<float> b) {
+  const float2 r = __fadd2_rn(make_float2(a.re, a.im), make_float2(b.re, b.im));
+  return {r.x, r.y};
+}
+__device__ __forceinline__ cx<float> operator-(cx<float> a, cx<float> b) {
+  const float2 r =
+      __ffma2_rn(make_float2(b.re, b.im), make_float2(-1.f, -1.f), make_float2(a.re, a.im));
+  return {r.x, r.y};
+}
 template <typename R>
 __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
@@ -69,6 +83,13 @@ __device__ __forceinline__ cx<R> rot(cx<R> a, double c, double s) {
     return {a.re * cc - a.im * ss, a.re * ss + a.im * cc};
   }
 }
+
+// a * exp(SIGN i pi/4) (Q = 1) or a * exp(SIGN i 3pi/4) (Q = 3).  The factor is
+// (+-1 + SIGN i) sqrt(1/2): in FP32 the sum and difference of the two parts
+// are formed first and then scaled by sqrt(1/2) as a hi + lo pair, two
+// additions and two packed FP32x2 instructions instead of eight.
+template <typename R, int SIGN, int Q>
+__device__ __forceinline__ cx<R> rot8(cx<R> a);
 
 // a * (wh + wl): product with a factor stored as a hi + lo pair (FP32 path).
 __device__ __forceinline__ cx<float> cmul_hl(cx<float> a, cx<float> wh, cx<float> wl) {
@@ -114,6 +135,23 @@ constexpr double kC8 = 0.70710678118654752440;   // cos(pi/4)
 constexpr double kC16 = 0.92387953251128675613;  // cos(pi/8)
 constexpr double kS16 = 0.38268343236508977173;  // sin(pi/8)
 
+template <typename R, int SIGN, int Q>
+__device__ __forceinline__ cx<R> rot8(cx<R> a) {
+  static_assert(Q == 1 || Q == 3, "rot8 turns by pi/4 or 3pi/4");
+  if constexpr (sizeof(R) == sizeof(float)) {
+    constexpr float h = (float)kC8;
+    constexpr float l = (float)(kC8 - (double)(float)kC8);
+    constexpr float sg = SIGN < 0 ? -1.f : 1.f;
+    const float p = Q == 1 ? a.re - sg * a.im : -a.re - sg * a.im;
+    const float q = Q == 1 ? a.im + sg * a.re : -a.im + sg * a.re;
+    const float2 r = __ffma2_rn(make_float2(p, q), make_float2(h, h),
+                                __fmul2_rn(make_float2(p, q), make_float2(l, l)));
+    return {r.x, r.y};
+  } else {
+    return rot<R, SIGN>(a, Q == 1 ? kC8 : -kC8, kC8);
+  }
+}
+
 template <typename R, int SIGN>
 __device__ __forceinline__ void dft8(cx<R>* a) {
   // radix-2 decimation in time over two 4-point DFTs
@@ -121,9 +159,9 @@ __device__ __forceinline__ void dft8(cx<R>* a) {
   cx<R> o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
   dft4<R, SIGN>(e0, e1, e2, e3);
   dft4<R, SIGN>(o0, o1, o2, o3);
-  o1 = rot<R, SIGN>(o1, kC8, kC8);
+  o1 = rot8<R, SIGN, 1>(o1);
   o2 = mul_si<R, SIGN>(o2);
-  o3 = rot<R, SIGN>(o3, -kC8, kC8);
+  o3 = rot8<R, SIGN, 3>(o3);
   a[0] = e0 + o0; a[4] = e0 - o0;
   a[1] = e1 + o1; a[5] = e1 - o1;
   a[2] = e2 + o2; a[6] = e2 - o2;
@@ -142,13 +180,13 @@ __device__ __forceinline__ void dft16(cx<R>* a) {
   }
   // twiddles W16^(n2 k1)
   b[5] = rot<R, SIGN>(b[5], kC16, kS16);     // n2=1,k1=1 -> 1
-  b[6] = rot<R, SIGN>(b[6], kC8, kC8);       // 1,2 -> 2
+  b[6] = rot8<R, SIGN, 1>(b[6]);             // 1,2 -> 2
   b[7] = rot<R, SIGN>(b[7], kS16, kC16);     // 1,3 -> 3
-  b[9] = rot<R, SIGN>(b[9], kC8, kC8);       // 2,1 -> 2
+  b[9] = rot8<R, SIGN, 1>(b[9]);             // 2,1 -> 2
   b[10] = mul_si<R, SIGN>(b[10]);            // 2,2 -> 4
-  b[11] = rot<R, SIGN>(b[11], -kC8, kC8);    // 2,3 -> 6
+  b[11] = rot8<R, SIGN, 3>(b[11]);           // 2,3 -> 6
   b[13] = rot<R, SIGN>(b[13], kS16, kC16);   // 3,1 -> 3
-  b[14] = rot<R, SIGN>(b[14], -kC8, kC8);    // 3,2 -> 6
+  b[14] = rot8<R, SIGN, 3>(b[14]);           // 3,2 -> 6
   b[15] = rot<R, SIGN>(b[15], -kC16, -kS16); // 3,3 -> 9
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
@@ -175,7 +213,11 @@ __device__ __forceinline__ void dft32(cx<R>* a) {
     // cos(k pi/16), sin(k pi/16) from the first-octant table
     const double c = (k <= 8) ? C[k] : -C[16 - k];
     const double s = (k <= 8) ? C[8 - k] : C[k - 8];
-    cx<R> w = (k == 0) ? o[k] : rot<R, SIGN>(o[k], c, s);
+    cx<R> w = (k == 0) ? o[k]
+              : (k == 8)  ? mul_si<R, SIGN>(o[k])
+              : (k == 4)  ? rot8<R, SIGN, 1>(o[k])
+              : (k == 12) ? rot8<R, SIGN, 3>(o[k])
+                          : rot<R, SIGN>(o[k], c, s);
     a[k] = e[k] + w;
     a[k + 16] = e[k] - w;
   }
@@ -210,8 +252,11 @@ struct Plan {
   static constexpr int R0 = N <= 16 ? N : (N == 32 ? 2 : N == 64 ? 4 : N == 128 ? 8 : N == 256 ? 16 : N == 512 ? 16 : 32);
   static constexpr int R1 = N / R0;
   static constexpr int STAGES = (R1 == 1) ? 1 : 2;
-  // padded shared-memory line: one pad slot per 16 elements, odd line stride
-  static constexpr int LS = N + N / 16 + 1;
+  // padded shared-memory line: one pad slot per PAD elements (PAD = the
+  // first-stage radix of the long lines, so that the runs a thread writes
+  // start at odd strides), odd line stride
+  static constexpr int PAD_SHIFT = N >= 1024 ? 5 : 4;
+  static constexpr int LS = N + (N >> PAD_SHIFT) + 1;
   // twiddle table entries: forward second stage (N) + inverse second stage (N)
   static constexpr int TWN = STAGES == 2 ? 2 * N : 0;
   // entries held per table in shared memory: FP32 keeps hi and lo parts
@@ -219,7 +264,8 @@ struct Plan {
   static constexpr int tw_words() { return sizeof(R) == sizeof(float) ? 2 * TWN : TWN; }
 };
 
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+template <int N>
+__device__ __forceinline__ int pidx(int i) { return i + (i >> Plan<N>::PAD_SHIFT); }
 
 // Twiddle table of length N: entry [r*R0 + j] = exp(-2 pi i j r / N) for the
 // forward second stage (r < R1, j < R0), followed by entry
@@ -253,13 +299,13 @@ __device__ __forceinline__ void line_transform(cx<R> (&v)[Plan<N>::E], cx<R>* li
         dft<R, SIGN, RA>(a);
         const int j = t + T * u;
 #pragma unroll
-        for (int q = 0; q < RA; ++q) line_buf[pidx(j * RA + q)] = a[q];
+        for (int q = 0; q < RA; ++q) line_buf[pidx<N>(j * RA + q)] = a[q];
       }
     }
     if (WARP_LOCAL) __syncwarp(); else __syncthreads();
     if (active) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = line_buf[pidx(t + T * m)];
+      for (int m = 0; m < E; ++m) v[m] = line_buf[pidx<N>(t + T * m)];
       const cx<R>* tw = tw_sm + (SIGN < 0 ? 0 : N);
 #pragma unroll
       for (int u = 0; u < UB; ++u) {

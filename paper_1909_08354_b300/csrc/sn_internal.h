@@ -30,7 +30,8 @@ enum PassKind {
 struct PsiPassArgs {
   float2* psi;
   long long outer, inner;  // lines = outer * inner; element stride inner (strided) or 1
-  const float2* mult;      // 2N entries: hi then lo parts of exp(i A k^2 tau) / N
+  const float2* mult;      // 2N entries: hi then lo parts of exp(i A k^2 tau) / N (TC engine)
+  const float4* lift;      // N entries: the same factor as three shears (FP32 engine)
   const float2* tw;        // twiddle table of this N (hi parts, then lo parts)
   const float2* rh_in;     // NPHASE: half spectrum [N/2+1][lines]
   const float* vext;       // NPHASE: optional V_ext in psi layout (NULL for none)
@@ -62,6 +63,10 @@ cudaError_t launch_psi_pass_f32(int N, bool strided, int variant, const PsiPassA
                                 cudaStream_t s);
 cudaError_t launch_rho_pass_f32(int N, bool strided, int op, const RhoPassArgs& a,
                                 cudaStream_t s);
+// Kinetic factor exp(i A k_j^2 tau) / n of the FP32 passes, j < n, as a rotation
+// by three shears: out[4j .. 4j+3] = (tan(phi/2), sin(phi), +-1/n, 0), phi the
+// angle reduced to [-pi/2, pi/2] (the sign of the scale carries the rest).
+void kinetic_lift_table(int n, double L, double A, double tau, float* out4);
 // FP16 fragment tables of the tensor-core engine (tc16.cuh), tc16::FRAG_WORDS words
 void tc16_fragment_table(std::vector<unsigned>& words);
 

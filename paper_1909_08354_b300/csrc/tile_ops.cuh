@@ -168,21 +168,37 @@ __device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float (
     r = fmaf(-kq, -1.74845553e-7f, r);
     float s, c;
     __sincosf(r, &s, &c);
-    const float f = fmaf(-0.5f, fmaf(c, c, fmaf(s, s, -1.f)), 1.f);
-    c *= f;
-    s *= f;
+    // one Newton step towards c^2 + s^2 = 1, applied as c + c e: the factor
+    // 1 + e itself would round to 1 whenever e is below an ulp (tiny angles,
+    // where the SFU cosine can sit one ulp under 1), and every such step
+    // would shrink the mass
+    const float e = -0.5f * fmaf(c, c, fmaf(s, s, -1.f));
+    c = fmaf(c, e, c);
+    s = fmaf(s, e, s);
     v[m] = {v[m].re * c + v[m].im * s, v[m].im * c - v[m].re * s};  // v * exp(-i th)
   }
 }
 
-// FFT . m . IFFT along my line (m: hi parts at [0, N), lo parts at [N, 2N)).
+// FFT . m . IFFT along my line, m = exp(i A k^2 tau) / N given per k as a
+// rotation by three shears, (x, y) -> x1 = x - t y, y1 = y + s x1,
+// x2 = x1 - t y1 with t = tan(phi/2), s = sin(phi), then the scale +-1/N.
+// Each shear is one FMA and the shear matrices have determinant 1, so the
+// rounded coefficients change the angle by ~1e-8 but not the norm: no mass
+// drift on average, where the product with a hi + lo factor (two roundings)
+// drifts by ~1e-8 per application on the structured spectra of lumps.
 template <int N, bool WL>
 __device__ __forceinline__ void kinetic(cx<float> (&v)[Plan<N>::E], cx<float>* line_buf,
-                                        const cx<float>* tw, const cx<float>* mult, int t) {
+                                        const cx<float>* tw, const float4* lift, int t) {
   constexpr int E = Plan<N>::E, T = Plan<N>::T;
   line_transform<float, N, -1, WL>(v, line_buf, tw, t, true);
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = cmul_hl(v[m], mult[t + T * m], mult[N + t + T * m]);
+  for (int m = 0; m < E; ++m) {
+    const float4 q = lift[t + T * m];
+    const float x1 = fmaf(-q.x, v[m].im, v[m].re);
+    const float y1 = fmaf(q.y, x1, v[m].im);
+    const float x2 = fmaf(-q.x, y1, x1);
+    v[m] = {x2 * q.z, y1 * q.z};
+  }
   line_transform<float, N, +1, WL>(v, line_buf, tw, t, true);
 }
 
@@ -218,7 +234,7 @@ __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], 
   __syncthreads();
   if (pa) {
 #pragma unroll
-    for (int q = 0; q < E; ++q) lines[l * LS + pidx(t + T * q)] = v[q];
+    for (int q = 0; q < E; ++q) lines[l * LS + pidx<N>(t + T * q)] = v[q];
   }
   __syncthreads();
   constexpr int NH = (H + T - 1) / T;
@@ -229,8 +245,8 @@ __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], 
     const int k = t + T * q;
     hs[q] = {0.f, 0.f};
     if (k < H) {
-      const cx<float> zk = zb[pidx(k)];
-      const cx<float> zn = cconj(zb[pidx((N - k) & (N - 1))]);
+      const cx<float> zk = zb[pidx<N>(k)];
+      const cx<float> zn = cconj(zb[pidx<N>((N - k) & (N - 1))]);
       if (pa) {
         hs[q] = cscale(zk + zn, 0.5f);
       } else {

@@ -230,23 +230,46 @@ def test_head_on_collision_3d_128_one_step(dtype):
 
 
 def test_head_on_collision_3d_128_c64_2000_steps():
-    """The 128^3 collision over its full 2000 steps in complex64 against the plain
-    FP64 GPU step (itself held to the oracle at 1e-12 per step): rel-L2 within the
-    per-step bar times the steps, mass to 1e-5.  The spread of the FP64 run under
-    the complex64 rounding of the initial state is reported beside it."""
+    """The 128^3 collision over its 2000 steps in complex64 against the plain FP64
+    GPU step (itself held to the oracle at 1e-12 per step).  The trajectory is
+    chaotic, so FP32 rounding grows far beyond the per-step bar.  The bound at
+    each checkpoint comes from a measured FP32 spread: the same complex64 step
+    run on the axis-reversed state (the same physics with its rounding in a
+    different order), mapped back.  The complex64 error must stay within five
+    times that spread, one sample of a chaotic quantity (or within the per-step
+    bar times the steps, when larger); the mass is held to 1e-5."""
     w = W.head_on_collision_3d()
     kw = kernel_kw(w.kernel)
     psi = w.psi0()
-    out32 = gpu_run(psi.astype(np.complex64), w.L, kw, "c64", w.dt, w.nsteps)
-    ref = gpu_run(psi, w.L, kw, "c128", w.dt, w.nsteps)
-    spread = gpu_run(psi.astype(np.complex64).astype(np.complex128), w.L, kw, "c128", w.dt,
-                     w.nsteps)
-    err = O.rel_l2(out32, ref)
-    print(f"collision 128^3, 2000 steps: rel-L2 c64 vs c128 {err:.3e}, "
-          f"c128 spread from the c64 rounding of psi0 {O.rel_l2(spread, ref):.3e}")
-    assert err <= w.nsteps * STEP_TOL["c64"]
-    m = lambda a: float(np.sum(np.abs(a.astype(np.complex128)) ** 2))  # noqa: E731
-    assert abs(m(out32) / m(psi) - 1) <= 1e-5
+    grids = {}
+    for name, dtype, start in (("c64", "c64", psi.astype(np.complex64)),
+                               ("c64_rev", "c64", np.ascontiguousarray(
+                                   psi.transpose(2, 1, 0)).astype(np.complex64)),
+                               ("ref", "c128", psi)):
+        g = sn.Grid(w.n, w.L, dtype)
+        g.set_kernel(**kw)
+        g.set_state(start)
+        grids[name] = g
+    m0 = float(np.sum(np.abs(psi) ** 2))
+    try:
+        done = 0
+        for k in (200, 1000, 2000):
+            for g in grids.values():
+                g.step(w.dt, k - done)
+            done = k
+            st = {n: g.get_state() for n, g in grids.items()}
+            rev = st["c64_rev"].transpose(2, 1, 0)
+            err = O.rel_l2(st["c64"], st["ref"])
+            spread = O.rel_l2(rev, st["c64"])
+            print(f"collision 128^3 at step {k}: c64 vs c128 {err:.3e}, "
+                  f"c64 spread (axis-reversed run) {spread:.3e}")
+            assert err <= max(k * STEP_TOL["c64"], 5.0 * spread), (k, err, spread)
+        mass = float(np.sum(np.abs(st["c64"].astype(np.complex128)) ** 2))
+        print(f"collision 128^3 complex64 mass drift over 2000 steps: {mass / m0 - 1:.3e}")
+        assert abs(mass / m0 - 1) <= 1e-5
+    finally:
+        for g in grids.values():
+            g.close()
 
 
 def test_nbody_3d_256_c64_one_step_vs_oracle():
