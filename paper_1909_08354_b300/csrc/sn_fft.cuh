@@ -132,8 +132,6 @@ __device__ __forceinline__ void dft4(cx<R>& x0, cx<R>& x1, cx<R>& x2, cx<R>& x3)
 }
 
 constexpr double kC8 = 0.70710678118654752440;   // cos(pi/4)
-constexpr double kC16 = 0.92387953251128675613;  // cos(pi/8)
-constexpr double kS16 = 0.38268343236508977173;  // sin(pi/8)
 
 template <typename R, int SIGN, int Q>
 __device__ __forceinline__ cx<R> rot8(cx<R> a) {
@@ -149,6 +147,62 @@ __device__ __forceinline__ cx<R> rot8(cx<R> a) {
     return {r.x, r.y};
   } else {
     return rot<R, SIGN>(a, Q == 1 ? kC8 : -kC8, kC8);
+  }
+}
+
+// tan(k pi / 32) and sin(k pi / 16), k = 0..8: the three-shear form of the
+// rotations by k pi / 16 inside the radix-16 and radix-32 kernels
+constexpr double kTan32[9] = {0.0, 0.0984914033571642530772, 0.198912367379658006912,
+                              0.303346683607342391676, 0.414213562373095048802,
+                              0.534511135950791641090, 0.668178637919298919998,
+                              0.820678790828660330972, 1.0};
+constexpr double kSin16[9] = {0.0, 0.195090322016128267848, 0.382683432365089771728,
+                              0.555570233019602224743, 0.707106781186547524401,
+                              0.831469612302545237079, 0.923879532511286756128,
+                              0.980785280403230449126, 1.0};
+
+// a * exp(SIGN i k pi / 16), 0 < k < 16.  In FP32 the rotation is three shears,
+// x1 = x - t y, y1 = y + s x1, x2 = x1 - t y1 with t = tan(phi/2), s = sin(phi):
+// three FMAs, and each shear has determinant 1, so the rounded t and s move
+// the angle by ~1e-8 but leave the norm alone (no mass drift), where a
+// product with a rounded cosine and sine pair would not.  Angles past pi/2 are
+// turned by phi - pi and negated (the negation folds into the FMA operands).
+template <typename R, int SIGN, int K>
+__device__ __forceinline__ cx<R> rot16(cx<R> a) {
+  static_assert(K > 0 && K < 16, "rot16 turns by k pi / 16, 0 < k < 16");
+  if constexpr (sizeof(R) == sizeof(float)) {
+    constexpr bool flip = K > 8;
+    constexpr int k = flip ? 16 - K : K;                  // |phi| = k pi / 16 after the flip
+    constexpr float sg = (SIGN < 0) != flip ? -1.f : 1.f;  // sign of phi
+    constexpr float t = sg * (float)kTan32[k], s = sg * (float)kSin16[k];
+    const float x1 = fmaf(-t, a.im, a.re);
+    const float y1 = fmaf(s, x1, a.im);
+    const float x2 = fmaf(-t, y1, x1);
+    if constexpr (flip) return {-x2, -y1};
+    else return {x2, y1};
+  } else {
+    constexpr double c = K <= 8 ? kSin16[8 - K] : -kSin16[K - 8];  // cos(K pi / 16)
+    constexpr double s = K <= 8 ? kSin16[K] : kSin16[16 - K];       // sin(K pi / 16)
+    return rot<R, SIGN>(a, c, s);
+  }
+}
+
+// rot16 with k known only after unrolling (folds to one case)
+template <typename R, int SIGN>
+__device__ __forceinline__ cx<R> rot16_at(cx<R> a, int k) {
+  switch (k) {
+    case 1: return rot16<R, SIGN, 1>(a);
+    case 2: return rot16<R, SIGN, 2>(a);
+    case 3: return rot16<R, SIGN, 3>(a);
+    case 5: return rot16<R, SIGN, 5>(a);
+    case 6: return rot16<R, SIGN, 6>(a);
+    case 7: return rot16<R, SIGN, 7>(a);
+    case 9: return rot16<R, SIGN, 9>(a);
+    case 10: return rot16<R, SIGN, 10>(a);
+    case 11: return rot16<R, SIGN, 11>(a);
+    case 13: return rot16<R, SIGN, 13>(a);
+    case 14: return rot16<R, SIGN, 14>(a);
+    default: return rot16<R, SIGN, 15>(a);
   }
 }
 
@@ -179,15 +233,15 @@ __device__ __forceinline__ void dft16(cx<R>* a) {
     b[4 * n2 + 0] = x0; b[4 * n2 + 1] = x1; b[4 * n2 + 2] = x2; b[4 * n2 + 3] = x3;
   }
   // twiddles W16^(n2 k1)
-  b[5] = rot<R, SIGN>(b[5], kC16, kS16);     // n2=1,k1=1 -> 1
+  b[5] = rot16<R, SIGN, 2>(b[5]);            // n2=1,k1=1 -> 1
   b[6] = rot8<R, SIGN, 1>(b[6]);             // 1,2 -> 2
-  b[7] = rot<R, SIGN>(b[7], kS16, kC16);     // 1,3 -> 3
+  b[7] = rot16<R, SIGN, 6>(b[7]);            // 1,3 -> 3
   b[9] = rot8<R, SIGN, 1>(b[9]);             // 2,1 -> 2
   b[10] = mul_si<R, SIGN>(b[10]);            // 2,2 -> 4
   b[11] = rot8<R, SIGN, 3>(b[11]);           // 2,3 -> 6
-  b[13] = rot<R, SIGN>(b[13], kS16, kC16);   // 3,1 -> 3
+  b[13] = rot16<R, SIGN, 6>(b[13]);          // 3,1 -> 3
   b[14] = rot8<R, SIGN, 3>(b[14]);           // 3,2 -> 6
-  b[15] = rot<R, SIGN>(b[15], -kC16, -kS16); // 3,3 -> 9
+  b[15] = rot16<R, -SIGN, 14>(b[15]);        // 3,3 -> 9 (18 pi/16 = -14 pi/16 mod 2 pi)
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
     cx<R> x0 = b[k1], x1 = b[4 + k1], x2 = b[8 + k1], x3 = b[12 + k1];
@@ -199,10 +253,6 @@ __device__ __forceinline__ void dft16(cx<R>* a) {
 template <typename R, int SIGN>
 __device__ __forceinline__ void dft32(cx<R>* a) {
   // radix-2 decimation in time over two 16-point DFTs; W32^k = exp(SIGN i pi k / 16)
-  constexpr double C[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613,
-                           0.83146961230254523708, 0.70710678118654752440,
-                           0.55557023301960222474, 0.38268343236508977173,
-                           0.19509032201612826785, 0.0};  // cos(k pi / 16), k = 0..8
   cx<R> e[16], o[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) { e[i] = a[2 * i]; o[i] = a[2 * i + 1]; }
@@ -210,14 +260,11 @@ __device__ __forceinline__ void dft32(cx<R>* a) {
   dft16<R, SIGN>(o);
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    // cos(k pi/16), sin(k pi/16) from the first-octant table
-    const double c = (k <= 8) ? C[k] : -C[16 - k];
-    const double s = (k <= 8) ? C[8 - k] : C[k - 8];
     cx<R> w = (k == 0) ? o[k]
               : (k == 8)  ? mul_si<R, SIGN>(o[k])
               : (k == 4)  ? rot8<R, SIGN, 1>(o[k])
               : (k == 12) ? rot8<R, SIGN, 3>(o[k])
-                          : rot<R, SIGN>(o[k], c, s);
+                          : rot16_at<R, SIGN>(o[k], k);
     a[k] = e[k] + w;
     a[k + 16] = e[k] - w;
   }
