@@ -178,8 +178,8 @@ psi_pass_kernel(PsiPassArgs a) {
       cp_async_commit();
       cp_async_wait<1>();
       __syncthreads();
-      tile::potential_c2r<N, LPB, WL, TC>(rstage + (it & 1) * (H * TSTR), lines, tw_sm, l, t,
-                                          vph, tabs);
+      tile::potential_c2r<N, LPB, WL, TC, STRIDED>(rstage + (it & 1) * (H * TSTR), lines, tw_sm,
+                                                   l, t, vph, tabs);
     }
 
     // ---- this tile's psi (loaded one iteration ago); start the next tile's load
@@ -214,8 +214,8 @@ psi_pass_kernel(PsiPassArgs a) {
       auto put = [&](int k, int ll, cx<float> z) {
         tile::stg_c(rh + (size_t)k * nlines + line0 + ll, z);
       };
-      tile::density_r2c<N, LPB, WL, decltype(put), TC>(v, valid, lines, tw_sm, l, t, tid, nvalid,
-                                                       put, tabs);
+      tile::density_r2c<N, LPB, WL, decltype(put), TC, STRIDED>(v, valid, lines, tw_sm, l, t, tid,
+                                                                nvalid, put, tabs);
     }
     __syncthreads();  // line buffers and the staging tile are reused next iteration
   }

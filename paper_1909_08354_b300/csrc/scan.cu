@@ -150,7 +150,7 @@ __device__ __noinline__ void psi_item(const Inst& d, int full, long long tau, un
       rtile[k * TSTR + ll] = z;
     }
     __syncthreads();
-    tile::potential_c2r<N, LPB, WL>(rtile, lines, tw, l, t, vph);
+    tile::potential_c2r<N, LPB, WL, false, STRIDED>(rtile, lines, tw, l, t, vph);
   }
   cx<float> v[E];
   tile::load_line<E, T, true>(v, d.psi + base, ustride, t, valid);
@@ -160,10 +160,9 @@ __device__ __noinline__ void psi_item(const Inst& d, int full, long long tau, un
   tile::store_line<E, T>(v, d.psi + base, ustride, t, valid);
   if constexpr (VARIANT == PSI_DENSITY) {
     float2* rh = d.rho;
-    tile::density_r2c<N, LPB, WL>(v, valid, lines, tw, l, t, tid, nvalid,
-                                  [&](int k, int ll, cx<float> z) {
-                                    tile::stg_c(rh + (size_t)k * N + line0 + ll, z);
-                                  });
+    auto put = [&](int k, int ll, cx<float> z) { tile::stg_c(rh + (size_t)k * N + line0 + ll, z); };
+    tile::density_r2c<N, LPB, WL, decltype(put), false, STRIDED>(v, valid, lines, tw, l, t, tid,
+                                                                 nvalid, put);
   }
 }
 

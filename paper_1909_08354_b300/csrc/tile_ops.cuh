@@ -109,46 +109,73 @@ __device__ __forceinline__ void store_line(const cx<float> (&v)[E], float2* p, u
 // V h on my line's elements (pattern P) from a staged [k][line] half-spectrum
 // tile: C2R inverse FFT of lines (l, l + LPB/2) packed as A + iB.  On entry the
 // tile is visible to all threads and the line buffers are free.
-template <int N, int LPB, bool WL, bool TC = false>
+// REMAP (strided passes): the thread of (l, t) in the pass's own mapping holds
+// line l at position t spread over all warps, so half of every warp would idle
+// through the packed transform; the transform then runs in the contiguous
+// mapping (line tid / T, position tid % T: whole warps busy, warp-local
+// exchanges) and V reaches the owners through shared memory.
+template <int N, int LPB, bool WL, bool TC = false, bool REMAP = false>
 __device__ __forceinline__ void potential_c2r(const cx<float>* rtile, cx<float>* lines,
                                               const cx<float>* tw, int l, int t,
                                               float (&vph)[Plan<N>::E],
                                               const tc16::Tabs* tb = nullptr) {
   using C = Cfg<N, LPB>;
   constexpr int E = C::E, T = C::T, LS = C::LS, TSTR = C::TSTR, HALF = LPB / 2;
+  constexpr bool WLC = REMAP ? true : WL;  // T <= 32: a contiguous-mapped line is warp-local
+  const int lc = REMAP ? (int)threadIdx.x / T : l;
+  const int tc = REMAP ? (int)threadIdx.x % T : t;
   cx<float> v[E];
-  const bool pa = l < HALF;
+  const bool pa = lc < HALF;
   if (pa) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const int k = t + T * m;
+      const int k = tc + T * m;
       cx<float> A, B;
       if (k <= N / 2) {
-        A = rtile[k * TSTR + l];
-        B = rtile[k * TSTR + l + HALF];
+        A = rtile[k * TSTR + lc];
+        B = rtile[k * TSTR + lc + HALF];
         if (k == 0 || k == N / 2) { A.im = 0.f; B.im = 0.f; }
       } else {
-        A = cconj(rtile[(N - k) * TSTR + l]);
-        B = cconj(rtile[(N - k) * TSTR + l + HALF]);
+        A = cconj(rtile[(N - k) * TSTR + lc]);
+        B = cconj(rtile[(N - k) * TSTR + lc + HALF]);
       }
       v[m] = {A.re - B.im, A.im + B.re};  // A + i B
     }
   }
-  xform<N, +1, WL, TC>(v, lines, tw, tb, l, t, HALF);
-  __syncthreads();
-  if (pa) {
-    float* up = reinterpret_cast<float*>(lines + (l + HALF) * LS);
+  xform<N, +1, WLC, TC>(v, lines, tw, tb, lc, tc, HALF);
+  if constexpr (REMAP) {
+    // the line buffer of lc is read by its own warp only (FP32 engine); the
+    // tensor-core engine shares all buffers across the CTA
+    if constexpr (TC) __syncthreads(); else __syncwarp();
+    if (pa) {
+      float* a = reinterpret_cast<float*>(lines + lc * LS);
+      float* b = reinterpret_cast<float*>(lines + (lc + HALF) * LS);
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      vph[m] = v[m].re;
-      up[t + T * m] = v[m].im;
+      for (int m = 0; m < E; ++m) {
+        a[tc + T * m] = v[m].re;
+        b[tc + T * m] = v[m].im;
+      }
     }
-  }
-  __syncthreads();
-  if (!pa) {
-    const float* up = reinterpret_cast<const float*>(lines + l * LS);
+    __syncthreads();
+    const float* mine = reinterpret_cast<const float*>(lines + l * LS);
 #pragma unroll
-    for (int m = 0; m < E; ++m) vph[m] = up[t + T * m];
+    for (int m = 0; m < E; ++m) vph[m] = mine[t + T * m];
+  } else {
+    __syncthreads();
+    if (pa) {
+      float* up = reinterpret_cast<float*>(lines + (l + HALF) * LS);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        vph[m] = v[m].re;
+        up[t + T * m] = v[m].im;
+      }
+    }
+    __syncthreads();
+    if (!pa) {
+      const float* up = reinterpret_cast<const float*>(lines + l * LS);
+#pragma unroll
+      for (int m = 0; m < E; ++m) vph[m] = up[t + T * m];
+    }
   }
 }
 
@@ -205,7 +232,9 @@ __device__ __forceinline__ void kinetic(cx<float> (&v)[Plan<N>::E], cx<float>* l
 // rho = |psi|^2 of the tile and its R2C FFT along the line (two real lines per
 // complex FFT).  put(k, ll, value) receives half-spectrum entry k of line ll
 // for the valid lines; the calls are spread over all threads with ll fastest.
-template <int N, int LPB, bool WL, class Put, bool TC = false>
+// REMAP: as in potential_c2r, the packed transform runs in the contiguous
+// mapping, fed with |psi|^2 through shared memory.
+template <int N, int LPB, bool WL, class Put, bool TC = false, bool REMAP = false>
 __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], bool valid,
                                             cx<float>* lines, const cx<float>* tw, int l, int t,
                                             int tid, int nvalid, Put put,
@@ -217,24 +246,34 @@ __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], 
   float rho[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) rho[m] = valid ? cnorm2(psi[m]) : 0.f;
-  const bool pa = l < HALF;
+  constexpr bool WLC = REMAP ? true : WL;
+  const int lc = REMAP ? tid / T : l;
+  const int tc = REMAP ? tid % T : t;
+  const bool pc = lc < HALF;  // this thread transforms packed line lc
+  const bool pa = l < HALF;   // my own line l is the real part of packed line l % HALF
   __syncthreads();
-  if (!pa) {
+  if (REMAP || !pa) {
     float* b = reinterpret_cast<float*>(lines + l * LS);
 #pragma unroll
     for (int m = 0; m < E; ++m) b[t + T * m] = rho[m];
   }
   __syncthreads();
-  if (pa) {
-    const float* b = reinterpret_cast<const float*>(lines + (l + HALF) * LS);
+  if (pc) {
+    const float* bb = reinterpret_cast<const float*>(lines + (lc + HALF) * LS);
+    if constexpr (REMAP) {
+      const float* ba = reinterpret_cast<const float*>(lines + lc * LS);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = {rho[m], b[t + T * m]};
+      for (int m = 0; m < E; ++m) v[m] = {ba[tc + T * m], bb[tc + T * m]};
+    } else {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = {rho[m], bb[tc + T * m]};
+    }
   }
-  xform<N, -1, WL, TC>(v, lines, tw, tb, l, t, HALF);
+  xform<N, -1, WLC, TC>(v, lines, tw, tb, lc, tc, HALF);
   __syncthreads();
-  if (pa) {
+  if (pc) {
 #pragma unroll
-    for (int q = 0; q < E; ++q) lines[l * LS + pidx<N>(t + T * q)] = v[q];
+    for (int q = 0; q < E; ++q) lines[lc * LS + pidx<N>(tc + T * q)] = v[q];
   }
   __syncthreads();
   constexpr int NH = (H + T - 1) / T;
