@@ -46,6 +46,7 @@ struct sn_fno_s {
   float *GU = nullptr, *GV = nullptr, *work = nullptr;
   std::vector<float*> v, z, Vh;
   double* norms = nullptr;  // per sample (||out - t||^2, ||t||^2)
+  double* chan_part = nullptr;  // channel-sum partials [max channels][kChanParts]
   int lastB = 0;
   ll work_floats = 0;
   std::vector<void*> allocs;
@@ -87,23 +88,53 @@ __device__ __forceinline__ float gelu_grad(float x) {
          x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }
 
+// bias_act over rows of P values: about 8 blocks per row, at least one
+inline dim3 rows_grid(ll rows, ll P) {
+  const ll per = std::max<ll>(1, std::min<ll>(8, (P + 1023) / 1024));
+  return dim3((unsigned)per, (unsigned)rows);
+}
+
 inline unsigned blocks_for(ll n) {
   const ll b = (n + 255) / 256;
   return (unsigned)(b < 8192 ? b : 8192);
 }
 
-// z[b][c][p] += bias[c]; v = gelu(z) (act) or z
-__global__ void bias_act_kernel(float* z, const float* bias, float* v, ll C, ll P, ll n, int act) {
-  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
-    const ll c = (i / P) % C;
-    const float x = z[i] + bias[c];
-    z[i] = x;
-    if (v != nullptr) v[i] = act ? gelu(x) : x;
+// z[b][c][p] += bias[c]; v = gelu(z) (act) or z.  Block (x, r) covers a span of
+// row r = b C + c (P contiguous values), four values per thread step.
+__global__ void bias_act_kernel(float* z, const float* bias, float* v, ll C, ll P, int act) {
+  const ll r = blockIdx.y;
+  const float bc = bias[r % C];
+  float* zr = z + r * P;
+  float* vr = v != nullptr ? v + r * P : nullptr;
+  const ll span = (P + gridDim.x - 1) / gridDim.x;
+  const ll p0 = blockIdx.x * span, p1 = min(P, p0 + span);
+  if ((P & 3) == 0 && (span & 3) == 0) {
+    for (ll p = p0 + 4 * threadIdx.x; p < p1; p += 4 * blockDim.x) {
+      float4 x = *reinterpret_cast<float4*>(zr + p);
+      x.x += bc; x.y += bc; x.z += bc; x.w += bc;
+      *reinterpret_cast<float4*>(zr + p) = x;
+      if (vr != nullptr) {
+        if (act) x = make_float4(gelu(x.x), gelu(x.y), gelu(x.z), gelu(x.w));
+        *reinterpret_cast<float4*>(vr + p) = x;
+      }
+    }
+  } else {
+    for (ll p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      const float x = zr[p] + bc;
+      zr[p] = x;
+      if (vr != nullptr) vr[p] = act ? gelu(x) : x;
+    }
   }
 }
 
 __global__ void gelu_bwd_kernel(const float* dv, const float* z, float* dz, ll n) {
-  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x)
+  const ll n4 = n / 4;
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n4; i += (ll)gridDim.x * blockDim.x) {
+    const float4 d = reinterpret_cast<const float4*>(dv)[i], x = reinterpret_cast<const float4*>(z)[i];
+    reinterpret_cast<float4*>(dz)[i] =
+        make_float4(d.x * gelu_grad(x.x), d.y * gelu_grad(x.y), d.z * gelu_grad(x.z), d.w * gelu_grad(x.w));
+  }
+  for (ll i = 4 * n4 + blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x)
     dz[i] = dv[i] * gelu_grad(z[i]);
 }
 
@@ -136,12 +167,20 @@ __global__ void head_bwd_kernel(const float* a, const float* y, const float* dou
   }
 }
 
-// out[c] (+)= sum_b sum_p X[b][c][p]; one block per channel, fixed order
-__global__ void channel_sum_kernel(const float* X, ll B, ll C, ll P, float* out) {
+// out[c] = sum_b sum_p X[b][c][p] in a fixed order: block (c, j) sums span j of
+// every row of channel c into part[c][j] (FP64), then one thread per channel
+// adds its parts.
+constexpr int kChanParts = 64;
+__global__ void channel_part_kernel(const float* X, ll B, ll C, ll P, double* part) {
   const ll c = blockIdx.x;
+  const int j = blockIdx.y;
+  const ll span = (P + kChanParts - 1) / kChanParts;
+  const ll p0 = j * span, p1 = min(P, p0 + span);
   double s = 0.0;
-  for (ll b = 0; b < B; ++b)
-    for (ll p = threadIdx.x; p < P; p += blockDim.x) s += X[(b * C + c) * P + p];
+  for (ll b = 0; b < B; ++b) {
+    const float* row = X + (b * C + c) * P;
+    for (ll p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += row[p];
+  }
   __shared__ double red[256];
   red[threadIdx.x] = s;
   __syncthreads();
@@ -149,7 +188,14 @@ __global__ void channel_sum_kernel(const float* X, ll B, ll C, ll P, float* out)
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[c] = (float)red[0];
+  if (threadIdx.x == 0) part[c * kChanParts + j] = red[0];
+}
+__global__ void channel_final_kernel(const double* part, ll C, float* out) {
+  const ll c = blockIdx.x * (ll)blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double s = 0.0;
+  for (int j = 0; j < kChanParts; ++j) s += part[c * kChanParts + j];
+  out[c] = (float)s;
 }
 
 // per sample b: norms[2b] = ||out_b - t_b||^2, norms[2b+1] = ||t_b||^2 (one block per sample)
@@ -253,8 +299,19 @@ cudaError_t gemm(sn_fno f, int M, int N, int K, int Z, const float* A, ll sAz, l
 }
 
 // dW (M x N, row-major) = sum_b dY[b] (M x P) X[b]^T (X[b] is N x P), split over K
+// out[c] = sum over samples and pixels of X[b][c][p] (bias gradients)
+cudaError_t channel_sum(sn_fno f, const float* X, ll B, ll C, ll P, float* out) {
+  channel_part_kernel<<<dim3((unsigned)C, kChanParts), 256, 0, f->stream>>>(X, B, C, P, f->chan_part);
+  channel_final_kernel<<<(unsigned)((C + 127) / 128), 128, 0, f->stream>>>(f->chan_part, C, out);
+  return cudaGetLastError();
+}
+
+// Split-K width of the weight-gradient GEMMs (K = pixels): narrow enough that
+// B x (P / kWgChunk) blocks fill the GPU.
+constexpr int kWgChunk = 1024;
+
 cudaError_t weight_grad(sn_fno f, const float* dY, const float* X, int B, int M, int N, float* dW) {
-  const int kchunk = 8192;
+  const int kchunk = kWgChunk;
   const int nsplit = (int)((f->P + kchunk - 1) / kchunk);
   GemmArgs g{};
   g.A = dY; g.sAz = (ll)M * f->P; g.sAm = f->P; g.sAk = 1;
@@ -461,7 +518,8 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
   ok = ok && falloc(f, &f->dv2, plane) == cudaSuccess;
   ok = ok && falloc(f, &f->dz, plane) == cudaSuccess;
   ok = ok && falloc(f, &f->norms, 2 * B) == cudaSuccess;
-  const ll nsplit = (P + 8191) / 8192;
+  ok = ok && falloc(f, &f->chan_part, kChanParts * (size_t)std::max<ll>(proj, width)) == cudaSuccess;
+  const ll nsplit = (P + kWgChunk - 1) / kWgChunk;
   const ll mn = std::max<ll>((ll)proj * C, std::max<ll>(C * C, C * (ll)c_in));
   f->work_floats = B * nsplit * std::max<ll>(mn, 3LL * proj);
   ok = ok && falloc(f, &f->work, f->work_floats) == cudaSuccess;
@@ -507,23 +565,23 @@ sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
   FCHK(cudaMemcpyAsync(f->a, in, (size_t)B * ci * P * sizeof(float), cudaMemcpyDeviceToDevice, st));
   // lift
   FCHK(gemm(f, (int)C, (int)P, (int)ci, B, prm + f->off_P, 0, ci, 1, f->a, ci * P, P, 1, f->v[0], C * P, P, 1));
-  bias_act_kernel<<<blocks_for(B * C * P), 256, 0, st>>>(f->v[0], prm + f->off_pb, nullptr, C, P, B * C * P, 0);
+  bias_act_kernel<<<rows_grid(B * C, P), 256, 0, st>>>(f->v[0], prm + f->off_pb, nullptr, C, P, 0);
   FCHK(cudaGetLastError());
   for (int l = 0; l < f->L; ++l) {
     FCHK(dft_forward(f, f->v[l], B, (int)C, f->ExF, f->Vh[l]));
     FCHK(mode_mix(f, f->Vh[l], prm + f->off_R[l], B, f->Uh));
     FCHK(dft_inverse(f, f->Uh, B, (int)C, f->WxI, f->z[l], 0.f));
     FCHK(gemm(f, (int)C, (int)P, (int)C, B, prm + f->off_W[l], 0, C, 1, f->v[l], C * P, P, 1, f->z[l], C * P, P, 1, 1.f, 1.f));
-    bias_act_kernel<<<blocks_for(B * C * P), 256, 0, st>>>(f->z[l], prm + f->off_b[l], f->v[l + 1], C, P, B * C * P,
+    bias_act_kernel<<<rows_grid(B * C, P), 256, 0, st>>>(f->z[l], prm + f->off_b[l], f->v[l + 1], C, P,
                                                           l < f->L - 1 ? 1 : 0);
     FCHK(cudaGetLastError());
   }
   // projection
   FCHK(gemm(f, (int)J, (int)P, (int)C, B, prm + f->off_Q1, 0, C, 1, f->v[f->L], C * P, P, 1, f->g1, J * P, P, 1));
-  bias_act_kernel<<<blocks_for(B * J * P), 256, 0, st>>>(f->g1, prm + f->off_q1b, f->h, J, P, B * J * P, 1);
+  bias_act_kernel<<<rows_grid(B * J, P), 256, 0, st>>>(f->g1, prm + f->off_q1b, f->h, J, P, 1);
   FCHK(cudaGetLastError());
   FCHK(gemm(f, 3, (int)P, (int)J, B, prm + f->off_Q2, 0, J, 1, f->h, J * P, P, 1, f->yh, 3 * P, P, 1));
-  bias_act_kernel<<<blocks_for(B * 3 * P), 256, 0, st>>>(f->yh, prm + f->off_q2b, nullptr, 3, P, B * 3 * P, 0);
+  bias_act_kernel<<<rows_grid(B * 3, P), 256, 0, st>>>(f->yh, prm + f->off_q2b, nullptr, 3, P, 0);
   head_kernel<<<blocks_for(B * P), 256, 0, st>>>(f->a, f->yh, f->out, ci, P, B * P);
   FCHK(cudaGetLastError());
   if (out != f->out)
@@ -559,12 +617,12 @@ sn_status sn_fno_backward(sn_fno f) {
   head_bwd_kernel<<<blocks_for(B * P), 256, 0, st>>>(f->a, f->yh, f->dout, f->dy, ci, P, B * P);
   FCHK(cudaGetLastError());
   FCHK(weight_grad(f, f->dy, f->h, B, 3, (int)J, gr + f->off_Q2));
-  channel_sum_kernel<<<3, 256, 0, st>>>(f->dy, B, 3, P, gr + f->off_q2b);
+  channel_sum(f, f->dy, B, 3, P, gr + f->off_q2b);
   FCHK(gemm(f, (int)J, (int)P, 3, B, prm + f->off_Q2, 0, 1, J, f->dy, 3 * P, P, 1, f->dh, J * P, P, 1));
   gelu_bwd_kernel<<<blocks_for(B * J * P), 256, 0, st>>>(f->dh, f->g1, f->dh, B * J * P);
   FCHK(cudaGetLastError());
   FCHK(weight_grad(f, f->dh, f->v[f->L], B, (int)J, (int)C, gr + f->off_Q1));
-  channel_sum_kernel<<<(unsigned)J, 256, 0, st>>>(f->dh, B, J, P, gr + f->off_q1b);
+  channel_sum(f, f->dh, B, J, P, gr + f->off_q1b);
   FCHK(gemm(f, (int)C, (int)P, (int)J, B, prm + f->off_Q1, 0, 1, C, f->dh, J * P, P, 1, f->dv, C * P, P, 1));
   for (int l = f->L - 1; l >= 0; --l) {
     const float* dz = f->dv;
@@ -574,7 +632,7 @@ sn_status sn_fno_backward(sn_fno f) {
       dz = f->dz;
     }
     FCHK(weight_grad(f, dz, f->v[l], B, (int)C, (int)C, gr + f->off_W[l]));
-    channel_sum_kernel<<<(unsigned)C, 256, 0, st>>>(dz, B, C, P, gr + f->off_b[l]);
+    channel_sum(f, dz, B, C, P, gr + f->off_b[l]);
     FCHK(gemm(f, (int)C, (int)P, (int)C, B, prm + f->off_W[l], 0, 1, C, dz, C * P, P, 1, f->dv2, C * P, P, 1));
     // spectral branch
     FCHK(dft_forward(f, dz, B, (int)C, f->ExFw, f->GU));
@@ -583,7 +641,7 @@ sn_status sn_fno_backward(sn_fno f) {
     std::swap(f->dv, f->dv2);
   }
   FCHK(weight_grad(f, f->dv, f->a, B, (int)C, (int)ci, gr + f->off_P));
-  channel_sum_kernel<<<(unsigned)C, 256, 0, st>>>(f->dv, B, C, P, gr + f->off_pb);
+  channel_sum(f, f->dv, B, C, P, gr + f->off_pb);
   FCHK(cudaGetLastError());
   return SN_OK;
 }
