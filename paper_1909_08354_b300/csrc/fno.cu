@@ -13,6 +13,7 @@
 // cos/sin matrix, along y per plane with a 4m x s block matrix.  Mode mixing
 // is a batch of Nm complex C x C GEMMs written as four real ones.
 // Activations are planar [B][C][s][s] FP32; modes are [B][C][re|im][Nm].
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -176,11 +177,14 @@ __global__ void channel_part_kernel(const float* X, ll B, ll C, ll P, double* pa
   const int j = blockIdx.y;
   const ll span = (P + kChanParts - 1) / kChanParts;
   const ll p0 = j * span, p1 = min(P, p0 + span);
-  double s = 0.0;
+  // per-thread sums in FP32 (at most a few hundred terms; FP64 adds are slow
+  // on this GPU), combined across the block in FP64
+  float sf = 0.f;
   for (ll b = 0; b < B; ++b) {
     const float* row = X + (b * C + c) * P;
-    for (ll p = p0 + threadIdx.x; p < p1; p += blockDim.x) s += row[p];
+    for (ll p = p0 + threadIdx.x; p < p1; p += blockDim.x) sf += row[p];
   }
+  const double s = sf;
   __shared__ double red[256];
   red[threadIdx.x] = s;
   __syncthreads();
@@ -284,6 +288,88 @@ __global__ void mass_kernel(const float2* psi, ll P, double* out) {
   if (threadIdx.x == 0) out[b] = red[0];
 }
 
+// ---- per-mode complex channel mixing ---------------------------------------
+// U[b][o](mode) = sum_i V[b][i](mode) R[mode][i][o], complex, with the planar
+// layout X[b][c][re/im][mode] of V and U and R[mode][i][o][re/im].  One block
+// per mode; V, R and (backward) GU are rounded to BF16 on load like the GEMM
+// operands, products accumulate in FP32.
+__device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__global__ void mode_mix_kernel(const float* V, const float* R, float* U, int B, int C, ll Nm) {
+  extern __shared__ float mm_sm[];
+  float2* Vs = reinterpret_cast<float2*>(mm_sm);  // [B][C]
+  const ll mode = blockIdx.x;
+  const ll is = 2 * Nm, bs = (ll)C * is;
+  for (int e = threadIdx.x; e < B * C; e += blockDim.x) {
+    const int b = e / C, i = e % C;
+    const float* v = V + b * bs + i * is + mode;
+    Vs[e] = make_float2(bf(v[0]), bf(v[Nm]));
+  }
+  __syncthreads();
+  const float2* Rm = reinterpret_cast<const float2*>(R) + mode * (ll)C * C;
+  for (int e = threadIdx.x; e < B * C; e += blockDim.x) {
+    const int b = e / C, o = e % C;
+    float ar = 0.f, ai = 0.f;
+    for (int i = 0; i < C; ++i) {
+      const float2 x = Vs[b * C + i];
+      const float2 r = Rm[i * C + o];
+      const float rr = bf(r.x), ri = bf(r.y);
+      ar = fmaf(x.x, rr, fmaf(-x.y, ri, ar));
+      ai = fmaf(x.x, ri, fmaf(x.y, rr, ai));
+    }
+    float* u = U + b * bs + o * is + mode;
+    u[0] = ar;
+    u[Nm] = ai;
+  }
+}
+
+// GR[mode][i][o] = sum_b conj(V[b][i]) GU[b][o];  GV[b][i] = sum_o conj(R[i][o]) GU[b][o]
+__global__ void mode_mix_bwd_kernel(const float* V, const float* R, const float* GU, float* GR,
+                                    float* GV, int B, int C, ll Nm) {
+  extern __shared__ float mm_sm[];
+  float2* Vs = reinterpret_cast<float2*>(mm_sm);  // [B][C]
+  float2* Gs = Vs + B * C;                         // [B][C]
+  float2* Rs = Gs + B * C;                         // [C][C]
+  const ll mode = blockIdx.x;
+  const ll is = 2 * Nm, bs = (ll)C * is;
+  for (int e = threadIdx.x; e < B * C; e += blockDim.x) {
+    const int b = e / C, i = e % C;
+    const float* v = V + b * bs + i * is + mode;
+    const float* g = GU + b * bs + i * is + mode;
+    Vs[e] = make_float2(bf(v[0]), bf(v[Nm]));
+    Gs[e] = make_float2(bf(g[0]), bf(g[Nm]));
+  }
+  const float2* Rm = reinterpret_cast<const float2*>(R) + mode * (ll)C * C;
+  for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+    const float2 r = Rm[e];
+    Rs[e] = make_float2(bf(r.x), bf(r.y));
+  }
+  __syncthreads();
+  float2* GRm = reinterpret_cast<float2*>(GR) + mode * (ll)C * C;
+  for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+    const int i = e / C, o = e % C;
+    float ar = 0.f, ai = 0.f;
+    for (int b = 0; b < B; ++b) {
+      const float2 x = Vs[b * C + i], g = Gs[b * C + o];
+      ar = fmaf(x.x, g.x, fmaf(x.y, g.y, ar));   // conj(x) g
+      ai = fmaf(x.x, g.y, fmaf(-x.y, g.x, ai));
+    }
+    GRm[e] = make_float2(ar, ai);
+  }
+  for (int e = threadIdx.x; e < B * C; e += blockDim.x) {
+    const int b = e / C, i = e % C;
+    float ar = 0.f, ai = 0.f;
+    for (int o = 0; o < C; ++o) {
+      const float2 r = Rs[i * C + o], g = Gs[b * C + o];
+      ar = fmaf(r.x, g.x, fmaf(r.y, g.y, ar));   // conj(r) g
+      ai = fmaf(r.x, g.y, fmaf(-r.y, g.x, ai));
+    }
+    float* gv = GV + b * bs + i * is + mode;
+    gv[0] = ar;
+    gv[Nm] = ai;
+  }
+}
+
 // ---- GEMM plumbing --------------------------------------------------------------
 
 cudaError_t gemm(sn_fno f, int M, int N, int K, int Z, const float* A, ll sAz, ll sAm, ll sAk,
@@ -359,36 +445,17 @@ cudaError_t dft_inverse(sn_fno f, const float* U, int B, int Cn, const float* Wx
 
 // U[b][o] = sum_i R[mode][i][o] V[b][i] per mode (complex), four real GEMMs
 cudaError_t mode_mix(sn_fno f, const float* V, const float* R, int B, float* U) {
-  const int C = f->C;
-  const ll Nm = f->Nm, bs = (ll)C * 2 * Nm, is = 2 * Nm, Rz = 2LL * C * C;
-  const float* Vre = V;
-  const float* Vim = V + Nm;
-  float* Ure = U;
-  float* Uim = U + Nm;
-  cudaError_t e;
-  // Ure = Vre Rre - Vim Rim ; Uim = Vre Rim + Vim Rre
-  if ((e = gemm(f, B, C, C, (int)Nm, Vre, 1, bs, is, R, Rz, 2 * C, 2, Ure, 1, bs, is)) != cudaSuccess) return e;
-  if ((e = gemm(f, B, C, C, (int)Nm, Vim, 1, bs, is, R + 1, Rz, 2 * C, 2, Ure, 1, bs, is, -1.f, 1.f)) != cudaSuccess) return e;
-  if ((e = gemm(f, B, C, C, (int)Nm, Vre, 1, bs, is, R + 1, Rz, 2 * C, 2, Uim, 1, bs, is)) != cudaSuccess) return e;
-  return gemm(f, B, C, C, (int)Nm, Vim, 1, bs, is, R, Rz, 2 * C, 2, Uim, 1, bs, is, 1.f, 1.f);
+  const size_t sm = sizeof(float2) * (size_t)B * f->C;
+  mode_mix_kernel<<<(unsigned)f->Nm, 256, sm, f->stream>>>(V, R, U, B, f->C, f->Nm);
+  return cudaGetLastError();
 }
 
 // backward of mode_mix: GR[mode][i][o] = sum_b conj(V_i) GU_o ; GV[b][i] = sum_o conj(R_io) GU_o
 cudaError_t mode_mix_bwd(sn_fno f, const float* V, const float* R, const float* GU, int B, float* GR,
                          float* GV) {
-  const int C = f->C;
-  const ll Nm = f->Nm, bs = (ll)C * 2 * Nm, is = 2 * Nm, Rz = 2LL * C * C;
-  cudaError_t e;
-  // GRre = Vre^T GUre + Vim^T GUim ; GRim = Vre^T GUim - Vim^T GUre   (A: (i, b), B: (b, o))
-  if ((e = gemm(f, C, C, B, (int)Nm, V, 1, is, bs, GU, 1, bs, is, GR, Rz, 2 * C, 2)) != cudaSuccess) return e;
-  if ((e = gemm(f, C, C, B, (int)Nm, V + Nm, 1, is, bs, GU + Nm, 1, bs, is, GR, Rz, 2 * C, 2, 1.f, 1.f)) != cudaSuccess) return e;
-  if ((e = gemm(f, C, C, B, (int)Nm, V, 1, is, bs, GU + Nm, 1, bs, is, GR + 1, Rz, 2 * C, 2)) != cudaSuccess) return e;
-  if ((e = gemm(f, C, C, B, (int)Nm, V + Nm, 1, is, bs, GU, 1, bs, is, GR + 1, Rz, 2 * C, 2, -1.f, 1.f)) != cudaSuccess) return e;
-  // GVre = GUre Rre^T + GUim Rim^T ; GVim = GUim Rre^T - GUre Rim^T   (A: (b, o), B: (o, i))
-  if ((e = gemm(f, B, C, C, (int)Nm, GU, 1, bs, is, R, Rz, 2, 2 * C, GV, 1, bs, is)) != cudaSuccess) return e;
-  if ((e = gemm(f, B, C, C, (int)Nm, GU + Nm, 1, bs, is, R + 1, Rz, 2, 2 * C, GV, 1, bs, is, 1.f, 1.f)) != cudaSuccess) return e;
-  if ((e = gemm(f, B, C, C, (int)Nm, GU + Nm, 1, bs, is, R, Rz, 2, 2 * C, GV + Nm, 1, bs, is)) != cudaSuccess) return e;
-  return gemm(f, B, C, C, (int)Nm, GU, 1, bs, is, R + 1, Rz, 2, 2 * C, GV + Nm, 1, bs, is, -1.f, 1.f);
+  const size_t sm = sizeof(float2) * (2 * (size_t)B * f->C + (size_t)f->C * f->C);
+  mode_mix_bwd_kernel<<<(unsigned)f->Nm, 256, sm, f->stream>>>(V, R, GU, GR, GV, B, f->C, f->Nm);
+  return cudaGetLastError();
 }
 
 std::vector<float> dft_matrix(int kind, int s, int m) {
@@ -523,6 +590,16 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
   const ll mn = std::max<ll>((ll)proj * C, std::max<ll>(C * C, C * (ll)c_in));
   f->work_floats = B * nsplit * std::max<ll>(mn, 3LL * proj);
   ok = ok && falloc(f, &f->work, f->work_floats) == cudaSuccess;
+  {
+    // per-mode mixing keeps V, GU (B x C) and R (C x C) of one mode in shared memory
+    const size_t sm_fwd = sizeof(float2) * (size_t)B * C;
+    const size_t sm_bwd = sizeof(float2) * (2 * (size_t)B * C + (size_t)C * C);
+    if (sm_bwd > 200 * 1024) return bail(ffail(SN_ENOTSUP, "sn_fno_create: batch_max * width too large"));
+    ok = ok && cudaFuncSetAttribute(mode_mix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm_fwd) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(mode_mix_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm_bwd) == cudaSuccess;
+  }
   if (!ok) return bail(ffail(SN_ENOMEM, "sn_fno_create: device allocation failed"));
   *out = f;
   return SN_OK;
