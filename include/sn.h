@@ -204,7 +204,7 @@ void sn_destroy_batch(sn_batch b);
 /* ---------------------------------------------------------------------------
  * Fourier-neural-operator surrogate of the solver: predicts the 2D state 50
  * steps ahead from the state and the kernel parameters given as constant
- * input channels; the plain split step is its fallback and judge.
+ * input channels; the plain split step is its fallback and its reference.
  *   v0 = P a + pb;  z_l = Spec_l(v_l) + W_l v_l + b_l,  v_{l+1} = gelu(z_l)
  *   (no gelu after the last layer);  Spec(v) keeps the modes
  *   ky in {0..m-1} u {s-m..s-1}, kx in {0..m-1}:

@@ -7,7 +7,7 @@
   sn_fno_forward / sn_fno_loss / sn_fno_backward / sn_fno_adam.
 * Rollout: psi is advanced `stride` steps per network call; a prediction
   whose mass differs from its input's by more than `drift_tol` is replaced by
-  `stride` solver steps (the solver is the fallback and the judge).
+  `stride` solver steps (the solver is both the fallback and the reference).
 
 Device memory comes from torch tensors; every computation is a library call.
 Every call is queued on torch's current CUDA stream, which must be a
