@@ -316,7 +316,9 @@ rho_pass_kernel(RhoPassArgs a) {
 // number of tiles.
 template <typename K>
 unsigned persistent_ctas(K kern, int threads, size_t smem, long long ntiles) {
-  static int sms = 0;
+  static int sms_of[kDeviceSlots] = {};
+  const int slot = device_slot();
+  int& sms = sms_of[slot];
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -341,7 +343,8 @@ cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
   constexpr size_t smem = psi_smem_bytes<N, VARIANT, TC>();
   constexpr int threads = cta_threads<N>();
   auto kern = psi_pass_kernel<N, STRIDED, VARIANT, TC>;
-  static bool attr = false;
+  static bool attr_of[kDeviceSlots] = {};
+  bool& attr = attr_of[device_slot()];
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -357,7 +360,8 @@ cudaError_t launch_rho_t(const RhoPassArgs& a, cudaStream_t s) {
   constexpr size_t smem = rho_smem_bytes<N, TC>();
   constexpr int threads = cta_threads<N>();
   auto kern = rho_pass_kernel<N, STRIDED, OP, TC>;
-  static bool attr = false;
+  static bool attr_of[kDeviceSlots] = {};
+  bool& attr = attr_of[device_slot()];
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

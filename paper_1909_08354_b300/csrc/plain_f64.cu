@@ -75,7 +75,8 @@ cudaError_t launch_fft_t(double2* d, long long outer, long long inner, const dou
   constexpr int LPB = LinesF64<N>::value;
   constexpr size_t smem = (size_t)(Plan<N>::TWN + LPB * Plan<N>::LS) * sizeof(cx<double>);
   auto kern = fft_f64_kernel<N, STRIDED, SIGN>;
-  static bool attr = false;
+  static bool attr_of[kDeviceSlots] = {};
+  bool& attr = attr_of[device_slot()];
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

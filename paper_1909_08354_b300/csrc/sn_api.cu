@@ -92,6 +92,12 @@ struct Launch {
 
 void sn::set_thread_error(const char* msg) { g_tls_error = msg; }
 
+int sn::device_slot() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  return dev < kDeviceSlots ? dev : kDeviceSlots - 1;
+}
+
 void sn::kinetic_lift_table(int n, double L, double A, double tau, float* out4) {
   for (int j = 0; j < n; ++j) {
     const double k = wavenumber(j, n, L);

@@ -56,6 +56,11 @@ struct RhoPassArgs {
 // Message returned by sn_last_error(NULL) on this thread.
 void set_thread_error(const char* msg);
 
+// Per-device once-only settings (kernel attributes, SM counts) are kept in
+// arrays indexed by the current device, clamped to [0, kDeviceSlots).
+constexpr int kDeviceSlots = 64;
+int device_slot();
+
 enum PsiVariant { PSI_PLAIN = 0, PSI_NPHASE = 1, PSI_DENSITY = 2 };
 enum RhoOp { RHO_FWD = 0, RHO_GREEN = 1, RHO_INV = 2 };
 
