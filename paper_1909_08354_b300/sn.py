@@ -396,23 +396,44 @@ class Fno:
             pass
 
 
+def _cuda_tensor(t, dtype, name, numel=None):
+    """Check a CUDA tensor before its pointer crosses the C-ABI (the library
+    cannot check sizes behind a plain pointer)."""
+    if not (_is_torch(t) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, {numel} needed")
+    return t.data_ptr()
+
+
 def sn_fno_pack(psi, feats, X, stream=None):
     """psi: (B, s, s) complex64 CUDA; feats: (B, nfeat) float32 CUDA; X: (B, 2+nfeat, s, s)."""
-    B = psi.shape[0]
-    _check(None, lib().sn_fno_pack(psi.data_ptr(), feats.data_ptr() if feats is not None else None,
-                                   feats.shape[1] if feats is not None else 0, X.data_ptr(), B,
-                                   psi[0].numel(), ctypes.c_void_p(stream) if stream else None))
+    import torch
+    B, cells = psi.shape[0], psi[0].numel()
+    nfeat = feats.shape[1] if feats is not None else 0
+    pp = _cuda_tensor(psi, torch.complex64, "psi")
+    fp = _cuda_tensor(feats, torch.float32, "feats", B * nfeat) if feats is not None else None
+    xp = _cuda_tensor(X, torch.float32, "X", B * (2 + nfeat) * cells)
+    _check(None, lib().sn_fno_pack(pp, fp, nfeat, xp, B, cells,
+                                   ctypes.c_void_p(stream) if stream else None))
 
 
 def sn_fno_unpack(Y, psi, stream=None):
-    _check(None, lib().sn_fno_unpack(Y.data_ptr(), psi.data_ptr(), psi.shape[0], psi[0].numel(),
-                                     ctypes.c_void_p(stream) if stream else None))
+    """Y: (B, 2, s, s) float32 CUDA -> psi: (B, s, s) complex64 CUDA."""
+    import torch
+    B, cells = psi.shape[0], psi[0].numel()
+    pp = _cuda_tensor(psi, torch.complex64, "psi")
+    yp = _cuda_tensor(Y, torch.float32, "Y", B * 2 * cells)
+    _check(None, lib().sn_fno_unpack(yp, pp, B, cells, ctypes.c_void_p(stream) if stream else None))
 
 
 def sn_mass_c64(psi, out, stream=None):
     """out: (B,) float64 CUDA tensor receiving sum |psi_b|^2."""
-    _check(None, lib().sn_mass_c64(psi.data_ptr(), psi.shape[0], psi[0].numel(), out.data_ptr(),
-                                   ctypes.c_void_p(stream) if stream else None))
+    import torch
+    B, cells = psi.shape[0], psi[0].numel()
+    pp = _cuda_tensor(psi, torch.complex64, "psi")
+    op = _cuda_tensor(out, torch.float64, "out", B)
+    _check(None, lib().sn_mass_c64(pp, B, cells, op, ctypes.c_void_p(stream) if stream else None))
 
 
 def sn_test_line_fft_f32(data, n: int, sign: int, engine: int = SN_ENGINE_FP32, stream=None):
@@ -428,8 +449,15 @@ def sn_test_line_fft_f32(data, n: int, sign: int, engine: int = SN_ENGINE_FP32, 
 
 def sn_test_gemm_bf16(A, sA, B, sB, C, sC, M, N, K, Z, alpha=1.0, beta=0.0):
     """Test hook: strided batched BF16 GEMM on CUDA float32 tensors; s* = (sz, s_row, s_col)."""
-    _check(None, lib().sn_test_gemm_bf16(A.data_ptr(), *sA, B.data_ptr(), *sB, C.data_ptr(), *sC,
-                                         M, N, K, Z, alpha, beta))
+    import torch
+
+    def extent(s, rows, cols):  # one past the largest element offset the GEMM touches
+        return (Z - 1) * s[0] + (rows - 1) * s[1] + (cols - 1) * s[2] + 1
+
+    ap = _cuda_tensor(A, torch.float32, "A", extent(sA, M, K))
+    bp = _cuda_tensor(B, torch.float32, "B", extent(sB, K, N))
+    cp = _cuda_tensor(C, torch.float32, "C", extent(sC, M, N))
+    _check(None, lib().sn_test_gemm_bf16(ap, *sA, bp, *sB, cp, *sC, M, N, K, Z, alpha, beta))
 
 
 class Batch:
