@@ -62,26 +62,13 @@ __device__ __forceinline__ cx<R> mul_si(cx<R> a) {
   else return {-a.im, a.re};
 }
 
-// a * exp(SIGN * i * theta) with (c, s) = (cos theta, sin theta) given in FP64.
-// In FP32 the constant is carried as a hi + lo pair of floats, so the factor is
-// unimodular to ~1e-15: a single rounded float pair has |w|^2 - 1 of order
-// 1e-8 with a fixed sign (e.g. 2 fl(sqrt(1/2))^2 = 1 - 3.4e-8), which would
-// shrink the norm by the same amount on every butterfly.  Only the products
-// are rounded, and those errors are unbiased.
+// a * exp(SIGN * i * theta) with (c, s) = (cos theta, sin theta): the FP64
+// engine's constant rotations (the FP32 engine uses rot8 and rot16).
 template <typename R, int SIGN>
 __device__ __forceinline__ cx<R> rot(cx<R> a, double c, double s) {
-  if constexpr (sizeof(R) == sizeof(float)) {
-    const double ss = SIGN < 0 ? -s : s;
-    const float ch = (float)c, sh = (float)ss;
-    const float cl = (float)(c - (double)ch), sl = (float)(ss - (double)sh);
-    const float ur = a.re * cl - a.im * sl;
-    const float ui = a.re * sl + a.im * cl;
-    return {fmaf(a.re, ch, fmaf(-a.im, sh, ur)), fmaf(a.re, sh, fmaf(a.im, ch, ui))};
-  } else {
-    const R cc = (R)c;
-    const R ss = (R)(SIGN < 0 ? -s : s);
-    return {a.re * cc - a.im * ss, a.re * ss + a.im * cc};
-  }
+  const R cc = (R)c;
+  const R ss = (R)(SIGN < 0 ? -s : s);
+  return {a.re * cc - a.im * ss, a.re * ss + a.im * cc};
 }
 
 // a * exp(SIGN i pi/4) (Q = 1) or a * exp(SIGN i 3pi/4) (Q = 3).  The factor is
