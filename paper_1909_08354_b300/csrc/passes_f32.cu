@@ -170,16 +170,16 @@ psi_pass_kernel(PsiPassArgs a) {
     const bool valid = l < nvalid;
     const long long taun = tau + gridDim.x;
     cx<float> v[E];
-    float vph[E];
-    (void)vph;
+    const float* vrow = nullptr;
+    (void)vrow;
 
     if constexpr (NPHASE) {
       if (taun < tiles.count) stage_rho(rstage + ((it + 1) & 1) * (H * TSTR), taun);
       cp_async_commit();
       cp_async_wait<1>();
       __syncthreads();
-      tile::potential_c2r<N, LPB, WL, TC, STRIDED>(rstage + (it & 1) * (H * TSTR), lines, tw_sm,
-                                                   l, t, vph, tabs);
+      vrow = tile::potential_c2r<N, LPB, WL, TC, STRIDED>(rstage + (it & 1) * (H * TSTR), lines,
+                                                          tw_sm, l, t, tabs);
     }
 
     // ---- this tile's psi (loaded one iteration ago); start the next tile's load
@@ -198,7 +198,7 @@ psi_pass_kernel(PsiPassArgs a) {
     }
 
     if constexpr (NPHASE) {
-      tile::nonlinear_phase<E, T>(v, vph, a.gh, a.vext != nullptr ? a.vext + base : nullptr, a.h,
+      tile::nonlinear_phase<E, T>(v, vrow, a.gh, a.vext != nullptr ? a.vext + base : nullptr, a.h,
                                   ustride, t, valid);
     }
     if constexpr (TC) {

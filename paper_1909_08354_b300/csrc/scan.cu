@@ -82,11 +82,15 @@ struct Inst {
   unsigned t_psi, t_rho;  // tiles per psi pass and per Green's pass
 };
 
+// One work item of a round: queue position of the instance, slot | (items of
+// the instance's earlier slots in the round) << 2, tile, items of the
+// instance per round.  Item q of the launch is entry q mod per_round of round
+// q / per_round.
 struct ScanArgs {
   const Inst* inst;
   int count;
   int nsteps;
-  const unsigned long long* slot_prefix;  // [3 * (count + 1)]: prefix of tiles per slot
+  const int4* items;                      // [per_round] items of one round in queue order
   unsigned long long per_round;           // items of a full round
   unsigned long long total;               // items of the whole launch
   unsigned* done;                         // [count] finished items per instance
@@ -140,8 +144,8 @@ __device__ __noinline__ void psi_item(const Inst& d, int full, long long tau, un
   const unsigned ustride = STRIDED ? (unsigned)N : 1u;
   const cx<float>* tw = reinterpret_cast<const cx<float>*>(d.tw);
   const float4* lift = reinterpret_cast<const float4*>(d.mult) + full * N;
-  float vph[E];
-  (void)vph;
+  const float* vrow = nullptr;
+  (void)vrow;
   if constexpr (VARIANT == PSI_NPHASE) {
     for (int idx = tid; idx < H * LPB; idx += kThreads) {
       const int ll = idx % LPB, k = idx / LPB;
@@ -150,12 +154,12 @@ __device__ __noinline__ void psi_item(const Inst& d, int full, long long tau, un
       rtile[k * TSTR + ll] = z;
     }
     __syncthreads();
-    tile::potential_c2r<N, LPB, WL, false, STRIDED>(rtile, lines, tw, l, t, vph);
+    vrow = tile::potential_c2r<N, LPB, WL, false, STRIDED>(rtile, lines, tw, l, t);
   }
   cx<float> v[E];
   tile::load_line<E, T, true>(v, d.psi + base, ustride, t, valid);
   if constexpr (VARIANT == PSI_NPHASE)
-    tile::nonlinear_phase<E, T>(v, vph, d.gh, nullptr, 0.f, ustride, t, valid);
+    tile::nonlinear_phase<E, T>(v, vrow, d.gh, nullptr, 0.f, ustride, t, valid);
   tile::kinetic<N, WL>(v, lines + l * LS, tw, lift, t);
   tile::store_line<E, T>(v, d.psi + base, ustride, t, valid);
   if constexpr (VARIANT == PSI_DENSITY) {
@@ -216,33 +220,25 @@ __device__ void run_item(const Inst& d, int r, int s, int nsteps, long long tau,
 
 __global__ void __launch_bounds__(kThreads, 2) scan_kernel(ScanArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_go;
-  const unsigned long long C = a.count;
-  const unsigned long long* pre = a.slot_prefix;
+  __shared__ int4 s_item;
+  __shared__ int s_round, s_go;
   for (unsigned long long q = blockIdx.x; q < a.total; q += gridDim.x) {
-    // decode q -> (round, slot, instance, tile)
-    const unsigned long long r = q / a.per_round;
-    unsigned long long rem = q - r * a.per_round;
-    int s = 0;
-    while (s < 2 && rem >= pre[s * (C + 1) + C]) {
-      rem -= pre[s * (C + 1) + C];
-      ++s;
+    // thread 0 decodes q -> (round, instance, slot, tile) and waits for the
+    // instance's previous slot; the others meet it at the barrier
+    if (threadIdx.x == 0) {
+      const unsigned long long r = q / a.per_round;
+      const int4 e = __ldg(a.items + (q - r * a.per_round));
+      const unsigned req = (unsigned)r * (unsigned)e.w + ((unsigned)e.y >> 2);
+      s_item = e;
+      s_round = (int)r;
+      s_go = (ld_relaxed(a.err) == 0) && wait_for(a, e.x, req, q);
     }
-    const unsigned long long* ps = pre + s * (C + 1);
-    int lo = 0, hi = (int)C - 1;  // last instance with ps[i] <= rem
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (ps[mid] <= rem) lo = mid;
-      else hi = mid - 1;
-    }
-    const int inst = lo;
-    const long long tau = (long long)(rem - ps[inst]);
-    const Inst d = a.inst[inst];
-    const unsigned per_inst_round = 2 * d.t_psi + d.t_rho;
-    const unsigned req = (unsigned)r * per_inst_round + (s >= 1 ? d.t_psi : 0) + (s >= 2 ? d.t_psi : 0);
-    if (threadIdx.x == 0) s_go = (ld_relaxed(a.err) == 0) && wait_for(a, inst, req, q);
     __syncthreads();
     if (!s_go) return;
+    const int4 e = s_item;
+    const int inst = e.x, s = e.y & 3;
+    const long long r = s_round, tau = e.z;
+    const Inst d = a.inst[inst];
     switch (d.n) {
       case 8: run_item<8>(d, (int)r, s, a.nsteps, tau, smem); break;
       case 16: run_item<16>(d, (int)r, s, a.nsteps, tau, smem); break;
@@ -282,7 +278,8 @@ struct sn_batch_s {
   float2* tw[kMaxLog2 + 1] = {};
   std::vector<float2*> mult;
   std::vector<float*> k2;
-  unsigned long long* slot_prefix = nullptr;
+  int4* items = nullptr;  // one round's work items in queue order
+  unsigned long long per_round = 0, last = 0;  // items of a full round; of the last (psi passes only)
   unsigned* done = nullptr;
   int* err = nullptr;
   long long wait_limit = 4000000000LL;  // about 2 s at the B300's 2 GHz
@@ -393,7 +390,6 @@ sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* 
   b->order.resize(count);
   for (int i = 0; i < count; ++i) b->order[i] = i;
   std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return n[x] > n[y]; });
-  std::vector<unsigned long long> prefix(3 * (count + 1), 0);
   for (int i = 0; i < count; ++i) {
     Inst& d = b->host_inst[i];
     const int N = n[i];
@@ -430,17 +426,22 @@ sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* 
       return bail(bcuda(e, "cudaMemcpy(k2)"));
     d.k2 = b->k2[i];
   }
-  for (int p = 0; p < count; ++p) {
-    const Inst& d = b->host_inst[b->order[p]];
-    prefix[0 * (count + 1) + p + 1] = prefix[0 * (count + 1) + p] + d.t_psi;
-    prefix[1 * (count + 1) + p + 1] = prefix[1 * (count + 1) + p] + d.t_psi;
-    prefix[2 * (count + 1) + p + 1] = prefix[2 * (count + 1) + p] + d.t_rho;
-  }
-  if ((e = balloc(b, &b->slot_prefix, prefix.size())) != cudaSuccess)
-    return bail(bcuda(e, "cudaMalloc(prefix)"));
-  if ((e = cudaMemcpy(b->slot_prefix, prefix.data(), prefix.size() * sizeof(unsigned long long),
-                      cudaMemcpyHostToDevice)) != cudaSuccess)
-    return bail(bcuda(e, "cudaMemcpy(prefix)"));
+  // one round: slot 0 of every instance (in queue order), then slot 1, then slot 2
+  std::vector<int4> items;
+  for (int s = 0; s < 3; ++s)
+    for (int p = 0; p < count; ++p) {
+      const Inst& d = b->host_inst[b->order[p]];
+      const unsigned tiles = s == 2 ? d.t_rho : d.t_psi;
+      const int before = (s >= 1 ? (int)d.t_psi : 0) + (s >= 2 ? (int)d.t_psi : 0);
+      for (unsigned j = 0; j < tiles; ++j)
+        items.push_back(make_int4(p, s | (before << 2), (int)j, (int)(2 * d.t_psi + d.t_rho)));
+    }
+  b->per_round = items.size();
+  for (int i = 0; i < count; ++i) b->last += 2ull * b->host_inst[i].t_psi;
+  if ((e = balloc(b, &b->items, items.size())) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(items)"));
+  if ((e = cudaMemcpy(b->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return bail(bcuda(e, "cudaMemcpy(items)"));
   if ((e = balloc(b, &b->dev_inst, (size_t)count)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(inst)"));
   if ((e = balloc(b, &b->done, (size_t)count)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(done)"));
   if ((e = balloc(b, &b->err, (size_t)2)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(err)"));
@@ -549,18 +550,13 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
                         cudaMemcpyHostToDevice)) != cudaSuccess)
       return bcuda(e, "cudaMemcpy(inst)");
   }
-  unsigned long long per_round = 0, last = 0;
-  for (int i = 0; i < b->count; ++i) {
-    per_round += 2ull * b->host_inst[i].t_psi + b->host_inst[i].t_rho;
-    last += 2ull * b->host_inst[i].t_psi;
-  }
   ScanArgs a{};
   a.inst = b->dev_inst;
   a.count = b->count;
   a.nsteps = nsteps;
-  a.slot_prefix = b->slot_prefix;
-  a.per_round = per_round;
-  a.total = per_round * (unsigned long long)nsteps + last;
+  a.items = b->items;
+  a.per_round = b->per_round;
+  a.total = b->per_round * (unsigned long long)nsteps + b->last;
   a.done = b->done;
   a.err = b->err;
   a.wait_limit = b->wait_limit;

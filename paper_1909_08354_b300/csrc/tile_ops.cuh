@@ -106,19 +106,20 @@ __device__ __forceinline__ void store_line(const cx<float> (&v)[E], float2* p, u
   }
 }
 
-// V h on my line's elements (pattern P) from a staged [k][line] half-spectrum
-// tile: C2R inverse FFT of lines (l, l + LPB/2) packed as A + iB.  On entry the
-// tile is visible to all threads and the line buffers are free.
+// V h of the tile's lines from a staged [k][line] half-spectrum tile: C2R
+// inverse FFT of lines (l, l + LPB/2) packed as A + iB.  On entry the tile is
+// visible to all threads and the line buffers are free.  Returns the row that
+// holds V h of my line, element t + T m at [t + T m], in line l's buffer
+// (read before the buffer's next use, which starts with a barrier).
 // REMAP (strided passes): the thread of (l, t) in the pass's own mapping holds
 // line l at position t spread over all warps, so half of every warp would idle
 // through the packed transform; the transform then runs in the contiguous
 // mapping (line tid / T, position tid % T: whole warps busy, warp-local
 // exchanges) and V reaches the owners through shared memory.
 template <int N, int LPB, bool WL, bool TC = false, bool REMAP = false>
-__device__ __forceinline__ void potential_c2r(const cx<float>* rtile, cx<float>* lines,
-                                              const cx<float>* tw, int l, int t,
-                                              float (&vph)[Plan<N>::E],
-                                              const tc16::Tabs* tb = nullptr) {
+__device__ __forceinline__ const float* potential_c2r(const cx<float>* rtile, cx<float>* lines,
+                                                      const cx<float>* tw, int l, int t,
+                                                      const tc16::Tabs* tb = nullptr) {
   using C = Cfg<N, LPB>;
   constexpr int E = C::E, T = C::T, LS = C::LS, TSTR = C::TSTR, HALF = LPB / 2;
   constexpr bool WLC = REMAP ? true : WL;  // T <= 32: a contiguous-mapped line is warp-local
@@ -156,39 +157,32 @@ __device__ __forceinline__ void potential_c2r(const cx<float>* rtile, cx<float>*
         b[tc + T * m] = v[m].im;
       }
     }
-    __syncthreads();
-    const float* mine = reinterpret_cast<const float*>(lines + l * LS);
-#pragma unroll
-    for (int m = 0; m < E; ++m) vph[m] = mine[t + T * m];
   } else {
     __syncthreads();
     if (pa) {
-      float* up = reinterpret_cast<float*>(lines + (l + HALF) * LS);
+      float* a = reinterpret_cast<float*>(lines + l * LS);
+      float* b = reinterpret_cast<float*>(lines + (l + HALF) * LS);
 #pragma unroll
       for (int m = 0; m < E; ++m) {
-        vph[m] = v[m].re;
-        up[t + T * m] = v[m].im;
+        a[t + T * m] = v[m].re;
+        b[t + T * m] = v[m].im;
       }
     }
-    __syncthreads();
-    if (!pa) {
-      const float* up = reinterpret_cast<const float*>(lines + l * LS);
-#pragma unroll
-      for (int m = 0; m < E; ++m) vph[m] = up[t + T * m];
-    }
   }
+  __syncthreads();
+  return reinterpret_cast<const float*>(lines + l * LS);
 }
 
 // psi <- exp(-i (V h + V_ext h + g h |psi|^2)) psi.  The angle is reduced to
 // [-pi, pi] with a two-part 2 pi, the SFU sine and cosine are taken there and
 // the pair is renormalised to unit modulus by one Newton step.
 template <int E, int T>
-__device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float (&vph)[E],
+__device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float* vrow,
                                                 float gh, const float* vx, float h,
                                                 unsigned ustride, int t, bool valid) {
 #pragma unroll
   for (int m = 0; m < E; ++m) {
-    float th = vph[m] + gh * cnorm2(v[m]);
+    float th = vrow[t + T * m] + gh * cnorm2(v[m]);
     if (vx != nullptr && valid) th += vx[(unsigned)(t + T * m) * ustride] * h;
     const float kq = rintf(th * 0.159154943091895336f);
     float r = fmaf(-kq, 6.28318548202514648f, th);
