@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "fft_plan.h"
 #include "sn.h"
 #include "sn_internal.h"
 
@@ -62,24 +63,6 @@ void split_hilo(const double2* v, int n, float2* out) {
     out[i] = make_float2(hr, hi);
     out[n + i] = make_float2((float)(v[i].x - (double)hr), (float)(v[i].y - (double)hi));
   }
-}
-
-// Stage twiddles of the two-stage plan for length N (N <= 512): 2N entries, none for N <= 16.
-int twiddles(int N, double2* tw) {
-  if (N <= 16) return 0;
-  const int R0 = N == 32 ? 2 : N == 64 ? 4 : N == 128 ? 8 : 16;
-  const int R1 = N / R0;
-  for (int r = 0; r < R1; ++r)
-    for (int j = 0; j < R0; ++j) {
-      const double a = -2.0 * kPi * (double)((long long)j * r % N) / N;
-      tw[r * R0 + j] = make_double2(std::cos(a), std::sin(a));
-    }
-  for (int r = 0; r < R0; ++r)
-    for (int j = 0; j < R1; ++j) {
-      const double a = 2.0 * kPi * (double)((long long)j * r % N) / N;
-      tw[N + r * R1 + j] = make_double2(std::cos(a), std::sin(a));
-    }
-  return 2 * N;
 }
 
 // Once per device, with that device current: the device address of the array.
@@ -148,7 +131,7 @@ extern "C" sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, d
   float2 t32[4 * kMaxN];
   float kf[kMaxN];
   for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
-    const int ntw = twiddles(n[a], t64);
+    const int ntw = snfft::plan_twiddles(n[a], t64);  // at most 2 n[a] entries
     if (ntw > 0) {
       split_hilo(t64, ntw, t32);
       e = cudaMemcpyAsync(tw[a], t32, 2 * ntw * sizeof(float2), cudaMemcpyHostToDevice, stream);

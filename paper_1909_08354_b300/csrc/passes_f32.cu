@@ -108,8 +108,8 @@ psi_pass_kernel(PsiPassArgs a) {
   constexpr int E = P::E, T = P::T, NT = LPB * T, LS = P::LS, H = N / 2 + 1;
   constexpr bool NPHASE = VARIANT == PSI_NPHASE;
   constexpr bool DENSITY = VARIANT == PSI_DENSITY;
-  constexpr bool PF = E <= 16;  // register prefetch of the next tile (lines up to 256)
-  constexpr bool WL = !STRIDED && T <= 32;  // a contiguous line lives in one warp
+  constexpr bool PF = E <= 16;  // register prefetch of the next tile
+  constexpr bool CONTIG = !STRIDED;  // line l held by threads [l T, (l + 1) T)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw_sm = reinterpret_cast<cx<float>*>(smem_raw);
   cx<float>* mult_sm = tw_sm + 2 * P::TWN;
@@ -178,7 +178,7 @@ psi_pass_kernel(PsiPassArgs a) {
       cp_async_commit();
       cp_async_wait<1>();
       __syncthreads();
-      vrow = tile::potential_c2r<N, LPB, WL, TC, STRIDED>(rstage + (it & 1) * (H * TSTR), lines,
+      vrow = tile::potential_c2r<N, LPB, CONTIG, TC, STRIDED>(rstage + (it & 1) * (H * TSTR), lines,
                                                           tw_sm, l, t, tabs);
     }
 
@@ -205,7 +205,7 @@ psi_pass_kernel(PsiPassArgs a) {
       const tc16::MultTable mt{mult_tc, mult_tc + tc16::MT};
       tc16::fmi(v, lines, *tabs, l, t, [&](int) { return mt; });
     } else {
-      tile::kinetic<N, WL>(v, lines + l * LS, tw_sm, reinterpret_cast<const float4*>(mult_sm), t);
+      tile::kinetic<N, CONTIG>(v, lines + l * LS, tw_sm, reinterpret_cast<const float4*>(mult_sm), t);
     }
     store_line<E, T>(v, a.psi + base, ustride, t, valid);
 
@@ -214,7 +214,7 @@ psi_pass_kernel(PsiPassArgs a) {
       auto put = [&](int k, int ll, cx<float> z) {
         tile::stg_c(rh + (size_t)k * nlines + line0 + ll, z);
       };
-      tile::density_r2c<N, LPB, WL, decltype(put), TC, STRIDED>(v, valid, lines, tw_sm, l, t, tid,
+      tile::density_r2c<N, LPB, CONTIG, decltype(put), TC, STRIDED>(v, valid, lines, tw_sm, l, t, tid,
                                                                 nvalid, put, tabs);
     }
     __syncthreads();  // line buffers and the staging tile are reused next iteration
@@ -242,8 +242,8 @@ rho_pass_kernel(RhoPassArgs a) {
   const int t = STRIDED ? (tid / LPB) : (tid % T);
   const tile::Tiles<LPB, STRIDED> tiles(a.outer, a.inner);
   const unsigned ustride = STRIDED ? (unsigned)a.inner : 1u;
-  constexpr bool PF = E <= 16;  // register prefetch of the next tile (lines up to 256)
-  constexpr bool WL = !STRIDED && T <= 32;  // a contiguous line lives in one warp
+  constexpr bool PF = E <= 16;  // register prefetch of the next tile
+  constexpr bool CONTIG = !STRIDED;  // line l held by threads [l T, (l + 1) T)
   if constexpr (TC) {
     tc16::load_tabs(tabs, a.tc, a.tw, tid, NT);
     if constexpr (OP == RHO_GREEN)
@@ -285,9 +285,9 @@ rho_pass_kernel(RhoPassArgs a) {
       load_line<E, T>(v, a.data + base, ustride, t, valid);
     }
     if constexpr (OP == RHO_INV) {
-      tile::xform<N, +1, WL, TC>(v, lines, tw_sm, tabs, l, t, LPB);
+      tile::xform<N, +1, CONTIG, TC>(v, lines, tw_sm, tabs, l, t, LPB);
     } else if constexpr (OP == RHO_FWD) {
-      tile::xform<N, -1, WL, TC>(v, lines, tw_sm, tabs, l, t, LPB);
+      tile::xform<N, -1, CONTIG, TC>(v, lines, tw_sm, tabs, l, t, LPB);
     } else {
       long long plane, mid;
       if constexpr (STRIDED) {
@@ -305,7 +305,7 @@ rho_pass_kernel(RhoPassArgs a) {
           return tc16::GreenMult{k2l_tc, k2pm_sm[L], a.cN, a.cY, a.mu2};
         });
       } else {
-        tile::green<N, WL>(v, lines + l * LS, tw_sm, a.k2l, k2pm, a.cN, a.cY, a.mu2, t);
+        tile::green<N, CONTIG>(v, lines + l * LS, tw_sm, a.k2l, k2pm, a.cN, a.cY, a.mu2, t);
       }
     }
     store_line<E, T>(v, a.data + base, ustride, t, valid);

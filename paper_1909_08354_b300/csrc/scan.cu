@@ -64,10 +64,7 @@ int log2i(int n) {
   return l;
 }
 
-int lines_per_tile(int n) {
-  const int E = n <= 16 ? n : (n <= 256 ? 16 : 32);
-  return kThreads / (n / E);
-}
+int lines_per_tile(int n) { return kThreads / (n / snfft::plan_e(n)); }
 
 // Per-instance description, device resident.
 struct Inst {
@@ -125,11 +122,11 @@ __device__ bool wait_for(const ScanArgs& a, int i, unsigned req, unsigned long l
 }
 
 template <int N, bool STRIDED, int VARIANT>
-__device__ __noinline__ void psi_item(const Inst& d, int full, long long tau, unsigned char* smem) {
+__device__ __forceinline__ void psi_item(const Inst& d, int full, long long tau, unsigned char* smem) {
   using S = ScanCfg<N>;
   using C = typename S::C;
   constexpr int LPB = S::LPB, E = C::E, T = C::T, LS = C::LS, H = C::H, TSTR = C::TSTR;
-  constexpr bool WL = !STRIDED;  // T <= 32 for every N
+  constexpr bool CONTIG = !STRIDED;  // line l held by threads [l T, (l + 1) T)
   cx<float>* lines = reinterpret_cast<cx<float>*>(smem);
   cx<float>* rtile = lines + LPB * LS;
   const int tid = threadIdx.x;
@@ -154,24 +151,24 @@ __device__ __noinline__ void psi_item(const Inst& d, int full, long long tau, un
       rtile[k * TSTR + ll] = z;
     }
     __syncthreads();
-    vrow = tile::potential_c2r<N, LPB, WL, false, STRIDED>(rtile, lines, tw, l, t);
+    vrow = tile::potential_c2r<N, LPB, CONTIG, false, STRIDED>(rtile, lines, tw, l, t);
   }
   cx<float> v[E];
   tile::load_line<E, T, true>(v, d.psi + base, ustride, t, valid);
   if constexpr (VARIANT == PSI_NPHASE)
     tile::nonlinear_phase<E, T>(v, vrow, d.gh, nullptr, 0.f, ustride, t, valid);
-  tile::kinetic<N, WL>(v, lines + l * LS, tw, lift, t);
+  tile::kinetic<N, CONTIG>(v, lines + l * LS, tw, lift, t);
   tile::store_line<E, T>(v, d.psi + base, ustride, t, valid);
   if constexpr (VARIANT == PSI_DENSITY) {
     float2* rh = d.rho;
     auto put = [&](int k, int ll, cx<float> z) { tile::stg_c(rh + (size_t)k * N + line0 + ll, z); };
-    tile::density_r2c<N, LPB, WL, decltype(put), false, STRIDED>(v, valid, lines, tw, l, t, tid,
+    tile::density_r2c<N, LPB, CONTIG, decltype(put), false, STRIDED>(v, valid, lines, tw, l, t, tid,
                                                                  nvalid, put);
   }
 }
 
 template <int N>
-__device__ __noinline__ void green_item(const Inst& d, long long tau, unsigned char* smem) {
+__device__ __forceinline__ void green_item(const Inst& d, long long tau, unsigned char* smem) {
   using S = ScanCfg<N>;
   using C = typename S::C;
   constexpr int LPB = S::LPB, E = C::E, T = C::T, LS = C::LS;
@@ -218,7 +215,7 @@ __device__ void run_item(const Inst& d, int r, int s, int nsteps, long long tau,
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) scan_kernel(ScanArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) scan_kernel(ScanArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int4 s_item;
   __shared__ int s_round, s_go;
@@ -324,25 +321,6 @@ void split_hilo(const std::vector<double2>& v, float2* out) {
   }
 }
 
-std::vector<double2> twiddles(int N) {
-  std::vector<double2> tw;
-  if (N <= 16) return tw;
-  const int R0 = N == 32 ? 2 : N == 64 ? 4 : N == 128 ? 8 : N == 256 ? 16 : N == 512 ? 16 : 32;
-  const int R1 = N / R0;
-  tw.resize(2 * N);
-  for (int r = 0; r < R1; ++r)
-    for (int j = 0; j < R0; ++j) {
-      const double a = -2.0 * kPi * (double)((long long)j * r % N) / N;
-      tw[r * R0 + j] = make_double2(std::cos(a), std::sin(a));
-    }
-  for (int r = 0; r < R0; ++r)
-    for (int j = 0; j < R1; ++j) {
-      const double a = 2.0 * kPi * (double)((long long)j * r % N) / N;
-      tw[N + r * R1 + j] = make_double2(std::cos(a), std::sin(a));
-    }
-  return tw;
-}
-
 double wavenumber(int j, int n, double L) { return 2.0 * kPi / L * (double)(j < n / 2 ? j : j - n); }
 
 }  // namespace
@@ -405,7 +383,8 @@ sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* 
       return bail(bcuda(e, "cudaMalloc(rho)"));
     const int l2 = log2i(N);
     if (!b->tw[l2]) {
-      std::vector<double2> t64 = twiddles(N);
+      std::vector<double2> t64((size_t)snfft::plan_twn(N));
+      snfft::plan_twiddles(N, t64.data());
       std::vector<float2> t32(std::max<size_t>(2 * t64.size(), 2));
       if (!t64.empty()) split_hilo(t64, t32.data());
       if ((e = balloc(b, &b->tw[l2], t32.size())) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(tw)"));

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "fft_plan.h"
 #include "sn.h"
 #include "sn_internal.h"
 
@@ -43,38 +44,10 @@ void split_hilo(const std::vector<double2>& v, std::vector<float2>& out) {
   }
 }
 
-// Twiddle table of the two-stage Stockham plan for length N (see sn_fft.cuh):
-// [r*R0 + j] = exp(-2 pi i j r / N) (forward second stage, r < R1, j < R0) and
-// [N + r*R1 + j] = exp(+2 pi i j r / N) (inverse second stage, r < R0, j < R1).
-void plan_radices(int N, int* R0, int* R1) {
-  if (N <= 16) { *R0 = N; *R1 = 1; return; }
-  switch (N) {
-    case 32: *R0 = 2; break;
-    case 64: *R0 = 4; break;
-    case 128: *R0 = 8; break;
-    case 256: *R0 = 16; break;
-    case 512: *R0 = 16; break;
-    default: *R0 = 32; break;
-  }
-  *R1 = N / *R0;
-}
-
+// Stage twiddles of the line-FFT plan of length N in FP64 (fft_plan.h)
 std::vector<double2> twiddles_f64(int N) {
-  int R0, R1;
-  plan_radices(N, &R0, &R1);
-  std::vector<double2> tw;
-  if (R1 == 1) return tw;
-  tw.resize(2 * N);
-  for (int r = 0; r < R1; ++r)
-    for (int j = 0; j < R0; ++j) {
-      const double a = -2.0 * kPi * (double)((long long)j * r % N) / N;
-      tw[r * R0 + j] = make_double2(std::cos(a), std::sin(a));
-    }
-  for (int r = 0; r < R0; ++r)
-    for (int j = 0; j < R1; ++j) {
-      const double a = 2.0 * kPi * (double)((long long)j * r % N) / N;
-      tw[N + r * R1 + j] = make_double2(std::cos(a), std::sin(a));
-    }
+  std::vector<double2> tw((size_t)snfft::plan_twn(N));
+  snfft::plan_twiddles(N, tw.data());
   return tw;
 }
 

@@ -11,13 +11,15 @@
 // registers v[m].  Every transform reads pattern P and leaves its result in
 // pattern P with the natural frequency / space index, so a forward transform,
 // a pointwise multiplier and an inverse transform chain without reordering.
-// N = R0 * R1 (at most two Stockham stages); the data crosses shared memory
-// once per transform, between the two stages.  Stage twiddles come from a
-// host-built FP64 table rounded once to the working precision.
+// N = R0 * R1 (* R2): two or three Stockham stages (fft_plan.h); the data
+// crosses shared memory between consecutive stages.  Stage twiddles come from
+// a host-built FP64 table rounded once to the working precision.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "fft_plan.h"
 
 namespace snfft {
 
@@ -97,6 +99,19 @@ __device__ __forceinline__ cx<R> tmul(cx<R> a, const cx<R>* tab, int idx, int n)
   }
 }
 
+// a * w (SIGN < 0) or a * conj(w) (SIGN > 0), w = table entry idx
+template <typename R, int SIGN>
+__device__ __forceinline__ cx<R> tmul_dir(cx<R> a, const cx<R>* tab, int idx, int n) {
+  if constexpr (SIGN < 0) {
+    return tmul(a, tab, idx, n);
+  } else if constexpr (sizeof(R) == sizeof(float)) {
+    return cmul_hl(a, cconj(tab[idx]), cconj(tab[n + idx]));
+  } else {
+    (void)n;
+    return cmul(a, cconj(tab[idx]));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Small DFTs in registers:  X[q] = sum_r x[r] exp(SIGN 2 pi i r q / RAD)
 // ---------------------------------------------------------------------------
@@ -138,7 +153,7 @@ __device__ __forceinline__ cx<R> rot8(cx<R> a) {
 }
 
 // tan(k pi / 32) and sin(k pi / 16), k = 0..8: the three-shear form of the
-// rotations by k pi / 16 inside the radix-16 and radix-32 kernels
+// rotations by k pi / 16 inside the radix-16 kernel
 constexpr double kTan32[9] = {0.0, 0.0984914033571642530772, 0.198912367379658006912,
                               0.303346683607342391676, 0.414213562373095048802,
                               0.534511135950791641090, 0.668178637919298919998,
@@ -171,25 +186,6 @@ __device__ __forceinline__ cx<R> rot16(cx<R> a) {
     constexpr double c = K <= 8 ? kSin16[8 - K] : -kSin16[K - 8];  // cos(K pi / 16)
     constexpr double s = K <= 8 ? kSin16[K] : kSin16[16 - K];       // sin(K pi / 16)
     return rot<R, SIGN>(a, c, s);
-  }
-}
-
-// rot16 with k known only after unrolling (folds to one case)
-template <typename R, int SIGN>
-__device__ __forceinline__ cx<R> rot16_at(cx<R> a, int k) {
-  switch (k) {
-    case 1: return rot16<R, SIGN, 1>(a);
-    case 2: return rot16<R, SIGN, 2>(a);
-    case 3: return rot16<R, SIGN, 3>(a);
-    case 5: return rot16<R, SIGN, 5>(a);
-    case 6: return rot16<R, SIGN, 6>(a);
-    case 7: return rot16<R, SIGN, 7>(a);
-    case 9: return rot16<R, SIGN, 9>(a);
-    case 10: return rot16<R, SIGN, 10>(a);
-    case 11: return rot16<R, SIGN, 11>(a);
-    case 13: return rot16<R, SIGN, 13>(a);
-    case 14: return rot16<R, SIGN, 14>(a);
-    default: return rot16<R, SIGN, 15>(a);
   }
 }
 
@@ -237,26 +233,6 @@ __device__ __forceinline__ void dft16(cx<R>* a) {
   }
 }
 
-template <typename R, int SIGN>
-__device__ __forceinline__ void dft32(cx<R>* a) {
-  // radix-2 decimation in time over two 16-point DFTs; W32^k = exp(SIGN i pi k / 16)
-  cx<R> e[16], o[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) { e[i] = a[2 * i]; o[i] = a[2 * i + 1]; }
-  dft16<R, SIGN>(e);
-  dft16<R, SIGN>(o);
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    cx<R> w = (k == 0) ? o[k]
-              : (k == 8)  ? mul_si<R, SIGN>(o[k])
-              : (k == 4)  ? rot8<R, SIGN, 1>(o[k])
-              : (k == 12) ? rot8<R, SIGN, 3>(o[k])
-                          : rot16_at<R, SIGN>(o[k], k);
-    a[k] = e[k] + w;
-    a[k + 16] = e[k] - w;
-  }
-}
-
 template <typename R, int SIGN, int RAD>
 __device__ __forceinline__ void dft(cx<R>* a) {
   if constexpr (RAD == 1) {
@@ -266,11 +242,9 @@ __device__ __forceinline__ void dft(cx<R>* a) {
     dft4<R, SIGN>(a[0], a[1], a[2], a[3]);
   } else if constexpr (RAD == 8) {
     dft8<R, SIGN>(a);
-  } else if constexpr (RAD == 16) {
-    dft16<R, SIGN>(a);
   } else {
-    static_assert(RAD == 32, "unsupported radix");
-    dft32<R, SIGN>(a);
+    static_assert(RAD == 16, "unsupported radix");
+    dft16<R, SIGN>(a);
   }
 }
 
@@ -281,18 +255,18 @@ __device__ __forceinline__ void dft(cx<R>* a) {
 template <int N>
 struct Plan {
   static_assert(N >= 8 && N <= 1024 && (N & (N - 1)) == 0, "N must be a power of two in [8,1024]");
-  static constexpr int E = N <= 16 ? N : (N <= 256 ? 16 : 32);
+  static constexpr int E = plan_e(N);
   static constexpr int T = N / E;
-  static constexpr int R0 = N <= 16 ? N : (N == 32 ? 2 : N == 64 ? 4 : N == 128 ? 8 : N == 256 ? 16 : N == 512 ? 16 : 32);
-  static constexpr int R1 = N / R0;
-  static constexpr int STAGES = (R1 == 1) ? 1 : 2;
-  // padded shared-memory line: one pad slot per PAD elements (PAD = the
-  // first-stage radix of the long lines, so that the runs a thread writes
-  // start at odd strides), odd line stride
-  static constexpr int PAD_SHIFT = N >= 1024 ? 5 : 4;
-  static constexpr int LS = N + (N >> PAD_SHIFT) + 1;
-  // twiddle table entries: forward second stage (N) + inverse second stage (N)
-  static constexpr int TWN = STAGES == 2 ? 2 * N : 0;
+  static constexpr int R0 = plan_r0(N), R1 = plan_r1(N), R2 = plan_r2(N);
+  static constexpr int STAGES = plan_stages(N);
+  // padded shared-memory line: one pad slot per 16 elements, so that the
+  // runs a thread writes start at odd strides; the line stride is odd for
+  // two stages and 2 or 4 modulo 16 for three, which keeps the exchanges of
+  // the strided passes (lanes spread over 4 to 16 lines) conflict-free
+  static constexpr int PAD_SHIFT = 4;
+  static constexpr int LS = N + (N >> PAD_SHIFT) + (STAGES < 3 ? 1 : (N == 1024 ? 4 : 2));
+  // twiddle table entries (fft_plan.h)
+  static constexpr int TWN = plan_twn(N);
   // entries held per table in shared memory: FP32 keeps hi and lo parts
   template <typename R>
   static constexpr int tw_words() { return sizeof(R) == sizeof(float) ? 2 * TWN : TWN; }
@@ -301,17 +275,31 @@ struct Plan {
 template <int N>
 __device__ __forceinline__ int pidx(int i) { return i + (i >> Plan<N>::PAD_SHIFT); }
 
-// Twiddle table of length N: entry [r*R0 + j] = exp(-2 pi i j r / N) for the
-// forward second stage (r < R1, j < R0), followed by entry
-// [N + r*R1 + j] = exp(+2 pi i j r / N) for the inverse second stage
-// (r < R0, j < R1).  The FP32 table appends the lo parts of all 2N entries.
+// Twiddle tables: fft_plan.h.  The FP32 table appends the lo parts of all TWN
+// entries.
+
+// Barrier among the threads that share one line buffer.  CONTIG: line l is
+// held by the consecutive threads [l T, (l + 1) T); a line of T <= 32
+// threads then sits in one warp (warp barrier) and one of 64 threads in a
+// warp pair (named barrier 1 + tid / 64, at most 15 pairs per CTA).  Lines
+// spread over the CTA (strided mapping) take the CTA barrier.
+template <int N, bool CONTIG>
+__device__ __forceinline__ void line_sync() {
+  constexpr int T = Plan<N>::T;
+  if constexpr (CONTIG && T <= 32) {
+    __syncwarp();
+  } else if constexpr (CONTIG && T == 64) {
+    asm volatile("bar.sync %0, 64;\n" ::"r"(1 + (int)(threadIdx.x >> 6)) : "memory");
+  } else {
+    __syncthreads();
+  }
+}
 
 // In-place transform of one line held in pattern P.  Every thread of the CTA
-// must call it (it contains __syncthreads); `active` masks the arithmetic and
-// shared-memory traffic of threads whose line is idle in this transform.
-// WARP_LOCAL: every line is held by threads of a single warp, so the
-// exchange needs only a warp barrier (all 32 lanes must still call).
-template <typename R, int N, int SIGN, bool WARP_LOCAL = false>
+// must call it (it contains barriers: line_sync); `active` masks the
+// arithmetic and shared-memory traffic of threads whose line is idle in this
+// transform.  CONTIG: the line mapping of line_sync.
+template <typename R, int N, int SIGN, bool CONTIG = false>
 __device__ __forceinline__ void line_transform(cx<R> (&v)[Plan<N>::E], cx<R>* line_buf,
                                                const cx<R>* tw_sm, int t, bool active) {
   using P = Plan<N>;
@@ -319,11 +307,11 @@ __device__ __forceinline__ void line_transform(cx<R> (&v)[Plan<N>::E], cx<R>* li
   if constexpr (P::STAGES == 1) {
     if (active) dft<R, SIGN, E>(v);
     return;
-  } else {
+  } else if constexpr (P::STAGES == 2) {
     constexpr int RA = SIGN < 0 ? P::R0 : P::R1;  // first stage radix (Ns = 1)
     constexpr int RB = SIGN < 0 ? P::R1 : P::R0;  // second stage radix (Ns = RA)
     constexpr int UA = E / RA, UB = E / RB;
-    if (WARP_LOCAL) __syncwarp(); else __syncthreads();  // previous readers of line_buf are done
+    line_sync<N, CONTIG>();  // previous readers of line_buf are done
     if (active) {
 #pragma unroll
       for (int u = 0; u < UA; ++u) {
@@ -336,7 +324,7 @@ __device__ __forceinline__ void line_transform(cx<R> (&v)[Plan<N>::E], cx<R>* li
         for (int q = 0; q < RA; ++q) line_buf[pidx<N>(j * RA + q)] = a[q];
       }
     }
-    if (WARP_LOCAL) __syncwarp(); else __syncthreads();
+    line_sync<N, CONTIG>();
     if (active) {
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = line_buf[pidx<N>(t + T * m)];
@@ -352,6 +340,68 @@ __device__ __forceinline__ void line_transform(cx<R> (&v)[Plan<N>::E], cx<R>* li
         dft<R, SIGN, RB>(a);
 #pragma unroll
         for (int q = 0; q < RB; ++q) v[u + q * UB] = a[q];
+      }
+    }
+  } else {
+    // three stages R0, R1, R2 in both directions; the inverse multiplies by
+    // the conjugate twiddles.  Stage s (span Ns, radix R) maps input j + r N/R
+    // (j < N/R) to output (j / Ns) Ns R + j % Ns + q Ns after the twiddle
+    // exp(SIGN 2 pi i (j % Ns) r / (Ns R)).
+    constexpr int RA = P::R0, RB = P::R1, RC = P::R2, NB = RA * RB;
+    constexpr int UA = E / RA, UB = E / RB, UC = E / RC;
+    line_sync<N, CONTIG>();  // previous readers of line_buf are done
+    if (active) {
+#pragma unroll
+      for (int u = 0; u < UA; ++u) {
+        cx<R> a[RA];
+#pragma unroll
+        for (int r = 0; r < RA; ++r) a[r] = v[u + r * UA];
+        dft<R, SIGN, RA>(a);
+        const int j = t + T * u;
+#pragma unroll
+        for (int q = 0; q < RA; ++q) line_buf[pidx<N>(j * RA + q)] = a[q];
+      }
+    }
+    line_sync<N, CONTIG>();
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = line_buf[pidx<N>(t + T * m)];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int jm = (t + T * u) & (RA - 1);
+        cx<R> a[RB];
+        a[0] = v[u];
+#pragma unroll
+        for (int r = 1; r < RB; ++r) a[r] = tmul_dir<R, SIGN>(v[u + r * UB], tw_sm, r * RA + jm, P::TWN);
+        dft<R, SIGN, RB>(a);
+#pragma unroll
+        for (int q = 0; q < RB; ++q) v[u + q * UB] = a[q];
+      }
+    }
+    line_sync<N, CONTIG>();  // every read of line_buf is done
+    if (active) {
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int j = t + T * u;
+        const int o = (j / RA) * NB + (j & (RA - 1));
+#pragma unroll
+        for (int q = 0; q < RB; ++q) line_buf[pidx<N>(o + q * RA)] = v[u + q * UB];
+      }
+    }
+    line_sync<N, CONTIG>();
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = line_buf[pidx<N>(t + T * m)];
+#pragma unroll
+      for (int u = 0; u < UC; ++u) {
+        const int j = t + T * u;  // < NB
+        cx<R> a[RC];
+        a[0] = v[u];
+#pragma unroll
+        for (int r = 1; r < RC; ++r) a[r] = tmul_dir<R, SIGN>(v[u + r * UC], tw_sm, NB + r * NB + j, P::TWN);
+        dft<R, SIGN, RC>(a);
+#pragma unroll
+        for (int q = 0; q < RC; ++q) v[u + q * UC] = a[q];
       }
     }
   }

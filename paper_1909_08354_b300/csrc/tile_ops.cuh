@@ -4,7 +4,9 @@
 // A tile's lines are numbered l = 0..LPB-1; the T threads of line l hold its
 // elements in pattern P (see sn_fft.cuh).  `lines` is LPB padded line buffers
 // of Plan<N>::LS complex values; `tw` and `mult` point at hi/lo FP32 tables in
-// shared or global memory.  WL says that each line lives inside one warp.
+// shared or global memory.  CONTIG says that line l is held by the
+// consecutive threads [l T, (l + 1) T) (contiguous mapping), so that its
+// exchanges need only the barrier of a warp or warp pair (snfft::line_sync).
 #pragma once
 
 #include "sn_fft.cuh"
@@ -24,7 +26,7 @@ using snfft::Plan;
 
 // One DFT of the lines l < nact of the tile (pattern P in and out): the
 // FP32 Stockham engine, or the tensor-core engine for 256-point lines (TC).
-template <int N, int SIGN, bool WL, bool TC>
+template <int N, int SIGN, bool CONTIG, bool TC>
 __device__ __forceinline__ void xform(cx<float> (&v)[Plan<N>::E], cx<float>* lines,
                                       const cx<float>* tw, const tc16::Tabs* tb, int l, int t,
                                       int nact) {
@@ -32,7 +34,7 @@ __device__ __forceinline__ void xform(cx<float> (&v)[Plan<N>::E], cx<float>* lin
     static_assert(N == tc16::N, "the tensor-core engine handles 256-point lines");
     tc16::transform<SIGN < 0 ? 0 : 1>(v, lines, *tb, l, t, nact);
   } else {
-    line_transform<float, N, SIGN, WL>(v, lines + l * Plan<N>::LS, tw, t, l < nact);
+    line_transform<float, N, SIGN, CONTIG>(v, lines + l * Plan<N>::LS, tw, t, l < nact);
   }
 }
 
@@ -116,13 +118,13 @@ __device__ __forceinline__ void store_line(const cx<float> (&v)[E], float2* p, u
 // through the packed transform; the transform then runs in the contiguous
 // mapping (line tid / T, position tid % T: whole warps busy, warp-local
 // exchanges) and V reaches the owners through shared memory.
-template <int N, int LPB, bool WL, bool TC = false, bool REMAP = false>
+template <int N, int LPB, bool CONTIG, bool TC = false, bool REMAP = false>
 __device__ __forceinline__ const float* potential_c2r(const cx<float>* rtile, cx<float>* lines,
                                                       const cx<float>* tw, int l, int t,
                                                       const tc16::Tabs* tb = nullptr) {
   using C = Cfg<N, LPB>;
   constexpr int E = C::E, T = C::T, LS = C::LS, TSTR = C::TSTR, HALF = LPB / 2;
-  constexpr bool WLC = REMAP ? true : WL;  // T <= 32: a contiguous-mapped line is warp-local
+  constexpr bool CC = REMAP || CONTIG;  // the mapping of the packed transform
   const int lc = REMAP ? (int)threadIdx.x / T : l;
   const int tc = REMAP ? (int)threadIdx.x % T : t;
   cx<float> v[E];
@@ -143,11 +145,11 @@ __device__ __forceinline__ const float* potential_c2r(const cx<float>* rtile, cx
       v[m] = {A.re - B.im, A.im + B.re};  // A + i B
     }
   }
-  xform<N, +1, WLC, TC>(v, lines, tw, tb, lc, tc, HALF);
+  xform<N, +1, CC, TC>(v, lines, tw, tb, lc, tc, HALF);
   if constexpr (REMAP) {
-    // the line buffer of lc is read by its own warp only (FP32 engine); the
-    // tensor-core engine shares all buffers across the CTA
-    if constexpr (TC) __syncthreads(); else __syncwarp();
+    // the line buffer of lc is read by the threads of line lc only (FP32
+    // engine); the tensor-core engine shares all buffers across the CTA
+    if constexpr (TC) __syncthreads(); else snfft::line_sync<N, true>();
     if (pa) {
       float* a = reinterpret_cast<float*>(lines + lc * LS);
       float* b = reinterpret_cast<float*>(lines + (lc + HALF) * LS);
@@ -207,11 +209,11 @@ __device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float* 
 // rounded coefficients change the angle by ~1e-8 but not the norm: no mass
 // drift on average, where the product with a hi + lo factor (two roundings)
 // drifts by ~1e-8 per application on the structured spectra of lumps.
-template <int N, bool WL>
+template <int N, bool CONTIG>
 __device__ __forceinline__ void kinetic(cx<float> (&v)[Plan<N>::E], cx<float>* line_buf,
                                         const cx<float>* tw, const float4* lift, int t) {
   constexpr int E = Plan<N>::E, T = Plan<N>::T;
-  line_transform<float, N, -1, WL>(v, line_buf, tw, t, true);
+  line_transform<float, N, -1, CONTIG>(v, line_buf, tw, t, true);
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const float4 q = lift[t + T * m];
@@ -220,7 +222,7 @@ __device__ __forceinline__ void kinetic(cx<float> (&v)[Plan<N>::E], cx<float>* l
     const float x2 = fmaf(-q.x, y1, x1);
     v[m] = {x2 * q.z, y1 * q.z};
   }
-  line_transform<float, N, +1, WL>(v, line_buf, tw, t, true);
+  line_transform<float, N, +1, CONTIG>(v, line_buf, tw, t, true);
 }
 
 // rho = |psi|^2 of the tile and its R2C FFT along the line (two real lines per
@@ -228,7 +230,7 @@ __device__ __forceinline__ void kinetic(cx<float> (&v)[Plan<N>::E], cx<float>* l
 // for the valid lines; the calls are spread over all threads with ll fastest.
 // REMAP: as in potential_c2r, the packed transform runs in the contiguous
 // mapping, fed with |psi|^2 through shared memory.
-template <int N, int LPB, bool WL, class Put, bool TC = false, bool REMAP = false>
+template <int N, int LPB, bool CONTIG, class Put, bool TC = false, bool REMAP = false>
 __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], bool valid,
                                             cx<float>* lines, const cx<float>* tw, int l, int t,
                                             int tid, int nvalid, Put put,
@@ -240,7 +242,7 @@ __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], 
   float rho[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) rho[m] = valid ? cnorm2(psi[m]) : 0.f;
-  constexpr bool WLC = REMAP ? true : WL;
+  constexpr bool CC = REMAP || CONTIG;
   const int lc = REMAP ? tid / T : l;
   const int tc = REMAP ? tid % T : t;
   const bool pc = lc < HALF;  // this thread transforms packed line lc
@@ -263,7 +265,7 @@ __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], 
       for (int m = 0; m < E; ++m) v[m] = {rho[m], bb[tc + T * m]};
     }
   }
-  xform<N, -1, WLC, TC>(v, lines, tw, tb, lc, tc, HALF);
+  xform<N, -1, CC, TC>(v, lines, tw, tb, lc, tc, HALF);
   __syncthreads();
   if (pc) {
 #pragma unroll
@@ -304,12 +306,12 @@ __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], 
 
 // FFT . K(k) . IFFT along my line of the half spectrum, K = cN/k2 + cY/(k2 + mu2)
 // with K(0) = 0; k2 = k2pm (the two other axes) + k2l[k] (this axis).
-template <int N, bool WL>
+template <int N, bool CONTIG>
 __device__ __forceinline__ void green(cx<float> (&v)[Plan<N>::E], cx<float>* line_buf,
                                       const cx<float>* tw, const float* k2l, float k2pm, float cN,
                                       float cY, float mu2, int t) {
   constexpr int E = Plan<N>::E, T = Plan<N>::T;
-  line_transform<float, N, -1, WL>(v, line_buf, tw, t, true);
+  line_transform<float, N, -1, CONTIG>(v, line_buf, tw, t, true);
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     // one division; K's relative error of a few ulp moves the phase V h by far
@@ -319,7 +321,7 @@ __device__ __forceinline__ void green(cx<float> (&v)[Plan<N>::E], cx<float>* lin
     const float K = (k2 > 0.f) ? __fdividef(fmaf(cN, k2 + mu2, cY * k2), den) : 0.f;
     v[m] = cscale(v[m], K);
   }
-  line_transform<float, N, +1, WL>(v, line_buf, tw, t, true);
+  line_transform<float, N, +1, CONTIG>(v, line_buf, tw, t, true);
 }
 
 }  // namespace tile
