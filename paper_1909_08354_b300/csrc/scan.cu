@@ -34,6 +34,7 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kThreads = 256;  // threads per CTA for every line length
+constexpr int kCtasPerSm = 3;  // resident CTAs per SM the registers are sized for (80 each)
 constexpr int kMaxLog2 = 10;
 
 template <int N>
@@ -41,7 +42,11 @@ struct ScanCfg {
   static constexpr int T = Plan<N>::T;
   static constexpr int LPB = kThreads / T;  // lines per tile
   using C = tile::Cfg<N, LPB>;
-  static constexpr size_t smem_words = (size_t)LPB * C::LS + (size_t)C::H * C::TSTR;
+  // the line buffers; the staged half-spectrum tile of a potential item
+  // ([H][LPB + 1]) is read into registers before they are used, so it
+  // occupies them too
+  static constexpr size_t smem_words = (size_t)LPB * C::LS;
+  static_assert((size_t)C::H * C::TSTR <= smem_words, "half-spectrum tile must fit the line buffers");
 };
 
 constexpr size_t max_words() {
@@ -128,7 +133,7 @@ __device__ __forceinline__ void psi_item(const Inst& d, int full, long long tau,
   constexpr int LPB = S::LPB, E = C::E, T = C::T, LS = C::LS, H = C::H, TSTR = C::TSTR;
   constexpr bool CONTIG = !STRIDED;  // line l held by threads [l T, (l + 1) T)
   cx<float>* lines = reinterpret_cast<cx<float>*>(smem);
-  cx<float>* rtile = lines + LPB * LS;
+  cx<float>* rtile = lines;  // staged tile of a potential item, read before the lines are used
   const int tid = threadIdx.x;
   const int l = STRIDED ? (tid % LPB) : (tid / T);
   const int t = STRIDED ? (tid / LPB) : (tid % T);
@@ -151,7 +156,7 @@ __device__ __forceinline__ void psi_item(const Inst& d, int full, long long tau,
       rtile[k * TSTR + ll] = z;
     }
     __syncthreads();
-    vrow = tile::potential_c2r<N, LPB, CONTIG, false, STRIDED>(rtile, lines, tw, l, t);
+    vrow = tile::potential_c2r<N, LPB, CONTIG, false, STRIDED, true>(rtile, lines, tw, l, t);
   }
   cx<float> v[E];
   tile::load_line<E, T, true>(v, d.psi + base, ustride, t, valid);
@@ -215,7 +220,7 @@ __device__ void run_item(const Inst& d, int r, int s, int nsteps, long long tau,
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) scan_kernel(ScanArgs a) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) scan_kernel(ScanArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int4 s_item;
   __shared__ int s_round, s_go;
@@ -428,9 +433,19 @@ sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* 
   if ((e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kSmemBytes)) != cudaSuccess)
     return bail(bcuda(e, "cudaFuncSetAttribute"));
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0, per_sm = 0, smem_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (smem_sm > 0) {
+    // shared memory for the resident CTAs (1 KB reserved each), the rest of
+    // the SM's 256 KB stays L1 for the twiddle and kinetic tables and spills
+    const double need = (double)kCtasPerSm * (double)(kSmemBytes + 1024 + 64);
+    const int pct = std::min(100, (int)std::ceil(100.0 * need / smem_sm));
+    if ((e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) !=
+        cudaSuccess)
+      return bail(bcuda(e, "cudaFuncSetAttribute(carveout)"));
+  }
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kThreads, kSmemBytes)) !=
       cudaSuccess)
     return bail(bcuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));

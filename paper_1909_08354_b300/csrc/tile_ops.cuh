@@ -113,12 +113,15 @@ __device__ __forceinline__ void store_line(const cx<float> (&v)[E], float2* p, u
 // visible to all threads and the line buffers are free.  Returns the row that
 // holds V h of my line, element t + T m at [t + T m], in line l's buffer
 // (read before the buffer's next use, which starts with a barrier).
+// TILE_IN_LINES: the staged tile occupies the line buffers themselves, so
+// every read of it completes before the transform writes them.
 // REMAP (strided passes): the thread of (l, t) in the pass's own mapping holds
 // line l at position t spread over all warps, so half of every warp would idle
 // through the packed transform; the transform then runs in the contiguous
 // mapping (line tid / T, position tid % T: whole warps busy, warp-local
 // exchanges) and V reaches the owners through shared memory.
-template <int N, int LPB, bool CONTIG, bool TC = false, bool REMAP = false>
+template <int N, int LPB, bool CONTIG, bool TC = false, bool REMAP = false,
+          bool TILE_IN_LINES = false>
 __device__ __forceinline__ const float* potential_c2r(const cx<float>* rtile, cx<float>* lines,
                                                       const cx<float>* tw, int l, int t,
                                                       const tc16::Tabs* tb = nullptr) {
@@ -145,6 +148,7 @@ __device__ __forceinline__ const float* potential_c2r(const cx<float>* rtile, cx
       v[m] = {A.re - B.im, A.im + B.re};  // A + i B
     }
   }
+  if constexpr (TILE_IN_LINES) __syncthreads();
   xform<N, +1, CC, TC>(v, lines, tw, tb, lc, tc, HALF);
   if constexpr (REMAP) {
     // the line buffer of lc is read by the threads of line lc only (FP32
