@@ -58,12 +58,14 @@ def parse():
     p.add_argument("--engine", choices=["fp32", "tc16"], default="fp32",
                    help="line engine of the timed grid (tc16: tensor cores on 256-point axes)")
     p.add_argument("--no-fno", action="store_true")
+    p.add_argument("--no-optical", action="store_true",
+                   help="skip the thermo-optical (Eq. 4) kernel on a 1024^2 plane")
     return p.parse_args()
 
 
 def kernel_kw(kp):
     return dict(coeff_lap=kp.coeff_lap, G=kp.G, alpha_Y=kp.alpha_Y, lambda_Y=kp.lambda_Y,
-                g_local=kp.g_local)
+                g_local=kp.g_local, kind=kp.kind, B=kp.B, C=kp.C, D=kp.D)
 
 
 def measured_peaks():
@@ -275,6 +277,47 @@ def run_tc16(sn, torch, stream, w, kw, psi0, peak, ref1, steps=200):
                            "GBps": v["bytes"] / (v["ms"] / 1e3) / 1e9} for k, v in kinds.items()}}
 
 
+def run_optical(sn, torch, stream, peak, steps=500):
+    """Eq. 2 kernel of a thermo-optical medium (Eq. 4) on a 1024^2 transverse plane:
+    beams of Eq. 3, complex64 fused passes, timed like the main line; accuracy is the
+    one-step rel-L2 against the plain FP64 GPU step from the same input."""
+    w = W.optical_beams_2d(nsteps=steps)
+    kw = kernel_kw(w.kernel)
+    psi0 = w.psi0(np.complex64)
+    g = sn.Grid(w.n, w.L, "c64", stream=stream.cuda_stream)
+    g.set_kernel(**kw)
+    g.set_state(psi0)
+    g.step(w.dt, 1)
+    out1 = g.get_state()
+    g64 = sn.Grid(w.n, w.L, "c128", stream=stream.cuda_stream)
+    g64.set_kernel(**kw)
+    g64.set_state(psi0.astype(np.complex128))
+    g64.step(w.dt, 1)
+    ref1 = g64.get_state()
+    g64.close()
+    rel = float(np.linalg.norm((out1 - ref1).ravel()) / np.linalg.norm(ref1.ravel()))
+    g.set_state(psi0)
+    m0 = g.observables()["mass"]
+    g.step(w.dt, 5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(w.dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    drift = g.observables()["mass"] / m0 - 1.0
+    g.close()
+    value = w.cells * steps / t
+    gbs = 48.0 * value / 1e9
+    return {"workload": f"optical2d_1024: 1024^2, L=100, complex64, thermo-optical kernel "
+                        f"(Eq. 4: C=-1/25, D=-2, B=1), {len(w.lumps)} beams seed 6000, dt=1e-2",
+            "value": value, "unit": UNIT, "ms_per_step": 1e3 * t / steps, "steps": steps,
+            "rel_l2_vs_fp64_one_step": rel, "mass_drift": drift,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "bytes_per_cell_step": 48.0}}
+
+
 def run_fno(sn, torch, stream, iters=10):
     """Training throughput of the FNO surrogate at its full size (256^2, width 64,
     24x24 modes, 4 layers, projection 128, batch 16): forward + loss + backward + Adam."""
@@ -454,6 +497,10 @@ def main():
     if not args.no_tc and args.n == 256 and args.engine == "fp32":
         tc = run_tc16(sn, torch, stream, w, kw, psi0, peak, ref1)
 
+    optical = None
+    if not args.no_optical and world == 1:
+        optical = run_optical(sn, torch, stream, peak)
+
     scan = None
     if not args.no_scan:
         scan = run_scan(sn, torch, stream, peak, args.scan_count, args.scan_steps)
@@ -495,6 +542,7 @@ def main():
             "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu,
             "tensor_core_engine": tc,
+            "optical_kernel": optical,
             "batched_scan": scan,
             "fno_surrogate": fno,
         }

@@ -5,12 +5,18 @@
  * The system (Sec. II, Eqs. 1-2) is
  *     i dpsi/dt = A lap(psi) + B phi psi + G(|psi|^2) psi,
  *     lap(phi) + C phi = D |psi|^2,
- * with B = 1 and the local nonlinearity G(|psi|^2) = g |psi|^2.  The potential
- * is solved spectrally (Sec. III) with the Newton + Yukawa multiplier that the
- * modified Poisson equation of the non-minimal matter-curvature coupling gives
- * for constant coefficients (Eq. 9; Eq. 14 is its alpha -> 0 limit):
- *     phi_k = K(k) rho_k,  K(k) = -4 pi G [1/k^2 + alpha_Y / (k^2 + 1/lambda_Y^2)],
- *     K(0) = 0 (the mean density is removed).
+ * and the local nonlinearity G(|psi|^2) = g |psi|^2.  The potential is solved
+ * spectrally (Sec. III): B phi_k = K(k) rho_k with K(0) = 0 (the mean density
+ * is removed) and one of two kernels (sn_kernel.kind):
+ *   SN_KERNEL_NMC: the Newton + Yukawa multiplier that the modified Poisson
+ *     equation of the non-minimal matter-curvature coupling gives for constant
+ *     coefficients (Eq. 9; Eq. 14 is its alpha -> 0 limit), B = 1:
+ *       K(k) = -4 pi G [1/k^2 + alpha_Y / (k^2 + 1/lambda_Y^2)];
+ *   SN_KERNEL_POISSON: Eq. 2 itself with constants B, C <= 0, D, the form of
+ *     the optical media of Sec. II A -- thermo-optical (Eq. 4: phi = dn,
+ *     C = -1/sigma^2, D = -zeta mu / kappa) and nematic liquid crystals
+ *     (Eq. 5: phi = theta, C = -2q/nu, D = -2/nu):
+ *       K(k) = B D / (C - k^2).
  * Time stepping is the symmetric split-step Fourier method (Sec. III):
  *     S(h) = Kin(h/2) Nl(h) Kin(h/2),
  *     Kin(tau) = F^-1 exp(i A k^2 tau) F,
@@ -55,17 +61,27 @@ typedef enum {
   SN_C128 = 1  /* complex128 state; plain FP64 step */
 } sn_dtype;
 
-/* Parameters of Eqs. 1-2 as used by the step (Sec. II; Eq. 9 / Eq. 14). */
+/* Kernel of the potential (see the top of this file). */
+typedef enum {
+  SN_KERNEL_NMC = 0,     /* Newton + Yukawa of Eq. 9 / Eq. 14: G, alpha_Y, lambda_Y */
+  SN_KERNEL_POISSON = 1  /* Eq. 2 with constants B, C, D (Eqs. 4 and 5)             */
+} sn_kernel_kind;
+
+/* Parameters of Eqs. 1-2 as used by the step (Sec. II; Eq. 9 / Eq. 14).
+ * Zero-initialise it and set what is needed: kind 0 is SN_KERNEL_NMC. */
 typedef struct {
   double coeff_lap;  /* A of Eq. 1; -0.5 for i psi_t = -(1/2) lap psi + ...   */
-  double G;          /* K(k) = -4 pi G (1/k^2 + alpha_Y / (k^2 + 1/lambda_Y^2)) */
-  double alpha_Y;    /* Yukawa strength; 0 gives the pure Newton kernel         */
-  double lambda_Y;   /* Yukawa range (> 0 when alpha_Y != 0)                    */
+  double G;          /* NMC: K(k) = -4 pi G (1/k^2 + alpha_Y / (k^2 + 1/lambda_Y^2)) */
+  double alpha_Y;    /* NMC: Yukawa strength; 0 gives the pure Newton kernel    */
+  double lambda_Y;   /* NMC: Yukawa range (> 0 when alpha_Y != 0)               */
   double g_local;    /* local term g |psi|^2                                     */
   int zero_k0;       /* must be 1: the whole multiplier is zero at k = 0         */
   const double* v_ext; /* optional real external potential (C order, ncells
                           doubles), NULL for none; copied by sn_set_kernel       */
   int v_ext_on_device; /* 1 if v_ext is a device pointer, 0 if host             */
+  int kind;          /* sn_kernel_kind                                           */
+  double B, C, D;    /* POISSON: B of Eq. 1 and C (<= 0), D of Eq. 2;
+                        K(k) = B D / (C - k^2); ignored for NMC                  */
 } sn_kernel;
 
 /* Observables at the current integer step (FP64, computed on the device).
@@ -92,8 +108,8 @@ sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, 
                          void* cuda_stream);
 
 /* Set the parameters of Eqs. 1-2 (see sn_kernel).  Copies v_ext.  Errors:
- * SN_EINVAL for non-finite values, lambda_Y <= 0 with alpha_Y != 0, or
- * zero_k0 != 1. */
+ * SN_EINVAL for non-finite values, an unknown kind, lambda_Y <= 0 with
+ * alpha_Y != 0 (NMC), C > 0 (POISSON), or zero_k0 != 1. */
 sn_status sn_set_kernel(sn_grid g, const sn_kernel* k);
 
 /* Copy a state in: psi holds ncells complex values of the grid's dtype,

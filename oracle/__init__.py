@@ -5,8 +5,8 @@ benchmark's CPU-baseline leg, never by the CUDA library or its binding.
 """
 from .sn_oracle import (dft_naive, fft_radix2, fftn, wavenumbers, k_squared, cell_volume,
                         green_multiplier, kinetic, potential, nonlinear, strang_step, evolve,
-                        kernel_kwargs, observables, rel_l2)
+                        kernel_kwargs, observables, rel_l2, KIND_NMC, KIND_POISSON)
 
 __all__ = ["dft_naive", "fft_radix2", "fftn", "wavenumbers", "k_squared", "cell_volume",
            "green_multiplier", "kinetic", "potential", "nonlinear", "strang_step", "evolve",
-           "kernel_kwargs", "observables", "rel_l2"]
+           "kernel_kwargs", "observables", "rel_l2", "KIND_NMC", "KIND_POISSON"]

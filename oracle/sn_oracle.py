@@ -9,10 +9,15 @@ It is the plain, slow, readable statement of what the solver computes:
 * Eq. 1 (Sec. II):  i dpsi/dt = A lap(psi) + B phi psi + G(|psi|^2) psi, with
   B = 1 and the local term G(|psi|^2) = g |psi|^2.
 * Eq. 2 (Sec. II):  lap(phi) + C phi = D |psi|^2, solved spectrally
-  (Sec. III: "also with spectral methods").  A sum of two such equations gives
-  the Newton + Yukawa multiplier of the modified Poisson equation (Eq. 9 with
-  constant coefficients; Eq. 14 is its alpha -> 0 limit):
+  (Sec. III: "also with spectral methods").  Two kernel kinds:
+  - KIND_NMC: a sum of two such equations gives the Newton + Yukawa
+    multiplier of the modified Poisson equation (Eq. 9 with constant
+    coefficients; Eq. 14 is its alpha -> 0 limit), with B = 1:
       K(k) = -4 pi G [ 1/k^2 + alpha_Y / (k^2 + 1/lambda_Y^2) ],  K(0) := 0.
+  - KIND_POISSON: Eq. 2 itself with constants B (Eq. 1), C <= 0 and D, the
+    form of the optical media of Sec. II A (thermo-optical, Eq. 4:
+    C = -1/sigma^2; nematic liquid crystals, Eq. 5: C = -2q/nu, D = -2/nu):
+      K(k) = B D / (C - k^2),  K(0) := 0.
 * Sec. III: the symmetric split-step Fourier method,
       S(h) = Kin(h/2) o Nl(h) o Kin(h/2),
   Kin(tau) = F^-1 exp(i A k^2 tau) F          (exact free propagator of Eq. 1),
@@ -36,6 +41,8 @@ from typing import Dict, Optional, Sequence, Tuple
 import numpy as np
 
 TWO_PI = 2.0 * math.pi
+KIND_NMC = 0      # Newton + Yukawa kernel of Eq. 9 / Eq. 14 (G, alpha_Y, lambda_Y)
+KIND_POISSON = 1  # Eq. 2 with constants B, C, D (Eqs. 4 and 5)
 
 
 # ----------------------------------------------------------------------------
@@ -137,17 +144,30 @@ def cell_volume(n: Sequence[int], L: Sequence[float]) -> float:
 
 
 def green_multiplier(n: Sequence[int], L: Sequence[float], G: float = 1.0,
-                     alpha_Y: float = 0.0, lambda_Y: float = 1.0) -> np.ndarray:
-    """Spectral solution operator of the Poisson-type equation (Eq. 2, Eq. 9).
+                     alpha_Y: float = 0.0, lambda_Y: float = 1.0, kind: int = KIND_NMC,
+                     B: float = 1.0, C: float = 0.0, D: float = 0.0) -> np.ndarray:
+    """Spectral solution operator of the Poisson-type equation (Eq. 2, Eq. 9):
+    the potential B phi entering Eq. 1 is F^-1[K F rho].
 
-    Newton part (C = 0, D = 4 pi G):  phi_k = -4 pi G rho_k / k^2.
-    Yukawa part (C = -1/lambda_Y^2, D = 4 pi G alpha_Y):
-        phi_k = -4 pi G alpha_Y rho_k / (k^2 + 1/lambda_Y^2).
+    Eq. 2 in Fourier space reads (C - k^2) phi_k = D rho_k, so one equation
+    gives K = B D / (C - k^2).
+    KIND_NMC (B = 1):
+      Newton part (C = 0, D = 4 pi G):  phi_k = -4 pi G rho_k / k^2;
+      Yukawa part (C = -1/lambda_Y^2, D = 4 pi G alpha_Y):
+          phi_k = -4 pi G alpha_Y rho_k / (k^2 + 1/lambda_Y^2).
+    KIND_POISSON: K = B D / (C - k^2) with the caller's B, C <= 0, D.
     The whole multiplier is zero at k = 0 (removes the mean density).
     """
     k2 = k_squared(n, L)
     K = np.zeros_like(k2)
     nz = k2 > 0
+    if kind == KIND_POISSON:
+        if not C <= 0.0:
+            raise ValueError("KIND_POISSON needs C <= 0")
+        K[nz] = B * D / (C - k2[nz])
+        return K
+    if kind != KIND_NMC:
+        raise ValueError(f"unknown kernel kind {kind}")
     K[nz] = -4.0 * math.pi * G * (1.0 / k2[nz])
     if alpha_Y != 0.0:
         K[nz] += -4.0 * math.pi * G * alpha_Y / (k2[nz] + 1.0 / (lambda_Y * lambda_Y))
@@ -168,22 +188,24 @@ def kinetic(psi: np.ndarray, tau: float, L: Sequence[float], coeff_lap: float = 
 
 
 def potential(rho: np.ndarray, L: Sequence[float], G: float = 1.0, alpha_Y: float = 0.0,
-              lambda_Y: float = 1.0) -> np.ndarray:
+              lambda_Y: float = 1.0, kind: int = KIND_NMC, B: float = 1.0, C: float = 0.0,
+              D: float = 0.0) -> np.ndarray:
     """V = F^-1[K F rho] (Eq. 2 solved spectrally, Sec. III); real for real rho."""
-    K = green_multiplier(rho.shape, L, G, alpha_Y, lambda_Y)
+    K = green_multiplier(rho.shape, L, G, alpha_Y, lambda_Y, kind, B, C, D)
     return fftn(K * fftn(rho), inverse=True).real
 
 
 def nonlinear(psi: np.ndarray, h: float, L: Sequence[float], G: float = 1.0,
               alpha_Y: float = 0.0, lambda_Y: float = 1.0, g_local: float = 0.0,
-              v_ext: Optional[np.ndarray] = None) -> np.ndarray:
+              v_ext: Optional[np.ndarray] = None, kind: int = KIND_NMC, B: float = 1.0,
+              C: float = 0.0, D: float = 0.0) -> np.ndarray:
     """Exact propagator of i dpsi/dt = (V + V_ext + g|psi|^2) psi over time h.
 
     |psi|^2 does not change under this sub-step, so V is computed once from the
     input density and the update is the pointwise phase exp(-i(...) h).
     """
     rho = (psi * np.conj(psi)).real
-    V = potential(rho, L, G, alpha_Y, lambda_Y)
+    V = potential(rho, L, G, alpha_Y, lambda_Y, kind, B, C, D)
     if v_ext is not None:
         V = V + v_ext
     return psi * np.exp(-1j * (V + g_local * rho) * h)
@@ -191,10 +213,12 @@ def nonlinear(psi: np.ndarray, h: float, L: Sequence[float], G: float = 1.0,
 
 def strang_step(psi: np.ndarray, h: float, L: Sequence[float], G: float = 1.0,
                 alpha_Y: float = 0.0, lambda_Y: float = 1.0, g_local: float = 0.0,
-                coeff_lap: float = -0.5, v_ext: Optional[np.ndarray] = None) -> np.ndarray:
+                coeff_lap: float = -0.5, v_ext: Optional[np.ndarray] = None,
+                kind: int = KIND_NMC, B: float = 1.0, C: float = 0.0,
+                D: float = 0.0) -> np.ndarray:
     """One symmetric split step S(h) = Kin(h/2) Nl(h) Kin(h/2) (Sec. III)."""
     psi = kinetic(psi, 0.5 * h, L, coeff_lap)
-    psi = nonlinear(psi, h, L, G, alpha_Y, lambda_Y, g_local, v_ext)
+    psi = nonlinear(psi, h, L, G, alpha_Y, lambda_Y, g_local, v_ext, kind, B, C, D)
     return kinetic(psi, 0.5 * h, L, coeff_lap)
 
 
@@ -207,9 +231,14 @@ def evolve(psi: np.ndarray, h: float, nsteps: int, L: Sequence[float], **kernel)
 
 
 def kernel_kwargs(kp) -> Dict[str, float]:
-    """Keyword arguments of the sub-steps from a parameter object with the same field names."""
-    return dict(G=kp.G, alpha_Y=kp.alpha_Y, lambda_Y=kp.lambda_Y, g_local=kp.g_local,
-                coeff_lap=kp.coeff_lap)
+    """Keyword arguments of the sub-steps from a parameter object with the same field
+    names (kind, B, C, D when it has them)."""
+    kw = dict(G=kp.G, alpha_Y=kp.alpha_Y, lambda_Y=kp.lambda_Y, g_local=kp.g_local,
+              coeff_lap=kp.coeff_lap)
+    for name in ("kind", "B", "C", "D"):
+        if hasattr(kp, name):
+            kw[name] = getattr(kp, name)
+    return kw
 
 
 # ----------------------------------------------------------------------------
@@ -218,7 +247,8 @@ def kernel_kwargs(kp) -> Dict[str, float]:
 
 def observables(psi: np.ndarray, L: Sequence[float], G: float = 1.0, alpha_Y: float = 0.0,
                 lambda_Y: float = 1.0, g_local: float = 0.0, coeff_lap: float = -0.5,
-                v_ext: Optional[np.ndarray] = None) -> Dict[str, object]:
+                v_ext: Optional[np.ndarray] = None, kind: int = KIND_NMC, B: float = 1.0,
+                C: float = 0.0, D: float = 0.0) -> Dict[str, object]:
     """Mass, Hamiltonian parts, periodic centroids and momentum of psi.
 
     H is the conserved energy of Eq. 1 with the Hartree potential:
@@ -238,7 +268,7 @@ def observables(psi: np.ndarray, L: Sequence[float], G: float = 1.0, alpha_Y: fl
     pk2 = (psik * np.conj(psik)).real
     mass = dV * rho.sum()
     e_kin = -coeff_lap * dV / N * float((k_squared(n, L) * pk2).sum())
-    V = potential(rho, L, G, alpha_Y, lambda_Y)
+    V = potential(rho, L, G, alpha_Y, lambda_Y, kind, B, C, D)
     e_pot = 0.5 * dV * float((V * rho).sum())
     if v_ext is not None:
         e_pot += dV * float((v_ext * rho).sum())

@@ -14,6 +14,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <string>
 
 #include "fft_plan.h"
 #include "sn.h"
@@ -102,12 +103,8 @@ extern "C" sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, d
   }
   if (!std::isfinite(dt)) return fail(SN_EINVAL, "sn_step_2d_noalloc: dt must be finite");
   if (nsteps < 0) return fail(SN_EINVAL, "sn_step_2d_noalloc: nsteps must be >= 0");
-  if (!std::isfinite(k->coeff_lap) || !std::isfinite(k->G) || !std::isfinite(k->alpha_Y) ||
-      !std::isfinite(k->lambda_Y) || !std::isfinite(k->g_local))
-    return fail(SN_EINVAL, "sn_step_2d_noalloc: kernel parameters must be finite");
-  if (k->alpha_Y != 0.0 && !(k->lambda_Y > 0.0))
-    return fail(SN_EINVAL, "sn_step_2d_noalloc: lambda_Y must be > 0 when alpha_Y != 0");
-  if (k->zero_k0 != 1) return fail(SN_EINVAL, "sn_step_2d_noalloc: zero_k0 must be 1");
+  if (const char* why = kernel_invalid(*k))
+    return fail(SN_EINVAL, (std::string("sn_step_2d_noalloc: ") + why).c_str());
   if (k->v_ext) return fail(SN_ENOTSUP, "sn_step_2d_noalloc: v_ext is not supported");
   if (nsteps == 0) return SN_OK;
 
@@ -153,8 +150,8 @@ extern "C" sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, d
   if (e != cudaSuccess) return cuda_fail(e, "table upload");
 
   const long long cells = (long long)ny * nx;
-  const double mu2 = (k->alpha_Y != 0.0) ? 1.0 / (k->lambda_Y * k->lambda_Y) : 1.0;
-  const double cN = -4.0 * kPi * k->G * dt / (double)cells;
+  const GreenCoeffs gc = green_coeffs(*k);
+  const double mu2 = gc.mu2, cN = gc.cN * dt / (double)cells, cY = gc.cY * dt / (double)cells;
   float2* p = reinterpret_cast<float2*>(psi);
   // Merged Strang steps: round r applies the kinetic factor along both axes
   // (half step in the first and last round), with the nonlinear phase in the
@@ -195,7 +192,7 @@ extern "C" sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, d
       ra.k2l = k2[c];
       ra.mid_n = 1;
       ra.cN = (float)cN;
-      ra.cY = (float)(cN * k->alpha_Y);
+      ra.cY = (float)cY;
       ra.mu2 = (float)mu2;
       e = launch_rho_pass_f32(n[c], false, RHO_GREEN, ra, stream);
       if (e != cudaSuccess) return cuda_fail(e, "green pass launch");

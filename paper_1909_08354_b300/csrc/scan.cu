@@ -459,12 +459,8 @@ sn_status sn_set_kernel_batch(sn_batch b, const sn_kernel* k) {
   if (!b || !k) return bfail(SN_EINVAL, "sn_set_kernel_batch: NULL argument");
   for (int i = 0; i < b->count; ++i) {
     const sn_kernel& x = k[i];
-    if (!std::isfinite(x.coeff_lap) || !std::isfinite(x.G) || !std::isfinite(x.alpha_Y) ||
-        !std::isfinite(x.lambda_Y) || !std::isfinite(x.g_local))
-      return bfail(SN_EINVAL, "sn_set_kernel_batch: parameters must be finite");
-    if (x.alpha_Y != 0.0 && !(x.lambda_Y > 0.0))
-      return bfail(SN_EINVAL, "sn_set_kernel_batch: lambda_Y must be > 0 when alpha_Y != 0");
-    if (x.zero_k0 != 1) return bfail(SN_EINVAL, "sn_set_kernel_batch: zero_k0 must be 1");
+    if (const char* why = kernel_invalid(x))
+      return bfail(SN_EINVAL, std::string("sn_set_kernel_batch: ") + why);
     if (x.v_ext) return bfail(SN_ENOTSUP, "sn_set_kernel_batch: v_ext is not supported in a batch");
   }
   for (int i = 0; i < b->count; ++i) {
@@ -518,11 +514,11 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
     const int N = b->n[i];
     const double h = dt[i];
     const double cells = (double)N * N;
-    const double cN = -4.0 * kPi * k.G * h / cells;
+    const GreenCoeffs gc = green_coeffs(k);
     const Inst before = d;
-    d.cN = (float)cN;
-    d.cY = (float)(cN * k.alpha_Y);
-    d.mu2 = (float)((k.alpha_Y != 0.0) ? 1.0 / (k.lambda_Y * k.lambda_Y) : 1.0);
+    d.cN = (float)(gc.cN * h / cells);
+    d.cY = (float)(gc.cY * h / cells);
+    d.mu2 = (float)gc.mu2;
     d.gh = (float)(k.g_local * h);
     if (std::memcmp(&before, &d, sizeof(Inst)) != 0) changed = true;
     if (!(h == b->dt[i])) {

@@ -65,6 +65,41 @@ struct Launch {
 
 void sn::set_thread_error(const char* msg) { g_tls_error = msg; }
 
+sn::GreenCoeffs sn::green_coeffs(const sn_kernel& k) {
+  GreenCoeffs c{0.0, 0.0, 1.0};
+  if (k.kind == SN_KERNEL_POISSON) {
+    if (k.C < 0.0) {
+      c.cY = -k.B * k.D;
+      c.mu2 = -k.C;
+    } else {
+      c.cN = -k.B * k.D;
+    }
+    return c;
+  }
+  c.cN = -4.0 * kPi * k.G;
+  c.cY = c.cN * k.alpha_Y;
+  c.mu2 = (k.alpha_Y != 0.0) ? 1.0 / (k.lambda_Y * k.lambda_Y) : 1.0;
+  return c;
+}
+
+const char* sn::kernel_invalid(const sn_kernel& k) {
+  if (!std::isfinite(k.coeff_lap) || !std::isfinite(k.g_local)) return "parameters must be finite";
+  if (k.zero_k0 != 1) return "zero_k0 must be 1";
+  if (k.kind == SN_KERNEL_NMC) {
+    if (!std::isfinite(k.G) || !std::isfinite(k.alpha_Y) || !std::isfinite(k.lambda_Y))
+      return "parameters must be finite";
+    if (k.alpha_Y != 0.0 && !(k.lambda_Y > 0.0)) return "lambda_Y must be > 0 when alpha_Y != 0";
+    return nullptr;
+  }
+  if (k.kind == SN_KERNEL_POISSON) {
+    if (!std::isfinite(k.B) || !std::isfinite(k.C) || !std::isfinite(k.D))
+      return "parameters must be finite";
+    if (k.C > 0.0) return "C must be <= 0 (Eq. 2 with a screening or no C term)";
+    return nullptr;
+  }
+  return "unknown kernel kind";
+}
+
 int sn::device_slot() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
@@ -262,7 +297,6 @@ LineGeom psi_geom(sn_grid g, int a) {
   return {outer, inner, a != g->ndim - 1};
 }
 
-double kernel_cN(sn_grid g, double scale) { return -4.0 * kPi * g->kp.G * scale; }
 
 // ---- fused FP32 step ----------------------------------------------------------
 
@@ -306,9 +340,9 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
     if (b != h) rest[nr++] = b;
   // rho-hat dims (P, n[rest[0]], [n[rest[1]]])
   const double bytes = 16.0 * (double)P * ((double)g->cells / g->n[h]);
-  const double mu2 = (g->kp.alpha_Y != 0.0) ? 1.0 / (g->kp.lambda_Y * g->kp.lambda_Y) : 1.0;
-  const double cN = kernel_cN(g, dt / (double)g->cells);
-  const double cY = cN * g->kp.alpha_Y;
+  const GreenCoeffs gc = green_coeffs(g->kp);
+  const double scale = dt / (double)g->cells;
+  const double mu2 = gc.mu2, cN = gc.cN * scale, cY = gc.cY * scale;
   RhoPassArgs ra{};
   ra.data = g->rhohat;
   ra.tw = nullptr;
@@ -420,15 +454,16 @@ sn_status step_f64(sn_grid g, double dt, int nsteps) {
   if (st != SN_OK) return st;
   double2* psi = reinterpret_cast<double2*>(g->psi);
   double2* w = g->w64b;
-  const double mu2 = (g->kp.alpha_Y != 0.0) ? 1.0 / (g->kp.lambda_Y * g->kp.lambda_Y) : 1.0;
-  const double cN = kernel_cN(g, dt / (double)g->cells);
+  const GreenCoeffs gc = green_coeffs(g->kp);
+  const double scale = dt / (double)g->cells;
   const double* k2[3] = {g->k2_64[0], g->k2_64[1], g->k2_64[2]};
   for (int s = 0; s < nsteps; ++s) {
     if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
     SN_LAUNCH(g, K_F64_EW, 32.0 * g->cells, launch_density_f64(psi, w, g->cells, g->stream));
     if ((st = fftn_f64(g, w, -1)) != SN_OK) return st;
     SN_LAUNCH(g, K_F64_EW, 32.0 * g->cells,
-              launch_green_f64(w, g->n, g->ndim, k2, cN, cN * g->kp.alpha_Y, mu2, g->stream));
+              launch_green_f64(w, g->n, g->ndim, k2, gc.cN * scale, gc.cY * scale, gc.mu2,
+                               g->stream));
     if ((st = fftn_f64(g, w, +1)) != SN_OK) return st;
     SN_LAUNCH(g, K_F64_EW, (48.0 + (g->has_vext ? 8.0 : 0.0)) * g->cells,
               launch_phase_f64(psi, w, g->has_vext ? g->vext64 : nullptr, dt,
@@ -490,6 +525,10 @@ sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, 
   g->kp.g_local = 0.0;
   g->kp.zero_k0 = 1;
   g->kp.v_ext = nullptr;
+  g->kp.kind = SN_KERNEL_NMC;
+  g->kp.B = 1.0;
+  g->kp.C = 0.0;
+  g->kp.D = 0.0;
 
   auto bail = [&](sn_status st) {
     g_tls_error = g->err;
@@ -569,12 +608,8 @@ sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, 
 sn_status sn_set_kernel(sn_grid g, const sn_kernel* k) {
   if (!g) return fail(nullptr, SN_EINVAL, "sn_set_kernel: grid is NULL");
   if (!k) return fail(g, SN_EINVAL, "sn_set_kernel: kernel is NULL");
-  if (!std::isfinite(k->coeff_lap) || !std::isfinite(k->G) || !std::isfinite(k->alpha_Y) ||
-      !std::isfinite(k->lambda_Y) || !std::isfinite(k->g_local))
-    return fail(g, SN_EINVAL, "sn_set_kernel: parameters must be finite");
-  if (k->alpha_Y != 0.0 && !(k->lambda_Y > 0.0))
-    return fail(g, SN_EINVAL, "sn_set_kernel: lambda_Y must be > 0 when alpha_Y != 0");
-  if (k->zero_k0 != 1) return fail(g, SN_EINVAL, "sn_set_kernel: zero_k0 must be 1");
+  if (const char* why = kernel_invalid(*k))
+    return fail(g, SN_EINVAL, std::string("sn_set_kernel: ") + why);
   cudaError_t e = cudaStreamSynchronize(g->stream);  // queued steps still read the old vext
   if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamSynchronize");
   if (k->v_ext) {
@@ -680,11 +715,10 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
               launch_fft_f64(g->n[a], lg.strided, -1, w, lg.outer, lg.inner,
                              g->tw64[log2i(g->n[a])], g->stream));
   }
-  const double mu2 = (g->kp.alpha_Y != 0.0) ? 1.0 / (g->kp.lambda_Y * g->kp.lambda_Y) : 1.0;
-  const double cN = kernel_cN(g, 1.0);
+  const GreenCoeffs gc = green_coeffs(g->kp);
   const double* k2[3] = {g->k2_64[0], g->k2_64[1], g->k2_64[2]};
   SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
-            launch_obs_green(w, g->n, d, k2, cN, cN * g->kp.alpha_Y, mu2, g->partials, g->stream));
+            launch_obs_green(w, g->n, d, k2, gc.cN, gc.cY, gc.mu2, g->partials, g->stream));
   SN_LAUNCH(g, K_OBS, 0.0, launch_obs_finish(g->partials, Q_NUM, g->obs_out, g->stream));
   double q[Q_NUM];
   e = cudaMemcpyAsync(q, g->obs_out, sizeof(q), cudaMemcpyDeviceToHost, g->stream);

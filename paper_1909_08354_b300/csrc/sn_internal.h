@@ -56,6 +56,18 @@ struct RhoPassArgs {
 // Message returned by sn_last_error(NULL) on this thread.
 void set_thread_error(const char* msg);
 
+// The kernel of sn_kernel as K(k) = cN / k^2 + cY / (k^2 + mu2) for k != 0
+// (K(0) = 0), before any step or normalisation factor:
+//   NMC:     cN = -4 pi G, cY = -4 pi G alpha_Y, mu2 = 1/lambda_Y^2 (1 if alpha_Y = 0);
+//   POISSON: B D / (C - k^2) = cY / (k^2 + mu2) with cY = -B D, mu2 = -C (C < 0),
+//            or cN = -B D (C = 0).
+struct GreenCoeffs {
+  double cN, cY, mu2;
+};
+GreenCoeffs green_coeffs(const sn_kernel& k);
+// NULL if k is a valid kernel, else the reason (for an SN_EINVAL message).
+const char* kernel_invalid(const sn_kernel& k);
+
 // Per-device once-only settings (kernel attributes, SM counts) are kept in
 // arrays indexed by the current device, clamped to [0, kDeviceSlots).
 constexpr int kDeviceSlots = 64;

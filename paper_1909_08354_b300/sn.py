@@ -19,6 +19,7 @@ LIB_PATH = os.environ.get("SN_LIB_PATH") or os.path.join(_HERE, "libsn.so")
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 SN_ENGINE_FP32, SN_ENGINE_TC16 = 0, 1
 SN_C64, SN_C128 = 0, 1
+SN_KERNEL_NMC, SN_KERNEL_POISSON = 0, 1
 _STATUS = {0: "SN_OK", -1: "SN_EINVAL", -2: "SN_ENOMEM", -3: "SN_ECUDA", -4: "SN_ETIMEOUT",
            -5: "SN_ENONFINITE", -6: "SN_ENOTSUP"}
 
@@ -27,7 +28,17 @@ class SnKernel(ctypes.Structure):
     _fields_ = [("coeff_lap", ctypes.c_double), ("G", ctypes.c_double),
                 ("alpha_Y", ctypes.c_double), ("lambda_Y", ctypes.c_double),
                 ("g_local", ctypes.c_double), ("zero_k0", ctypes.c_int),
-                ("v_ext", ctypes.c_void_p), ("v_ext_on_device", ctypes.c_int)]
+                ("v_ext", ctypes.c_void_p), ("v_ext_on_device", ctypes.c_int),
+                ("kind", ctypes.c_int), ("B", ctypes.c_double), ("C", ctypes.c_double),
+                ("D", ctypes.c_double)]
+
+
+def _kernel(coeff_lap=-0.5, G=1.0, alpha_Y=0.0, lambda_Y=1.0, g_local=0.0, zero_k0=1,
+            kind=SN_KERNEL_NMC, B=1.0, C=0.0, D=0.0) -> SnKernel:
+    """An sn_kernel without V_ext: SN_KERNEL_NMC uses G, alpha_Y, lambda_Y;
+    SN_KERNEL_POISSON uses B, C, D (see sn_kernel in include/sn.h)."""
+    return SnKernel(float(coeff_lap), float(G), float(alpha_Y), float(lambda_Y), float(g_local),
+                    int(zero_k0), None, 0, int(kind), float(B), float(C), float(D))
 
 
 class SnObs(ctypes.Structure):
@@ -171,9 +182,9 @@ def sn_create_grid(n: Sequence[int], L: Sequence[float], dtype: int = SN_C64, st
 
 
 def sn_set_kernel(g, coeff_lap=-0.5, G=1.0, alpha_Y=0.0, lambda_Y=1.0, g_local=0.0,
-                  v_ext=None, zero_k0=1):
+                  v_ext=None, zero_k0=1, kind=SN_KERNEL_NMC, B=1.0, C=0.0, D=0.0):
     keep = None
-    k = SnKernel(coeff_lap, G, alpha_Y, lambda_Y, g_local, zero_k0, None, 0)
+    k = _kernel(coeff_lap, G, alpha_Y, lambda_Y, g_local, zero_k0, kind, B, C, D)
     if v_ext is not None:
         if _is_torch(v_ext):
             import torch
@@ -238,14 +249,15 @@ def sn_profile_step(g, dt: float, nsteps: int) -> dict:
 
 
 def sn_step_2d_noalloc(psi, L, dt: float, nsteps: int, coeff_lap=-0.5, G=1.0, alpha_Y=0.0,
-                       lambda_Y=1.0, g_local=0.0, stream=None):
+                       lambda_Y=1.0, g_local=0.0, stream=None, kind=SN_KERNEL_NMC, B=1.0, C=0.0,
+                       D=0.0):
     """In-place steps of a 2D complex64 CUDA tensor psi (ny, nx) without device
     allocation (see sn_step_2d_noalloc in include/sn.h)."""
     import torch
     if not (_is_torch(psi) and psi.is_cuda and psi.dtype == torch.complex64 and psi.dim() == 2
             and psi.is_contiguous()):
         raise ValueError("psi must be a contiguous 2D complex64 CUDA tensor")
-    k = SnKernel(coeff_lap, G, alpha_Y, lambda_Y, g_local, 1, None, 0)
+    k = _kernel(coeff_lap, G, alpha_Y, lambda_Y, g_local, 1, kind, B, C, D)
     st = lib().sn_step_2d_noalloc(psi.data_ptr(), psi.shape[0], psi.shape[1], float(L[0]),
                                   float(L[1]), ctypes.byref(k), float(dt), int(nsteps),
                                   ctypes.c_void_p(stream) if stream else None)
@@ -280,8 +292,10 @@ def sn_set_kernel_batch(b, kernels):
     """kernels: sequence of dicts with the keyword arguments of sn_set_kernel."""
     arr = (SnKernel * len(kernels))()
     for i, kw in enumerate(kernels):
-        arr[i] = SnKernel(kw.get("coeff_lap", -0.5), kw.get("G", 1.0), kw.get("alpha_Y", 0.0),
-                          kw.get("lambda_Y", 1.0), kw.get("g_local", 0.0), 1, None, 0)
+        arr[i] = _kernel(kw.get("coeff_lap", -0.5), kw.get("G", 1.0), kw.get("alpha_Y", 0.0),
+                         kw.get("lambda_Y", 1.0), kw.get("g_local", 0.0), 1,
+                         kw.get("kind", SN_KERNEL_NMC), kw.get("B", 1.0), kw.get("C", 0.0),
+                         kw.get("D", 0.0))
     _check(None, lib().sn_set_kernel_batch(b, arr))
 
 

@@ -183,6 +183,86 @@ def test_yukawa_only_screened_poisson_residual_by_finite_differences():
     assert np.abs(res).max() < 1e-6 * np.abs(src).max()
 
 
+def yukawa_gaussian_free_space(r, s, mu):
+    """int exp(-|y|^2/s^2) exp(-mu |x - y|) / |x - y| dy at |x| = r > 0 (3D), the
+    textbook screened potential of a Gaussian charge of per-axis variance
+    sig^2 = s^2/2 and total pi^(3/2) s^3:
+      M0 e^(mu^2 sig^2/2) / (2r) [e^(-mu r) erfc((mu sig^2 - r)/(sig sqrt 2))
+                                  - e^(mu r) erfc((mu sig^2 + r)/(sig sqrt 2))]."""
+    from scipy.special import erfc
+    sig = s / np.sqrt(2.0)
+    m0 = np.pi ** 1.5 * s ** 3
+    a = np.exp(-mu * r) * erfc((mu * sig * sig - r) / (sig * np.sqrt(2.0)))
+    b = np.exp(mu * r) * erfc((mu * sig * sig + r) / (sig * np.sqrt(2.0)))
+    return m0 * np.exp(mu * mu * sig * sig / 2.0) / (2.0 * r) * (a - b)
+
+
+def test_poisson_kind_matches_free_space_screened_gaussian():
+    """Eq. 2 with C = -mu^2 < 0 in 3D: lap(phi) - mu^2 phi = D rho has the Green's function
+    -exp(-mu r)/(4 pi r), so phi = -(D/4 pi) (Yukawa potential of rho).  The box is many
+    screening lengths wide, so periodic images are negligible; removing k = 0 subtracts the
+    box mean D M0 / (C L^3).  The kinetic-free potential is B phi."""
+    n, Lb = 64, 32.0
+    L = (Lb, Lb, Lb)
+    s, mu, B, D = 1.5, 1.2, 0.8, -2.5
+    C = -mu * mu
+    x = W.coords(n, Lb)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    rho = np.exp(-(X * X + Y * Y + Z * Z) / (s * s))
+    V = O.potential(rho, L, kind=O.KIND_POISSON, B=B, C=C, D=D)
+    c = n // 2  # x = 0 is the node n/2
+    r = x[c + 1:c + 13]  # 0.5 .. 6
+    m0 = np.pi ** 1.5 * s ** 3
+    ref = B * (-(D / (4 * np.pi)) * yukawa_gaussian_free_space(r, s, mu) - D * m0 / (C * Lb ** 3))
+    got = V[c, c, c + 1:c + 13]
+    assert np.abs(got - ref).max() < 1e-8 * np.abs(ref).max()
+
+
+def test_poisson_kind_residual_by_finite_differences():
+    """(lap + C) V = B D (rho - <rho>) for KIND_POISSON (k = 0 removed), checked on a fine
+    1D-like grid with a 4th-order finite-difference Laplacian, independent of the spectral k^2.
+    The parameters are those of a nematic liquid crystal, Eq. 5 (nu lap theta - 2 q theta =
+    -2 rho): C = -2q/nu, D = -2/nu."""
+    n, L = (8, 512), (1.0, 24.0)
+    x = W.coords(n[1], L[1])
+    rho = np.tile(np.exp(-x ** 2 / 3.0), (n[0], 1))
+    nu, q, B = 1.5, 0.6, 0.9
+    C, D = -2 * q / nu, -2 / nu
+    V = O.potential(rho, L, kind=O.KIND_POISSON, B=B, C=C, D=D)[0]
+    dx = L[1] / n[1]
+    lap = (-np.roll(V, 2) + 16 * np.roll(V, 1) - 30 * V + 16 * np.roll(V, -1)
+           - np.roll(V, -2)) / (12 * dx * dx)
+    src = B * D * (rho[0] - rho[0].mean())
+    assert np.abs(lap + C * V - src).max() < 1e-6 * np.abs(src).max()
+
+
+def test_poisson_kind_unscreened_limit_is_newton():
+    """C = 0, B D = 4 pi G: Eq. 2 is Newton's law, the alpha_Y = 0 kernel of Eq. 14."""
+    rho = np.abs(crand((16, 8, 32))) ** 2
+    L = (3.0, 4.0, 5.0)
+    G = 1.7
+    Vp = O.potential(rho, L, kind=O.KIND_POISSON, B=2.0, C=0.0, D=4 * np.pi * G / 2.0)
+    Vn = O.potential(rho, L, G=G)
+    assert np.abs(Vp - Vn).max() < 1e-13 * np.abs(Vn).max()
+
+
+def test_thermo_optical_index_peaks_on_the_beam():
+    """Eq. 4, lap(dn) - dn/sigma^2 = -(zeta mu/kappa)|E|^2 with zeta mu/kappa > 0: the index
+    change (B = 1) is largest where the intensity is, and smallest far from the beam."""
+    n, L = (64, 64), (30.0, 30.0)
+    x = W.coords(n[0], L[0])
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    rho = np.exp(-(X * X + Y * Y) / 4.0)
+    dn = O.potential(rho, L, kind=O.KIND_POISSON, B=1.0, C=-1.0 / 9.0, D=-0.5)
+    assert dn[32, 32] == dn.max()
+    assert dn[0, 0] == pytest.approx(dn.min(), rel=1e-6)
+
+
+def test_poisson_kind_rejects_antiscreening():
+    with pytest.raises(ValueError):
+        O.green_multiplier((8, 8), (1.0, 1.0), kind=O.KIND_POISSON, B=1.0, C=0.5, D=1.0)
+
+
 # ----------------------------------------------------------------------------
 # Nonlinear sub-step
 # ----------------------------------------------------------------------------

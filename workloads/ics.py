@@ -36,14 +36,19 @@ class Lump:
 class KernelParams:
     """Parameters of the potential and the local term.
 
-    Green's multiplier K(k) = -4 pi G [1/k^2 + alpha_Y/(k^2 + 1/lambda_Y^2)],
-    K(0) := 0; local term g |psi|^2; Laplacian coefficient A (Eq. 1).
+    kind 0: Green's multiplier K(k) = -4 pi G [1/k^2 + alpha_Y/(k^2 + 1/lambda_Y^2)];
+    kind 1: Eq. 2 with constants B, C <= 0, D, K(k) = B D / (C - k^2);
+    K(0) := 0 for both; local term g |psi|^2; Laplacian coefficient A (Eq. 1).
     """
     G: float = 1.0
     alpha_Y: float = 0.0
     lambda_Y: float = 1.0
     g_local: float = 0.0
     coeff_lap: float = -0.5
+    kind: int = 0
+    B: float = 1.0
+    C: float = 0.0
+    D: float = 0.0
 
 
 @dataclass
@@ -155,6 +160,27 @@ def scan_instance_2d(i: int, sizes: Sequence[int] = SCAN_SIZES, L: float = 40.0,
                      g_local=r.uniform(0.0, 0.05))
     return Workload(f"scan2d_{i}_{n}", (n, n), (L, L), lumps, k, dt, nsteps,
                     meta={"seed": seed, "index": i})
+
+
+def optical_beams_2d(n: int = 1024, L: float = 100.0, seed: int = 6000, sigma_nl: float = 5.0,
+                     zeta_mu_over_kappa: float = 2.0, dt: float = 1e-2,
+                     nsteps: int = 500) -> Workload:
+    """Beams in a thermo-optical medium (Eq. 3 with the nonlocal index of Eq. 4):
+    2 to 6 Gaussian beams (waist U[2, 4], amplitude U[0.5, 1], centres uniform,
+    transverse tilts N(0, 0.3)) in the transverse plane, nonlocal length
+    sigma_nl; kernel kind 1 with C = -1/sigma_nl^2, D = -zeta mu / kappa, B = 1."""
+    r = SplitMix64(seed)
+    nb = r.randint(2, 6)
+    lumps = []
+    for _ in range(nb):
+        sigma = r.uniform(2.0, 4.0)
+        amp = r.uniform(0.5, 1.0)
+        centre = tuple(r.uniform(-0.5 * L, 0.5 * L) for _ in range(2))
+        vel = tuple(r.normal(0.0, 0.3) for _ in range(2))
+        lumps.append(Lump(centre, sigma, amp, vel))
+    k = KernelParams(G=0.0, g_local=0.0, kind=1, B=1.0, C=-1.0 / (sigma_nl * sigma_nl),
+                     D=-zeta_mu_over_kappa)
+    return Workload(f"optical2d_{n}", (n, n), (L, L), lumps, k, dt, nsteps, meta={"seed": seed})
 
 
 def random_small(n: Sequence[int], seed: int, L: float | Sequence[float] = 10.0,
