@@ -180,15 +180,17 @@ __device__ __forceinline__ const float* potential_c2r(const cx<float>* rtile, cx
 }
 
 // psi <- exp(-i (V h + V_ext h + g h |psi|^2)) psi.  The angle is reduced to
-// r in [-pi, pi] with a two-part 2 pi, and past pi/2 to r - pi (the rotation
-// is then negated).  The rotation by -r is three shears, x1 = x + T y,
-// y1 = y - S x1, x2 = x1 + T y1 with T = tan(r/2), S = sin r from the SFU
-// sine and cosine of r/2: each shear has determinant 1, so the rounded T and
-// S move the angle by ~1e-7 but not the norm.  A rotation by a rounded
-// (cos r, sin r) pair would change the norm by c^2 + s^2 - 1, which neither
-// the SFU pair nor a Newton step towards unit modulus keeps unbiased at small
-// angles (the step's rounding left a mean of -3e-8 per application, a mass
-// drift of -1.6e-8 per step under a strong nonlocal potential).
+// [-pi, pi] with a two-part 2 pi and the SFU sine and cosine are taken there.
+// The pair is then pulled towards unit modulus by one Newton step,
+// (c, s) <- (c, s)(1 - eta/2) with eta = c^2 + s^2 - 1, applied as c + c e so
+// that a correction below an ulp of c is not rounded away against 1 + e.
+// eta is formed without cancellation: the larger of |c|, |s| (call it b)
+// enters as (b - 1)(b + 1), exact up to one rounding, since one factor is
+// exact.  Computed as fma(c, c, fma(s, s, -1)) instead, eta carried the
+// rounding of s^2 - 1 to the grid near -1, and the corrected pair was biased
+// low by ~3e-8 at angles below 0.03: a mass drift of -1.6e-8 per step under a
+// strong nonlocal potential (Eq. 4).  The bias is now ~1e-10 (+3e-9 below
+// 1e-3 rad, where c itself rounds one-sidedly to the grid at 1).
 template <int E, int T>
 __device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float* vrow,
                                                 float gh, const float* vx, float h,
@@ -200,20 +202,14 @@ __device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float* 
     const float kq = rintf(th * 0.159154943091895336f);
     float r = fmaf(-kq, 6.28318548202514648f, th);
     r = fmaf(-kq, -1.74845553e-7f, r);
-    const bool flip = fabsf(r) > 1.57079632679489662f;
-    if (flip) {  // r -+ pi with a two-part pi
-      const float sg = r > 0.f ? 1.f : -1.f;
-      r = fmaf(-sg, 3.14159274101257324f, r);
-      r = fmaf(sg, 8.74227766e-8f, r);
-    }
-    float sh, ch;
-    __sincosf(0.5f * r, &sh, &ch);  // |r/2| <= pi/4: ch >= 0.707
-    const float tq = __fdividef(sh, ch);
-    const float sq = 2.f * sh * ch;
-    const float x1 = fmaf(tq, v[m].im, v[m].re);
-    const float y1 = fmaf(-sq, x1, v[m].im);
-    const float x2 = fmaf(tq, y1, x1);
-    v[m] = flip ? cx<float>{-x2, -y1} : cx<float>{x2, y1};
+    float sn, cs;
+    __sincosf(r, &sn, &cs);
+    const bool cbig = fabsf(cs) >= fabsf(sn);
+    const float b = cbig ? cs : sn, a = cbig ? sn : cs;
+    const float e = -0.5f * fmaf(a, a, (b - 1.f) * (b + 1.f));
+    cs = fmaf(cs, e, cs);
+    sn = fmaf(sn, e, sn);
+    v[m] = {v[m].re * cs + v[m].im * sn, v[m].im * cs - v[m].re * sn};  // v * exp(-i th)
   }
 }
 
