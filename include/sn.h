@@ -112,6 +112,43 @@ sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, 
  * alpha_Y != 0 (NMC), C > 0 (POISSON), or zero_k0 != 1. */
 sn_status sn_set_kernel(sn_grid g, const sn_kernel* k);
 
+/* Self-gravitating fluid of Sec. II B: the Madelung form of the continuity
+ * and Euler equations of a polytropic fluid (P = w rho^n) with gravity from
+ * General Relativity's Newtonian limit or from the pure non-minimal
+ * matter-curvature coupling (alpha = 0), Eq. 16:
+ *     i nu psi_t = -(nu^2/2) lap psi + [nu^2 V_B + phi_N + phi_C + V_p] psi,
+ *   V_B = lap(sqrt rho) / (2 sqrt rho)                       (Bohm potential),
+ *   lap phi_N = beta(r) lap rho + gamma(r) rho, k = 0 removed      (Eq. 15),
+ *   phi_C = ln[1 - (r0/(r + r0))^lambda]                           (Eq. 13),
+ *   V_p = w ln rho (n = 1) or n w/(n - 1) rho^(n - 1)              (Eq. 17),
+ *   GR:  gamma = 1/2, beta = 0, phi_C = 0;
+ *   NMC: gamma = (1 - q)/2, beta = lambda q/(r + r0), q = (r0/(r + r0))^lambda
+ *        (Eqs. 11-12), r0 = M / (4 pi),
+ * rho = |psi|^2, r the distance from the box centre (the node x = 0), taken
+ * as at least half the smallest grid spacing (phi_C is -infinite at r = 0);
+ * sqrt rho and ln rho use max(rho, rho_floor). */
+typedef enum { SN_GRAVITY_GR = 0, SN_GRAVITY_NMC = 1 } sn_gravity;
+typedef struct {
+  double nu;        /* > 0: the analogue of hbar, psi = sqrt(rho) exp(i Phi / nu) */
+  double w;         /* polytropic coefficient                                    */
+  double n_poly;    /* polytropic exponent (any finite value)                    */
+  int model;        /* sn_gravity                                                */
+  double lambda;    /* NMC: coupling strength (> 0)                              */
+  double M;         /* NMC: mass setting r0 = M / (4 pi) (> 0)                   */
+  double rho_floor; /* > 0                                                       */
+} sn_fluid;
+
+/* Switch an SN_C128 grid to the fluid model of Eq. 16 (f != NULL) or back
+ * to Eqs. 1-2 (f == NULL; sn_set_kernel also switches back).  sn_step then
+ * takes symmetric split steps of Eq. 16: Kin(h/2) with A = -nu/2, the exact
+ * potential sub-step psi exp(-i U h / nu) (U depends on rho only), Kin(h/2).
+ * The profiles gamma, beta, phi_C are built once here, in FP64 on the host.
+ * In this mode sn_observables reports mass, e_kin (with A = -nu/2),
+ * centroids and momenta; e_pot and e_nl are 0.  Errors: SN_ENOTSUP on SN_C64
+ * grids (this build steps Eq. 16 in FP64 only), SN_EINVAL for bad values,
+ * SN_ENOMEM, SN_ECUDA. */
+sn_status sn_set_fluid(sn_grid g, const sn_fluid* f);
+
 /* Copy a state in: psi holds ncells complex values of the grid's dtype,
  * host memory (on_device = 0; the call returns after the copy) or device
  * memory (on_device = 1; ordered on the grid's stream).  Resets the step

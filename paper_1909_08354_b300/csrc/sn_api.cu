@@ -162,6 +162,13 @@ struct sn_grid_s {
   double* vext64 = nullptr;
   bool has_vext = false;
 
+  // self-gravitating fluid (Eq. 16), SN_C128 grids: parameters, profiles
+  // gamma, beta, phi_C per cell (NMC only), and a third FP64 scratch array
+  bool fluid = false;
+  sn_fluid fl{};
+  double* prof64[3] = {};
+  double2* w64c = nullptr;
+
   // line-transform engine: SN_ENGINE_FP32, or SN_ENGINE_TC16 (tensor cores on
   // 256-point axes; tc_frag holds its FP16 fragment tables)
   int engine = SN_ENGINE_FP32;
@@ -473,13 +480,68 @@ sn_status step_f64(sn_grid g, double dt, int nsteps) {
   return SN_OK;
 }
 
+// Symmetric split steps of Eq. 16 (Sec. II B) on a complex128 grid: the
+// kinetic half steps use A = -nu/2 (set by sn_set_fluid); the potential
+// sub-step forms rho and sqrt(rho), their spectral Laplacians, the source of
+// Eq. 15 and its inverse Laplacian, then turns psi by U h / nu.
+sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
+  sn_status st = ensure_f64_scratch(g);
+  if (st != SN_OK) return st;
+  if (!g->w64c) {
+    cudaError_t e = dalloc(g, &g->w64c, (size_t)g->cells);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMalloc(fluid scratch)");
+  }
+  double2* psi = reinterpret_cast<double2*>(g->psi);
+  double2* w = g->w64b;   // rho -> lap rho -> source -> phi_N
+  double2* wa = g->w64c;  // sqrt rho -> lap sqrt rho
+  const double* k2[3] = {g->k2_64[0], g->k2_64[1], g->k2_64[2]};
+  const double inv_n = 1.0 / (double)g->cells;
+  const bool nmc = g->fl.model == SN_GRAVITY_NMC;
+  FluidPhase fp{};
+  fp.nu = g->fl.nu;
+  fp.h_over_nu = dt / g->fl.nu;
+  fp.w = g->fl.w;
+  fp.n_poly = g->fl.n_poly;
+  fp.cp = g->fl.n_poly == 1.0 ? 0.0 : g->fl.n_poly * g->fl.w / (g->fl.n_poly - 1.0);
+  fp.rho_floor = g->fl.rho_floor;
+  const double ew = 32.0 * g->cells;
+  for (int s = 0; s < nsteps; ++s) {
+    if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
+    SN_LAUNCH(g, K_F64_EW, 48.0 * g->cells,
+              launch_fluid_prep_f64(psi, w, wa, fp.rho_floor, g->cells, g->stream));
+    // Bohm: lap(sqrt rho)
+    if ((st = fftn_f64(g, wa, -1)) != SN_OK) return st;
+    SN_LAUNCH(g, K_F64_EW, ew, launch_lap_mult_f64(wa, g->n, g->ndim, k2, inv_n, g->stream));
+    if ((st = fftn_f64(g, wa, +1)) != SN_OK) return st;
+    // Eq. 15: lap rho (NMC only), source, inverse Laplacian
+    if (nmc) {
+      if ((st = fftn_f64(g, w, -1)) != SN_OK) return st;
+      SN_LAUNCH(g, K_F64_EW, ew, launch_lap_mult_f64(w, g->n, g->ndim, k2, inv_n, g->stream));
+      if ((st = fftn_f64(g, w, +1)) != SN_OK) return st;
+    }
+    SN_LAUNCH(g, K_F64_EW, ew,
+              launch_fluid_source_f64(psi, w, nmc ? g->prof64[0] : nullptr,
+                                      nmc ? g->prof64[1] : nullptr, g->cells, g->stream));
+    if ((st = fftn_f64(g, w, -1)) != SN_OK) return st;
+    SN_LAUNCH(g, K_F64_EW, ew,
+              launch_green_f64(w, g->n, g->ndim, k2, -inv_n, 0.0, 1.0, g->stream));
+    if ((st = fftn_f64(g, w, +1)) != SN_OK) return st;
+    SN_LAUNCH(g, K_F64_EW, (nmc ? 56.0 : 48.0) * g->cells,
+              launch_fluid_phase_f64(psi, w, wa, nmc ? g->prof64[2] : nullptr, fp, g->cells,
+                                     g->stream));
+    if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
+  }
+  return SN_OK;
+}
+
 sn_status do_step(sn_grid g, double dt, int nsteps) {
   if (!std::isfinite(dt)) return fail(g, SN_EINVAL, "sn_step: dt must be finite");
   if (nsteps < 0) return fail(g, SN_EINVAL, "sn_step: nsteps must be >= 0");
   if (nsteps == 0) return SN_OK;
   sn_status st = ensure_mult_tables(g, dt);
   if (st != SN_OK) return st;
-  st = (g->dtype == SN_C64) ? step_f32(g, dt, nsteps) : step_f64(g, dt, nsteps);
+  if (g->fluid) st = step_fluid_f64(g, dt, nsteps);
+  else st = (g->dtype == SN_C64) ? step_f32(g, dt, nsteps) : step_f64(g, dt, nsteps);
   if (st == SN_OK) g->step += nsteps;
   return st;
 }
@@ -636,7 +698,67 @@ sn_status sn_set_kernel(sn_grid g, const sn_kernel* k) {
   const double oldA = g->kp.coeff_lap;
   g->kp = *k;
   g->kp.v_ext = nullptr;
+  g->fluid = false;
   if (oldA != k->coeff_lap) g->mult_dt = std::nan("");
+  return SN_OK;
+}
+
+sn_status sn_set_fluid(sn_grid g, const sn_fluid* f) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_set_fluid: grid is NULL");
+  if (!f) {
+    g->fluid = false;
+    return SN_OK;
+  }
+  if (g->dtype != SN_C128)
+    return fail(g, SN_ENOTSUP, "sn_set_fluid: the fluid model runs on complex128 grids");
+  if (!(f->nu > 0.0) || !std::isfinite(f->nu) || !std::isfinite(f->w) ||
+      !std::isfinite(f->n_poly) || !(f->rho_floor > 0.0) || !std::isfinite(f->rho_floor))
+    return fail(g, SN_EINVAL, "sn_set_fluid: nu and rho_floor must be finite and > 0, w and n finite");
+  if (f->model != SN_GRAVITY_GR && f->model != SN_GRAVITY_NMC)
+    return fail(g, SN_EINVAL, "sn_set_fluid: model must be SN_GRAVITY_GR or SN_GRAVITY_NMC");
+  if (f->model == SN_GRAVITY_NMC && (!(f->lambda > 0.0) || !std::isfinite(f->lambda) ||
+                                     !(f->M > 0.0) || !std::isfinite(f->M)))
+    return fail(g, SN_EINVAL, "sn_set_fluid: NMC needs finite lambda > 0 and M > 0");
+  cudaError_t e = cudaStreamSynchronize(g->stream);  // queued steps still read the old profiles
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamSynchronize");
+  if (f->model == SN_GRAVITY_NMC) {
+    // gamma, beta, phi_C of Eqs. 11-13 at r = max(|x|, h_min / 2), x from the box centre
+    const int d = g->ndim;
+    double hmin = g->L[0] / g->n[0];
+    for (int a = 1; a < d; ++a) hmin = std::min(hmin, g->L[a] / g->n[a]);
+    const double r0 = f->M / (4.0 * kPi);
+    std::vector<double> gam((size_t)g->cells), bet((size_t)g->cells), phc((size_t)g->cells);
+    const int n0 = d == 3 ? g->n[0] : 1, n1 = d == 3 ? g->n[1] : g->n[0], n2 = d == 3 ? g->n[2] : g->n[1];
+    const double L0 = d == 3 ? g->L[0] : 1.0, L1 = d == 3 ? g->L[1] : g->L[0], L2 = d == 3 ? g->L[2] : g->L[1];
+    size_t c = 0;
+    for (int i0 = 0; i0 < n0; ++i0) {
+      const double x0 = d == 3 ? -0.5 * L0 + i0 * (L0 / n0) : 0.0;
+      for (int i1 = 0; i1 < n1; ++i1) {
+        const double x1 = -0.5 * L1 + i1 * (L1 / n1);
+        for (int i2 = 0; i2 < n2; ++i2, ++c) {
+          const double x2 = -0.5 * L2 + i2 * (L2 / n2);
+          const double r = std::max(std::sqrt(x0 * x0 + x1 * x1 + x2 * x2), 0.5 * hmin);
+          const double q = std::pow(r0 / (r + r0), f->lambda);
+          gam[c] = 0.5 * (1.0 - q);
+          bet[c] = f->lambda * q / (r + r0);
+          phc[c] = std::log1p(-q);
+        }
+      }
+    }
+    std::vector<double>* src[3] = {&gam, &bet, &phc};
+    for (int k = 0; k < 3; ++k) {
+      if (!g->prof64[k] && (e = dalloc(g, &g->prof64[k], (size_t)g->cells)) != cudaSuccess)
+        return cuda_fail(g, e, "cudaMalloc(fluid profiles)");
+      if ((e = cudaMemcpy(g->prof64[k], src[k]->data(), src[k]->size() * sizeof(double),
+                          cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(g, e, "cudaMemcpy(fluid profiles)");
+    }
+  }
+  g->fl = *f;
+  g->fluid = true;
+  const double A = -0.5 * f->nu;
+  if (g->kp.coeff_lap != A) g->mult_dt = std::nan("");
+  g->kp.coeff_lap = A;
   return SN_OK;
 }
 
@@ -738,8 +860,8 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
     out->centroid[a] = g->L[a] / (2.0 * kPi) * std::atan2(q[Q_SX0 + 2 * a3], q[Q_CX0 + 2 * a3]);
   }
   out->e_kin = -g->kp.coeff_lap * dV * ek;
-  out->e_pot = 0.5 * dV / N * q[Q_EPOT] + dV * q[Q_VEXT];
-  out->e_nl = 0.5 * g->kp.g_local * dV * q[Q_RHO2];
+  out->e_pot = g->fluid ? 0.0 : 0.5 * dV / N * q[Q_EPOT] + dV * q[Q_VEXT];
+  out->e_nl = g->fluid ? 0.0 : 0.5 * g->kp.g_local * dV * q[Q_RHO2];
   out->e_total = out->e_kin + out->e_pot + out->e_nl;
   out->step = g->step;
   for (int i = 0; i < Q_NUM; ++i)

@@ -100,6 +100,22 @@ cudaError_t launch_phase_f64(double2* psi, const double2* w, const double* vext,
 cudaError_t launch_widen_f32_to_f64(const float2* in, double2* out, long long cells,
                                     cudaStream_t s);
 
+// ---- self-gravitating fluid, Eq. 16 (FP64, fluid_f64.cu) -------------------
+struct FluidPhase {
+  double nu, h_over_nu;  // psi <- psi exp(-i U h / nu)
+  double w, n_poly, cp;  // V_p = w ln rho (n = 1) or cp rho^(n-1), cp = n w / (n - 1)
+  double rho_floor;      // floor of rho under sqrt and ln
+};
+cudaError_t launch_fluid_prep_f64(const double2* psi, double2* w, double2* wa, double floor,
+                                  long long cells, cudaStream_t s);
+cudaError_t launch_lap_mult_f64(double2* w, const int* n, int ndim, const double* const* k2,
+                                double scale, cudaStream_t s);
+cudaError_t launch_fluid_source_f64(const double2* psi, double2* w, const double* gamma,
+                                    const double* beta, long long cells, cudaStream_t s);
+cudaError_t launch_fluid_phase_f64(double2* psi, const double2* wphi, const double2* wlap,
+                                   const double* phi_c, const FluidPhase& p, long long cells,
+                                   cudaStream_t s);
+
 // ---- observables (FP64) ----------------------------------------------------
 enum ObsQ {
   Q_MASS = 0, Q_RHO2, Q_VEXT, Q_CX0, Q_SX0, Q_CX1, Q_SX1, Q_CX2, Q_SX2,

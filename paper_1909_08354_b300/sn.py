@@ -41,6 +41,15 @@ def _kernel(coeff_lap=-0.5, G=1.0, alpha_Y=0.0, lambda_Y=1.0, g_local=0.0, zero_
                     int(zero_k0), None, 0, int(kind), float(B), float(C), float(D))
 
 
+SN_GRAVITY_GR, SN_GRAVITY_NMC = 0, 1
+
+
+class SnFluid(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("w", ctypes.c_double), ("n_poly", ctypes.c_double),
+                ("model", ctypes.c_int), ("lambda_", ctypes.c_double), ("M", ctypes.c_double),
+                ("rho_floor", ctypes.c_double)]
+
+
 class SnObs(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("e_kin", ctypes.c_double),
                 ("e_pot", ctypes.c_double), ("e_nl", ctypes.c_double),
@@ -74,6 +83,7 @@ _SIGNATURES = [
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     ("sn_kind_name", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_set_engine", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_set_fluid", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SnFluid)]),
     ("sn_test_line_fft_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("sn_step_2d_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -556,6 +566,17 @@ class Grid:
 
     def observables(self) -> dict:
         return sn_observables(self.h)
+
+    def set_fluid(self, nu=1.0, w=1.02, n_poly=1.0, model=SN_GRAVITY_NMC, lam=1.0, M=25.0,
+                  rho_floor=1e-12, off=False):
+        """Eq. 16 (self-gravitating fluid, GR or NMC) on a complex128 grid; off=True
+        returns to Eqs. 1-2 (see sn_set_fluid in include/sn.h)."""
+        if off:
+            _check(self.h, lib().sn_set_fluid(self.h, None))
+            return
+        f = SnFluid(float(nu), float(w), float(n_poly), int(model), float(lam), float(M),
+                    float(rho_floor))
+        _check(self.h, lib().sn_set_fluid(self.h, ctypes.byref(f)))
 
     def set_engine(self, engine: int):
         """SN_ENGINE_FP32 or SN_ENGINE_TC16 (tensor cores on 256-point axes)."""

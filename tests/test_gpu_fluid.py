@@ -1,0 +1,140 @@
+"""The self-gravitating fluid model of Sec. II B (Eq. 16, GR and the pure
+non-minimal coupling) on complex128 grids, through the C-ABI, against the FP64
+oracle of oracle/cosmo_oracle.py.
+
+Bar: the plain FP64 path's, rel-L2 <= 1e-12 per split step from the same input
+(k steps: k times that); mass to 1e-12 relative (every sub-step is unitary).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.cosmo_oracle as C
+import workloads as W
+from paper_1909_08354_b300 import sn
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def gaussian_fluid(n, L, M0=25.0, sigma=3.0, seed=0):
+    """A Gaussian mass distribution of total mass M0 (Figs. 3-4) with a weak random
+    velocity field, so that no symmetry hides an axis or sign slip."""
+    d = len(n)
+    grids = np.meshgrid(*[W.coords(n[a], L[a]) for a in range(d)], indexing="ij")
+    r2 = sum(g * g for g in grids)
+    rho = M0 / (2 * math.pi * sigma * sigma) ** (d / 2) * np.exp(-r2 / (2 * sigma * sigma))
+    rng = np.random.default_rng(seed)
+    phase = sum(0.3 * rng.standard_normal() * np.sin(2 * math.pi * (a + 1) * grids[a] / L[a])
+                for a in range(d))
+    return np.sqrt(rho) * np.exp(1j * phase)
+
+
+def params(model, **kw):
+    base = dict(nu=1.0, w=1.02, n_poly=1.0, lam=1.0, M=25.0, rho_floor=1e-10)
+    base.update(kw)
+    return base
+
+
+def to_oracle(model, p):
+    return C.CosmoParams(nu=p["nu"], w=p["w"], n_poly=p["n_poly"], model=model, lam=p["lam"],
+                         M=p["M"], rho_floor=p["rho_floor"])
+
+
+def gpu_fluid(psi, L, model, p, dt, nsteps):
+    g = sn.Grid(psi.shape, L, "c128")
+    try:
+        g.set_fluid(model=model, **p)
+        g.set_state(psi)
+        g.step(dt, nsteps)
+        return g.get_state()
+    finally:
+        g.close()
+
+
+CASES = [
+    ("GR 2D", (64, 128), (24.0, 32.0), sn.SN_GRAVITY_GR, params(sn.SN_GRAVITY_GR)),
+    ("NMC 2D (Figs. 3-4 parameters)", (128, 128), (30.0, 30.0), sn.SN_GRAVITY_NMC,
+     params(sn.SN_GRAVITY_NMC)),
+    ("NMC 2D, n = 5/3, nu = 0.7", (64, 64), (24.0, 24.0), sn.SN_GRAVITY_NMC,
+     params(sn.SN_GRAVITY_NMC, n_poly=5.0 / 3.0, nu=0.7, lam=1.6, M=12.0)),
+    ("NMC 3D", (32, 32, 16), (24.0, 24.0, 20.0), sn.SN_GRAVITY_NMC,
+     params(sn.SN_GRAVITY_NMC, n_poly=2.0)),
+    ("GR 3D", (16, 32, 64), (20.0, 24.0, 28.0), sn.SN_GRAVITY_GR, params(sn.SN_GRAVITY_GR)),
+]
+
+
+@pytest.mark.parametrize("name,shape,L,model,p", CASES, ids=[c[0] for c in CASES])
+def test_fluid_steps_match_oracle(name, shape, L, model, p):
+    psi = gaussian_fluid(shape, L, seed=len(name))
+    dt = 0.01
+    for nsteps in (1, 3):
+        out = gpu_fluid(psi, L, model, p, dt, nsteps)
+        ref = C.cosmo_evolve(psi, dt, nsteps, L, to_oracle(model, p))
+        assert O.rel_l2(out, ref) <= nsteps * TOL, (nsteps, O.rel_l2(out, ref))
+    assert O.rel_l2(ref, psi) > 1e-4  # the steps move the state
+
+
+def test_fluid_mass_conservation_and_time_reversal():
+    shape, L = (128, 128), (30.0, 30.0)
+    psi = gaussian_fluid(shape, L, seed=5)
+    g = sn.Grid(shape, L, "c128")
+    try:
+        g.set_fluid(model=sn.SN_GRAVITY_NMC, **params(sn.SN_GRAVITY_NMC))
+        g.set_state(psi)
+        m0 = g.observables()["mass"]
+        g.step(0.01, 40)
+        obs = g.observables()
+        assert abs(obs["mass"] / m0 - 1) < 1e-12
+        assert obs["e_pot"] == 0.0 and obs["e_nl"] == 0.0
+        g.step(-0.01, 40)
+        back = g.get_state()
+    finally:
+        g.close()
+    assert np.abs(back - psi).max() < 1e-9 * np.abs(psi).max()
+
+
+def test_nmc_and_gr_differ_and_set_kernel_switches_back():
+    shape, L = (64, 64), (24.0, 24.0)
+    psi = gaussian_fluid(shape, L, seed=2)
+    gr = gpu_fluid(psi, L, sn.SN_GRAVITY_GR, params(sn.SN_GRAVITY_GR), 0.01, 20)
+    nmc = gpu_fluid(psi, L, sn.SN_GRAVITY_NMC, params(sn.SN_GRAVITY_NMC), 0.01, 20)
+    assert O.rel_l2(nmc, gr) > 1e-3
+    g = sn.Grid(shape, L, "c128")
+    try:
+        g.set_fluid(model=sn.SN_GRAVITY_NMC)
+        g.set_kernel(coeff_lap=-0.5, G=1.0, g_local=0.01)  # back to Eqs. 1-2
+        g.set_state(psi)
+        g.step(0.01, 2)
+        out = g.get_state()
+    finally:
+        g.close()
+    ref = O.evolve(psi, 0.01, 2, L, coeff_lap=-0.5, G=1.0, g_local=0.01)
+    assert O.rel_l2(out, ref) <= 2 * TOL
+
+
+@pytest.mark.parametrize("bad", [dict(nu=0.0), dict(rho_floor=0.0), dict(lam=-1.0), dict(M=0.0),
+                                 dict(model=5), dict(w=float("nan"))])
+def test_invalid_fluid_parameters_are_rejected(bad):
+    g = sn.Grid((8, 8), (1.0, 1.0), "c128")
+    try:
+        kw = dict(params(sn.SN_GRAVITY_NMC), model=sn.SN_GRAVITY_NMC)
+        kw.update(bad)
+        with pytest.raises(sn.SNError) as e:
+            g.set_fluid(**kw)
+        assert e.value.status == sn.SN_EINVAL
+    finally:
+        g.close()
+
+
+def test_fluid_needs_a_complex128_grid():
+    g = sn.Grid((8, 8), (1.0, 1.0), "c64")
+    try:
+        with pytest.raises(sn.SNError) as e:
+            g.set_fluid()
+        assert e.value.status == sn.SN_ENOTSUP
+    finally:
+        g.close()
