@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--engine", choices=["fp32", "tc16"], default="fp32",
                    help="line engine of the timed grid (tc16: tensor cores on 256-point axes)")
     p.add_argument("--no-fno", action="store_true")
+    p.add_argument("--no-fluid", action="store_true",
+                   help="skip the Eq. 16 fluid model (GR and NMC) on a 512^2 complex128 plane")
     p.add_argument("--no-optical", action="store_true",
                    help="skip the thermo-optical (Eq. 4) kernel on a 1024^2 plane")
     return p.parse_args()
@@ -318,6 +320,56 @@ def run_optical(sn, torch, stream, peak, steps=500):
                          "frac": gbs / peak, "bytes_per_cell_step": 48.0}}
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 (non-tensor) nominal rate; no measured FP64 peak
+
+
+def run_fluid(sn, torch, stream, n=512, L=40.0, steps=400, dt=1e-2):
+    """The self-gravitating fluid of Eq. 16 (Figs. 3-4 parameters: M0 = 25, nu = 1,
+    w = 1.02, n = 1, lambda = 1) on an n^2 complex128 grid: GR and NMC from the same
+    Gaussian, the NMC run timed.  The plain FP64 path: ten full complex FFTs per
+    NMC step (kinetic 4, Bohm 2, Eq. 15 4) at 5 N log2 N flops each."""
+    x = -0.5 * L + np.arange(n) * (L / n)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    r2 = X * X + Y * Y
+    sigma, M0 = 3.0, 25.0
+    psi0 = np.sqrt(M0 / (2 * np.pi * sigma ** 2) * np.exp(-r2 / (2 * sigma ** 2))).astype(np.complex128)
+
+    def summary(psi):
+        rho = np.abs(psi) ** 2
+        return {"rho_centre": float(rho[n // 2, n // 2]),
+                "mass_within_L_over_8": float(rho[np.sqrt(r2) <= L / 8].sum() / rho.sum())}
+
+    out = {"workload": f"fluid2d_{n}: {n}^2, L={L:g}, complex128, Gaussian sigma=3 of mass 25, "
+                       f"nu=1, w=1.02, n=1, lambda=1, dt={dt:g}, {steps} steps",
+           "initial": summary(psi0)}
+    for name, model in (("GR", sn.SN_GRAVITY_GR), ("NMC", sn.SN_GRAVITY_NMC)):
+        g = sn.Grid((n, n), (L, L), "c128", stream=stream.cuda_stream)
+        g.set_fluid(nu=1.0, w=1.02, n_poly=1.0, model=model, lam=1.0, M=M0, rho_floor=1e-12)
+        g.set_state(psi0)
+        m0 = g.observables()["mass"]
+        g.step(dt, 3)
+        g.set_state(psi0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(dt, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        final = g.get_state()
+        drift = g.observables()["mass"] / m0 - 1.0
+        g.close()
+        ffts = 10 if model == sn.SN_GRAVITY_NMC else 8
+        flops = ffts * 5.0 * n * n * np.log2(n * n)
+        out[name] = {"value": n * n * steps / t, "unit": "cell-steps/s",
+                     "ms_per_step": 1e3 * t / steps, "mass_drift": drift, "final": summary(final),
+                     "roofline": {"bound": "alu", "achieved": flops * steps / t / 1e12,
+                                  "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": flops * steps / t / 1e12 / FP64_NOMINAL_TFLOPS,
+                                  "peak_source": "nominal FP64"}}
+    return out
+
+
 def run_fno(sn, torch, stream, iters=10):
     """Training throughput of the FNO surrogate at its full size (256^2, width 64,
     24x24 modes, 4 layers, projection 128, batch 16): forward + loss + backward + Adam."""
@@ -501,6 +553,10 @@ def main():
     if not args.no_optical and world == 1:
         optical = run_optical(sn, torch, stream, peak)
 
+    fluid = None
+    if not args.no_fluid and world == 1:
+        fluid = run_fluid(sn, torch, stream)
+
     scan = None
     if not args.no_scan:
         scan = run_scan(sn, torch, stream, peak, args.scan_count, args.scan_steps)
@@ -543,6 +599,7 @@ def main():
             "cpu_baseline": cpu,
             "tensor_core_engine": tc,
             "optical_kernel": optical,
+            "fluid_model": fluid,
             "batched_scan": scan,
             "fno_surrogate": fno,
         }
