@@ -54,6 +54,17 @@ constexpr int min_ctas() {
   return want < 1 ? 1 : (want > 16 ? 16 : want);
 }
 
+// Programmatic dependent launch: the pass kernels of a step follow one
+// another on one stream, each reading what the previous one wrote.  Each
+// kernel lets the next one launch at once (its CTAs take SMs as this one's
+// CTAs retire and stage their constant tables), and waits for the previous
+// grid to complete, with its writes visible, before it touches psi or the
+// half spectrum.  Without a programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_allow_next() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 __device__ __forceinline__ cx<float> ldc(const float2* p) {
   const float2 v = *p;
   return {v.x, v.y};
@@ -128,6 +139,7 @@ psi_pass_kernel(PsiPassArgs a) {
   // bits (a grid holds at most 2^30 cells)
   const unsigned ustride = STRIDED ? (unsigned)a.inner : 1u;
 
+  pdl_allow_next();
   if constexpr (TC) {
     tc16::load_tabs(tabs, a.tc, a.tw, tid, NT);
     for (int k = tid; k < 2 * N; k += NT) mult_tc[(k / N) * tc16::MT + tc16::pt(k % N)] = a.mult[k];
@@ -135,6 +147,7 @@ psi_pass_kernel(PsiPassArgs a) {
     for (int k = tid; k < 2 * P::TWN; k += NT) tw_sm[k] = ldc(a.tw + k);
     for (int k = tid; k < N; k += NT) reinterpret_cast<float4*>(mult_sm)[k] = a.lift[k];
   }
+  pdl_wait_prev();  // psi and the half spectrum come from the previous pass
 
   // P1: stage the [k][line] half-spectrum tile of tile tau into shared memory
   auto stage_rho = [&](cx<float>* dst, long long tau) {
@@ -244,6 +257,7 @@ rho_pass_kernel(RhoPassArgs a) {
   const unsigned ustride = STRIDED ? (unsigned)a.inner : 1u;
   constexpr bool PF = E <= 16;  // register prefetch of the next tile
   constexpr bool CONTIG = !STRIDED;  // line l held by threads [l T, (l + 1) T)
+  pdl_allow_next();
   if constexpr (TC) {
     tc16::load_tabs(tabs, a.tc, a.tw, tid, NT);
     if constexpr (OP == RHO_GREEN)
@@ -251,6 +265,7 @@ rho_pass_kernel(RhoPassArgs a) {
   } else {
     for (int k = tid; k < 2 * P::TWN; k += NT) tw_sm[k] = ldc(a.tw + k);
   }
+  pdl_wait_prev();  // the half spectrum comes from the previous pass
 
   cx<float> vn[E];
   long long tau = blockIdx.x;
@@ -333,6 +348,22 @@ unsigned persistent_ctas(K kern, int threads, size_t smem, long long ntiles) {
   return (unsigned)(ntiles < cap ? ntiles : cap);
 }
 
+// Launch with programmatic stream serialisation (see pdl_allow_next).
+template <typename K, typename A>
+cudaError_t launch_pdl(K kern, unsigned grid, int threads, size_t smem, cudaStream_t s, const A& a) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 template <int LPB, bool STRIDED>
 long long host_tiles(long long outer, long long inner) {
   return STRIDED ? outer * ((inner + LPB - 1) / LPB) : (outer + LPB - 1) / LPB;
@@ -351,8 +382,7 @@ cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
     attr = true;
   }
   const long long ntiles = host_tiles<lpb<N>(), STRIDED>(a.outer, a.inner);
-  kern<<<persistent_ctas(kern, threads, smem, ntiles), threads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, persistent_ctas(kern, threads, smem, ntiles), threads, smem, s, a);
 }
 
 template <int N, bool STRIDED, int OP, bool TC = false>
@@ -368,8 +398,7 @@ cudaError_t launch_rho_t(const RhoPassArgs& a, cudaStream_t s) {
     attr = true;
   }
   const long long ntiles = host_tiles<lpb<N>(), STRIDED>(a.outer, a.inner);
-  kern<<<persistent_ctas(kern, threads, smem, ntiles), threads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(kern, persistent_ctas(kern, threads, smem, ntiles), threads, smem, s, a);
 }
 
 // tensor-core engine: 256-point lines when the caller passes the fragment table
