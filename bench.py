@@ -38,7 +38,7 @@ UNIT = "cell-steps/s"
 BYTES_PER_CELL_STEP = 80.0  # algorithmic HBM bytes of the fused 3D complex64 step
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch from the ncu capture
 # summarised in profiles/fused_step_nbody_256.md; set to None when the kernel changes
-NCU_TRAFFIC = {"psi_pass_nphase": 201.91e6 + 77.64e6}
+NCU_TRAFFIC = {"psi_pass_nphase": 201.91e6 + 78.02e6}
 
 
 def parse():
