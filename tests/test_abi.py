@@ -58,6 +58,7 @@ def test_null_handles_are_rejected():
     L = sn.lib()
     assert L.sn_step(None, 0.1, 1) == sn.SN_EINVAL
     assert L.sn_set_state(None, None, 0) == sn.SN_EINVAL
+    assert L.sn_set_fluid(None, None) == sn.SN_EINVAL
     assert L.sn_observables(None, None) == sn.SN_EINVAL
     assert L.sn_launch_count(None) == 0
     L.sn_destroy_grid(None)
