@@ -326,8 +326,9 @@ FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 (non-tensor) nominal rate; no measured F
 def run_fluid(sn, torch, stream, n=512, L=40.0, steps=400, dt=1e-2):
     """The self-gravitating fluid of Eq. 16 (Figs. 3-4 parameters: M0 = 25, nu = 1,
     w = 1.02, n = 1, lambda = 1) on an n^2 complex128 grid: GR and NMC from the same
-    Gaussian, the NMC run timed.  The plain FP64 path: ten full complex FFTs per
-    NMC step (kinetic 4, Bohm 2, Eq. 15 4) at 5 N log2 N flops each."""
+    Gaussian, both timed.  The plain FP64 path: eight full complex FFTs per step
+    (kinetic 4, both Laplacians of rho + i sqrt(rho) 2, Eq. 15 2) at 5 N log2 N flops
+    each."""
     x = -0.5 * L + np.arange(n) * (L / n)
     X, Y = np.meshgrid(x, x, indexing="ij")
     r2 = X * X + Y * Y
@@ -359,7 +360,7 @@ def run_fluid(sn, torch, stream, n=512, L=40.0, steps=400, dt=1e-2):
         final = g.get_state()
         drift = g.observables()["mass"] / m0 - 1.0
         g.close()
-        ffts = 10 if model == sn.SN_GRAVITY_NMC else 8
+        ffts = 8
         flops = ffts * 5.0 * n * n * np.log2(n * n)
         out[name] = {"value": n * n * steps / t, "unit": "cell-steps/s",
                      "ms_per_step": 1e3 * t / steps, "mass_drift": drift, "final": summary(final),

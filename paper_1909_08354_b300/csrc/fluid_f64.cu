@@ -26,14 +26,14 @@ __device__ __forceinline__ double density(const double2* psi, long long c) {
   return z.x * z.x + z.y * z.y;
 }
 
-// w = rho, wa = sqrt(max(rho, floor)) (both real, stored as complex values)
-__global__ void prep_kernel(const double2* psi, double2* w, double2* wa, double floor,
-                            long long cells) {
+// wa = rho + i sqrt(max(rho, floor)): two real fields in one complex array, so
+// that one FFT, the Laplacian multiplier and one inverse FFT give both
+// Laplacians (real part: lap rho, imaginary part: lap sqrt rho)
+__global__ void prep_kernel(const double2* psi, double2* wa, double floor, long long cells) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const double rho = density(psi, c);
-    w[c] = make_double2(rho, 0.0);
-    wa[c] = make_double2(sqrt(fmax(rho, floor)), 0.0);
+    wa[c] = make_double2(rho, sqrt(fmax(rho, floor)));
   }
 }
 
@@ -52,15 +52,15 @@ __global__ void lap_mult_kernel(double2* w, long long n0, long long n1, long lon
   }
 }
 
-// w = beta lap(rho) + gamma rho with lap(rho) = Re w on entry; beta == NULL
-// means beta = 0 (w is then not read), gamma == NULL means gamma = 1/2 (GR)
-__global__ void source_kernel(const double2* psi, double2* w, const double* gamma,
-                              const double* beta, long long cells) {
+// w = beta lap(rho) + gamma rho with lap(rho) = Re wlap; beta == NULL means
+// beta = 0, gamma == NULL means gamma = 1/2 (GR)
+__global__ void source_kernel(const double2* psi, const double2* wlap, double2* w,
+                              const double* gamma, const double* beta, long long cells) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const double g = gamma ? gamma[c] : 0.5;
     double s = g * density(psi, c);
-    if (beta) s = fma(beta[c], w[c].x, s);
+    if (beta) s = fma(beta[c], wlap[c].x, s);
     w[c] = make_double2(s, 0.0);
   }
 }
@@ -71,7 +71,7 @@ __global__ void phase_kernel(double2* psi, const double2* wphi, const double2* w
        c += (long long)gridDim.x * blockDim.x) {
     const double2 z = psi[c];
     const double rf = fmax(z.x * z.x + z.y * z.y, p.rho_floor);
-    const double vb = wlap[c].x / (2.0 * sqrt(rf));
+    const double vb = wlap[c].y / (2.0 * sqrt(rf));  // lap sqrt rho / (2 sqrt rho)
     const double vp = p.n_poly == 1.0 ? p.w * log(rf) : p.cp * pow(rf, p.n_poly - 1.0);
     double u = fma(p.nu * p.nu, vb, wphi[c].x + vp);
     if (phi_c) u += phi_c[c];
@@ -83,9 +83,9 @@ __global__ void phase_kernel(double2* psi, const double2* wphi, const double2* w
 
 }  // namespace
 
-cudaError_t launch_fluid_prep_f64(const double2* psi, double2* w, double2* wa, double floor,
-                                  long long cells, cudaStream_t s) {
-  prep_kernel<<<blocks_for(cells), kThreads, 0, s>>>(psi, w, wa, floor, cells);
+cudaError_t launch_fluid_prep_f64(const double2* psi, double2* wa, double floor, long long cells,
+                                  cudaStream_t s) {
+  prep_kernel<<<blocks_for(cells), kThreads, 0, s>>>(psi, wa, floor, cells);
   return cudaGetLastError();
 }
 
@@ -100,9 +100,10 @@ cudaError_t launch_lap_mult_f64(double2* w, const int* n, int ndim, const double
   return cudaGetLastError();
 }
 
-cudaError_t launch_fluid_source_f64(const double2* psi, double2* w, const double* gamma,
-                                    const double* beta, long long cells, cudaStream_t s) {
-  source_kernel<<<blocks_for(cells), kThreads, 0, s>>>(psi, w, gamma, beta, cells);
+cudaError_t launch_fluid_source_f64(const double2* psi, const double2* wlap, double2* w,
+                                    const double* gamma, const double* beta, long long cells,
+                                    cudaStream_t s) {
+  source_kernel<<<blocks_for(cells), kThreads, 0, s>>>(psi, wlap, w, gamma, beta, cells);
   return cudaGetLastError();
 }
 

@@ -482,8 +482,9 @@ sn_status step_f64(sn_grid g, double dt, int nsteps) {
 
 // Symmetric split steps of Eq. 16 (Sec. II B) on a complex128 grid: the
 // kinetic half steps use A = -nu/2 (set by sn_set_fluid); the potential
-// sub-step forms rho and sqrt(rho), their spectral Laplacians, the source of
-// Eq. 15 and its inverse Laplacian, then turns psi by U h / nu.
+// sub-step forms rho + i sqrt(rho) and takes both spectral Laplacians with one
+// FFT pair, forms the source of Eq. 15 and its inverse Laplacian, then turns
+// psi by U h / nu: eight full complex FFTs per step.
 sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
   sn_status st = ensure_f64_scratch(g);
   if (st != SN_OK) return st;
@@ -492,8 +493,8 @@ sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
     if (e != cudaSuccess) return cuda_fail(g, e, "cudaMalloc(fluid scratch)");
   }
   double2* psi = reinterpret_cast<double2*>(g->psi);
-  double2* w = g->w64b;   // rho -> lap rho -> source -> phi_N
-  double2* wa = g->w64c;  // sqrt rho -> lap sqrt rho
+  double2* w = g->w64b;   // source -> phi_N
+  double2* wa = g->w64c;  // rho + i sqrt rho -> lap rho + i lap sqrt rho
   const double* k2[3] = {g->k2_64[0], g->k2_64[1], g->k2_64[2]};
   const double inv_n = 1.0 / (double)g->cells;
   const bool nmc = g->fl.model == SN_GRAVITY_NMC;
@@ -507,20 +508,15 @@ sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
   const double ew = 32.0 * g->cells;
   for (int s = 0; s < nsteps; ++s) {
     if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
-    SN_LAUNCH(g, K_F64_EW, 48.0 * g->cells,
-              launch_fluid_prep_f64(psi, w, wa, fp.rho_floor, g->cells, g->stream));
-    // Bohm: lap(sqrt rho)
+    SN_LAUNCH(g, K_F64_EW, 32.0 * g->cells,
+              launch_fluid_prep_f64(psi, wa, fp.rho_floor, g->cells, g->stream));
+    // lap rho (Eq. 15) and lap sqrt rho (Bohm) in one FFT pair
     if ((st = fftn_f64(g, wa, -1)) != SN_OK) return st;
     SN_LAUNCH(g, K_F64_EW, ew, launch_lap_mult_f64(wa, g->n, g->ndim, k2, inv_n, g->stream));
     if ((st = fftn_f64(g, wa, +1)) != SN_OK) return st;
-    // Eq. 15: lap rho (NMC only), source, inverse Laplacian
-    if (nmc) {
-      if ((st = fftn_f64(g, w, -1)) != SN_OK) return st;
-      SN_LAUNCH(g, K_F64_EW, ew, launch_lap_mult_f64(w, g->n, g->ndim, k2, inv_n, g->stream));
-      if ((st = fftn_f64(g, w, +1)) != SN_OK) return st;
-    }
+    // Eq. 15: source, inverse Laplacian
     SN_LAUNCH(g, K_F64_EW, ew,
-              launch_fluid_source_f64(psi, w, nmc ? g->prof64[0] : nullptr,
+              launch_fluid_source_f64(psi, wa, w, nmc ? g->prof64[0] : nullptr,
                                       nmc ? g->prof64[1] : nullptr, g->cells, g->stream));
     if ((st = fftn_f64(g, w, -1)) != SN_OK) return st;
     SN_LAUNCH(g, K_F64_EW, ew,

@@ -106,12 +106,14 @@ struct FluidPhase {
   double w, n_poly, cp;  // V_p = w ln rho (n = 1) or cp rho^(n-1), cp = n w / (n - 1)
   double rho_floor;      // floor of rho under sqrt and ln
 };
-cudaError_t launch_fluid_prep_f64(const double2* psi, double2* w, double2* wa, double floor,
-                                  long long cells, cudaStream_t s);
+cudaError_t launch_fluid_prep_f64(const double2* psi, double2* wa, double floor, long long cells,
+                                  cudaStream_t s);
 cudaError_t launch_lap_mult_f64(double2* w, const int* n, int ndim, const double* const* k2,
                                 double scale, cudaStream_t s);
-cudaError_t launch_fluid_source_f64(const double2* psi, double2* w, const double* gamma,
-                                    const double* beta, long long cells, cudaStream_t s);
+cudaError_t launch_fluid_source_f64(const double2* psi, const double2* wlap, double2* w,
+                                    const double* gamma, const double* beta, long long cells,
+                                    cudaStream_t s);
+// wphi: phi_N (real part); wlap: lap sqrt rho (imaginary part)
 cudaError_t launch_fluid_phase_f64(double2* psi, const double2* wphi, const double2* wlap,
                                    const double* phi_c, const FluidPhase& p, long long cells,
                                    cudaStream_t s);
