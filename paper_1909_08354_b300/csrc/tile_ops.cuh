@@ -164,7 +164,9 @@ __device__ __forceinline__ const float* potential_c2r(const cx<float>* rtile, cx
       }
     }
   } else {
-    __syncthreads();
+    // my line's buffer was last read by its own transform (line_sync); line
+    // l + HALF sat out the transform, so its buffer is free (FP32 engine)
+    if constexpr (TC) __syncthreads(); else snfft::line_sync<N, CONTIG>();
     if (pa) {
       float* a = reinterpret_cast<float*>(lines + l * LS);
       float* b = reinterpret_cast<float*>(lines + (l + HALF) * LS);
