@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-fno", action="store_true")
     p.add_argument("--no-fluid", action="store_true",
                    help="skip the Eq. 16 fluid model (GR and NMC) on a 512^2 complex128 plane")
+    p.add_argument("--no-fields", action="store_true",
+                   help="skip the two coupled fields at 256^3")
     p.add_argument("--no-optical", action="store_true",
                    help="skip the thermo-optical (Eq. 4) kernel on a 1024^2 plane")
     return p.parse_args()
@@ -320,6 +322,60 @@ def run_optical(sn, torch, stream, peak, steps=500):
                          "frac": gbs / peak, "bytes_per_cell_step": 48.0}}
 
 
+def fields_bytes_per_cell_step(m: int) -> float:
+    """Algorithmic HBM bytes per grid cell and step of m coupled fields on a 3D
+    complex64 grid: per field three psi passes (16 B each) and the half-spectrum
+    read of its potential pass (4 B); the first density pass writes the half
+    spectrum (4 B), each further one reads and writes it (8 B); the three
+    half-spectrum passes once (8 B each).  m = 1 gives the 80 B of one field."""
+    return 52.0 * m + 4.0 + 8.0 * (m - 1) + 24.0
+
+
+def run_fields(sn, torch, stream, peak, m=2, n=256, L=80.0, steps=500):
+    """m coupled fields sharing one potential (the multi-wave-function form of
+    Eqs. 1-2) on an n^3 complex64 grid: field j is the N-body workload of seed
+    3000 + j; timed like the main line; accuracy is the one-step rel-L2 against
+    the plain FP64 GPU step of the same fields."""
+    ws = [W.nbody_3d(n=n, L=L, seed=3000 + j) for j in range(m)]
+    kw = kernel_kw(ws[0].kernel)
+    psis = np.stack([w.psi0(np.complex64) for w in ws])
+    g = sn.Grid(ws[0].n, ws[0].L, "c64", stream=stream.cuda_stream)
+    g.set_fields(m)
+    g.set_kernel(**kw)
+    g.set_state(psis)
+    g.step(ws[0].dt, 1)
+    out1 = g.get_state()
+    g64 = sn.Grid(ws[0].n, ws[0].L, "c128", stream=stream.cuda_stream)
+    g64.set_fields(m)
+    g64.set_kernel(**kw)
+    g64.set_state(psis.astype(np.complex128))
+    g64.step(ws[0].dt, 1)
+    ref1 = g64.get_state()
+    g64.close()
+    rel = float(np.linalg.norm((out1 - ref1).ravel()) / np.linalg.norm(ref1.ravel()))
+    del out1, ref1
+    g.set_state(psis)
+    g.step(ws[0].dt, 5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(ws[0].dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    g.close()
+    cells = ws[0].cells
+    bpc = fields_bytes_per_cell_step(m)
+    gbs = bpc * cells * steps / t / 1e9
+    return {"workload": f"fields{m}_nbody3d_{n}: {m} coupled fields on {n}^3, L={L:g}, complex64, "
+                        f"field j = 16 lumps of seed {3000}+j, alpha_Y={kw['alpha_Y']}, "
+                        f"dt={ws[0].dt}",
+            "value": m * cells * steps / t, "unit": "field-cell-steps/s",
+            "ms_per_step": 1e3 * t / steps, "steps": steps, "rel_l2_vs_fp64_one_step": rel,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "bytes_per_cell_step": bpc}}
+
+
 FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 (non-tensor) nominal rate; no measured FP64 peak
 
 
@@ -558,6 +614,10 @@ def main():
     if not args.no_fluid and world == 1:
         fluid = run_fluid(sn, torch, stream)
 
+    fields = None
+    if not args.no_fields and world == 1 and args.n == 256:
+        fields = run_fields(sn, torch, stream, peak)
+
     scan = None
     if not args.no_scan:
         scan = run_scan(sn, torch, stream, peak, args.scan_count, args.scan_steps)
@@ -601,6 +661,7 @@ def main():
             "tensor_core_engine": tc,
             "optical_kernel": optical,
             "fluid_model": fluid,
+            "coupled_fields": fields,
             "batched_scan": scan,
             "fno_surrogate": fno,
         }

@@ -145,14 +145,32 @@ typedef struct {
  * The profiles gamma, beta, phi_C are built once here, in FP64 on the host.
  * In this mode sn_observables reports mass, e_kin (with A = -nu/2),
  * centroids and momenta; e_pot and e_nl are 0.  Errors: SN_ENOTSUP on SN_C64
- * grids (this build steps Eq. 16 in FP64 only), SN_EINVAL for bad values,
- * SN_ENOMEM, SN_ECUDA. */
+ * grids (this build steps Eq. 16 in FP64 only) and on grids of several fields
+ * (sn_set_fields), SN_EINVAL for bad values, SN_ENOMEM, SN_ECUDA. */
 sn_status sn_set_fluid(sn_grid g, const sn_fluid* f);
 
-/* Copy a state in: psi holds ncells complex values of the grid's dtype,
- * host memory (on_device = 0; the call returns after the copy) or device
- * memory (on_device = 1; ordered on the grid's stream).  Resets the step
- * counter to 0. */
+/* Several coupled wave functions (Sec. II: Eqs. 1-2 generalize to multiple
+ * wave functions coupled through the nonlinearities).  The grid holds count
+ * fields psi_0 .. psi_{count-1}; each obeys Eq. 1 with the same A, and all
+ * see one index change: phi of Eq. 2 (or the Newton + Yukawa kernel) sourced
+ * by the total density rho = sum_j |psi_j|^2, the local term g_local rho of
+ * that same total density, and v_ext.  With count = 1 this is Eqs. 1-2.
+ * Each field's mass is conserved.  sn_observables then reports mass, e_kin
+ * and momenta summed over the fields, and the centroids, e_pot and e_nl of
+ * the total density (e_total is the Hamiltonian of the coupled system).
+ * The call synchronises the grid's stream, sets the state to zero and the
+ * step counter to 0.  Errors: SN_EINVAL (count outside [1, SN_MAX_FIELDS]),
+ * SN_ENOTSUP (count > 1 in the fluid mode of sn_set_fluid), SN_ENOMEM,
+ * SN_ECUDA.  sn_get_fields returns the count (0 for a NULL grid). */
+#define SN_MAX_FIELDS 16
+sn_status sn_set_fields(sn_grid g, int count);
+int sn_get_fields(sn_grid g);
+
+/* Copy a state in: psi holds fields x ncells complex values of the grid's
+ * dtype, field j at offset j ncells (fields = 1 unless sn_set_fields set
+ * more), host memory (on_device = 0; the call returns after the copy) or
+ * device memory (on_device = 1; ordered on the grid's stream).  Resets the
+ * step counter to 0. */
 sn_status sn_set_state(sn_grid g, const void* psi, int on_device);
 
 /* Copy the state out (same layout as sn_set_state).  Host copies block until

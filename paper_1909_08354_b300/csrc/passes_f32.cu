@@ -224,8 +224,11 @@ psi_pass_kernel(PsiPassArgs a) {
 
     if constexpr (DENSITY) {
       float2* rh = a.rh_out;
+      const bool accum = a.rh_accum != 0;
       auto put = [&](int k, int ll, cx<float> z) {
-        tile::stg_c(rh + (size_t)k * nlines + line0 + ll, z);
+        float2* p = rh + (size_t)k * nlines + line0 + ll;
+        if (accum) z = z + tile::ldg_c<true>(p);  // each element has one writer per launch
+        tile::stg_c(p, z);
       };
       tile::density_r2c<N, LPB, CONTIG, decltype(put), TC, STRIDED>(v, valid, lines, tw_sm, l, t, tid,
                                                                 nvalid, put, tabs);
@@ -317,10 +320,10 @@ rho_pass_kernel(RhoPassArgs a) {
       if constexpr (TC) {
         if (t == 0) k2pm_sm[l] = k2pm;  // read after the entry barriers of fmi
         tc16::fmi(v, lines, *tabs, l, t, [&](int L) {
-          return tc16::GreenMult{k2l_tc, k2pm_sm[L], a.cN, a.cY, a.mu2};
+          return tc16::GreenMult{k2l_tc, k2pm_sm[L], a.cN, a.cY, a.mu2, a.cL};
         });
       } else {
-        tile::green<N, CONTIG>(v, lines + l * LS, tw_sm, a.k2l, k2pm, a.cN, a.cY, a.mu2, t);
+        tile::green<N, CONTIG>(v, lines + l * LS, tw_sm, a.k2l, k2pm, a.cN, a.cY, a.mu2, a.cL, t);
       }
     }
     store_line<E, T>(v, a.data + base, ustride, t, valid);

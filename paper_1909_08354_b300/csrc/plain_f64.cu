@@ -127,22 +127,22 @@ __global__ void mult_kinetic_kernel(double2* psi, Dims d, const double2* m0, con
   }
 }
 
-__global__ void density_kernel(const double2* psi, double2* w, long long cells) {
+__global__ void density_kernel(const double2* psi, double2* w, long long cells, bool accumulate) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const cx<double> z = ldd(psi + c);
-    w[c] = make_double2(cnorm2(z), 0.0);
+    w[c] = make_double2((accumulate ? w[c].x : 0.0) + cnorm2(z), 0.0);
   }
 }
 
 __global__ void green_kernel(double2* w, Dims d, const double* k20, const double* k21,
-                             const double* k22, double cN, double cY, double mu2) {
+                             const double* k22, double cN, double cY, double mu2, double cL) {
   const long long cells = d.n0 * d.n1 * d.n2;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const long long i2 = c % d.n2, i1 = (c / d.n2) % d.n1, i0 = c / (d.n2 * d.n1);
     const double k2 = (k20 ? k20[i0] : 0.0) + k21[i1] + k22[i2];
-    const double K = (k2 > 0.0) ? (cN / k2 + cY / (k2 + mu2)) : 0.0;
+    const double K = ((k2 > 0.0) ? (cN / k2 + cY / (k2 + mu2)) : 0.0) + cL;
     std2(w + c, cscale(ldd(w + c), K));
   }
 }
@@ -168,7 +168,20 @@ __global__ void widen_kernel(const float2* in, double2* out, long long cells) {
   }
 }
 
-// ---- observables: per-block partial sums, fixed reduction order -------------
+template <class Z>
+__global__ void total_amplitude_kernel(const Z* psi, int count, long long cells, double2* out) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    double rho = 0.0;
+    for (int j = 0; j < count; ++j) {
+      const Z z = psi[(size_t)j * cells + c];
+      rho += (double)z.x * (double)z.x + (double)z.y * (double)z.y;
+    }
+    out[c] = make_double2(sqrt(rho), 0.0);
+  }
+}
+
+// ---- observables: per-block partial sums added to partials, fixed order -----
 
 template <int NQ>
 __device__ __forceinline__ void block_reduce_store(double (&acc)[NQ], double* partials, int q0) {
@@ -185,7 +198,7 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NQ], double* pa
   if (threadIdx.x < NQ) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-    partials[(size_t)blockIdx.x * Q_NUM + q0 + threadIdx.x] = s;
+    partials[(size_t)blockIdx.x * Q_NUM + q0 + threadIdx.x] += s;
   }
 }
 
@@ -285,18 +298,20 @@ cudaError_t launch_mult_kinetic_f64(double2* psi, const int* n, int ndim, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_density_f64(const double2* psi, double2* w, long long cells, cudaStream_t s) {
-  density_kernel<<<ew_blocks(cells), kEwThreads, 0, s>>>(psi, w, cells);
+cudaError_t launch_density_f64(const double2* psi, double2* w, long long cells, cudaStream_t s,
+                               bool accumulate) {
+  density_kernel<<<ew_blocks(cells), kEwThreads, 0, s>>>(psi, w, cells, accumulate);
   return cudaGetLastError();
 }
 
 cudaError_t launch_green_f64(double2* w, const int* n, int ndim, const double* const* k2,
-                             double cN, double cY, double mu2, cudaStream_t s) {
+                             double cN, double cY, double mu2, cudaStream_t s, double cL) {
   const Dims d = dims_of(n, ndim);
   const double* a0 = ndim == 3 ? k2[0] : nullptr;
   const double* a1 = ndim == 3 ? k2[1] : k2[0];
   const double* a2 = ndim == 3 ? k2[2] : k2[1];
-  green_kernel<<<ew_blocks(d.n0 * d.n1 * d.n2), kEwThreads, 0, s>>>(w, d, a0, a1, a2, cN, cY, mu2);
+  green_kernel<<<ew_blocks(d.n0 * d.n1 * d.n2), kEwThreads, 0, s>>>(w, d, a0, a1, a2, cN, cY, mu2,
+                                                                    cL);
   return cudaGetLastError();
 }
 
@@ -309,6 +324,17 @@ cudaError_t launch_phase_f64(double2* psi, const double2* w, const double* vext,
 cudaError_t launch_widen_f32_to_f64(const float2* in, double2* out, long long cells,
                                     cudaStream_t s) {
   widen_kernel<<<ew_blocks(cells), kEwThreads, 0, s>>>(in, out, cells);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_total_amplitude(const void* psi, bool f32, int count, long long cells,
+                                   double2* out, cudaStream_t s) {
+  if (f32)
+    total_amplitude_kernel<<<ew_blocks(cells), kEwThreads, 0, s>>>(
+        static_cast<const float2*>(psi), count, cells, out);
+  else
+    total_amplitude_kernel<<<ew_blocks(cells), kEwThreads, 0, s>>>(
+        static_cast<const double2*>(psi), count, cells, out);
   return cudaGetLastError();
 }
 

@@ -190,7 +190,7 @@ __device__ __forceinline__ void green_item(const Inst& d, long long tau, unsigne
   tile::load_line<E, T, true>(v, d.rho + base, 1u, t, valid);
   const float k2pm = valid ? d.k2[o] : 0.f;
   tile::green<N, true>(v, lines + l * LS, reinterpret_cast<const cx<float>*>(d.tw), d.k2, k2pm,
-                       d.cN, d.cY, d.mu2, t);
+                       d.cN, d.cY, d.mu2, 0.f, t);
   tile::store_line<E, T>(v, d.rho + base, 1u, t, valid);
 }
 

@@ -133,7 +133,9 @@ struct sn_grid_s {
   long long launches = 0;
   std::string err;
 
-  void* psi = nullptr;         // float2* or double2*
+  void* psi = nullptr;         // float2* or double2*: fields psi_j at psi + j cells
+  int fields = 1;              // coupled fields sharing one potential (sn_set_fields)
+  int fields_cap = 1;          // fields the psi allocation holds
   float2* rhohat = nullptr;    // C64: half spectrum
   double2* w64a = nullptr;     // FP64 scratch (psi copy / work)
   double2* w64b = nullptr;
@@ -307,10 +309,12 @@ LineGeom psi_geom(sn_grid g, int a) {
 
 // ---- fused FP32 step ----------------------------------------------------------
 
-sn_status psi_pass(sn_grid g, int a, int variant, int full, double dt) {
+// Field j of the grid.  With several fields the local term g rho of the total
+// density is applied through the Green's multiplier (rho_passes), not per field.
+sn_status psi_pass(sn_grid g, int j, int a, int variant, int full, double dt) {
   const LineGeom lg = psi_geom(g, a);
   PsiPassArgs pa{};
-  pa.psi = reinterpret_cast<float2*>(g->psi);
+  pa.psi = reinterpret_cast<float2*>(g->psi) + (size_t)j * g->cells;
   pa.outer = lg.outer;
   pa.inner = lg.inner;
   pa.mult = g->mult32[a][full];
@@ -319,8 +323,9 @@ sn_status psi_pass(sn_grid g, int a, int variant, int full, double dt) {
   pa.rh_in = g->rhohat;
   pa.vext = g->has_vext ? g->vext32 : nullptr;
   pa.h = (float)dt;
-  pa.gh = (float)(g->kp.g_local * dt);
+  pa.gh = g->fields > 1 ? 0.f : (float)(g->kp.g_local * dt);
   pa.rh_out = g->rhohat;
+  pa.rh_accum = variant == PSI_DENSITY && j > 0;
   pa.tc = g->engine == SN_ENGINE_TC16 ? g->tc_frag : nullptr;
   const double P = g->n[a] / 2 + 1, lines = (double)g->cells / g->n[a];
   double bytes = 16.0 * g->cells;
@@ -330,7 +335,7 @@ sn_status psi_pass(sn_grid g, int a, int variant, int full, double dt) {
     if (g->has_vext) bytes += 4.0 * g->cells;
     kind = K_PSI_NPHASE;
   } else if (variant == PSI_DENSITY) {
-    bytes += 8.0 * P * lines;
+    bytes += (j > 0 ? 16.0 : 8.0) * P * lines;
     kind = K_PSI_DENSITY;
   }
   SN_LAUNCH(g, kind, bytes, launch_psi_pass_f32(g->n[a], lg.strided, variant, pa, g->stream));
@@ -339,6 +344,8 @@ sn_status psi_pass(sn_grid g, int a, int variant, int full, double dt) {
 
 // Half-spectrum passes after the density of axis h: forward along the middle
 // axis (3D), Green's multiply along the remaining axis, inverse along the middle.
+// With several fields the multiplier also carries the local term: g rho of the
+// total density is F^-1[g F rho], a constant added to K(k) at every k.
 sn_status rho_passes(sn_grid g, int h, double dt) {
   const int d = g->ndim;
   const long long P = g->n[h] / 2 + 1;
@@ -356,6 +363,7 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
   ra.cN = (float)cN;
   ra.cY = (float)cY;
   ra.mu2 = (float)mu2;
+  ra.cL = g->fields > 1 ? (float)(g->kp.g_local * scale) : 0.f;
   ra.tc = g->engine == SN_ENGINE_TC16 ? g->tc_frag : nullptr;
   if (d == 2) {
     const int c = rest[0];
@@ -419,12 +427,16 @@ sn_status step_f32(sn_grid g, double dt, int nsteps) {
     const int full = (r == 0 || r == nsteps) ? 0 : 1;
     int order[3];
     for (int i = 0; i < d; ++i) order[i] = odd ? d - 1 - i : i;
+    // axis by axis over the fields: every field's potential pass reads the
+    // half spectrum before the first density pass overwrites it
     for (int i = 0; i < d; ++i) {
       int variant = PSI_PLAIN;
       if (i == 0 && r > 0) variant = PSI_NPHASE;
       if (i == d - 1 && r < nsteps) variant = PSI_DENSITY;
-      sn_status st = psi_pass(g, order[i], variant, full, dt);
-      if (st != SN_OK) return st;
+      for (int j = 0; j < g->fields; ++j) {
+        sn_status st = psi_pass(g, j, order[i], variant, full, dt);
+        if (st != SN_OK) return st;
+      }
     }
     if (r < nsteps) {
       prev_h = order[d - 1];
@@ -447,8 +459,8 @@ sn_status fftn_f64(sn_grid g, double2* buf, int sign) {
   return SN_OK;
 }
 
-sn_status kinetic_f64(sn_grid g, int full) {
-  double2* psi = reinterpret_cast<double2*>(g->psi);
+sn_status kinetic_f64(sn_grid g, int full, int j = 0) {
+  double2* psi = reinterpret_cast<double2*>(g->psi) + (size_t)j * g->cells;
   sn_status st = fftn_f64(g, psi, -1);
   if (st != SN_OK) return st;
   const double2* m[3] = {g->mult64[0][full], g->mult64[1][full], g->mult64[2][full]};
@@ -464,18 +476,27 @@ sn_status step_f64(sn_grid g, double dt, int nsteps) {
   const GreenCoeffs gc = green_coeffs(g->kp);
   const double scale = dt / (double)g->cells;
   const double* k2[3] = {g->k2_64[0], g->k2_64[1], g->k2_64[2]};
+  // several fields: the local term of the total density rides on the multiplier
+  const int nf = g->fields;
+  const double cL = nf > 1 ? g->kp.g_local * scale : 0.0;
+  const double gh = nf > 1 ? 0.0 : g->kp.g_local * dt;
   for (int s = 0; s < nsteps; ++s) {
-    if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
-    SN_LAUNCH(g, K_F64_EW, 32.0 * g->cells, launch_density_f64(psi, w, g->cells, g->stream));
+    for (int j = 0; j < nf; ++j)
+      if ((st = kinetic_f64(g, 0, j)) != SN_OK) return st;
+    for (int j = 0; j < nf; ++j)
+      SN_LAUNCH(g, K_F64_EW, (j > 0 ? 48.0 : 32.0) * g->cells,
+                launch_density_f64(psi + (size_t)j * g->cells, w, g->cells, g->stream, j > 0));
     if ((st = fftn_f64(g, w, -1)) != SN_OK) return st;
     SN_LAUNCH(g, K_F64_EW, 32.0 * g->cells,
               launch_green_f64(w, g->n, g->ndim, k2, gc.cN * scale, gc.cY * scale, gc.mu2,
-                               g->stream));
+                               g->stream, cL));
     if ((st = fftn_f64(g, w, +1)) != SN_OK) return st;
-    SN_LAUNCH(g, K_F64_EW, (48.0 + (g->has_vext ? 8.0 : 0.0)) * g->cells,
-              launch_phase_f64(psi, w, g->has_vext ? g->vext64 : nullptr, dt,
-                               g->kp.g_local * dt, g->cells, g->stream));
-    if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
+    for (int j = 0; j < nf; ++j)
+      SN_LAUNCH(g, K_F64_EW, (48.0 + (g->has_vext ? 8.0 : 0.0)) * g->cells,
+                launch_phase_f64(psi + (size_t)j * g->cells, w, g->has_vext ? g->vext64 : nullptr,
+                                 dt, gh, g->cells, g->stream));
+    for (int j = 0; j < nf; ++j)
+      if ((st = kinetic_f64(g, 0, j)) != SN_OK) return st;
   }
   return SN_OK;
 }
@@ -707,6 +728,7 @@ sn_status sn_set_fluid(sn_grid g, const sn_fluid* f) {
   }
   if (g->dtype != SN_C128)
     return fail(g, SN_ENOTSUP, "sn_set_fluid: the fluid model runs on complex128 grids");
+  if (g->fields > 1) return fail(g, SN_ENOTSUP, "sn_set_fluid: the fluid model evolves one field");
   if (!(f->nu > 0.0) || !std::isfinite(f->nu) || !std::isfinite(f->w) ||
       !std::isfinite(f->n_poly) || !(f->rho_floor > 0.0) || !std::isfinite(f->rho_floor))
     return fail(g, SN_EINVAL, "sn_set_fluid: nu and rho_floor must be finite and > 0, w and n finite");
@@ -758,10 +780,39 @@ sn_status sn_set_fluid(sn_grid g, const sn_fluid* f) {
   return SN_OK;
 }
 
+sn_status sn_set_fields(sn_grid g, int count) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_set_fields: grid is NULL");
+  if (count < 1 || count > SN_MAX_FIELDS)
+    return fail(g, SN_EINVAL, "sn_set_fields: count must be in [1, SN_MAX_FIELDS]");
+  if (count > 1 && g->fluid)
+    return fail(g, SN_ENOTSUP, "sn_set_fields: the fluid model evolves one field");
+  cudaError_t e = cudaStreamSynchronize(g->stream);  // queued steps still use the old state
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamSynchronize");
+  const size_t esz = g->dtype == SN_C64 ? sizeof(float2) : sizeof(double2);
+  if (count > g->fields_cap) {
+    void* p = nullptr;
+    e = cudaMalloc(&p, (size_t)count * g->cells * esz);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMalloc(psi fields)");
+    for (auto& q : g->allocs)
+      if (q == g->psi) q = p;
+    cudaFree(g->psi);
+    g->psi = p;
+    g->fields_cap = count;
+  }
+  e = cudaMemset(g->psi, 0, (size_t)count * g->cells * esz);
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemset(psi fields)");
+  g->fields = count;
+  g->step = 0;
+  return SN_OK;
+}
+
+int sn_get_fields(sn_grid g) { return g ? g->fields : 0; }
+
 sn_status sn_set_state(sn_grid g, const void* psi, int on_device) {
   if (!g) return fail(nullptr, SN_EINVAL, "sn_set_state: grid is NULL");
   if (!psi) return fail(g, SN_EINVAL, "sn_set_state: psi is NULL");
-  const size_t bytes = (size_t)g->cells * (g->dtype == SN_C64 ? sizeof(float2) : sizeof(double2));
+  const size_t bytes = (size_t)g->fields * g->cells *
+                       (g->dtype == SN_C64 ? sizeof(float2) : sizeof(double2));
   cudaError_t e = cudaMemcpyAsync(g->psi, psi, bytes,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                   g->stream);
@@ -774,7 +825,8 @@ sn_status sn_set_state(sn_grid g, const void* psi, int on_device) {
 sn_status sn_get_state(sn_grid g, void* psi_out, int on_device) {
   if (!g) return fail(nullptr, SN_EINVAL, "sn_get_state: grid is NULL");
   if (!psi_out) return fail(g, SN_EINVAL, "sn_get_state: psi_out is NULL");
-  const size_t bytes = (size_t)g->cells * (g->dtype == SN_C64 ? sizeof(float2) : sizeof(double2));
+  const size_t bytes = (size_t)g->fields * g->cells *
+                       (g->dtype == SN_C64 ? sizeof(float2) : sizeof(double2));
   cudaError_t e = cudaMemcpyAsync(psi_out, g->psi, bytes,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                   g->stream);
@@ -801,32 +853,55 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
   sn_status st = ensure_f64_scratch(g);
   if (st != SN_OK) return st;
   const int d = g->ndim;
-  double2* psi64;
-  if (g->dtype == SN_C64) {
-    psi64 = g->w64a;
-    SN_LAUNCH(g, K_OBS, 24.0 * g->cells,
-              launch_widen_f32_to_f64(reinterpret_cast<const float2*>(g->psi), psi64, g->cells,
-                                      g->stream));
-  } else {
-    psi64 = reinterpret_cast<double2*>(g->psi);
-  }
+  const int nf = g->fields;
+  const bool f32 = g->dtype == SN_C64;
+  // field j in FP64 (widened into w64a for complex64 grids)
+  auto field64 = [&](int j, double2** dst) -> sn_status {
+    if (f32) {
+      SN_LAUNCH(g, K_OBS, 24.0 * g->cells,
+                launch_widen_f32_to_f64(reinterpret_cast<const float2*>(g->psi) + (size_t)j * g->cells,
+                                        g->w64a, g->cells, g->stream));
+      *dst = g->w64a;
+    } else {
+      *dst = reinterpret_cast<double2*>(g->psi) + (size_t)j * g->cells;
+    }
+    return SN_OK;
+  };
   cudaError_t e = cudaMemsetAsync(g->partials, 0, sizeof(double) * kObsBlocks * Q_NUM, g->stream);
   if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemsetAsync");
-  SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
-            launch_obs_space(psi64, g->has_vext ? g->vext64 : nullptr, g->n, d, g->cs_64,
-                             g->cs_one, g->partials, g->stream));
-  double2* w = g->w64b;
-  for (int a = 0; a < d; ++a) {
-    e = cudaMemcpyAsync(w, psi64, sizeof(double2) * g->cells, cudaMemcpyDeviceToDevice, g->stream);
-    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemcpyAsync");
-    const LineGeom lg = psi_geom(g, a);
-    SN_LAUNCH(g, K_OBS, 32.0 * g->cells,
-              launch_fft_f64(g->n[a], lg.strided, -1, w, lg.outer, lg.inner,
-                             g->tw64[log2i(g->n[a])], g->stream));
-    SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
-              launch_obs_kaxis(w, g->n, d, a, g->kax_64[a], g->partials, g->stream));
+  // mass, centroids, rho^2 and V_ext terms, and the potential energy are those of
+  // the total density: with several fields they are taken from a single state
+  // sqrt(sum_j |psi_j|^2) that carries it
+  double2* dens;
+  if (nf > 1) {
+    if (!g->w64c && (e = dalloc(g, &g->w64c, (size_t)g->cells)) != cudaSuccess)
+      return cuda_fail(g, e, "cudaMalloc(observables scratch)");
+    dens = g->w64c;
+    SN_LAUNCH(g, K_OBS, (8.0 * nf * (f32 ? 1 : 2) + 16.0) * g->cells,
+              launch_total_amplitude(g->psi, f32, nf, g->cells, dens, g->stream));
+  } else if ((st = field64(0, &dens)) != SN_OK) {
+    return st;
   }
-  SN_LAUNCH(g, K_OBS, 32.0 * g->cells, launch_density_f64(psi64, w, g->cells, g->stream));
+  SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
+            launch_obs_space(dens, g->has_vext ? g->vext64 : nullptr, g->n, d, g->cs_64,
+                             g->cs_one, g->partials, g->stream));
+  // kinetic energy and momentum add up over the fields
+  double2* w = g->w64b;
+  for (int j = 0; j < nf; ++j) {
+    double2* psi64 = dens;
+    if (nf > 1 && (st = field64(j, &psi64)) != SN_OK) return st;
+    for (int a = 0; a < d; ++a) {
+      e = cudaMemcpyAsync(w, psi64, sizeof(double2) * g->cells, cudaMemcpyDeviceToDevice, g->stream);
+      if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemcpyAsync");
+      const LineGeom lg = psi_geom(g, a);
+      SN_LAUNCH(g, K_OBS, 32.0 * g->cells,
+                launch_fft_f64(g->n[a], lg.strided, -1, w, lg.outer, lg.inner,
+                               g->tw64[log2i(g->n[a])], g->stream));
+      SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
+                launch_obs_kaxis(w, g->n, d, a, g->kax_64[a], g->partials, g->stream));
+    }
+  }
+  SN_LAUNCH(g, K_OBS, 32.0 * g->cells, launch_density_f64(dens, w, g->cells, g->stream));
   for (int a = d - 1; a >= 0; --a) {
     const LineGeom lg = psi_geom(g, a);
     SN_LAUNCH(g, K_OBS, 32.0 * g->cells,

@@ -38,6 +38,7 @@ struct PsiPassArgs {
   float h;                 // NPHASE: step h (multiplies V_ext)
   float gh;                // NPHASE: g * h
   float2* rh_out;          // DENSITY: half spectrum [N/2+1][lines]
+  int rh_accum;            // DENSITY: add to rh_out (the density of a further field)
   const uint4* tc;         // tensor-core fragment table (256-point lines), or NULL
 };
 
@@ -50,6 +51,7 @@ struct RhoPassArgs {
   const float* k2l;  // GREEN: k^2 of the line axis
   long long mid_n;   // GREEN, contiguous lines: outer = plane * mid_n + mid
   float cN, cY, mu2; // GREEN: K = cN/k2 + cY/(k2 + mu2), zero at k2 = 0
+  float cL;          // GREEN: constant added to K at every k (a local term)
   const uint4* tc;   // tensor-core fragment table (256-point lines), or NULL
 };
 
@@ -92,13 +94,20 @@ cudaError_t launch_fft_f64(int N, bool strided, int sign, double2* data, long lo
                            long long inner, const double2* tw, cudaStream_t s);
 cudaError_t launch_mult_kinetic_f64(double2* psi, const int* n, int ndim, const double2* const* m,
                                     cudaStream_t s);
-cudaError_t launch_density_f64(const double2* psi, double2* w, long long cells, cudaStream_t s);
+// w = |psi|^2, or w += |psi|^2 with accumulate
+cudaError_t launch_density_f64(const double2* psi, double2* w, long long cells, cudaStream_t s,
+                               bool accumulate = false);
+// w *= K(k) + cL, K as in GreenCoeffs (zero at k = 0)
 cudaError_t launch_green_f64(double2* w, const int* n, int ndim, const double* const* k2,
-                             double cN, double cY, double mu2, cudaStream_t s);
+                             double cN, double cY, double mu2, cudaStream_t s, double cL = 0.0);
 cudaError_t launch_phase_f64(double2* psi, const double2* w, const double* vext, double h,
                              double gh, long long cells, cudaStream_t s);
 cudaError_t launch_widen_f32_to_f64(const float2* in, double2* out, long long cells,
                                     cudaStream_t s);
+// out = (sqrt(sum_j |psi_j|^2), 0) over count fields psi_j = psi + j cells
+// (complex64 if f32, else complex128): a state whose density is the total one
+cudaError_t launch_total_amplitude(const void* psi, bool f32, int count, long long cells,
+                                   double2* out, cudaStream_t s);
 
 // ---- self-gravitating fluid, Eq. 16 (FP64, fluid_f64.cu) -------------------
 struct FluidPhase {
@@ -124,6 +133,8 @@ enum ObsQ {
   Q_EKIN0, Q_P0, Q_EKIN1, Q_P1, Q_EKIN2, Q_P2, Q_EPOT, Q_NUM
 };
 constexpr int kObsBlocks = 592;  // 4 x 148 SMs
+// The observables kernels add their per-block sums to partials (zeroed first),
+// so that several fields accumulate into one set.
 // cs[a][j] = (cos, sin)(2 pi x_j / L_a) for the ndim axes; cs_one = {(1, 0)}
 cudaError_t launch_obs_space(const double2* psi, const double* vext, const int* n, int ndim,
                              const double2* const* cs, const double2* cs_one, double* partials,

@@ -288,11 +288,11 @@ struct MultTable {
 };
 struct GreenMult {
   const float* k2l;  // padded [MT]
-  float k2pm, cN, cY, mu2;
+  float k2pm, cN, cY, mu2, cL;  // cL: constant added at every k
   __device__ __forceinline__ cx<float> operator()(cx<float> z, int k) const {
     const float k2 = k2pm + k2l[pt(k)];
     const float den = k2 * (k2 + mu2);
-    const float K = (k2 > 0.f) ? __fdividef(fmaf(cN, k2 + mu2, cY * k2), den) : 0.f;
+    const float K = ((k2 > 0.f) ? __fdividef(fmaf(cN, k2 + mu2, cY * k2), den) : 0.f) + cL;
     return {z.re * K, z.im * K};
   }
 };

@@ -318,11 +318,12 @@ __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], 
 }
 
 // FFT . K(k) . IFFT along my line of the half spectrum, K = cN/k2 + cY/(k2 + mu2)
-// with K(0) = 0; k2 = k2pm (the two other axes) + k2l[k] (this axis).
+// with K(0) = 0, plus the constant cL at every k; k2 = k2pm (the two other
+// axes) + k2l[k] (this axis).
 template <int N, bool CONTIG>
 __device__ __forceinline__ void green(cx<float> (&v)[Plan<N>::E], cx<float>* line_buf,
                                       const cx<float>* tw, const float* k2l, float k2pm, float cN,
-                                      float cY, float mu2, int t) {
+                                      float cY, float mu2, float cL, int t) {
   constexpr int E = Plan<N>::E, T = Plan<N>::T;
   line_transform<float, N, -1, CONTIG>(v, line_buf, tw, t, true);
 #pragma unroll
@@ -331,7 +332,7 @@ __device__ __forceinline__ void green(cx<float> (&v)[Plan<N>::E], cx<float>* lin
     // less than the FP32 rounding of psi
     const float k2 = k2pm + k2l[t + T * m];
     const float den = k2 * (k2 + mu2);
-    const float K = (k2 > 0.f) ? __fdividef(fmaf(cN, k2 + mu2, cY * k2), den) : 0.f;
+    const float K = ((k2 > 0.f) ? __fdividef(fmaf(cN, k2 + mu2, cY * k2), den) : 0.f) + cL;
     v[m] = cscale(v[m], K);
   }
   line_transform<float, N, +1, CONTIG>(v, line_buf, tw, t, true);

@@ -42,6 +42,7 @@ def _kernel(coeff_lap=-0.5, G=1.0, alpha_Y=0.0, lambda_Y=1.0, g_local=0.0, zero_
 
 
 SN_GRAVITY_GR, SN_GRAVITY_NMC = 0, 1
+SN_MAX_FIELDS = 16  # include/sn.h
 
 
 class SnFluid(ctypes.Structure):
@@ -84,6 +85,8 @@ _SIGNATURES = [
     ("sn_kind_name", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_set_engine", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sn_set_fluid", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SnFluid)]),
+    ("sn_set_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_get_fields", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_test_line_fft_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("sn_step_2d_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -544,6 +547,7 @@ class Grid:
         self.L = tuple(float(v) for v in L)
         self.dtype = SN_C64 if dtype in ("c64", "complex64", SN_C64) else SN_C128
         self.cells = int(np.prod(self.n))
+        self.fields = 1
         self.h = sn_create_grid(self.n, self.L, self.dtype, stream)
 
     @property
@@ -553,13 +557,23 @@ class Grid:
     def set_kernel(self, **kw):
         sn_set_kernel(self.h, **kw)
 
+    def set_fields(self, count: int):
+        """Several coupled fields sharing one potential (see sn_set_fields in
+        include/sn.h); the state is then an array of shape (count, *n)."""
+        _check(self.h, lib().sn_set_fields(self.h, int(count)))
+        self.fields = int(count)
+
+    @property
+    def state_shape(self):
+        return self.n if self.fields == 1 else (self.fields,) + self.n
+
     def set_state(self, psi):
-        sn_set_state(self.h, psi, self.dtype, self.cells)
+        sn_set_state(self.h, psi, self.dtype, self.fields * self.cells)
 
     def get_state(self, out=None):
         if out is None:
-            out = np.empty(self.n, dtype=self.np_dtype)
-        return sn_get_state(self.h, out, self.dtype, self.cells)
+            out = np.empty(self.state_shape, dtype=self.np_dtype)
+        return sn_get_state(self.h, out, self.dtype, self.fields * self.cells)
 
     def step(self, dt: float, nsteps: int = 1):
         sn_step(self.h, dt, nsteps)

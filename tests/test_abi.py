@@ -59,7 +59,14 @@ def test_null_handles_are_rejected():
     assert L.sn_step(None, 0.1, 1) == sn.SN_EINVAL
     assert L.sn_set_state(None, None, 0) == sn.SN_EINVAL
     assert L.sn_set_fluid(None, None) == sn.SN_EINVAL
+    assert L.sn_set_fields(None, 2) == sn.SN_EINVAL
+    assert L.sn_get_fields(None) == 0
     assert L.sn_observables(None, None) == sn.SN_EINVAL
     assert L.sn_launch_count(None) == 0
     L.sn_destroy_grid(None)
     assert sn.sn_kind_names()[0] == "psi_pass"
+
+
+def test_binding_constants_match_the_header():
+    text = open(os.path.join(ROOT, "include", "sn.h")).read()
+    assert int(re.search(r"#define SN_MAX_FIELDS (\d+)", text).group(1)) == sn.SN_MAX_FIELDS

@@ -201,3 +201,13 @@ def random_small(n: Sequence[int], seed: int, L: float | Sequence[float] = 10.0,
                               g_local=r.uniform(0.0, 0.05))
     return Workload(f"small_{'x'.join(map(str, n))}_{seed}", n, Ls, lumps, kernel, 1e-2, 1,
                     meta={"seed": seed})
+
+
+def random_fields(n: Sequence[int], seed: int, count: int, L: float | Sequence[float] = 10.0,
+                  kernel: KernelParams | None = None):
+    """count coupled fields for the multi-wave-function tests: field j is the
+    state of random_small(n, seed + j) (its own lumps and ramps); the kernel is
+    field 0's unless one is given.  Returns (psis of shape (count, *n), L, kernel)."""
+    ws = [random_small(n, seed + j, L) for j in range(count)]
+    psis = np.stack([w.psi0() for w in ws])
+    return psis, ws[0].L, (kernel if kernel is not None else ws[0].kernel)
