@@ -324,11 +324,11 @@ def run_optical(sn, torch, stream, peak, steps=500):
 
 def fields_bytes_per_cell_step(m: int) -> float:
     """Algorithmic HBM bytes per grid cell and step of m coupled fields on a 3D
-    complex64 grid: per field three psi passes (16 B each) and the half-spectrum
-    read of its potential pass (4 B); the first density pass writes the half
-    spectrum (4 B), each further one reads and writes it (8 B); the three
-    half-spectrum passes once (8 B each).  m = 1 gives the 80 B of one field."""
-    return 52.0 * m + 4.0 + 8.0 * (m - 1) + 24.0
+    complex64 grid: per field three psi passes (16 B each); the fused potential
+    pass reads the half spectrum once for all fields (4 B) and the fused density
+    pass writes it once (4 B); the three half-spectrum passes once (8 B each).
+    m = 1 gives the 80 B of one field."""
+    return 48.0 * m + 8.0 + 24.0
 
 
 def run_fields(sn, torch, stream, peak, m=2, n=256, L=80.0, steps=500):

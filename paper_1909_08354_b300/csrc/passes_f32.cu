@@ -110,10 +110,16 @@ constexpr size_t rho_smem_bytes() {
   }
 }
 
-template <int N, bool STRIDED, int VARIANT, bool TC>
+// FIELDS: a.nfields coupled fields, a.fstride elements apart, in one launch
+// (NPHASE, DENSITY; FP32 engine).  Each tile's potential C2R (NPHASE) or
+// density R2C (DENSITY) runs once for all fields: the fields' lines of a tile
+// follow one another through the kinetic transform, with the potential row
+// kept in registers across them, or their densities summed in registers.
+template <int N, bool STRIDED, int VARIANT, bool TC, bool FIELDS = false>
 __global__ void __launch_bounds__(cta_threads<N>(), min_ctas<N>())
 psi_pass_kernel(PsiPassArgs a) {
   static_assert(!TC || N == tc16::N, "the tensor-core engine handles 256-point lines");
+  static_assert(!FIELDS || (!TC && VARIANT != PSI_PLAIN), "fused fields: FP32 NPHASE, DENSITY");
   using P = Plan<N>;
   constexpr int LPB = lpb<N>(), TSTR = LPB + 1;
   constexpr int E = P::E, T = P::T, NT = LPB * T, LS = P::LS, H = N / 2 + 1;
@@ -174,6 +180,72 @@ psi_pass_kernel(PsiPassArgs a) {
   }
   if constexpr (NPHASE) cp_async_commit();
   __syncthreads();  // tables
+
+  if constexpr (FIELDS) {
+    static_assert(PF, "the fields loop prefetches the next line");
+    const int nf = a.nfields;
+    const size_t fs = (size_t)a.fstride;
+    for (int it = 0; tau < tiles.count; ++it, tau += gridDim.x) {
+      long long line0, o, i;
+      int nvalid;
+      size_t base;
+      tiles.at(tau, l, N, line0, nvalid, base, o, i);
+      const bool valid = l < nvalid;
+      const long long taun = tau + gridDim.x;
+      float vr[E];   // NPHASE: this tile's potential row, for every field
+      float rho[E];  // DENSITY: sum of the fields' |psi|^2
+      if constexpr (NPHASE) {
+        if (taun < tiles.count) stage_rho(rstage + ((it + 1) & 1) * (H * TSTR), taun);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const float* vrow = tile::potential_c2r<N, LPB, CONTIG, false, STRIDED>(
+            rstage + (it & 1) * (H * TSTR), lines, tw_sm, l, t, tabs);
+#pragma unroll
+        for (int m = 0; m < E; ++m) vr[m] = vrow[t + T * m];
+      } else {
+#pragma unroll
+        for (int m = 0; m < E; ++m) rho[m] = 0.f;
+      }
+      for (int j = 0; j < nf; ++j) {
+        cx<float> v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = vn[m];
+        // start the load of the next (tile, field)
+        if (j + 1 < nf) {
+          load_line<E, T>(vn, a.psi + base + (size_t)(j + 1) * fs, ustride, t, valid);
+        } else if (taun < tiles.count) {
+          long long line0n, on, in;
+          int nvalidn;
+          size_t basen;
+          tiles.at(taun, l, N, line0n, nvalidn, basen, on, in);
+          load_line<E, T>(vn, a.psi + basen, ustride, t, l < nvalidn);
+        }
+        if constexpr (NPHASE) {
+          tile::nonlinear_phase<E, T>(v, vr, a.gh, a.vext != nullptr ? a.vext + base : nullptr, a.h,
+                                      ustride, t, valid);
+        }
+        tile::kinetic<N, CONTIG>(v, lines + l * LS, tw_sm, reinterpret_cast<const float4*>(mult_sm),
+                                 t);
+        store_line<E, T>(v, a.psi + base + (size_t)j * fs, ustride, t, valid);
+        if constexpr (DENSITY) {
+#pragma unroll
+          for (int m = 0; m < E; ++m) rho[m] += valid ? cnorm2(v[m]) : 0.f;
+        }
+      }
+      if constexpr (DENSITY) {
+        float2* rh = a.rh_out;
+        auto put = [&](int k, int ll, cx<float> z) {
+          tile::stg_c(rh + (size_t)k * nlines + line0 + ll, z);
+        };
+        tile::density_r2c_rho<N, LPB, CONTIG, decltype(put), false, STRIDED>(rho, lines, tw_sm, l, t,
+                                                                          tid, nvalid, put);
+      }
+      __syncthreads();  // line buffers and the staging tile are reused next iteration
+    }
+    if constexpr (NPHASE) cp_async_wait<0>();
+    return;
+  }
 
   for (int it = 0; tau < tiles.count; ++it, tau += gridDim.x) {
     long long line0, o, i;
@@ -372,11 +444,11 @@ long long host_tiles(long long outer, long long inner) {
   return STRIDED ? outer * ((inner + LPB - 1) / LPB) : (outer + LPB - 1) / LPB;
 }
 
-template <int N, bool STRIDED, int VARIANT, bool TC = false>
+template <int N, bool STRIDED, int VARIANT, bool TC = false, bool FIELDS = false>
 cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
   constexpr size_t smem = psi_smem_bytes<N, VARIANT, TC>();
   constexpr int threads = cta_threads<N>();
-  auto kern = psi_pass_kernel<N, STRIDED, VARIANT, TC>;
+  auto kern = psi_pass_kernel<N, STRIDED, VARIANT, TC, FIELDS>;
   static bool attr_of[kDeviceSlots] = {};
   bool& attr = attr_of[device_slot()];
   if (!attr) {
@@ -437,6 +509,13 @@ cudaError_t rho_dispatch_tc(bool strided, int op, const RhoPassArgs& a, cudaStre
 
 template <int N>
 cudaError_t psi_dispatch(bool strided, int variant, const PsiPassArgs& a, cudaStream_t s) {
+  if (a.nfields > 1 && variant != PSI_PLAIN) {
+    if (strided)
+      return variant == PSI_NPHASE ? launch_psi_t<N, true, PSI_NPHASE, false, true>(a, s)
+                                   : launch_psi_t<N, true, PSI_DENSITY, false, true>(a, s);
+    return variant == PSI_NPHASE ? launch_psi_t<N, false, PSI_NPHASE, false, true>(a, s)
+                                 : launch_psi_t<N, false, PSI_DENSITY, false, true>(a, s);
+  }
   if (strided) {
     switch (variant) {
       case PSI_PLAIN: return launch_psi_t<N, true, PSI_PLAIN>(a, s);
@@ -471,7 +550,10 @@ cudaError_t rho_dispatch(bool strided, int op, const RhoPassArgs& a, cudaStream_
 
 cudaError_t launch_psi_pass_f32(int N, bool strided, int variant, const PsiPassArgs& a,
                                 cudaStream_t s) {
-  if (a.tc != nullptr && N == tc16::N) return psi_dispatch_tc(strided, variant, a, s);
+  if (a.tc != nullptr && N == tc16::N) {
+    if (a.nfields > 1 && variant != PSI_PLAIN) return cudaErrorInvalidValue;  // one field per launch
+    return psi_dispatch_tc(strided, variant, a, s);
+  }
   switch (N) {
     case 8: return psi_dispatch<8>(strided, variant, a, s);
     case 16: return psi_dispatch<16>(strided, variant, a, s);

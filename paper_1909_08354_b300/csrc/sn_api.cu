@@ -309,13 +309,20 @@ LineGeom psi_geom(sn_grid g, int a) {
 
 // ---- fused FP32 step ----------------------------------------------------------
 
-// Field j of the grid.  With several fields the local term g rho of the total
-// density is applied through the Green's multiplier (rho_passes), not per field.
-sn_status psi_pass(sn_grid g, int j, int a, int variant, int full, double dt) {
+// Fields j .. j + nf - 1 of the grid in one launch.  A plain pass takes them
+// as nf times the lines (field-major, the fields extend the slowest axis); a
+// potential or density pass of the FP32 engine runs the fused fields kernel,
+// one C2R or R2C per tile for all of them.  A density pass of field j > 0
+// alone adds to the half spectrum.  With several fields the local term g rho
+// of the total density is applied through the Green's multiplier
+// (rho_passes), not per field.
+sn_status psi_pass(sn_grid g, int j, int nf, int a, int variant, int full, double dt) {
   const LineGeom lg = psi_geom(g, a);
   PsiPassArgs pa{};
   pa.psi = reinterpret_cast<float2*>(g->psi) + (size_t)j * g->cells;
-  pa.outer = lg.outer;
+  pa.outer = lg.outer * (variant == PSI_PLAIN ? nf : 1);
+  pa.nfields = variant == PSI_PLAIN ? 1 : nf;
+  pa.fstride = g->cells;
   pa.inner = lg.inner;
   pa.mult = g->mult32[a][full];
   pa.lift = g->lift32[a][full];
@@ -328,11 +335,11 @@ sn_status psi_pass(sn_grid g, int j, int a, int variant, int full, double dt) {
   pa.rh_accum = variant == PSI_DENSITY && j > 0;
   pa.tc = g->engine == SN_ENGINE_TC16 ? g->tc_frag : nullptr;
   const double P = g->n[a] / 2 + 1, lines = (double)g->cells / g->n[a];
-  double bytes = 16.0 * g->cells;
+  double bytes = 16.0 * g->cells * nf;
   int kind = K_PSI;
   if (variant == PSI_NPHASE) {
     bytes += 8.0 * P * lines;  // C2R reads the half spectrum along this axis
-    if (g->has_vext) bytes += 4.0 * g->cells;
+    if (g->has_vext) bytes += 4.0 * g->cells * nf;
     kind = K_PSI_NPHASE;
   } else if (variant == PSI_DENSITY) {
     bytes += (j > 0 ? 16.0 : 8.0) * P * lines;
@@ -433,8 +440,12 @@ sn_status step_f32(sn_grid g, double dt, int nsteps) {
       int variant = PSI_PLAIN;
       if (i == 0 && r > 0) variant = PSI_NPHASE;
       if (i == d - 1 && r < nsteps) variant = PSI_DENSITY;
-      for (int j = 0; j < g->fields; ++j) {
-        sn_status st = psi_pass(g, j, order[i], variant, full, dt);
+      // the tensor-core potential and density passes take one field per launch
+      const bool tc_axis = g->engine == SN_ENGINE_TC16 && g->n[order[i]] == 256;
+      const bool one_launch = variant == PSI_PLAIN || !tc_axis;
+      const int nf = one_launch ? g->fields : 1;
+      for (int j = 0; j < g->fields; j += nf) {
+        sn_status st = psi_pass(g, j, nf, order[i], variant, full, dt);
         if (st != SN_OK) return st;
       }
     }

@@ -39,6 +39,8 @@ struct PsiPassArgs {
   float gh;                // NPHASE: g * h
   float2* rh_out;          // DENSITY: half spectrum [N/2+1][lines]
   int rh_accum;            // DENSITY: add to rh_out (the density of a further field)
+  int nfields;             // NPHASE, DENSITY (FP32 engine): fields in this launch (0, 1: one)
+  long long fstride;       // elements from one field to the next
   const uint4* tc;         // tensor-core fragment table (256-point lines), or NULL
 };
 

@@ -193,13 +193,14 @@ __device__ __forceinline__ const float* potential_c2r(const cx<float>* rtile, cx
 // low by ~3e-8 at angles below 0.03: a mass drift of -1.6e-8 per step under a
 // strong nonlocal potential (Eq. 4).  The bias is now ~1e-10 (+3e-9 below
 // 1e-3 rad, where c itself rounds one-sidedly to the grid at 1).
-template <int E, int T>
-__device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float* vrow,
-                                                float gh, const float* vx, float h,
-                                                unsigned ustride, int t, bool valid) {
+// vat(m): V at position t + T m of the line.
+template <int E, int T, class VAt>
+__device__ __forceinline__ void nonlinear_phase_at(cx<float> (&v)[E], VAt vat, float gh,
+                                                   const float* vx, float h, unsigned ustride,
+                                                   int t, bool valid) {
 #pragma unroll
   for (int m = 0; m < E; ++m) {
-    float th = vrow[t + T * m] + gh * cnorm2(v[m]);
+    float th = vat(m) + gh * cnorm2(v[m]);
     if (vx != nullptr && valid) th += vx[(unsigned)(t + T * m) * ustride] * h;
     const float kq = rintf(th * 0.159154943091895336f);
     float r = fmaf(-kq, 6.28318548202514648f, th);
@@ -213,6 +214,20 @@ __device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float* 
     sn = fmaf(sn, e, sn);
     v[m] = {v[m].re * cs + v[m].im * sn, v[m].im * cs - v[m].re * sn};  // v * exp(-i th)
   }
+}
+// V from the line's row in shared memory
+template <int E, int T>
+__device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float* vrow,
+                                                float gh, const float* vx, float h,
+                                                unsigned ustride, int t, bool valid) {
+  nonlinear_phase_at<E, T>(v, [&](int m) { return vrow[t + T * m]; }, gh, vx, h, ustride, t, valid);
+}
+// V held in registers, vr[m] at position t + T m
+template <int E, int T>
+__device__ __forceinline__ void nonlinear_phase(cx<float> (&v)[E], const float (&vr)[E],
+                                                float gh, const float* vx, float h,
+                                                unsigned ustride, int t, bool valid) {
+  nonlinear_phase_at<E, T>(v, [&](int m) { return vr[m]; }, gh, vx, h, ustride, t, valid);
 }
 
 // FFT . m . IFFT along my line, m = exp(i A k^2 tau) / N given per k as a
@@ -243,18 +258,33 @@ __device__ __forceinline__ void kinetic(cx<float> (&v)[Plan<N>::E], cx<float>* l
 // for the valid lines; the calls are spread over all threads with ll fastest.
 // REMAP: as in potential_c2r, the packed transform runs in the contiguous
 // mapping, fed with |psi|^2 through shared memory.
+// density_r2c_rho: the same from the density itself (rho[m] at position
+// t + T m of line l; 0 on invalid lines), e.g. a sum over several fields.
+template <int N, int LPB, bool CONTIG, class Put, bool TC = false, bool REMAP = false>
+__device__ __forceinline__ void density_r2c_rho(const float (&rho)[Plan<N>::E], cx<float>* lines,
+                                                const cx<float>* tw, int l, int t, int tid,
+                                                int nvalid, Put put,
+                                                const tc16::Tabs* tb = nullptr);
+
 template <int N, int LPB, bool CONTIG, class Put, bool TC = false, bool REMAP = false>
 __device__ __forceinline__ void density_r2c(const cx<float> (&psi)[Plan<N>::E], bool valid,
                                             cx<float>* lines, const cx<float>* tw, int l, int t,
                                             int tid, int nvalid, Put put,
                                             const tc16::Tabs* tb = nullptr) {
+  float rho[Plan<N>::E];
+#pragma unroll
+  for (int m = 0; m < Plan<N>::E; ++m) rho[m] = valid ? cnorm2(psi[m]) : 0.f;
+  density_r2c_rho<N, LPB, CONTIG, Put, TC, REMAP>(rho, lines, tw, l, t, tid, nvalid, put, tb);
+}
+
+template <int N, int LPB, bool CONTIG, class Put, bool TC, bool REMAP>
+__device__ __forceinline__ void density_r2c_rho(const float (&rho)[Plan<N>::E], cx<float>* lines,
+                                                const cx<float>* tw, int l, int t, int tid,
+                                                int nvalid, Put put, const tc16::Tabs* tb) {
   using C = Cfg<N, LPB>;
   constexpr int E = C::E, T = C::T, NT = C::NT, LS = C::LS, H = C::H, TSTR = C::TSTR;
   constexpr int HALF = LPB / 2;
   cx<float> v[E];
-  float rho[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) rho[m] = valid ? cnorm2(psi[m]) : 0.f;
   constexpr bool CC = REMAP || CONTIG;
   const int lc = REMAP ? tid / T : l;
   const int tc = REMAP ? tid % T : t;
