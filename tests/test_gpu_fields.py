@@ -48,7 +48,7 @@ def inputs(shape, m, seed, L=10.0):
 
 
 CASES = [((64, 128), 2), ((8, 8), 3), ((128, 32), 4), ((32, 16, 64), 2), ((16, 16, 16), 3),
-         ((8, 32, 256), 2)]
+         ((8, 32, 256), 2), ((16, 1024), 2), ((512, 16), 3), ((8, 512, 8), 2)]
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
