@@ -89,10 +89,13 @@ __device__ __forceinline__ void cp_async_wait() {
 // and for P1 two staging tiles of the half spectrum.  The tensor-core engine
 // (TC, 256-point lines) keeps its fragment and twiddle tables, a padded copy
 // of the kinetic factors and padded line buffers instead.
-template <int N, int VARIANT, bool TC>
+template <int N, int VARIANT, bool TC, bool FIELDS = false>
 constexpr size_t psi_smem_bytes() {
+  // P1: two half-spectrum staging tiles; fused-fields P3: the density sum
   constexpr size_t stage =
-      (VARIANT == PSI_NPHASE ? 2 * (N / 2 + 1) * (lpb<N>() + 1) : 0) * sizeof(cx<float>);
+      VARIANT == PSI_NPHASE ? 2 * (N / 2 + 1) * (lpb<N>() + 1) * sizeof(cx<float>)
+      : (VARIANT == PSI_DENSITY && FIELDS) ? (size_t)N * (lpb<N>() + 1) * sizeof(float)
+                                           : 0;
   if constexpr (TC) {
     return sizeof(tc16::Tabs) + 2 * tc16::MT * sizeof(float2) +
            (size_t)lpb<N>() * tc16::LS * sizeof(float2) + stage;
@@ -114,7 +117,8 @@ constexpr size_t rho_smem_bytes() {
 // (NPHASE, DENSITY; FP32 engine).  Each tile's potential C2R (NPHASE) or
 // density R2C (DENSITY) runs once for all fields: the fields' lines of a tile
 // follow one another through the kinetic transform, with the potential row
-// kept in registers across them, or their densities summed in registers.
+// kept across them in the tile's staging buffer (free once the C2R has read
+// it), or their densities summed in registers.
 template <int N, bool STRIDED, int VARIANT, bool TC, bool FIELDS = false>
 __global__ void __launch_bounds__(cta_threads<N>(), min_ctas<N>())
 psi_pass_kernel(PsiPassArgs a) {
@@ -192,8 +196,11 @@ psi_pass_kernel(PsiPassArgs a) {
       tiles.at(tau, l, N, line0, nvalid, base, o, i);
       const bool valid = l < nvalid;
       const long long taun = tau + gridDim.x;
-      float vr[E];   // NPHASE: this tile's potential row, for every field
-      float rho[E];  // DENSITY: sum of the fields' |psi|^2
+      // NPHASE: this tile's potential row, for every field; DENSITY: the sum of
+      // the fields' |psi|^2.  Both at [position][line] with an odd row pitch
+      // (conflict-free in both mappings; a staging tile's (N + 2)(LPB + 1)
+      // floats fit N (LPB + 1)); each thread reads back only what it wrote.
+      float* keep = reinterpret_cast<float*>(rstage + (NPHASE ? (it & 1) * (H * TSTR) : 0));
       if constexpr (NPHASE) {
         if (taun < tiles.count) stage_rho(rstage + ((it + 1) & 1) * (H * TSTR), taun);
         cp_async_commit();
@@ -201,11 +208,9 @@ psi_pass_kernel(PsiPassArgs a) {
         __syncthreads();
         const float* vrow = tile::potential_c2r<N, LPB, CONTIG, false, STRIDED>(
             rstage + (it & 1) * (H * TSTR), lines, tw_sm, l, t, tabs);
+        // the C2R ended with a CTA barrier after its last read of the staging tile
 #pragma unroll
-        for (int m = 0; m < E; ++m) vr[m] = vrow[t + T * m];
-      } else {
-#pragma unroll
-        for (int m = 0; m < E; ++m) rho[m] = 0.f;
+        for (int m = 0; m < E; ++m) keep[(t + T * m) * TSTR + l] = vrow[t + T * m];
       }
       for (int j = 0; j < nf; ++j) {
         cx<float> v[E];
@@ -222,18 +227,25 @@ psi_pass_kernel(PsiPassArgs a) {
           load_line<E, T>(vn, a.psi + basen, ustride, t, l < nvalidn);
         }
         if constexpr (NPHASE) {
-          tile::nonlinear_phase<E, T>(v, vr, a.gh, a.vext != nullptr ? a.vext + base : nullptr, a.h,
-                                      ustride, t, valid);
+          tile::nonlinear_phase_at<E, T>(
+              v, [&](int m) { return keep[(t + T * m) * TSTR + l]; }, a.gh,
+              a.vext != nullptr ? a.vext + base : nullptr, a.h, ustride, t, valid);
         }
         tile::kinetic<N, CONTIG>(v, lines + l * LS, tw_sm, reinterpret_cast<const float4*>(mult_sm),
                                  t);
         store_line<E, T>(v, a.psi + base + (size_t)j * fs, ustride, t, valid);
         if constexpr (DENSITY) {
 #pragma unroll
-          for (int m = 0; m < E; ++m) rho[m] += valid ? cnorm2(v[m]) : 0.f;
+          for (int m = 0; m < E; ++m) {
+            float& r = keep[(t + T * m) * TSTR + l];
+            r = (j > 0 ? r : 0.f) + (valid ? cnorm2(v[m]) : 0.f);
+          }
         }
       }
       if constexpr (DENSITY) {
+        float rho[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) rho[m] = keep[(t + T * m) * TSTR + l];
         float2* rh = a.rh_out;
         auto put = [&](int k, int ll, cx<float> z) {
           tile::stg_c(rh + (size_t)k * nlines + line0 + ll, z);
@@ -446,7 +458,7 @@ long long host_tiles(long long outer, long long inner) {
 
 template <int N, bool STRIDED, int VARIANT, bool TC = false, bool FIELDS = false>
 cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
-  constexpr size_t smem = psi_smem_bytes<N, VARIANT, TC>();
+  constexpr size_t smem = psi_smem_bytes<N, VARIANT, TC, FIELDS>();
   constexpr int threads = cta_threads<N>();
   auto kern = psi_pass_kernel<N, STRIDED, VARIANT, TC, FIELDS>;
   static bool attr_of[kDeviceSlots] = {};
