@@ -184,3 +184,43 @@ def test_fields_and_the_fluid_model_exclude_each_other():
         assert e.value.status == sn.SN_ENOTSUP
     finally:
         g.close()
+
+
+def test_fields_through_device_pointers_on_a_torch_stream():
+    torch = pytest.importorskip("torch")
+    psis, L, kw = inputs((32, 64), 2, seed=300)
+    psis = psis.astype(np.complex64)
+    s = torch.cuda.Stream()
+    g = sn.Grid((32, 64), L, "c64", stream=s.cuda_stream)
+    try:
+        g.set_fields(2)
+        g.set_kernel(**kw)
+        dev = torch.from_numpy(psis).cuda()
+        torch.cuda.synchronize()
+        g.set_state(dev)
+        g.step(0.02, 3)
+        out = torch.empty_like(dev)
+        g.get_state(out)
+        g.sync()
+    finally:
+        g.close()
+    host = gpu_fields(psis, L, kw, "c64", 0.02, 3)
+    assert np.array_equal(out.cpu().numpy(), host)  # the same kernels, bit for bit
+
+
+def test_launches_per_step_do_not_grow_with_the_fields():
+    # one launch per pass for all fields: a 3D step is six launches for any count
+    counts = []
+    for m in (1, 3):
+        psis, L, kw = inputs((16, 32, 16), m, seed=400)
+        g = sn.Grid((16, 32, 16), L, "c64")
+        try:
+            g.set_fields(m)
+            g.set_kernel(**kw)
+            g.set_state(psis.astype(np.complex64))
+            n0 = g.launch_count()
+            g.step(0.02, 10)
+            counts.append(g.launch_count() - n0)
+        finally:
+            g.close()
+    assert counts[0] == counts[1] == 6 * 10 + 3
