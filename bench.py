@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-fno", action="store_true")
     p.add_argument("--no-fluid", action="store_true",
                    help="skip the Eq. 16 fluid model (GR and NMC) on a 512^2 complex128 plane")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default schedule of the fused passes")
     p.add_argument("--no-fields", action="store_true",
                    help="skip the two coupled fields at 256^3")
     p.add_argument("--no-optical", action="store_true",
@@ -530,6 +532,9 @@ def main():
         g.set_engine(sn.SN_ENGINE_TC16)
     g.set_kernel(**kw)
     g.set_state(psi0)
+    # schedule of the fused passes, picked by timing them (setup, before the timed region;
+    # the state is left as it was)
+    schedule = None if args.no_autotune else g.autotune(w.dt, steps=10)
     m0 = g.observables()["mass"]
 
     # ---- device-resident throughput
@@ -643,6 +648,9 @@ def main():
                                    f"dt=1e-2",
                        "parallelism": "replicas" if world > 1 else "single",
                        "engine": args.engine,
+                       "schedule": ("default" if schedule is None else
+                                    "autotuned, CTAs per SM by [pass kind][axis] (0 = as many as "
+                                    f"fit): {schedule}"),
                        "l2": "working set 202 MB > 126 MB L2; no flush"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom) if args.engine == "fp32" else None,

@@ -205,6 +205,27 @@ sn_status sn_profile_step(sn_grid g, double dt, int nsteps, double* ms, long lon
 /* Name of kernel kind k, or NULL past the last kind. */
 const char* sn_kind_name(int k);
 
+/* Schedule of the fused complex64 passes: for each pass kind k < SN_SCHED_KINDS
+ * (the first kinds of sn_kind_name: psi_pass, psi_pass_nphase,
+ * psi_pass_density, rho_fwd, rho_green, rho_inv) and axis a < 3 (psi passes:
+ * the axis of the transformed lines; half-spectrum passes: the half axis), the
+ * CTAs per SM of its persistent grid: 0 = as many as fit (the default),
+ * 1 .. SN_SCHED_MAX_CTAS = at most that many, -1 = one CTA per tile of lines.
+ * Every schedule computes bit-identical results; only the speed differs.
+ * Layout of the 3 SN_SCHED_KINDS values: [3 k + a].
+ * sn_get_schedule: out holds at least that many values.  sn_set_schedule:
+ * exactly that many, each in [-1, SN_SCHED_MAX_CTAS], else SN_EINVAL.
+ * sn_autotune: time each pass kind and axis of sn_step(g, dt, steps) under
+ * the candidates 0, -1, 1, 2, 3, 4, 6, 8, and keep for each the fastest if it
+ * beats the default by more than 3% (device time by CUDA events; the state
+ * and the step counter are restored; blocks until done).  Errors: SN_ENOTSUP
+ * on SN_C128 grids, SN_EINVAL (non-finite dt, steps < 1), SN_ENOMEM, SN_ECUDA. */
+#define SN_SCHED_KINDS 6
+#define SN_SCHED_MAX_CTAS 64
+sn_status sn_get_schedule(sn_grid g, int* out, int n);
+sn_status sn_set_schedule(sn_grid g, const int* in, int n);
+sn_status sn_autotune(sn_grid g, double dt, int steps);
+
 /* Line-transform engine of a complex64 grid's fused step.  Every pass of
  * sn_step is a batch of 1D DFTs along one axis (the split-step Fourier method
  * of Sec. III: the kinetic factor of Eq. 1 per axis, and the spectral solve of

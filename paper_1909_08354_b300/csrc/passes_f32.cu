@@ -414,10 +414,13 @@ rho_pass_kernel(RhoPassArgs a) {
   }
 }
 
-// Persistent grid: as many CTAs as fit on the device at once, capped by the
-// number of tiles.
+// Persistent grid: as many CTAs as fit on the device at once (cps = 0), at
+// most cps per SM (cps > 0), or one CTA per tile (cps = -1); never more CTAs
+// than tiles.  The kernels walk their tiles with a stride of gridDim.x, so
+// every choice computes the same values.
 template <typename K>
-unsigned persistent_ctas(K kern, int threads, size_t smem, long long ntiles) {
+unsigned persistent_ctas(K kern, int threads, size_t smem, long long ntiles, int cps) {
+  if (cps < 0) return (unsigned)(ntiles < 0x7fffffffLL ? ntiles : 0x7fffffffLL);
   static int sms_of[kDeviceSlots] = {};
   const int slot = device_slot();
   int& sms = sms_of[slot];
@@ -431,6 +434,7 @@ unsigned persistent_ctas(K kern, int threads, size_t smem, long long ntiles) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
+  if (cps > 0 && cps < per_sm) per_sm = cps;
   const long long cap = (long long)per_sm * sms;
   return (unsigned)(ntiles < cap ? ntiles : cap);
 }
@@ -469,7 +473,8 @@ cudaError_t launch_psi_t(const PsiPassArgs& a, cudaStream_t s) {
     attr = true;
   }
   const long long ntiles = host_tiles<lpb<N>(), STRIDED>(a.outer, a.inner);
-  return launch_pdl(kern, persistent_ctas(kern, threads, smem, ntiles), threads, smem, s, a);
+  return launch_pdl(kern, persistent_ctas(kern, threads, smem, ntiles, a.ctas_per_sm), threads, smem,
+                    s, a);
 }
 
 template <int N, bool STRIDED, int OP, bool TC = false>
@@ -485,7 +490,8 @@ cudaError_t launch_rho_t(const RhoPassArgs& a, cudaStream_t s) {
     attr = true;
   }
   const long long ntiles = host_tiles<lpb<N>(), STRIDED>(a.outer, a.inner);
-  return launch_pdl(kern, persistent_ctas(kern, threads, smem, ntiles), threads, smem, s, a);
+  return launch_pdl(kern, persistent_ctas(kern, threads, smem, ntiles, a.ctas_per_sm), threads, smem,
+                    s, a);
 }
 
 // tensor-core engine: 256-point lines when the caller passes the fragment table

@@ -57,6 +57,7 @@ double wavenumber(int j, int n, double L) {
 
 struct Launch {
   int kind;
+  int axis;  // psi passes: the line axis; half-spectrum passes: the half axis
   double bytes;
   cudaEvent_t e0, e1;
 };
@@ -176,6 +177,12 @@ struct sn_grid_s {
   int engine = SN_ENGINE_FP32;
   uint4* tc_frag = nullptr;
 
+  // schedule of the fused FP32 passes: CTAs per SM (0 = as many as fit,
+  // k > 0 = at most k, -1 = one per tile), by pass kind (K_PSI .. K_RHO_INV)
+  // and axis (psi passes: the line axis; half-spectrum passes: the half axis)
+  int sched[SN_SCHED_KINDS][3] = {};
+  int cur_axis = 0;
+
   // profiling
   bool profiling = false;
   std::vector<Launch> prof;
@@ -221,6 +228,7 @@ struct LaunchScope {
   Launch rec;
   LaunchScope(sn_grid g_, int kind, double bytes) : g(g_) {
     rec.kind = kind;
+    rec.axis = g->cur_axis;
     rec.bytes = bytes;
     rec.e0 = rec.e1 = nullptr;
     if (g->profiling) {
@@ -345,6 +353,8 @@ sn_status psi_pass(sn_grid g, int j, int nf, int a, int variant, int full, doubl
     bytes += (j > 0 ? 16.0 : 8.0) * P * lines;
     kind = K_PSI_DENSITY;
   }
+  pa.ctas_per_sm = g->sched[kind][a];
+  g->cur_axis = a;
   SN_LAUNCH(g, kind, bytes, launch_psi_pass_f32(g->n[a], lg.strided, variant, pa, g->stream));
   return SN_OK;
 }
@@ -372,7 +382,9 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
   ra.mu2 = (float)mu2;
   ra.cL = g->fields > 1 ? (float)(g->kp.g_local * scale) : 0.f;
   ra.tc = g->engine == SN_ENGINE_TC16 ? g->tc_frag : nullptr;
+  g->cur_axis = h;
   if (d == 2) {
+    ra.ctas_per_sm = g->sched[K_RHO_GREEN][h];
     const int c = rest[0];
     ra.outer = P;
     ra.inner = 1;
@@ -407,6 +419,7 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
     RhoPassArgs x = ra;
     const bool st = geom(y, x);
     x.tw = g->tw32[log2i(g->n[y])];
+    x.ctas_per_sm = g->sched[K_RHO_FWD][h];
     SN_LAUNCH(g, K_RHO_FWD, bytes, launch_rho_pass_f32(g->n[y], st, RHO_FWD, x, g->stream));
   }
   {
@@ -415,12 +428,14 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
     x.tw = g->tw32[log2i(g->n[third])];
     x.k2p = g->k2_32[h];
     x.k2l = g->k2_32[third];
+    x.ctas_per_sm = g->sched[K_RHO_GREEN][h];
     SN_LAUNCH(g, K_RHO_GREEN, bytes, launch_rho_pass_f32(g->n[third], st, RHO_GREEN, x, g->stream));
   }
   {
     RhoPassArgs x = ra;
     const bool st = geom(y, x);
     x.tw = g->tw32[log2i(g->n[y])];
+    x.ctas_per_sm = g->sched[K_RHO_INV][h];
     SN_LAUNCH(g, K_RHO_INV, bytes, launch_rho_pass_f32(g->n[y], st, RHO_INV, x, g->stream));
   }
   return SN_OK;
@@ -1040,6 +1055,96 @@ sn_status sn_profile_step(sn_grid g, double dt, int nsteps, double* ms, long lon
   g->prof.clear();
   if (st != SN_OK) return st;
   if (e != cudaSuccess) return cuda_fail(g, e, "sn_profile_step");
+  return SN_OK;
+}
+
+sn_status sn_get_schedule(sn_grid g, int* out, int n) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_get_schedule: grid is NULL");
+  if (!out || n < SN_SCHED_KINDS * 3)
+    return fail(g, SN_EINVAL, "sn_get_schedule: out must hold SN_SCHED_KINDS * 3 values");
+  for (int k = 0; k < SN_SCHED_KINDS; ++k)
+    for (int a = 0; a < 3; ++a) out[3 * k + a] = g->sched[k][a];
+  return SN_OK;
+}
+
+sn_status sn_set_schedule(sn_grid g, const int* in, int n) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_set_schedule: grid is NULL");
+  if (!in || n != SN_SCHED_KINDS * 3)
+    return fail(g, SN_EINVAL, "sn_set_schedule: in must hold SN_SCHED_KINDS * 3 values");
+  for (int i = 0; i < n; ++i)
+    if (in[i] < -1 || in[i] > SN_SCHED_MAX_CTAS)
+      return fail(g, SN_EINVAL, "sn_set_schedule: values must be in [-1, SN_SCHED_MAX_CTAS]");
+  for (int k = 0; k < SN_SCHED_KINDS; ++k)
+    for (int a = 0; a < 3; ++a) g->sched[k][a] = in[3 * k + a];
+  return SN_OK;
+}
+
+// Times every pass kind and axis of the fused step under each candidate
+// schedule (steps profiled steps after one unprofiled step per candidate) and
+// keeps, per pass, the fastest candidate when it beats the default by more
+// than 3%.  The state and the step counter are restored.
+sn_status sn_autotune(sn_grid g, double dt, int steps) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_autotune: grid is NULL");
+  if (g->dtype != SN_C64)
+    return fail(g, SN_ENOTSUP, "sn_autotune: the schedule applies to the fused complex64 passes");
+  if (!std::isfinite(dt) || steps < 1)
+    return fail(g, SN_EINVAL, "sn_autotune: dt must be finite and steps >= 1");
+  sn_status st = ensure_mult_tables(g, dt);
+  if (st != SN_OK) return st;
+  const size_t bytes = (size_t)g->fields * g->cells * sizeof(float2);
+  void* keep = nullptr;
+  cudaError_t e = cudaMalloc(&keep, bytes);
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaMalloc(autotune state)");
+  e = cudaMemcpyAsync(keep, g->psi, bytes, cudaMemcpyDeviceToDevice, g->stream);
+  const long long step0 = g->step;
+  int saved[SN_SCHED_KINDS][3];
+  std::memcpy(saved, g->sched, sizeof(saved));
+  const int cand[] = {0, -1, 1, 2, 3, 4, 6, 8};
+  double t_of[sizeof(cand) / sizeof(cand[0])][SN_SCHED_KINDS][3] = {};
+  for (size_t c = 0; c < sizeof(cand) / sizeof(cand[0]) && e == cudaSuccess && st == SN_OK; ++c) {
+    for (int k = 0; k < SN_SCHED_KINDS; ++k)
+      for (int a = 0; a < 3; ++a) g->sched[k][a] = cand[c];
+    st = do_step(g, dt, 1);
+    if (st != SN_OK) break;
+    g->profiling = true;
+    g->prof.clear();
+    st = do_step(g, dt, steps);
+    g->profiling = false;
+    e = cudaStreamSynchronize(g->stream);
+    double ms[SN_SCHED_KINDS][3] = {};
+    int cnt[SN_SCHED_KINDS][3] = {};
+    for (const Launch& L : g->prof) {
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, L.e0, L.e1);
+      if (L.kind < SN_SCHED_KINDS && L.axis >= 0 && L.axis < 3) {
+        ms[L.kind][L.axis] += t;
+        cnt[L.kind][L.axis] += 1;
+      }
+      cudaEventDestroy(L.e0);
+      cudaEventDestroy(L.e1);
+    }
+    g->prof.clear();
+    for (int k = 0; k < SN_SCHED_KINDS; ++k)
+      for (int a = 0; a < 3; ++a) t_of[c][k][a] = cnt[k][a] ? ms[k][a] / cnt[k][a] : 0.0;
+  }
+  if (e == cudaSuccess && st == SN_OK) {
+    for (int k = 0; k < SN_SCHED_KINDS; ++k)
+      for (int a = 0; a < 3; ++a) {
+        int best = 0;  // cand[0], the default
+        for (size_t c = 1; c < sizeof(cand) / sizeof(cand[0]); ++c)
+          if (t_of[c][k][a] > 0.0 && t_of[c][k][a] < t_of[best][k][a]) best = (int)c;
+        g->sched[k][a] = t_of[best][k][a] < 0.97 * t_of[0][k][a] ? cand[best] : 0;
+      }
+  } else {
+    std::memcpy(g->sched, saved, sizeof(saved));
+  }
+  cudaError_t e2 = cudaMemcpyAsync(g->psi, keep, bytes, cudaMemcpyDeviceToDevice, g->stream);
+  if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(g->stream);
+  cudaFree(keep);
+  g->step = step0;
+  if (st != SN_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(g, e, "sn_autotune");
+  if (e2 != cudaSuccess) return cuda_fail(g, e2, "sn_autotune: restoring the state");
   return SN_OK;
 }
 

@@ -41,6 +41,7 @@ struct PsiPassArgs {
   int rh_accum;            // DENSITY: add to rh_out (the density of a further field)
   int nfields;             // NPHASE, DENSITY (FP32 engine): fields in this launch (0, 1: one)
   long long fstride;       // elements from one field to the next
+  int ctas_per_sm;         // schedule: 0 = as many as fit, k > 0 = at most k, -1 = one per tile
   const uint4* tc;         // tensor-core fragment table (256-point lines), or NULL
 };
 
@@ -54,6 +55,7 @@ struct RhoPassArgs {
   long long mid_n;   // GREEN, contiguous lines: outer = plane * mid_n + mid
   float cN, cY, mu2; // GREEN: K = cN/k2 + cY/(k2 + mu2), zero at k2 = 0
   float cL;          // GREEN: constant added to K at every k (a local term)
+  int ctas_per_sm;   // schedule, as in PsiPassArgs
   const uint4* tc;   // tensor-core fragment table (256-point lines), or NULL
 };
 

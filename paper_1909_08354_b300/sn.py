@@ -8,6 +8,7 @@ arrays or CPU torch tensors (host memory, pinned or not) or CUDA torch tensors
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 from typing import Optional, Sequence
 
@@ -43,6 +44,7 @@ def _kernel(coeff_lap=-0.5, G=1.0, alpha_Y=0.0, lambda_Y=1.0, g_local=0.0, zero_
 
 SN_GRAVITY_GR, SN_GRAVITY_NMC = 0, 1
 SN_MAX_FIELDS = 16  # include/sn.h
+SN_SCHED_KINDS, SN_SCHED_MAX_CTAS = 6, 64  # include/sn.h
 
 
 class SnFluid(ctypes.Structure):
@@ -86,6 +88,9 @@ _SIGNATURES = [
     ("sn_set_engine", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sn_set_fluid", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SnFluid)]),
     ("sn_set_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("sn_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("sn_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
     ("sn_get_fields", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_test_line_fft_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
@@ -536,6 +541,50 @@ class Batch:
 
 
 # ----------------------------------------------------------------------------
+# Schedule cache (JSON): {key: [3 * SN_SCHED_KINDS CTAs-per-SM values]}
+# ----------------------------------------------------------------------------
+
+def schedule_key(device: str, n: Sequence[int], engine: int, fields: int) -> str:
+    return f"{device}|{'x'.join(str(int(v)) for v in n)}|c64|engine{int(engine)}|fields{int(fields)}"
+
+
+def load_schedule(path: str, key: str):
+    """The cached schedule of key, or None (no file, no entry, or a malformed one)."""
+    try:
+        with open(path) as f:
+            vals = json.load(f).get(key)
+    except (OSError, ValueError, AttributeError):
+        return None
+    if (not isinstance(vals, list) or len(vals) != 3 * SN_SCHED_KINDS
+            or not all(isinstance(v, int) and -1 <= v <= SN_SCHED_MAX_CTAS for v in vals)):
+        return None
+    return vals
+
+
+def store_schedule(path: str, key: str, vals) -> None:
+    try:
+        with open(path) as f:
+            table = json.load(f)
+        if not isinstance(table, dict):
+            table = {}
+    except (OSError, ValueError):
+        table = {}
+    table[key] = [int(v) for v in vals]
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _device_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(torch.cuda.current_device())
+    except Exception:  # no torch or no device: one shared key
+        return "unknown-device"
+
+
+# ----------------------------------------------------------------------------
 # Convenience object over the same calls
 # ----------------------------------------------------------------------------
 
@@ -548,6 +597,7 @@ class Grid:
         self.dtype = SN_C64 if dtype in ("c64", "complex64", SN_C64) else SN_C128
         self.cells = int(np.prod(self.n))
         self.fields = 1
+        self.engine = SN_ENGINE_FP32
         self.h = sn_create_grid(self.n, self.L, self.dtype, stream)
 
     @property
@@ -592,9 +642,39 @@ class Grid:
                     float(rho_floor))
         _check(self.h, lib().sn_set_fluid(self.h, ctypes.byref(f)))
 
+    def schedule(self) -> list:
+        """CTAs per SM of each fused pass kind and axis, [3 k + a] (sn_get_schedule)."""
+        buf = (ctypes.c_int * (3 * SN_SCHED_KINDS))()
+        _check(self.h, lib().sn_get_schedule(self.h, buf, len(buf)))
+        return list(buf)
+
+    def set_schedule(self, values):
+        vals = [int(v) for v in values]
+        buf = (ctypes.c_int * len(vals))(*vals)
+        _check(self.h, lib().sn_set_schedule(self.h, buf, len(vals)))
+
+    def autotune(self, dt: float, steps: int = 10, cache: Optional[str] = None,
+                 device: Optional[str] = None) -> list:
+        """Pick the schedule of the fused passes by timing them (sn_autotune),
+        or take it from the JSON file `cache` when it holds one for this device,
+        shape, engine and field count; a new result is added to the file."""
+        key = schedule_key(device if device is not None else _device_name(), self.n,
+                           self.engine, self.fields)
+        if cache:
+            got = load_schedule(cache, key)
+            if got is not None:
+                self.set_schedule(got)
+                return got
+        _check(self.h, lib().sn_autotune(self.h, float(dt), int(steps)))
+        vals = self.schedule()
+        if cache:
+            store_schedule(cache, key, vals)
+        return vals
+
     def set_engine(self, engine: int):
         """SN_ENGINE_FP32 or SN_ENGINE_TC16 (tensor cores on 256-point axes)."""
         _check(self.h, lib().sn_set_engine(self.h, int(engine)))
+        self.engine = int(engine)
 
     def sync(self):
         sn_sync(self.h)

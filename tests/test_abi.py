@@ -70,3 +70,44 @@ def test_null_handles_are_rejected():
 def test_binding_constants_match_the_header():
     text = open(os.path.join(ROOT, "include", "sn.h")).read()
     assert int(re.search(r"#define SN_MAX_FIELDS (\d+)", text).group(1)) == sn.SN_MAX_FIELDS
+
+
+def test_schedule_constants_match_the_header():
+    text = open(os.path.join(ROOT, "include", "sn.h")).read()
+    assert int(re.search(r"#define SN_SCHED_KINDS (\d+)", text).group(1)) == sn.SN_SCHED_KINDS
+    assert int(re.search(r"#define SN_SCHED_MAX_CTAS (\d+)", text).group(1)) == sn.SN_SCHED_MAX_CTAS
+    # the schedule kinds are the first kernel kinds, in order
+    assert sn.sn_kind_names()[:sn.SN_SCHED_KINDS] == ["psi_pass", "psi_pass_nphase",
+                                                      "psi_pass_density", "rho_fwd", "rho_green",
+                                                      "rho_inv"]
+
+
+def test_schedule_calls_reject_null_grids():
+    L = sn.lib()
+    buf = (ctypes.c_int * 18)()
+    assert L.sn_get_schedule(None, buf, 18) == sn.SN_EINVAL
+    assert L.sn_set_schedule(None, buf, 18) == sn.SN_EINVAL
+    assert L.sn_autotune(None, 0.01, 1) == sn.SN_EINVAL
+
+
+def test_schedule_cache_round_trip(tmp_path):
+    path = str(tmp_path / "sched.json")
+    k1 = sn.schedule_key("B300", (256, 256, 256), sn.SN_ENGINE_FP32, 1)
+    k2 = sn.schedule_key("B300", (256, 256, 256), sn.SN_ENGINE_FP32, 2)
+    assert k1 != k2 and "256x256x256" in k1
+    assert sn.load_schedule(path, k1) is None  # no file yet
+    v1 = [0, 1, 2] * 6
+    sn.store_schedule(path, k1, v1)
+    sn.store_schedule(path, k2, [-1] * 18)
+    assert sn.load_schedule(path, k1) == v1
+    assert sn.load_schedule(path, k2) == [-1] * 18
+    # malformed entries and files are ignored, not trusted
+    sn.store_schedule(path, k1, [0] * 17)
+    assert sn.load_schedule(path, k1) is None
+    sn.store_schedule(path, k1, [99] * 18)
+    assert sn.load_schedule(path, k1) is None
+    with open(path, "w") as f:
+        f.write("not json")
+    assert sn.load_schedule(path, k2) is None
+    sn.store_schedule(path, k2, v1)  # a broken file is replaced
+    assert sn.load_schedule(path, k2) == v1
