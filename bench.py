@@ -283,7 +283,7 @@ def run_tc16(sn, torch, stream, w, kw, psi0, peak, ref1, steps=200):
                            "GBps": v["bytes"] / (v["ms"] / 1e3) / 1e9} for k, v in kinds.items()}}
 
 
-def run_optical(sn, torch, stream, peak, steps=500):
+def run_optical(sn, torch, stream, peak, steps=500, autotune=True):
     """Eq. 2 kernel of a thermo-optical medium (Eq. 4) on a 1024^2 transverse plane:
     beams of Eq. 3, complex64 fused passes, timed like the main line; accuracy is the
     one-step rel-L2 against the plain FP64 GPU step from the same input."""
@@ -303,6 +303,7 @@ def run_optical(sn, torch, stream, peak, steps=500):
     g64.close()
     rel = float(np.linalg.norm((out1 - ref1).ravel()) / np.linalg.norm(ref1.ravel()))
     g.set_state(psi0)
+    schedule = g.autotune(w.dt, steps=20) if autotune else None
     m0 = g.observables()["mass"]
     g.step(w.dt, 5)
     torch.cuda.synchronize()
@@ -320,6 +321,7 @@ def run_optical(sn, torch, stream, peak, steps=500):
                         f"(Eq. 4: C=-1/25, D=-2, B=1), {len(w.lumps)} beams seed 6000, dt=1e-2",
             "value": value, "unit": UNIT, "ms_per_step": 1e3 * t / steps, "steps": steps,
             "rel_l2_vs_fp64_one_step": rel, "mass_drift": drift,
+            "schedule": "default" if schedule is None else schedule,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "bytes_per_cell_step": 48.0}}
 
@@ -333,7 +335,7 @@ def fields_bytes_per_cell_step(m: int) -> float:
     return 48.0 * m + 8.0 + 24.0
 
 
-def run_fields(sn, torch, stream, peak, m=2, n=256, L=80.0, steps=500):
+def run_fields(sn, torch, stream, peak, m=2, n=256, L=80.0, steps=500, autotune=True):
     """m coupled fields sharing one potential (the multi-wave-function form of
     Eqs. 1-2) on an n^3 complex64 grid: field j is the N-body workload of seed
     3000 + j; timed like the main line; accuracy is the one-step rel-L2 against
@@ -357,6 +359,7 @@ def run_fields(sn, torch, stream, peak, m=2, n=256, L=80.0, steps=500):
     rel = float(np.linalg.norm((out1 - ref1).ravel()) / np.linalg.norm(ref1.ravel()))
     del out1, ref1
     g.set_state(psis)
+    schedule = g.autotune(ws[0].dt, steps=10) if autotune else None
     g.step(ws[0].dt, 5)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -374,6 +377,7 @@ def run_fields(sn, torch, stream, peak, m=2, n=256, L=80.0, steps=500):
                         f"dt={ws[0].dt}",
             "value": m * cells * steps / t, "unit": "field-cell-steps/s",
             "ms_per_step": 1e3 * t / steps, "steps": steps, "rel_l2_vs_fp64_one_step": rel,
+            "schedule": "default" if schedule is None else schedule,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "bytes_per_cell_step": bpc}}
 
@@ -613,7 +617,7 @@ def main():
 
     optical = None
     if not args.no_optical and world == 1:
-        optical = run_optical(sn, torch, stream, peak)
+        optical = run_optical(sn, torch, stream, peak, autotune=not args.no_autotune)
 
     fluid = None
     if not args.no_fluid and world == 1:
@@ -621,7 +625,7 @@ def main():
 
     fields = None
     if not args.no_fields and world == 1 and args.n == 256:
-        fields = run_fields(sn, torch, stream, peak)
+        fields = run_fields(sn, torch, stream, peak, autotune=not args.no_autotune)
 
     scan = None
     if not args.no_scan:

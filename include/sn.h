@@ -215,11 +215,14 @@ const char* sn_kind_name(int k);
  * Layout of the 3 SN_SCHED_KINDS values: [3 k + a].
  * sn_get_schedule: out holds at least that many values.  sn_set_schedule:
  * exactly that many, each in [-1, SN_SCHED_MAX_CTAS], else SN_EINVAL.
- * sn_autotune: time each pass kind and axis of sn_step(g, dt, steps) under
- * the candidates 0, -1, 1, 2, 3, 4, 6, 8, and keep for each the fastest if it
- * beats the default by more than 3% (device time by CUDA events; the state
- * and the step counter are restored; blocks until done).  Errors: SN_ENOTSUP
- * on SN_C128 grids, SN_EINVAL (non-finite dt, steps < 1), SN_ENOMEM, SN_ECUDA. */
+ * sn_autotune: pick the schedule by the device time of whole steps (CUDA
+ * events around sn_step(g, dt, steps) only, so the overlap of consecutive
+ * passes counts).  For each pass kind and axis the step uses, one after
+ * another, the candidates 0, -1, 1, 2, 3, 4, 6, 8 are timed and the fastest
+ * kept if it is more than 1% faster; the result is kept only if it beats the
+ * default schedule by at least 0.5% over 3 x steps.  The state and the step
+ * counter are restored; blocks until done.  Errors: SN_ENOTSUP on SN_C128
+ * grids, SN_EINVAL (non-finite dt, steps < 1), SN_ENOMEM, SN_ECUDA. */
 #define SN_SCHED_KINDS 6
 #define SN_SCHED_MAX_CTAS 64
 sn_status sn_get_schedule(sn_grid g, int* out, int n);

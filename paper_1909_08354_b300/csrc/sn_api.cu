@@ -1079,10 +1079,14 @@ sn_status sn_set_schedule(sn_grid g, const int* in, int n) {
   return SN_OK;
 }
 
-// Times every pass kind and axis of the fused step under each candidate
-// schedule (steps profiled steps after one unprofiled step per candidate) and
-// keeps, per pass, the fastest candidate when it beats the default by more
-// than 3%.  The state and the step counter are restored.
+// Picks the schedule by the time of whole steps, so that the overlap of
+// consecutive passes (programmatic dependent launch) counts: one profiled
+// step finds the pass kinds and axes the step uses; then, one entry at a
+// time, each candidate is timed over `steps` steps (CUDA events around the
+// steps only) and kept if it beats the entry's current best by more than 1%.
+// A final comparison over 3 x steps against the default schedule keeps the
+// result only if it is at least 0.5% faster.  The state and the step counter
+// are restored.
 sn_status sn_autotune(sn_grid g, double dt, int steps) {
   if (!g) return fail(nullptr, SN_EINVAL, "sn_autotune: grid is NULL");
   if (g->dtype != SN_C64)
@@ -1099,45 +1103,73 @@ sn_status sn_autotune(sn_grid g, double dt, int steps) {
   const long long step0 = g->step;
   int saved[SN_SCHED_KINDS][3];
   std::memcpy(saved, g->sched, sizeof(saved));
-  const int cand[] = {0, -1, 1, 2, 3, 4, 6, 8};
-  double t_of[sizeof(cand) / sizeof(cand[0])][SN_SCHED_KINDS][3] = {};
-  for (size_t c = 0; c < sizeof(cand) / sizeof(cand[0]) && e == cudaSuccess && st == SN_OK; ++c) {
-    for (int k = 0; k < SN_SCHED_KINDS; ++k)
-      for (int a = 0; a < 3; ++a) g->sched[k][a] = cand[c];
-    st = do_step(g, dt, 1);
-    if (st != SN_OK) break;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  // device time of n steps after one untimed step
+  auto timed = [&](int n, double* ms) -> bool {
+    if ((st = do_step(g, dt, 1)) != SN_OK) return false;
+    if ((e = cudaEventRecord(t0, g->stream)) != cudaSuccess) return false;
+    if ((st = do_step(g, dt, n)) != SN_OK) return false;
+    if ((e = cudaEventRecord(t1, g->stream)) != cudaSuccess) return false;
+    if ((e = cudaEventSynchronize(t1)) != cudaSuccess) return false;
+    float f = 0.f;
+    if ((e = cudaEventElapsedTime(&f, t0, t1)) != cudaSuccess) return false;
+    *ms = f;
+    return true;
+  };
+  bool ok = e == cudaSuccess;
+  // the entries this step uses
+  bool used[SN_SCHED_KINDS][3] = {};
+  if (ok) {
     g->profiling = true;
     g->prof.clear();
-    st = do_step(g, dt, steps);
+    st = do_step(g, dt, 1);
     g->profiling = false;
     e = cudaStreamSynchronize(g->stream);
-    double ms[SN_SCHED_KINDS][3] = {};
-    int cnt[SN_SCHED_KINDS][3] = {};
     for (const Launch& L : g->prof) {
-      float t = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, L.e0, L.e1);
-      if (L.kind < SN_SCHED_KINDS && L.axis >= 0 && L.axis < 3) {
-        ms[L.kind][L.axis] += t;
-        cnt[L.kind][L.axis] += 1;
-      }
+      if (L.kind < SN_SCHED_KINDS && L.axis >= 0 && L.axis < 3) used[L.kind][L.axis] = true;
       cudaEventDestroy(L.e0);
       cudaEventDestroy(L.e1);
     }
     g->prof.clear();
-    for (int k = 0; k < SN_SCHED_KINDS; ++k)
-      for (int a = 0; a < 3; ++a) t_of[c][k][a] = cnt[k][a] ? ms[k][a] / cnt[k][a] : 0.0;
+    ok = st == SN_OK && e == cudaSuccess;
   }
-  if (e == cudaSuccess && st == SN_OK) {
-    for (int k = 0; k < SN_SCHED_KINDS; ++k)
-      for (int a = 0; a < 3; ++a) {
-        int best = 0;  // cand[0], the default
-        for (size_t c = 1; c < sizeof(cand) / sizeof(cand[0]); ++c)
-          if (t_of[c][k][a] > 0.0 && t_of[c][k][a] < t_of[best][k][a]) best = (int)c;
-        g->sched[k][a] = t_of[best][k][a] < 0.97 * t_of[0][k][a] ? cand[best] : 0;
+  const int cand[] = {0, -1, 1, 2, 3, 4, 6, 8};
+  double base = 0.0;
+  for (int k = 0; k < SN_SCHED_KINDS; ++k)
+    for (int a = 0; a < 3; ++a) g->sched[k][a] = 0;
+  if (ok) ok = timed(steps, &base);
+  for (int k = 0; k < SN_SCHED_KINDS && ok; ++k)
+    for (int a = 0; a < 3 && ok; ++a) {
+      if (!used[k][a]) continue;
+      int best = g->sched[k][a];
+      double best_ms = base;
+      for (size_t c = 1; c < sizeof(cand) / sizeof(cand[0]) && ok; ++c) {
+        g->sched[k][a] = cand[c];
+        double ms = 0.0;
+        ok = timed(steps, &ms);
+        if (ok && ms < 0.99 * best_ms) {
+          best_ms = ms;
+          best = cand[c];
+        }
       }
-  } else {
-    std::memcpy(g->sched, saved, sizeof(saved));
+      g->sched[k][a] = best;
+      base = best_ms;
+    }
+  if (ok) {
+    // confirm against the default over longer runs
+    int tuned[SN_SCHED_KINDS][3];
+    std::memcpy(tuned, g->sched, sizeof(tuned));
+    double ms_tuned = 0.0, ms_default = 0.0;
+    ok = timed(3 * steps, &ms_tuned);
+    std::memset(g->sched, 0, sizeof(tuned));
+    if (ok) ok = timed(3 * steps, &ms_default);
+    if (ok && ms_tuned < 0.995 * ms_default) std::memcpy(g->sched, tuned, sizeof(tuned));
   }
+  if (!ok) std::memcpy(g->sched, saved, sizeof(saved));
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
   cudaError_t e2 = cudaMemcpyAsync(g->psi, keep, bytes, cudaMemcpyDeviceToDevice, g->stream);
   if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(g->stream);
   cudaFree(keep);
