@@ -321,6 +321,10 @@ sn_status sn_fno_set_params(sn_fno f, const float* p, int on_device);
 sn_status sn_fno_get_params(sn_fno f, float* p, int on_device);
 /* Gradients of the last sn_fno_backward (same layout as the parameters). */
 sn_status sn_fno_get_grads(sn_fno f, float* g, int on_device);
+/* Replace the gradients that sn_fno_adam will apply (same layout), e.g. by
+ * their average over data-parallel ranks.  Blocks until copied.  Errors:
+ * SN_EINVAL (NULL argument), SN_ECUDA. */
+sn_status sn_fno_set_grads(sn_fno f, const float* g, int on_device);
 /* out[B][2][s][s] from in[B][c_in][s][s]; keeps the activations for backward. */
 sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B);
 /* loss = mean_b ||out_b - target_b|| / ||target_b|| of the last forward (host

@@ -633,6 +633,14 @@ sn_status sn_fno_get_grads(sn_fno f, float* g, int on_device) {
   return SN_OK;
 }
 
+sn_status sn_fno_set_grads(sn_fno f, const float* g, int on_device) {
+  if (!f || !g) return ffail(SN_EINVAL, "sn_fno_set_grads: NULL argument");
+  FCHK(cudaMemcpyAsync(f->grads, g, f->nparams * sizeof(float),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, f->stream));
+  FCHK(cudaStreamSynchronize(f->stream));
+  return SN_OK;
+}
+
 sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
   if (!f || !in || !out) return ffail(SN_EINVAL, "sn_fno_forward: NULL argument");
   if (B < 1 || B > f->Bmax) return ffail(SN_EINVAL, "sn_fno_forward: batch must be in [1, batch_max]");

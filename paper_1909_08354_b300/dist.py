@@ -7,7 +7,8 @@ ranks and the throughput counts the cells of all replicas.  Independent
 problems (the instances of a parameter scan, the trajectories of a training
 set) are partitioned across ranks instead, balanced by their cost, with no
 collective on the data path: only the timing and the per-instance results are
-gathered at the end.
+gathered at the end.  Data-parallel training of the surrogate has the one real
+exchange: the gradients are averaged over the ranks before each Adam step.
 
 Every function works with any process-group backend (nccl for CUDA tensors,
 gloo for CPU tensors), so the logic is tested with gloo ranks on the CPU.
@@ -56,6 +57,20 @@ def sum_over_ranks(x: float) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def average_gradients(buf) -> None:
+    """Data-parallel training: replace buf (a tensor on this backend's device)
+    by its mean over the ranks, in place, with one all-reduce.  Training the
+    surrogate is the one exchange step of the path: each rank computes the
+    gradients of its own minibatch, and every rank then applies the same mean
+    gradient, so the replicas' parameters stay identical."""
+    n = world()
+    if n == 1:
+        return
+    import torch.distributed as dist
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM)
+    buf.div_(n)
 
 
 def barrier() -> None:

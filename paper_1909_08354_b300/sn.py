@@ -119,6 +119,7 @@ _SIGNATURES = [
     ("sn_fno_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("sn_fno_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("sn_fno_get_grads", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("sn_fno_set_grads", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("sn_fno_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("sn_fno_loss", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_double)]),
@@ -390,10 +391,25 @@ class Fno:
         _check(None, lib().sn_fno_get_params(self.h, out.ctypes.data, 0))
         return out
 
-    def get_grads(self):
+    def get_grads(self, out=None):
+        """Gradients of the last backward: into a float32 CUDA tensor `out`, or a
+        new host array."""
+        if out is not None and _is_torch(out):
+            _check(None, lib().sn_fno_get_grads(self.h, self._dev(out, self.nparams), 1))
+            return out
         out = np.empty(self.nparams, np.float32)
         _check(None, lib().sn_fno_get_grads(self.h, out.ctypes.data, 0))
         return out
+
+    def set_grads(self, g):
+        """Gradients for the next adam (a float32 CUDA tensor or a host array)."""
+        if _is_torch(g):
+            _check(None, lib().sn_fno_set_grads(self.h, self._dev(g, self.nparams), 1))
+        else:
+            a = np.ascontiguousarray(g, dtype=np.float32)
+            if a.size != self.nparams:
+                raise ValueError(f"expected {self.nparams} gradients")
+            _check(None, lib().sn_fno_set_grads(self.h, a.ctypes.data, 0))
 
     def forward(self, x, out):
         B = x.shape[0]

@@ -96,12 +96,21 @@ def generate_pairs(torch, ws, stride=50, nsnap=10, chunk=512, seed=0):
 
 
 def train(net, X, Y, iters: int, batch: int, lr: float = 1e-3, time_budget: float = None,
-          log=None):
-    """Adam on contiguous minibatches with a cosine-decayed rate; returns the losses."""
+          log=None, data_parallel: bool = False, device: str = "cuda"):
+    """Adam on contiguous minibatches with a cosine-decayed rate; returns the losses.
+
+    data_parallel: this process is one rank of a process group and X, Y are its
+    shard; the gradients are averaged over the ranks (dist.average_gradients)
+    between each backward and Adam step, so all ranks keep the same parameters
+    (they must start from the same ones).  device: where the output and
+    gradient buffers live (the network's own; "cuda" for sn.Fno)."""
     import math
     import torch
+    from . import dist as D
     n = X.shape[0]
-    out = torch.empty((batch, 2, X.shape[2], X.shape[3]), dtype=torch.float32, device="cuda")
+    out = torch.empty((batch, 2, X.shape[2], X.shape[3]), dtype=torch.float32, device=device)
+    gbuf = (torch.empty(net.nparams, dtype=torch.float32, device=device)
+            if data_parallel and D.world() > 1 else None)
     losses, t0 = [], time.perf_counter()
     nb = n // batch
     for it in range(1, iters + 1):
@@ -110,11 +119,20 @@ def train(net, X, Y, iters: int, batch: int, lr: float = 1e-3, time_budget: floa
         net.forward(xb, out)
         losses.append(net.loss(yb, batch))
         net.backward()
+        if gbuf is not None:
+            net.get_grads(gbuf)
+            D.average_gradients(gbuf)
+            net.set_grads(gbuf)
         net.adam(lr * 0.5 * (1.0 + math.cos(math.pi * (it - 1) / iters)), it)
         if log and it % 100 == 0:
             log(f"iter {it} loss {np.mean(losses[-100:]):.4f} ({time.perf_counter() - t0:.0f} s)")
-        if time_budget is not None and time.perf_counter() - t0 > time_budget:
-            break
+        if time_budget is not None:
+            over = time.perf_counter() - t0 > time_budget
+            # data-parallel ranks stop together, or one would wait in an all-reduce
+            if gbuf is not None:
+                over = D.max_over_ranks(1.0 if over else 0.0) > 0.0
+            if over:
+                break
     net.sync()
     return losses
 
@@ -216,10 +234,17 @@ def main(argv=None):
     Prints one JSON line with the training loss, the held-out single-prediction
     error against the persistence guess and the zero guess (whose relative error
     is 1 by definition), and the rollout's fallback fraction, final error and
-    wall times against the batched solver alone."""
+    wall times against the batched solver alone.
+
+    Under torchrun (WORLD_SIZE > 1, one process per GPU, NCCL) the training is
+    data-parallel: each rank generates the pairs of its share of the training
+    trajectories (every world-th), all ranks start from the same parameters and
+    average their gradients before every Adam step; rank 0 evaluates."""
     import argparse
     import json
+    import os
     import torch
+    from . import dist as D
     ap = argparse.ArgumentParser()
     ap.add_argument("--s", type=int, default=256)
     ap.add_argument("--train", type=int, default=4096, help="training trajectories")
@@ -238,15 +263,22 @@ def main(argv=None):
     ap.add_argument("--drift-tol", type=float, default=1e-3)
     ap.add_argument("--init-seed", type=int, default=0)
     a = ap.parse_args(argv)
-    log = lambda m: print(m, flush=True)  # noqa: E731
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    rank, world = D.rank(), D.world()
+    log = (lambda m: print(m, flush=True)) if rank == 0 else (lambda m: None)  # noqa: E731
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
-    X, Y = generate_pairs(torch, instances(a.train, 5000, a.s), a.stride, a.nsnap, seed=1)
-    test_ws = instances(a.heldout, 9000, a.s)
-    Xt, Yt = generate_pairs(torch, test_ws, a.stride, 2, seed=2)
+    X, Y = generate_pairs(torch, instances(a.train, 5000, a.s)[rank::world], a.stride, a.nsnap,
+                          seed=1)
+    test_ws = instances(a.heldout, 9000, a.s) if rank == 0 else []
+    Xt, Yt = generate_pairs(torch, test_ws, a.stride, 2, seed=2) if rank == 0 else (None, None)
     t_gen = time.perf_counter() - t0
-    log(f"pairs: {X.shape[0]} train, {Xt.shape[0]} held out ({t_gen:.0f} s)")
+    log(f"pairs: {X.shape[0]} train per rank x {world}, "
+        f"{Xt.shape[0] if Xt is not None else 0} held out ({t_gen:.0f} s)")
     net = sn.Fno(s=a.s, c_in=5, width=a.width, modes=a.modes, layers=a.layers, proj=a.proj,
                  batch_max=a.batch, stream=stream.cuda_stream)
     p0 = _init_params(a)
@@ -254,9 +286,13 @@ def main(argv=None):
         raise RuntimeError("parameter layout mismatch")
     net.set_params(p0)
     t0 = time.perf_counter()
-    losses = train(net, X, Y, a.iters, a.batch, a.lr, a.budget, log)
+    losses = train(net, X, Y, a.iters, a.batch, a.lr, a.budget, log, data_parallel=world > 1)
     t_train = time.perf_counter() - t0
     del X, Y
+    if rank != 0:
+        D.barrier()
+        net.close()
+        return
     e_net, e_id = one_step_errors(torch, net, Xt, Yt, a.batch)
     res = rollout(torch, net, test_ws, a.rounds, a.stride, a.drift_tol)
     res.update({"grid": a.s, "train_pairs": a.train * a.nsnap, "train_iters": len(losses),
@@ -266,7 +302,12 @@ def main(argv=None):
                 "heldout_rel_l2_net": e_net, "heldout_rel_l2_persistence": e_id,
                 "heldout_rel_l2_zero": 1.0, "params": net.nparams})
     res.pop("fallbacks_per_round", None)
+    if world > 1:
+        res["data_parallel_ranks"] = world
+        res["train_samples_per_s"] *= world
     print(json.dumps(res), flush=True)
+    if world > 1:
+        D.barrier()
     net.close()
 
 

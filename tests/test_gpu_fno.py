@@ -105,3 +105,31 @@ def test_training_reduces_loss():
         net.adam(2e-3, it)
     assert losses[-1] < 0.3 * losses[0], (losses[0], losses[-1])
     net.close()
+
+
+def test_set_grads_feeds_adam():
+    """The data-parallel exchange replaces the gradients between backward and
+    Adam (sn_fno_set_grads): the first Adam step must use exactly them."""
+    torch = pytest.importorskip("torch")
+    net = make_net(SMALL, 2)
+    try:
+        rng = np.random.default_rng(3)
+        p0 = (0.01 * rng.standard_normal(net.nparams)).astype(np.float32)
+        net.set_params(p0)
+        g = rng.standard_normal(net.nparams).astype(np.float32)
+        g[::7] = 0.0
+        gd = torch.from_numpy(g).cuda()
+        net.set_grads(gd)
+        back = torch.empty_like(gd)
+        net.get_grads(back)
+        assert torch.equal(back, gd)
+        assert np.array_equal(net.get_grads(), g)
+        net.adam(1e-3, 1)
+        net.sync()
+        step = net.get_params().astype(np.float64) - p0
+        # first step: -lr m_hat / (sqrt(v_hat) + eps) with m_hat = g, v_hat = g^2
+        expect = -1e-3 * g / (np.abs(g) + 1e-8)
+        assert np.allclose(step, expect, rtol=1e-3, atol=1e-9)
+        assert np.all(step[::7] == 0.0)
+    finally:
+        net.close()
