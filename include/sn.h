@@ -174,13 +174,21 @@ int sn_get_fields(sn_grid g);
 sn_status sn_set_state(sn_grid g, const void* psi, int on_device);
 
 /* Copy the state out (same layout as sn_set_state).  Host copies block until
- * done.  The state is always at an integer step. */
+ * done.  The state is always at an integer step: on a complex64 grid whose
+ * merge is open (see sn_step) the closing Nl(h) Kin(h/2) is applied to a copy
+ * (three psi passes), and the grid's own state stays open. */
 sn_status sn_get_state(sn_grid g, void* psi_out, int on_device);
 
 /* Advance nsteps symmetric split steps of size dt (Sec. III).  Consecutive
- * steps are merged (Kin(h/2) Kin(h/2) = Kin(h)); the call opens and closes
- * the merge, so psi is at an integer step on return.  nsteps = 0 is a no-op.
- * dt may be negative (time reversal).  Asynchronous on the grid's stream.
+ * steps are merged (Kin(h/2) Kin(h/2) = Kin(h)).  On complex64 grids the
+ * merge stays open across calls: the grid keeps Kin(h/2) psi and the
+ * potential of its density, and a following sn_step with the same dt
+ * continues the merge, so n steps cost n rounds of passes however the calls
+ * split them.  Every call that reads the state (sn_get_state, sn_observables)
+ * sees it at the integer step; a change of dt, of the kernel (sn_set_kernel),
+ * of the engine or an sn_autotune first closes the merge in place.  Complex128
+ * grids close the merge within each step.  nsteps = 0 is a no-op.  dt may be
+ * negative (time reversal).  Asynchronous on the grid's stream.
  * Errors: SN_EINVAL (non-finite dt, nsteps < 0), SN_ECUDA. */
 sn_status sn_step(sn_grid g, double dt, int nsteps);
 
@@ -370,17 +378,19 @@ sn_status sn_test_gemm_bf16(const float* A, long long sAz, long long sAm, long l
  * half spectrum and the per-call tables, about 1.1 MB) is one file-scope
  * static device array of fixed size, which every GPU that loads the library
  * holds until the process exits.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture.  All calls share the
- * array, so calls whose work overlaps on the GPU (e.g. on two streams) race
- * and give wrong results; serialise them.  Each call rewrites the tables it
- * uses, and the half spectrum is always written before it is read.  The table
- * upload copies from host memory on cuda_stream and waits for the stream's
- * earlier work; the steps themselves are queued asynchronously.
+ * array's device address (cudaGetSymbolAddress) with the device current.
+ * All calls share the array, so calls whose work overlaps on the GPU (e.g. on
+ * two streams) race and give wrong results; serialise them.  Each call
+ * rewrites the tables it uses, and the half spectrum is always written before
+ * it is read.  The table upload copies from host (stack) memory on
+ * cuda_stream; the steps themselves are queued asynchronously.  Because a
+ * captured graph would replay those copies from host memory that no longer
+ * holds the tables, the call is refused (SN_ENOTSUP) while cuda_stream is
+ * being captured.
  *
  * Errors (message in sn_last_error(NULL)): SN_ENOTSUP if ny or nx exceeds
- * SN_NOALLOC_MAX_N or v_ext is given; SN_EINVAL for other bad arguments;
- * SN_ECUDA if a CUDA call fails. */
+ * SN_NOALLOC_MAX_N, v_ext is given, or cuda_stream is being captured;
+ * SN_EINVAL for other bad arguments; SN_ECUDA if a CUDA call fails. */
 sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, double Lx,
                              const sn_kernel* k, double dt, int nsteps, void* cuda_stream);
 

@@ -12,6 +12,7 @@
 // loads the library holds that array until the process exits.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <string>
@@ -42,7 +43,9 @@ constexpr size_t kScratchWords = kOffZero + 32;
 static __device__ __align__(256) float2 sn_noalloc_scratch[kScratchWords];
 
 constexpr int kMaxDevices = 64;
-float2* g_scratch_ptr[kMaxDevices] = {};  // device address of the array, per device
+// device address of the array, per device; atomic because two host threads may
+// make the first call on one device at the same time (both store the same value)
+std::atomic<float2*> g_scratch_ptr[kMaxDevices] = {};
 
 sn_status fail(sn_status st, const char* m) {
   set_thread_error(m);
@@ -72,13 +75,15 @@ sn_status scratch_for_current_device(float2** out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return fail(SN_ENOTSUP, "sn_step_2d_noalloc: device index too large");
-  if (!g_scratch_ptr[dev]) {
+  float2* ptr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!ptr) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, sn_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-    g_scratch_ptr[dev] = reinterpret_cast<float2*>(p);
+    ptr = reinterpret_cast<float2*>(p);
+    g_scratch_ptr[dev].store(ptr, std::memory_order_release);
   }
-  *out = g_scratch_ptr[dev];
+  *out = ptr;
   return SN_OK;
 }
 
@@ -107,11 +112,22 @@ extern "C" sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, d
     return fail(SN_EINVAL, (std::string("sn_step_2d_noalloc: ") + why).c_str());
   if (k->v_ext) return fail(SN_ENOTSUP, "sn_step_2d_noalloc: v_ext is not supported");
   if (nsteps == 0) return SN_OK;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  // The tables below are copied from host (stack) memory, which a captured
+  // graph would read again, long after this call returned: refused while the
+  // stream is being captured.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(stream, &cap);
+  if (ce != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    if (ce != cudaSuccess) (void)cudaGetLastError();
+    return fail(SN_ENOTSUP,
+                "sn_step_2d_noalloc: the stream is being captured; the call uploads its tables "
+                "from host memory and cannot run inside a stream capture");
+  }
 
   float2* s = nullptr;
   sn_status st = scratch_for_current_device(&s);
   if (st != SN_OK) return st;
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   float2* rhohat = s;
   float2* tw[2] = {s + kOffTw, s + kOffTw + kTwWords};
   float2* mult[2][2] = {{s + kOffMult, s + kOffMult + kMultWords},
@@ -121,29 +137,32 @@ extern "C" sn_status sn_step_2d_noalloc(float* psi, int ny, int nx, double Ly, d
   float* zero = reinterpret_cast<float*>(s + kOffZero);
 
   // Tables for this call (the array keeps whatever an earlier call left).  They
-  // are built on the stack; copies from pageable host memory are staged before
-  // cudaMemcpyAsync returns, so the stack buffers may go out of scope.
+  // are built on the stack, one buffer per upload (about 76 KB in all); a copy
+  // from pageable host memory is staged before cudaMemcpyAsync returns, so the
+  // buffers may go out of scope when the call returns.
   cudaError_t e = cudaSuccess;
   double2 t64[2 * kMaxN];
-  float2 t32[4 * kMaxN];
-  float kf[kMaxN];
+  float2 tw32[2][4 * kMaxN];
+  float lift32[2][2][4 * kMaxN];
+  float kf[2][kMaxN];
   for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
     const int ntw = snfft::plan_twiddles(n[a], t64);  // at most 2 n[a] entries
     if (ntw > 0) {
-      split_hilo(t64, ntw, t32);
-      e = cudaMemcpyAsync(tw[a], t32, 2 * ntw * sizeof(float2), cudaMemcpyHostToDevice, stream);
+      split_hilo(t64, ntw, tw32[a]);
+      e = cudaMemcpyAsync(tw[a], tw32[a], 2 * ntw * sizeof(float2), cudaMemcpyHostToDevice,
+                          stream);
     }
     for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
-      float* l32 = reinterpret_cast<float*>(t32);
-      sn::kinetic_lift_table(n[a], L[a], k->coeff_lap, f ? dt : 0.5 * dt, l32);
-      e = cudaMemcpyAsync(mult[a][f], l32, 4 * n[a] * sizeof(float), cudaMemcpyHostToDevice, stream);
+      sn::kinetic_lift_table(n[a], L[a], k->coeff_lap, f ? dt : 0.5 * dt, lift32[a][f]);
+      e = cudaMemcpyAsync(mult[a][f], lift32[a][f], 4 * n[a] * sizeof(float),
+                          cudaMemcpyHostToDevice, stream);
     }
     if (e == cudaSuccess) {
       for (int j = 0; j < n[a]; ++j) {
         const double kk = wavenumber(j, n[a], L[a]);
-        kf[j] = (float)(kk * kk);
+        kf[a][j] = (float)(kk * kk);
       }
-      e = cudaMemcpyAsync(k2[a], kf, n[a] * sizeof(float), cudaMemcpyHostToDevice, stream);
+      e = cudaMemcpyAsync(k2[a], kf[a], n[a] * sizeof(float), cudaMemcpyHostToDevice, stream);
     }
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(zero, 0, sizeof(float), stream);

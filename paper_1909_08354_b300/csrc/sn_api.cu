@@ -183,6 +183,21 @@ struct sn_grid_s {
   int sched[SN_SCHED_KINDS][3] = {};
   int cur_axis = 0;
 
+  // Merged steps stay open across sn_step calls (complex64 grids).  While
+  // `open`, psi holds Kin(h/2) of the state at the current integer step and
+  // the half spectrum holds the potential (times h, h = open_dt) of that
+  // psi's density: the step still owes Nl(h) Kin(h/2).  The next sn_step with
+  // the same h continues the merge (Kin(h/2) Kin(h/2) = Kin(h)), so n steps
+  // cost n rounds of passes however the calls split them.  Reading the state
+  // closes the merge into `closed` (a scratch copy of all fields) and leaves
+  // psi open; a parameter change closes it in place.  next_odd is the axis
+  // order of the next round.
+  bool open = false;
+  double open_dt = 0.0;
+  bool next_odd = false;
+  void* closed = nullptr;
+  bool closed_valid = false;
+
   // profiling
   bool profiling = false;
   std::vector<Launch> prof;
@@ -324,10 +339,10 @@ LineGeom psi_geom(sn_grid g, int a) {
 // alone adds to the half spectrum.  With several fields the local term g rho
 // of the total density is applied through the Green's multiplier
 // (rho_passes), not per field.
-sn_status psi_pass(sn_grid g, int j, int nf, int a, int variant, int full, double dt) {
+sn_status psi_pass(sn_grid g, void* base, int j, int nf, int a, int variant, int full, double dt) {
   const LineGeom lg = psi_geom(g, a);
   PsiPassArgs pa{};
-  pa.psi = reinterpret_cast<float2*>(g->psi) + (size_t)j * g->cells;
+  pa.psi = reinterpret_cast<float2*>(base) + (size_t)j * g->cells;
   pa.outer = lg.outer * (variant == PSI_PLAIN ? nf : 1);
   pa.nfields = variant == PSI_PLAIN ? 1 : nf;
   pa.fstride = g->cells;
@@ -441,35 +456,84 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
   return SN_OK;
 }
 
-sn_status step_f32(sn_grid g, double dt, int nsteps) {
+// One round of psi passes over the fields at `base`, axes in the order of
+// `odd`: the nonlinear phase Nl(h) of the open step on the first axis
+// (nphase), the kinetic factor Kin(h) (full) or Kin(h/2) on every axis, and
+// (density) |psi|^2 of the result with its half-spectrum passes, which leave
+// the potential of the next Nl(h) in the half spectrum.
+sn_status round_f32(sn_grid g, void* base, bool odd, bool nphase, int full, bool density,
+                    double dt) {
   const int d = g->ndim;
-  int prev_h = -1;
-  for (int r = 0; r <= nsteps; ++r) {
-    const bool odd = (r & 1) != 0;
-    const int full = (r == 0 || r == nsteps) ? 0 : 1;
-    int order[3];
-    for (int i = 0; i < d; ++i) order[i] = odd ? d - 1 - i : i;
-    // axis by axis over the fields: every field's potential pass reads the
-    // half spectrum before the first density pass overwrites it
-    for (int i = 0; i < d; ++i) {
-      int variant = PSI_PLAIN;
-      if (i == 0 && r > 0) variant = PSI_NPHASE;
-      if (i == d - 1 && r < nsteps) variant = PSI_DENSITY;
-      // the tensor-core potential and density passes take one field per launch
-      const bool tc_axis = g->engine == SN_ENGINE_TC16 && g->n[order[i]] == 256;
-      const bool one_launch = variant == PSI_PLAIN || !tc_axis;
-      const int nf = one_launch ? g->fields : 1;
-      for (int j = 0; j < g->fields; j += nf) {
-        sn_status st = psi_pass(g, j, nf, order[i], variant, full, dt);
-        if (st != SN_OK) return st;
-      }
-    }
-    if (r < nsteps) {
-      prev_h = order[d - 1];
-      sn_status st = rho_passes(g, prev_h, dt);
+  int order[3];
+  for (int i = 0; i < d; ++i) order[i] = odd ? d - 1 - i : i;
+  // axis by axis over the fields: every field's potential pass reads the
+  // half spectrum before the first density pass overwrites it
+  for (int i = 0; i < d; ++i) {
+    int variant = PSI_PLAIN;
+    if (i == 0 && nphase) variant = PSI_NPHASE;
+    if (i == d - 1 && density) variant = PSI_DENSITY;
+    // the tensor-core potential and density passes take one field per launch
+    const bool tc_axis = g->engine == SN_ENGINE_TC16 && g->n[order[i]] == 256;
+    const bool one_launch = variant == PSI_PLAIN || !tc_axis;
+    const int nf = one_launch ? g->fields : 1;
+    for (int j = 0; j < g->fields; j += nf) {
+      sn_status st = psi_pass(g, base, j, nf, order[i], variant, full, dt);
       if (st != SN_OK) return st;
     }
   }
+  if (density) return rho_passes(g, order[d - 1], dt);
+  return SN_OK;
+}
+
+// n merged steps: round r applies the open step's Nl(h) (none on a closed
+// state), Kin(h) (Kin(h/2) on a closed state) and the density for the next
+// Nl(h).  The merge is left open (see sn_grid_s::open).
+sn_status step_f32(sn_grid g, double dt, int nsteps) {
+  for (int r = 0; r < nsteps; ++r) {
+    const bool cont = g->open;
+    sn_status st = round_f32(g, g->psi, g->next_odd, cont, cont ? 1 : 0, true, dt);
+    if (st != SN_OK) return st;
+    g->next_odd = !g->next_odd;
+    g->open = true;
+    g->open_dt = dt;
+    g->closed_valid = false;
+  }
+  return SN_OK;
+}
+
+// The state at the current integer step: psi itself, or for an open merge its
+// closing round Nl(h) Kin(h/2) applied to a copy in g->closed (psi stays open).
+sn_status closed_state(sn_grid g, void** out) {
+  if (!g->open) {
+    *out = g->psi;
+    return SN_OK;
+  }
+  const size_t bytes = (size_t)g->fields * g->cells * sizeof(float2);
+  cudaError_t e;
+  if (!g->closed) {
+    if ((e = cudaMalloc(&g->closed, bytes)) != cudaSuccess)
+      return cuda_fail(g, e, "cudaMalloc(closed state)");
+    g->allocs.push_back(g->closed);
+  }
+  if (!g->closed_valid) {
+    e = cudaMemcpyAsync(g->closed, g->psi, bytes, cudaMemcpyDeviceToDevice, g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemcpyAsync(closed state)");
+    sn_status st = round_f32(g, g->closed, g->next_odd, true, 0, false, g->open_dt);
+    if (st != SN_OK) return st;
+    g->closed_valid = true;
+  }
+  *out = g->closed;
+  return SN_OK;
+}
+
+// Close an open merge in place (before anything the closing round depends on
+// changes: dt, the kernel, v_ext, the engine, the fields).
+sn_status settle(sn_grid g) {
+  if (!g->open) return SN_OK;
+  sn_status st = round_f32(g, g->psi, g->next_odd, true, 0, false, g->open_dt);
+  if (st != SN_OK) return st;
+  g->open = false;
+  g->closed_valid = false;
   return SN_OK;
 }
 
@@ -581,7 +645,10 @@ sn_status do_step(sn_grid g, double dt, int nsteps) {
   if (!std::isfinite(dt)) return fail(g, SN_EINVAL, "sn_step: dt must be finite");
   if (nsteps < 0) return fail(g, SN_EINVAL, "sn_step: nsteps must be >= 0");
   if (nsteps == 0) return SN_OK;
-  sn_status st = ensure_mult_tables(g, dt);
+  // an open merge of another h is closed with its own tables first
+  sn_status st = (g->open && dt != g->open_dt) ? settle(g) : SN_OK;
+  if (st != SN_OK) return st;
+  st = ensure_mult_tables(g, dt);
   if (st != SN_OK) return st;
   if (g->fluid) st = step_fluid_f64(g, dt, nsteps);
   else st = (g->dtype == SN_C64) ? step_f32(g, dt, nsteps) : step_f64(g, dt, nsteps);
@@ -715,6 +782,9 @@ sn_status sn_set_kernel(sn_grid g, const sn_kernel* k) {
   if (!k) return fail(g, SN_EINVAL, "sn_set_kernel: kernel is NULL");
   if (const char* why = kernel_invalid(*k))
     return fail(g, SN_EINVAL, std::string("sn_set_kernel: ") + why);
+  // an open merge owes Nl(h) Kin(h/2) of the old parameters
+  sn_status st = settle(g);
+  if (st != SN_OK) return st;
   cudaError_t e = cudaStreamSynchronize(g->stream);  // queued steps still read the old vext
   if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamSynchronize");
   if (k->v_ext) {
@@ -825,10 +895,19 @@ sn_status sn_set_fields(sn_grid g, int count) {
     g->psi = p;
     g->fields_cap = count;
   }
+  if (g->closed && count > g->fields) {
+    // the closed copy holds all fields: reallocated at the next read
+    for (auto it = g->allocs.begin(); it != g->allocs.end(); ++it)
+      if (*it == g->closed) { g->allocs.erase(it); break; }
+    cudaFree(g->closed);
+    g->closed = nullptr;
+  }
   e = cudaMemset(g->psi, 0, (size_t)count * g->cells * esz);
   if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemset(psi fields)");
   g->fields = count;
   g->step = 0;
+  g->open = false;
+  g->closed_valid = false;
   return SN_OK;
 }
 
@@ -845,6 +924,8 @@ sn_status sn_set_state(sn_grid g, const void* psi, int on_device) {
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(g, e, "sn_set_state copy");
   g->step = 0;
+  g->open = false;
+  g->closed_valid = false;
   return SN_OK;
 }
 
@@ -853,7 +934,10 @@ sn_status sn_get_state(sn_grid g, void* psi_out, int on_device) {
   if (!psi_out) return fail(g, SN_EINVAL, "sn_get_state: psi_out is NULL");
   const size_t bytes = (size_t)g->fields * g->cells *
                        (g->dtype == SN_C64 ? sizeof(float2) : sizeof(double2));
-  cudaError_t e = cudaMemcpyAsync(psi_out, g->psi, bytes,
+  void* src = nullptr;
+  sn_status st = closed_state(g, &src);
+  if (st != SN_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(psi_out, src, bytes,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                   g->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(g->stream);
@@ -878,6 +962,8 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
   if (!out) return fail(g, SN_EINVAL, "sn_observables: out is NULL");
   sn_status st = ensure_f64_scratch(g);
   if (st != SN_OK) return st;
+  void* psi_now = nullptr;  // the state at the current integer step
+  if ((st = closed_state(g, &psi_now)) != SN_OK) return st;
   const int d = g->ndim;
   const int nf = g->fields;
   const bool f32 = g->dtype == SN_C64;
@@ -885,11 +971,11 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
   auto field64 = [&](int j, double2** dst) -> sn_status {
     if (f32) {
       SN_LAUNCH(g, K_OBS, 24.0 * g->cells,
-                launch_widen_f32_to_f64(reinterpret_cast<const float2*>(g->psi) + (size_t)j * g->cells,
+                launch_widen_f32_to_f64(reinterpret_cast<const float2*>(psi_now) + (size_t)j * g->cells,
                                         g->w64a, g->cells, g->stream));
       *dst = g->w64a;
     } else {
-      *dst = reinterpret_cast<double2*>(g->psi) + (size_t)j * g->cells;
+      *dst = reinterpret_cast<double2*>(psi_now) + (size_t)j * g->cells;
     }
     return SN_OK;
   };
@@ -904,7 +990,7 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
       return cuda_fail(g, e, "cudaMalloc(observables scratch)");
     dens = g->w64c;
     SN_LAUNCH(g, K_OBS, (8.0 * nf * (f32 ? 1 : 2) + 16.0) * g->cells,
-              launch_total_amplitude(g->psi, f32, nf, g->cells, dens, g->stream));
+              launch_total_amplitude(psi_now, f32, nf, g->cells, dens, g->stream));
   } else if ((st = field64(0, &dens)) != SN_OK) {
     return st;
   }
@@ -974,6 +1060,10 @@ sn_status sn_set_engine(sn_grid g, int engine) {
     return fail(g, SN_EINVAL, "sn_set_engine: unknown engine");
   if (engine == SN_ENGINE_TC16 && g->dtype != SN_C64)
     return fail(g, SN_ENOTSUP, "sn_set_engine: the tensor-core engine needs a complex64 grid");
+  if (engine != g->engine) {
+    sn_status st = settle(g);  // the open step closes on the engine that opened it
+    if (st != SN_OK) return st;
+  }
   if (engine == SN_ENGINE_TC16 && !g->tc_frag) {
     std::vector<unsigned> w;
     tc16_fragment_table(w);
@@ -1093,7 +1183,10 @@ sn_status sn_autotune(sn_grid g, double dt, int steps) {
     return fail(g, SN_ENOTSUP, "sn_autotune: the schedule applies to the fused complex64 passes");
   if (!std::isfinite(dt) || steps < 1)
     return fail(g, SN_EINVAL, "sn_autotune: dt must be finite and steps >= 1");
-  sn_status st = ensure_mult_tables(g, dt);
+  // tuning steps overwrite the half spectrum: close an open merge first
+  sn_status st = settle(g);
+  if (st != SN_OK) return st;
+  st = ensure_mult_tables(g, dt);
   if (st != SN_OK) return st;
   const size_t bytes = (size_t)g->fields * g->cells * sizeof(float2);
   void* keep = nullptr;
@@ -1171,6 +1264,8 @@ sn_status sn_autotune(sn_grid g, double dt, int steps) {
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);
   cudaError_t e2 = cudaMemcpyAsync(g->psi, keep, bytes, cudaMemcpyDeviceToDevice, g->stream);
+  g->open = false;
+  g->closed_valid = false;
   if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(g->stream);
   cudaFree(keep);
   g->step = step0;

@@ -111,6 +111,13 @@ def train(net, X, Y, iters: int, batch: int, lr: float = 1e-3, time_budget: floa
     out = torch.empty((batch, 2, X.shape[2], X.shape[3]), dtype=torch.float32, device=device)
     gbuf = (torch.empty(net.nparams, dtype=torch.float32, device=device)
             if data_parallel and D.world() > 1 else None)
+    # a shard smaller than one batch has no minibatch: every rank must learn of it
+    # before the first all-reduce, or the ranks that have one would wait there
+    short = 1.0 if n < batch else 0.0
+    if gbuf is not None:
+        short = D.max_over_ranks(short)
+    if short > 0.0:
+        raise ValueError(f"train: a rank holds fewer pairs than one batch ({n} < {batch})")
     losses, t0 = [], time.perf_counter()
     nb = n // batch
     for it in range(1, iters + 1):
@@ -288,6 +295,9 @@ def main(argv=None):
     t0 = time.perf_counter()
     losses = train(net, X, Y, a.iters, a.batch, a.lr, a.budget, log, data_parallel=world > 1)
     t_train = time.perf_counter() - t0
+    # the aggregate rate: every rank's samples over the slowest rank's time
+    samples_all = D.sum_over_ranks(len(losses) * a.batch)
+    t_train_max = D.max_over_ranks(t_train)
     del X, Y
     if rank != 0:
         D.barrier()
@@ -296,7 +306,7 @@ def main(argv=None):
     e_net, e_id = one_step_errors(torch, net, Xt, Yt, a.batch)
     res = rollout(torch, net, test_ws, a.rounds, a.stride, a.drift_tol)
     res.update({"grid": a.s, "train_pairs": a.train * a.nsnap, "train_iters": len(losses),
-                "train_samples_per_s": len(losses) * a.batch / t_train, "train_s": t_train,
+                "train_samples_per_s": samples_all / t_train_max, "train_s": t_train_max,
                 "loss_first100": float(np.mean(losses[:100])),
                 "loss_last100": float(np.mean(losses[-100:])),
                 "heldout_rel_l2_net": e_net, "heldout_rel_l2_persistence": e_id,
@@ -304,7 +314,6 @@ def main(argv=None):
     res.pop("fallbacks_per_round", None)
     if world > 1:
         res["data_parallel_ranks"] = world
-        res["train_samples_per_s"] *= world
     print(json.dumps(res), flush=True)
     if world > 1:
         D.barrier()

@@ -166,3 +166,38 @@ def test_data_parallel_training_loop_on_two_gloo_ranks():
     assert res[0]["p"] == res[1]["p"]  # the replicas stay identical
     assert all(abs(v - 2.0) < 0.05 for v in res[0]["p"])
     assert res[0]["iters"] == res[1]["iters"] < 1000
+
+
+def _short_shard_worker(rank, world, port, q):
+    tdist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                             world_size=world)
+    try:
+        from paper_1909_08354_b300 import surrogate as S
+        # rank 1's shard holds one pair, less than a batch of 2: every rank must
+        # raise before the first gradient all-reduce instead of waiting in it
+        n = 4 if rank == 0 else 1
+        X, Y = torch.zeros(n, 5, 2, 2), torch.zeros(n, 2, 2, 2)
+        try:
+            S.train(_StandInNet(3, target=1.0), X, Y, iters=10, batch=2, lr=0.1,
+                    data_parallel=True, device="cpu")
+            q.put((rank, "trained"))
+        except ValueError as e:
+            q.put((rank, "ValueError" if "fewer pairs than one batch" in str(e) else str(e)))
+    finally:
+        tdist.destroy_process_group()
+
+
+def test_a_shard_smaller_than_a_batch_stops_every_rank():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_short_shard_worker, args=(r, world, port, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == {0: "ValueError", 1: "ValueError"}

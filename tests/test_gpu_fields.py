@@ -223,4 +223,4 @@ def test_launches_per_step_do_not_grow_with_the_fields():
             counts.append(g.launch_count() - n0)
         finally:
             g.close()
-    assert counts[0] == counts[1] == 6 * 10 + 3
+    assert counts[0] == counts[1] == 6 * 10

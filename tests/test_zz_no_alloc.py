@@ -41,7 +41,11 @@ def rel_l2(a, b):
 
 def test_noalloc_matches_grid_api_on_two_calls_in_a_row():
     torch = pytest.importorskip("torch")
-    cases = [((256, 128), 31, 0.02, 4), ((64, 512), 32, 0.03, 3)]
+    # the largest grid (its half spectrum fills the array's region for it), a
+    # grid with a 16-point axis (no twiddle table is uploaded for it), and two
+    # uneven shapes
+    cases = [((256, 128), 31, 0.02, 4), ((64, 512), 32, 0.03, 3), ((512, 512), 33, 0.02, 2),
+             ((16, 32), 34, 0.02, 3)]
     prepared = []
     for shape, seed, dt, nsteps in cases:
         w = W.random_small(shape, seed=seed)
