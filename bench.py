@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-fno", action="store_true")
     p.add_argument("--no-fluid", action="store_true",
                    help="skip the Eq. 16 fluid model (GR and NMC) on a 512^2 complex128 plane")
+    p.add_argument("--staging", choices=["tma", "registers"], default="tma",
+                   help="how the fused passes move their tiles (the same results bit for bit)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default schedule of the fused passes")
     p.add_argument("--no-fields", action="store_true",
@@ -81,6 +83,34 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6400.0, "fallback"
+
+
+class _Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (ctypes): the SM
+    clock, its maximum, and the active clock-event (throttle) reasons."""
+
+    CLOCK_SM = 1
+
+    def __init__(self, index: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByIndex_v2 failed")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def read(self):
+        ct = self.ct
+        sm, mx, rs = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.CLOCK_SM, ct.byref(sm)) != 0 or \
+                self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.CLOCK_SM, ct.byref(mx)) != 0 or \
+                self.reasons_fn(self.h, ct.byref(rs)) != 0:
+            raise RuntimeError("NVML query failed")
+        return (sm.value, mx.value, rs.value)
 
 
 class ClockSampler:
@@ -105,10 +135,7 @@ class ClockSampler:
         self._thread = None
         self._nvml = None
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self._nvml = pynvml
-            self._h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self._nvml = _Nvml(index)
         except Exception as e:  # no NVML: nvidia-smi reads only
             self.error = f"nvml: {e}"[:200]
 
@@ -131,10 +158,7 @@ class ClockSampler:
         nv = self._nvml
         while not self._stop.is_set():
             try:
-                sm = nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM)
-                mx = nv.nvmlDeviceGetMaxClockInfo(self._h, nv.NVML_CLOCK_SM)
-                rs = nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
-                self.samples.append((sm, mx, rs))
+                self.samples.append(nv.read())
             except Exception as e:
                 self.error = f"nvml: {e}"[:200]
                 return
@@ -623,6 +647,7 @@ def main():
     g = sn.Grid(w.n, w.L, "c64", stream=stream.cuda_stream)
     if args.engine == "tc16":
         g.set_engine(sn.SN_ENGINE_TC16)
+    g.set_staging(sn.SN_STAGING_TMA if args.staging == "tma" else sn.SN_STAGING_REGISTERS)
     g.set_kernel(**kw)
     g.set_state(psi0)
     # schedule of the fused passes, picked by timing them (setup, before the timed region;
@@ -760,7 +785,7 @@ def main():
                                    f"16 lumps seed 3000, alpha_Y={args.alpha}, lambda_Y=10, "
                                    f"dt=1e-2",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "engine": args.engine,
+                       "engine": args.engine, "staging": args.staging,
                        "schedule": ("default" if schedule is None else
                                     "autotuned, CTAs per SM by [pass kind][axis] (0 = as many as "
                                     f"fit): {schedule}"),

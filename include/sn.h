@@ -254,6 +254,21 @@ sn_status sn_autotune(sn_grid g, double dt, int steps);
 typedef enum { SN_ENGINE_FP32 = 0, SN_ENGINE_TC16 = 1 } sn_engine;
 sn_status sn_set_engine(sn_grid g, int engine);
 
+/* How the fused complex64 passes move their tiles of lines between HBM and
+ * shared memory; the arithmetic, and so every result, is the same bit for bit.
+ *   SN_STAGING_TMA (default): each tile travels as one bulk tensor copy of the
+ *     tensor-memory accelerator into a shared-memory slot, and back out, while
+ *     the CTA transforms the tile in its other slot.  Taken by the plain
+ *     kinetic passes and the half-spectrum passes of 128- and 256-point lines
+ *     on the FP32 engine; the other passes keep register staging.  A tile wait
+ *     that does not end within about 2 s makes the next synchronising call
+ *     (sn_sync, sn_get_state to host, sn_observables) return SN_ETIMEOUT.
+ *   SN_STAGING_REGISTERS: every thread loads its elements of the next tile
+ *     into registers while it transforms the current one.
+ * Errors: SN_EINVAL (NULL grid, unknown mode). */
+typedef enum { SN_STAGING_TMA = 0, SN_STAGING_REGISTERS = 1 } sn_staging;
+sn_status sn_set_staging(sn_grid g, int mode);
+
 /* Test hook: in-place unnormalised DFTs, sign -1 (exp(-i ...)) or +1, of
  * nlines contiguous complex64 lines of length n (power of two, 8..1024) in
  * device memory, computed by the fused passes' line engine (engine as in

@@ -182,6 +182,10 @@ struct sn_grid_s {
   // and axis (psi passes: the line axis; half-spectrum passes: the half axis)
   int sched[SN_SCHED_KINDS][3] = {};
   int cur_axis = 0;
+  // how the fused passes move their tiles (sn_set_staging), and the device word
+  // the TMA passes set when a bounded tile wait expires
+  int staging = SN_STAGING_TMA;
+  int* status = nullptr;
 
   // Merged steps stay open across sn_step calls (complex64 grids).  While
   // `open`, psi holds Kin(h/2) of the state at the current integer step and
@@ -332,6 +336,36 @@ LineGeom psi_geom(sn_grid g, int a) {
 
 // ---- fused FP32 step ----------------------------------------------------------
 
+// Whether a pass over lines of length N takes the TMA-staged kernels.
+bool use_tma(sn_grid g, int N, bool strided, long long outer, long long inner) {
+  return g->staging == SN_STAGING_TMA && g->engine == SN_ENGINE_FP32 &&
+         line_pass_tma_supported(N, strided, outer, inner);
+}
+
+// A half-spectrum pass: TMA-staged when possible, else register-staged.
+cudaError_t rho_launch(sn_grid g, int N, bool strided, int op, const RhoPassArgs& ra) {
+  if (use_tma(g, N, strided, ra.outer, ra.inner)) {
+    LinePassArgs la{};
+    la.data = ra.data;
+    la.outer = ra.outer;
+    la.inner = ra.inner;
+    la.tw = ra.tw;
+    la.k2p = ra.k2p;
+    la.k2m = ra.k2m;
+    la.k2l = ra.k2l;
+    la.mid_n = ra.mid_n;
+    la.cN = ra.cN;
+    la.cY = ra.cY;
+    la.mu2 = ra.mu2;
+    la.cL = ra.cL;
+    la.status = g->status;
+    la.ctas_per_sm = ra.ctas_per_sm;
+    const int lop = op == RHO_FWD ? LINE_FWD : op == RHO_GREEN ? LINE_GREEN : LINE_INV;
+    return launch_line_pass_tma(N, strided, lop, la, g->stream);
+  }
+  return launch_rho_pass_f32(N, strided, op, ra, g->stream);
+}
+
 // Fields j .. j + nf - 1 of the grid in one launch.  A plain pass takes them
 // as nf times the lines (field-major, the fields extend the slowest axis); a
 // potential or density pass of the FP32 engine runs the fused fields kernel,
@@ -370,6 +404,24 @@ sn_status psi_pass(sn_grid g, void* base, int j, int nf, int a, int variant, int
   }
   pa.ctas_per_sm = g->sched[kind][a];
   g->cur_axis = a;
+  if (variant == PSI_PLAIN && use_tma(g, g->n[a], lg.strided, pa.outer, pa.inner)) {
+    LinePassArgs la{};
+    la.data = pa.psi;
+    la.outer = pa.outer;
+    la.inner = pa.inner;
+    la.tw = pa.tw;
+    la.lift = pa.lift;
+    la.status = g->status;
+    la.ctas_per_sm = pa.ctas_per_sm;
+    SN_LAUNCH(g, kind, bytes, launch_line_pass_tma(g->n[a], lg.strided, LINE_KINETIC, la, g->stream));
+    return SN_OK;
+  }
+  if (variant != PSI_PLAIN && pa.nfields <= 1 && !pa.rh_accum &&
+      use_tma(g, g->n[a], lg.strided, pa.outer, pa.inner)) {
+    SN_LAUNCH(g, kind, bytes,
+              launch_edge_pass_tma(g->n[a], lg.strided, variant, pa, g->status, g->stream));
+    return SN_OK;
+  }
   SN_LAUNCH(g, kind, bytes, launch_psi_pass_f32(g->n[a], lg.strided, variant, pa, g->stream));
   return SN_OK;
 }
@@ -408,7 +460,7 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
     ra.k2m = g->zero32;
     ra.k2l = g->k2_32[c];
     ra.mid_n = 1;
-    SN_LAUNCH(g, K_RHO_GREEN, bytes, launch_rho_pass_f32(g->n[c], false, RHO_GREEN, ra, g->stream));
+    SN_LAUNCH(g, K_RHO_GREEN, bytes, rho_launch(g, g->n[c], false, RHO_GREEN, ra));
     return SN_OK;
   }
   // 3D: y (array axis 1) is always the middle axis of the rho-hat passes
@@ -435,7 +487,7 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
     const bool st = geom(y, x);
     x.tw = g->tw32[log2i(g->n[y])];
     x.ctas_per_sm = g->sched[K_RHO_FWD][h];
-    SN_LAUNCH(g, K_RHO_FWD, bytes, launch_rho_pass_f32(g->n[y], st, RHO_FWD, x, g->stream));
+    SN_LAUNCH(g, K_RHO_FWD, bytes, rho_launch(g, g->n[y], st, RHO_FWD, x));
   }
   {
     RhoPassArgs x = ra;
@@ -444,14 +496,14 @@ sn_status rho_passes(sn_grid g, int h, double dt) {
     x.k2p = g->k2_32[h];
     x.k2l = g->k2_32[third];
     x.ctas_per_sm = g->sched[K_RHO_GREEN][h];
-    SN_LAUNCH(g, K_RHO_GREEN, bytes, launch_rho_pass_f32(g->n[third], st, RHO_GREEN, x, g->stream));
+    SN_LAUNCH(g, K_RHO_GREEN, bytes, rho_launch(g, g->n[third], st, RHO_GREEN, x));
   }
   {
     RhoPassArgs x = ra;
     const bool st = geom(y, x);
     x.tw = g->tw32[log2i(g->n[y])];
     x.ctas_per_sm = g->sched[K_RHO_INV][h];
-    SN_LAUNCH(g, K_RHO_INV, bytes, launch_rho_pass_f32(g->n[y], st, RHO_INV, x, g->stream));
+    SN_LAUNCH(g, K_RHO_INV, bytes, rho_launch(g, g->n[y], st, RHO_INV, x));
   }
   return SN_OK;
 }
@@ -523,6 +575,23 @@ sn_status closed_state(sn_grid g, void** out) {
     g->closed_valid = true;
   }
   *out = g->closed;
+  return SN_OK;
+}
+
+// After the grid's stream is synchronised: SN_ETIMEOUT if a TMA pass recorded
+// an expired tile wait since the last check (the word is cleared).
+sn_status check_status(sn_grid g) {
+  int st = 0;
+  cudaError_t e = cudaMemcpy(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(g, e, "reading the pass status");
+  if (st != 0) {
+    cudaMemset(g->status, 0, sizeof(int));
+    if (st == 2)
+      return fail(g, SN_ECUDA, "a TMA pass found its shared-memory tile slots misaligned and did "
+                               "not run; the state is incomplete");
+    return fail(g, SN_ETIMEOUT, "a pass kernel's bounded wait for a tile copy expired; the state is "
+                                "incomplete");
+  }
   return SN_OK;
 }
 
@@ -732,6 +801,9 @@ sn_status sn_create_grid(sn_grid* out, int ndim, const int* n, const double* L, 
   }
   if ((e = dalloc(g, &g->partials, (size_t)kObsBlocks * Q_NUM)) != cudaSuccess)
     return bail(cuda_fail(g, e, "cudaMalloc(partials)"));
+  if ((e = dalloc(g, &g->status, 1)) != cudaSuccess) return bail(cuda_fail(g, e, "cudaMalloc(status)"));
+  if ((e = cudaMemset(g->status, 0, sizeof(int))) != cudaSuccess)
+    return bail(cuda_fail(g, e, "cudaMemset(status)"));
   if ((e = dalloc(g, &g->obs_out, (size_t)Q_NUM)) != cudaSuccess)
     return bail(cuda_fail(g, e, "cudaMalloc(obs)"));
   for (int a = 0; a < ndim; ++a) {
@@ -942,7 +1014,7 @@ sn_status sn_get_state(sn_grid g, void* psi_out, int on_device) {
                                   g->stream);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(g, e, "sn_get_state copy");
-  return SN_OK;
+  return on_device ? SN_OK : check_status(g);
 }
 
 sn_status sn_step(sn_grid g, double dt, int nsteps) {
@@ -954,7 +1026,7 @@ sn_status sn_sync(sn_grid g) {
   if (!g) return fail(nullptr, SN_EINVAL, "sn_sync: grid is NULL");
   cudaError_t e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(g, e, "sn_sync");
-  return SN_OK;
+  return check_status(g);
 }
 
 sn_status sn_observables(sn_grid g, sn_obs* out) {
@@ -1029,6 +1101,7 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
   e = cudaMemcpyAsync(q, g->obs_out, sizeof(q), cudaMemcpyDeviceToHost, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   if (e != cudaSuccess) return cuda_fail(g, e, "sn_observables");
+  if ((st = check_status(g)) != SN_OK) return st;
 
   double dV = 1.0;
   for (int a = 0; a < d; ++a) dV *= g->L[a] / g->n[a];
@@ -1073,6 +1146,14 @@ sn_status sn_set_engine(sn_grid g, int engine) {
     if (e != cudaSuccess) return cuda_fail(g, e, "sn_set_engine: upload");
   }
   g->engine = engine;
+  return SN_OK;
+}
+
+sn_status sn_set_staging(sn_grid g, int mode) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_set_staging: grid is NULL");
+  if (mode != SN_STAGING_TMA && mode != SN_STAGING_REGISTERS)
+    return fail(g, SN_EINVAL, "sn_set_staging: unknown mode");
+  g->staging = mode;
   return SN_OK;
 }
 

@@ -84,6 +84,37 @@ enum RhoOp { RHO_FWD = 0, RHO_GREEN = 1, RHO_INV = 2 };
 
 cudaError_t launch_psi_pass_f32(int N, bool strided, int variant, const PsiPassArgs& a,
                                 cudaStream_t s);
+
+// ---- TMA-staged line passes (passes_tma.cu) ------------------------------------
+// The plain kinetic pass and the three half-spectrum passes with their tiles
+// moved by the tensor-memory accelerator; same arithmetic as the
+// register-staged kernels above, bit for bit.
+enum LineOp { LINE_KINETIC = 0, LINE_FWD = 1, LINE_GREEN = 2, LINE_INV = 3 };
+struct LinePassArgs {
+  void* data;              // complex64 lines, in place
+  long long outer, inner;  // as in PsiPassArgs
+  const float2* tw;        // twiddles of N
+  const float4* lift;      // LINE_KINETIC: kinetic shears
+  const float* k2p;        // LINE_GREEN: as in RhoPassArgs
+  const float* k2m;
+  const float* k2l;
+  long long mid_n;
+  float cN, cY, mu2, cL;
+  int* status;             // device word set to 1 if a bounded tile wait expired
+  int ctas_per_sm;         // schedule, as in PsiPassArgs
+};
+// Whether the TMA passes take lines of length N in this geometry (N = 128 or
+// 256, a driver that exports the tensor-map encoder).
+bool line_pass_tma_supported(int N, bool strided, long long outer, long long inner);
+// cudaErrorNotSupported if !line_pass_tma_supported.
+cudaError_t launch_line_pass_tma(int N, bool strided, int op, const LinePassArgs& a,
+                                 cudaStream_t s);
+// The potential pass (PSI_NPHASE) and the density pass (PSI_DENSITY) of one
+// field on the FP32 engine, TMA-staged; cudaErrorNotSupported for geometries
+// or options it does not take (several fields, an accumulated density, the
+// tensor-core engine).  status as in LinePassArgs.
+cudaError_t launch_edge_pass_tma(int N, bool strided, int variant, const PsiPassArgs& a,
+                                 int* status, cudaStream_t s);
 cudaError_t launch_rho_pass_f32(int N, bool strided, int op, const RhoPassArgs& a,
                                 cudaStream_t s);
 // Kinetic factor exp(i A k_j^2 tau) / n of the FP32 passes, j < n, as a rotation

@@ -1,0 +1,185 @@
+// Device building blocks of the TMA-staged pass kernels (passes_tma.cu).
+//
+// A pass kernel moves each tile of LPB lines between HBM and shared memory
+// with the tensor-memory accelerator (cp.async.bulk.tensor): a load completes
+// on an mbarrier, a store is a bulk group read from shared memory by the copy
+// engine.  The threads only transform: they read the tile into registers in
+// pattern P (sn_fft.cuh), run the line transforms with their stage exchanges
+// in the tile's own shared memory, and write the result back for the store.
+//
+// Exchange layouts (8-byte words, 32 banks = 16 bank pairs per half-warp):
+//   strided lines (half-warp = 16 lines at one position): [pos][line], the
+//     TMA tile's own layout, so the 16 lanes always hit 16 bank pairs;
+//   contiguous lines (half-warp = the T threads of 16 / T lines): [line][pos]
+//     with the low four bits of pos XOR-swizzled (swz below), chosen so that
+//     every write and read of the 2-stage Stockham exchange of 128- and
+//     256-point lines is served in the minimum two wavefronts per warp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sn_fft.cuh"
+
+namespace sn {
+namespace tma {
+
+using snfft::cx;
+using snfft::Plan;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// ---- mbarriers ---------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+// make the initialised barriers visible to the async proxy (the TMA unit)
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of bar, giving up after `budget` clock cycles.
+// Returns whether the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  long long budget) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+
+// ---- bulk tensor copies ---------------------------------------------------------
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const void* map, int c0, int c1, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const void* map, int c0, int c1, int c2,
+                                             const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// at most N of this thread's bulk groups still reading shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+// every bulk group of this thread complete (its global writes done)
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+// generic-proxy writes to shared memory, made visible to a following bulk store
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// ---- exchange layouts -----------------------------------------------------------
+// Word of position pos of line l in a tile slot (see the top of this file).
+template <int N, bool STRIDED, int LPB>
+__device__ __forceinline__ int xw(int l, int pos) {
+  if constexpr (STRIDED) {
+    return pos * LPB + l;
+  } else if constexpr (N == 256) {
+    return l * N + (pos ^ ((pos >> 4) & 15));
+  } else if constexpr (N == 128) {
+    return l * N + (pos ^ ((pos >> 3) & 6) ^ ((pos >> 6) & 1) ^ ((l & 1) ? 9 : 0));
+  } else {
+    return l * N + pos;
+  }
+}
+
+// Barrier among the threads that touch one line's words: the CTA for strided
+// tiles (a line's positions are spread over every warp), the warp otherwise
+// (a line of T <= 32 threads sits in one warp, and its words in its own row).
+template <bool STRIDED>
+__device__ __forceinline__ void xsync() {
+  if constexpr (STRIDED) __syncthreads();
+  else __syncwarp();
+}
+
+// In-place transform of my line (pattern P in and out), 2-stage Stockham plans
+// (32 <= N <= 256), with the stage exchange in the tile slot `buf` at the
+// words xw(l, pos).  Same arithmetic as snfft::line_transform.
+template <int N, int SIGN, bool STRIDED, int LPB>
+__device__ __forceinline__ void xform(cx<float> (&v)[Plan<N>::E], cx<float>* buf,
+                                      const cx<float>* tw_sm, int l, int t) {
+  using P = Plan<N>;
+  static_assert(P::STAGES == 2, "the TMA passes take 2-stage line plans");
+  constexpr int E = P::E, T = P::T;
+  constexpr int RA = SIGN < 0 ? P::R0 : P::R1;
+  constexpr int RB = SIGN < 0 ? P::R1 : P::R0;
+  constexpr int UA = E / RA, UB = E / RB;
+  xsync<STRIDED>();  // earlier readers of these words are done
+#pragma unroll
+  for (int u = 0; u < UA; ++u) {
+    cx<float> a[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) a[r] = v[u + r * UA];
+    snfft::dft<float, SIGN, RA>(a);
+    const int j = t + T * u;
+#pragma unroll
+    for (int q = 0; q < RA; ++q) buf[xw<N, STRIDED, LPB>(l, j * RA + q)] = a[q];
+  }
+  xsync<STRIDED>();
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = buf[xw<N, STRIDED, LPB>(l, t + T * m)];
+  const cx<float>* tw = tw_sm + (SIGN < 0 ? 0 : N);
+#pragma unroll
+  for (int u = 0; u < UB; ++u) {
+    const int j = t + T * u;
+    const int jm = j & (RA - 1);
+    cx<float> a[RB];
+    a[0] = v[u];
+#pragma unroll
+    for (int r = 1; r < RB; ++r) a[r] = snfft::tmul(v[u + r * UB], tw, r * RA + jm, P::TWN);
+    snfft::dft<float, SIGN, RB>(a);
+#pragma unroll
+    for (int q = 0; q < RB; ++q) v[u + q * UB] = a[q];
+  }
+}
+
+}  // namespace tma
+}  // namespace sn

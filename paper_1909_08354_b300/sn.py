@@ -19,6 +19,7 @@ LIB_PATH = os.environ.get("SN_LIB_PATH") or os.path.join(_HERE, "libsn.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 SN_ENGINE_FP32, SN_ENGINE_TC16 = 0, 1
+SN_STAGING_TMA, SN_STAGING_REGISTERS = 0, 1
 SN_C64, SN_C128 = 0, 1
 SN_KERNEL_NMC, SN_KERNEL_POISSON = 0, 1
 _STATUS = {0: "SN_OK", -1: "SN_EINVAL", -2: "SN_ENOMEM", -3: "SN_ECUDA", -4: "SN_ETIMEOUT",
@@ -86,6 +87,7 @@ _SIGNATURES = [
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     ("sn_kind_name", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_set_engine", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_set_staging", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sn_set_fluid", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SnFluid)]),
     ("sn_set_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sn_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -691,6 +693,11 @@ class Grid:
         """SN_ENGINE_FP32 or SN_ENGINE_TC16 (tensor cores on 256-point axes)."""
         _check(self.h, lib().sn_set_engine(self.h, int(engine)))
         self.engine = int(engine)
+
+    def set_staging(self, mode: int):
+        """SN_STAGING_TMA (tiles moved by bulk tensor copies) or SN_STAGING_REGISTERS;
+        the results are the same bit for bit."""
+        _check(self.h, lib().sn_set_staging(self.h, int(mode)))
 
     def sync(self):
         sn_sync(self.h)
