@@ -82,8 +82,8 @@ line_pass_tma_kernel(const __grid_constant__ TmaLineArgs a) {
   // 128 bytes and its base rounded up
   unsigned char* smem_raw = smem_dyn + ((128u - (tma::smem_u32(smem_dyn) & 127u)) & 127u);
   cx<float>* slots = reinterpret_cast<cx<float>*>(smem_raw);
-  cx<float>* tw_sm = slots + kSlots * TILE;
-  float4* lift_sm = reinterpret_cast<float4*>(tw_sm + 2 * P::TWN);
+  float4* tw_sm = reinterpret_cast<float4*>(slots + kSlots * TILE);
+  float4* lift_sm = tw_sm + P::TWN;
   uint64_t* bar = reinterpret_cast<uint64_t*>(lift_sm + N);
 
   const int tid = threadIdx.x;
@@ -93,10 +93,7 @@ line_pass_tma_kernel(const __grid_constant__ TmaLineArgs a) {
   const long long count = STRIDED ? a.outer * tiles_i : (a.outer + kLpb - 1) / kLpb;
 
   pdl_allow_next();
-  for (int k = tid; k < 2 * P::TWN; k += NT) {
-    const float2 w = a.tw[k];
-    tw_sm[k] = {w.x, w.y};
-  }
+  tma::stage_twiddles<N>(tw_sm, a.tw, tid, NT);
   if constexpr (OP == LINE_KINETIC)
     for (int k = tid; k < N; k += NT) lift_sm[k] = a.lift[k];
   if (tid == 0) {
@@ -294,8 +291,8 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
   // the swizzled regions need 1024-byte alignment: the window is over-allocated
   // by 1 KB and its base rounded up
   unsigned char* smem_raw = smem_dyn + ((1024u - (tma::smem_u32(smem_dyn) & 1023u)) & 1023u);
-  cx<float>* tw_sm = reinterpret_cast<cx<float>*>(smem_raw + 2 * SLOT);
-  float4* lift_sm = reinterpret_cast<float4*>(tw_sm + 2 * P::TWN);
+  float4* tw_sm = reinterpret_cast<float4*>(smem_raw + 2 * SLOT);
+  float4* lift_sm = tw_sm + P::TWN;
   uint64_t* bar = reinterpret_cast<uint64_t*>(lift_sm + N);
   auto psi_of = [&](int s) { return reinterpret_cast<cx<float>*>(smem_raw + s * SLOT); };
   auto rh_of = [&](int s) {
@@ -311,10 +308,7 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
   const long long count = STRIDED ? a.outer * tiles_i : (a.outer + kLpb - 1) / kLpb;
 
   pdl_allow_next();
-  for (int k = tid; k < 2 * P::TWN; k += NT) {
-    const float2 w = a.tw[k];
-    tw_sm[k] = {w.x, w.y};
-  }
+  tma::stage_twiddles<N>(tw_sm, a.tw, tid, NT);
   for (int k = tid; k < N; k += NT) lift_sm[k] = a.lift[k];
   if (tid == 0) {
     tma::mbar_init(&bar[0], 1);

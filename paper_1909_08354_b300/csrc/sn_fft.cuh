@@ -56,6 +56,11 @@ template <typename R>
 __device__ __forceinline__ cx<R> cconj(cx<R> a) { return {a.re, -a.im}; }
 template <typename R>
 __device__ __forceinline__ R cnorm2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+// FP32: the contraction written out (re^2 + fl(im^2) with one rounding of the
+// sum), so that every kernel rounds it alike whatever the compiler would fuse
+__device__ __forceinline__ float cnorm2(cx<float> a) {
+  return fmaf(a.re, a.re, __fmul_rn(a.im, a.im));
+}
 
 // a * (SIGN * i)
 template <typename R, int SIGN>
@@ -81,9 +86,11 @@ template <typename R, int SIGN, int Q>
 __device__ __forceinline__ cx<R> rot8(cx<R> a);
 
 // a * (wh + wl): product with a factor stored as a hi + lo pair (FP32 path).
+// Every product and sum is an explicit fmaf or rounded multiply, so all
+// kernels that inline it round alike.
 __device__ __forceinline__ cx<float> cmul_hl(cx<float> a, cx<float> wh, cx<float> wl) {
-  const float ur = a.re * wl.re - a.im * wl.im;
-  const float ui = a.re * wl.im + a.im * wl.re;
+  const float ur = fmaf(a.re, wl.re, __fmul_rn(-a.im, wl.im));
+  const float ui = fmaf(a.re, wl.im, __fmul_rn(a.im, wl.re));
   return {fmaf(a.re, wh.re, fmaf(-a.im, wh.im, ur)), fmaf(a.re, wh.im, fmaf(a.im, wh.re, ui))};
 }
 

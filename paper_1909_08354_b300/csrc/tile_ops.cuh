@@ -200,8 +200,10 @@ __device__ __forceinline__ void nonlinear_phase_at(cx<float> (&v)[E], VAt vat, f
                                                    int t, bool valid) {
 #pragma unroll
   for (int m = 0; m < E; ++m) {
-    float th = vat(m) + gh * cnorm2(v[m]);
-    if (vx != nullptr && valid) th += vx[(unsigned)(t + T * m) * ustride] * h;
+    // products and sums as explicit fmaf / rounded multiplies: every kernel
+    // that inlines this rounds alike
+    float th = fmaf(gh, cnorm2(v[m]), vat(m));
+    if (vx != nullptr && valid) th = fmaf(vx[(unsigned)(t + T * m) * ustride], h, th);
     const float kq = rintf(th * 0.159154943091895336f);
     float r = fmaf(-kq, 6.28318548202514648f, th);
     r = fmaf(-kq, -1.74845553e-7f, r);
@@ -212,7 +214,8 @@ __device__ __forceinline__ void nonlinear_phase_at(cx<float> (&v)[E], VAt vat, f
     const float e = -0.5f * fmaf(a, a, (b - 1.f) * (b + 1.f));
     cs = fmaf(cs, e, cs);
     sn = fmaf(sn, e, sn);
-    v[m] = {v[m].re * cs + v[m].im * sn, v[m].im * cs - v[m].re * sn};  // v * exp(-i th)
+    v[m] = {fmaf(v[m].re, cs, __fmul_rn(v[m].im, sn)),
+            fmaf(v[m].im, cs, __fmul_rn(-v[m].re, sn))};  // v * exp(-i th)
   }
 }
 // V from the line's row in shared memory

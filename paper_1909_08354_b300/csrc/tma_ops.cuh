@@ -140,12 +140,25 @@ __device__ __forceinline__ void xsync() {
   else __syncwarp();
 }
 
+// Twiddle table of N in shared memory as one float4 (hi.re, hi.im, lo.re,
+// lo.im) per entry, from the global table's hi parts [0, TWN) and lo parts
+// [TWN, 2 TWN): one 128-bit load per twiddle product.
+template <int N>
+__device__ __forceinline__ void stage_twiddles(float4* tw4, const float2* tw, int tid, int nt) {
+  constexpr int TWN = Plan<N>::TWN;
+  for (int k = tid; k < TWN; k += nt) {
+    const float2 h = tw[k], lo = tw[TWN + k];
+    tw4[k] = make_float4(h.x, h.y, lo.x, lo.y);
+  }
+}
+
 // In-place transform of my line (pattern P in and out), 2-stage Stockham plans
 // (32 <= N <= 256), with the stage exchange in the tile slot `buf` at the
-// words xw(l, pos).  Same arithmetic as snfft::line_transform.
+// words xw(l, pos).  Same arithmetic as snfft::line_transform (the twiddle
+// product is snfft::cmul_hl of the same hi and lo parts).
 template <int N, int SIGN, bool STRIDED, int LPB>
 __device__ __forceinline__ void xform(cx<float> (&v)[Plan<N>::E], cx<float>* buf,
-                                      const cx<float>* tw_sm, int l, int t) {
+                                      const float4* tw4, int l, int t) {
   using P = Plan<N>;
   static_assert(P::STAGES == 2, "the TMA passes take 2-stage line plans");
   constexpr int E = P::E, T = P::T;
@@ -166,7 +179,7 @@ __device__ __forceinline__ void xform(cx<float> (&v)[Plan<N>::E], cx<float>* buf
   xsync<STRIDED>();
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = buf[xw<N, STRIDED, LPB>(l, t + T * m)];
-  const cx<float>* tw = tw_sm + (SIGN < 0 ? 0 : N);
+  const float4* tw = tw4 + (SIGN < 0 ? 0 : N);
 #pragma unroll
   for (int u = 0; u < UB; ++u) {
     const int j = t + T * u;
@@ -174,7 +187,10 @@ __device__ __forceinline__ void xform(cx<float> (&v)[Plan<N>::E], cx<float>* buf
     cx<float> a[RB];
     a[0] = v[u];
 #pragma unroll
-    for (int r = 1; r < RB; ++r) a[r] = snfft::tmul(v[u + r * UB], tw, r * RA + jm, P::TWN);
+    for (int r = 1; r < RB; ++r) {
+      const float4 w = tw[r * RA + jm];
+      a[r] = snfft::cmul_hl(v[u + r * UB], {w.x, w.y}, {w.z, w.w});
+    }
     snfft::dft<float, SIGN, RB>(a);
 #pragma unroll
     for (int q = 0; q < RB; ++q) v[u + q * UB] = a[q];
