@@ -33,7 +33,11 @@ namespace sn {
 namespace {
 
 constexpr int kLpb = 16;                     // lines per tile
-constexpr int kSlots = 2;                    // tile slots per CTA
+// Tile slots per CTA: two for the passes with a transform pair per tile,
+// three for the forward and inverse half-spectrum passes, which have one
+// transform per tile and so need more tiles in flight to cover the loads.
+template <int OP>
+__host__ __device__ constexpr int line_slots() { return (OP == LINE_FWD || OP == LINE_INV) ? 3 : 2; }
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at the B300's clock
 
 // Kernel parameter block; the tensor map (aligned by its own type) must be a
@@ -58,12 +62,13 @@ __device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.w
 
 template <int N>
 constexpr int tma_threads() { return kLpb * Plan<N>::T; }
-// resident CTAs the registers are sized for (two tile slots per CTA in shared memory)
+// resident CTAs the registers are sized for (two or three tile slots per CTA)
 template <int N>
 constexpr int tma_min_ctas() { return N == 256 ? 2 : 4; }
 
-template <int N>
+template <int N, int OP>
 constexpr size_t tma_smem_bytes() {
+  constexpr int kSlots = line_slots<OP>();
   return 128 + kSlots * (size_t)kLpb * N * sizeof(float2)    // alignment, tile slots
          + 2 * (size_t)Plan<N>::TWN * sizeof(float2)          // twiddles (hi, lo)
          + (size_t)N * sizeof(float4)                         // kinetic shears
@@ -77,6 +82,7 @@ line_pass_tma_kernel(const __grid_constant__ TmaLineArgs a) {
   constexpr int E = P::E, T = P::T, NT = kLpb * T;
   constexpr int TILE = kLpb * N;  // words per slot
   constexpr unsigned TILE_BYTES = (unsigned)(TILE * sizeof(float2));
+  constexpr int kSlots = line_slots<OP>();
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   // the tile slots need 128-byte alignment: the window is over-allocated by
   // 128 bytes and its base rounded up
@@ -125,23 +131,27 @@ line_pass_tma_kernel(const __grid_constant__ TmaLineArgs a) {
     tma::bulk_commit();
   };
 
-  // Tile it of this CTA sits in slot it % 2.  The first two tiles are loaded
-  // up front.  Tile it is stored from its slot at the end of iteration it;
-  // thread 0 loads tile it + 2 into that slot one step later, once it holds
-  // the next tile in registers, so that the store has had that time to read
-  // the slot.
+  // Tile it of this CTA sits in slot it % kSlots.  The first kSlots tiles are
+  // loaded up front.  Tile it is stored from its slot at the end of iteration
+  // it; thread 0 loads tile it + kSlots into that slot one step later, once it
+  // holds the next tile in registers, so that the store has had that time to
+  // read the slot.
   long long tau = blockIdx.x;
   // loads issued into each slot, and waits completed on it (thread 0's count)
   int issued[kSlots] = {}, used[kSlots] = {};
   if (tid == 0) {
-    if (tau < count) { issue_load(0, tau); ++issued[0]; }
-    if (tau + gridDim.x < count) { issue_load(1, tau + gridDim.x); ++issued[1]; }
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q)
+      if (tau + (long long)q * gridDim.x < count) {
+        issue_load(q, tau + (long long)q * gridDim.x);
+        ++issued[q];
+      }
   }
   long long pend_tau = -1;  // thread 0: a load owed to slot pend_s
   int pend_s = 0;
 
   bool failed = false;
-  for (int it = 0, s = 0; tau < count; ++it, tau += gridDim.x, s ^= 1) {
+  for (int it = 0, s = 0; tau < count; ++it, tau += gridDim.x, s = (s + 1 == kSlots ? 0 : s + 1)) {
     cx<float>* buf = slots + s * TILE;
     const bool ok = tma::mbar_wait_bounded(&bar[s], (unsigned)(used[s] & 1), kWaitCycles);
     if (!__syncthreads_and(ok)) {
@@ -211,7 +221,7 @@ line_pass_tma_kernel(const __grid_constant__ TmaLineArgs a) {
     __syncthreads();
     if (tid == 0) {
       issue_store(s, tau);
-      const long long tau2 = tau + 2 * (long long)gridDim.x;
+      const long long tau2 = tau + (long long)kSlots * gridDim.x;
       if (tau2 < count) {
         pend_tau = tau2;
         pend_s = s;
@@ -636,7 +646,7 @@ unsigned tma_grid(K kern, int threads, size_t smem, long long ntiles, int cps) {
 
 template <int N, bool STRIDED, int OP>
 cudaError_t launch_t(const LinePassArgs& in, cudaStream_t s) {
-  constexpr size_t smem = tma_smem_bytes<N>();
+  constexpr size_t smem = tma_smem_bytes<N, OP>();
   constexpr int threads = tma_threads<N>();
   auto kern = line_pass_tma_kernel<N, STRIDED, OP>;
   static bool attr_of[kDeviceSlots] = {};
