@@ -220,19 +220,28 @@ const char* sn_kind_name(int k);
  * CTAs per SM of its persistent grid: 0 = as many as fit (the default),
  * 1 .. SN_SCHED_MAX_CTAS = at most that many, -1 = one CTA per tile of lines.
  * Every schedule computes bit-identical results; only the speed differs.
- * Layout of the 3 SN_SCHED_KINDS values: [3 k + a].
- * sn_get_schedule: out holds at least that many values.  sn_set_schedule:
- * exactly that many, each in [-1, SN_SCHED_MAX_CTAS], else SN_EINVAL.
+ * Layout of the 3 SN_SCHED_KINDS values: [3 k + a].  A full schedule
+ * (SN_SCHED_VALUES values) appends, at [3 SN_SCHED_KINDS + 3 k + a], the tile
+ * staging of each kind and axis: SN_STAGING_TMA, SN_STAGING_REGISTERS (see
+ * sn_set_staging), or -1 for the grid's own staging.
+ * sn_get_schedule: out holds at least 3 SN_SCHED_KINDS values (the staging
+ * part is written when it holds SN_SCHED_VALUES).  sn_set_schedule: exactly
+ * 3 SN_SCHED_KINDS values (the CTAs; staging entries unchanged) or
+ * SN_SCHED_VALUES values, CTAs in [-1, SN_SCHED_MAX_CTAS] and staging in
+ * [-1, SN_STAGING_REGISTERS], else SN_EINVAL.
  * sn_autotune: pick the schedule by the device time of whole steps (CUDA
  * events around sn_step(g, dt, steps) only, so the overlap of consecutive
  * passes counts).  For each pass kind and axis the step uses, one after
- * another, the candidates 0, -1, 1, 2, 3, 4, 6, 8 are timed and the fastest
- * kept if it is more than 1% faster; the result is kept only if it beats the
- * default schedule by at least 0.5% over 3 x steps.  The state and the step
+ * another, first the other staging is timed and kept if it is more than 1%
+ * faster, then the CTA candidates 0, -1, 1, 2, 3, 4, 6, 8 are timed and the
+ * fastest kept if it is more than 1% faster; the result is kept only if it
+ * beats the default schedule by at least 0.5% over 3 x steps.  An open merge
+ * (sn_step) is closed first.  The state and the step
  * counter are restored; blocks until done.  Errors: SN_ENOTSUP on SN_C128
  * grids, SN_EINVAL (non-finite dt, steps < 1), SN_ENOMEM, SN_ECUDA. */
 #define SN_SCHED_KINDS 6
 #define SN_SCHED_MAX_CTAS 64
+#define SN_SCHED_VALUES (6 * SN_SCHED_KINDS)
 sn_status sn_get_schedule(sn_grid g, int* out, int n);
 sn_status sn_set_schedule(sn_grid g, const int* in, int n);
 sn_status sn_autotune(sn_grid g, double dt, int steps);

@@ -181,6 +181,10 @@ struct sn_grid_s {
   // k > 0 = at most k, -1 = one per tile), by pass kind (K_PSI .. K_RHO_INV)
   // and axis (psi passes: the line axis; half-spectrum passes: the half axis)
   int sched[SN_SCHED_KINDS][3] = {};
+  // staging of each pass kind and axis: SN_STAGING_TMA, SN_STAGING_REGISTERS,
+  // or -1 for the grid's own (sn_set_staging)
+  int sched_st[SN_SCHED_KINDS][3] = {{-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1},
+                                     {-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}};
   int cur_axis = 0;
   // how the fused passes move their tiles (sn_set_staging), and the device word
   // the TMA passes set when a bounded tile wait expires
@@ -336,15 +340,19 @@ LineGeom psi_geom(sn_grid g, int a) {
 
 // ---- fused FP32 step ----------------------------------------------------------
 
-// Whether a pass over lines of length N takes the TMA-staged kernels.
-bool use_tma(sn_grid g, int N, bool strided, long long outer, long long inner) {
-  return g->staging == SN_STAGING_TMA && g->engine == SN_ENGINE_FP32 &&
+// Whether a pass of kind `kind` along `axis` over lines of length N takes the
+// TMA-staged kernels: its schedule entry's staging, else the grid's.
+bool use_tma(sn_grid g, int kind, int axis, int N, bool strided, long long outer,
+             long long inner) {
+  const int st = g->sched_st[kind][axis] >= 0 ? g->sched_st[kind][axis] : g->staging;
+  return st == SN_STAGING_TMA && g->engine == SN_ENGINE_FP32 &&
          line_pass_tma_supported(N, strided, outer, inner);
 }
 
 // A half-spectrum pass: TMA-staged when possible, else register-staged.
 cudaError_t rho_launch(sn_grid g, int N, bool strided, int op, const RhoPassArgs& ra) {
-  if (use_tma(g, N, strided, ra.outer, ra.inner)) {
+  const int kind = op == RHO_FWD ? K_RHO_FWD : op == RHO_GREEN ? K_RHO_GREEN : K_RHO_INV;
+  if (use_tma(g, kind, g->cur_axis, N, strided, ra.outer, ra.inner)) {
     LinePassArgs la{};
     la.data = ra.data;
     la.outer = ra.outer;
@@ -404,7 +412,7 @@ sn_status psi_pass(sn_grid g, void* base, int j, int nf, int a, int variant, int
   }
   pa.ctas_per_sm = g->sched[kind][a];
   g->cur_axis = a;
-  if (variant == PSI_PLAIN && use_tma(g, g->n[a], lg.strided, pa.outer, pa.inner)) {
+  if (variant == PSI_PLAIN && use_tma(g, kind, a, g->n[a], lg.strided, pa.outer, pa.inner)) {
     LinePassArgs la{};
     la.data = pa.psi;
     la.outer = pa.outer;
@@ -417,7 +425,7 @@ sn_status psi_pass(sn_grid g, void* base, int j, int nf, int a, int variant, int
     return SN_OK;
   }
   if (variant != PSI_PLAIN && pa.nfields <= 1 && !pa.rh_accum &&
-      use_tma(g, g->n[a], lg.strided, pa.outer, pa.inner)) {
+      use_tma(g, kind, a, g->n[a], lg.strided, pa.outer, pa.inner)) {
     SN_LAUNCH(g, kind, bytes,
               launch_edge_pass_tma(g->n[a], lg.strided, variant, pa, g->status, g->stream));
     return SN_OK;
@@ -1234,19 +1242,30 @@ sn_status sn_get_schedule(sn_grid g, int* out, int n) {
   if (!out || n < SN_SCHED_KINDS * 3)
     return fail(g, SN_EINVAL, "sn_get_schedule: out must hold SN_SCHED_KINDS * 3 values");
   for (int k = 0; k < SN_SCHED_KINDS; ++k)
-    for (int a = 0; a < 3; ++a) out[3 * k + a] = g->sched[k][a];
+    for (int a = 0; a < 3; ++a) {
+      out[3 * k + a] = g->sched[k][a];
+      if (n >= SN_SCHED_VALUES) out[SN_SCHED_KINDS * 3 + 3 * k + a] = g->sched_st[k][a];
+    }
   return SN_OK;
 }
 
 sn_status sn_set_schedule(sn_grid g, const int* in, int n) {
   if (!g) return fail(nullptr, SN_EINVAL, "sn_set_schedule: grid is NULL");
-  if (!in || n != SN_SCHED_KINDS * 3)
-    return fail(g, SN_EINVAL, "sn_set_schedule: in must hold SN_SCHED_KINDS * 3 values");
-  for (int i = 0; i < n; ++i)
+  if (!in || (n != SN_SCHED_KINDS * 3 && n != SN_SCHED_VALUES))
+    return fail(g, SN_EINVAL,
+                "sn_set_schedule: in must hold SN_SCHED_KINDS * 3 or SN_SCHED_VALUES values");
+  for (int i = 0; i < SN_SCHED_KINDS * 3; ++i)
     if (in[i] < -1 || in[i] > SN_SCHED_MAX_CTAS)
-      return fail(g, SN_EINVAL, "sn_set_schedule: values must be in [-1, SN_SCHED_MAX_CTAS]");
+      return fail(g, SN_EINVAL, "sn_set_schedule: CTA values must be in [-1, SN_SCHED_MAX_CTAS]");
+  for (int i = SN_SCHED_KINDS * 3; i < n; ++i)
+    if (in[i] < -1 || in[i] > SN_STAGING_REGISTERS)
+      return fail(g, SN_EINVAL, "sn_set_schedule: staging values must be -1, SN_STAGING_TMA or "
+                                "SN_STAGING_REGISTERS");
   for (int k = 0; k < SN_SCHED_KINDS; ++k)
-    for (int a = 0; a < 3; ++a) g->sched[k][a] = in[3 * k + a];
+    for (int a = 0; a < 3; ++a) {
+      g->sched[k][a] = in[3 * k + a];
+      if (n == SN_SCHED_VALUES) g->sched_st[k][a] = in[SN_SCHED_KINDS * 3 + 3 * k + a];
+    }
   return SN_OK;
 }
 
@@ -1275,8 +1294,9 @@ sn_status sn_autotune(sn_grid g, double dt, int steps) {
   if (e != cudaSuccess) return cuda_fail(g, e, "cudaMalloc(autotune state)");
   e = cudaMemcpyAsync(keep, g->psi, bytes, cudaMemcpyDeviceToDevice, g->stream);
   const long long step0 = g->step;
-  int saved[SN_SCHED_KINDS][3];
+  int saved[SN_SCHED_KINDS][3], saved_st[SN_SCHED_KINDS][3];
   std::memcpy(saved, g->sched, sizeof(saved));
+  std::memcpy(saved_st, g->sched_st, sizeof(saved_st));
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -1312,8 +1332,21 @@ sn_status sn_autotune(sn_grid g, double dt, int steps) {
   const int cand[] = {0, -1, 1, 2, 3, 4, 6, 8};
   double base = 0.0;
   for (int k = 0; k < SN_SCHED_KINDS; ++k)
-    for (int a = 0; a < 3; ++a) g->sched[k][a] = 0;
+    for (int a = 0; a < 3; ++a) {
+      g->sched[k][a] = 0;
+      g->sched_st[k][a] = -1;
+    }
   if (ok) ok = timed(steps, &base);
+  // the staging of each entry first (the grid's own, then the other)
+  for (int k = 0; k < SN_SCHED_KINDS && ok; ++k)
+    for (int a = 0; a < 3 && ok; ++a) {
+      if (!used[k][a]) continue;
+      g->sched_st[k][a] = g->staging == SN_STAGING_TMA ? SN_STAGING_REGISTERS : SN_STAGING_TMA;
+      double ms = 0.0;
+      ok = timed(steps, &ms);
+      if (ok && ms < 0.99 * base) base = ms;
+      else g->sched_st[k][a] = -1;
+    }
   for (int k = 0; k < SN_SCHED_KINDS && ok; ++k)
     for (int a = 0; a < 3 && ok; ++a) {
       if (!used[k][a]) continue;
@@ -1333,15 +1366,24 @@ sn_status sn_autotune(sn_grid g, double dt, int steps) {
     }
   if (ok) {
     // confirm against the default over longer runs
-    int tuned[SN_SCHED_KINDS][3];
+    int tuned[SN_SCHED_KINDS][3], tuned_st[SN_SCHED_KINDS][3];
     std::memcpy(tuned, g->sched, sizeof(tuned));
+    std::memcpy(tuned_st, g->sched_st, sizeof(tuned_st));
     double ms_tuned = 0.0, ms_default = 0.0;
     ok = timed(3 * steps, &ms_tuned);
     std::memset(g->sched, 0, sizeof(tuned));
+    for (int k = 0; k < SN_SCHED_KINDS; ++k)
+      for (int a = 0; a < 3; ++a) g->sched_st[k][a] = -1;
     if (ok) ok = timed(3 * steps, &ms_default);
-    if (ok && ms_tuned < 0.995 * ms_default) std::memcpy(g->sched, tuned, sizeof(tuned));
+    if (ok && ms_tuned < 0.995 * ms_default) {
+      std::memcpy(g->sched, tuned, sizeof(tuned));
+      std::memcpy(g->sched_st, tuned_st, sizeof(tuned_st));
+    }
   }
-  if (!ok) std::memcpy(g->sched, saved, sizeof(saved));
+  if (!ok) {
+    std::memcpy(g->sched, saved, sizeof(saved));
+    std::memcpy(g->sched_st, saved_st, sizeof(saved_st));
+  }
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);
   cudaError_t e2 = cudaMemcpyAsync(g->psi, keep, bytes, cudaMemcpyDeviceToDevice, g->stream);

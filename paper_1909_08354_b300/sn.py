@@ -46,6 +46,7 @@ def _kernel(coeff_lap=-0.5, G=1.0, alpha_Y=0.0, lambda_Y=1.0, g_local=0.0, zero_
 SN_GRAVITY_GR, SN_GRAVITY_NMC = 0, 1
 SN_MAX_FIELDS = 16  # include/sn.h
 SN_SCHED_KINDS, SN_SCHED_MAX_CTAS = 6, 64  # include/sn.h
+SN_SCHED_VALUES = 6 * SN_SCHED_KINDS  # CTAs per SM, then the staging, of each kind and axis
 
 
 class SnFluid(ctypes.Structure):
@@ -559,7 +560,8 @@ class Batch:
 
 
 # ----------------------------------------------------------------------------
-# Schedule cache (JSON): {key: [3 * SN_SCHED_KINDS CTAs-per-SM values]}
+# Schedule cache (JSON): {key: [SN_SCHED_VALUES values: 3 * SN_SCHED_KINDS CTAs per SM,
+# then 3 * SN_SCHED_KINDS stagings]}
 # ----------------------------------------------------------------------------
 
 def schedule_key(device: str, n: Sequence[int], engine: int, fields: int) -> str:
@@ -573,8 +575,11 @@ def load_schedule(path: str, key: str):
             vals = json.load(f).get(key)
     except (OSError, ValueError, AttributeError):
         return None
-    if (not isinstance(vals, list) or len(vals) != 3 * SN_SCHED_KINDS
-            or not all(isinstance(v, int) and -1 <= v <= SN_SCHED_MAX_CTAS for v in vals)):
+    m = 3 * SN_SCHED_KINDS
+    if (not isinstance(vals, list) or len(vals) != SN_SCHED_VALUES
+            or not all(isinstance(v, int) for v in vals)
+            or not all(-1 <= v <= SN_SCHED_MAX_CTAS for v in vals[:m])
+            or not all(-1 <= v <= SN_STAGING_REGISTERS for v in vals[m:])):
         return None
     return vals
 
@@ -661,8 +666,9 @@ class Grid:
         _check(self.h, lib().sn_set_fluid(self.h, ctypes.byref(f)))
 
     def schedule(self) -> list:
-        """CTAs per SM of each fused pass kind and axis, [3 k + a] (sn_get_schedule)."""
-        buf = (ctypes.c_int * (3 * SN_SCHED_KINDS))()
+        """CTAs per SM of each fused pass kind and axis, [3 k + a], then the staging of
+        each, [3 SN_SCHED_KINDS + 3 k + a] (sn_get_schedule)."""
+        buf = (ctypes.c_int * SN_SCHED_VALUES)()
         _check(self.h, lib().sn_get_schedule(self.h, buf, len(buf)))
         return list(buf)
 

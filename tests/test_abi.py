@@ -76,6 +76,10 @@ def test_schedule_constants_match_the_header():
     text = open(os.path.join(ROOT, "include", "sn.h")).read()
     assert int(re.search(r"#define SN_SCHED_KINDS (\d+)", text).group(1)) == sn.SN_SCHED_KINDS
     assert int(re.search(r"#define SN_SCHED_MAX_CTAS (\d+)", text).group(1)) == sn.SN_SCHED_MAX_CTAS
+    m = re.search(r"#define SN_SCHED_VALUES \((\d+) \* SN_SCHED_KINDS\)", text)
+    assert int(m.group(1)) * sn.SN_SCHED_KINDS == sn.SN_SCHED_VALUES
+    m = re.search(r"SN_STAGING_TMA = (\d+), SN_STAGING_REGISTERS = (\d+)", text)
+    assert (int(m.group(1)), int(m.group(2))) == (sn.SN_STAGING_TMA, sn.SN_STAGING_REGISTERS)
     # the schedule kinds are the first kernel kinds, in order
     assert sn.sn_kind_names()[:sn.SN_SCHED_KINDS] == ["psi_pass", "psi_pass_nphase",
                                                       "psi_pass_density", "rho_fwd", "rho_green",
@@ -96,15 +100,19 @@ def test_schedule_cache_round_trip(tmp_path):
     k2 = sn.schedule_key("B300", (256, 256, 256), sn.SN_ENGINE_FP32, 2)
     assert k1 != k2 and "256x256x256" in k1
     assert sn.load_schedule(path, k1) is None  # no file yet
-    v1 = [0, 1, 2] * 6
+    v1 = [0, 1, 2] * 6 + [-1, 0, 1] * 6
     sn.store_schedule(path, k1, v1)
-    sn.store_schedule(path, k2, [-1] * 18)
+    sn.store_schedule(path, k2, [-1] * sn.SN_SCHED_VALUES)
     assert sn.load_schedule(path, k1) == v1
-    assert sn.load_schedule(path, k2) == [-1] * 18
+    assert sn.load_schedule(path, k2) == [-1] * sn.SN_SCHED_VALUES
     # malformed entries and files are ignored, not trusted
-    sn.store_schedule(path, k1, [0] * 17)
+    sn.store_schedule(path, k1, [0] * (sn.SN_SCHED_VALUES - 1))
     assert sn.load_schedule(path, k1) is None
-    sn.store_schedule(path, k1, [99] * 18)
+    sn.store_schedule(path, k1, [0] * 18)  # a schedule without its staging part
+    assert sn.load_schedule(path, k1) is None
+    sn.store_schedule(path, k1, [99] * 18 + [0] * 18)
+    assert sn.load_schedule(path, k1) is None
+    sn.store_schedule(path, k1, [0] * 18 + [2] * 18)  # no staging mode 2
     assert sn.load_schedule(path, k1) is None
     with open(path, "w") as f:
         f.write("not json")

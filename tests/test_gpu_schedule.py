@@ -9,7 +9,7 @@ from paper_1909_08354_b300 import sn
 
 pytestmark = pytest.mark.gpu
 
-N_SCHED = 3 * sn.SN_SCHED_KINDS
+N_SCHED = 3 * sn.SN_SCHED_KINDS  # the CTA part of a schedule
 
 
 def kernel_kw(kp):
@@ -36,13 +36,17 @@ def run(shape, schedule=None, fields=1, engine=sn.SN_ENGINE_FP32, seed=5, steps=
 
 @pytest.mark.parametrize("shape,fields,engine", [
     ((32, 64, 16), 1, sn.SN_ENGINE_FP32), ((1024, 16), 1, sn.SN_ENGINE_FP32),
-    ((16, 512), 2, sn.SN_ENGINE_FP32), ((16, 256, 8), 1, sn.SN_ENGINE_TC16)])
+    ((16, 512), 2, sn.SN_ENGINE_FP32), ((16, 256, 8), 1, sn.SN_ENGINE_TC16),
+    ((64, 256, 128), 1, sn.SN_ENGINE_FP32), ((16, 128, 256), 2, sn.SN_ENGINE_FP32)])
 def test_every_schedule_gives_the_same_bits(shape, fields, engine):
     ref = run(shape, None, fields, engine)
     for c in (-1, 1, 2, 3, 8, sn.SN_SCHED_MAX_CTAS):
         assert np.array_equal(run(shape, [c] * N_SCHED, fields, engine), ref), c
     mixed = [(-1, 0, 1, 2)[i % 4] for i in range(N_SCHED)]
     assert np.array_equal(run(shape, mixed, fields, engine), ref)
+    # the staging of each pass kind and axis, chosen per entry
+    staged = mixed + [(-1, sn.SN_STAGING_TMA, sn.SN_STAGING_REGISTERS)[i % 3] for i in range(N_SCHED)]
+    assert np.array_equal(run(shape, staged, fields, engine), ref)
 
 
 def test_autotune_keeps_the_state_and_the_bits(tmp_path):
@@ -57,7 +61,9 @@ def test_autotune_keeps_the_state_and_the_bits(tmp_path):
         step0 = g.observables()["step"]
         cache = str(tmp_path / "sched.json")
         vals = g.autotune(0.02, steps=4, cache=cache, device="test-device")
-        assert len(vals) == N_SCHED and all(-1 <= v <= sn.SN_SCHED_MAX_CTAS for v in vals)
+        assert len(vals) == sn.SN_SCHED_VALUES
+        assert all(-1 <= v <= sn.SN_SCHED_MAX_CTAS for v in vals[:N_SCHED])
+        assert all(-1 <= v <= sn.SN_STAGING_REGISTERS for v in vals[N_SCHED:])
         assert g.schedule() == vals
         assert np.array_equal(g.get_state(), before)
         assert g.observables()["step"] == step0
@@ -82,12 +88,19 @@ def test_autotune_keeps_the_state_and_the_bits(tmp_path):
 def test_schedule_validation():
     g = sn.Grid((16, 16), (4.0, 4.0), "c64")
     try:
-        assert g.schedule() == [0] * N_SCHED
+        # a new grid: every pass as many CTAs as fit, with the grid's own staging
+        assert g.schedule() == [0] * N_SCHED + [-1] * N_SCHED
         for bad in ([0] * (N_SCHED - 1), [-2] + [0] * (N_SCHED - 1),
-                    [sn.SN_SCHED_MAX_CTAS + 1] + [0] * (N_SCHED - 1)):
+                    [sn.SN_SCHED_MAX_CTAS + 1] + [0] * (N_SCHED - 1),
+                    [0] * N_SCHED + [2] * N_SCHED, [0] * N_SCHED + [-2] * N_SCHED,
+                    [0] * (N_SCHED + 1)):
             with pytest.raises(sn.SNError) as e:
                 g.set_schedule(bad)
             assert e.value.status == sn.SN_EINVAL
+        # the short form sets the CTAs and keeps the staging
+        g.set_schedule([1] * N_SCHED + [sn.SN_STAGING_REGISTERS] * N_SCHED)
+        g.set_schedule([2] * N_SCHED)
+        assert g.schedule() == [2] * N_SCHED + [sn.SN_STAGING_REGISTERS] * N_SCHED
         for bad_dt, bad_steps in ((float("nan"), 2), (0.01, 0)):
             with pytest.raises(sn.SNError) as e:
                 sn._check(g.h, sn.lib().sn_autotune(g.h, bad_dt, bad_steps))
