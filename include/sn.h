@@ -126,7 +126,11 @@ sn_status sn_set_kernel(sn_grid g, const sn_kernel* k);
  *        (Eqs. 11-12), r0 = M / (4 pi),
  * rho = |psi|^2, r the distance from the box centre (the node x = 0), taken
  * as at least half the smallest grid spacing (phi_C is -infinite at r = 0);
- * sqrt rho and ln rho use max(rho, rho_floor). */
+ * sqrt rho and ln rho use max(rho, rho_floor), or with floor_mode =
+ * SN_FLOOR_SMOOTH rho + rho_floor: the kink of sqrt(max(rho, floor)) where
+ * the density crosses the floor makes the Bohm term spike there, by an
+ * amount that grows as the grid refines, and the spike radiates
+ * high-wavenumber waves (group speed ~ nu k) across the box. */
 typedef enum { SN_GRAVITY_GR = 0, SN_GRAVITY_NMC = 1 } sn_gravity;
 typedef struct {
   double nu;        /* > 0: the analogue of hbar, psi = sqrt(rho) exp(i Phi / nu) */
@@ -136,15 +140,23 @@ typedef struct {
   double lambda;    /* NMC: coupling strength (> 0)                              */
   double M;         /* NMC: mass setting r0 = M / (4 pi) (> 0)                   */
   double rho_floor; /* > 0                                                       */
+  int floor_mode;   /* SN_FLOOR_MAX: sqrt rho and ln rho of max(rho, rho_floor);
+                       SN_FLOOR_SMOOTH: of rho + rho_floor (no kink where rho
+                       crosses the floor)                                        */
 } sn_fluid;
+enum { SN_FLOOR_MAX = 0, SN_FLOOR_SMOOTH = 1 };
 
 /* Switch an SN_C128 grid to the fluid model of Eq. 16 (f != NULL) or back
  * to Eqs. 1-2 (f == NULL; sn_set_kernel also switches back).  sn_step then
  * takes symmetric split steps of Eq. 16: Kin(h/2) with A = -nu/2, the exact
  * potential sub-step psi exp(-i U h / nu) (U depends on rho only), Kin(h/2).
  * The profiles gamma, beta, phi_C are built once here, in FP64 on the host.
- * In this mode sn_observables reports mass, e_kin (with A = -nu/2),
- * centroids and momenta; e_pot and e_nl are 0.  Errors: SN_ENOTSUP on SN_C64
+ * In this mode sn_observables reports mass, centroids, momenta and the
+ * energies of the solver's form i psi_t = -(nu/2) lap psi + (U/nu) psi:
+ * e_kin = (nu/2) int |grad psi|^2, e_pot = (1/2 int phi_N rho + int phi_C
+ * rho) / nu, e_nl = (-(nu^2/2) int |grad sqrt rho|^2 + int eps(rho)) / nu with
+ * eps the polytropic internal energy (d eps / d rho = V_p); under GR their sum
+ * is the conserved Hamiltonian.  Errors: SN_ENOTSUP on SN_C64
  * grids (this build steps Eq. 16 in FP64 only) and on grids of several fields
  * (sn_set_fields), SN_EINVAL for bad values, SN_ENOMEM, SN_ECUDA. */
 sn_status sn_set_fluid(sn_grid g, const sn_fluid* f);
@@ -374,6 +386,12 @@ void sn_fno_destroy(sn_fno f);
 sn_status sn_fno_pack(const float* psi, const float* feats, int nfeat, float* X, int B,
                       long long cells, void* cuda_stream);
 sn_status sn_fno_unpack(const float* Y, float* psi, int B, long long cells, void* cuda_stream);
+/* Input of the corrector form of the surrogate: X[b] = (re a, im a, re c,
+ * im c, feats[b][0..nfeat-1] as constant planes), planar [B][4+nfeat][cells],
+ * from two interleaved complex64 states per sample (a: the state the head
+ * turns, e.g. a coarse solve of the same horizon; c: the starting state). */
+sn_status sn_fno_pack2(const float* psi_a, const float* psi_c, const float* feats, int nfeat,
+                       float* X, int B, long long cells, void* cuda_stream);
 /* out[b] = sum |psi_b|^2 (FP64, device output) for B complex64 states of `cells` values. */
 sn_status sn_mass_c64(const float* psi, int B, long long cells, double* out, void* cuda_stream);
 /* Test hook: the BF16 tensor-core GEMM C[z] = alpha A[z] B[z] + beta C[z] on

@@ -48,6 +48,7 @@ class CosmoParams:
     lam: float = 1.0        # NMC strength lambda (Eqs. 11-13)
     M: float = 25.0         # mass setting r0 = M / (4 pi)
     rho_floor: float = 1e-12
+    floor_mode: int = 0     # 0: max(rho, floor) under sqrt and ln; 1: rho + floor (smooth)
 
 
 def radius(n: Sequence[int], L: Sequence[float]) -> np.ndarray:
@@ -81,9 +82,15 @@ def spectral_laplacian(f: np.ndarray, L: Sequence[float]) -> np.ndarray:
     return fftn(-k_squared(f.shape, L) * fftn(f), inverse=True).real
 
 
-def bohm_potential(rho: np.ndarray, L: Sequence[float], rho_floor: float) -> np.ndarray:
-    """V_B = lap(sqrt rho) / (2 sqrt rho), sqrt rho of max(rho, rho_floor)."""
-    a = np.sqrt(np.maximum(rho, rho_floor))
+def floored(rho: np.ndarray, rho_floor: float, floor_mode: int = 0) -> np.ndarray:
+    """rho as it enters sqrt and ln: max(rho, floor), or rho + floor (floor_mode 1)."""
+    return rho + rho_floor if floor_mode == 1 else np.maximum(rho, rho_floor)
+
+
+def bohm_potential(rho: np.ndarray, L: Sequence[float], rho_floor: float,
+                   floor_mode: int = 0) -> np.ndarray:
+    """V_B = lap(sqrt rho) / (2 sqrt rho), sqrt rho of the floored rho."""
+    a = np.sqrt(floored(rho, rho_floor, floor_mode))
     return spectral_laplacian(a, L) / (2.0 * a)
 
 
@@ -100,7 +107,7 @@ def newtonian_potential(rho: np.ndarray, L: Sequence[float], gamma: np.ndarray,
 
 def pressure_potential(rho: np.ndarray, p: CosmoParams) -> np.ndarray:
     """V_p of P = w rho^n: w ln rho (n = 1) or n w / (n - 1) rho^(n-1)."""
-    r = np.maximum(rho, p.rho_floor)
+    r = floored(rho, p.rho_floor, p.floor_mode)
     if p.n_poly == 1.0:
         return p.w * np.log(r)
     return p.n_poly * p.w / (p.n_poly - 1.0) * r ** (p.n_poly - 1.0)
@@ -109,7 +116,7 @@ def pressure_potential(rho: np.ndarray, p: CosmoParams) -> np.ndarray:
 def total_potential(rho: np.ndarray, L: Sequence[float], p: CosmoParams) -> np.ndarray:
     """U = nu^2 V_B + phi_N + phi_C + V_p (the bracket of Eq. 16)."""
     gamma, beta, phi_c = coupling_profiles(rho.shape, L, p)
-    return (p.nu ** 2 * bohm_potential(rho, L, p.rho_floor)
+    return (p.nu ** 2 * bohm_potential(rho, L, p.rho_floor, p.floor_mode)
             + newtonian_potential(rho, L, gamma, beta) + phi_c + pressure_potential(rho, p))
 
 
@@ -128,6 +135,40 @@ def cosmo_evolve(psi: np.ndarray, h: float, nsteps: int, L: Sequence[float],
     for _ in range(nsteps):
         psi = cosmo_step(psi, h, L, p)
     return psi
+
+
+def internal_energy(rho: np.ndarray, p: CosmoParams) -> np.ndarray:
+    """eps(rho) with d eps / d rho = V_p (P = w rho^n): w rho (ln rho - 1) for n = 1,
+    w rho^n / (n - 1) otherwise; rho under ln and the power taken as max(rho, floor)."""
+    r = floored(rho, p.rho_floor, p.floor_mode)
+    if p.n_poly == 1.0:
+        return p.w * rho * (np.log(r) - 1.0)
+    return p.w * rho * r ** (p.n_poly - 1.0) / (p.n_poly - 1.0)
+
+
+def fluid_energies(psi: np.ndarray, L: Sequence[float], p: CosmoParams) -> Dict[str, float]:
+    """Energies of Eq. 16 in the solver's form i psi_t = -(nu/2) lap psi + (U/nu) psi,
+    whose Hamiltonian is int [(nu/2)|grad psi|^2] + (1/nu) times the functional
+    whose rho-derivative is U:
+      e_kin = (nu/2) int |grad psi|^2                     (spectral, as sn_oracle),
+      e_pot = (1/nu) [ (1/2) int phi_N rho + int phi_C rho ],
+      e_nl  = (1/nu) [ -(nu^2/2) int |grad sqrt rho|^2 + int eps(rho) ]
+    (-(nu^2/2) int |grad a|^2 has rho-derivative nu^2 V_B, eps has V_p; the
+    gradient term is -int a lap a on the periodic box, a = sqrt(max(rho, floor))).
+    Under GR (phi_N linear and symmetric in rho) e_kin + e_pot + e_nl is the
+    conserved Hamiltonian of the exact flow."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    rho = (psi * np.conj(psi)).real
+    dV = cell_volume(psi.shape, L)
+    gamma, beta, phi_c = coupling_profiles(psi.shape, L, p)
+    phi_n = newtonian_potential(rho, L, gamma, beta)
+    a = np.sqrt(floored(rho, p.rho_floor, p.floor_mode))
+    grad_a2 = -float((a * spectral_laplacian(a, L)).sum()) * dV
+    psik = fftn(psi)
+    e_kin = 0.5 * p.nu * dV / psi.size * float((k_squared(psi.shape, L) * np.abs(psik) ** 2).sum())
+    e_pot = dV * (0.5 * float((phi_n * rho).sum()) + float((phi_c * rho).sum())) / p.nu
+    e_nl = (-0.5 * p.nu ** 2 * grad_a2 + dV * float(internal_energy(rho, p).sum())) / p.nu
+    return dict(e_kin=e_kin, e_pot=e_pot, e_nl=e_nl, e_total=e_kin + e_pot + e_nl)
 
 
 def mass(psi: np.ndarray, L: Sequence[float]) -> float:

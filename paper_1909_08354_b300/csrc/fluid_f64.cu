@@ -26,14 +26,20 @@ __device__ __forceinline__ double density(const double2* psi, long long c) {
   return z.x * z.x + z.y * z.y;
 }
 
+// rho as it enters sqrt and ln: max(rho, floor) or rho + floor (smooth)
+__device__ __forceinline__ double floored(double rho, double floor, int mode) {
+  return mode == 1 ? rho + floor : fmax(rho, floor);
+}
+
 // wa = rho + i sqrt(max(rho, floor)): two real fields in one complex array, so
 // that one FFT, the Laplacian multiplier and one inverse FFT give both
 // Laplacians (real part: lap rho, imaginary part: lap sqrt rho)
-__global__ void prep_kernel(const double2* psi, double2* wa, double floor, long long cells) {
+__global__ void prep_kernel(const double2* psi, double2* wa, double floor, int mode,
+                            long long cells) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const double rho = density(psi, c);
-    wa[c] = make_double2(rho, sqrt(fmax(rho, floor)));
+    wa[c] = make_double2(rho, sqrt(floored(rho, floor, mode)));
   }
 }
 
@@ -70,7 +76,7 @@ __global__ void phase_kernel(double2* psi, const double2* wphi, const double2* w
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const double2 z = psi[c];
-    const double rf = fmax(z.x * z.x + z.y * z.y, p.rho_floor);
+    const double rf = floored(z.x * z.x + z.y * z.y, p.rho_floor, p.floor_mode);
     const double vb = wlap[c].y / (2.0 * sqrt(rf));  // lap sqrt rho / (2 sqrt rho)
     const double vp = p.n_poly == 1.0 ? p.w * log(rf) : p.cp * pow(rf, p.n_poly - 1.0);
     double u = fma(p.nu * p.nu, vb, wphi[c].x + vp);
@@ -83,9 +89,9 @@ __global__ void phase_kernel(double2* psi, const double2* wphi, const double2* w
 
 }  // namespace
 
-cudaError_t launch_fluid_prep_f64(const double2* psi, double2* wa, double floor, long long cells,
-                                  cudaStream_t s) {
-  prep_kernel<<<blocks_for(cells), kThreads, 0, s>>>(psi, wa, floor, cells);
+cudaError_t launch_fluid_prep_f64(const double2* psi, double2* wa, double floor, int floor_mode,
+                                  long long cells, cudaStream_t s) {
+  prep_kernel<<<blocks_for(cells), kThreads, 0, s>>>(psi, wa, floor, floor_mode, cells);
   return cudaGetLastError();
 }
 

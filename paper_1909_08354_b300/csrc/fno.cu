@@ -263,6 +263,22 @@ __global__ void pack_kernel(const float2* psi, const float* feats, int nf, float
   }
 }
 
+// X[b] = (re a, im a, re c, im c, f0, f1, ...) planes from interleaved a[b], c[b]
+// and feats[b][nf]
+__global__ void pack2_kernel(const float2* a, const float2* c, const float* feats, int nf, float* X,
+                             ll P, ll n) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
+    const ll b = i / P, p = i - b * P;
+    const float2 za = a[i], zc = c[i];
+    float* x = X + b * (4 + nf) * P + p;
+    x[0] = za.x;
+    x[P] = za.y;
+    x[2 * P] = zc.x;
+    x[3 * P] = zc.y;
+    for (int k = 0; k < nf; ++k) x[(4 + k) * P] = feats[b * nf + k];
+  }
+}
+
 __global__ void unpack_kernel(const float* Y, float2* psi, ll P, ll n) {
   for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
     const ll b = i / P, p = i - b * P;
@@ -761,6 +777,17 @@ sn_status sn_fno_pack(const float* psi, const float* feats, int nfeat, float* X,
     return ffail(SN_EINVAL, "sn_fno_pack: bad argument");
   pack_kernel<<<blocks_for((ll)B * cells), 256, 0, (cudaStream_t)cuda_stream>>>(
       reinterpret_cast<const float2*>(psi), feats, nfeat, X, cells, (ll)B * cells);
+  FCHK(cudaGetLastError());
+  return SN_OK;
+}
+
+sn_status sn_fno_pack2(const float* psi_a, const float* psi_c, const float* feats, int nfeat,
+                       float* X, int B, long long cells, void* cuda_stream) {
+  if (!psi_a || !psi_c || !X || B < 1 || cells < 1 || nfeat < 0 || (nfeat > 0 && !feats))
+    return ffail(SN_EINVAL, "sn_fno_pack2: bad argument");
+  pack2_kernel<<<blocks_for((ll)B * cells), 256, 0, (cudaStream_t)cuda_stream>>>(
+      reinterpret_cast<const float2*>(psi_a), reinterpret_cast<const float2*>(psi_c), feats, nfeat,
+      X, cells, (ll)B * cells);
   FCHK(cudaGetLastError());
   return SN_OK;
 }

@@ -263,6 +263,26 @@ __global__ void obs_green_kernel(const double2* rh, Dims d, const double* k20, c
   block_reduce_store<1>(acc, partials, Q_EPOT);
 }
 
+// Energy terms of the self-gravitating fluid (Eq. 16), into partials[0..3]:
+// sum rho phi_N, sum rho phi_C, sum eps(rho) (the polytropic internal energy,
+// d eps / d rho = V_p), sum a lap(a) with a = sqrt(max(rho, floor)).
+__global__ void obs_fluid_kernel(const double2* psi, const double2* wphi, const double2* wlap,
+                                 const double* phi_c, double w, double n_poly, double floor,
+                                 int mode, long long cells, double* partials) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    const double rho = cnorm2(ldd(psi + c));
+    const double rf = mode == 1 ? rho + floor : fmax(rho, floor);
+    acc[0] += rho * wphi[c].x;
+    if (phi_c != nullptr) acc[1] += rho * phi_c[c];
+    acc[2] += n_poly == 1.0 ? w * rho * (log(rf) - 1.0)
+                            : w * rho * pow(rf, n_poly - 1.0) / (n_poly - 1.0);
+    acc[3] += sqrt(rf) * wlap[c].y;
+  }
+  block_reduce_store<4>(acc, partials, 0);
+}
+
 __global__ void obs_finish_kernel(const double* partials, int nblocks, double* out) {
   const int q = threadIdx.x;
   if (q >= Q_NUM) return;
@@ -365,6 +385,14 @@ cudaError_t launch_obs_green(const double2* rhohat, const int* n, int ndim,
   const double* a2 = ndim == 3 ? k2[2] : k2[1];
   obs_green_kernel<<<kObsBlocks, kEwThreads, 0, s>>>(rhohat, dims_of(n, ndim), a0, a1, a2, cN, cY,
                                                      mu2, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_obs_fluid(const double2* psi, const double2* wphi, const double2* wlap,
+                             const double* phi_c, double w, double n_poly, double floor,
+                             int floor_mode, long long cells, double* partials, cudaStream_t s) {
+  obs_fluid_kernel<<<kObsBlocks, 256, 0, s>>>(psi, wphi, wlap, phi_c, w, n_poly, floor,
+                                              floor_mode, cells, partials);
   return cudaGetLastError();
 }
 

@@ -673,18 +673,44 @@ sn_status step_f64(sn_grid g, double dt, int nsteps) {
 // sub-step forms rho + i sqrt(rho) and takes both spectral Laplacians with one
 // FFT pair, forms the source of Eq. 15 and its inverse Laplacian, then turns
 // psi by U h / nu: eight full complex FFTs per step.
-sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
+// The fields of Eq. 16's potential from psi: wa = lap rho + i lap sqrt(rho)
+// (sqrt of max(rho, floor); both Laplacians from one FFT pair of rho + i sqrt
+// rho) and w = phi_N of Eq. 15 (real part).  Four full complex FFTs.
+sn_status fluid_fields(sn_grid g, const double2* psi, double2* wa, double2* w) {
+  sn_status st;
+  const double* k2[3] = {g->k2_64[0], g->k2_64[1], g->k2_64[2]};
+  const double inv_n = 1.0 / (double)g->cells;
+  const bool nmc = g->fl.model == SN_GRAVITY_NMC;
+  const double ew = 32.0 * g->cells;
+  SN_LAUNCH(g, K_F64_EW, ew,
+            launch_fluid_prep_f64(psi, wa, g->fl.rho_floor, g->fl.floor_mode, g->cells, g->stream));
+  if ((st = fftn_f64(g, wa, -1)) != SN_OK) return st;
+  SN_LAUNCH(g, K_F64_EW, ew, launch_lap_mult_f64(wa, g->n, g->ndim, k2, inv_n, g->stream));
+  if ((st = fftn_f64(g, wa, +1)) != SN_OK) return st;
+  SN_LAUNCH(g, K_F64_EW, ew,
+            launch_fluid_source_f64(psi, wa, w, nmc ? g->prof64[0] : nullptr,
+                                    nmc ? g->prof64[1] : nullptr, g->cells, g->stream));
+  if ((st = fftn_f64(g, w, -1)) != SN_OK) return st;
+  SN_LAUNCH(g, K_F64_EW, ew, launch_green_f64(w, g->n, g->ndim, k2, -inv_n, 0.0, 1.0, g->stream));
+  return fftn_f64(g, w, +1);
+}
+
+sn_status ensure_fluid_scratch(sn_grid g) {
   sn_status st = ensure_f64_scratch(g);
   if (st != SN_OK) return st;
   if (!g->w64c) {
     cudaError_t e = dalloc(g, &g->w64c, (size_t)g->cells);
     if (e != cudaSuccess) return cuda_fail(g, e, "cudaMalloc(fluid scratch)");
   }
+  return SN_OK;
+}
+
+sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
+  sn_status st = ensure_fluid_scratch(g);
+  if (st != SN_OK) return st;
   double2* psi = reinterpret_cast<double2*>(g->psi);
   double2* w = g->w64b;   // source -> phi_N
   double2* wa = g->w64c;  // rho + i sqrt rho -> lap rho + i lap sqrt rho
-  const double* k2[3] = {g->k2_64[0], g->k2_64[1], g->k2_64[2]};
-  const double inv_n = 1.0 / (double)g->cells;
   const bool nmc = g->fl.model == SN_GRAVITY_NMC;
   FluidPhase fp{};
   fp.nu = g->fl.nu;
@@ -693,23 +719,11 @@ sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
   fp.n_poly = g->fl.n_poly;
   fp.cp = g->fl.n_poly == 1.0 ? 0.0 : g->fl.n_poly * g->fl.w / (g->fl.n_poly - 1.0);
   fp.rho_floor = g->fl.rho_floor;
-  const double ew = 32.0 * g->cells;
+  fp.floor_mode = g->fl.floor_mode;
   for (int s = 0; s < nsteps; ++s) {
     if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
-    SN_LAUNCH(g, K_F64_EW, 32.0 * g->cells,
-              launch_fluid_prep_f64(psi, wa, fp.rho_floor, g->cells, g->stream));
-    // lap rho (Eq. 15) and lap sqrt rho (Bohm) in one FFT pair
-    if ((st = fftn_f64(g, wa, -1)) != SN_OK) return st;
-    SN_LAUNCH(g, K_F64_EW, ew, launch_lap_mult_f64(wa, g->n, g->ndim, k2, inv_n, g->stream));
-    if ((st = fftn_f64(g, wa, +1)) != SN_OK) return st;
-    // Eq. 15: source, inverse Laplacian
-    SN_LAUNCH(g, K_F64_EW, ew,
-              launch_fluid_source_f64(psi, wa, w, nmc ? g->prof64[0] : nullptr,
-                                      nmc ? g->prof64[1] : nullptr, g->cells, g->stream));
-    if ((st = fftn_f64(g, w, -1)) != SN_OK) return st;
-    SN_LAUNCH(g, K_F64_EW, ew,
-              launch_green_f64(w, g->n, g->ndim, k2, -inv_n, 0.0, 1.0, g->stream));
-    if ((st = fftn_f64(g, w, +1)) != SN_OK) return st;
+    // lap rho (Eq. 15) and lap sqrt rho (Bohm) in one FFT pair, then phi_N
+    if ((st = fluid_fields(g, psi, wa, w)) != SN_OK) return st;
     SN_LAUNCH(g, K_F64_EW, (nmc ? 56.0 : 48.0) * g->cells,
               launch_fluid_phase_f64(psi, w, wa, nmc ? g->prof64[2] : nullptr, fp, g->cells,
                                      g->stream));
@@ -908,6 +922,8 @@ sn_status sn_set_fluid(sn_grid g, const sn_fluid* f) {
   if (!(f->nu > 0.0) || !std::isfinite(f->nu) || !std::isfinite(f->w) ||
       !std::isfinite(f->n_poly) || !(f->rho_floor > 0.0) || !std::isfinite(f->rho_floor))
     return fail(g, SN_EINVAL, "sn_set_fluid: nu and rho_floor must be finite and > 0, w and n finite");
+  if (f->floor_mode != SN_FLOOR_MAX && f->floor_mode != SN_FLOOR_SMOOTH)
+    return fail(g, SN_EINVAL, "sn_set_fluid: floor_mode must be SN_FLOOR_MAX or SN_FLOOR_SMOOTH");
   if (f->model != SN_GRAVITY_GR && f->model != SN_GRAVITY_NMC)
     return fail(g, SN_EINVAL, "sn_set_fluid: model must be SN_GRAVITY_GR or SN_GRAVITY_NMC");
   if (f->model == SN_GRAVITY_NMC && (!(f->lambda > 0.0) || !std::isfinite(f->lambda) ||
@@ -1124,12 +1140,38 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
     out->centroid[a] = g->L[a] / (2.0 * kPi) * std::atan2(q[Q_SX0 + 2 * a3], q[Q_CX0 + 2 * a3]);
   }
   out->e_kin = -g->kp.coeff_lap * dV * ek;
-  out->e_pot = g->fluid ? 0.0 : 0.5 * dV / N * q[Q_EPOT] + dV * q[Q_VEXT];
-  out->e_nl = g->fluid ? 0.0 : 0.5 * g->kp.g_local * dV * q[Q_RHO2];
-  out->e_total = out->e_kin + out->e_pot + out->e_nl;
+  out->e_pot = 0.5 * dV / N * q[Q_EPOT] + dV * q[Q_VEXT];
+  out->e_nl = 0.5 * g->kp.g_local * dV * q[Q_RHO2];
   out->step = g->step;
   for (int i = 0; i < Q_NUM; ++i)
     if (!std::isfinite(q[i])) return fail(g, SN_ENONFINITE, "sn_observables: state is not finite");
+  if (g->fluid) {
+    // Eq. 16 in the solver's form i psi_t = -(nu/2) lap psi + (U / nu) psi: the
+    // energies of U / nu, e_pot = (1/2 int phi_N rho + int phi_C rho) / nu and
+    // e_nl = (-(nu^2/2) int |grad a|^2 + int eps(rho)) / nu with a = sqrt(rho)
+    // (int |grad a|^2 = -int a lap a on the periodic box)
+    if ((st = ensure_fluid_scratch(g)) != SN_OK) return st;
+    const double2* psi64 = reinterpret_cast<const double2*>(psi_now);
+    if ((st = fluid_fields(g, psi64, g->w64c, g->w64b)) != SN_OK) return st;
+    e = cudaMemsetAsync(g->partials, 0, sizeof(double) * kObsBlocks * Q_NUM, g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemsetAsync");
+    const bool nmc = g->fl.model == SN_GRAVITY_NMC;
+    SN_LAUNCH(g, K_OBS, 48.0 * g->cells,
+              launch_obs_fluid(psi64, g->w64b, g->w64c, nmc ? g->prof64[2] : nullptr, g->fl.w,
+                               g->fl.n_poly, g->fl.rho_floor, g->fl.floor_mode, g->cells,
+                               g->partials, g->stream));
+    SN_LAUNCH(g, K_OBS, 0.0, launch_obs_finish(g->partials, 4, g->obs_out, g->stream));
+    double f[Q_NUM];
+    e = cudaMemcpyAsync(f, g->obs_out, sizeof(f), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "sn_observables (fluid energies)");
+    const double nu = g->fl.nu;
+    out->e_pot = dV * (0.5 * f[0] + f[1]) / nu;
+    out->e_nl = dV * (0.5 * nu * nu * f[3] + f[2]) / nu;
+    for (int i = 0; i < 4; ++i)
+      if (!std::isfinite(f[i])) return fail(g, SN_ENONFINITE, "sn_observables: state is not finite");
+  }
+  out->e_total = out->e_kin + out->e_pot + out->e_nl;
   return SN_OK;
 }
 

@@ -149,9 +149,10 @@ struct FluidPhase {
   double nu, h_over_nu;  // psi <- psi exp(-i U h / nu)
   double w, n_poly, cp;  // V_p = w ln rho (n = 1) or cp rho^(n-1), cp = n w / (n - 1)
   double rho_floor;      // floor of rho under sqrt and ln
+  int floor_mode;        // SN_FLOOR_MAX: max(rho, floor); SN_FLOOR_SMOOTH: rho + floor
 };
-cudaError_t launch_fluid_prep_f64(const double2* psi, double2* wa, double floor, long long cells,
-                                  cudaStream_t s);
+cudaError_t launch_fluid_prep_f64(const double2* psi, double2* wa, double floor, int floor_mode,
+                                  long long cells, cudaStream_t s);
 cudaError_t launch_lap_mult_f64(double2* w, const int* n, int ndim, const double* const* k2,
                                 double scale, cudaStream_t s);
 cudaError_t launch_fluid_source_f64(const double2* psi, const double2* wlap, double2* w,
@@ -180,6 +181,12 @@ cudaError_t launch_obs_green(const double2* rhohat, const int* n, int ndim,
                              const double* const* k2, double cN, double cY, double mu2,
                              double* partials, cudaStream_t s);
 cudaError_t launch_obs_finish(const double* partials, int nq, double* out, cudaStream_t s);
+// Fluid energy sums (Eq. 16) into partials [kObsBlocks][Q_NUM] at q = 0..3 (zeroed
+// first): rho phi_N (Re wphi), rho phi_C (phi_c may be NULL), eps(rho), a lap(a)
+// (Im wlap = lap a, a = sqrt(max(rho, floor)))
+cudaError_t launch_obs_fluid(const double2* psi, const double2* wphi, const double2* wlap,
+                             const double* phi_c, double w, double n_poly, double floor,
+                             int floor_mode, long long cells, double* partials, cudaStream_t s);
 
 // ---- BF16 tensor-core GEMM (FNO surrogate) -------------------------------
 // C[z] = alpha * A[z] B[z] + beta * C[z]; element (m,k) of A[z] at

@@ -20,6 +20,7 @@ LIB_PATH = os.environ.get("SN_LIB_PATH") or os.path.join(_HERE, "libsn.so")
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 SN_ENGINE_FP32, SN_ENGINE_TC16 = 0, 1
 SN_STAGING_TMA, SN_STAGING_REGISTERS = 0, 1
+SN_FLOOR_MAX, SN_FLOOR_SMOOTH = 0, 1
 SN_C64, SN_C128 = 0, 1
 SN_KERNEL_NMC, SN_KERNEL_POISSON = 0, 1
 _STATUS = {0: "SN_OK", -1: "SN_EINVAL", -2: "SN_ENOMEM", -3: "SN_ECUDA", -4: "SN_ETIMEOUT",
@@ -52,7 +53,7 @@ SN_SCHED_VALUES = 6 * SN_SCHED_KINDS  # CTAs per SM, then the staging, of each k
 class SnFluid(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("w", ctypes.c_double), ("n_poly", ctypes.c_double),
                 ("model", ctypes.c_int), ("lambda_", ctypes.c_double), ("M", ctypes.c_double),
-                ("rho_floor", ctypes.c_double)]
+                ("rho_floor", ctypes.c_double), ("floor_mode", ctypes.c_int)]
 
 
 class SnObs(ctypes.Structure):
@@ -135,6 +136,9 @@ _SIGNATURES = [
                                    ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p]),
     ("sn_fno_unpack", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_longlong, ctypes.c_void_p]),
+    ("sn_fno_pack2", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+                                    ctypes.c_void_p]),
     ("sn_mass_c64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
                                    ctypes.c_void_p, ctypes.c_void_p]),
     ("sn_test_gemm_bf16", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_longlong] * 3
@@ -469,6 +473,20 @@ def sn_fno_pack(psi, feats, X, stream=None):
                                    ctypes.c_void_p(stream) if stream else None))
 
 
+def sn_fno_pack2(psi_a, psi_c, feats, X, stream=None):
+    """psi_a, psi_c: (B, s, s) complex64 CUDA; feats: (B, nfeat) float32 CUDA;
+    X: (B, 4+nfeat, s, s) = (re a, im a, re c, im c, feats...)."""
+    import torch
+    B, cells = psi_a.shape[0], psi_a[0].numel()
+    nfeat = feats.shape[1] if feats is not None else 0
+    ap = _cuda_tensor(psi_a, torch.complex64, "psi_a")
+    cp = _cuda_tensor(psi_c, torch.complex64, "psi_c", B * cells)
+    fp = _cuda_tensor(feats, torch.float32, "feats", B * nfeat) if feats is not None else None
+    xp = _cuda_tensor(X, torch.float32, "X", B * (4 + nfeat) * cells)
+    _check(None, lib().sn_fno_pack2(ap, cp, fp, nfeat, xp, B, cells,
+                                    ctypes.c_void_p(stream) if stream else None))
+
+
 def sn_fno_unpack(Y, psi, stream=None):
     """Y: (B, 2, s, s) float32 CUDA -> psi: (B, s, s) complex64 CUDA."""
     import torch
@@ -655,14 +673,14 @@ class Grid:
         return sn_observables(self.h)
 
     def set_fluid(self, nu=1.0, w=1.02, n_poly=1.0, model=SN_GRAVITY_NMC, lam=1.0, M=25.0,
-                  rho_floor=1e-12, off=False):
+                  rho_floor=1e-12, off=False, floor_mode=0):
         """Eq. 16 (self-gravitating fluid, GR or NMC) on a complex128 grid; off=True
         returns to Eqs. 1-2 (see sn_set_fluid in include/sn.h)."""
         if off:
             _check(self.h, lib().sn_set_fluid(self.h, None))
             return
         f = SnFluid(float(nu), float(w), float(n_poly), int(model), float(lam), float(M),
-                    float(rho_floor))
+                    float(rho_floor), int(floor_mode))
         _check(self.h, lib().sn_set_fluid(self.h, ctypes.byref(f)))
 
     def schedule(self) -> list:

@@ -8,6 +8,12 @@
 * Rollout: psi is advanced `stride` steps per network call; a prediction
   whose mass differs from its input's by more than `drift_tol` is replaced by
   `stride` solver steps (the solver is both the fallback and the reference).
+* Corrector form (coarse > 0): the network also sees a coarse solve of the
+  same horizon (`coarse` split steps of stride dt / coarse, from psi(t)) and
+  its head turns that coarse state instead of psi(t): it learns what the
+  coarse solve misses.  Input channels (re, im of the coarse state, re, im of
+  psi(t), features); the coarse solve without the network is the method it
+  is measured against.
 
 Device memory comes from torch tensors; every computation is a library call.
 Every call is queued on torch's current CUDA stream, which must be a
@@ -60,23 +66,43 @@ def _batch(torch, ws, stream):
     return b
 
 
-def generate_pairs(torch, ws, stride=50, nsnap=10, chunk=512, seed=0):
-    """X (N, 5, s, s), Y (N, 2, s, s) float32 CUDA tensors, N = len(ws) * nsnap, in a
-    seeded random order so that contiguous slices are shuffled minibatches."""
+def input_channels(coarse: int) -> int:
+    """Network input channels: (re, im) of psi and 3 features, plus the (re, im)
+    of the coarse solve in the corrector form."""
+    return 7 if coarse > 0 else 5
+
+
+def coarse_solve(torch, bc, psi, dt, coarse, out):
+    """out[i] = `coarse` split steps of dt from psi[i], on the batch bc (one
+    instance per state)."""
+    for i in range(psi.shape[0]):
+        bc.set_state(i, psi[i])
+    bc.step(dt, coarse)
+    for i in range(psi.shape[0]):
+        bc.get_state(i, out[i])
+
+
+def generate_pairs(torch, ws, stride=50, nsnap=10, chunk=512, seed=0, coarse=0):
+    """X (N, c_in, s, s), Y (N, 2, s, s) float32 CUDA tensors, N = len(ws) * nsnap, in a
+    seeded random order so that contiguous slices are shuffled minibatches.  With
+    coarse > 0, X holds the corrector's input (coarse solve, psi(t), features)."""
     stream = _stream(torch)
     s = ws[0].n[0]
     n = len(ws) * nsnap
+    cin = input_channels(coarse)
     perm = np.random.default_rng(seed).permutation(n)
-    X = torch.empty((n, 5, s, s), dtype=torch.float32, device="cuda")
+    X = torch.empty((n, cin, s, s), dtype=torch.float32, device="cuda")
     Y = torch.empty((n, 2, s, s), dtype=torch.float32, device="cuda")
     for c0 in range(0, len(ws), chunk):
         part = ws[c0:c0 + chunk]
         c = len(part)
         feat = torch.from_numpy(features(part)).cuda()
         b = _batch(torch, part, stream)
+        bc = _batch(torch, part, stream) if coarse > 0 else None
         cur = torch.empty((c, s, s), dtype=torch.complex64, device="cuda")
         nxt = torch.empty_like(cur)
-        xs = torch.empty((c, 5, s, s), dtype=torch.float32, device="cuda")
+        crs = torch.empty_like(cur) if coarse > 0 else None
+        xs = torch.empty((c, cin, s, s), dtype=torch.float32, device="cuda")
         ys = torch.empty((c, 2, s, s), dtype=torch.float32, device="cuda")
         for k in range(nsnap):
             for i in range(c):
@@ -84,13 +110,19 @@ def generate_pairs(torch, ws, stride=50, nsnap=10, chunk=512, seed=0):
             b.step(part[0].dt, stride)
             for i in range(c):
                 b.get_state(i, nxt[i])
-            sn.sn_fno_pack(cur, feat, xs, stream)
+            if coarse > 0:
+                coarse_solve(torch, bc, cur, part[0].dt * stride / coarse, coarse, crs)
+                sn.sn_fno_pack2(crs, cur, feat, xs, stream)
+            else:
+                sn.sn_fno_pack(cur, feat, xs, stream)
             sn.sn_fno_pack(nxt, None, ys, stream)
             for i in range(c):
                 j = int(perm[(c0 + i) * nsnap + k])
                 X[j].copy_(xs[i])
                 Y[j].copy_(ys[i])
         b.close()
+        if bc is not None:
+            bc.close()
     torch.cuda.synchronize()
     return X, Y
 
@@ -150,10 +182,13 @@ def _masses(torch, psi, stream=None):
     return out
 
 
-def rollout(torch, net, ws, rounds=20, stride=50, drift_tol=1e-3, perturb=None):
+def rollout(torch, net, ws, rounds=20, stride=50, drift_tol=1e-3, perturb=None, coarse=0):
     """Advance every instance `rounds` x `stride` steps by the surrogate with
     fallback, and by the solver alone; compare.  `perturb(r, psi)` may alter
-    the predictions (used to exercise the fallback)."""
+    the predictions (used to exercise the fallback).  With coarse > 0 every
+    network call first takes the coarse solve of its horizon (timed with it),
+    and the coarse solves alone are rolled out too, as the method without the
+    network."""
     stream = _stream(torch)
     s = ws[0].n[0]
     n = len(ws)
@@ -175,19 +210,41 @@ def rollout(torch, net, ws, rounds=20, stride=50, drift_tol=1e-3, perturb=None):
     b.step(dt, rounds * stride)
     b.sync()
     t_solver = time.perf_counter() - t0
+    dt_c = dt * stride / coarse if coarse > 0 else 0.0
+    bc = _batch(torch, ws, stream) if coarse > 0 else None
+    # the coarse solves alone (the method without the network), and their errors
+    coarse_errs = None
+    if coarse > 0:
+        crs_only = psi0.clone()
+        tmp = torch.empty_like(crs_only)
+        first_err = None
+        for r in range(rounds):
+            coarse_solve(torch, bc, crs_only, dt_c, coarse, tmp)
+            crs_only, tmp = tmp, crs_only
+            if r == 0:
+                first_err = _rel_errors(crs_only, ref[0])
+        coarse_errs = {"coarse_only_first_call_rel_l2_mean": float(np.mean(first_err)),
+                       "coarse_only_final_rel_l2_mean": float(np.mean(_rel_errors(crs_only, ref[rounds - 1])))}
     # surrogate with fallback
     B = net.batch_max
-    X = torch.empty((B, 5, s, s), dtype=torch.float32, device="cuda")
+    X = torch.empty((B, input_channels(coarse), s, s), dtype=torch.float32, device="cuda")
     Yb = torch.empty((B, 2, s, s), dtype=torch.float32, device="cuda")
     psi = psi0.clone()
     nxt = torch.empty_like(psi)
+    crs = torch.empty_like(psi) if coarse > 0 else None
     errors, fallbacks = [], []
+    first_call = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for r in range(rounds):
+        if coarse > 0:
+            coarse_solve(torch, bc, psi, dt_c, coarse, crs)
         for c0 in range(0, n, B):
             c = min(B, n - c0)
-            sn.sn_fno_pack(psi[c0:c0 + c], feat[c0:c0 + c], X, stream)
+            if coarse > 0:
+                sn.sn_fno_pack2(crs[c0:c0 + c], psi[c0:c0 + c], feat[c0:c0 + c], X, stream)
+            else:
+                sn.sn_fno_pack(psi[c0:c0 + c], feat[c0:c0 + c], X, stream)
             net.forward(X[:c], Yb[:c])
             sn.sn_fno_unpack(Yb[:c], nxt[c0:c0 + c], stream)
         if perturb is not None:
@@ -207,22 +264,64 @@ def rollout(torch, net, ws, rounds=20, stride=50, drift_tol=1e-3, perturb=None):
             fb.close()
         psi, nxt = nxt, psi
         fallbacks.append(len(bad))
+        if r == 0:
+            first_call = psi.clone()
     torch.cuda.synchronize()
     t_sur = time.perf_counter() - t0
+    first_errs = _rel_errors(first_call, ref[0])
+    if bc is not None:
+        bc.close()
     # relative L2 error of the final surrogate state against the solver's (host, FP64)
     fin = psi.cpu().numpy().astype(np.complex128)
     want = ref[rounds - 1].cpu().numpy().astype(np.complex128)
     errs = [float(np.linalg.norm(fin[i] - want[i]) / np.linalg.norm(want[i])) for i in range(n)]
     b.close()
-    return {"instances": n, "rounds": rounds, "stride": stride, "t_surrogate_s": t_sur,
-            "t_solver_s": t_solver, "fallbacks_per_round": fallbacks,
-            "fallback_fraction": float(sum(fallbacks)) / (rounds * n),
-            "final_rel_l2_mean": float(np.mean(errs)), "final_rel_l2_max": float(np.max(errs))}
+    res = {"instances": n, "rounds": rounds, "stride": stride, "t_surrogate_s": t_sur,
+           "t_solver_s": t_solver, "fallbacks_per_round": fallbacks,
+           "fallback_fraction": float(sum(fallbacks)) / (rounds * n),
+           "first_call_rel_l2_mean": float(np.mean(first_errs)),
+           "final_rel_l2_mean": float(np.mean(errs)), "final_rel_l2_max": float(np.max(errs))}
+    if coarse_errs is not None:
+        res.update(coarse_errs)
+        res["coarse_steps"] = coarse
+    return res
+
+
+def _rel_errors(a, b):
+    """Relative L2 distance of each state of a (B, s, s) from b's (host FP64)."""
+    x = a.cpu().numpy().astype(np.complex128).reshape(a.shape[0], -1)
+    y = b.cpu().numpy().astype(np.complex128).reshape(b.shape[0], -1)
+    return np.linalg.norm(x - y, axis=1) / np.linalg.norm(y, axis=1)
+
+
+def plain_fp64_time(torch, ws, steps, sample=4):
+    """Seconds of `steps` plain FP64 GPU steps (one complex128 grid per instance,
+    one after another), estimated from the first `sample` instances."""
+    stream = _stream(torch)
+    grids = []
+    for w in ws[:sample]:
+        g = sn.Grid(w.n, w.L, "c128", stream=stream)
+        g.set_kernel(**kernel_kw(w.kernel))
+        g.set_state(w.psi0(np.complex128))
+        g.step(w.dt, 2)
+        grids.append(g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in grids:
+        g.step(ws[0].dt, steps)
+    for g in grids:
+        g.sync()
+    t = (time.perf_counter() - t0) * len(ws) / len(grids)
+    for g in grids:
+        g.close()
+    return t
 
 
 def one_step_errors(torch, net, X, Y, batch):
-    """Mean relative L2 error of single predictions and of the persistence guess
-    psi(t + stride dt) ~ psi(t) over the pairs (X, Y) (host FP64 for the latter)."""
+    """Mean relative L2 error of single predictions and of the state the head
+    turns (channels 0, 1 of X) taken as the prediction, over the pairs (X, Y)
+    (host FP64 for the latter): the persistence guess psi(t + stride dt) ~ psi(t),
+    or in the corrector form the coarse solve alone."""
     out = torch.empty((batch, 2, X.shape[2], X.shape[3]), dtype=torch.float32, device="cuda")
     e_net, e_id = [], []
     for k in range(X.shape[0] // batch):
@@ -269,6 +368,8 @@ def main(argv=None):
     ap.add_argument("--proj", type=int, default=128)
     ap.add_argument("--drift-tol", type=float, default=1e-3)
     ap.add_argument("--init-seed", type=int, default=0)
+    ap.add_argument("--coarse", type=int, default=10,
+                    help="coarse split steps per call of the corrector form (0: the plain map)")
     a = ap.parse_args(argv)
     if int(os.environ.get("WORLD_SIZE", "1")) > 1:
         import torch.distributed as dist
@@ -280,14 +381,15 @@ def main(argv=None):
     torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
     X, Y = generate_pairs(torch, instances(a.train, 5000, a.s)[rank::world], a.stride, a.nsnap,
-                          seed=1)
+                          seed=1, coarse=a.coarse)
     test_ws = instances(a.heldout, 9000, a.s) if rank == 0 else []
-    Xt, Yt = generate_pairs(torch, test_ws, a.stride, 2, seed=2) if rank == 0 else (None, None)
+    Xt, Yt = (generate_pairs(torch, test_ws, a.stride, 2, seed=2, coarse=a.coarse)
+              if rank == 0 else (None, None))
     t_gen = time.perf_counter() - t0
     log(f"pairs: {X.shape[0]} train per rank x {world}, "
         f"{Xt.shape[0] if Xt is not None else 0} held out ({t_gen:.0f} s)")
-    net = sn.Fno(s=a.s, c_in=5, width=a.width, modes=a.modes, layers=a.layers, proj=a.proj,
-                 batch_max=a.batch, stream=stream.cuda_stream)
+    net = sn.Fno(s=a.s, c_in=input_channels(a.coarse), width=a.width, modes=a.modes,
+                 layers=a.layers, proj=a.proj, batch_max=a.batch, stream=stream.cuda_stream)
     p0 = _init_params(a)
     if p0.size != net.nparams:
         raise RuntimeError("parameter layout mismatch")
@@ -304,13 +406,18 @@ def main(argv=None):
         net.close()
         return
     e_net, e_id = one_step_errors(torch, net, Xt, Yt, a.batch)
-    res = rollout(torch, net, test_ws, a.rounds, a.stride, a.drift_tol)
+    res = rollout(torch, net, test_ws, a.rounds, a.stride, a.drift_tol, coarse=a.coarse)
+    t64 = plain_fp64_time(torch, test_ws, a.rounds * a.stride)
     res.update({"grid": a.s, "train_pairs": a.train * a.nsnap, "train_iters": len(losses),
                 "train_samples_per_s": samples_all / t_train_max, "train_s": t_train_max,
                 "loss_first100": float(np.mean(losses[:100])),
                 "loss_last100": float(np.mean(losses[-100:])),
-                "heldout_rel_l2_net": e_net, "heldout_rel_l2_persistence": e_id,
-                "heldout_rel_l2_zero": 1.0, "params": net.nparams})
+                "heldout_rel_l2_net": e_net,
+                ("heldout_rel_l2_coarse" if a.coarse > 0 else "heldout_rel_l2_persistence"): e_id,
+                "heldout_rel_l2_zero": 1.0, "params": net.nparams,
+                "t_plain_fp64_gpu_s": t64,
+                "speedup_vs_plain_fp64_gpu": t64 / res["t_surrogate_s"],
+                "speedup_vs_batched_fp32_solver": res["t_solver_s"] / res["t_surrogate_s"]})
     res.pop("fallbacks_per_round", None)
     if world > 1:
         res["data_parallel_ranks"] = world
@@ -326,7 +433,8 @@ def _init_params(a):
     by 1/(width^2))."""
     rng = np.random.default_rng(a.init_seed)
     w, m2, m, P = a.width, 2 * a.modes, a.modes, a.proj
-    parts = [rng.uniform(-1, 1, (w, 5)) / np.sqrt(5), np.zeros(w)]
+    cin = input_channels(a.coarse)
+    parts = [rng.uniform(-1, 1, (w, cin)) / np.sqrt(cin), np.zeros(w)]
     for _ in range(a.layers):
         parts += [rng.uniform(0, 1, (m2, m, w, w, 2)) / (w * w),
                   rng.uniform(-1, 1, (w, w)) / np.sqrt(w), np.zeros(w)]
