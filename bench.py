@@ -488,12 +488,13 @@ def run_fields(sn, torch, stream, peak, m=2, n=256, L=80.0, steps=500, autotune=
 FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 (non-tensor) nominal rate; no measured FP64 peak
 
 
-def run_fluid(sn, torch, stream, n=512, L=40.0, steps=400, dt=1e-2):
+def run_fluid(sn, torch, stream, n=256, L=40.0, steps=2000, dt=5e-4):
     """The self-gravitating fluid of Eq. 16 (Figs. 3-4 parameters: M0 = 25, nu = 1,
     w = 1.02, n = 1, lambda = 1) on an n^2 complex128 grid: GR and NMC from the same
-    Gaussian, both timed.  The plain FP64 path: eight full complex FFTs per step
-    (kinetic 4, both Laplacians of rho + i sqrt(rho) 2, Eq. 15 2) at 5 N log2 N flops
-    each."""
+    Gaussian to t = 1, both timed.  The step resolves the kinetic and Bohm rotation of
+    the highest wavenumber (k_max^2 dt / 2 = 0.2 rad at 256^2).  The plain FP64 path:
+    eight full complex FFTs per step (kinetic 4, both Laplacians of rho + i sqrt(rho) 2,
+    Eq. 15 2) at 5 N log2 N flops each."""
     x = -0.5 * L + np.arange(n) * (L / n)
     X, Y = np.meshgrid(x, x, indexing="ij")
     r2 = X * X + Y * Y
@@ -512,7 +513,8 @@ def run_fluid(sn, torch, stream, n=512, L=40.0, steps=400, dt=1e-2):
         g = sn.Grid((n, n), (L, L), "c128", stream=stream.cuda_stream)
         g.set_fluid(nu=1.0, w=1.02, n_poly=1.0, model=model, lam=1.0, M=M0, rho_floor=1e-12)
         g.set_state(psi0)
-        m0 = g.observables()["mass"]
+        o0 = g.observables()
+        m0 = o0["mass"]
         g.step(dt, 3)
         g.set_state(psi0)
         torch.cuda.synchronize()
@@ -523,12 +525,15 @@ def run_fluid(sn, torch, stream, n=512, L=40.0, steps=400, dt=1e-2):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
         final = g.get_state()
-        drift = g.observables()["mass"] / m0 - 1.0
+        o1 = g.observables()
+        drift = o1["mass"] / m0 - 1.0
         g.close()
         ffts = 8
         flops = ffts * 5.0 * n * n * np.log2(n * n)
         out[name] = {"value": n * n * steps / t, "unit": "cell-steps/s",
                      "ms_per_step": 1e3 * t / steps, "mass_drift": drift, "final": summary(final),
+                     "energy": {"e_kin": o1["e_kin"], "e_pot": o1["e_pot"], "e_nl": o1["e_nl"],
+                                "e_total_change": o1["e_total"] - o0["e_total"]},
                      "roofline": {"bound": "alu", "achieved": flops * steps / t / 1e12,
                                   "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                                   "frac": flops * steps / t / 1e12 / FP64_NOMINAL_TFLOPS,

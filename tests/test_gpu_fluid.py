@@ -159,3 +159,40 @@ def test_fluid_energies_match_oracle(name, shape, L, model, p):
     scale = max(abs(ref[k]) for k in ("e_kin", "e_pot", "e_nl"))
     for k in ("e_kin", "e_pot", "e_nl", "e_total"):
         assert abs(got[k] - ref[k]) <= 1e-10 * scale, (k, got[k], ref[k])
+
+
+def test_nmc_concentrates_the_centre_faster_than_gr():
+    """The qualitative result of Figs. 3-4's run (M0 = 25, nu = 1, w = 1.02, n = 1,
+    lambda = 1, a Gaussian of sigma = 3 at rest on a 40-wide box), in the regime where the
+    split step resolves the kinetic and Bohm rotation of the highest wavenumber
+    (k_max^2 h / 2 <= 1/4): at t = 1 the non-minimal coupling holds a central density
+    several times that of General Relativity and a larger mass fraction within L/8, with
+    the same sign under 2x changes of the time step, of the grid (h scaled as dx^2) and of
+    the density floor (max form and smooth form)."""
+    L, sigma, M0 = 40.0, 3.0, 25.0
+    runs = [(256, 5e-4, 1e-12, sn.SN_FLOOR_MAX), (256, 1e-3, 1e-12, sn.SN_FLOOR_MAX),
+            (256, 5e-4, 1e-10, sn.SN_FLOOR_MAX), (256, 5e-4, 1e-6, sn.SN_FLOOR_SMOOTH),
+            (512, 2.5e-4, 1e-12, sn.SN_FLOOR_MAX)]
+    for n, dt, floor, mode in runs:
+        x = W.coords(n, L)
+        X, Y = np.meshgrid(x, x, indexing="ij")
+        r2 = X * X + Y * Y
+        psi0 = np.sqrt(M0 / (2 * math.pi * sigma ** 2) * np.exp(-r2 / (2 * sigma ** 2))) + 0j
+        summary = {}
+        for name, model in (("GR", sn.SN_GRAVITY_GR), ("NMC", sn.SN_GRAVITY_NMC)):
+            g = sn.Grid((n, n), (L, L), "c128")
+            try:
+                g.set_fluid(nu=1.0, w=1.02, n_poly=1.0, model=model, lam=1.0, M=M0,
+                            rho_floor=floor, floor_mode=mode)
+                g.set_state(psi0)
+                g.step(dt, int(round(1.0 / dt)))
+                rho = np.abs(g.get_state()) ** 2
+            finally:
+                g.close()
+            inner = float(rho[np.sqrt(r2) <= L / 8].sum() * (L / n) ** 2 / M0)
+            summary[name] = (float(rho[n // 2, n // 2]), inner)
+        print(f"fluid n={n} dt={dt:g} floor={floor:g} mode={mode}: centre GR {summary['GR'][0]:.3f} "
+              f"NMC {summary['NMC'][0]:.3f}, inner mass GR {summary['GR'][1]:.4f} "
+              f"NMC {summary['NMC'][1]:.4f}")
+        assert summary["NMC"][0] > 2.0 * summary["GR"][0]
+        assert summary["NMC"][1] > summary["GR"][1]
