@@ -286,8 +286,13 @@ sn_status sn_set_engine(sn_grid g, int engine);
  *     (sn_sync, sn_get_state to host, sn_observables) return SN_ETIMEOUT.
  *   SN_STAGING_REGISTERS: every thread loads its elements of the next tile
  *     into registers while it transforms the current one.
+ *   SN_STAGING_RESIDENT: on a square 2D grid of 64^2 or 128^2 cells (one
+ *     field, FP32 engine, no V_ext) the whole state stays in one CTA's shared
+ *     memory for all steps of an sn_step call: one launch per call, no HBM
+ *     traffic between the passes (one SM; pays off where the tiled passes are
+ *     launch-bound).  Other grids take SN_STAGING_TMA.  Same bits.
  * Errors: SN_EINVAL (NULL grid, unknown mode). */
-typedef enum { SN_STAGING_TMA = 0, SN_STAGING_REGISTERS = 1 } sn_staging;
+typedef enum { SN_STAGING_TMA = 0, SN_STAGING_REGISTERS = 1, SN_STAGING_RESIDENT = 2 } sn_staging;
 sn_status sn_set_staging(sn_grid g, int mode);
 
 /* Test hook: in-place unnormalised DFTs, sign -1 (exp(-i ...)) or +1, of

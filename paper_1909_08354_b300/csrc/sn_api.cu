@@ -23,7 +23,7 @@ thread_local std::string g_tls_error = "";
 
 const char* const kKindNames[K_NUM_KINDS] = {
     "psi_pass", "psi_pass_nphase", "psi_pass_density", "rho_fwd", "rho_green", "rho_inv",
-    "f64_fft", "f64_elementwise", "observables"};
+    "f64_fft", "f64_elementwise", "observables", "resident_2d"};
 
 int log2i(int n) {
   int l = 0;
@@ -344,7 +344,8 @@ LineGeom psi_geom(sn_grid g, int a) {
 // TMA-staged kernels: its schedule entry's staging, else the grid's.
 bool use_tma(sn_grid g, int kind, int axis, int N, bool strided, long long outer,
              long long inner) {
-  const int st = g->sched_st[kind][axis] >= 0 ? g->sched_st[kind][axis] : g->staging;
+  int st = g->sched_st[kind][axis] >= 0 ? g->sched_st[kind][axis] : g->staging;
+  if (st == SN_STAGING_RESIDENT) st = SN_STAGING_TMA;  // a grid the resident kernel does not take
   return st == SN_STAGING_TMA && g->engine == SN_ENGINE_FP32 &&
          line_pass_tma_supported(N, strided, outer, inner);
 }
@@ -545,10 +546,46 @@ sn_status round_f32(sn_grid g, void* base, bool odd, bool nphase, int full, bool
   return SN_OK;
 }
 
+// Whether a grid's steps run plane-resident (SN_STAGING_RESIDENT on a square
+// 64^2 or 128^2 grid of one field on the FP32 engine, without V_ext).
+bool use_resident(sn_grid g) {
+  return g->staging == SN_STAGING_RESIDENT && g->ndim == 2 && g->engine == SN_ENGINE_FP32 &&
+         g->fields == 1 && !g->has_vext && resident_2d_supported(g->n[0], g->n[1]);
+}
+
 // n merged steps: round r applies the open step's Nl(h) (none on a closed
 // state), Kin(h) (Kin(h/2) on a closed state) and the density for the next
 // Nl(h).  The merge is left open (see sn_grid_s::open).
 sn_status step_f32(sn_grid g, double dt, int nsteps) {
+  if (use_resident(g) && nsteps > 0) {
+    const GreenCoeffs gc = green_coeffs(g->kp);
+    const double scale = dt / (double)g->cells;
+    Resident2dArgs ra{};
+    ra.psi = reinterpret_cast<float2*>(g->psi);
+    ra.rh = g->rhohat;
+    ra.tw = g->tw32[log2i(g->n[0])];
+    for (int a = 0; a < 2; ++a) {
+      ra.lift[2 * a] = g->lift32[a][0];
+      ra.lift[2 * a + 1] = g->lift32[a][1];
+      ra.k2[a] = g->k2_32[a];
+    }
+    ra.cN = (float)(gc.cN * scale);
+    ra.cY = (float)(gc.cY * scale);
+    ra.mu2 = (float)gc.mu2;
+    ra.gh = (float)(g->kp.g_local * dt);
+    ra.rounds = nsteps;
+    ra.nphase = g->open ? 1 : 0;
+    ra.full = g->open ? 1 : 0;
+    ra.odd = g->next_odd ? 1 : 0;
+    g->cur_axis = 0;
+    SN_LAUNCH(g, K_RESIDENT, 16.0 * g->cells + 16.0 * (g->n[0] / 2 + 1) * g->n[1],
+              launch_resident_2d(g->n[0], ra, g->stream));
+    if (nsteps & 1) g->next_odd = !g->next_odd;
+    g->open = true;
+    g->open_dt = dt;
+    g->closed_valid = false;
+    return SN_OK;
+  }
   for (int r = 0; r < nsteps; ++r) {
     const bool cont = g->open;
     sn_status st = round_f32(g, g->psi, g->next_odd, cont, cont ? 1 : 0, true, dt);
@@ -1201,7 +1238,7 @@ sn_status sn_set_engine(sn_grid g, int engine) {
 
 sn_status sn_set_staging(sn_grid g, int mode) {
   if (!g) return fail(nullptr, SN_EINVAL, "sn_set_staging: grid is NULL");
-  if (mode != SN_STAGING_TMA && mode != SN_STAGING_REGISTERS)
+  if (mode != SN_STAGING_TMA && mode != SN_STAGING_REGISTERS && mode != SN_STAGING_RESIDENT)
     return fail(g, SN_EINVAL, "sn_set_staging: unknown mode");
   g->staging = mode;
   return SN_OK;

@@ -24,6 +24,7 @@ enum PassKind {
   K_F64_FFT,        // plain FP64 step: one axis FFT
   K_F64_EW,         // plain FP64 step: one elementwise kernel
   K_OBS,            // observables kernels
+  K_RESIDENT,       // plane-resident 2D steps (all rounds of a call in one launch)
   K_NUM_KINDS
 };
 
@@ -109,6 +110,23 @@ bool line_pass_tma_supported(int N, bool strided, long long outer, long long inn
 // cudaErrorNotSupported if !line_pass_tma_supported.
 cudaError_t launch_line_pass_tma(int N, bool strided, int op, const LinePassArgs& a,
                                  cudaStream_t s);
+// ---- plane-resident 2D steps (resident_2d.cu) -----------------------------------
+// Rounds of merged split steps of an N x N complex64 grid held in one CTA's
+// shared memory; the same arithmetic as the tiled passes, bit for bit.
+struct Resident2dArgs {
+  float2* psi;             // N x N state, read at the start and written at the end
+  float2* rh;              // half spectrum [N/2 + 1][N], likewise (the open merge's potential)
+  const float2* tw;        // twiddles of N (hi parts, then lo parts)
+  const float4* lift[4];   // kinetic shears [2 axis + full] (half step, full step)
+  const float* k2[2];      // k^2 per axis
+  float cN, cY, mu2;       // Green's multiplier (h / N folded in), as RhoPassArgs
+  float gh;                // g h
+  int rounds;              // rounds of this launch
+  int nphase, full, odd;   // the first round: nonlinear phase, full kinetic step, axis order
+};
+bool resident_2d_supported(int ny, int nx);
+cudaError_t launch_resident_2d(int n, const Resident2dArgs& a, cudaStream_t s);
+
 // The potential pass (PSI_NPHASE) and the density pass (PSI_DENSITY) of one
 // field on the FP32 engine, TMA-staged; cudaErrorNotSupported for geometries
 // or options it does not take (several fields, an accumulated density, the

@@ -11,8 +11,8 @@
 //   strided lines (half-warp = 16 lines at one position): [pos][line], the
 //     TMA tile's own layout, so the 16 lanes always hit 16 bank pairs;
 //   contiguous lines (half-warp = the T threads of 16 / T lines): [line][pos]
-//     with the low four bits of pos XOR-swizzled (swz below), chosen so that
-//     every write and read of the 2-stage Stockham exchange of 128- and
+//     with the low four bits of pos XOR-swizzled (xw below), chosen so that
+//     every write and read of the 2-stage Stockham exchange of 64-, 128- and
 //     256-point lines is served in the minimum two wavefronts per warp.
 #pragma once
 
@@ -126,6 +126,11 @@ __device__ __forceinline__ int xw(int l, int pos) {
     return l * N + (pos ^ ((pos >> 4) & 15));
   } else if constexpr (N == 128) {
     return l * N + (pos ^ ((pos >> 3) & 6) ^ ((pos >> 6) & 1) ^ ((l & 1) ? 9 : 0));
+  } else if constexpr (N == 64) {
+    // a half-warp holds 4 lines of 4 threads: the low bits take pos bits 4, 5
+    // and the line's two low bits
+    const int sw = ((pos >> 4) & 1) ^ (((pos >> 5) & 1) << 1) ^ ((l & 1) ? 5 : 0) ^ ((l & 2) ? 10 : 0);
+    return l * N + (pos ^ sw);
   } else {
     return l * N + pos;
   }

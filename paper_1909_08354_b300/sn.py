@@ -19,7 +19,7 @@ LIB_PATH = os.environ.get("SN_LIB_PATH") or os.path.join(_HERE, "libsn.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 SN_ENGINE_FP32, SN_ENGINE_TC16 = 0, 1
-SN_STAGING_TMA, SN_STAGING_REGISTERS = 0, 1
+SN_STAGING_TMA, SN_STAGING_REGISTERS, SN_STAGING_RESIDENT = 0, 1, 2
 SN_FLOOR_MAX, SN_FLOOR_SMOOTH = 0, 1
 SN_C64, SN_C128 = 0, 1
 SN_KERNEL_NMC, SN_KERNEL_POISSON = 0, 1

@@ -78,8 +78,8 @@ def test_schedule_constants_match_the_header():
     assert int(re.search(r"#define SN_SCHED_MAX_CTAS (\d+)", text).group(1)) == sn.SN_SCHED_MAX_CTAS
     m = re.search(r"#define SN_SCHED_VALUES \((\d+) \* SN_SCHED_KINDS\)", text)
     assert int(m.group(1)) * sn.SN_SCHED_KINDS == sn.SN_SCHED_VALUES
-    m = re.search(r"SN_STAGING_TMA = (\d+), SN_STAGING_REGISTERS = (\d+)", text)
-    assert (int(m.group(1)), int(m.group(2))) == (sn.SN_STAGING_TMA, sn.SN_STAGING_REGISTERS)
+    m = re.search(r"SN_STAGING_TMA = (\d+), SN_STAGING_REGISTERS = (\d+), SN_STAGING_RESIDENT = (\d+)", text)
+    assert tuple(map(int, m.groups())) == (sn.SN_STAGING_TMA, sn.SN_STAGING_REGISTERS, sn.SN_STAGING_RESIDENT)
     # the schedule kinds are the first kernel kinds, in order
     assert sn.sn_kind_names()[:sn.SN_SCHED_KINDS] == ["psi_pass", "psi_pass_nphase",
                                                       "psi_pass_density", "rho_fwd", "rho_green",
