@@ -295,6 +295,33 @@ sn_status sn_set_engine(sn_grid g, int engine);
 typedef enum { SN_STAGING_TMA = 0, SN_STAGING_REGISTERS = 1, SN_STAGING_RESIDENT = 2 } sn_staging;
 sn_status sn_set_staging(sn_grid g, int mode);
 
+/* Slab blocking of the 3D FP32 step (Sec. III; the merged Strang round of
+ * Eqs. 1-2).  Of the three psi passes of a round, the ones along y and x
+ * (array axes 1 and 2) stay within the planes of fixed z.  With planes > 0 the
+ * pair runs slab by slab over z, `planes` planes per slab: the second pass of
+ * the pair reads the slab the first one has just written while it is still
+ * in L2, instead of the whole state from HBM.  It applies to grids of one
+ * field on the FP32 engine whose pair of passes both take the TMA-staged
+ * kernels (128- or 256-point lines), with planes < n[0]; other grids ignore it.
+ * The arithmetic and the results are the same bit for bit; only the launches
+ * change (two per slab instead of two per round).  0 (the default) turns it
+ * off.  Errors: SN_EINVAL (NULL grid, planes < 0). */
+sn_status sn_set_blocking(sn_grid g, int planes);
+
+/* How sn_observables computes (the quantities of sn_obs, Sec. III):
+ *   SN_OBS_FP64 (default): the state widened to FP64, FP64 FFTs and sums;
+ *   SN_OBS_FP32 (complex64 grids): the FP32 line transforms of the step with
+ *     FP64 sums -- e_kin and the momenta from one read-only pass per axis (1D
+ *     Parseval per line), the density's half spectrum along the last axis
+ *     (mass, rho^2, V_ext and centroid sums in the same pass), e_pot from
+ *     sum K(k) |F rho|^2 over it.  About 1e-7 relative to the FP64 values,
+ *     at a small fraction of their cost (FP64 arithmetic is slow on B300).
+ * The Eq. 16 fluid's observables always take the FP64 path.
+ * Errors: SN_EINVAL (NULL grid, unknown mode), SN_ENOTSUP (SN_OBS_FP32 on a
+ * complex128 grid). */
+typedef enum { SN_OBS_FP64 = 0, SN_OBS_FP32 = 1 } sn_obs_mode;
+sn_status sn_set_obs_mode(sn_grid g, int mode);
+
 /* Test hook: in-place unnormalised DFTs, sign -1 (exp(-i ...)) or +1, of
  * nlines contiguous complex64 lines of length n (power of two, 8..1024) in
  * device memory, computed by the fused passes' line engine (engine as in

@@ -590,12 +590,14 @@ cudaError_t encode_lines(CUtensorMap* map, void* base, int N, bool strided, long
 // inner): strided lines as the 3D array (inner, outer, N/2 + 1) with boxes
 // (kLpb, 1, N/2 + 1), so that a tile narrower than kLpb lines stops at the
 // end of its row of lines; contiguous lines as the 2D array (lines, N/2 + 1)
-// with boxes (kLpb, N/2 + 1).  128-byte swizzle.
+// with boxes (kLpb, N/2 + 1).  A row holds row_lines >= outer * inner lines
+// (a launch over a slab of them; 0: exactly outer * inner).  128-byte swizzle.
 cudaError_t encode_half(CUtensorMap* map, void* base, int N, bool strided, long long outer,
-                        long long inner) {
+                        long long inner, long long row_lines) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const long long nlines = outer * inner;
+  const long long rowl = row_lines > 0 ? row_lines : nlines;
   const cuuint32_t H = (cuuint32_t)(N / 2 + 1);
   cuuint64_t dims[3], strides[2];
   cuuint32_t box[3], estr[3] = {1, 1, 1};
@@ -606,7 +608,7 @@ cudaError_t encode_half(CUtensorMap* map, void* base, int N, bool strided, long 
     dims[1] = (cuuint64_t)outer;
     dims[2] = H;
     strides[0] = (cuuint64_t)inner * 8;
-    strides[1] = (cuuint64_t)nlines * 8;
+    strides[1] = (cuuint64_t)rowl * 8;
     box[0] = kLpb;
     box[1] = 1;
     box[2] = H;
@@ -614,7 +616,7 @@ cudaError_t encode_half(CUtensorMap* map, void* base, int N, bool strided, long 
     rank = 2;
     dims[0] = (cuuint64_t)nlines;
     dims[1] = H;
-    strides[0] = (cuuint64_t)nlines * 8;
+    strides[0] = (cuuint64_t)rowl * 8;
     box[0] = kLpb;
     box[1] = H;
   }
@@ -705,7 +707,7 @@ cudaError_t launch_edge_t(const PsiPassArgs& in, int* status, cudaStream_t s) {
   cudaError_t e = encode_lines(&a.psi_map, in.psi, N, STRIDED, in.outer, in.inner);
   if (e == cudaSuccess)
     e = encode_half(&a.rh_map, EDGE == EDGE_PHASE ? (void*)in.rh_in : (void*)in.rh_out, N, STRIDED,
-                    in.outer, in.inner);
+                    in.outer, in.inner, in.rh_lines);
   if (e != cudaSuccess) return e;
   a.outer = in.outer;
   a.inner = in.inner;

@@ -141,6 +141,10 @@ struct sn_grid_s {
   double2* w64a = nullptr;     // FP64 scratch (psi copy / work)
   double2* w64b = nullptr;
   double* partials = nullptr;  // observables partials [kObsBlocks][Q_NUM]
+  // how sn_observables transforms (sn_set_obs_mode), and the FP32 mode's half
+  // spectrum of rho (allocated at its first use)
+  int obs_mode = SN_OBS_FP64;
+  float2* obs_rh32 = nullptr;
   double* obs_out = nullptr;   // [Q_NUM]
 
   // per-length twiddles, indexed by log2 N
@@ -189,6 +193,8 @@ struct sn_grid_s {
   // how the fused passes move their tiles (sn_set_staging), and the device word
   // the TMA passes set when a bounded tile wait expires
   int staging = SN_STAGING_TMA;
+  // planes per slab of the blocked y/x pass pairs of 3D rounds (sn_set_blocking; 0: off)
+  int block_planes = 0;
   int* status = nullptr;
 
   // Merged steps stay open across sn_step calls (complex64 grids).  While
@@ -382,10 +388,18 @@ cudaError_t rho_launch(sn_grid g, int N, bool strided, int op, const RhoPassArgs
 // alone adds to the half spectrum.  With several fields the local term g rho
 // of the total density is applied through the Green's multiplier
 // (rho_passes), not per field.
-sn_status psi_pass(sn_grid g, void* base, int j, int nf, int a, int variant, int full, double dt) {
-  const LineGeom lg = psi_geom(g, a);
+//
+// A 3D pass along y or x may cover the slab of planes [z0, z0 + zs) alone
+// (zs > 0; one field): its lines are those of the slab, which for x (the
+// contiguous axis) are a range of the half spectrum's columns as well.
+sn_status psi_pass(sn_grid g, void* base, int j, int nf, int a, int variant, int full, double dt,
+                   long long z0 = 0, long long zs = 0) {
+  LineGeom lg = psi_geom(g, a);
+  const bool slab = zs > 0;
+  const long long plane = slab ? (long long)(g->cells / g->n[0]) : 0;
   PsiPassArgs pa{};
-  pa.psi = reinterpret_cast<float2*>(base) + (size_t)j * g->cells;
+  pa.psi = reinterpret_cast<float2*>(base) + (size_t)j * g->cells + (size_t)(z0 * plane);
+  if (slab) lg.outer = lg.outer / g->n[0] * zs;  // lines before axis a: z times (y for x)
   pa.outer = lg.outer * (variant == PSI_PLAIN ? nf : 1);
   pa.nfields = variant == PSI_PLAIN ? 1 : nf;
   pa.fstride = g->cells;
@@ -393,19 +407,23 @@ sn_status psi_pass(sn_grid g, void* base, int j, int nf, int a, int variant, int
   pa.mult = g->mult32[a][full];
   pa.lift = g->lift32[a][full];
   pa.tw = g->tw32[log2i(g->n[a])];
-  pa.rh_in = g->rhohat;
-  pa.vext = g->has_vext ? g->vext32 : nullptr;
+  // half-spectrum column of the slab's first line (rows of cells / n[a] lines)
+  const long long rh_col = slab ? z0 * (plane / g->n[a]) : 0;
+  pa.rh_in = g->rhohat + rh_col;
+  pa.rh_lines = slab ? (long long)(g->cells / g->n[a]) : 0;
+  pa.vext = g->has_vext ? g->vext32 + (size_t)(z0 * plane) : nullptr;
   pa.h = (float)dt;
   pa.gh = g->fields > 1 ? 0.f : (float)(g->kp.g_local * dt);
-  pa.rh_out = g->rhohat;
+  pa.rh_out = g->rhohat + rh_col;
   pa.rh_accum = variant == PSI_DENSITY && j > 0;
   pa.tc = g->engine == SN_ENGINE_TC16 ? g->tc_frag : nullptr;
-  const double P = g->n[a] / 2 + 1, lines = (double)g->cells / g->n[a];
-  double bytes = 16.0 * g->cells * nf;
+  const double part = slab ? (double)zs / g->n[0] : 1.0;
+  const double P = g->n[a] / 2 + 1, lines = part * g->cells / g->n[a];
+  double bytes = 16.0 * part * g->cells * nf;
   int kind = K_PSI;
   if (variant == PSI_NPHASE) {
     bytes += 8.0 * P * lines;  // C2R reads the half spectrum along this axis
-    if (g->has_vext) bytes += 4.0 * g->cells * nf;
+    if (g->has_vext) bytes += 4.0 * part * g->cells * nf;
     kind = K_PSI_NPHASE;
   } else if (variant == PSI_DENSITY) {
     bytes += (j > 0 ? 16.0 : 8.0) * P * lines;
@@ -431,8 +449,29 @@ sn_status psi_pass(sn_grid g, void* base, int j, int nf, int a, int variant, int
               launch_edge_pass_tma(g->n[a], lg.strided, variant, pa, g->status, g->stream));
     return SN_OK;
   }
+  if (slab) return fail(g, SN_ECUDA, "psi_pass: a slab pass needs the TMA-staged kernels");
   SN_LAUNCH(g, kind, bytes, launch_psi_pass_f32(g->n[a], lg.strided, variant, pa, g->stream));
   return SN_OK;
+}
+
+// Whether round_f32 runs the y and x passes of a 3D round slab by slab
+// (sn_set_blocking): one field on the FP32 engine, every pass of the pair
+// TMA-staged, and more than one slab.
+bool blocked_pair(sn_grid g, const int* order, int i0, const int* variants) {
+  if (g->ndim != 3 || g->block_planes <= 0 || g->block_planes >= g->n[0] || g->fields != 1 ||
+      g->engine != SN_ENGINE_FP32)
+    return false;
+  for (int i = i0; i < i0 + 2; ++i) {
+    const int a = order[i];
+    if (a == 0) return false;
+    const int kind = variants[i] == PSI_NPHASE ? K_PSI_NPHASE
+                     : variants[i] == PSI_DENSITY ? K_PSI_DENSITY : K_PSI;
+    LineGeom lg = psi_geom(g, a);
+    if (!use_tma(g, kind, a, g->n[a], lg.strided, lg.outer, lg.inner)) return false;
+    // the slab's first half-spectrum column stays 16-byte aligned
+    if (variants[i] != PSI_PLAIN && (g->cells / g->n[0] / g->n[a]) % 2 != 0) return false;
+  }
+  return true;
 }
 
 // Half-spectrum passes after the density of axis h: forward along the middle
@@ -527,12 +566,33 @@ sn_status round_f32(sn_grid g, void* base, bool odd, bool nphase, int full, bool
   const int d = g->ndim;
   int order[3];
   for (int i = 0; i < d; ++i) order[i] = odd ? d - 1 - i : i;
+  int variants[3];
+  for (int i = 0; i < d; ++i) {
+    variants[i] = PSI_PLAIN;
+    if (i == 0 && nphase) variants[i] = PSI_NPHASE;
+    if (i == d - 1 && density) variants[i] = PSI_DENSITY;
+  }
+  // the y and x passes of a 3D round (passes 1, 2 of an even round, 0, 1 of an
+  // odd one) stay within the planes of fixed z: slab by slab, the second pass
+  // reads the slab the first just wrote while it is still in L2
+  const int pair = d == 3 ? (odd ? 0 : 1) : -1;
+  const bool blocked = pair >= 0 && blocked_pair(g, order, pair, variants);
   // axis by axis over the fields: every field's potential pass reads the
   // half spectrum before the first density pass overwrites it
   for (int i = 0; i < d; ++i) {
-    int variant = PSI_PLAIN;
-    if (i == 0 && nphase) variant = PSI_NPHASE;
-    if (i == d - 1 && density) variant = PSI_DENSITY;
+    const int variant = variants[i];
+    if (blocked && i == pair) {
+      const long long nz = g->n[0], zs = g->block_planes;
+      for (long long z0 = 0; z0 < nz; z0 += zs) {
+        const long long s = z0 + zs <= nz ? zs : nz - z0;
+        for (int k = pair; k < pair + 2; ++k) {
+          sn_status st = psi_pass(g, base, 0, 1, order[k], variants[k], full, dt, z0, s);
+          if (st != SN_OK) return st;
+        }
+      }
+      ++i;  // the pair's second pass is done
+      continue;
+    }
     // the tensor-core potential and density passes take one field per launch
     const bool tc_axis = g->engine == SN_ENGINE_TC16 && g->n[order[i]] == 256;
     const bool one_launch = variant == PSI_PLAIN || !tc_axis;
@@ -1090,16 +1150,79 @@ sn_status sn_sync(sn_grid g) {
   return check_status(g);
 }
 
+// The observables' partial sums of a complex64 state from FP32 line transforms
+// (obs_f32.cu), into the slots the FP64 path fills, and their totals in
+// g->obs_out.  The half spectrum of rho is taken along the last axis h; in 3D
+// the forward FFT along y is the step's own half-spectrum pass and the
+// Green's sum runs along z, in the geometry of the step's Green's pass.
+sn_status obs_partials_f32(sn_grid g, const void* psi_now) {
+  const int d = g->ndim, h = d - 1;
+  const long long P = g->n[h] / 2 + 1, lines = g->cells / g->n[h];
+  cudaError_t e;
+  if (!g->obs_rh32) {
+    if ((e = cudaMalloc(&g->obs_rh32, sizeof(float2) * (size_t)(P * lines))) != cudaSuccess)
+      return cuda_fail(g, e, "cudaMalloc(observables half spectrum)");
+    g->allocs.push_back(g->obs_rh32);
+  }
+  e = cudaMemsetAsync(g->partials, 0, sizeof(double) * kObsBlocks * Q_NUM, g->stream);
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemsetAsync");
+  const float2* psi = reinterpret_cast<const float2*>(psi_now);
+  const int nf = g->fields;
+  for (int a = 0; a < d; ++a) {
+    const LineGeom lg = psi_geom(g, a);
+    // the fields extend the slowest axis: nf times the lines
+    SN_LAUNCH(g, K_OBS, 8.0 * nf * g->cells,
+              launch_obs32_spec(g->n[a], psi, lg.outer * nf, lg.inner, g->tw32[log2i(g->n[a])],
+                                g->L[a], a, g->partials, g->stream));
+  }
+  const int n0 = d == 3 ? g->n[0] : 1, n1 = d == 3 ? g->n[1] : g->n[0];
+  SN_LAUNCH(g, K_OBS, 8.0 * nf * g->cells + 8.0 * P * lines,
+            launch_obs32_density(g->n[h], psi, nf, g->cells, g->has_vext ? g->vext32 : nullptr,
+                                 g->obs_rh32, n0, n1, g->tw32[log2i(g->n[h])], g->partials,
+                                 g->stream));
+  const GreenCoeffs gc = green_coeffs(g->kp);
+  const double rbytes = 16.0 * (double)P * lines;
+  if (d == 2) {
+    // half spectrum (P, n0): lines along axis 0, contiguous, plane = k_h
+    SN_LAUNCH(g, K_OBS, 0.5 * rbytes,
+              launch_obs32_green(g->n[0], g->obs_rh32, P, 1, 1, g->k2_32[h], g->zero32,
+                                 g->k2_32[0], g->n[h], gc.cN, gc.cY, gc.mu2,
+                                 g->tw32[log2i(g->n[0])], g->partials, g->stream));
+  } else {
+    // half spectrum (P, nz, ny): the forward FFT along y (contiguous), then the
+    // Green's sum along z (strided: plane k_h, mid y)
+    RhoPassArgs x{};
+    x.data = g->obs_rh32;
+    x.outer = P * g->n[0];
+    x.inner = 1;
+    x.tw = g->tw32[log2i(g->n[1])];
+    x.ctas_per_sm = g->sched[K_RHO_FWD][h];
+    g->cur_axis = h;
+    SN_LAUNCH(g, K_OBS, rbytes, rho_launch(g, g->n[1], false, RHO_FWD, x));
+    SN_LAUNCH(g, K_OBS, 0.5 * rbytes,
+              launch_obs32_green(g->n[0], g->obs_rh32, P, g->n[1], 1, g->k2_32[h], g->k2_32[1],
+                                 g->k2_32[0], g->n[h], gc.cN, gc.cY, gc.mu2,
+                                 g->tw32[log2i(g->n[0])], g->partials, g->stream));
+  }
+  SN_LAUNCH(g, K_OBS, 0.0, launch_obs_finish(g->partials, Q_NUM, g->obs_out, g->stream));
+  return SN_OK;
+}
+
 sn_status sn_observables(sn_grid g, sn_obs* out) {
   if (!g) return fail(nullptr, SN_EINVAL, "sn_observables: grid is NULL");
   if (!out) return fail(g, SN_EINVAL, "sn_observables: out is NULL");
-  sn_status st = ensure_f64_scratch(g);
+  const bool fast = g->obs_mode == SN_OBS_FP32 && g->dtype == SN_C64 && !g->fluid;
+  sn_status st = fast ? SN_OK : ensure_f64_scratch(g);
   if (st != SN_OK) return st;
   void* psi_now = nullptr;  // the state at the current integer step
   if ((st = closed_state(g, &psi_now)) != SN_OK) return st;
   const int d = g->ndim;
   const int nf = g->fields;
   const bool f32 = g->dtype == SN_C64;
+  cudaError_t e;
+  if (fast) {
+    if ((st = obs_partials_f32(g, psi_now)) != SN_OK) return st;
+  } else {
   // field j in FP64 (widened into w64a for complex64 grids)
   auto field64 = [&](int j, double2** dst) -> sn_status {
     if (f32) {
@@ -1112,7 +1235,7 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
     }
     return SN_OK;
   };
-  cudaError_t e = cudaMemsetAsync(g->partials, 0, sizeof(double) * kObsBlocks * Q_NUM, g->stream);
+  e = cudaMemsetAsync(g->partials, 0, sizeof(double) * kObsBlocks * Q_NUM, g->stream);
   if (e != cudaSuccess) return cuda_fail(g, e, "cudaMemsetAsync");
   // mass, centroids, rho^2 and V_ext terms, and the potential energy are those of
   // the total density: with several fields they are taken from a single state
@@ -1158,6 +1281,7 @@ sn_status sn_observables(sn_grid g, sn_obs* out) {
   SN_LAUNCH(g, K_OBS, 16.0 * g->cells,
             launch_obs_green(w, g->n, d, k2, gc.cN, gc.cY, gc.mu2, g->partials, g->stream));
   SN_LAUNCH(g, K_OBS, 0.0, launch_obs_finish(g->partials, Q_NUM, g->obs_out, g->stream));
+  }
   double q[Q_NUM];
   e = cudaMemcpyAsync(q, g->obs_out, sizeof(q), cudaMemcpyDeviceToHost, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
@@ -1233,6 +1357,23 @@ sn_status sn_set_engine(sn_grid g, int engine) {
     if (e != cudaSuccess) return cuda_fail(g, e, "sn_set_engine: upload");
   }
   g->engine = engine;
+  return SN_OK;
+}
+
+sn_status sn_set_obs_mode(sn_grid g, int mode) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_set_obs_mode: grid is NULL");
+  if (mode != SN_OBS_FP64 && mode != SN_OBS_FP32)
+    return fail(g, SN_EINVAL, "sn_set_obs_mode: unknown mode");
+  if (mode == SN_OBS_FP32 && g->dtype != SN_C64)
+    return fail(g, SN_ENOTSUP, "sn_set_obs_mode: SN_OBS_FP32 takes complex64 grids");
+  g->obs_mode = mode;
+  return SN_OK;
+}
+
+sn_status sn_set_blocking(sn_grid g, int planes) {
+  if (!g) return fail(nullptr, SN_EINVAL, "sn_set_blocking: grid is NULL");
+  if (planes < 0) return fail(g, SN_EINVAL, "sn_set_blocking: planes must be >= 0");
+  g->block_planes = planes;
   return SN_OK;
 }
 

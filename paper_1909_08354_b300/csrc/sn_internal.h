@@ -44,6 +44,8 @@ struct PsiPassArgs {
   long long fstride;       // elements from one field to the next
   int ctas_per_sm;         // schedule: 0 = as many as fit, k > 0 = at most k, -1 = one per tile
   const uint4* tc;         // tensor-core fragment table (256-point lines), or NULL
+  long long rh_lines;      // TMA edge passes: lines of a half-spectrum row (its stride;
+                           // 0 = outer * inner), more when the launch covers a slab of them
 };
 
 struct RhoPassArgs {
@@ -199,6 +201,24 @@ cudaError_t launch_obs_green(const double2* rhohat, const int* n, int ndim,
                              const double* const* k2, double cN, double cY, double mu2,
                              double* partials, cudaStream_t s);
 cudaError_t launch_obs_finish(const double* partials, int nq, double* out, cudaStream_t s);
+// FP32-transform observables of complex64 states (obs_f32.cu), into the same
+// partial slots: spectral sums along `axis` (lines (outer, inner) of N
+// points, L the axis length) into Q_EKIN0 + 2 axis and Q_P0 + 2 axis; the
+// density pass along the last axis (contiguous lines of N points; n0, n1 the
+// padded 3D sizes of the axes before it) into Q_MASS .. Q_SX2, writing the
+// half spectrum of rho [N/2 + 1][cells / N] to rh; the Green's sum over the
+// half spectrum's lines of N points (geometry and k^2 tables as the step's
+// Green's pass, nh the half axis' length) into Q_EPOT.
+cudaError_t launch_obs32_spec(int N, const float2* psi, long long outer, long long inner,
+                              const float2* tw, double L, int axis, double* partials,
+                              cudaStream_t s);
+cudaError_t launch_obs32_density(int N, const float2* psi, int nfields, long long cells,
+                                 const float* vext, float2* rh, int n0, int n1, const float2* tw,
+                                 double* partials, cudaStream_t s);
+cudaError_t launch_obs32_green(int N, const float2* rh, long long outer, long long inner,
+                               long long mid_n, const float* k2p, const float* k2m,
+                               const float* k2l, int nh, double cN, double cY, double mu2,
+                               const float2* tw, double* partials, cudaStream_t s);
 // Fluid energy sums (Eq. 16) into partials [kObsBlocks][Q_NUM] at q = 0..3 (zeroed
 // first): rho phi_N (Re wphi), rho phi_C (phi_c may be NULL), eps(rho), a lap(a)
 // (Im wlap = lap a, a = sqrt(max(rho, floor)))

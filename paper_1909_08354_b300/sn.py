@@ -20,6 +20,7 @@ LIB_PATH = os.environ.get("SN_LIB_PATH") or os.path.join(_HERE, "libsn.so")
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 SN_ENGINE_FP32, SN_ENGINE_TC16 = 0, 1
 SN_STAGING_TMA, SN_STAGING_REGISTERS, SN_STAGING_RESIDENT = 0, 1, 2
+SN_OBS_FP64, SN_OBS_FP32 = 0, 1
 SN_FLOOR_MAX, SN_FLOOR_SMOOTH = 0, 1
 SN_C64, SN_C128 = 0, 1
 SN_KERNEL_NMC, SN_KERNEL_POISSON = 0, 1
@@ -90,6 +91,8 @@ _SIGNATURES = [
     ("sn_kind_name", ctypes.c_char_p, [ctypes.c_int]),
     ("sn_set_engine", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sn_set_staging", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_set_blocking", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_set_obs_mode", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sn_set_fluid", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SnFluid)]),
     ("sn_set_fields", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sn_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -722,6 +725,16 @@ class Grid:
         """SN_STAGING_TMA (tiles moved by bulk tensor copies) or SN_STAGING_REGISTERS;
         the results are the same bit for bit."""
         _check(self.h, lib().sn_set_staging(self.h, int(mode)))
+
+    def set_obs_mode(self, mode: int):
+        """SN_OBS_FP64 (FP64 transforms) or SN_OBS_FP32 (the step's FP32 line
+        transforms with FP64 sums, complex64 grids)."""
+        _check(self.h, lib().sn_set_obs_mode(self.h, int(mode)))
+
+    def set_blocking(self, planes: int):
+        """Run the y/x pass pair of each 3D round in slabs of `planes` z-planes
+        (0: off); the results are the same bit for bit."""
+        _check(self.h, lib().sn_set_blocking(self.h, int(planes)))
 
     def sync(self):
         sn_sync(self.h)
