@@ -248,6 +248,30 @@ def cpu_model():
     return "unknown"
 
 
+def time_observables(sn, torch, g, reps=5):
+    """sn_observables on the bench grid in both modes (FP64 transforms; FP32
+    line transforms with FP64 sums), best of reps calls each, and the largest
+    relative difference of mass and energies between them."""
+    out, got = {}, {}
+    for mode, name in ((sn.SN_OBS_FP64, "fp64"), (sn.SN_OBS_FP32, "fp32")):
+        g.set_obs_mode(mode)
+        got[name] = g.observables()  # warm-up (allocates the mode's scratch)
+        best = float("inf")
+        for _ in range(reps):
+            g.sync()
+            t0 = time.perf_counter()
+            got[name] = g.observables()
+            best = min(best, time.perf_counter() - t0)
+        out[name + "_ms"] = 1e3 * best
+    g.set_obs_mode(sn.SN_OBS_FP64)
+    out["fp32_max_rel_diff"] = max(abs(got["fp32"][k] - got["fp64"][k]) / abs(got["fp64"][k])
+                                   for k in ("mass", "e_kin", "e_pot", "e_total")
+                                   if got["fp64"][k] != 0.0)
+    out["note"] = ("host wall time of one sn_observables call, best of %d per mode; the "
+                   "closing round of the open state ran once, in the first (warm-up) call" % reps)
+    return out
+
+
 def run_scan(sn, torch, stream, peak, count=96, steps=500):
     """The batched parameter scan: 96 2D instances (128^2..1024^2), 500 steps, one launch.
     With several ranks the instances are partitioned by cost (n^2 log n) and each
@@ -685,6 +709,7 @@ def main():
     t = min(region_s)
     value = world * w.cells * args.steps / t
     mass_drift = abs(g.observables()["mass"] / m0 - 1.0)
+    observables = time_observables(sn, torch, g)
 
     # ---- per-kernel timing (CUDA events around every launch, same steps)
     prof = g.profile_step(w.dt, min(args.steps, 200))
@@ -808,6 +833,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "mass_drift": mass_drift,
+            "observables": observables,
             "fp64_plain_gpu": fp64,
             "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu,
