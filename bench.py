@@ -37,6 +37,40 @@ METRIC = "cell-steps/s at 256^3: fast forms vs plain FP64 GPU step at <=1e-6 rel
 UNIT = "cell-steps/s"
 BYTES_PER_CELL_STEP = 80.0  # algorithmic HBM bytes of the fused 3D complex64 step
 REGIONS = 5  # timed regions of K steps each; the value is the best of them
+
+# DRAM bytes (read + write) of one launch of the dominant kernel at 256^3, from
+# an ncu capture (--set full, one launch of the contiguous potential pass
+# edge_pass_tma_kernel<256, 0, 0>; ncu flushes the caches, so the potential's
+# half spectrum, L2-resident in the running step, is read from DRAM there, and
+# the part of psi still in L2 at the kernel's end is not yet written), with a
+# SHA-256 of the kernel's sources.  The line carries it only while the sources
+# hash to the same value.
+NCU_TRAFFIC = {"kernel": "psi_pass_nphase", "bytes": 201.964288e6 + 81.139456e6,
+               "sources": ["paper_1909_08354_b300/csrc/passes_tma.cu",
+                           "paper_1909_08354_b300/csrc/tma_ops.cuh",
+                           "paper_1909_08354_b300/csrc/tile_ops.cuh",
+                           "paper_1909_08354_b300/csrc/sn_fft.cuh",
+                           "paper_1909_08354_b300/csrc/fft_plan.h"],
+               "sha256": "0125ca8c5757ca3217969c3a3f71ed2aa211f9f59100fb3e52810fd52d0c3739"}
+
+
+def captured_traffic(kernel: str):
+    """(bytes, note): the ncu DRAM bytes of `kernel` if its sources are those
+    of the capture, else (None, why)."""
+    import hashlib
+    if kernel != NCU_TRAFFIC["kernel"]:
+        return None, f"no ncu capture of {kernel}"
+    h = hashlib.sha256()
+    try:
+        for f in NCU_TRAFFIC["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+    except OSError as e:
+        return None, f"kernel sources unreadable ({e})"
+    if h.hexdigest() != NCU_TRAFFIC["sha256"]:
+        return None, "the kernel's sources changed since the ncu capture"
+    return NCU_TRAFFIC["bytes"], ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                                  "(x variant, caches flushed by ncu), sources unchanged since")
 CPU_ALL_N = 128     # grid of each process of the all-core oracle baseline
 CPU_MAX_PROCS = 64  # at most this many oracle processes (about 0.4 GB of host memory each)
 
@@ -718,6 +752,7 @@ def main():
     peak, peak_src = measured_peaks()
     dk = kinds[dom]
     achieved = dk["bytes"] / (dk["ms"] / 1e3) / 1e9
+    traffic, traffic_note = captured_traffic(dom)
     total_ms = sum(v["ms"] for v in kinds.values())
     passes = {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / v["launches"],
                   "share": v["ms"] / total_ms,
@@ -821,9 +856,9 @@ def main():
                                     f"fit): {schedule}"),
                        "l2": "working set 202 MB > 126 MB L2; no flush"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                         "traffic_note": "DRAM bytes of the dominant kernel are taken by ncu "
-                                         "outside this run; not carried in the line",
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "traffic_note": traffic_note,
+                         "algorithmic_bytes_per_launch": dk["bytes"] / dk["launches"],
                          "peak_source": peak_src,
                          "step_achieved": step_gbs, "step_frac": step_gbs / peak,
                          "bytes_per_cell_step": BYTES_PER_CELL_STEP},
