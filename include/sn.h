@@ -368,6 +368,12 @@ sn_status sn_observables_batch(sn_batch b, int index, sn_obs* out);
 sn_status sn_batch_sync(sn_batch b);
 /* Clock cycles one dependency wait may spin before it gives up (>= 0). */
 sn_status sn_set_batch_wait_limit(sn_batch b, long long cycles);
+/* Register budget of the batch's launch: per_sm = 3 (80 registers a thread,
+ * three resident CTAs per SM; the default), 2 (128) or 1 (255).  The launch
+ * stays cooperative with as many CTAs as are resident, so the dependency
+ * waits end whatever the choice; the results are the same bit for bit.
+ * Errors: SN_EINVAL (NULL batch, per_sm outside 1..3). */
+sn_status sn_set_batch_ctas(sn_batch b, int per_sm);
 /* Kernel launches of this batch (one per sn_step_batch call). */
 long long sn_batch_launch_count(sn_batch b);
 void sn_destroy_batch(sn_batch b);

@@ -34,7 +34,11 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kThreads = 256;  // threads per CTA for every line length
-constexpr int kCtasPerSm = 3;  // resident CTAs per SM the registers are sized for (80 each)
+// Resident CTAs per SM the registers are sized for: 3 (80 registers a
+// thread, the default), 2 (128) or 1 (255), chosen per batch
+// (sn_set_batch_ctas): fewer CTAs hide less latency, more spill the three-stage
+// 512- and 1024-point items.
+constexpr int kDefaultCtasPerSm = 3;
 constexpr int kMaxLog2 = 10;
 
 template <int N>
@@ -220,7 +224,8 @@ __device__ void run_item(const Inst& d, int r, int s, int nsteps, long long tau,
   }
 }
 
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) scan_kernel(ScanArgs a) {
+template <int CPS>
+__global__ void __launch_bounds__(kThreads, CPS) scan_kernel(ScanArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int4 s_item;
   __shared__ int s_round, s_go;
@@ -285,12 +290,15 @@ struct sn_batch_s {
   unsigned* done = nullptr;
   int* err = nullptr;
   long long wait_limit = 4000000000LL;  // about 2 s at the B300's 2 GHz
-  int grid = 0;
+  int grid = 0;               // CTAs of the launch: resident CTAs per SM x SMs
+  int cps = kDefaultCtasPerSm;  // the register budget's CTAs per SM (1 .. 3)
+  int grid_of[4] = {};        // grid per budget
   long long launches = 0;
   // a captured launch (memsets + kernel), keyed by nsteps
   cudaGraphExec_t graph = nullptr;
   int graph_steps = -1;
   long long graph_limit = -1;
+  int graph_cps = -1;
   // observables of one instance go through a grid of the same shape
   std::vector<sn_grid> obs_grid;
   std::vector<void*> allocs;
@@ -331,6 +339,33 @@ double wavenumber(int j, int n, double L) { return 2.0 * kPi / L * (double)(j < 
 }  // namespace
 
 extern "C" {
+
+namespace {
+using ScanKern = void (*)(ScanArgs);
+ScanKern scan_kernel_of(int cps) {
+  return cps == 1 ? scan_kernel<1> : cps == 2 ? scan_kernel<2> : scan_kernel<3>;
+}
+// Kernel attributes of register budget cps and its cooperative grid: the
+// shared memory of the resident CTAs (1 KB reserved each), the rest of the
+// SM's 256 KB left to L1 for the twiddle and kinetic tables and spills; at
+// most cps CTAs per SM.
+cudaError_t prep_scan_kernel(int cps, int smem_sm, int sms, int* grid) {
+  ScanKern k = scan_kernel_of(cps);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e != cudaSuccess) return e;
+  if (smem_sm > 0) {
+    const double need = (double)cps * (double)(kSmemBytes + 1024 + 64);
+    const int pct = std::min(100, (int)std::ceil(100.0 * need / smem_sm));
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) != cudaSuccess)
+      return e;
+  }
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, kSmemBytes)) != cudaSuccess)
+    return e;
+  *grid = std::min(per_sm, cps) * sms;
+  return cudaSuccess;
+}
+}  // namespace
 
 sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* L,
                           void* cuda_stream) {
@@ -430,27 +465,16 @@ sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* 
   if ((e = balloc(b, &b->done, (size_t)count)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(done)"));
   if ((e = balloc(b, &b->err, (size_t)2)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(err)"));
   if ((e = cudaMemset(b->err, 0, 2 * sizeof(int))) != cudaSuccess) return bail(bcuda(e, "cudaMemset(err)"));
-  if ((e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kSmemBytes)) != cudaSuccess)
-    return bail(bcuda(e, "cudaFuncSetAttribute"));
-  int dev = 0, sms = 0, per_sm = 0, smem_sm = 0;
+  int dev = 0, sms = 0, smem_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  if (smem_sm > 0) {
-    // shared memory for the resident CTAs (1 KB reserved each), the rest of
-    // the SM's 256 KB stays L1 for the twiddle and kinetic tables and spills
-    const double need = (double)kCtasPerSm * (double)(kSmemBytes + 1024 + 64);
-    const int pct = std::min(100, (int)std::ceil(100.0 * need / smem_sm));
-    if ((e = cudaFuncSetAttribute(scan_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) !=
-        cudaSuccess)
-      return bail(bcuda(e, "cudaFuncSetAttribute(carveout)"));
+  for (int c = 1; c <= 3; ++c) {
+    if ((e = prep_scan_kernel(c, smem_sm, sms, &b->grid_of[c])) != cudaSuccess)
+      return bail(bcuda(e, "scan kernel attributes"));
+    if (b->grid_of[c] < 1) return bail(bfail(SN_ENOTSUP, "sn_create_batch: scan kernel does not fit on an SM"));
   }
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_kernel, kThreads, kSmemBytes)) !=
-      cudaSuccess)
-    return bail(bcuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
-  if (per_sm < 1) return bail(bfail(SN_ENOTSUP, "sn_create_batch: scan kernel does not fit on an SM"));
-  b->grid = per_sm * sms;
+  b->grid = b->grid_of[b->cps];
   *out = b;
   return SN_OK;
 }
@@ -551,7 +575,8 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
   a.err = b->err;
   a.wait_limit = b->wait_limit;
 
-  if (b->graph && (b->graph_steps != nsteps || b->graph_limit != b->wait_limit)) {
+  if (b->graph && (b->graph_steps != nsteps || b->graph_limit != b->wait_limit ||
+                   b->graph_cps != b->cps)) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
@@ -571,7 +596,7 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e2 = e1 == cudaSuccess ? cudaLaunchKernelEx(&cfg, scan_kernel, a) : e1;
+    cudaError_t e2 = e1 == cudaSuccess ? cudaLaunchKernelEx(&cfg, scan_kernel_of(b->cps), a) : e1;
     e = cudaStreamEndCapture(b->stream, &gr);
     if (e2 != cudaSuccess) {
       if (gr) cudaGraphDestroy(gr);
@@ -583,9 +608,18 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
     if (e != cudaSuccess) return bcuda(e, "cudaGraphInstantiate");
     b->graph_steps = nsteps;
     b->graph_limit = b->wait_limit;
+    b->graph_cps = b->cps;
   }
   if ((e = cudaGraphLaunch(b->graph, b->stream)) != cudaSuccess) return bcuda(e, "cudaGraphLaunch");
   b->launches += 1;
+  return SN_OK;
+}
+
+sn_status sn_set_batch_ctas(sn_batch b, int per_sm) {
+  if (!b) return bfail(SN_EINVAL, "sn_set_batch_ctas: batch is NULL");
+  if (per_sm < 1 || per_sm > 3) return bfail(SN_EINVAL, "sn_set_batch_ctas: per_sm must be 1, 2 or 3");
+  b->cps = per_sm;
+  b->grid = b->grid_of[per_sm];
   return SN_OK;
 }
 

@@ -117,6 +117,7 @@ _SIGNATURES = [
     ("sn_observables_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(SnObs)]),
     ("sn_batch_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_set_batch_wait_limit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
+    ("sn_set_batch_ctas", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sn_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("sn_destroy_batch", None, [ctypes.c_void_p]),
     ("sn_fno_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
@@ -359,6 +360,10 @@ def sn_set_batch_wait_limit(b, cycles: int):
     _check(None, lib().sn_set_batch_wait_limit(b, int(cycles)))
 
 
+def sn_set_batch_ctas(b, per_sm: int):
+    _check(None, lib().sn_set_batch_ctas(b, int(per_sm)))
+
+
 def sn_batch_launch_count(b) -> int:
     return int(lib().sn_batch_launch_count(b))
 
@@ -564,6 +569,10 @@ class Batch:
 
     def set_wait_limit(self, cycles: int):
         sn_set_batch_wait_limit(self.h, cycles)
+
+    def set_ctas(self, per_sm: int):
+        """Register budget of the launch: 3 (default), 2 or 1 resident CTAs per SM."""
+        sn_set_batch_ctas(self.h, per_sm)
 
     def launch_count(self) -> int:
         return sn_batch_launch_count(self.h)

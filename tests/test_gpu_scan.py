@@ -126,3 +126,34 @@ def test_parameter_scan_96_instances_500_steps():
     e_batch = O.rel_l2(b.get_state(i), exact)
     assert e_batch <= 2 * e_grid + 1e-5, (e_batch, e_grid)
     b.close()
+
+
+def test_every_register_budget_gives_the_same_bits():
+    """sn_set_batch_ctas changes the CTAs of the cooperative launch and the
+    registers of its threads, not the arithmetic: the same bits for 1, 2 and
+    3 CTAs per SM, on every line length the scan takes."""
+    sizes = [1024, 512, 256, 128, 64, 32, 16, 8, 256, 1024]
+    ws = [W.random_small((n, n), seed=400 + i, L=16.0) for i, n in enumerate(sizes)]
+    psis = [w.psi0().astype(np.complex64) for w in ws]
+    outs = {}
+    for cps in (3, 2, 1):
+        b = sn.Batch(sizes, [w.L[0] for w in ws])
+        b.set_kernels([kw_of(w.kernel) for w in ws])
+        b.set_ctas(cps)
+        for i, p in enumerate(psis):
+            b.set_state(i, p)
+        b.step(0.01, 3)
+        b.sync()
+        outs[cps] = [b.get_state(i).copy() for i in range(len(sizes))]
+        b.close()
+    for cps in (2, 1):
+        for i in range(len(sizes)):
+            assert np.array_equal(outs[cps][i], outs[3][i]), (cps, sizes[i])
+    b = sn.Batch([8], [4.0])
+    try:
+        for bad in (0, 4):
+            with pytest.raises(sn.SNError) as e:
+                b.set_ctas(bad)
+            assert e.value.status == sn.SN_EINVAL
+    finally:
+        b.close()
