@@ -277,11 +277,13 @@ sn_status sn_set_engine(sn_grid g, int engine);
 
 /* How the fused complex64 passes move their tiles of lines between HBM and
  * shared memory; the arithmetic, and so every result, is the same bit for bit.
- *   SN_STAGING_TMA (default): each tile travels as one bulk tensor copy of the
+ *   SN_STAGING_TMA: each tile travels as one bulk tensor copy of the
  *     tensor-memory accelerator into a shared-memory slot, and back out, while
- *     the CTA transforms the tile in its other slot.  Taken by the plain
- *     kinetic passes and the half-spectrum passes of 128- and 256-point lines
- *     on the FP32 engine; the other passes keep register staging.  A tile wait
+ *     the CTA transforms the tile in its other slot.  Taken by the passes of
+ *     128- and 256-point lines on the FP32 engine: the plain kinetic, the
+ *     potential, the density and the half-spectrum passes of one field, the
+ *     plain and half-spectrum passes of several; the other passes keep
+ *     register staging.  A tile wait
  *     that does not end within about 2 s makes the next synchronising call
  *     (sn_sync, sn_get_state to host, sn_observables) return SN_ETIMEOUT.
  *   SN_STAGING_REGISTERS: every thread loads its elements of the next tile
@@ -291,6 +293,9 @@ sn_status sn_set_engine(sn_grid g, int engine);
  *     memory for all steps of an sn_step call: one launch per call, no HBM
  *     traffic between the passes (one SM; pays off where the tiled passes are
  *     launch-bound).  Other grids take SN_STAGING_TMA.  Same bits.
+ * Without a call, a grid of one field takes SN_STAGING_TMA and a grid of
+ * several fields (sn_set_fields) SN_STAGING_REGISTERS, whose plain passes keep
+ * the overlap with the fused-fields potential and density passes.
  * Errors: SN_EINVAL (NULL grid, unknown mode). */
 typedef enum { SN_STAGING_TMA = 0, SN_STAGING_REGISTERS = 1, SN_STAGING_RESIDENT = 2 } sn_staging;
 sn_status sn_set_staging(sn_grid g, int mode);
