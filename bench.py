@@ -89,6 +89,8 @@ def parse():
     p.add_argument("--scan-count", type=int, default=96, help="instances of the batched scan")
     p.add_argument("--scan-steps", type=int, default=500, help="steps of the batched scan")
     p.add_argument("--no-tc", action="store_true")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the 128^3 collision (c64, c128) and the alpha_Y = 0, 0.5 runs")
     p.add_argument("--engine", choices=["fp32", "tc16"], default="fp32",
                    help="line engine of the timed grid (tc16: tensor cores on 256-point axes)")
     p.add_argument("--no-fno", action="store_true")
@@ -404,6 +406,57 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500):
             "plain_fp64_ms_estimated": 1e3 * t64,
             "plain_fp64_sample": f"{k64} steps per instance, scaled to {steps}",
             "speedup_vs_plain_fp64": t64 / t_batch}
+
+
+def time_grid_steps(sn, torch, stream, w, dtype, steps, kwargs=None):
+    """Best of three regions of `steps` steps of workload w on one grid
+    (CUDA events on the grid's stream), after 5 warm-up steps; seconds per step."""
+    g = sn.Grid(w.n, w.L, dtype, stream=stream.cuda_stream)
+    try:
+        g.set_kernel(**(kwargs or kernel_kw(w.kernel)))
+        g.set_state(w.psi0().astype(np.complex64 if dtype == "c64" else np.complex128))
+        g.step(w.dt, 5)
+        best = float("inf")
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            g.sync()
+            e0.record(stream)
+            g.step(w.dt, steps)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3 / steps)
+        return best
+    finally:
+        g.close()
+
+
+def run_configs(sn, torch, stream, peak, main_value):
+    """The other configurations of the metric's table: the 128^3 head-on
+    collision in complex64 and complex128 (its 16.8 MB complex64 state stays in
+    the 126 MB L2 between passes, so its 80 B/cell-step rate is an L2 rate
+    against the 256^3 HBM-bound step) and the 256^3 N-body workload at the
+    other alpha_Y values of the table."""
+    out = {}
+    c2 = W.head_on_collision_3d()
+    t32 = time_grid_steps(sn, torch, stream, c2, "c64", 200)
+    t64 = time_grid_steps(sn, torch, stream, c2, "c128", 10)
+    gbs = BYTES_PER_CELL_STEP * c2.cells / t32 / 1e9
+    out["collision_128"] = {
+        "workload": "sn3d_collision_128: 128^3, L=40, two lumps sigma 2 at x=+-8, |v|=0.3, "
+                    "alpha_Y=0.1, lambda_Y=5, g=0.01, dt=5e-3",
+        "complex64": {"value": c2.cells / t32, "unit": UNIT, "ms_per_step": 1e3 * t32,
+                      "GBps_at_80B_per_cell_step": gbs, "frac_of_measured_hbm": gbs / peak,
+                      "working_set": "16.8 MB psi + 8.5 MB half spectrum: L2-resident (126 MB)"},
+        "complex128_plain_fp64": {"value": c2.cells / t64, "unit": UNIT, "ms_per_step": 1e3 * t64},
+        "speedup_fp32_vs_fp64": t64 / t32,
+        "vs_256_cubed_hbm_bound": (c2.cells / t32) / main_value}
+    for alpha in (0.0, 0.5):
+        w = W.nbody_3d(alpha_Y=alpha)
+        t = time_grid_steps(sn, torch, stream, w, "c64", 200)
+        out[f"nbody_256_alpha_{alpha:g}"] = {"value": w.cells / t, "unit": UNIT,
+                                             "ms_per_step": 1e3 * t}
+    return out
 
 
 def run_tc16(sn, torch, stream, w, kw, psi0, peak, ref1, steps=200):
@@ -799,6 +852,10 @@ def main():
         g64.close()
     g.close()
 
+    configs = None
+    if not args.no_configs and world == 1 and args.n == 256:
+        configs = run_configs(sn, torch, stream, peak, value / world)
+
     tc = None
     if not args.no_tc and args.n == 256 and args.engine == "fp32":
         tc = run_tc16(sn, torch, stream, w, kw, psi0, peak, ref1)
@@ -872,6 +929,7 @@ def main():
             "fp64_plain_gpu": fp64,
             "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu,
+            "other_configs": configs,
             "tensor_core_engine": tc,
             "optical_kernel": optical,
             "fluid_model": fluid,
