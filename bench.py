@@ -347,6 +347,7 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500):
     b.set_kernels(kws)
     for i, p in enumerate(psis):
         b.set_state(i, p)
+    budget = b.autotune(ws[0].dt, steps=min(steps, 100))  # register budget, CTAs per SM
     b.step(ws[0].dt, steps)  # capture + warm-up
     b.sync()
     for i, p in enumerate(psis):
@@ -400,6 +401,7 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500):
                         f"{steps} steps",
             "cells": cells, "steps": steps, "value": value, "unit": "cell-steps/s",
             "ms_total": 1e3 * t_batch, "launches": 1,
+            "ctas_per_sm": budget, "ctas_per_sm_source": "sn_autotune_batch over 100 steps",
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "bytes_per_cell_step": 48.0},
             "sequential_fused_ms": 1e3 * t_seq, "speedup_vs_sequential_fused": t_seq / t_batch,

@@ -379,6 +379,12 @@ sn_status sn_set_batch_wait_limit(sn_batch b, long long cycles);
  * waits end whatever the choice; the results are the same bit for bit.
  * Errors: SN_EINVAL (NULL batch, per_sm outside 1..3). */
 sn_status sn_set_batch_ctas(sn_batch b, int per_sm);
+/* Time `steps` merged steps of the batch (steps dt[i]) at each register
+ * budget (3, 2, 1 CTAs per SM), keep the fastest (another budget must beat
+ * the current one by 2 %), and restore every instance's state.  *chosen (if
+ * not NULL) receives the budget kept.  Blocks.  Errors: SN_EINVAL (NULL
+ * batch or dt, steps < 1), SN_ECUDA, SN_ETIMEOUT as sn_batch_sync. */
+sn_status sn_autotune_batch(sn_batch b, const double* dt, int steps, int* chosen);
 /* Kernel launches of this batch (one per sn_step_batch call). */
 long long sn_batch_launch_count(sn_batch b);
 void sn_destroy_batch(sn_batch b);

@@ -623,6 +623,63 @@ sn_status sn_set_batch_ctas(sn_batch b, int per_sm) {
   return SN_OK;
 }
 
+sn_status sn_autotune_batch(sn_batch b, const double* dt, int steps, int* chosen) {
+  if (!b || !dt) return bfail(SN_EINVAL, "sn_autotune_batch: NULL argument");
+  if (steps < 1) return bfail(SN_EINVAL, "sn_autotune_batch: steps must be >= 1");
+  cudaError_t e;
+  // the instances' states, restored after the timed launches
+  size_t total = 0;
+  for (int i = 0; i < b->count; ++i) total += (size_t)b->host_inst[i].n * b->host_inst[i].n;
+  float2* saved = nullptr;
+  if ((e = cudaMalloc(&saved, total * sizeof(float2))) != cudaSuccess)
+    return bcuda(e, "cudaMalloc(autotune copy)");
+  auto copy_all = [&](bool save) {
+    size_t off = 0;
+    for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+      const size_t cells = (size_t)b->host_inst[i].n * b->host_inst[i].n;
+      float2* p = b->host_inst[i].psi;
+      e = cudaMemcpyAsync(save ? saved + off : p, save ? p : saved + off, cells * sizeof(float2),
+                          cudaMemcpyDeviceToDevice, b->stream);
+      off += cells;
+    }
+  };
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  copy_all(true);
+  const int keep = b->cps;
+  int best = keep;
+  float best_ms = 0.f, keep_ms = 0.f;
+  sn_status st = SN_OK;
+  for (int c = 3; c >= 1 && e == cudaSuccess && st == SN_OK; --c) {
+    b->cps = c;
+    b->grid = b->grid_of[c];
+    // the first launch captures this budget's graph; the second is timed
+    if ((st = sn_step_batch(b, dt, steps)) != SN_OK) break;
+    if ((e = cudaEventRecord(t0, b->stream)) != cudaSuccess) break;
+    if ((st = sn_step_batch(b, dt, steps)) != SN_OK) break;
+    if ((e = cudaEventRecord(t1, b->stream)) != cudaSuccess) break;
+    if ((st = sn_batch_sync(b)) != SN_OK) break;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) break;
+    if (c == keep) keep_ms = ms;
+    if (best_ms == 0.f || ms < best_ms) { best_ms = ms; best = c; }
+  }
+  // a budget other than the current one must be at least 2% faster
+  if (keep_ms > 0.f && best != keep && best_ms > 0.98f * keep_ms) best = keep;
+  copy_all(false);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(saved);
+  b->cps = best;
+  b->grid = b->grid_of[best];
+  if (st != SN_OK) return st;
+  if (e != cudaSuccess) return bcuda(e, "sn_autotune_batch");
+  if (chosen) *chosen = best;
+  return SN_OK;
+}
+
 sn_status sn_batch_sync(sn_batch b) {
   if (!b) return bfail(SN_EINVAL, "sn_batch_sync: batch is NULL");
   cudaError_t e = cudaStreamSynchronize(b->stream);

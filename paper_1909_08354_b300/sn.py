@@ -118,6 +118,8 @@ _SIGNATURES = [
     ("sn_batch_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_set_batch_wait_limit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     ("sn_set_batch_ctas", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_autotune_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("sn_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
     ("sn_destroy_batch", None, [ctypes.c_void_p]),
     ("sn_fno_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
@@ -573,6 +575,15 @@ class Batch:
     def set_ctas(self, per_sm: int):
         """Register budget of the launch: 3 (default), 2 or 1 resident CTAs per SM."""
         sn_set_batch_ctas(self.h, per_sm)
+
+    def autotune(self, dt, steps: int = 50) -> int:
+        """Time `steps` steps at each register budget, keep the fastest, restore
+        the states; returns the budget kept (CTAs per SM)."""
+        dts = [float(dt)] * len(self.n) if np.isscalar(dt) else [float(x) for x in dt]
+        arr = (ctypes.c_double * len(dts))(*dts)
+        out = ctypes.c_int(0)
+        _check(None, lib().sn_autotune_batch(self.h, arr, int(steps), ctypes.byref(out)))
+        return out.value
 
     def launch_count(self) -> int:
         return sn_batch_launch_count(self.h)

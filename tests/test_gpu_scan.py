@@ -157,3 +157,37 @@ def test_every_register_budget_gives_the_same_bits():
             assert e.value.status == sn.SN_EINVAL
     finally:
         b.close()
+
+
+def test_batch_autotune_keeps_the_states():
+    sizes = [256, 128, 128, 64, 512]
+    ws = [W.random_small((n, n), seed=500 + i, L=16.0) for i, n in enumerate(sizes)]
+    psis = [w.psi0().astype(np.complex64) for w in ws]
+    b = sn.Batch(sizes, [w.L[0] for w in ws])
+    try:
+        b.set_kernels([kw_of(w.kernel) for w in ws])
+        for i, p in enumerate(psis):
+            b.set_state(i, p)
+        chosen = b.autotune(0.01, steps=5)
+        assert chosen in (1, 2, 3)
+        for i, p in enumerate(psis):
+            assert np.array_equal(b.get_state(i), p), i
+        b.step(0.01, 3)
+        b.sync()
+        tuned = [b.get_state(i).copy() for i in range(len(sizes))]
+    finally:
+        b.close()
+    b = sn.Batch(sizes, [w.L[0] for w in ws])
+    try:
+        b.set_kernels([kw_of(w.kernel) for w in ws])
+        for i, p in enumerate(psis):
+            b.set_state(i, p)
+        b.step(0.01, 3)
+        b.sync()
+        for i in range(len(sizes)):
+            assert np.array_equal(b.get_state(i), tuned[i]), sizes[i]
+        with pytest.raises(sn.SNError) as e:
+            b.autotune(0.01, steps=0)
+        assert e.value.status == sn.SN_EINVAL
+    finally:
+        b.close()
