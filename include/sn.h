@@ -272,7 +272,7 @@ sn_status sn_autotune(sn_grid g, double dt, int steps);
  * has no counterpart of this switch (its FFTs are library calls).
  * Errors: SN_EINVAL (NULL grid, unknown engine), SN_ENOTSUP (TC16 on a
  * complex128 grid), SN_ENOMEM / SN_ECUDA (table upload). */
-typedef enum { SN_ENGINE_FP32 = 0, SN_ENGINE_TC16 = 1 } sn_engine;
+typedef enum { SN_ENGINE_FP32 = 0, SN_ENGINE_TC16 = 1, SN_ENGINE_UMMA = 2 } sn_engine;
 sn_status sn_set_engine(sn_grid g, int engine);
 
 /* How the fused complex64 passes move their tiles of lines between HBM and
@@ -335,6 +335,21 @@ sn_status sn_set_obs_mode(sn_grid g, int mode);
  * sn_last_error(NULL)). */
 sn_status sn_test_line_fft_f32(void* data, long long nlines, int n, int sign, int engine,
                                void* cuda_stream);
+
+/* Test and measurement hook: reps launches of in-place unnormalised DFTs of
+ * nlines contiguous complex64 lines of length n in device memory (the data
+ * is transformed reps times), on one of three line engines:
+ *   SN_ENGINE_FP32, SN_ENGINE_TC16: the fused passes' engines, as
+ *     sn_test_line_fft_f32;
+ *   SN_ENGINE_UMMA (n = 256 only; not an engine of sn_set_engine): both
+ *     radix-16 stages of each line on tcgen05.mma, split-FP16 operands in
+ *     shared memory and FP32 accumulators in tensor memory (Sec. III's FFT in
+ *     the tensor-core form of the split step).
+ * *ms_per_launch (if not NULL) receives the CUDA-event time of one launch.
+ * Synchronous on cuda_stream.  Errors: SN_EINVAL, SN_ECUDA, SN_ETIMEOUT (a
+ * bounded wait of the UMMA kernel expired; the data is incomplete). */
+sn_status sn_test_line_fft_engines(void* data, long long nlines, int n, int sign, int engine,
+                                   int reps, double* ms_per_launch, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------
  * Batched scan: many independent 2D complex64 problems of uneven size

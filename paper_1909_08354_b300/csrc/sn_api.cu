@@ -1350,6 +1350,9 @@ long long sn_launch_count(sn_grid g) { return g ? g->launches : 0; }
 
 sn_status sn_set_engine(sn_grid g, int engine) {
   if (!g) return fail(nullptr, SN_EINVAL, "sn_set_engine: grid is NULL");
+  if (engine == SN_ENGINE_UMMA)
+    return fail(g, SN_ENOTSUP, "sn_set_engine: the tcgen05 line engine runs only in "
+                               "sn_test_line_fft_engines");
   if (engine != SN_ENGINE_FP32 && engine != SN_ENGINE_TC16)
     return fail(g, SN_EINVAL, "sn_set_engine: unknown engine");
   if (engine == SN_ENGINE_TC16 && g->dtype != SN_C64)
@@ -1432,6 +1435,73 @@ sn_status sn_test_line_fft_f32(void* data, long long nlines, int n, int sign, in
     set_thread_error((std::string("sn_test_line_fft_f32: ") + cudaGetErrorString(e)).c_str());
     return SN_ECUDA;
   }
+  return SN_OK;
+}
+
+sn_status sn_test_line_fft_engines(void* data, long long nlines, int n, int sign, int engine,
+                                   int reps, double* ms_per_launch, void* cuda_stream) {
+  const bool umma = engine == SN_ENGINE_UMMA;
+  if (!data || nlines < 0 || reps < 1 || !is_pow2_in_range(n) || (sign != 1 && sign != -1) ||
+      (engine != SN_ENGINE_FP32 && engine != SN_ENGINE_TC16 && !umma) || (umma && n != 256))
+    return fail(nullptr, SN_EINVAL, "sn_test_line_fft_engines: bad argument");
+  if (ms_per_launch) *ms_per_launch = 0.0;
+  if (nlines == 0) return SN_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<float2> tw;
+  std::vector<unsigned> frag;
+  std::vector<uint16_t> bmat;
+  if (umma) {
+    umma_line_tables(sign, bmat, tw);
+  } else {
+    std::vector<double2> t64 = twiddles_f64(n);
+    if (t64.empty()) t64.push_back(make_double2(1.0, 0.0));
+    split_hilo(t64, tw);
+    tc16_fragment_table(frag);
+  }
+  void *dtw = nullptr, *dtab = nullptr, *dstatus = nullptr;
+  const size_t tab_bytes = umma ? bmat.size() * sizeof(uint16_t) : frag.size() * sizeof(unsigned);
+  cudaError_t e = cudaMalloc(&dtw, tw.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&dtab, tab_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&dstatus, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(dstatus, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(dtw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(dtab, umma ? (const void*)bmat.data() : (const void*)frag.data(), tab_bytes,
+                   cudaMemcpyHostToDevice);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  auto launch = [&]() -> cudaError_t {
+    if (umma)
+      return launch_umma_line(static_cast<float2*>(data), nlines, static_cast<const float2*>(dtw), dtab,
+                              static_cast<int*>(dstatus), s);
+    RhoPassArgs ra{};
+    ra.data = static_cast<float2*>(data);
+    ra.outer = nlines;
+    ra.inner = 1;
+    ra.tw = static_cast<const float2*>(dtw);
+    ra.tc = engine == SN_ENGINE_TC16 ? static_cast<const uint4*>(dtab) : nullptr;
+    return launch_rho_pass_f32(n, false, sign < 0 ? RHO_FWD : RHO_INV, ra, s);
+  };
+  if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(dtw);
+  cudaFree(dtab);
+  cudaFree(dstatus);
+  if (e != cudaSuccess) {
+    set_thread_error((std::string("sn_test_line_fft_engines: ") + cudaGetErrorString(e)).c_str());
+    return SN_ECUDA;
+  }
+  if (st != 0) return fail(nullptr, SN_ETIMEOUT, "sn_test_line_fft_engines: a bounded wait expired");
+  if (ms_per_launch) *ms_per_launch = ms / reps;
   return SN_OK;
 }
 

@@ -127,6 +127,14 @@ struct Resident2dArgs {
   int nphase, full, odd;   // the first round: nonlinear phase, full kinetic step, axis order
 };
 bool resident_2d_supported(int ny, int nx);
+
+// ---- the tcgen05 line engine (umma_line.cu), a measurement form ---------------
+// In-place 256-point DFTs (sign as in sn_test_line_fft_f32) of nlines
+// contiguous complex64 lines, both radix-16 stages on tcgen05.mma; tw and bmat
+// from umma_line_tables (device copies); status set to 1 on an expired wait.
+void umma_line_tables(int sign, std::vector<uint16_t>& bmat, std::vector<float2>& tw);
+cudaError_t launch_umma_line(float2* data, long long nlines, const float2* tw, const void* bmat,
+                             int* status, cudaStream_t s);
 cudaError_t launch_resident_2d(int n, const Resident2dArgs& a, cudaStream_t s);
 
 // The potential pass (PSI_NPHASE) and the density pass (PSI_DENSITY) of one

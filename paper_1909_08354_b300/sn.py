@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("SN_LIB_PATH") or os.path.join(_HERE, "libsn.so")
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-SN_ENGINE_FP32, SN_ENGINE_TC16 = 0, 1
+SN_ENGINE_FP32, SN_ENGINE_TC16, SN_ENGINE_UMMA = 0, 1, 2
 SN_STAGING_TMA, SN_STAGING_REGISTERS, SN_STAGING_RESIDENT = 0, 1, 2
 SN_OBS_FP64, SN_OBS_FP32 = 0, 1
 SN_FLOOR_MAX, SN_FLOOR_SMOOTH = 0, 1
@@ -101,6 +101,9 @@ _SIGNATURES = [
     ("sn_get_fields", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_test_line_fft_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("sn_test_line_fft_engines", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("sn_step_2d_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double,
                                           ctypes.POINTER(SnKernel), ctypes.c_double, ctypes.c_int,
@@ -524,6 +527,20 @@ def sn_test_line_fft_f32(data, n: int, sign: int, engine: int = SN_ENGINE_FP32, 
         raise ValueError("data must be a contiguous complex64 CUDA tensor of whole lines")
     _check(None, lib().sn_test_line_fft_f32(data.data_ptr(), data.numel() // n, n, sign, engine,
                                             ctypes.c_void_p(stream) if stream else None))
+
+
+def sn_test_line_fft_engines(data, n: int, sign: int, engine: int, reps: int = 1, stream=None) -> float:
+    """reps in-place unnormalised DFTs of the lines of length n in a contiguous
+    complex64 CUDA tensor on one line engine (SN_ENGINE_UMMA: the tcgen05 form,
+    n = 256); returns the CUDA-event time of one launch in ms."""
+    import torch
+    if not (_is_torch(data) and data.is_cuda and data.dtype == torch.complex64 and data.is_contiguous()):
+        raise ValueError("data must be a contiguous complex64 CUDA tensor")
+    ms = ctypes.c_double(0.0)
+    _check(None, lib().sn_test_line_fft_engines(data.data_ptr(), data.numel() // n, n, sign, engine,
+                                                int(reps), ctypes.byref(ms),
+                                                ctypes.c_void_p(stream) if stream else None))
+    return ms.value
 
 
 def sn_test_gemm_bf16(A, sA, B, sB, C, sC, M, N, K, Z, alpha=1.0, beta=0.0):

@@ -1,0 +1,92 @@
+"""The tcgen05 form of the tensor-core line engine (SN_ENGINE_UMMA).
+
+Both radix-16 stages of each 256-point line run as tcgen05.mma products with
+split-FP16 operands and FP32 accumulators in tensor memory.  Each line's DFT
+must match numpy's to the precision of the split (about 2^-21 per product),
+in both directions, on ragged tiles of lines, zero lines and lines whose
+magnitudes span many decades (the per-row power-of-two scaling); and the
+three line engines are timed on the same lines.
+"""
+import numpy as np
+import pytest
+
+from paper_1909_08354_b300 import sn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def lines(nlines, seed, spread=0.0):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((nlines, 256)) + 1j * rng.standard_normal((nlines, 256))
+    if spread:
+        x *= 10.0 ** rng.uniform(-spread, spread, size=(nlines, 1))
+    return x.astype(np.complex64)
+
+
+def run(x, sign, engine=sn.SN_ENGINE_UMMA):
+    d = torch.from_numpy(x.copy()).cuda()
+    sn.sn_test_line_fft_engines(d, 256, sign, engine)
+    return d.cpu().numpy()
+
+
+def per_line_rel(got, ref):
+    return np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+
+
+@pytest.mark.parametrize("sign", [-1, 1])
+@pytest.mark.parametrize("nlines", [1, 8, 299, 4096])
+def test_umma_lines_match_numpy(sign, nlines):
+    x = lines(nlines, seed=nlines + (sign > 0))
+    got = run(x, sign)
+    x64 = x.astype(np.complex128)
+    ref = np.fft.fft(x64, axis=1) if sign < 0 else np.fft.ifft(x64, axis=1) * 256
+    assert per_line_rel(got, ref).max() <= 2e-6
+
+
+def test_umma_scaling_zero_and_wide_range_lines():
+    x = lines(64, seed=7, spread=15.0)
+    x[5] = 0
+    x[9, :] = 0
+    x[9, 3] = 1e-30
+    got = run(x, -1)
+    ref = np.fft.fft(x.astype(np.complex128), axis=1)
+    assert np.all(got[5] == 0)
+    rel = per_line_rel(got, ref)
+    rel[5] = 0
+    assert rel.max() <= 2e-6
+
+
+def test_umma_engine_is_not_a_grid_engine():
+    g = sn.Grid((16, 16), (1.0, 1.0), "c64")
+    try:
+        with pytest.raises(sn.SNError) as e:
+            g.set_engine(sn.SN_ENGINE_UMMA)
+        assert e.value.status == sn.SN_ENOTSUP
+    finally:
+        g.close()
+    d = torch.zeros(128, dtype=torch.complex64, device="cuda")
+    with pytest.raises(sn.SNError) as e:
+        sn.sn_test_line_fft_engines(d, 128, -1, sn.SN_ENGINE_UMMA)
+    assert e.value.status == sn.SN_EINVAL
+
+
+def test_line_engines_timed_on_the_same_lines():
+    """65536 lines of 256 points (one axis of the 256^3 grid): each engine's
+    time per launch, and its error against numpy on a sample."""
+    x = lines(65536, seed=1)
+    x64 = x[:256].astype(np.complex128)
+    ref = np.fft.fft(x64, axis=1)
+    d = torch.from_numpy(x).cuda()
+    out = {}
+    for engine, name in ((sn.SN_ENGINE_FP32, "fp32"), (sn.SN_ENGINE_TC16, "tc16 mma.sync"),
+                         (sn.SN_ENGINE_UMMA, "tcgen05")):
+        y = d.clone()
+        sn.sn_test_line_fft_engines(y, 256, -1, engine)
+        err = per_line_rel(y[:256].cpu().numpy(), ref).max()
+        ms = sn.sn_test_line_fft_engines(y, 256, -1, engine, reps=10)
+        out[name] = (ms, err)
+        print(f"line engine {name}: {ms * 1e3:.1f} us per launch of 65536 lines, "
+              f"max rel error {err:.2e}")
+        assert err <= 2e-6
