@@ -669,12 +669,20 @@ def run_fno(sn, torch, stream, iters=10):
         net.forward(x, y); net.loss(tgt, B); net.backward(); net.adam(1e-4, it)
     net.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(iters):
+    t_form = {}
+    for form in (sn.SN_FNO_LAYER_GEMMS, sn.SN_FNO_LAYER_UMMA):
+        net.set_layer_form(form)
         net.forward(x, y)
-    e1.record(stream)
-    net.sync()
-    t_fwd = e0.elapsed_time(e1) / 1e3 / iters
+        e0.record(stream)
+        for _ in range(iters):
+            net.forward(x, y)
+        e1.record(stream)
+        net.sync()
+        t_form[form] = e0.elapsed_time(e1) / 1e3 / iters
+    # training in the faster form
+    best = min(t_form, key=t_form.get)
+    net.set_layer_form(best)
+    t_fwd = t_form[best]
     t0 = time.perf_counter()
     for it in range(4, 4 + iters):
         net.forward(x, y); net.loss(tgt, B); net.backward(); net.adam(1e-4, it)
@@ -686,7 +694,12 @@ def run_fno(sn, torch, stream, iters=10):
                        "phase head", "params": n, "batch": B,
             "forward_samples_per_s": B / t_fwd, "train_samples_per_s": B / t_train,
             "train_step_ms": 1e3 * t_train,
-            "gemm": "mma.sync m16n8k16 BF16, FP32 accumulation"}
+            "forward_ms": {"gemm_layers": 1e3 * t_form[sn.SN_FNO_LAYER_GEMMS],
+                           "tcgen05_layers": 1e3 * t_form[sn.SN_FNO_LAYER_UMMA]},
+            "layer_form": "tcgen05" if best == sn.SN_FNO_LAYER_UMMA else "gemms",
+            "gemm": "the layers' inverse DFT along x, 1x1 convolution, bias and GELU: one "
+                    "tcgen05.mma kernel (BF16, FP32 accumulators in tensor memory) or mma.sync "
+                    "m16n8k16 BF16 GEMMs; every other contraction: mma.sync BF16 GEMMs"}
 
 
 REF_MAX_STEPS = 3   # oracle steps at 256^3 take ~25 s each on one host thread

@@ -442,7 +442,23 @@ sn_status sn_fno_loss(sn_fno f, const float* target, int B, double* loss);
 sn_status sn_fno_backward(sn_fno f);
 /* One Adam step with step count t >= 1 (bias-corrected moments). */
 sn_status sn_fno_adam(sn_fno f, double lr, double beta1, double beta2, double eps, int t);
+/* Wait for the network's work.  SN_ETIMEOUT if a bounded wait of the fused
+ * layer kernel (SN_FNO_LAYER_UMMA) expired; the outputs are then incomplete. */
 sn_status sn_fno_sync(sn_fno f);
+/* How the second half of each spectral layer runs: the inverse truncated DFT
+ * along x, the 1x1 convolution, the bias and the activation.
+ *   SN_FNO_LAYER_GEMMS: two strided BF16 GEMMs (mma.sync) and an
+ *     elementwise bias/activation pass;
+ *   SN_FNO_LAYER_UMMA (the default where it applies): one tcgen05 kernel,
+ *     both products as one accumulation
+ *     in tensor memory (BF16 operands, FP32 accumulation) with the bias and
+ *     the activation in its epilogue, three passes over the activations
+ *     instead of six.  Width <= 64, 2 x modes <= 64, s <= 256.
+ * The backward and every other contraction are the same in both forms.
+ * Errors: SN_EINVAL (NULL, unknown form), SN_ENOTSUP (a network the fused
+ * form does not take). */
+typedef enum { SN_FNO_LAYER_GEMMS = 0, SN_FNO_LAYER_UMMA = 1 } sn_fno_layer_form;
+sn_status sn_fno_set_layer_form(sn_fno f, int form);
 void sn_fno_destroy(sn_fno f);
 /* Surrogate input/output marshalling on the device: X[b] = (re psi, im psi,
  * feats[b][0..nfeat-1] as constant planes), planar [B][2+nfeat][cells];

@@ -44,6 +44,10 @@ struct sn_fno_s {
   float *a = nullptr, *A1 = nullptr, *Uh = nullptr, *B1 = nullptr, *g1 = nullptr, *h = nullptr;
   float *out = nullptr, *dout = nullptr, *dv = nullptr, *dv2 = nullptr, *dz = nullptr, *dh = nullptr;
   float *yh = nullptr, *dy = nullptr;  // head channels (phi, dr, di) and their gradient
+  // how a spectral layer's inverse DFT along x, 1x1 convolution, bias and
+  // activation run (sn_fno_set_layer_form), and the fused form's status word
+  int layer_form = SN_FNO_LAYER_GEMMS;  // sn_fno_create takes the fused form where it applies
+  int* status = nullptr;
   float *GU = nullptr, *GV = nullptr, *work = nullptr;
   std::vector<float*> v, z, Vh;
   double* norms = nullptr;  // per sample (||out - t||^2, ||t||^2)
@@ -442,17 +446,25 @@ cudaError_t dft_forward(sn_fno f, const float* X, int B, int Cn, const float* Ex
               2 * f->Nm, m, 1, 1.f, 1.f);
 }
 
+// the inverse DFT along y of modes U[B][C][2][Nm]: B1[B][C][s][2m], per row y
+// the coefficients (re q | im q) of the inverse DFT along x
+cudaError_t dft_inverse_y(sn_fno f, const float* U, int B, int Cn) {
+  const int s = f->s, m = f->m;
+  const ll planes = (ll)B * Cn;
+  // per plane: B1re (s x m) = EyIre (s x 4m) U (4m x m); B1im likewise; B1 is [y][re|im][q]
+  cudaError_t e = gemm(f, s, m, 4 * m, (int)planes, f->EyIre, 0, 4 * m, 1, U, 2 * f->Nm, m, 1,
+                       f->B1, (ll)s * 2 * m, 2 * m, 1);
+  if (e != cudaSuccess) return e;
+  return gemm(f, s, m, 4 * m, (int)planes, f->EyIim, 0, 4 * m, 1, U, 2 * f->Nm, m, 1, f->B1 + m,
+              (ll)s * 2 * m, 2 * m, 1);
+}
+
 // planes Y[B][C][s][s] (=, or += with beta) from modes U[B][C][2][Nm]; Wx: 2m x s
 cudaError_t dft_inverse(sn_fno f, const float* U, int B, int Cn, const float* Wx, float* Y,
                         float beta) {
   const int s = f->s, m = f->m;
   const ll planes = (ll)B * Cn;
-  // along y, per plane: B1re (s x m) = EyIre (s x 4m) U (4m x m); B1im likewise; B1 is [y][re|im][q]
-  cudaError_t e = gemm(f, s, m, 4 * m, (int)planes, f->EyIre, 0, 4 * m, 1, U, 2 * f->Nm, m, 1,
-                       f->B1, (ll)s * 2 * m, 2 * m, 1);
-  if (e != cudaSuccess) return e;
-  e = gemm(f, s, m, 4 * m, (int)planes, f->EyIim, 0, 4 * m, 1, U, 2 * f->Nm, m, 1, f->B1 + m,
-           (ll)s * 2 * m, 2 * m, 1);
+  cudaError_t e = dft_inverse_y(f, U, B, Cn);
   if (e != cudaSuccess) return e;
   // along x: Y (planes*s x s) = B1 (planes*s x 2m) Wx (2m x s)
   return gemm(f, (int)(planes * s), s, 2 * m, 1, f->B1, 0, 2 * m, 1, Wx, 0, s, 1, Y, 0, s, 1, 1.f,
@@ -587,6 +599,8 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
   }
   ok = ok && falloc(f, &f->A1, B * C * s * 2LL * modes) == cudaSuccess;
   ok = ok && falloc(f, &f->B1, B * C * s * 2LL * modes) == cudaSuccess;
+  ok = ok && cudaMalloc(&f->status, sizeof(int)) == cudaSuccess &&
+       cudaMemset(f->status, 0, sizeof(int)) == cudaSuccess;
   ok = ok && falloc(f, &f->Uh, B * C * 2 * Nm) == cudaSuccess;
   ok = ok && falloc(f, &f->GU, B * C * 2 * Nm) == cudaSuccess;
   ok = ok && falloc(f, &f->GV, B * C * 2 * Nm) == cudaSuccess;
@@ -617,6 +631,7 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
                                     (int)sm_bwd) == cudaSuccess;
   }
   if (!ok) return bail(ffail(SN_ENOMEM, "sn_fno_create: device allocation failed"));
+  if (fno_layer_umma_supported(f->C, 2 * f->m, f->s)) f->layer_form = SN_FNO_LAYER_UMMA;
   *out = f;
   return SN_OK;
 }
@@ -671,10 +686,17 @@ sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
   for (int l = 0; l < f->L; ++l) {
     FCHK(dft_forward(f, f->v[l], B, (int)C, f->ExF, f->Vh[l]));
     FCHK(mode_mix(f, f->Vh[l], prm + f->off_R[l], B, f->Uh));
+    const int act = l < f->L - 1 ? 1 : 0;
+    if (f->layer_form == SN_FNO_LAYER_UMMA) {
+      // the inverse DFT along x, the 1x1 convolution, bias and activation in one kernel
+      FCHK(dft_inverse_y(f, f->Uh, B, (int)C));
+      FCHK(launch_fno_layer_umma(f->v[l], f->B1, f->WxI, prm + f->off_W[l], prm + f->off_b[l],
+                                 f->z[l], f->v[l + 1], B, (int)C, f->s, 2 * f->m, act, f->status, st));
+      continue;
+    }
     FCHK(dft_inverse(f, f->Uh, B, (int)C, f->WxI, f->z[l], 0.f));
     FCHK(gemm(f, (int)C, (int)P, (int)C, B, prm + f->off_W[l], 0, C, 1, f->v[l], C * P, P, 1, f->z[l], C * P, P, 1, 1.f, 1.f));
-    bias_act_kernel<<<rows_grid(B * C, P), 256, 0, st>>>(f->z[l], prm + f->off_b[l], f->v[l + 1], C, P,
-                                                          l < f->L - 1 ? 1 : 0);
+    bias_act_kernel<<<rows_grid(B * C, P), 256, 0, st>>>(f->z[l], prm + f->off_b[l], f->v[l + 1], C, P, act);
     FCHK(cudaGetLastError());
   }
   // projection
@@ -760,12 +782,30 @@ sn_status sn_fno_adam(sn_fno f, double lr, double beta1, double beta2, double ep
 sn_status sn_fno_sync(sn_fno f) {
   if (!f) return ffail(SN_EINVAL, "sn_fno_sync: NULL");
   FCHK(cudaStreamSynchronize(f->stream));
+  int st = 0;
+  FCHK(cudaMemcpy(&st, f->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    cudaMemset(f->status, 0, sizeof(int));
+    return ffail(SN_ETIMEOUT, "sn_fno_sync: a bounded wait of the fused layer kernel expired");
+  }
+  return SN_OK;
+}
+
+sn_status sn_fno_set_layer_form(sn_fno f, int form) {
+  if (!f) return ffail(SN_EINVAL, "sn_fno_set_layer_form: NULL");
+  if (form != SN_FNO_LAYER_GEMMS && form != SN_FNO_LAYER_UMMA)
+    return ffail(SN_EINVAL, "sn_fno_set_layer_form: unknown form");
+  if (form == SN_FNO_LAYER_UMMA && !fno_layer_umma_supported(f->C, 2 * f->m, f->s))
+    return ffail(SN_ENOTSUP, "sn_fno_set_layer_form: the fused layer takes width <= 64, 2 modes <= 64, "
+                             "s <= 256");
+  f->layer_form = form;
   return SN_OK;
 }
 
 void sn_fno_destroy(sn_fno f) {
   if (!f) return;
   if (f->stream) cudaStreamSynchronize(f->stream);
+  if (f->status) cudaFree(f->status);
   for (void* p : f->allocs) cudaFree(p);
   if (f->own_stream && f->stream) cudaStreamDestroy(f->stream);
   delete f;

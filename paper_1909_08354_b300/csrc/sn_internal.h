@@ -135,6 +135,14 @@ bool resident_2d_supported(int ny, int nx);
 void umma_line_tables(int sign, std::vector<uint16_t>& bmat, std::vector<float2>& tw);
 cudaError_t launch_umma_line(float2* data, long long nlines, const float2* tw, const void* bmat,
                              int* status, cudaStream_t s);
+
+// ---- the fused FNO layer (fno_layer_umma.cu) --------------------------------------
+// z = WxI^T B1 + W v + bias and vout = act ? GELU(z) : z for every (b, o, y, x)
+// of a spectral layer (layouts as in fno.cu); tcgen05.mma with BF16 operands.
+bool fno_layer_umma_supported(int C, int Q, int s);
+cudaError_t launch_fno_layer_umma(const float* v, const float* B1, const float* WxI, const float* W,
+                                  const float* bias, float* z, float* vout, int B, int C, int s, int Q,
+                                  int act, int* status, cudaStream_t st);
 cudaError_t launch_resident_2d(int n, const Resident2dArgs& a, cudaStream_t s);
 
 // The potential pass (PSI_NPHASE) and the density pass (PSI_DENSITY) of one

@@ -21,6 +21,7 @@ SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 
 SN_ENGINE_FP32, SN_ENGINE_TC16, SN_ENGINE_UMMA = 0, 1, 2
 SN_STAGING_TMA, SN_STAGING_REGISTERS, SN_STAGING_RESIDENT = 0, 1, 2
 SN_OBS_FP64, SN_OBS_FP32 = 0, 1
+SN_FNO_LAYER_GEMMS, SN_FNO_LAYER_UMMA = 0, 1
 SN_FLOOR_MAX, SN_FLOOR_SMOOTH = 0, 1
 SN_C64, SN_C128 = 0, 1
 SN_KERNEL_NMC, SN_KERNEL_POISSON = 0, 1
@@ -139,6 +140,7 @@ _SIGNATURES = [
     ("sn_fno_backward", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_fno_adam", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+    ("sn_fno_set_layer_form", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("sn_fno_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_fno_destroy", None, [ctypes.c_void_p]),
     ("sn_fno_pack", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
@@ -451,6 +453,10 @@ class Fno:
 
     def sync(self):
         _check(None, lib().sn_fno_sync(self.h))
+
+    def set_layer_form(self, form: int):
+        """SN_FNO_LAYER_GEMMS or SN_FNO_LAYER_UMMA (the fused tcgen05 layer)."""
+        _check(None, lib().sn_fno_set_layer_form(self.h, int(form)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -82,15 +82,17 @@ def rel(a, b):
 FWD_TOL, GRAD_TOL = 2e-2, 1e-2
 
 
+@pytest.mark.parametrize("form", [sn.SN_FNO_LAYER_GEMMS, sn.SN_FNO_LAYER_UMMA], ids=["gemms", "tcgen05"])
 @pytest.mark.parametrize("sh,rscale,group_tol", [(SMALL, 30.0, 2e-2), (PROD, 10.0, 1e-2)],
                          ids=["small", "production"])
-def test_forward_and_gradients_match_oracle(sh, rscale, group_tol):
+def test_forward_and_gradients_match_oracle(sh, rscale, group_tol, form):
     p, a, t = problem(sh, rscale=rscale)
     out_ref, cache = F.forward(p, a, sh)
     loss_ref, dout = F.rel_l2_loss(out_ref, t)
     g_ref = F.backward(p, cache, dout, sh)
     net = make_net(sh, 2)
     try:
+        net.set_layer_form(form)
         net.set_params(F.flatten(sh, p).astype(np.float32))
         x = torch.from_numpy(a.astype(np.float32)).cuda()
         y = torch.empty((2, 2, sh.s, sh.s), dtype=torch.float32, device="cuda")
@@ -163,3 +165,35 @@ def test_set_grads_feeds_adam():
         assert np.all(step[::7] == 0.0)
     finally:
         net.close()
+
+
+def test_fused_layer_matches_the_gemm_layers_at_256():
+    """The surrogate's own network at 256^2: the tcgen05 layer form gives the
+    GEMM form's forward to BF16 rounding and is timed against it."""
+    sh = F.FnoShape(s=256, c_in=5, width=64, modes=24, layers=4, proj=128)
+    rng = np.random.default_rng(3)
+    p = F.init_params(sh, 2)
+    a = rng.standard_normal((4, sh.c_in, sh.s, sh.s)).astype(np.float32)
+    x = torch.from_numpy(a).cuda()
+    outs, ms = {}, {}
+    for form in (sn.SN_FNO_LAYER_GEMMS, sn.SN_FNO_LAYER_UMMA):
+        net = make_net(sh, 4)
+        try:
+            net.set_layer_form(form)
+            net.set_params(F.flatten(sh, p).astype(np.float32))
+            y = torch.empty((4, 2, sh.s, sh.s), dtype=torch.float32, device="cuda")
+            net.forward(x, y)
+            net.sync()
+            import time
+            t0 = time.perf_counter()
+            for _ in range(5):
+                net.forward(x, y)
+            net.sync()
+            ms[form] = (time.perf_counter() - t0) / 5 * 1e3
+            outs[form] = y.cpu().numpy()
+        finally:
+            net.close()
+    d = rel(outs[sn.SN_FNO_LAYER_UMMA], outs[sn.SN_FNO_LAYER_GEMMS])
+    print(f"FNO 256^2 forward, batch 4: GEMM layers {ms[sn.SN_FNO_LAYER_GEMMS]:.3f} ms, "
+          f"tcgen05 layers {ms[sn.SN_FNO_LAYER_UMMA]:.3f} ms, rel difference {d:.2e}")
+    assert d <= 1e-2
