@@ -177,6 +177,25 @@ __global__ void __launch_bounds__(kThreads, 2) fno_layer_kernel(LayerArgs a) {
     const int x = h * kRows + row;
     unsigned char* A2 = sm + P.a2[u];
     const size_t plane = (size_t)s * s;
+    if ((s & 3) == 0) {
+      // float4 along x: warp g takes channels 8 g .. 8 g + 7, lane l the four
+      // rows 4 l .. 4 l + 3 (a warp's load is 512 contiguous bytes)
+      const int g = tid >> 5, l = tid & 31;
+      const int xr = h * kRows + 4 * l;
+      for (int cb = 8 * g; cb < P.K2; cb += 8 * (kThreads / 32)) {
+        const float* vp4 = a.v + ((size_t)b * C * s + y) * s + xr + (size_t)cb * plane;
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+          float4 p0 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p0;
+          if (xr < s && cb + c < C) p0 = __ldg(reinterpret_cast<const float4*>(vp4 + (size_t)c * plane));
+          if (xr < s && cb + c + 1 < C) p1 = __ldg(reinterpret_cast<const float4*>(vp4 + (size_t)(c + 1) * plane));
+          put_bf16x2(A2, opo(4 * l + 0, cb + c, P.K2), p0.x, p1.x);
+          put_bf16x2(A2, opo(4 * l + 1, cb + c, P.K2), p0.y, p1.y);
+          put_bf16x2(A2, opo(4 * l + 2, cb + c, P.K2), p0.z, p1.z);
+          put_bf16x2(A2, opo(4 * l + 3, cb + c, P.K2), p0.w, p1.w);
+        }
+      }
+    } else {
     const int ch = P.K2 / 2, c0 = part * ch;  // my channels [c0, c0 + ch)
     const int cend = min(c0 + ch, x < s ? C : 0);  // channels with data; the rest are zero
     const float* vp = a.v + ((size_t)b * C * s + y) * s + x + (size_t)c0 * plane;
@@ -190,6 +209,7 @@ __global__ void __launch_bounds__(kThreads, 2) fno_layer_kernel(LayerArgs a) {
       const float w0 = c < cend ? vp[0] : 0.f;
       put_bf16x2(A2, opo(row, c, P.K2), w0, 0.f);
       vp += 2 * plane;
+    }
     }
 
     unsigned char* B1s = sm + P.b1[u];
