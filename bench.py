@@ -89,6 +89,8 @@ def parse():
     p.add_argument("--scan-count", type=int, default=96, help="instances of the batched scan")
     p.add_argument("--scan-steps", type=int, default=500, help="steps of the batched scan")
     p.add_argument("--no-tc", action="store_true")
+    p.add_argument("--no-f2", action="store_true",
+                   help="skip the plane-resident / slab-blocked schedule timings")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the 128^3 collision (c64, c128) and the alpha_Y = 0, 0.5 runs")
     p.add_argument("--engine", choices=["fp32", "tc16"], default="fp32",
@@ -458,6 +460,62 @@ def run_configs(sn, torch, stream, peak, main_value):
         t = time_grid_steps(sn, torch, stream, w, "c64", 200)
         out[f"nbody_256_alpha_{alpha:g}"] = {"value": w.cells / t, "unit": UNIT,
                                              "ms_per_step": 1e3 * t}
+    return out
+
+
+def run_f2(sn, torch, stream, peak):
+    """The plane-resident and plane-blocked schedules against the tiled one:
+    the 64^2 and 128^2 grids resident in one CTA for a whole call, the 256^3
+    step with its y/x pass pair blocked by slabs of z, and the distributed
+    shared-memory rates a cluster-resident plane would exchange at."""
+    out = {}
+    for n in (64, 128):
+        w = W.random_small((n, n), seed=21)
+        dt = 0.01
+        row = {}
+        for mode, name in ((sn.SN_STAGING_TMA, "tiled"), (sn.SN_STAGING_RESIDENT, "resident")):
+            g = sn.Grid(w.n, w.L, "c64", stream=stream.cuda_stream)
+            try:
+                g.set_staging(mode)
+                g.set_kernel(**kernel_kw(w.kernel))
+                g.set_state(w.psi0().astype(np.complex64))
+                g.step(dt, 20)
+                best = float("inf")
+                for _ in range(3):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    g.sync()
+                    e0.record(stream)
+                    g.step(dt, 1000)
+                    e1.record(stream)
+                    e1.synchronize()
+                    best = min(best, e0.elapsed_time(e1) / 1e3 / 1000)
+                row[name + "_us_per_step"] = 1e6 * best
+            finally:
+                g.close()
+        out[f"grid_{n}x{n}"] = row
+    wb = W.nbody_3d()
+    blk = {}
+    for planes in (0, 128, 64, 16):
+        g = sn.Grid(wb.n, wb.L, "c64", stream=stream.cuda_stream)
+        try:
+            g.set_blocking(planes)
+            g.set_kernel(**kernel_kw(wb.kernel))
+            g.set_state(wb.psi0().astype(np.complex64))
+            g.step(wb.dt, 5)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            g.sync()
+            e0.record(stream)
+            g.step(wb.dt, 100)
+            e1.record(stream)
+            e1.synchronize()
+            blk[str(planes)] = e0.elapsed_time(e1) / 100
+        finally:
+            g.close()
+    out["nbody_256_ms_per_step_by_slab_planes"] = blk
+    out["dsmem_cluster_4_gbs"] = sn.sn_test_dsmem_rates(4)
+    out["hbm_peak_gbs"] = peak
     return out
 
 
@@ -870,6 +928,9 @@ def main():
     configs = None
     if not args.no_configs and world == 1 and args.n == 256:
         configs = run_configs(sn, torch, stream, peak, value / world)
+    f2 = None
+    if not args.no_f2 and world == 1 and args.n == 256:
+        f2 = run_f2(sn, torch, stream, peak)
 
     tc = None
     if not args.no_tc and args.n == 256 and args.engine == "fp32":
@@ -945,6 +1006,7 @@ def main():
             "speedup_vs_fp64_plain": (value / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu,
             "other_configs": configs,
+            "f2_schedules": f2,
             "tensor_core_engine": tc,
             "optical_kernel": optical,
             "fluid_model": fluid,

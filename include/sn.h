@@ -351,6 +351,17 @@ sn_status sn_test_line_fft_f32(void* data, long long nlines, int n, int sign, in
 sn_status sn_test_line_fft_engines(void* data, long long nlines, int n, int sign, int engine,
                                    int reps, double* ms_per_launch, void* cuda_stream);
 
+/* Measurement hook: the distributed-shared-memory rates of thread-block
+ * clusters of cluster_size CTAs (2, 4 or 8), as many clusters as are
+ * resident, one CTA per SM.  rates[0]: float4 reads of a peer's 128 KB of
+ * shared memory (map_shared_rank), rates[1]: the same reads of the CTA's own,
+ * rates[2]: bulk copies (cp.async.bulk.shared::cluster) pushed into a peer's
+ * shared memory; aggregate GB/s over the GPU.  These are the exchange rates
+ * of a plane held across a cluster (Sec. III's transposes between the axis
+ * passes of one plane).  Blocks.  Errors: SN_EINVAL, SN_ECUDA, SN_ETIMEOUT (a
+ * bounded copy wait expired). */
+sn_status sn_test_dsmem_rates(int cluster_size, double* rates);
+
 /* ---------------------------------------------------------------------------
  * Batched scan: many independent 2D complex64 problems of uneven size
  * advanced together (Sec. III step applied to each; e.g. a scan over the

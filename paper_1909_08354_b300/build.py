@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsn.so")
 
-SOURCES = ["sn_api.cu", "passes_f32.cu", "passes_tma.cu", "resident_2d.cu", "obs_f32.cu", "umma_line.cu", "fno_layer_umma.cu", "plain_f64.cu", "fluid_f64.cu", "noalloc.cu", "scan.cu", "scan_k1.cu", "scan_k2.cu", "scan_k3.cu",
+SOURCES = ["sn_api.cu", "passes_f32.cu", "passes_tma.cu", "resident_2d.cu", "obs_f32.cu", "umma_line.cu", "fno_layer_umma.cu", "dsmem_rate.cu", "plain_f64.cu", "fluid_f64.cu", "noalloc.cu", "scan.cu", "scan_k1.cu", "scan_k2.cu", "scan_k3.cu",
            "gemm_bf16.cu", "fno.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,

@@ -140,6 +140,13 @@ cudaError_t launch_umma_line(float2* data, long long nlines, const float2* tw, c
 // z = WxI^T B1 + W v + bias and vout = act ? GELU(z) : z for every (b, o, y, x)
 // of a spectral layer (layouts as in fno.cu); tcgen05.mma with BF16 operands.
 bool fno_layer_umma_supported(int C, int Q, int s);
+
+// ---- distributed shared memory rates (dsmem_rate.cu) ---------------------------
+// Aggregate GB/s over the GPU for clusters of csize CTAs: remote float4 reads
+// of a peer's shared memory, the same reads of a CTA's own, and bulk copies
+// pushed into a peer's shared memory.  cudaErrorLaunchTimeout if a bounded
+// copy wait expired.
+cudaError_t measure_dsmem(int csize, double* read_remote, double* read_local, double* push);
 cudaError_t launch_fno_layer_umma(const float* v, const float* B1, const float* WxI, const float* W,
                                   const float* bias, float* z, float* vout, int B, int C, int s, int Q,
                                   int act, int* status, cudaStream_t st);

@@ -102,6 +102,7 @@ _SIGNATURES = [
     ("sn_get_fields", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_test_line_fft_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("sn_test_dsmem_rates", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("sn_test_line_fft_engines", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
@@ -533,6 +534,14 @@ def sn_test_line_fft_f32(data, n: int, sign: int, engine: int = SN_ENGINE_FP32, 
         raise ValueError("data must be a contiguous complex64 CUDA tensor of whole lines")
     _check(None, lib().sn_test_line_fft_f32(data.data_ptr(), data.numel() // n, n, sign, engine,
                                             ctypes.c_void_p(stream) if stream else None))
+
+
+def sn_test_dsmem_rates(cluster_size: int) -> dict:
+    """Distributed-shared-memory rates of clusters of cluster_size CTAs (see
+    sn_test_dsmem_rates in include/sn.h): aggregate GB/s."""
+    out = (ctypes.c_double * 3)()
+    _check(None, lib().sn_test_dsmem_rates(int(cluster_size), out))
+    return {"remote_read_gbs": out[0], "local_read_gbs": out[1], "push_gbs": out[2]}
 
 
 def sn_test_line_fft_engines(data, n: int, sign: int, engine: int, reps: int = 1, stream=None) -> float:
