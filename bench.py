@@ -310,7 +310,7 @@ def time_observables(sn, torch, g, reps=5):
     return out
 
 
-def run_scan(sn, torch, stream, peak, count=96, steps=500):
+def run_scan(sn, torch, stream, peak, count=96, steps=500, no_autotune=False):
     """The batched parameter scan: 96 2D instances (128^2..1024^2), 500 steps, one launch.
     With several ranks the instances are partitioned by cost (n^2 log n) and each
     rank advances its share in one launch; the time is the slowest rank's."""
@@ -349,7 +349,7 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500):
     b.set_kernels(kws)
     for i, p in enumerate(psis):
         b.set_state(i, p)
-    budget = b.autotune(ws[0].dt, steps=min(steps, 100))  # register budget, CTAs per SM
+    budget = 3 if no_autotune else b.autotune(ws[0].dt, steps=min(steps, 100))  # CTAs per SM
     b.step(ws[0].dt, steps)  # capture + warm-up
     b.sync()
     for i, p in enumerate(psis):
@@ -403,7 +403,8 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500):
                         f"{steps} steps",
             "cells": cells, "steps": steps, "value": value, "unit": "cell-steps/s",
             "ms_total": 1e3 * t_batch, "launches": 1,
-            "ctas_per_sm": budget, "ctas_per_sm_source": "sn_autotune_batch over 100 steps",
+            "ctas_per_sm": budget,
+            "ctas_per_sm_source": "default" if no_autotune else "sn_autotune_batch over 100 steps",
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "bytes_per_cell_step": 48.0},
             "sequential_fused_ms": 1e3 * t_seq, "speedup_vs_sequential_fused": t_seq / t_batch,
@@ -950,7 +951,7 @@ def main():
 
     scan = None
     if not args.no_scan:
-        scan = run_scan(sn, torch, stream, peak, args.scan_count, args.scan_steps)
+        scan = run_scan(sn, torch, stream, peak, args.scan_count, args.scan_steps, args.no_autotune)
 
     fno = None
     if not args.no_fno and world == 1:
