@@ -90,3 +90,27 @@ def test_line_engines_timed_on_the_same_lines():
         print(f"line engine {name}: {ms * 1e3:.1f} us per launch of 65536 lines, "
               f"max rel error {err:.2e}")
         assert err <= 2e-6
+
+
+def test_round_trip_norm_drift_of_the_engines():
+    """Forward then inverse (scaled by 1/256), 100 times, on 4096 lines: the
+    FP32 engine keeps the norm to rounding; the tcgen05 stages, whose FP32
+    accumulation in tensor memory shrinks each product, lose it steadily (the
+    bias the mma.sync engine takes back with its Parseval correction)."""
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal((4096, 256)) + 1j * rng.standard_normal((4096, 256))).astype(np.complex64)
+    n0 = np.sum(np.abs(x.astype(np.complex128)) ** 2)
+    drift = {}
+    for engine in (sn.SN_ENGINE_FP32, sn.SN_ENGINE_TC16, sn.SN_ENGINE_UMMA):
+        d = torch.from_numpy(x.copy()).cuda()
+        for _ in range(100):
+            sn.sn_test_line_fft_engines(d, 256, -1, engine)
+            sn.sn_test_line_fft_engines(d, 256, +1, engine)
+            d.mul_(1.0 / 256)
+        y = d.cpu().numpy().astype(np.complex128)
+        drift[engine] = np.sum(np.abs(y) ** 2) / n0 - 1
+    print("norm drift over 100 round trips: FP32 %.2e, mma.sync %.2e, tcgen05 %.2e"
+          % (drift[sn.SN_ENGINE_FP32], drift[sn.SN_ENGINE_TC16], drift[sn.SN_ENGINE_UMMA]))
+    assert abs(drift[sn.SN_ENGINE_FP32]) < 1e-7
+    assert abs(drift[sn.SN_ENGINE_TC16]) < 1e-5
+    assert -1e-3 < drift[sn.SN_ENGINE_UMMA] < -1e-6
