@@ -22,6 +22,10 @@
 // wait sets the status word to 1, waits again, bounded, frees the tensor
 // memory and returns).
 //
+// Each line's output is rescaled to 256 times its input's squared norm
+// (Parseval): the tensor memory's FP32 accumulation loses a little of every
+// product, always in the same direction.
+//
 // This is the measurement form of the tcgen05 engine (sn_test_line_fft_engines);
 // the fused passes keep the FP32 and mma.sync engines.
 #include <cuda_fp16.h>
@@ -192,6 +196,13 @@ __global__ void __launch_bounds__(kThreads, 4) umma_line_kernel(UmmaArgs a) {
       xi[r] = z.y;
       mx = fmaxf(mx, fmaxf(fabsf(z.x), fabsf(z.y)));
     }
+    // the line's squared norm (its 16 threads are one half-warp): the output
+    // must carry 256 times it (Parseval)
+    float n_in = 0.f;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) n_in = fmaf(xr[r], xr[r], fmaf(xi[r], xi[r], n_in));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) n_in += __shfl_xor_sync(0xffffffffu, n_in, o);
     const int ea = row_exponent(mx);
     const float sa = ldexpf(1.f, -ea);
 #pragma unroll
@@ -240,11 +251,22 @@ __global__ void __launch_bounds__(kThreads, 4) umma_line_kernel(UmmaArgs a) {
     }
     tc_fence_after();
     tmem_ld32(my_rows, d);
-    // X[k1 + 16 k2] with k1 = c
+    // X[k1 + 16 k2] with k1 = c, rescaled so that the line keeps 256 times
+    // its input norm: the products' accumulation loses a little of it, always
+    // in the same direction, and a per-line factor above half an FP32 ulp
+    // takes the loss back on average
+    float n_out = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) n_out = fmaf(d[k], d[k], n_out);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) n_out += __shfl_xor_sync(0xffffffffu, n_out, o);
     const float ub = ldexpf(1.f, eb);
+    const float want = 256.f * n_in, have = n_out * ub * ub;
+    const float fix = (have > 0.f && want > 0.f) ? sqrtf(want / have) : 1.f;
+    const float ubf = ub * fix;
     if (valid) {
 #pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) row[c + 16 * k2] = make_float2(d[2 * k2] * ub, d[2 * k2 + 1] * ub);
+      for (int k2 = 0; k2 < 16; ++k2) row[c + 16 * k2] = make_float2(d[2 * k2] * ubf, d[2 * k2 + 1] * ubf);
     }
     tc_fence_before();
     __syncthreads();  // the accumulators are read before the next tile's products
