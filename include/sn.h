@@ -460,8 +460,9 @@ sn_status sn_fno_sync(sn_fno f);
  * along x, the 1x1 convolution, the bias and the activation.
  *   SN_FNO_LAYER_GEMMS: two strided BF16 GEMMs (mma.sync) and an
  *     elementwise bias/activation pass;
- *   SN_FNO_LAYER_UMMA (the default where it applies): one tcgen05 kernel,
- *     both products as one accumulation
+ *   SN_FNO_LAYER_UMMA (the default where it applies): one tcgen05 kernel
+ *     (and its backward form, W^T and GELU' of the layer below), both products
+ *     as one accumulation
  *     in tensor memory (BF16 operands, FP32 accumulation) with the bias and
  *     the activation in its epilogue, three passes over the activations
  *     instead of six.  Width <= 64, 2 x modes <= 64, s <= 256.

@@ -691,7 +691,8 @@ sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
       // the inverse DFT along x, the 1x1 convolution, bias and activation in one kernel
       FCHK(dft_inverse_y(f, f->Uh, B, (int)C));
       FCHK(launch_fno_layer_umma(f->v[l], f->B1, f->WxI, prm + f->off_W[l], prm + f->off_b[l],
-                                 f->z[l], f->v[l + 1], B, (int)C, f->s, 2 * f->m, act, f->status, st));
+                                 f->z[l], f->v[l + 1], nullptr, B, (int)C, f->s, 2 * f->m, act, 0,
+                                 f->status, st));
       continue;
     }
     FCHK(dft_inverse(f, f->Uh, B, (int)C, f->WxI, f->z[l], 0.f));
@@ -747,6 +748,28 @@ sn_status sn_fno_backward(sn_fno f) {
   FCHK(weight_grad(f, f->dh, f->v[f->L], B, (int)J, (int)C, gr + f->off_Q1));
   channel_sum(f, f->dh, B, J, P, gr + f->off_q1b);
   FCHK(gemm(f, (int)C, (int)P, (int)J, B, prm + f->off_Q1, 0, 1, C, f->dh, J * P, P, 1, f->dv, C * P, P, 1));
+  if (f->layer_form == SN_FNO_LAYER_UMMA) {
+    // dz of the last layer is dv (no activation after it); each layer's fused
+    // kernel leaves the next one's dz: (W^T dz + the spectral branch) times
+    // GELU' of the layer below, or, below layer 0, the lift's gradient dv
+    float* dz = f->dv;
+    float* nxt = f->dz;
+    for (int l = f->L - 1; l >= 0; --l) {
+      FCHK(weight_grad(f, dz, f->v[l], B, (int)C, (int)C, gr + f->off_W[l]));
+      channel_sum(f, dz, B, C, P, gr + f->off_b[l]);
+      FCHK(dft_forward(f, dz, B, (int)C, f->ExFw, f->GU));
+      FCHK(mode_mix_bwd(f, f->Vh[l], prm + f->off_R[l], f->GU, B, gr + f->off_R[l], f->GV));
+      FCHK(dft_inverse_y(f, f->GV, B, (int)C));
+      FCHK(launch_fno_layer_umma(dz, f->B1, f->WxI1, prm + f->off_W[l], nullptr, nullptr, nxt,
+                                 l > 0 ? f->z[l - 1] : nullptr, B, (int)C, f->s, 2 * f->m, 0, 1,
+                                 f->status, st));
+      std::swap(dz, nxt);
+    }
+    FCHK(weight_grad(f, dz, f->a, B, (int)C, (int)ci, gr + f->off_P));
+    channel_sum(f, dz, B, C, P, gr + f->off_pb);
+    FCHK(cudaGetLastError());
+    return SN_OK;
+  }
   for (int l = f->L - 1; l >= 0; --l) {
     const float* dz = f->dv;
     if (l < f->L - 1) {

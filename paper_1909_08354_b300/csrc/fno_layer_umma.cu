@@ -97,16 +97,23 @@ __device__ __forceinline__ void put_bf16x2(unsigned char* base, unsigned off, fl
 
 // GELU, the erf form of the network's other activation passes
 __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+// its derivative, the form of the network's other backward passes
+__device__ __forceinline__ float gelu_grad_erf(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
 
 struct LayerArgs {
-  const float* v;    // [B][C][s][s] layer input
+  const float* v;    // [B][C][s][s] layer input (backward: the gradient dz)
   const float* B1;   // [B][C][s][2m] the inverse DFT along y, per row
   const float* WxI;  // [2m][s] inverse DFT along x
   const float* W;    // [C][C] 1x1 weights W[o][c]
-  const float* bias; // [C]
-  float* z;          // [B][C][s][s] pre-activation (with the bias)
-  float* vout;       // [B][C][s][s] activation
+  const float* bias; // [C] (forward)
+  float* z;          // [B][C][s][s] forward: the pre-activation (with the bias)
+  float* vout;       // [B][C][s][s] forward: the activation; backward: the gradient out
+  const float* zp;   // backward: the previous layer's pre-activation (its GELU' scales
+                     // the gradient), or NULL for none
   int B, C, s, Q, act;
+  int back;          // 1: the backward form (W transposed, no bias, vout = D GELU'(zp))
   int* status;
 };
 
@@ -148,7 +155,9 @@ __global__ void __launch_bounds__(kThreads, 2) fno_layer_kernel(LayerArgs a) {
   }
   for (int i = tid; i < P.N * P.K2; i += kThreads) {
     const int o = i / P.K2, c = i % P.K2;
-    put_bf16(sm + P.b2, opo(o, c, P.K2), (o < C && c < C) ? a.W[(long long)o * C + c] : 0.f);
+    // forward: W[o][c]; backward: the transpose, W[c][o]
+    const long long wi = a.back ? (long long)c * C + o : (long long)o * C + c;
+    put_bf16(sm + P.b2, opo(o, c, P.K2), (o < C && c < C) ? a.W[wi] : 0.f);
   }
   if (tid == 0) {
     tma::mbar_init(&bar[0], 1);
@@ -276,7 +285,13 @@ __global__ void __launch_bounds__(kThreads, 2) fno_layer_kernel(LayerArgs a) {
     for (int c0 = part * 16; c0 < P.N; c0 += 32) {
       float r[16];
       ld16(d + (unsigned)c0, r);
-      if (x < s) {
+      if (x < s && a.back) {
+        // gradient: D, times GELU'(z) of the previous layer where it has one
+        float* gq = a.vout + base + (size_t)c0 * plane;
+        const float* zq = a.zp != nullptr ? a.zp + base + (size_t)c0 * plane : nullptr;
+        const int n = min(16, C - c0);
+        for (int j = 0; j < n; ++j) gq[j * plane] = zq != nullptr ? r[j] * gelu_grad_erf(zq[j * plane]) : r[j];
+      } else if (x < s) {
         float* zp = a.z + base + (size_t)c0 * plane;
         float* vq = a.vout + base + (size_t)c0 * plane;
         const int n = min(16, C - c0);
@@ -318,8 +333,8 @@ __global__ void __launch_bounds__(kThreads, 2) fno_layer_kernel(LayerArgs a) {
 bool fno_layer_umma_supported(int C, int Q, int s) { return C >= 1 && C <= kMaxC && Q >= 1 && Q <= kMaxQ && s <= 2 * kRows; }
 
 cudaError_t launch_fno_layer_umma(const float* v, const float* B1, const float* WxI, const float* W,
-                                  const float* bias, float* z, float* vout, int B, int C, int s, int Q,
-                                  int act, int* status, cudaStream_t st) {
+                                  const float* bias, float* z, float* vout, const float* zp, int B,
+                                  int C, int s, int Q, int act, int back, int* status, cudaStream_t st) {
   if (!fno_layer_umma_supported(C, Q, s)) return cudaErrorNotSupported;
   const Plan P = plan_of(C, Q);
   static bool attr_of[kDeviceSlots] = {};
@@ -352,7 +367,7 @@ cudaError_t launch_fno_layer_umma(const float* v, const float* B1, const float* 
   }
   const int per_sm = 2 * ((long long)P.bytes + 2048) <= (long long)smem_sm ? 2 : 1;
   const long long grid = std::min<long long>(tiles, (long long)per_sm * sms);
-  LayerArgs a{v, B1, WxI, W, bias, z, vout, B, C, s, Q, act, status};
+  LayerArgs a{v, B1, WxI, W, bias, z, vout, zp, B, C, s, Q, act, back, status};
   fno_layer_kernel<<<(unsigned)grid, kThreads, P.bytes, st>>>(a);
   return cudaGetLastError();
 }

@@ -137,9 +137,15 @@ cudaError_t launch_umma_line(float2* data, long long nlines, const float2* tw, c
                              int* status, cudaStream_t s);
 
 // ---- the fused FNO layer (fno_layer_umma.cu) --------------------------------------
-// z = WxI^T B1 + W v + bias and vout = act ? GELU(z) : z for every (b, o, y, x)
-// of a spectral layer (layouts as in fno.cu); tcgen05.mma with BF16 operands.
+// Forward (back = 0): z = WxI^T B1 + W v + bias and vout = act ? GELU(z) : z
+// for every (b, o, y, x) of a spectral layer (layouts as in fno.cu).  Backward
+// (back = 1, v the gradient dz): vout = (WxI^T B1 + W^T dz) GELU'(zp), or
+// without the factor when zp is NULL; z and bias unused.  tcgen05.mma with
+// BF16 operands.
 bool fno_layer_umma_supported(int C, int Q, int s);
+cudaError_t launch_fno_layer_umma(const float* v, const float* B1, const float* WxI, const float* W,
+                                  const float* bias, float* z, float* vout, const float* zp, int B,
+                                  int C, int s, int Q, int act, int back, int* status, cudaStream_t st);
 
 // ---- distributed shared memory rates (dsmem_rate.cu) ---------------------------
 // Aggregate GB/s over the GPU for clusters of csize CTAs: remote float4 reads
@@ -147,9 +153,6 @@ bool fno_layer_umma_supported(int C, int Q, int s);
 // pushed into a peer's shared memory.  cudaErrorLaunchTimeout if a bounded
 // copy wait expired.
 cudaError_t measure_dsmem(int csize, double* read_remote, double* read_local, double* push);
-cudaError_t launch_fno_layer_umma(const float* v, const float* B1, const float* WxI, const float* W,
-                                  const float* bias, float* z, float* vout, int B, int C, int s, int Q,
-                                  int act, int* status, cudaStream_t st);
 cudaError_t launch_resident_2d(int n, const Resident2dArgs& a, cudaStream_t s);
 
 // The potential pass (PSI_NPHASE) and the density pass (PSI_DENSITY) of one
