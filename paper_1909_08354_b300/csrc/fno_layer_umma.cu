@@ -330,7 +330,9 @@ __global__ void __launch_bounds__(kThreads, 2) fno_layer_kernel(LayerArgs a) {
 
 }  // namespace
 
-bool fno_layer_umma_supported(int C, int Q, int s) { return C >= 1 && C <= kMaxC && Q >= 1 && Q <= kMaxQ && s <= 2 * kRows; }
+bool fno_layer_umma_supported(int C, int Q, int s) {
+  return C >= 1 && C <= kMaxC && Q >= 2 && Q <= kMaxQ && (Q & 1) == 0 && s <= 2 * kRows;
+}
 
 cudaError_t launch_fno_layer_umma(const float* v, const float* B1, const float* WxI, const float* W,
                                   const float* bias, float* z, float* vout, const float* zp, int B,
