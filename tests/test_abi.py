@@ -119,3 +119,38 @@ def test_schedule_cache_round_trip(tmp_path):
     assert sn.load_schedule(path, k2) is None
     sn.store_schedule(path, k2, v1)  # a broken file is replaced
     assert sn.load_schedule(path, k2) == v1
+
+
+def test_later_calls_reject_bad_arguments_before_any_cuda_call():
+    """The grid options, the batch's register budget and tuner, the fused FNO
+    layer form and the measurement hooks check their arguments first."""
+    L = sn.lib()
+    assert L.sn_set_staging(None, 0) == sn.SN_EINVAL
+    assert L.sn_set_blocking(None, 4) == sn.SN_EINVAL
+    assert L.sn_set_obs_mode(None, sn.SN_OBS_FP32) == sn.SN_EINVAL
+    assert L.sn_set_batch_ctas(None, 2) == sn.SN_EINVAL
+    dt = (ctypes.c_double * 1)(0.01)
+    assert L.sn_autotune_batch(None, dt, 5, None) == sn.SN_EINVAL
+    assert L.sn_fno_set_layer_form(None, sn.SN_FNO_LAYER_UMMA) == sn.SN_EINVAL
+    ms = ctypes.c_double(0.0)
+    # NULL data, a bad length, a bad sign, the tcgen05 engine off 256 points, reps < 1
+    assert L.sn_test_line_fft_engines(None, 8, 256, -1, sn.SN_ENGINE_FP32, 1, ctypes.byref(ms), None) == sn.SN_EINVAL
+    dummy = ctypes.c_void_p(16)
+    assert L.sn_test_line_fft_engines(dummy, 8, 100, -1, sn.SN_ENGINE_FP32, 1, ctypes.byref(ms), None) == sn.SN_EINVAL
+    assert L.sn_test_line_fft_engines(dummy, 8, 256, 2, sn.SN_ENGINE_FP32, 1, ctypes.byref(ms), None) == sn.SN_EINVAL
+    assert L.sn_test_line_fft_engines(dummy, 8, 128, -1, sn.SN_ENGINE_UMMA, 1, ctypes.byref(ms), None) == sn.SN_EINVAL
+    assert L.sn_test_line_fft_engines(dummy, 8, 256, -1, sn.SN_ENGINE_UMMA, 0, ctypes.byref(ms), None) == sn.SN_EINVAL
+    rates = (ctypes.c_double * 3)()
+    for bad in (1, 3, 16):
+        assert L.sn_test_dsmem_rates(bad, rates) == sn.SN_EINVAL
+    assert L.sn_test_dsmem_rates(4, None) == sn.SN_EINVAL
+
+
+def test_new_header_enums_match_the_binding():
+    text = open(os.path.join(ROOT, "include", "sn.h")).read()
+    m = re.search(r"SN_OBS_FP64 = (\d+), SN_OBS_FP32 = (\d+)", text)
+    assert tuple(map(int, m.groups())) == (sn.SN_OBS_FP64, sn.SN_OBS_FP32)
+    m = re.search(r"SN_FNO_LAYER_GEMMS = (\d+), SN_FNO_LAYER_UMMA = (\d+)", text)
+    assert tuple(map(int, m.groups())) == (sn.SN_FNO_LAYER_GEMMS, sn.SN_FNO_LAYER_UMMA)
+    m = re.search(r"SN_ENGINE_FP32 = (\d+), SN_ENGINE_TC16 = (\d+), SN_ENGINE_UMMA = (\d+)", text)
+    assert tuple(map(int, m.groups())) == (sn.SN_ENGINE_FP32, sn.SN_ENGINE_TC16, sn.SN_ENGINE_UMMA)
