@@ -311,9 +311,12 @@ def time_observables(sn, torch, g, reps=5):
 
 
 def run_scan(sn, torch, stream, peak, count=96, steps=500, no_autotune=False):
-    """The batched parameter scan: 96 2D instances (128^2..1024^2), 500 steps, one launch.
-    With several ranks the instances are partitioned by cost (n^2 log n) and each
-    rank advances its share in one launch; the time is the slowest rank's."""
+    """The batched parameter scan: 96 2D instances (128^2..1024^2), 500 steps, on the
+    schedule sn_autotune_batch keeps (the persistent launch at one of its register
+    budgets, or a graph per round with an instance per branch); the other
+    schedule is timed too.  With several ranks the instances are partitioned by
+    cost (n^2 log n) and each rank advances its share; the time is the slowest
+    rank's."""
     from paper_1909_08354_b300 import dist as D
     all_ws = [W.scan_instance_2d(i, nsteps=steps) for i in range(count)]
     if D.world() > 1:
@@ -323,6 +326,8 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500, no_autotune=False):
         b.set_kernels([kernel_kw(w.kernel) for w in ws])
         for i, w in enumerate(ws):
             b.set_state(i, w.psi0(np.complex64))
+        if not no_autotune:
+            b.autotune(ws[0].dt, steps=min(steps, 100))
         b.step(ws[0].dt, steps)  # capture + warm-up
         b.sync()
         for i, w in enumerate(ws):
@@ -349,19 +354,28 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500, no_autotune=False):
     b.set_kernels(kws)
     for i, p in enumerate(psis):
         b.set_state(i, p)
-    budget = 3 if no_autotune else b.autotune(ws[0].dt, steps=min(steps, 100))  # CTAs per SM
-    b.step(ws[0].dt, steps)  # capture + warm-up
-    b.sync()
-    for i, p in enumerate(psis):
-        b.set_state(i, p)
-    torch.cuda.synchronize()
+    # 0: the graph schedule; 1..3: the persistent launch at that many CTAs per SM
+    chosen = 3 if no_autotune else b.autotune(ws[0].dt, steps=min(steps, 100))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.step(ws[0].dt, steps)
-    e1.record(stream)
-    b.sync()
-    t_batch = e0.elapsed_time(e1) / 1e3
+
+    def timed():
+        b.step(ws[0].dt, steps)  # capture + warm-up
+        b.sync()
+        for i, p in enumerate(psis):
+            b.set_state(i, p)
+        torch.cuda.synchronize()
+        n0 = b.launch_count()
+        e0.record(stream)
+        b.step(ws[0].dt, steps)
+        e1.record(stream)
+        b.sync()
+        return e0.elapsed_time(e1) / 1e3, b.launch_count() - n0
+
+    t_batch, launches = timed()
+    b.set_schedule(sn.SN_BATCH_PERSISTENT if chosen == 0 else sn.SN_BATCH_GRAPH)
+    t_other, _ = timed()
     b.close()
+    t_graph, t_persistent = (t_batch, t_other) if chosen == 0 else (t_other, t_batch)
     # the same instances one after another through the single-grid fused path
     grids = []
     for w, kw, p in zip(ws, kws, psis):
@@ -402,9 +416,11 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500, no_autotune=False):
                         f"complex64, alpha_Y~U[0,1], lambda_Y~U[1,20], g~U[0,0.05], dt=1e-2, "
                         f"{steps} steps",
             "cells": cells, "steps": steps, "value": value, "unit": "cell-steps/s",
-            "ms_total": 1e3 * t_batch, "launches": 1,
-            "ctas_per_sm": budget,
-            "ctas_per_sm_source": "default" if no_autotune else "sn_autotune_batch over 100 steps",
+            "ms_total": 1e3 * t_batch, "launches": launches,
+            "schedule": "graph" if chosen == 0 else "persistent",
+            "ctas_per_sm": None if chosen == 0 else chosen,
+            "schedule_source": "default" if no_autotune else "sn_autotune_batch over 100 steps",
+            "persistent_ms": 1e3 * t_persistent, "graph_ms": 1e3 * t_graph,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "bytes_per_cell_step": 48.0},
             "sequential_fused_ms": 1e3 * t_seq, "speedup_vs_sequential_fused": t_seq / t_batch,

@@ -367,10 +367,20 @@ sn_status sn_test_dsmem_rates(int cluster_size, double* rates);
  * advanced together (Sec. III step applied to each; e.g. a scan over the
  * coupling strength and range of the Eq. 9 kernel and over initial
  * conditions).  Instance i is an n[i] x n[i] periodic grid of box length L[i]
- * in both axes with its own kernel parameters and time step.  One
- * sn_step_batch call runs all merged steps of all instances in a single
- * persistent cooperative launch, captured once into a CUDA graph and replayed
- * while nsteps is unchanged.
+ * in both axes with its own kernel parameters and time step.  Two schedules
+ * (sn_set_batch_schedule):
+ *
+ * SN_BATCH_PERSISTENT (the default): one sn_step_batch call runs all merged
+ * steps of all instances in a single persistent cooperative launch, captured
+ * once into a CUDA graph and replayed while nsteps is unchanged.
+ *
+ * SN_BATCH_GRAPH: each round of merged steps (the psi passes along both axes
+ * and the Green's pass on the half spectrum) is a CUDA graph in which every
+ * instance is a branch of its own, running the fused pass kernels of the
+ * single-grid step (sn_step) on a grid of the instance's shape; the branches
+ * run concurrently and the graph is launched once per round.  Instance i then
+ * gives what sn_step gives for it, bit for bit.  Each call copies the states
+ * into those grids and back (16 bytes a cell per call).
  *
  * Inside the launch, work items (round, pass, instance, tile) are taken in a
  * fixed order (within a pass, larger instances first), and an item waits for
@@ -381,6 +391,11 @@ sn_status sn_test_dsmem_rates(int cluster_size, double* rates);
  * incomplete.  Batch calls report messages through sn_last_error(NULL).
  * ------------------------------------------------------------------------- */
 typedef struct sn_batch_s* sn_batch;
+
+enum sn_batch_schedule {
+  SN_BATCH_PERSISTENT = 0, /* one persistent cooperative launch per call */
+  SN_BATCH_GRAPH = 1       /* a graph per round, an instance per branch */
+};
 
 /* n[i]: power of two in [8, 1024]; L[i] > 0.  cuda_stream as for sn_create_grid.
  * States start at zero, kernels at {A=-0.5, G=1, alpha_Y=0, g=0}. */
@@ -395,7 +410,8 @@ sn_status sn_get_state_batch(sn_batch b, int index, void* psi_out, int on_device
 sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps);
 /* Observables of instance `index` (blocks). */
 sn_status sn_observables_batch(sn_batch b, int index, sn_obs* out);
-/* Wait for the batch's work; SN_ETIMEOUT if a dependency wait expired. */
+/* Wait for the batch's work; SN_ETIMEOUT if a dependency wait (persistent
+ * schedule) or a pass kernel's tile wait (graph schedule) expired. */
 sn_status sn_batch_sync(sn_batch b);
 /* Clock cycles one dependency wait may spin before it gives up (>= 0). */
 sn_status sn_set_batch_wait_limit(sn_batch b, long long cycles);
@@ -405,13 +421,25 @@ sn_status sn_set_batch_wait_limit(sn_batch b, long long cycles);
  * waits end whatever the choice; the results are the same bit for bit.
  * Errors: SN_EINVAL (NULL batch, per_sm outside 1..3). */
 sn_status sn_set_batch_ctas(sn_batch b, int per_sm);
-/* Time `steps` merged steps of the batch (steps dt[i]) at each register
- * budget (3, 2, 1 CTAs per SM), keep the fastest (another budget must beat
- * the current one by 2 %), and restore every instance's state.  *chosen (if
- * not NULL) receives the budget kept.  Blocks.  Errors: SN_EINVAL (NULL
- * batch or dt, steps < 1), SN_ECUDA, SN_ETIMEOUT as sn_batch_sync. */
+/* The batch's schedule: SN_BATCH_PERSISTENT or SN_BATCH_GRAPH (see above);
+ * it takes effect at the next sn_step_batch.  The graph schedule's first call
+ * makes a grid and a stream per instance, and its round graphs are captured
+ * again when a dt or a kernel changes.  Errors: SN_EINVAL (NULL batch, another
+ * value).  sn_get_batch_schedule returns the schedule, -1 for NULL. */
+sn_status sn_set_batch_schedule(sn_batch b, int schedule);
+int sn_get_batch_schedule(sn_batch b);
+/* Time `steps` merged steps of the batch (steps dt[i]) on the persistent
+ * schedule at each register budget (3, 2, 1 CTAs per SM) and on the graph
+ * schedule, keep the fastest (another candidate must beat the current one by
+ * 2 %), and restore every instance's state.  *chosen (if not NULL) receives
+ * the candidate kept: the budget 1..3 of the persistent schedule, or 0 for the
+ * graph schedule (which leaves the budget as it was).  Blocks.  Errors:
+ * SN_EINVAL (NULL batch or dt, steps < 1), SN_ECUDA, SN_ETIMEOUT as
+ * sn_batch_sync. */
 sn_status sn_autotune_batch(sn_batch b, const double* dt, int steps, int* chosen);
-/* Kernel launches of this batch (one per sn_step_batch call). */
+/* Kernel launches of this batch: one per sn_step_batch call on the persistent
+ * schedule; on the graph schedule the pass kernels of every round of every
+ * instance. */
 long long sn_batch_launch_count(sn_batch b);
 void sn_destroy_batch(sn_batch b);
 

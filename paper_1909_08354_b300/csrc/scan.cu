@@ -67,6 +67,18 @@ struct sn_batch_s {
   int graph_cps = -1;
   // observables of one instance go through a grid of the same shape
   std::vector<sn_grid> obs_grid;
+  // the graph schedule (SN_BATCH_GRAPH): a grid per instance on a stream of
+  // its own, only for capture; the captured rounds [first, middle even, middle
+  // odd, last even, last odd], with the kernels each launches, for the dt and
+  // kernels in graph_dt and graph_kp
+  int schedule = SN_BATCH_PERSISTENT;
+  std::vector<sn_grid> step_grid;
+  std::vector<cudaStream_t> step_stream;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  cudaGraphExec_t round_graph[5] = {};
+  long long round_launches[5] = {};
+  std::vector<double> graph_dt;
+  std::vector<sn_kernel> graph_kp;
   std::vector<void*> allocs;
 };
 
@@ -289,12 +301,117 @@ sn_status sn_set_batch_wait_limit(sn_batch b, long long cycles) {
   return SN_OK;
 }
 
+namespace {
+
+void drop_round_graphs(sn_batch b) {
+  for (cudaGraphExec_t& x : b->round_graph) {
+    if (x) cudaGraphExecDestroy(x);
+    x = nullptr;
+  }
+}
+
+// The graph schedule's grids and streams, made at its first use.
+sn_status ensure_step_grids(sn_batch b) {
+  if (!b->step_grid.empty()) return SN_OK;
+  cudaError_t e;
+  if ((e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming)) != cudaSuccess)
+    return bcuda(e, "cudaEventCreate");
+  b->step_grid.assign(b->count, nullptr);
+  b->step_stream.assign(b->count, nullptr);
+  for (int i = 0; i < b->count; ++i) {
+    if ((e = cudaStreamCreateWithFlags(&b->step_stream[i], cudaStreamNonBlocking)) != cudaSuccess)
+      return bcuda(e, "cudaStreamCreate");
+    const int n2[2] = {b->n[i], b->n[i]};
+    const double L2[2] = {b->L[i], b->L[i]};
+    sn_status st = sn_create_grid(&b->step_grid[i], 2, n2, L2, SN_C64, b->step_stream[i]);
+    if (st != SN_OK) return st;
+  }
+  return SN_OK;
+}
+
+// Round graph t (0: the first round; 1, 2: a middle round of even, odd index;
+// 3, 4: the last round of even, odd index): every instance's round on its own
+// branch, the largest instances first.
+sn_status capture_round(sn_batch b, int t, const double* dt) {
+  static const int rr[5] = {0, 2, 1, 2, 1}, nn[5] = {2, 4, 4, 2, 1};
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return bcuda(e, "cudaStreamBeginCapture");
+  sn_status st = SN_OK;
+  long long total = 0;
+  e = cudaEventRecord(b->fork_ev, b->stream);
+  for (int p = 0; p < b->count && e == cudaSuccess && st == SN_OK; ++p) {
+    const int i = b->order[p];
+    if ((e = cudaStreamWaitEvent(b->step_stream[i], b->fork_ev, 0)) != cudaSuccess) break;
+    long long k = 0;
+    st = batch_grid_round(b->step_grid[i], rr[t], nn[t], dt[i], &k);
+    total += k;
+    if (st != SN_OK) break;
+    if ((e = cudaEventRecord(b->join_ev, b->step_stream[i])) != cudaSuccess) break;
+    e = cudaStreamWaitEvent(b->stream, b->join_ev, 0);
+  }
+  const cudaError_t e_end = cudaStreamEndCapture(b->stream, &gr);
+  if (st == SN_OK && e == cudaSuccess) e = e_end;
+  if (st == SN_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->round_graph[t], gr, 0);
+  if (gr) cudaGraphDestroy(gr);
+  if (st != SN_OK) return st;
+  if (e != cudaSuccess) return bcuda(e, "round graph capture");
+  b->round_launches[t] = total;
+  return SN_OK;
+}
+
+// nsteps merged steps on the graph schedule: the states into the instance
+// grids, rounds 0 .. nsteps as graph launches, the states back.
+sn_status step_graph(sn_batch b, const double* dt, int nsteps) {
+  sn_status st = ensure_step_grids(b);
+  if (st != SN_OK) return st;
+  cudaError_t e;
+  bool same = b->graph_dt.size() == (size_t)b->count;
+  for (int i = 0; same && i < b->count; ++i)
+    same = b->graph_dt[i] == dt[i] &&
+           std::memcmp(&b->graph_kp[i], &b->kp[i], sizeof(sn_kernel)) == 0;
+  if (!same) {
+    // the captured launches carry the kernels' coefficients of dt; the
+    // tables they read may still be in use by queued rounds
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bcuda(e, "sync");
+    drop_round_graphs(b);
+    for (int i = 0; i < b->count; ++i)
+      if ((st = batch_grid_prepare(b->step_grid[i], b->kp[i], dt[i])) != SN_OK) return st;
+    b->graph_dt.assign(dt, dt + b->count);
+    b->graph_kp = b->kp;
+  }
+  for (int i = 0; i < b->count; ++i) {
+    const size_t bytes = (size_t)b->n[i] * b->n[i] * sizeof(float2);
+    if ((e = cudaMemcpyAsync(batch_grid_psi(b->step_grid[i]), b->host_inst[i].psi, bytes,
+                             cudaMemcpyDeviceToDevice, b->stream)) != cudaSuccess)
+      return bcuda(e, "state copy");
+  }
+  for (int r = 0; r <= nsteps; ++r) {
+    const int t = r == 0 ? 0 : r < nsteps ? 1 + (r & 1) : 3 + (r & 1);
+    if (!b->round_graph[t] && (st = capture_round(b, t, dt)) != SN_OK) return st;
+    if ((e = cudaGraphLaunch(b->round_graph[t], b->stream)) != cudaSuccess)
+      return bcuda(e, "cudaGraphLaunch");
+    b->launches += b->round_launches[t];
+  }
+  for (int i = 0; i < b->count; ++i) {
+    const size_t bytes = (size_t)b->n[i] * b->n[i] * sizeof(float2);
+    if ((e = cudaMemcpyAsync(b->host_inst[i].psi, batch_grid_psi(b->step_grid[i]), bytes,
+                             cudaMemcpyDeviceToDevice, b->stream)) != cudaSuccess)
+      return bcuda(e, "state copy");
+  }
+  return SN_OK;
+}
+
+}  // namespace
+
 sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
   if (!b || !dt) return bfail(SN_EINVAL, "sn_step_batch: NULL argument");
   if (nsteps < 0) return bfail(SN_EINVAL, "sn_step_batch: nsteps must be >= 0");
   for (int i = 0; i < b->count; ++i)
     if (!std::isfinite(dt[i])) return bfail(SN_EINVAL, "sn_step_batch: dt must be finite");
   if (nsteps == 0) return SN_OK;
+  if (b->schedule == SN_BATCH_GRAPH) return step_graph(b, dt, nsteps);
   cudaError_t e;
   bool changed = false;
   for (int i = 0; i < b->count; ++i) {
@@ -412,14 +529,19 @@ sn_status sn_autotune_batch(sn_batch b, const double* dt, int steps, int* chosen
   e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   copy_all(true);
-  const int keep = b->cps;
+  // candidates: the persistent kernel at 3, 2, 1 CTAs per SM (code c), the
+  // graph schedule (code 0)
+  const int keep = b->schedule == SN_BATCH_GRAPH ? 0 : b->cps, keep_cps = b->cps;
   int best = keep;
   float best_ms = 0.f, keep_ms = 0.f;
   sn_status st = SN_OK;
-  for (int c = 3; c >= 1 && e == cudaSuccess && st == SN_OK; --c) {
-    b->cps = c;
-    b->grid = b->grid_of[c];
-    // the first launch captures this budget's graph; the second is timed
+  for (int c = 3; c >= 0 && e == cudaSuccess && st == SN_OK; --c) {
+    b->schedule = c == 0 ? SN_BATCH_GRAPH : SN_BATCH_PERSISTENT;
+    if (c > 0) {
+      b->cps = c;
+      b->grid = b->grid_of[c];
+    }
+    // the first call captures this candidate's graphs; the second is timed
     if ((st = sn_step_batch(b, dt, steps)) != SN_OK) break;
     if ((e = cudaEventRecord(t0, b->stream)) != cudaSuccess) break;
     if ((st = sn_step_batch(b, dt, steps)) != SN_OK) break;
@@ -430,15 +552,18 @@ sn_status sn_autotune_batch(sn_batch b, const double* dt, int steps, int* chosen
     if (c == keep) keep_ms = ms;
     if (best_ms == 0.f || ms < best_ms) { best_ms = ms; best = c; }
   }
-  // a budget other than the current one must be at least 2% faster
+  // a candidate other than the current one must be at least 2% faster
   if (keep_ms > 0.f && best != keep && best_ms > 0.98f * keep_ms) best = keep;
   copy_all(false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);
   cudaFree(saved);
-  b->cps = best;
-  b->grid = b->grid_of[best];
+  // the graph schedule keeps the persistent kernel's budget as it was
+  b->schedule = best == 0 ? SN_BATCH_GRAPH : SN_BATCH_PERSISTENT;
+  const int cps = best == 0 ? keep_cps : best;
+  b->cps = cps;
+  b->grid = b->grid_of[cps];
   if (st != SN_OK) return st;
   if (e != cudaSuccess) return bcuda(e, "sn_autotune_batch");
   if (chosen) *chosen = best;
@@ -457,8 +582,24 @@ sn_status sn_batch_sync(sn_batch b) {
     return bfail(SN_ETIMEOUT, "sn_batch_sync: a dependency wait expired at work item " +
                                   std::to_string(err[1]) + "; the batch state is incomplete");
   }
+  // the graph schedule's pass kernels report through their grids' status words
+  for (sn_grid g : b->step_grid) {
+    if (!g) continue;
+    sn_status st = batch_grid_status(g);
+    if (st != SN_OK) return bfail(st, std::string("sn_batch_sync: ") + sn_last_error(g));
+  }
   return SN_OK;
 }
+
+sn_status sn_set_batch_schedule(sn_batch b, int schedule) {
+  if (!b) return bfail(SN_EINVAL, "sn_set_batch_schedule: batch is NULL");
+  if (schedule != SN_BATCH_PERSISTENT && schedule != SN_BATCH_GRAPH)
+    return bfail(SN_EINVAL, "sn_set_batch_schedule: schedule must be SN_BATCH_PERSISTENT or SN_BATCH_GRAPH");
+  b->schedule = schedule;
+  return SN_OK;
+}
+
+int sn_get_batch_schedule(sn_batch b) { return b ? b->schedule : -1; }
 
 long long sn_batch_launch_count(sn_batch b) { return b ? b->launches : 0; }
 
@@ -484,6 +625,12 @@ void sn_destroy_batch(sn_batch b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (sn_grid g : b->obs_grid) sn_destroy_grid(g);
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  drop_round_graphs(b);
+  for (sn_grid g : b->step_grid) sn_destroy_grid(g);
+  for (cudaStream_t s : b->step_stream)
+    if (s) cudaStreamDestroy(s);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
   for (void* p : b->allocs) cudaFree(p);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;

@@ -856,6 +856,28 @@ sn_status do_step(sn_grid g, double dt, int nsteps) {
 
 }  // namespace
 
+// ---- a batch instance stepped as a grid ----------------------------------------
+
+sn_status sn::batch_grid_prepare(sn_grid g, const sn_kernel& k, double dt) {
+  if (std::memcmp(&k, &g->kp, sizeof(sn_kernel)) != 0) {
+    sn_status st = sn_set_kernel(g, &k);
+    if (st != SN_OK) return st;
+  }
+  return ensure_mult_tables(g, dt);
+}
+
+sn_status sn::batch_grid_round(sn_grid g, int r, int nsteps, double dt, long long* launches) {
+  const long long before = g->launches;
+  sn_status st = round_f32(g, g->psi, (r & 1) != 0, r > 0, (r == 0 || r == nsteps) ? 0 : 1,
+                           r < nsteps, dt);
+  if (launches) *launches = g->launches - before;
+  return st;
+}
+
+sn_status sn::batch_grid_status(sn_grid g) { return check_status(g); }
+
+void* sn::batch_grid_psi(sn_grid g) { return g->psi; }
+
 // ============================================================================
 // C ABI
 // ============================================================================

@@ -153,6 +153,19 @@ cudaError_t launch_fno_layer_umma(const float* v, const float* B1, const float* 
 // pushed into a peer's shared memory.  cudaErrorLaunchTimeout if a bounded
 // copy wait expired.
 cudaError_t measure_dsmem(int csize, double* read_remote, double* read_local, double* push);
+
+// ---- a batch instance stepped as a grid (the scan's graph schedule) -----------
+// g is a 2D complex64 grid of one field on the FP32 engine without V_ext.
+// prepare: its kernel and the kinetic tables of dt, before any capture
+// (blocks while old tables may still be read).  round: round r of an n-step
+// call on its stream, the Strang merge closed at both ends (r = 0: Kin(h/2)
+// and the density; 0 < r < n: Nl(h), Kin(h), density; r = n: Nl(h), Kin(h/2));
+// *launches receives the kernels it launched.  status: its pass status word
+// (SN_ETIMEOUT after an expired tile wait).
+sn_status batch_grid_prepare(sn_grid g, const sn_kernel& k, double dt);
+sn_status batch_grid_round(sn_grid g, int r, int nsteps, double dt, long long* launches);
+sn_status batch_grid_status(sn_grid g);
+void* batch_grid_psi(sn_grid g);
 cudaError_t launch_resident_2d(int n, const Resident2dArgs& a, cudaStream_t s);
 
 // The potential pass (PSI_NPHASE) and the density pass (PSI_DENSITY) of one

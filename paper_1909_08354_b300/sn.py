@@ -21,6 +21,7 @@ SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 
 SN_ENGINE_FP32, SN_ENGINE_TC16, SN_ENGINE_UMMA = 0, 1, 2
 SN_STAGING_TMA, SN_STAGING_REGISTERS, SN_STAGING_RESIDENT = 0, 1, 2
 SN_OBS_FP64, SN_OBS_FP32 = 0, 1
+SN_BATCH_PERSISTENT, SN_BATCH_GRAPH = 0, 1
 SN_FNO_LAYER_GEMMS, SN_FNO_LAYER_UMMA = 0, 1
 SN_FLOOR_MAX, SN_FLOOR_SMOOTH = 0, 1
 SN_C64, SN_C128 = 0, 1
@@ -123,6 +124,8 @@ _SIGNATURES = [
     ("sn_batch_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_set_batch_wait_limit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     ("sn_set_batch_ctas", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_set_batch_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("sn_get_batch_schedule", ctypes.c_int, [ctypes.c_void_p]),
     ("sn_autotune_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("sn_batch_launch_count", ctypes.c_longlong, [ctypes.c_void_p]),
@@ -372,6 +375,14 @@ def sn_set_batch_ctas(b, per_sm: int):
     _check(None, lib().sn_set_batch_ctas(b, int(per_sm)))
 
 
+def sn_set_batch_schedule(b, schedule: int):
+    _check(None, lib().sn_set_batch_schedule(b, int(schedule)))
+
+
+def sn_get_batch_schedule(b) -> int:
+    return int(lib().sn_get_batch_schedule(b))
+
+
 def sn_batch_launch_count(b) -> int:
     return int(lib().sn_batch_launch_count(b))
 
@@ -608,9 +619,18 @@ class Batch:
         """Register budget of the launch: 3 (default), 2 or 1 resident CTAs per SM."""
         sn_set_batch_ctas(self.h, per_sm)
 
+    def set_schedule(self, schedule: int):
+        """SN_BATCH_PERSISTENT (one cooperative launch a call, the default) or
+        SN_BATCH_GRAPH (a graph per round, an instance per branch)."""
+        sn_set_batch_schedule(self.h, schedule)
+
+    def schedule(self) -> int:
+        return sn_get_batch_schedule(self.h)
+
     def autotune(self, dt, steps: int = 50) -> int:
-        """Time `steps` steps at each register budget, keep the fastest, restore
-        the states; returns the budget kept (CTAs per SM)."""
+        """Time `steps` steps on the persistent schedule at each register budget
+        and on the graph schedule, keep the fastest, restore the states; returns
+        the candidate kept: the budget (CTAs per SM) or 0 for the graph schedule."""
         dts = [float(dt)] * len(self.n) if np.isscalar(dt) else [float(x) for x in dt]
         arr = (ctypes.c_double * len(dts))(*dts)
         out = ctypes.c_int(0)

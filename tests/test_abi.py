@@ -129,6 +129,8 @@ def test_later_calls_reject_bad_arguments_before_any_cuda_call():
     assert L.sn_set_blocking(None, 4) == sn.SN_EINVAL
     assert L.sn_set_obs_mode(None, sn.SN_OBS_FP32) == sn.SN_EINVAL
     assert L.sn_set_batch_ctas(None, 2) == sn.SN_EINVAL
+    assert L.sn_set_batch_schedule(None, sn.SN_BATCH_GRAPH) == sn.SN_EINVAL
+    assert L.sn_get_batch_schedule(None) == -1
     dt = (ctypes.c_double * 1)(0.01)
     assert L.sn_autotune_batch(None, dt, 5, None) == sn.SN_EINVAL
     assert L.sn_fno_set_layer_form(None, sn.SN_FNO_LAYER_UMMA) == sn.SN_EINVAL
@@ -152,5 +154,7 @@ def test_new_header_enums_match_the_binding():
     assert tuple(map(int, m.groups())) == (sn.SN_OBS_FP64, sn.SN_OBS_FP32)
     m = re.search(r"SN_FNO_LAYER_GEMMS = (\d+), SN_FNO_LAYER_UMMA = (\d+)", text)
     assert tuple(map(int, m.groups())) == (sn.SN_FNO_LAYER_GEMMS, sn.SN_FNO_LAYER_UMMA)
+    m = re.search(r"SN_BATCH_PERSISTENT = (\d+), /\*[^*]*\*/\s*SN_BATCH_GRAPH = (\d+)", text)
+    assert tuple(map(int, m.groups())) == (sn.SN_BATCH_PERSISTENT, sn.SN_BATCH_GRAPH)
     m = re.search(r"SN_ENGINE_FP32 = (\d+), SN_ENGINE_TC16 = (\d+), SN_ENGINE_UMMA = (\d+)", text)
     assert tuple(map(int, m.groups())) == (sn.SN_ENGINE_FP32, sn.SN_ENGINE_TC16, sn.SN_ENGINE_UMMA)

@@ -1,10 +1,12 @@
-"""Batched scan of independent 2D instances of uneven size (one persistent launch).
+"""Batched scan of independent 2D instances of uneven size.
 
 Each instance of the batch must give what the oracle gives for it alone
 (per-step bar 1e-6 rel-L2 in complex64, k merged steps held to k times it),
-and what the single-grid path gives.  The bounded dependency waits are
-exercised by a zero wait limit: the launch must end with SN_ETIMEOUT and leave
-the GPU usable.
+and what the single-grid path gives: on the persistent schedule (one
+cooperative launch) within the per-step bar, on the graph schedule (the
+single-grid pass kernels, an instance per graph branch) bit for bit.  The
+bounded dependency waits are exercised by a zero wait limit: the launch must
+end with SN_ETIMEOUT and leave the GPU usable.
 """
 import numpy as np
 import pytest
@@ -33,10 +35,13 @@ def grid_run(psi, L, kw, dt, nsteps):
     return out
 
 
-def test_uneven_batch_matches_oracle_per_instance():
+@pytest.mark.parametrize("schedule", [sn.SN_BATCH_PERSISTENT, sn.SN_BATCH_GRAPH])
+def test_uneven_batch_matches_oracle_per_instance(schedule):
     sizes = [8, 16, 32, 64, 128, 256, 512, 64, 8, 128]
     ws = [W.random_small((n, n), seed=100 + i, L=12.0) for i, n in enumerate(sizes)]
     b = sn.Batch(sizes, [w.L[0] for w in ws])
+    b.set_schedule(schedule)
+    assert b.schedule() == schedule
     b.set_kernels([kw_of(w.kernel) for w in ws])
     psis = [w.psi0().astype(np.complex64) for w in ws]
     for i, p in enumerate(psis):
@@ -47,8 +52,54 @@ def test_uneven_batch_matches_oracle_per_instance():
     for i, w in enumerate(ws):
         ref = O.evolve(psis[i].astype(np.complex128), dts[i], 3, w.L, **kw_of(w.kernel))
         assert O.rel_l2(b.get_state(i), ref) <= 3 * STEP_TOL, (i, sizes[i])
-    assert b.launch_count() == 1
+    # persistent: one launch; graph: three passes per instance and round, two
+    # in the closing round
+    assert b.launch_count() == (1 if schedule == sn.SN_BATCH_PERSISTENT else 3 * 3 * 10 + 2 * 10)
     b.close()
+
+
+def test_graph_schedule_gives_the_single_grid_bits():
+    """The graph schedule runs each instance's round as the single-grid pass
+    kernels: the same bits as sn_step on a grid of the instance, over calls of
+    different lengths, with per-instance dt and kernels (Newton + Yukawa, local
+    term, the optical kernel), a dt change (recapture) and a schedule switch."""
+    sizes = [1024, 8, 512, 128, 256, 64, 1024, 16, 32, 128]
+    ws = [W.random_small((n, n), seed=600 + i, L=14.0 + i) for i, n in enumerate(sizes)]
+    kws = [kw_of(w.kernel) for w in ws]
+    kws[3] = dict(kws[3], alpha_Y=0.5, lambda_Y=2.0)
+    kws[4] = dict(kws[4], g_local=0.3)
+    kws[5] = dict(kind=sn.SN_KERNEL_POISSON, coeff_lap=-0.5, B=1.0, C=-0.04, D=-2.0)
+    psis = [w.psi0().astype(np.complex64) for w in ws]
+    dts = [0.01 + 0.001 * i for i in range(len(sizes))]
+    b = sn.Batch(sizes, [w.L[0] for w in ws])
+    try:
+        b.set_schedule(sn.SN_BATCH_GRAPH)
+        b.set_kernels(kws)
+        for i, p in enumerate(psis):
+            b.set_state(i, p)
+        b.step(dts, 3)
+        b.step(dts, 1)
+        b.step([2 * x for x in dts], 2)
+        b.sync()
+        got = [b.get_state(i).copy() for i in range(len(sizes))]
+        for i, w in enumerate(ws):
+            ref = grid_run(psis[i], w.L, kws[i], dts[i], 3)
+            ref = grid_run(ref, w.L, kws[i], dts[i], 1)
+            ref = grid_run(ref, w.L, kws[i], 2 * dts[i], 2)
+            assert np.array_equal(got[i], ref), (i, sizes[i])
+        # switching to the persistent schedule continues from the same states
+        b.set_schedule(sn.SN_BATCH_PERSISTENT)
+        b.step(dts, 2)
+        b.sync()
+        for i, w in enumerate(ws):
+            ref = grid_run(got[i], w.L, kws[i], dts[i], 2)
+            assert O.rel_l2(b.get_state(i), ref) <= 2 * STEP_TOL, (i, sizes[i])
+        for bad in (-1, 2):
+            with pytest.raises(sn.SNError) as e:
+                b.set_schedule(bad)
+            assert e.value.status == sn.SN_EINVAL
+    finally:
+        b.close()
 
 
 def test_batch_graph_replay_and_largest_size():
@@ -90,6 +141,31 @@ def test_expired_wait_reports_timeout_and_gpu_stays_usable():
     ref = grid_run(psi0, ws[0].L, kw_of(ws[0].kernel), 0.01, 2)
     assert O.rel_l2(b.get_state(0), ref) <= 2 * STEP_TOL
     b.close()
+
+
+def test_parameter_scan_96_instances_on_the_graph_schedule():
+    """The 96-instance scan workload on the graph schedule: 20 steps of every
+    instance give sn_step's bits, and the mass of every instance is kept."""
+    ws = [W.scan_instance_2d(i) for i in range(96)]
+    psis = [w.psi0().astype(np.complex64) for w in ws]
+    b = sn.Batch([w.n[0] for w in ws], [w.L[0] for w in ws])
+    try:
+        b.set_schedule(sn.SN_BATCH_GRAPH)
+        b.set_kernels([kw_of(w.kernel) for w in ws])
+        for i, p in enumerate(psis):
+            b.set_state(i, p)
+        b.step(ws[0].dt, 20)
+        b.sync()
+        for i in range(0, 96, 7):
+            w = ws[i]
+            ref = grid_run(psis[i], w.L, kw_of(w.kernel), w.dt, 20)
+            assert np.array_equal(b.get_state(i), ref), (i, w.n)
+        for i, p in enumerate(psis):
+            m0 = float(np.sum(np.abs(p.astype(np.complex128)) ** 2))
+            m = float(np.sum(np.abs(b.get_state(i).astype(np.complex128)) ** 2))
+            assert abs(m / m0 - 1) <= 1e-5, i
+    finally:
+        b.close()
 
 
 def test_parameter_scan_96_instances_500_steps():
@@ -169,7 +245,8 @@ def test_batch_autotune_keeps_the_states():
         for i, p in enumerate(psis):
             b.set_state(i, p)
         chosen = b.autotune(0.01, steps=5)
-        assert chosen in (1, 2, 3)
+        assert chosen in (0, 1, 2, 3)
+        assert b.schedule() == (sn.SN_BATCH_GRAPH if chosen == 0 else sn.SN_BATCH_PERSISTENT)
         for i, p in enumerate(psis):
             assert np.array_equal(b.get_state(i), p), i
         b.step(0.01, 3)
@@ -179,6 +256,10 @@ def test_batch_autotune_keeps_the_states():
         b.close()
     b = sn.Batch(sizes, [w.L[0] for w in ws])
     try:
+        if chosen == 0:
+            b.set_schedule(sn.SN_BATCH_GRAPH)
+        else:
+            b.set_ctas(chosen)
         b.set_kernels([kw_of(w.kernel) for w in ws])
         for i, p in enumerate(psis):
             b.set_state(i, p)
