@@ -350,6 +350,19 @@ sn_status sn_test_line_fft_f32(void* data, long long nlines, int n, int sign, in
  * bounded wait of the UMMA kernel expired; the data is incomplete). */
 sn_status sn_test_line_fft_engines(void* data, long long nlines, int n, int sign, int engine,
                                    int reps, double* ms_per_launch, void* cuda_stream);
+/* Where the tcgen05 line engine's time goes: one launch of SN_ENGINE_UMMA on
+ * nlines (>= 1) contiguous 256-point complex64 lines in device memory (in
+ * place, as sn_test_line_fft_engines), in a form whose thread 0 of each CTA
+ * reads the SM clock at the phase boundaries of every tile of 8 lines (the
+ * arithmetic is the same).  cycles_per_tile[5] receives the clock cycles of
+ * each phase per tile, averaged over all tiles: [0] stage A's operands (load,
+ * norm, scale, FP16 split into shared memory), [1] stage A's six products
+ * (issue to completion), [2] stage B's operands (tensor-memory read, twiddle,
+ * scale, split), [3] stage B's products, [4] the output (tensor-memory read,
+ * Parseval rescale, store).  *tiles receives the tiles done.  Synchronous on
+ * cuda_stream.  Errors: SN_EINVAL, SN_ECUDA, SN_ETIMEOUT. */
+sn_status sn_test_umma_phases(void* data, long long nlines, int sign, double* cycles_per_tile,
+                              long long* tiles, void* cuda_stream);
 
 /* Measurement hook: the distributed-shared-memory rates of thread-block
  * clusters of cluster_size CTAs (2, 4 or 8), as many clusters as are

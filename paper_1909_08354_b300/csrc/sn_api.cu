@@ -1460,12 +1460,15 @@ sn_status sn_test_line_fft_f32(void* data, long long nlines, int n, int sign, in
   return SN_OK;
 }
 
-sn_status sn_test_line_fft_engines(void* data, long long nlines, int n, int sign, int engine,
-                                   int reps, double* ms_per_launch, void* cuda_stream) {
+}  // extern "C"
+
+namespace {
+
+// The line engines' test launches; the tcgen05 engine's timed form when
+// phases is not NULL (its PH_COUNT phase totals, then the tiles done).
+sn_status line_engines(void* data, long long nlines, int n, int sign, int engine, int reps,
+                       double* ms_per_launch, unsigned long long* phases, void* cuda_stream) {
   const bool umma = engine == SN_ENGINE_UMMA;
-  if (!data || nlines < 0 || reps < 1 || !is_pow2_in_range(n) || (sign != 1 && sign != -1) ||
-      (engine != SN_ENGINE_FP32 && engine != SN_ENGINE_TC16 && !umma) || (umma && n != 256))
-    return fail(nullptr, SN_EINVAL, "sn_test_line_fft_engines: bad argument");
   if (ms_per_launch) *ms_per_launch = 0.0;
   if (nlines == 0) return SN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -1481,11 +1484,15 @@ sn_status sn_test_line_fft_engines(void* data, long long nlines, int n, int sign
     tc16_fragment_table(frag);
   }
   void *dtw = nullptr, *dtab = nullptr, *dstatus = nullptr;
+  unsigned long long* dcycles = nullptr;
+  constexpr int kPhaseWords = 6;
   const size_t tab_bytes = umma ? bmat.size() * sizeof(uint16_t) : frag.size() * sizeof(unsigned);
   cudaError_t e = cudaMalloc(&dtw, tw.size() * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&dtab, tab_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&dstatus, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(dstatus, 0, sizeof(int));
+  if (e == cudaSuccess && phases) e = cudaMalloc(&dcycles, kPhaseWords * sizeof(unsigned long long));
+  if (e == cudaSuccess && phases) e = cudaMemset(dcycles, 0, kPhaseWords * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemcpy(dtw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(dtab, umma ? (const void*)bmat.data() : (const void*)frag.data(), tab_bytes,
@@ -1496,7 +1503,7 @@ sn_status sn_test_line_fft_engines(void* data, long long nlines, int n, int sign
   auto launch = [&]() -> cudaError_t {
     if (umma)
       return launch_umma_line(static_cast<float2*>(data), nlines, static_cast<const float2*>(dtw), dtab,
-                              static_cast<int*>(dstatus), s);
+                              static_cast<int*>(dstatus), dcycles, s);
     RhoPassArgs ra{};
     ra.data = static_cast<float2*>(data);
     ra.outer = nlines;
@@ -1513,17 +1520,45 @@ sn_status sn_test_line_fft_engines(void* data, long long nlines, int n, int sign
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
   int st = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&st, dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && phases)
+    e = cudaMemcpy(phases, dcycles, kPhaseWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);
   cudaFree(dtw);
   cudaFree(dtab);
   cudaFree(dstatus);
+  cudaFree(dcycles);
   if (e != cudaSuccess) {
     set_thread_error((std::string("sn_test_line_fft_engines: ") + cudaGetErrorString(e)).c_str());
     return SN_ECUDA;
   }
   if (st != 0) return fail(nullptr, SN_ETIMEOUT, "sn_test_line_fft_engines: a bounded wait expired");
   if (ms_per_launch) *ms_per_launch = ms / reps;
+  return SN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sn_status sn_test_line_fft_engines(void* data, long long nlines, int n, int sign, int engine,
+                                   int reps, double* ms_per_launch, void* cuda_stream) {
+  const bool umma = engine == SN_ENGINE_UMMA;
+  if (!data || nlines < 0 || reps < 1 || !is_pow2_in_range(n) || (sign != 1 && sign != -1) ||
+      (engine != SN_ENGINE_FP32 && engine != SN_ENGINE_TC16 && !umma) || (umma && n != 256))
+    return fail(nullptr, SN_EINVAL, "sn_test_line_fft_engines: bad argument");
+  return line_engines(data, nlines, n, sign, engine, reps, ms_per_launch, nullptr, cuda_stream);
+}
+
+sn_status sn_test_umma_phases(void* data, long long nlines, int sign, double* cycles_per_tile,
+                              long long* tiles, void* cuda_stream) {
+  if (!data || nlines < 1 || (sign != 1 && sign != -1) || !cycles_per_tile || !tiles)
+    return fail(nullptr, SN_EINVAL, "sn_test_umma_phases: bad argument");
+  unsigned long long ph[6] = {};
+  sn_status st = line_engines(data, nlines, 256, sign, SN_ENGINE_UMMA, 1, nullptr, ph, cuda_stream);
+  if (st != SN_OK) return st;
+  *tiles = (long long)ph[5];
+  for (int i = 0; i < 5; ++i) cycles_per_tile[i] = ph[5] ? (double)ph[i] / (double)ph[5] : 0.0;
   return SN_OK;
 }
 

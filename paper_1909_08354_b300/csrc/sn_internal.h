@@ -132,9 +132,12 @@ bool resident_2d_supported(int ny, int nx);
 // In-place 256-point DFTs (sign as in sn_test_line_fft_f32) of nlines
 // contiguous complex64 lines, both radix-16 stages on tcgen05.mma; tw and bmat
 // from umma_line_tables (device copies); status set to 1 on an expired wait.
+// cycles (NULL: untimed): 6 device counters that receive the clock cycles of
+// each phase of a tile summed over tiles (stage A operands, stage A products,
+// stage B operands, stage B products, output), then the tiles done.
 void umma_line_tables(int sign, std::vector<uint16_t>& bmat, std::vector<float2>& tw);
 cudaError_t launch_umma_line(float2* data, long long nlines, const float2* tw, const void* bmat,
-                             int* status, cudaStream_t s);
+                             int* status, unsigned long long* cycles, cudaStream_t s);
 
 // ---- the fused FNO layer (fno_layer_umma.cu) --------------------------------------
 // Forward (back = 0): z = WxI^T B1 + W v + bias and vout = act ? GELU(z) : z

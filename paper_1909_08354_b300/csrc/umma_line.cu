@@ -141,8 +141,15 @@ struct UmmaArgs {
   const float2* tw;      // w256^j = exp(sign 2 pi i j / 256), j < 256
   const uint4* bmat;     // F_hi then F_lo (2 KB each) in the operand layout
   int* status;
+  // TIMED: clock cycles of each phase of a tile, summed over tiles and CTAs
+  // (as seen by thread 0, which meets every barrier), then the tiles done
+  unsigned long long* cycles;
 };
 
+// Phases of a tile, as timed by the TIMED form.
+enum { PH_STAGE_A_OPERANDS, PH_STAGE_A_MMA, PH_STAGE_B_OPERANDS, PH_STAGE_B_MMA, PH_OUTPUT, PH_COUNT };
+
+template <bool TIMED>
 __global__ void __launch_bounds__(kThreads, 4) umma_line_kernel(UmmaArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t bar;
@@ -183,7 +190,22 @@ __global__ void __launch_bounds__(kThreads, 4) umma_line_kernel(UmmaArgs a) {
   const long long tiles = (a.nlines + kLines - 1) / kLines;
   unsigned phase = 0;
   bool failed = false;
+  unsigned long long spent[PH_COUNT] = {};
+  unsigned long long done = 0;
+  long long mark_t = 0;
+  auto mark = [&](int ph) {
+    if constexpr (TIMED) {
+      if (tid == 0) {
+        const long long now = clock64();
+        spent[ph] += (unsigned long long)(now - mark_t);
+        mark_t = now;
+      }
+    }
+  };
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    if constexpr (TIMED) {
+      if (tid == 0) mark_t = clock64();
+    }
     const long long line = tile * kLines + li;
     const bool valid = line < a.nlines;
     float2* row = a.data + (valid ? line : 0) * kN;
@@ -210,6 +232,7 @@ __global__ void __launch_bounds__(kThreads, 4) umma_line_kernel(UmmaArgs a) {
     tma::fence_proxy_async();
     tc_fence_before();
     __syncthreads();
+    mark(PH_STAGE_A_OPERANDS);
     if (tid == 0) issue_stage();
     bool ok = tma::mbar_wait_bounded(&bar, phase, kWaitCycles);
     phase ^= 1u;
@@ -217,6 +240,7 @@ __global__ void __launch_bounds__(kThreads, 4) umma_line_kernel(UmmaArgs a) {
       failed = true;
       break;
     }
+    mark(PH_STAGE_A_MMA);
     tc_fence_after();
     float d[32];
     tmem_ld32(my_rows, d);
@@ -242,6 +266,7 @@ __global__ void __launch_bounds__(kThreads, 4) umma_line_kernel(UmmaArgs a) {
     for (int k1 = 0; k1 < 16; ++k1) put_split(A_hi, A_lo, li * 16 + k1, 2 * c, yr[k1] * sb, yi[k1] * sb);
     tma::fence_proxy_async();
     __syncthreads();
+    mark(PH_STAGE_B_OPERANDS);
     if (tid == 0) issue_stage();
     ok = tma::mbar_wait_bounded(&bar, phase, kWaitCycles);
     phase ^= 1u;
@@ -249,6 +274,7 @@ __global__ void __launch_bounds__(kThreads, 4) umma_line_kernel(UmmaArgs a) {
       failed = true;
       break;
     }
+    mark(PH_STAGE_B_MMA);
     tc_fence_after();
     tmem_ld32(my_rows, d);
     // X[k1 + 16 k2] with k1 = c, rescaled so that the line keeps 256 times
@@ -270,6 +296,14 @@ __global__ void __launch_bounds__(kThreads, 4) umma_line_kernel(UmmaArgs a) {
     }
     tc_fence_before();
     __syncthreads();  // the accumulators are read before the next tile's products
+    mark(PH_OUTPUT);
+    ++done;
+  }
+  if constexpr (TIMED) {
+    if (tid == 0 && a.cycles) {
+      for (int ph = 0; ph < PH_COUNT; ++ph) atomicAdd(a.cycles + ph, spent[ph]);
+      atomicAdd(a.cycles + PH_COUNT, done);
+    }
   }
   if (failed) {
     if (tid == 0) atomicExch(a.status, 1);
@@ -318,12 +352,15 @@ void umma_line_tables(int sign, std::vector<uint16_t>& bmat, std::vector<float2>
 }
 
 cudaError_t launch_umma_line(float2* data, long long nlines, const float2* tw, const void* bmat,
-                             int* status, cudaStream_t s) {
+                             int* status, unsigned long long* cycles, cudaStream_t s) {
   static bool attr_of[kDeviceSlots] = {};
   bool& attr = attr_of[device_slot()];
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(umma_line_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(umma_line_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(umma_line_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -337,8 +374,9 @@ cudaError_t launch_umma_line(float2* data, long long nlines, const float2* tw, c
   }
   const long long tiles = (nlines + kLines - 1) / kLines;
   const long long grid = std::min<long long>(tiles, 4LL * sms);
-  UmmaArgs a{data, nlines, tw, static_cast<const uint4*>(bmat), status};
-  umma_line_kernel<<<(unsigned)grid, kThreads, kSmemBytes, s>>>(a);
+  UmmaArgs a{data, nlines, tw, static_cast<const uint4*>(bmat), status, cycles};
+  if (cycles) umma_line_kernel<true><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(a);
+  else umma_line_kernel<false><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
 

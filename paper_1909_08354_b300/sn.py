@@ -107,6 +107,9 @@ _SIGNATURES = [
     ("sn_test_line_fft_engines", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    ("sn_test_umma_phases", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p]),
     ("sn_step_2d_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double,
                                           ctypes.POINTER(SnKernel), ctypes.c_double, ctypes.c_int,
@@ -567,6 +570,25 @@ def sn_test_line_fft_engines(data, n: int, sign: int, engine: int, reps: int = 1
                                                 int(reps), ctypes.byref(ms),
                                                 ctypes.c_void_p(stream) if stream else None))
     return ms.value
+
+
+UMMA_PHASES = ("stage A operands", "stage A products", "stage B operands", "stage B products",
+               "output")
+
+
+def sn_test_umma_phases(data, sign: int, stream=None):
+    """One launch of the tcgen05 line engine on the 256-point lines of a
+    contiguous complex64 CUDA tensor, timed by phase; returns
+    ({phase: clock cycles per tile of 8 lines}, tiles)."""
+    import torch
+    if not (_is_torch(data) and data.is_cuda and data.dtype == torch.complex64 and data.is_contiguous()):
+        raise ValueError("data must be a contiguous complex64 CUDA tensor")
+    cyc = (ctypes.c_double * 5)()
+    tiles = ctypes.c_longlong(0)
+    _check(None, lib().sn_test_umma_phases(data.data_ptr(), data.numel() // 256, sign, cyc,
+                                           ctypes.byref(tiles),
+                                           ctypes.c_void_p(stream) if stream else None))
+    return dict(zip(UMMA_PHASES, list(cyc))), tiles.value
 
 
 def sn_test_gemm_bf16(A, sA, B, sB, C, sC, M, N, K, Z, alpha=1.0, beta=0.0):

@@ -146,6 +146,12 @@ def test_later_calls_reject_bad_arguments_before_any_cuda_call():
     for bad in (1, 3, 16):
         assert L.sn_test_dsmem_rates(bad, rates) == sn.SN_EINVAL
     assert L.sn_test_dsmem_rates(4, None) == sn.SN_EINVAL
+    cyc = (ctypes.c_double * 5)()
+    tiles = ctypes.c_longlong(0)
+    assert L.sn_test_umma_phases(None, 8, -1, cyc, ctypes.byref(tiles), None) == sn.SN_EINVAL
+    assert L.sn_test_umma_phases(dummy, 0, -1, cyc, ctypes.byref(tiles), None) == sn.SN_EINVAL
+    assert L.sn_test_umma_phases(dummy, 8, 3, cyc, ctypes.byref(tiles), None) == sn.SN_EINVAL
+    assert L.sn_test_umma_phases(dummy, 8, -1, None, ctypes.byref(tiles), None) == sn.SN_EINVAL
 
 
 def test_new_header_enums_match_the_binding():

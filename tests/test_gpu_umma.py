@@ -92,6 +92,26 @@ def test_line_engines_timed_on_the_same_lines():
         assert err <= 2e-6
 
 
+def test_phase_cycles_of_the_tcgen05_engine():
+    """Where the tcgen05 engine's time goes, per tile of 8 lines, on lines in
+    HBM (65536) and in L2 (8192): the timed form gives the same bits as the
+    untimed one, every tile is counted, and the phases add up to about the
+    kernel's time (at 4 CTAs per SM the phases of one CTA overlap the other
+    CTAs')."""
+    for nlines in (65536, 8192):
+        x = lines(nlines, seed=9)
+        a = torch.from_numpy(x).cuda()
+        b = a.clone()
+        sn.sn_test_line_fft_engines(a, 256, -1, sn.SN_ENGINE_UMMA)
+        cyc, tiles = sn.sn_test_umma_phases(b, -1)
+        assert torch.equal(a, b)
+        assert tiles == nlines // 8
+        assert all(v > 0 for v in cyc.values()), cyc
+        total = sum(cyc.values())
+        print(f"{nlines} lines: tcgen05 cycles per tile " +
+              ", ".join(f"{k} {v:.0f} ({v / total:.0%})" for k, v in cyc.items()))
+
+
 def test_round_trip_norm_drift_of_the_engines():
     """Forward then inverse (scaled by 1/256), 100 times, on 4096 lines: the
     FP32 engine keeps the norm to rounding; both tensor-core engines correct
