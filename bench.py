@@ -354,8 +354,8 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500, no_autotune=False):
     b.set_kernels(kws)
     for i, p in enumerate(psis):
         b.set_state(i, p)
-    # 0: the graph schedule; 1..3: the persistent launch at that many CTAs per SM
-    chosen = 3 if no_autotune else b.autotune(ws[0].dt, steps=min(steps, 100))
+    budget = 3 if no_autotune else b.autotune(ws[0].dt, steps=min(steps, 100))  # CTAs per SM
+    chosen = b.schedule()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed():
@@ -372,10 +372,14 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500, no_autotune=False):
         return e0.elapsed_time(e1) / 1e3, b.launch_count() - n0
 
     t_batch, launches = timed()
-    b.set_schedule(sn.SN_BATCH_PERSISTENT if chosen == 0 else sn.SN_BATCH_GRAPH)
-    t_other, _ = timed()
+    names = {sn.SN_BATCH_PERSISTENT: "persistent", sn.SN_BATCH_CLASSES: "classes",
+             sn.SN_BATCH_GRAPH: "graph"}
+    t_of = {chosen: t_batch}
+    for other in names:  # the other schedules at the same budget, for the record
+        if other != chosen:
+            b.set_schedule(other)
+            t_of[other], _ = timed()
     b.close()
-    t_graph, t_persistent = (t_batch, t_other) if chosen == 0 else (t_other, t_batch)
     # the same instances one after another through the single-grid fused path
     grids = []
     for w, kw, p in zip(ws, kws, psis):
@@ -417,10 +421,10 @@ def run_scan(sn, torch, stream, peak, count=96, steps=500, no_autotune=False):
                         f"{steps} steps",
             "cells": cells, "steps": steps, "value": value, "unit": "cell-steps/s",
             "ms_total": 1e3 * t_batch, "launches": launches,
-            "schedule": "graph" if chosen == 0 else "persistent",
-            "ctas_per_sm": None if chosen == 0 else chosen,
+            "schedule": names[chosen],
+            "ctas_per_sm": budget,
             "schedule_source": "default" if no_autotune else "sn_autotune_batch over 100 steps",
-            "persistent_ms": 1e3 * t_persistent, "graph_ms": 1e3 * t_graph,
+            "schedule_ms": {names[k]: 1e3 * v for k, v in t_of.items()},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "bytes_per_cell_step": 48.0},
             "sequential_fused_ms": 1e3 * t_seq, "speedup_vs_sequential_fused": t_seq / t_batch,

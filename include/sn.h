@@ -380,12 +380,17 @@ sn_status sn_test_dsmem_rates(int cluster_size, double* rates);
  * advanced together (Sec. III step applied to each; e.g. a scan over the
  * coupling strength and range of the Eq. 9 kernel and over initial
  * conditions).  Instance i is an n[i] x n[i] periodic grid of box length L[i]
- * in both axes with its own kernel parameters and time step.  Two schedules
+ * in both axes with its own kernel parameters and time step.  Three schedules
  * (sn_set_batch_schedule):
  *
  * SN_BATCH_PERSISTENT (the default): one sn_step_batch call runs all merged
  * steps of all instances in a single persistent cooperative launch, captured
  * once into a CUDA graph and replayed while nsteps is unchanged.
+ *
+ * SN_BATCH_CLASSES: the same persistent kernel launched once per size class
+ * (the instances of one n, largest n first), each launch running all steps
+ * of its class; the launches are captured together.  The same bits as
+ * SN_BATCH_PERSISTENT.
  *
  * SN_BATCH_GRAPH: each round of merged steps (the psi passes along both axes
  * and the Green's pass on the half spectrum) is a CUDA graph in which every
@@ -407,7 +412,8 @@ typedef struct sn_batch_s* sn_batch;
 
 enum sn_batch_schedule {
   SN_BATCH_PERSISTENT = 0, /* one persistent cooperative launch per call */
-  SN_BATCH_GRAPH = 1       /* a graph per round, an instance per branch */
+  SN_BATCH_GRAPH = 1,      /* a graph per round, an instance per branch */
+  SN_BATCH_CLASSES = 2     /* one persistent launch per size class */
 };
 
 /* n[i]: power of two in [8, 1024]; L[i] > 0.  cuda_stream as for sn_create_grid.
@@ -434,7 +440,8 @@ sn_status sn_set_batch_wait_limit(sn_batch b, long long cycles);
  * waits end whatever the choice; the results are the same bit for bit.
  * Errors: SN_EINVAL (NULL batch, per_sm outside 1..3). */
 sn_status sn_set_batch_ctas(sn_batch b, int per_sm);
-/* The batch's schedule: SN_BATCH_PERSISTENT or SN_BATCH_GRAPH (see above);
+/* The batch's schedule: SN_BATCH_PERSISTENT, SN_BATCH_CLASSES or
+ * SN_BATCH_GRAPH (see above);
  * it takes effect at the next sn_step_batch.  The graph schedule's first call
  * makes a grid and a stream per instance, and its round graphs are captured
  * again when a dt or a kernel changes.  Errors: SN_EINVAL (NULL batch, another
@@ -442,17 +449,17 @@ sn_status sn_set_batch_ctas(sn_batch b, int per_sm);
 sn_status sn_set_batch_schedule(sn_batch b, int schedule);
 int sn_get_batch_schedule(sn_batch b);
 /* Time `steps` merged steps of the batch (steps dt[i]) on the persistent
- * schedule at each register budget (3, 2, 1 CTAs per SM) and on the graph
- * schedule, keep the fastest (another candidate must beat the current one by
- * 2 %), and restore every instance's state.  *chosen (if not NULL) receives
- * the candidate kept: the budget 1..3 of the persistent schedule, or 0 for the
- * graph schedule (which leaves the budget as it was).  Blocks.  Errors:
- * SN_EINVAL (NULL batch or dt, steps < 1), SN_ECUDA, SN_ETIMEOUT as
+ * and per-class schedules at each register budget (3, 2, 1 CTAs per SM) and
+ * on the graph schedule, keep the fastest (another candidate must beat the
+ * current one by 2 %), and restore every instance's state.  The schedule kept
+ * is read with sn_get_batch_schedule; *chosen (if not NULL) receives the
+ * register budget kept (the graph schedule leaves it as it was).  Blocks.
+ * Errors: SN_EINVAL (NULL batch or dt, steps < 1), SN_ECUDA, SN_ETIMEOUT as
  * sn_batch_sync. */
 sn_status sn_autotune_batch(sn_batch b, const double* dt, int steps, int* chosen);
 /* Kernel launches of this batch: one per sn_step_batch call on the persistent
- * schedule; on the graph schedule the pass kernels of every round of every
- * instance. */
+ * schedule, one per size class on the per-class schedule; on the graph
+ * schedule the pass kernels of every round of every instance. */
 long long sn_batch_launch_count(sn_batch b);
 void sn_destroy_batch(sn_batch b);
 

@@ -53,6 +53,10 @@ struct sn_batch_s {
   std::vector<float*> k2;
   int4* items = nullptr;  // one round's work items in queue order
   unsigned long long per_round = 0, last = 0;  // items of a full round; of the last (psi passes only)
+  // SN_BATCH_CLASSES: the same items class by class (instances of one n, in
+  // queue order), class c's round at class_items + class_off[c]
+  int4* class_items = nullptr;
+  std::vector<unsigned long long> class_off, class_per_round, class_last;
   unsigned* done = nullptr;
   int* err = nullptr;
   long long wait_limit = 4000000000LL;  // about 2 s at the B300's 2 GHz
@@ -65,6 +69,7 @@ struct sn_batch_s {
   int graph_steps = -1;
   long long graph_limit = -1;
   int graph_cps = -1;
+  int graph_sched = -1;
   // observables of one instance go through a grid of the same shape
   std::vector<sn_grid> obs_grid;
   // the graph schedule (SN_BATCH_GRAPH): a grid per instance on a stream of
@@ -234,10 +239,29 @@ sn_status sn_create_batch(sn_batch* out, int count, const int* n, const double* 
     }
   b->per_round = items.size();
   for (int i = 0; i < count; ++i) b->last += 2ull * b->host_inst[i].t_psi;
+  // class by class: the queue positions [p0, p1) of one n
+  std::vector<int4> citems;
+  for (int p0 = 0; p0 < count;) {
+    int p1 = p0;
+    while (p1 < count && n[b->order[p1]] == n[b->order[p0]]) ++p1;
+    b->class_off.push_back(citems.size());
+    unsigned long long last = 0;
+    for (const int4& it : items)
+      if (it.x >= p0 && it.x < p1) citems.push_back(it);
+    for (int p = p0; p < p1; ++p) last += 2ull * b->host_inst[b->order[p]].t_psi;
+    b->class_per_round.push_back(citems.size() - b->class_off.back());
+    b->class_last.push_back(last);
+    p0 = p1;
+  }
   if ((e = balloc(b, &b->items, items.size())) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(items)"));
   if ((e = cudaMemcpy(b->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice)) !=
       cudaSuccess)
     return bail(bcuda(e, "cudaMemcpy(items)"));
+  if ((e = balloc(b, &b->class_items, citems.size())) != cudaSuccess)
+    return bail(bcuda(e, "cudaMalloc(class items)"));
+  if ((e = cudaMemcpy(b->class_items, citems.data(), citems.size() * sizeof(int4),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(bcuda(e, "cudaMemcpy(class items)"));
   if ((e = balloc(b, &b->dev_inst, (size_t)count)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(inst)"));
   if ((e = balloc(b, &b->done, (size_t)count)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(done)"));
   if ((e = balloc(b, &b->err, (size_t)2)) != cudaSuccess) return bail(bcuda(e, "cudaMalloc(err)"));
@@ -458,12 +482,13 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
   a.wait_limit = b->wait_limit;
 
   if (b->graph && (b->graph_steps != nsteps || b->graph_limit != b->wait_limit ||
-                   b->graph_cps != b->cps)) {
+                   b->graph_cps != b->cps || b->graph_sched != b->schedule)) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
   if (!b->graph) {
-    // capture: zero the counters, then one cooperative launch of the whole scan
+    // capture: zero the counters, then one cooperative launch of the whole
+    // scan, or (SN_BATCH_CLASSES) one per class, largest n first
     cudaGraph_t gr = nullptr;
     if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return bcuda(e, "cudaStreamBeginCapture");
@@ -478,7 +503,18 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e2 = e1 == cudaSuccess ? cudaLaunchKernelEx(&cfg, scan_kernel_of(b->cps), a) : e1;
+    cudaError_t e2 = e1;
+    if (b->schedule == SN_BATCH_CLASSES) {
+      for (size_t c = 0; c < b->class_off.size() && e2 == cudaSuccess; ++c) {
+        ScanArgs ac = a;
+        ac.items = b->class_items + b->class_off[c];
+        ac.per_round = b->class_per_round[c];
+        ac.total = ac.per_round * (unsigned long long)nsteps + b->class_last[c];
+        e2 = cudaLaunchKernelEx(&cfg, scan_kernel_of(b->cps), ac);
+      }
+    } else if (e2 == cudaSuccess) {
+      e2 = cudaLaunchKernelEx(&cfg, scan_kernel_of(b->cps), a);
+    }
     e = cudaStreamEndCapture(b->stream, &gr);
     if (e2 != cudaSuccess) {
       if (gr) cudaGraphDestroy(gr);
@@ -491,9 +527,10 @@ sn_status sn_step_batch(sn_batch b, const double* dt, int nsteps) {
     b->graph_steps = nsteps;
     b->graph_limit = b->wait_limit;
     b->graph_cps = b->cps;
+    b->graph_sched = b->schedule;
   }
   if ((e = cudaGraphLaunch(b->graph, b->stream)) != cudaSuccess) return bcuda(e, "cudaGraphLaunch");
-  b->launches += 1;
+  b->launches += b->schedule == SN_BATCH_CLASSES ? (long long)b->class_off.size() : 1;
   return SN_OK;
 }
 
@@ -529,18 +566,27 @@ sn_status sn_autotune_batch(sn_batch b, const double* dt, int steps, int* chosen
   e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   copy_all(true);
-  // candidates: the persistent kernel at 3, 2, 1 CTAs per SM (code c), the
-  // graph schedule (code 0)
-  const int keep = b->schedule == SN_BATCH_GRAPH ? 0 : b->cps, keep_cps = b->cps;
-  int best = keep;
+  // candidates: the persistent kernel in one launch and one launch per class,
+  // each at 3, 2 and 1 CTAs per SM, and the graph schedule
+  struct Cand {
+    int schedule, cps;
+  };
+  std::vector<Cand> cands;
+  for (int sch : {SN_BATCH_PERSISTENT, SN_BATCH_CLASSES})
+    for (int c = 3; c >= 1; --c) cands.push_back({sch, c});
+  cands.push_back({SN_BATCH_GRAPH, b->cps});
+  const Cand keep{b->schedule, b->cps};
+  auto same = [](const Cand& x, const Cand& y) {
+    return x.schedule == y.schedule && (x.schedule == SN_BATCH_GRAPH || x.cps == y.cps);
+  };
+  Cand best = keep;
   float best_ms = 0.f, keep_ms = 0.f;
   sn_status st = SN_OK;
-  for (int c = 3; c >= 0 && e == cudaSuccess && st == SN_OK; --c) {
-    b->schedule = c == 0 ? SN_BATCH_GRAPH : SN_BATCH_PERSISTENT;
-    if (c > 0) {
-      b->cps = c;
-      b->grid = b->grid_of[c];
-    }
+  for (const Cand& cand : cands) {
+    if (e != cudaSuccess || st != SN_OK) break;
+    b->schedule = cand.schedule;
+    b->cps = cand.cps;
+    b->grid = b->grid_of[cand.cps];
     // the first call captures this candidate's graphs; the second is timed
     if ((st = sn_step_batch(b, dt, steps)) != SN_OK) break;
     if ((e = cudaEventRecord(t0, b->stream)) != cudaSuccess) break;
@@ -549,24 +595,26 @@ sn_status sn_autotune_batch(sn_batch b, const double* dt, int steps, int* chosen
     if ((st = sn_batch_sync(b)) != SN_OK) break;
     float ms = 0.f;
     if ((e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) break;
-    if (c == keep) keep_ms = ms;
-    if (best_ms == 0.f || ms < best_ms) { best_ms = ms; best = c; }
+    if (same(cand, keep)) keep_ms = ms;
+    if (best_ms == 0.f || ms < best_ms) {
+      best_ms = ms;
+      best = cand;
+    }
   }
   // a candidate other than the current one must be at least 2% faster
-  if (keep_ms > 0.f && best != keep && best_ms > 0.98f * keep_ms) best = keep;
+  if (keep_ms > 0.f && !same(best, keep) && best_ms > 0.98f * keep_ms) best = keep;
   copy_all(false);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);
   cudaFree(saved);
-  // the graph schedule keeps the persistent kernel's budget as it was
-  b->schedule = best == 0 ? SN_BATCH_GRAPH : SN_BATCH_PERSISTENT;
-  const int cps = best == 0 ? keep_cps : best;
-  b->cps = cps;
-  b->grid = b->grid_of[cps];
+  // the graph schedule keeps the budget as it was
+  b->schedule = best.schedule;
+  b->cps = best.schedule == SN_BATCH_GRAPH ? keep.cps : best.cps;
+  b->grid = b->grid_of[b->cps];
   if (st != SN_OK) return st;
   if (e != cudaSuccess) return bcuda(e, "sn_autotune_batch");
-  if (chosen) *chosen = best;
+  if (chosen) *chosen = b->cps;
   return SN_OK;
 }
 
@@ -593,8 +641,8 @@ sn_status sn_batch_sync(sn_batch b) {
 
 sn_status sn_set_batch_schedule(sn_batch b, int schedule) {
   if (!b) return bfail(SN_EINVAL, "sn_set_batch_schedule: batch is NULL");
-  if (schedule != SN_BATCH_PERSISTENT && schedule != SN_BATCH_GRAPH)
-    return bfail(SN_EINVAL, "sn_set_batch_schedule: schedule must be SN_BATCH_PERSISTENT or SN_BATCH_GRAPH");
+  if (schedule != SN_BATCH_PERSISTENT && schedule != SN_BATCH_GRAPH && schedule != SN_BATCH_CLASSES)
+    return bfail(SN_EINVAL, "sn_set_batch_schedule: unknown schedule");
   b->schedule = schedule;
   return SN_OK;
 }

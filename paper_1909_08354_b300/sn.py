@@ -21,7 +21,7 @@ SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ETIMEOUT, SN_ENONFINITE, SN_ENOTSUP = 
 SN_ENGINE_FP32, SN_ENGINE_TC16, SN_ENGINE_UMMA = 0, 1, 2
 SN_STAGING_TMA, SN_STAGING_REGISTERS, SN_STAGING_RESIDENT = 0, 1, 2
 SN_OBS_FP64, SN_OBS_FP32 = 0, 1
-SN_BATCH_PERSISTENT, SN_BATCH_GRAPH = 0, 1
+SN_BATCH_PERSISTENT, SN_BATCH_GRAPH, SN_BATCH_CLASSES = 0, 1, 2
 SN_FNO_LAYER_GEMMS, SN_FNO_LAYER_UMMA = 0, 1
 SN_FLOOR_MAX, SN_FLOOR_SMOOTH = 0, 1
 SN_C64, SN_C128 = 0, 1
@@ -642,7 +642,8 @@ class Batch:
         sn_set_batch_ctas(self.h, per_sm)
 
     def set_schedule(self, schedule: int):
-        """SN_BATCH_PERSISTENT (one cooperative launch a call, the default) or
+        """SN_BATCH_PERSISTENT (one cooperative launch a call, the default),
+        SN_BATCH_CLASSES (one cooperative launch per size class) or
         SN_BATCH_GRAPH (a graph per round, an instance per branch)."""
         sn_set_batch_schedule(self.h, schedule)
 
@@ -650,9 +651,10 @@ class Batch:
         return sn_get_batch_schedule(self.h)
 
     def autotune(self, dt, steps: int = 50) -> int:
-        """Time `steps` steps on the persistent schedule at each register budget
-        and on the graph schedule, keep the fastest, restore the states; returns
-        the candidate kept: the budget (CTAs per SM) or 0 for the graph schedule."""
+        """Time `steps` steps on the persistent and per-class schedules at each
+        register budget and on the graph schedule, keep the fastest, restore the
+        states; returns the budget kept (CTAs per SM); schedule() gives the
+        schedule kept."""
         dts = [float(dt)] * len(self.n) if np.isscalar(dt) else [float(x) for x in dt]
         arr = (ctypes.c_double * len(dts))(*dts)
         out = ctypes.c_int(0)

@@ -160,7 +160,9 @@ def test_new_header_enums_match_the_binding():
     assert tuple(map(int, m.groups())) == (sn.SN_OBS_FP64, sn.SN_OBS_FP32)
     m = re.search(r"SN_FNO_LAYER_GEMMS = (\d+), SN_FNO_LAYER_UMMA = (\d+)", text)
     assert tuple(map(int, m.groups())) == (sn.SN_FNO_LAYER_GEMMS, sn.SN_FNO_LAYER_UMMA)
-    m = re.search(r"SN_BATCH_PERSISTENT = (\d+), /\*[^*]*\*/\s*SN_BATCH_GRAPH = (\d+)", text)
-    assert tuple(map(int, m.groups())) == (sn.SN_BATCH_PERSISTENT, sn.SN_BATCH_GRAPH)
+    m = re.search(r"SN_BATCH_PERSISTENT = (\d+),\s*/\*[^*]*\*/\s*SN_BATCH_GRAPH = (\d+),"
+                  r"\s*/\*[^*]*\*/\s*SN_BATCH_CLASSES = (\d+)", text)
+    assert tuple(map(int, m.groups())) == (sn.SN_BATCH_PERSISTENT, sn.SN_BATCH_GRAPH,
+                                           sn.SN_BATCH_CLASSES)
     m = re.search(r"SN_ENGINE_FP32 = (\d+), SN_ENGINE_TC16 = (\d+), SN_ENGINE_UMMA = (\d+)", text)
     assert tuple(map(int, m.groups())) == (sn.SN_ENGINE_FP32, sn.SN_ENGINE_TC16, sn.SN_ENGINE_UMMA)

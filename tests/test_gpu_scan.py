@@ -35,7 +35,7 @@ def grid_run(psi, L, kw, dt, nsteps):
     return out
 
 
-@pytest.mark.parametrize("schedule", [sn.SN_BATCH_PERSISTENT, sn.SN_BATCH_GRAPH])
+@pytest.mark.parametrize("schedule", [sn.SN_BATCH_PERSISTENT, sn.SN_BATCH_CLASSES, sn.SN_BATCH_GRAPH])
 def test_uneven_batch_matches_oracle_per_instance(schedule):
     sizes = [8, 16, 32, 64, 128, 256, 512, 64, 8, 128]
     ws = [W.random_small((n, n), seed=100 + i, L=12.0) for i, n in enumerate(sizes)]
@@ -52,9 +52,10 @@ def test_uneven_batch_matches_oracle_per_instance(schedule):
     for i, w in enumerate(ws):
         ref = O.evolve(psis[i].astype(np.complex128), dts[i], 3, w.L, **kw_of(w.kernel))
         assert O.rel_l2(b.get_state(i), ref) <= 3 * STEP_TOL, (i, sizes[i])
-    # persistent: one launch; graph: three passes per instance and round, two
-    # in the closing round
-    assert b.launch_count() == (1 if schedule == sn.SN_BATCH_PERSISTENT else 3 * 3 * 10 + 2 * 10)
+    # persistent: one launch; per class: one for each of the 7 sizes; graph:
+    # three passes per instance and round, two in the closing round
+    want = {sn.SN_BATCH_PERSISTENT: 1, sn.SN_BATCH_CLASSES: 7, sn.SN_BATCH_GRAPH: 3 * 3 * 10 + 2 * 10}
+    assert b.launch_count() == want[schedule]
     b.close()
 
 
@@ -94,7 +95,7 @@ def test_graph_schedule_gives_the_single_grid_bits():
         for i, w in enumerate(ws):
             ref = grid_run(got[i], w.L, kws[i], dts[i], 2)
             assert O.rel_l2(b.get_state(i), ref) <= 2 * STEP_TOL, (i, sizes[i])
-        for bad in (-1, 2):
+        for bad in (-1, 3):
             with pytest.raises(sn.SNError) as e:
                 b.set_schedule(bad)
             assert e.value.status == sn.SN_EINVAL
@@ -206,25 +207,30 @@ def test_parameter_scan_96_instances_500_steps():
 
 def test_every_register_budget_gives_the_same_bits():
     """sn_set_batch_ctas changes the CTAs of the cooperative launch and the
-    registers of its threads, not the arithmetic: the same bits for 1, 2 and
-    3 CTAs per SM, on every line length the scan takes."""
+    registers of its threads, and SN_BATCH_CLASSES splits the launch by size
+    class; neither changes the arithmetic: the same bits for 1, 2 and 3 CTAs
+    per SM in one launch or one per class, on every line length the scan
+    takes."""
     sizes = [1024, 512, 256, 128, 64, 32, 16, 8, 256, 1024]
     ws = [W.random_small((n, n), seed=400 + i, L=16.0) for i, n in enumerate(sizes)]
     psis = [w.psi0().astype(np.complex64) for w in ws]
     outs = {}
-    for cps in (3, 2, 1):
-        b = sn.Batch(sizes, [w.L[0] for w in ws])
-        b.set_kernels([kw_of(w.kernel) for w in ws])
-        b.set_ctas(cps)
-        for i, p in enumerate(psis):
-            b.set_state(i, p)
-        b.step(0.01, 3)
-        b.sync()
-        outs[cps] = [b.get_state(i).copy() for i in range(len(sizes))]
-        b.close()
-    for cps in (2, 1):
+    for sched in (sn.SN_BATCH_PERSISTENT, sn.SN_BATCH_CLASSES):
+        for cps in (3, 2, 1):
+            b = sn.Batch(sizes, [w.L[0] for w in ws])
+            b.set_kernels([kw_of(w.kernel) for w in ws])
+            b.set_schedule(sched)
+            b.set_ctas(cps)
+            for i, p in enumerate(psis):
+                b.set_state(i, p)
+            b.step(0.01, 3)
+            b.sync()
+            outs[sched, cps] = [b.get_state(i).copy() for i in range(len(sizes))]
+            b.close()
+    ref = outs[sn.SN_BATCH_PERSISTENT, 3]
+    for key, out in outs.items():
         for i in range(len(sizes)):
-            assert np.array_equal(outs[cps][i], outs[3][i]), (cps, sizes[i])
+            assert np.array_equal(out[i], ref[i]), (key, sizes[i])
     b = sn.Batch([8], [4.0])
     try:
         for bad in (0, 4):
@@ -245,8 +251,9 @@ def test_batch_autotune_keeps_the_states():
         for i, p in enumerate(psis):
             b.set_state(i, p)
         chosen = b.autotune(0.01, steps=5)
-        assert chosen in (0, 1, 2, 3)
-        assert b.schedule() == (sn.SN_BATCH_GRAPH if chosen == 0 else sn.SN_BATCH_PERSISTENT)
+        assert chosen in (1, 2, 3)
+        schedule = b.schedule()
+        assert schedule in (sn.SN_BATCH_PERSISTENT, sn.SN_BATCH_CLASSES, sn.SN_BATCH_GRAPH)
         for i, p in enumerate(psis):
             assert np.array_equal(b.get_state(i), p), i
         b.step(0.01, 3)
@@ -256,10 +263,8 @@ def test_batch_autotune_keeps_the_states():
         b.close()
     b = sn.Batch(sizes, [w.L[0] for w in ws])
     try:
-        if chosen == 0:
-            b.set_schedule(sn.SN_BATCH_GRAPH)
-        else:
-            b.set_ctas(chosen)
+        b.set_schedule(schedule)
+        b.set_ctas(chosen)
         b.set_kernels([kw_of(w.kernel) for w in ws])
         for i, p in enumerate(psis):
             b.set_state(i, p)
