@@ -334,22 +334,43 @@ void drop_round_graphs(sn_batch b) {
   }
 }
 
-// The graph schedule's grids and streams, made at its first use.
+// The graph schedule's grids, streams and events (released together).
+void drop_step_grids(sn_batch b) {
+  drop_round_graphs(b);
+  for (sn_grid g : b->step_grid) sn_destroy_grid(g);
+  for (cudaStream_t s : b->step_stream)
+    if (s) cudaStreamDestroy(s);
+  b->step_grid.clear();
+  b->step_stream.clear();
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
+  b->fork_ev = b->join_ev = nullptr;
+  b->graph_dt.clear();
+}
+
+// ... made at the schedule's first use; a failure leaves none of them.
 sn_status ensure_step_grids(sn_batch b) {
   if (!b->step_grid.empty()) return SN_OK;
   cudaError_t e;
   if ((e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming)) != cudaSuccess)
+      (e = cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming)) != cudaSuccess) {
+    drop_step_grids(b);
     return bcuda(e, "cudaEventCreate");
+  }
   b->step_grid.assign(b->count, nullptr);
   b->step_stream.assign(b->count, nullptr);
   for (int i = 0; i < b->count; ++i) {
-    if ((e = cudaStreamCreateWithFlags(&b->step_stream[i], cudaStreamNonBlocking)) != cudaSuccess)
+    if ((e = cudaStreamCreateWithFlags(&b->step_stream[i], cudaStreamNonBlocking)) != cudaSuccess) {
+      drop_step_grids(b);
       return bcuda(e, "cudaStreamCreate");
+    }
     const int n2[2] = {b->n[i], b->n[i]};
     const double L2[2] = {b->L[i], b->L[i]};
     sn_status st = sn_create_grid(&b->step_grid[i], 2, n2, L2, SN_C64, b->step_stream[i]);
-    if (st != SN_OK) return st;
+    if (st != SN_OK) {
+      drop_step_grids(b);
+      return st;
+    }
   }
   return SN_OK;
 }
@@ -673,12 +694,7 @@ void sn_destroy_batch(sn_batch b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (sn_grid g : b->obs_grid) sn_destroy_grid(g);
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  drop_round_graphs(b);
-  for (sn_grid g : b->step_grid) sn_destroy_grid(g);
-  for (cudaStream_t s : b->step_stream)
-    if (s) cudaStreamDestroy(s);
-  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
-  if (b->join_ev) cudaEventDestroy(b->join_ev);
+  drop_step_grids(b);
   for (void* p : b->allocs) cudaFree(p);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
