@@ -1,0 +1,117 @@
+"""The largest grid the boundary takes: 1024^3 complex64 (2^30 cells, 8.6 GB a copy of psi).
+
+The passes' line offsets, tile counts and half-spectrum indices reach their
+limits here (a strided line of axis 0 spans 1023 * 2^20 elements; the half
+spectrum holds 513 * 2^20 values).  The FP64 oracle cannot step this grid in
+seconds, so two checks that need no oracle run at this size:
+
+* a free Gaussian (G = g = 0): the split step is then the exact free
+  propagator (Sec. III with a zero potential), and its closed form, summed
+  over periodic images, is evaluated at 4096 sampled cells spread over the
+  whole grid;
+* a self-gravitating Gaussian (G = 1, g = 0.1): the mass over a call is kept
+  to FP32 rounding, and steps of -h after steps of h come back to the initial
+  state within the per-step bar (the merged Strang step is time-reversible).
+
+The initial states are built on the device from their 1D factors (each is a
+product of three 1D Gaussians), and the outputs are compared on the device.
+The grid copies device states on its own stream: torch's work is finished
+before each copy in, and the grid's before torch reads a copy out.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_1909_08354_b300 import sn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+N = 1024
+L = 40.0
+SIGMA = 4.0
+
+
+def factor(t, images=2):
+    """The 1D factor of the free Gaussian exp(-x^2 / (2 sigma^2)) after time t
+    under i psi_t = -(1/2) psi_xx, summed over periodic images:
+    (sigma^2 / s)^(1/2) exp(-x^2 / (2 s)) with s = sigma^2 + i t."""
+    x = W.coords(N, L)
+    s = SIGMA * SIGMA + 1j * t
+    f = sum(np.exp(-(x + j * L) ** 2 / (2 * s)) for j in range(-images, images + 1))
+    return f * np.sqrt(SIGMA * SIGMA / s)
+
+
+def product_state(f):
+    fx = torch.from_numpy(f.astype(np.complex64)).cuda()
+    x = fx[:, None, None] * fx[None, :, None] * fx[None, None, :]
+    torch.cuda.synchronize()
+    return x
+
+
+def mass(x):
+    return float(torch.sum(torch.abs(x).double() ** 2))
+
+
+def test_free_gaussian_1024_cubed_matches_the_closed_form():
+    psi0 = product_state(factor(0.0))
+    g = sn.Grid((N, N, N), (L, L, L), "c64")
+    try:
+        g.set_kernel(G=0.0, g_local=0.0)
+        g.set_state(psi0)
+        g.sync()
+        del psi0
+        h, steps = 0.5, 2
+        g.step(h, steps)
+        out = torch.empty((N, N, N), dtype=torch.complex64, device="cuda")
+        torch.cuda.synchronize()
+        g.get_state(out)
+        g.sync()
+    finally:
+        g.close()
+    rng = np.random.default_rng(11)
+    idx = rng.integers(0, N, size=(4096, 3))
+    ti = torch.from_numpy(idx).cuda()
+    got = out[ti[:, 0], ti[:, 1], ti[:, 2]].cpu().numpy().astype(np.complex128)
+    f = factor(h * steps)
+    want = f[idx[:, 0]] * f[idx[:, 1]] * f[idx[:, 2]]
+    peak = np.abs(f).max() ** 3
+    err = np.abs(got - want).max() / peak
+    # the state moved: the closed form at t = 0 is far from it
+    f0 = factor(0.0)
+    moved = np.abs(f0[idx[:, 0]] * f0[idx[:, 1]] * f0[idx[:, 2]] - want).max() / peak
+    print(f"1024^3 free Gaussian: max |error| / peak {err:.2e} over 4096 cells (change {moved:.2e})")
+    assert moved > 1e-2
+    assert err <= 5e-6
+
+
+def test_self_gravitating_1024_cubed_mass_and_time_reversal():
+    psi0 = product_state(factor(0.0)) * 0.5
+    torch.cuda.synchronize()
+    m0 = mass(psi0)
+    g = sn.Grid((N, N, N), (L, L, L), "c64")
+    try:
+        g.set_kernel(G=1.0, alpha_Y=0.1, lambda_Y=10.0, g_local=0.1)
+        g.set_state(psi0)
+        g.sync()
+        h, steps = 0.01, 3
+        g.step(h, steps)
+        out = torch.empty_like(psi0)
+        torch.cuda.synchronize()
+        g.get_state(out)
+        g.sync()
+        m1 = mass(out)
+        change = float(torch.linalg.vector_norm(out - psi0) / torch.linalg.vector_norm(psi0))
+        torch.cuda.synchronize()
+        g.step(-h, steps)
+        g.get_state(out)
+        g.sync()
+    finally:
+        g.close()
+    back = float(torch.linalg.vector_norm(out - psi0) / torch.linalg.vector_norm(psi0))
+    print(f"1024^3 self-gravitating: mass change {m1 / m0 - 1:.2e} over {steps} steps, "
+          f"state change {change:.2e}, rel-L2 after {steps} steps back {back:.2e}")
+    assert change > 1e-4
+    assert abs(m1 / m0 - 1) <= 1e-6
+    assert back <= 2 * steps * 1e-6
