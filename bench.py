@@ -685,8 +685,9 @@ def run_fluid(sn, torch, stream, n=256, L=40.0, steps=2000, dt=5e-4):
     w = 1.02, n = 1, lambda = 1) on an n^2 complex128 grid: GR and NMC from the same
     Gaussian to t = 1, both timed.  The step resolves the kinetic and Bohm rotation of
     the highest wavenumber (k_max^2 dt / 2 = 0.2 rad at 256^2).  The plain FP64 path:
-    eight full complex FFTs per step (kinetic 4, both Laplacians of rho + i sqrt(rho) 2,
-    Eq. 15 2) at 5 N log2 N flops each."""
+    six full complex FFTs per step (the kinetic factor 2, the half steps of
+    neighbouring steps of a call merged; both Laplacians of rho + i sqrt(rho) 2;
+    Eq. 15 2) at 5 N log2 N flops each, and two more per call."""
     x = -0.5 * L + np.arange(n) * (L / n)
     X, Y = np.meshgrid(x, x, indexing="ij")
     r2 = X * X + Y * Y
@@ -720,8 +721,8 @@ def run_fluid(sn, torch, stream, n=256, L=40.0, steps=2000, dt=5e-4):
         o1 = g.observables()
         drift = o1["mass"] / m0 - 1.0
         g.close()
-        ffts = 8
-        flops = ffts * 5.0 * n * n * np.log2(n * n)
+        ffts = 6 * steps + 2  # the call's first and last half steps do not merge
+        flops = ffts * 5.0 * n * n * np.log2(n * n) / steps
         out[name] = {"value": n * n * steps / t, "unit": "cell-steps/s",
                      "ms_per_step": 1e3 * t / steps, "mass_drift": drift, "final": summary(final),
                      "energy": {"e_kin": o1["e_kin"], "e_pot": o1["e_pot"], "e_nl": o1["e_nl"],

@@ -26,13 +26,16 @@ template <int N>
 struct LinesF64 {
   // lines per CTA: keeps shared memory under ~110 KB for the long lines
   static constexpr int value = N <= 256 ? 16 : (N == 512 ? 8 : 4);
+  // a grid of few lines (a 2D plane of 256^2 or less, say) would leave most
+  // SMs idle at `value` lines a CTA: one warp's worth of lines a CTA instead
+  // (at least one line), the same per-line arithmetic
+  static constexpr int few = Plan<N>::T >= 32 ? 1 : 32 / Plan<N>::T;
 };
 
-template <int N, bool STRIDED, int SIGN>
-__global__ void __launch_bounds__(LinesF64<N>::value * Plan<N>::T)
+template <int N, bool STRIDED, int SIGN, int LPB>
+__global__ void __launch_bounds__(LPB * Plan<N>::T)
 fft_f64_kernel(double2* data, long long outer, long long inner, const double2* tw) {
   using P = Plan<N>;
-  constexpr int LPB = LinesF64<N>::value;
   constexpr int E = P::E, T = P::T, NT = LPB * T, LS = P::LS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<double>* tw_sm = reinterpret_cast<cx<double>*>(smem_raw);
@@ -69,12 +72,11 @@ fft_f64_kernel(double2* data, long long outer, long long inner, const double2* t
   }
 }
 
-template <int N, bool STRIDED, int SIGN>
-cudaError_t launch_fft_t(double2* d, long long outer, long long inner, const double2* tw,
-                         cudaStream_t s) {
-  constexpr int LPB = LinesF64<N>::value;
+template <int N, bool STRIDED, int SIGN, int LPB>
+cudaError_t launch_fft_lpb(double2* d, long long outer, long long inner, const double2* tw,
+                           cudaStream_t s) {
   constexpr size_t smem = (size_t)(Plan<N>::TWN + LPB * Plan<N>::LS) * sizeof(cx<double>);
-  auto kern = fft_f64_kernel<N, STRIDED, SIGN>;
+  auto kern = fft_f64_kernel<N, STRIDED, SIGN, LPB>;
   static bool attr_of[kDeviceSlots] = {};
   bool& attr = attr_of[device_slot()];
   if (!attr) {
@@ -87,6 +89,18 @@ cudaError_t launch_fft_t(double2* d, long long outer, long long inner, const dou
                       : dim3((unsigned)((outer + LPB - 1) / LPB));
   kern<<<grid, block, smem, s>>>(d, outer, inner, tw);
   return cudaGetLastError();
+}
+
+// Lines per CTA: LinesF64::value, or LinesF64::few when that leaves fewer
+// than two CTAs per SM of the B300's 148 (the results are the same bits).
+template <int N, bool STRIDED, int SIGN>
+cudaError_t launch_fft_t(double2* d, long long outer, long long inner, const double2* tw,
+                         cudaStream_t s) {
+  constexpr int LPB = LinesF64<N>::value, FEW = LinesF64<N>::few;
+  const long long lines = outer * inner;
+  if (FEW < LPB && (lines + LPB - 1) / LPB < 2 * 148)
+    return launch_fft_lpb<N, STRIDED, SIGN, FEW>(d, outer, inner, tw, s);
+  return launch_fft_lpb<N, STRIDED, SIGN, LPB>(d, outer, inner, tw, s);
 }
 
 template <int N>

@@ -827,14 +827,16 @@ sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
   fp.cp = g->fl.n_poly == 1.0 ? 0.0 : g->fl.n_poly * g->fl.w / (g->fl.n_poly - 1.0);
   fp.rho_floor = g->fl.rho_floor;
   fp.floor_mode = g->fl.floor_mode;
+  // S(h)^n = Kin(h/2) [Nl(h) Kin(h)]^(n-1) Nl(h) Kin(h/2): the half steps
+  // between two steps of the call merge into one Kin(h)
+  if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
   for (int s = 0; s < nsteps; ++s) {
-    if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
     // lap rho (Eq. 15) and lap sqrt rho (Bohm) in one FFT pair, then phi_N
     if ((st = fluid_fields(g, psi, wa, w)) != SN_OK) return st;
     SN_LAUNCH(g, K_F64_EW, (nmc ? 56.0 : 48.0) * g->cells,
               launch_fluid_phase_f64(psi, w, wa, nmc ? g->prof64[2] : nullptr, fp, g->cells,
                                      g->stream));
-    if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
+    if ((st = kinetic_f64(g, s + 1 < nsteps ? 1 : 0)) != SN_OK) return st;
   }
   return SN_OK;
 }
