@@ -173,6 +173,13 @@ struct sn_grid_s {
   // gamma, beta, phi_C per cell (NMC only), and a third FP64 scratch array
   bool fluid = false;
   sn_fluid fl{};
+  // the middle step of a fluid call (the potential sub-step and Kin(h)),
+  // captured for the dt in fluid_graph_dt and the fluid parameters in
+  // fluid_graph_fl, with the kernels it launches
+  cudaGraphExec_t fluid_graph = nullptr;
+  double fluid_graph_dt = std::nan("");
+  sn_fluid fluid_graph_fl{};
+  long long fluid_graph_launches = 0;
   double* prof64[3] = {};
   double2* w64c = nullptr;
 
@@ -779,7 +786,8 @@ sn_status step_f64(sn_grid g, double dt, int nsteps) {
 // kinetic half steps use A = -nu/2 (set by sn_set_fluid); the potential
 // sub-step forms rho + i sqrt(rho) and takes both spectral Laplacians with one
 // FFT pair, forms the source of Eq. 15 and its inverse Laplacian, then turns
-// psi by U h / nu: eight full complex FFTs per step.
+// psi by U h / nu: six full complex FFTs per step, the kinetic half steps of
+// neighbouring steps of a call merged into one.
 // The fields of Eq. 16's potential from psi: wa = lap rho + i lap sqrt(rho)
 // (sqrt of max(rho, floor); both Laplacians from one FFT pair of rho + i sqrt
 // rho) and w = phi_N of Eq. 15 (real part).  Four full complex FFTs.
@@ -827,18 +835,63 @@ sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
   fp.cp = g->fl.n_poly == 1.0 ? 0.0 : g->fl.n_poly * g->fl.w / (g->fl.n_poly - 1.0);
   fp.rho_floor = g->fl.rho_floor;
   fp.floor_mode = g->fl.floor_mode;
-  // S(h)^n = Kin(h/2) [Nl(h) Kin(h)]^(n-1) Nl(h) Kin(h/2): the half steps
-  // between two steps of the call merge into one Kin(h)
-  if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
-  for (int s = 0; s < nsteps; ++s) {
+  // Nl(h) then Kin(h) (full) or Kin(h/2)
+  auto step_body = [&](int full) -> sn_status {
     // lap rho (Eq. 15) and lap sqrt rho (Bohm) in one FFT pair, then phi_N
-    if ((st = fluid_fields(g, psi, wa, w)) != SN_OK) return st;
+    sn_status r = fluid_fields(g, psi, wa, w);
+    if (r != SN_OK) return r;
     SN_LAUNCH(g, K_F64_EW, (nmc ? 56.0 : 48.0) * g->cells,
               launch_fluid_phase_f64(psi, w, wa, nmc ? g->prof64[2] : nullptr, fp, g->cells,
                                      g->stream));
-    if ((st = kinetic_f64(g, s + 1 < nsteps ? 1 : 0)) != SN_OK) return st;
+    return kinetic_f64(g, full);
+  };
+  // S(h)^n = Kin(h/2) [Nl(h) Kin(h)]^(n-1) Nl(h) Kin(h/2): the half steps
+  // between two steps of the call merge into one Kin(h)
+  if ((st = kinetic_f64(g, 0)) != SN_OK) return st;
+  // the n - 1 middle steps replay one captured step (its launches carry
+  // dt and the fluid parameters); not while the passes are being profiled
+  const bool replay = nsteps > 2 && !g->profiling;
+  if (replay && g->fluid_graph &&
+      (g->fluid_graph_dt != dt || std::memcmp(&g->fluid_graph_fl, &g->fl, sizeof(sn_fluid)) != 0)) {
+    cudaGraphExecDestroy(g->fluid_graph);
+    g->fluid_graph = nullptr;
   }
-  return SN_OK;
+  bool replay_now = replay;
+  if (replay && !g->fluid_graph) {
+    // captured launches do not run: a stream that cannot be captured (the
+    // legacy default stream, say) steps without the graph
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      replay_now = false;
+    } else {
+      const long long before = g->launches;
+      const sn_status sc = step_body(1);
+      cudaError_t e = cudaStreamEndCapture(g->stream, &gr);
+      const long long captured = g->launches - before;
+      g->launches = before;
+      if (sc != SN_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return sc;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&g->fluid_graph, gr, 0);
+      if (gr) cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return cuda_fail(g, e, "fluid step capture");
+      g->fluid_graph_launches = captured;
+      g->fluid_graph_dt = dt;
+      g->fluid_graph_fl = g->fl;
+    }
+  }
+  for (int s = 0; s + 1 < nsteps; ++s) {
+    if (replay_now) {
+      const cudaError_t e = cudaGraphLaunch(g->fluid_graph, g->stream);
+      if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphLaunch");
+      g->launches += g->fluid_graph_launches;
+    } else if ((st = step_body(1)) != SN_OK) {
+      return st;
+    }
+  }
+  return step_body(0);
 }
 
 sn_status do_step(sn_grid g, double dt, int nsteps) {
@@ -1053,6 +1106,13 @@ sn_status sn_set_fluid(sn_grid g, const sn_fluid* f) {
   if (!(f->nu > 0.0) || !std::isfinite(f->nu) || !std::isfinite(f->w) ||
       !std::isfinite(f->n_poly) || !(f->rho_floor > 0.0) || !std::isfinite(f->rho_floor))
     return fail(g, SN_EINVAL, "sn_set_fluid: nu and rho_floor must be finite and > 0, w and n finite");
+  // queued steps may still read the profiles and the captured step
+  if (cudaError_t e0 = cudaStreamSynchronize(g->stream); e0 != cudaSuccess)
+    return cuda_fail(g, e0, "sn_set_fluid: cudaStreamSynchronize");
+  if (g->fluid_graph) {
+    cudaGraphExecDestroy(g->fluid_graph);
+    g->fluid_graph = nullptr;
+  }
   if (f->floor_mode != SN_FLOOR_MAX && f->floor_mode != SN_FLOOR_SMOOTH)
     return fail(g, SN_EINVAL, "sn_set_fluid: floor_mode must be SN_FLOOR_MAX or SN_FLOOR_SMOOTH");
   if (f->model != SN_GRAVITY_GR && f->model != SN_GRAVITY_NMC)
@@ -1766,6 +1826,7 @@ const char* sn_kind_name(int k) {
 void sn_destroy_grid(sn_grid g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->fluid_graph) cudaGraphExecDestroy(g->fluid_graph);
   for (void* p : g->allocs) cudaFree(p);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   delete g;

@@ -98,6 +98,32 @@ def test_fluid_mass_conservation_and_time_reversal():
     assert np.abs(back - psi).max() < 1e-9 * np.abs(psi).max()
 
 
+def test_replayed_steps_follow_dt_and_parameter_changes():
+    """A call of more than two steps replays its middle steps from a captured
+    step (the launches carry dt and the fluid parameters): a change of dt, of
+    the model and of nu between calls must each take effect."""
+    shape, L = (64, 64), (24.0, 24.0)
+    psi = gaussian_fluid(shape, L, seed=9)
+    pg = params(sn.SN_GRAVITY_GR)
+    pn = params(sn.SN_GRAVITY_NMC, nu=0.8)
+    g = sn.Grid(shape, L, "c128")
+    try:
+        g.set_fluid(model=sn.SN_GRAVITY_GR, **pg)
+        g.set_state(psi)
+        g.step(0.01, 4)
+        g.step(0.01, 3)
+        g.step(0.005, 4)
+        g.set_fluid(model=sn.SN_GRAVITY_NMC, **pn)
+        g.step(0.005, 5)
+        out = g.get_state()
+    finally:
+        g.close()
+    ref = C.cosmo_evolve(psi, 0.01, 7, L, to_oracle(sn.SN_GRAVITY_GR, pg))
+    ref = C.cosmo_evolve(ref, 0.005, 4, L, to_oracle(sn.SN_GRAVITY_GR, pg))
+    ref = C.cosmo_evolve(ref, 0.005, 5, L, to_oracle(sn.SN_GRAVITY_NMC, pn))
+    assert O.rel_l2(out, ref) <= 16 * TOL, O.rel_l2(out, ref)
+
+
 def test_nmc_and_gr_differ_and_set_kernel_switches_back():
     shape, L = (64, 64), (24.0, 24.0)
     psi = gaussian_fluid(shape, L, seed=2)
