@@ -172,6 +172,107 @@ __global__ void head_bwd_kernel(const float* a, const float* y, const float* dou
   }
 }
 
+// The lift, 1x1 from the input channels: v[b][c][p] = bias[c] + sum_i
+// W[c][i] a[b][i][p] (i in order), FP32.  Each thread takes four neighbouring
+// pixels of one sample (P is a multiple of 4) and writes every channel; W and
+// the bias sit in shared memory.
+constexpr int kLiftMaxIn = 16;
+__global__ void lift_kernel(const float* a, const float* W, const float* bias, float* v, int ci,
+                            int C, ll P, ll B) {
+  extern __shared__ float lift_sm[];
+  float* Ws = lift_sm;       // [C][ci]
+  float* bs = lift_sm + C * ci;
+  for (int k = threadIdx.x; k < C * ci; k += blockDim.x) Ws[k] = W[k];
+  for (int k = threadIdx.x; k < C; k += blockDim.x) bs[k] = bias[k];
+  __syncthreads();
+  const ll P4 = P / 4, n4 = B * P4;
+  for (ll q = blockIdx.x * (ll)blockDim.x + threadIdx.x; q < n4; q += (ll)gridDim.x * blockDim.x) {
+    const ll b = q / P4, p = 4 * (q - b * P4);
+    float4 x[kLiftMaxIn];
+#pragma unroll
+    for (int i = 0; i < kLiftMaxIn; ++i)
+      if (i < ci) x[i] = *reinterpret_cast<const float4*>(a + (b * ci + i) * P + p);
+    for (int c = 0; c < C; ++c) {
+      float4 acc = make_float4(bs[c], bs[c], bs[c], bs[c]);
+#pragma unroll
+      for (int i = 0; i < kLiftMaxIn; ++i) {
+        if (i < ci) {
+          const float w = Ws[c * ci + i];
+          acc.x = fmaf(w, x[i].x, acc.x);
+          acc.y = fmaf(w, x[i].y, acc.y);
+          acc.z = fmaf(w, x[i].z, acc.z);
+          acc.w = fmaf(w, x[i].w, acc.w);
+        }
+      }
+      *reinterpret_cast<float4*>(v + (b * C + c) * P + p) = acc;
+    }
+  }
+}
+
+// The projection's last 1x1 and the head, per pixel: y[k] = b2[k] + sum_j
+// Q2[k][j] h[b][j][p] (j in order, k = phi, dr, di), kept in yh for the
+// backward, then out = psi e^{-i phi} + (dr + i di) as head_kernel, FP32.
+__global__ void proj_head_kernel(const float* h, const float* Q2, const float* b2, const float* a,
+                                 float* yh, float* out, int J, int ci, ll P, ll B) {
+  extern __shared__ float head_sm[];
+  for (int k = threadIdx.x; k < 3 * J; k += blockDim.x) head_sm[k] = Q2[k];
+  __syncthreads();
+  const ll P4 = P / 4, n4 = B * P4;
+  for (ll q = blockIdx.x * (ll)blockDim.x + threadIdx.x; q < n4; q += (ll)gridDim.x * blockDim.x) {
+    const ll b = q / P4, p = 4 * (q - b * P4);
+    float4 y[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) y[k] = make_float4(b2[k], b2[k], b2[k], b2[k]);
+    const float* hb = h + b * J * P + p;
+    for (int j = 0; j < J; ++j) {
+      const float4 x = *reinterpret_cast<const float4*>(hb + (ll)j * P);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float w = head_sm[k * J + j];
+        y[k].x = fmaf(w, x.x, y[k].x);
+        y[k].y = fmaf(w, x.y, y[k].y);
+        y[k].z = fmaf(w, x.z, y[k].z);
+        y[k].w = fmaf(w, x.w, y[k].w);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) *reinterpret_cast<float4*>(yh + (b * 3 + k) * P + p) = y[k];
+    const float4 pr = *reinterpret_cast<const float4*>(a + b * ci * P + p);
+    const float4 pi = *reinterpret_cast<const float4*>(a + b * ci * P + P + p);
+    float4 o_r, o_i;
+    float s, c;
+    sincosf(y[0].x, &s, &c); o_r.x = pr.x * c + pi.x * s + y[1].x; o_i.x = pi.x * c - pr.x * s + y[2].x;
+    sincosf(y[0].y, &s, &c); o_r.y = pr.y * c + pi.y * s + y[1].y; o_i.y = pi.y * c - pr.y * s + y[2].y;
+    sincosf(y[0].z, &s, &c); o_r.z = pr.z * c + pi.z * s + y[1].z; o_i.z = pi.z * c - pr.z * s + y[2].z;
+    sincosf(y[0].w, &s, &c); o_r.w = pr.w * c + pi.w * s + y[1].w; o_i.w = pi.w * c - pr.w * s + y[2].w;
+    *reinterpret_cast<float4*>(out + b * 2 * P + p) = o_r;
+    *reinterpret_cast<float4*>(out + b * 2 * P + P + p) = o_i;
+  }
+}
+
+// The backward of the projection's last 1x1 through the GELU before it:
+// dh[b][j][p] = GELU'(g1[b][j][p]) sum_k Q2[k][j] dy[b][k][p], FP32.
+__global__ void proj_dh_kernel(const float* dy, const float* Q2, const float* g1, float* dh, int J,
+                               ll P, ll B) {
+  const ll P4 = P / 4, n4 = B * (ll)J * P4;
+  for (ll q = blockIdx.x * (ll)blockDim.x + threadIdx.x; q < n4; q += (ll)gridDim.x * blockDim.x) {
+    const ll row = q / P4, p = 4 * (q - row * P4);  // row = b J + j
+    const ll b = row / J;
+    const int j = (int)(row - b * J);
+    const float w0 = Q2[j], w1 = Q2[J + j], w2 = Q2[2 * J + j];
+    const float4 d0 = *reinterpret_cast<const float4*>(dy + (b * 3) * P + p);
+    const float4 d1 = *reinterpret_cast<const float4*>(dy + (b * 3 + 1) * P + p);
+    const float4 d2 = *reinterpret_cast<const float4*>(dy + (b * 3 + 2) * P + p);
+    const float4 z = *reinterpret_cast<const float4*>(g1 + row * P + p);
+    float4 r;
+    r.x = fmaf(w2, d2.x, fmaf(w1, d1.x, w0 * d0.x)) * gelu_grad(z.x);
+    r.y = fmaf(w2, d2.y, fmaf(w1, d1.y, w0 * d0.y)) * gelu_grad(z.y);
+    r.z = fmaf(w2, d2.z, fmaf(w1, d1.z, w0 * d0.z)) * gelu_grad(z.z);
+    r.w = fmaf(w2, d2.w, fmaf(w1, d1.w, w0 * d0.w)) * gelu_grad(z.w);
+    *reinterpret_cast<float4*>(dh + row * P + p) = r;
+  }
+}
+
 // out[c] = sum_b sum_p X[b][c][p] in a fixed order: block (c, j) sums span j of
 // every row of channel c into part[c][j] (FP64), then one thread per channel
 // adds its parts.
@@ -394,13 +495,15 @@ __global__ void mode_mix_bwd_kernel(const float* V, const float* R, const float*
 
 cudaError_t gemm(sn_fno f, int M, int N, int K, int Z, const float* A, ll sAz, ll sAm, ll sAk,
                  const float* B, ll sBz, ll sBk, ll sBn, float* C, ll sCz, ll sCm, ll sCn,
-                 float alpha = 1.f, float beta = 0.f) {
+                 float alpha = 1.f, float beta = 0.f, const float* bias = nullptr,
+                 float* C2 = nullptr, int act = 0) {
   GemmArgs g{};
   g.A = A; g.sAz = sAz; g.sAm = sAm; g.sAk = sAk;
   g.B = B; g.sBz = sBz; g.sBk = sBk; g.sBn = sBn;
   g.C = C; g.sCz = sCz; g.sCm = sCm; g.sCn = sCn; g.sCsp = 0;
   g.M = M; g.N = N; g.K = K; g.Z = Z; g.kchunk = 0;
   g.alpha = alpha; g.beta = beta;
+  g.bias = bias; g.C2 = C2; g.act = act;
   return gemm_bf16(g, f->stream);
 }
 
@@ -679,9 +782,14 @@ sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
   cudaStream_t st = f->stream;
   float* prm = f->params;
   FCHK(cudaMemcpyAsync(f->a, in, (size_t)B * ci * P * sizeof(float), cudaMemcpyDeviceToDevice, st));
-  // lift
-  FCHK(gemm(f, (int)C, (int)P, (int)ci, B, prm + f->off_P, 0, ci, 1, f->a, ci * P, P, 1, f->v[0], C * P, P, 1));
-  bias_act_kernel<<<rows_grid(B * C, P), 256, 0, st>>>(f->v[0], prm + f->off_pb, nullptr, C, P, 0);
+  // lift: one pass over the input on the CUDA cores (few input channels)
+  if (ci <= kLiftMaxIn && P % 4 == 0) {
+    lift_kernel<<<blocks_for(B * P / 4), 256, (size_t)(C * ci + C) * sizeof(float), st>>>(
+        f->a, prm + f->off_P, prm + f->off_pb, f->v[0], (int)ci, (int)C, P, B);
+  } else {
+    FCHK(gemm(f, (int)C, (int)P, (int)ci, B, prm + f->off_P, 0, ci, 1, f->a, ci * P, P, 1, f->v[0], C * P, P, 1));
+    bias_act_kernel<<<rows_grid(B * C, P), 256, 0, st>>>(f->v[0], prm + f->off_pb, nullptr, C, P, 0);
+  }
   FCHK(cudaGetLastError());
   for (int l = 0; l < f->L; ++l) {
     FCHK(dft_forward(f, f->v[l], B, (int)C, f->ExF, f->Vh[l]));
@@ -696,17 +804,23 @@ sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
       continue;
     }
     FCHK(dft_inverse(f, f->Uh, B, (int)C, f->WxI, f->z[l], 0.f));
-    FCHK(gemm(f, (int)C, (int)P, (int)C, B, prm + f->off_W[l], 0, C, 1, f->v[l], C * P, P, 1, f->z[l], C * P, P, 1, 1.f, 1.f));
-    bias_act_kernel<<<rows_grid(B * C, P), 256, 0, st>>>(f->z[l], prm + f->off_b[l], f->v[l + 1], C, P, act);
-    FCHK(cudaGetLastError());
+    // z = W v + the spectral branch + bias, and v' = GELU(z) (or z), in the GEMM's epilogue
+    FCHK(gemm(f, (int)C, (int)P, (int)C, B, prm + f->off_W[l], 0, C, 1, f->v[l], C * P, P, 1, f->z[l],
+              C * P, P, 1, 1.f, 1.f, prm + f->off_b[l], f->v[l + 1], act));
   }
   // projection
-  FCHK(gemm(f, (int)J, (int)P, (int)C, B, prm + f->off_Q1, 0, C, 1, f->v[f->L], C * P, P, 1, f->g1, J * P, P, 1));
-  bias_act_kernel<<<rows_grid(B * J, P), 256, 0, st>>>(f->g1, prm + f->off_q1b, f->h, J, P, 1);
-  FCHK(cudaGetLastError());
-  FCHK(gemm(f, 3, (int)P, (int)J, B, prm + f->off_Q2, 0, J, 1, f->h, J * P, P, 1, f->yh, 3 * P, P, 1));
-  bias_act_kernel<<<rows_grid(B * 3, P), 256, 0, st>>>(f->yh, prm + f->off_q2b, nullptr, 3, P, 0);
-  head_kernel<<<blocks_for(B * P), 256, 0, st>>>(f->a, f->yh, f->out, ci, P, B * P);
+  // g1 = Q1 v + bias and h = GELU(g1) in the GEMM's epilogue
+  FCHK(gemm(f, (int)J, (int)P, (int)C, B, prm + f->off_Q1, 0, C, 1, f->v[f->L], C * P, P, 1, f->g1,
+            J * P, P, 1, 1.f, 0.f, prm + f->off_q1b, f->h, 1));
+  if (P % 4 == 0) {
+    // the last 1x1 (three outputs) and the head in one pass over h
+    proj_head_kernel<<<blocks_for(B * P / 4), 256, (size_t)3 * J * sizeof(float), st>>>(
+        f->h, prm + f->off_Q2, prm + f->off_q2b, f->a, f->yh, f->out, (int)J, (int)ci, P, B);
+  } else {
+    FCHK(gemm(f, 3, (int)P, (int)J, B, prm + f->off_Q2, 0, J, 1, f->h, J * P, P, 1, f->yh, 3 * P, P, 1));
+    bias_act_kernel<<<rows_grid(B * 3, P), 256, 0, st>>>(f->yh, prm + f->off_q2b, nullptr, 3, P, 0);
+    head_kernel<<<blocks_for(B * P), 256, 0, st>>>(f->a, f->yh, f->out, ci, P, B * P);
+  }
   FCHK(cudaGetLastError());
   if (out != f->out)
     FCHK(cudaMemcpyAsync(out, f->out, (size_t)B * 2 * P * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -742,8 +856,13 @@ sn_status sn_fno_backward(sn_fno f) {
   FCHK(cudaGetLastError());
   FCHK(weight_grad(f, f->dy, f->h, B, 3, (int)J, gr + f->off_Q2));
   channel_sum(f, f->dy, B, 3, P, gr + f->off_q2b);
-  FCHK(gemm(f, (int)J, (int)P, 3, B, prm + f->off_Q2, 0, 1, J, f->dy, 3 * P, P, 1, f->dh, J * P, P, 1));
-  gelu_bwd_kernel<<<blocks_for(B * J * P), 256, 0, st>>>(f->dh, f->g1, f->dh, B * J * P);
+  if (P % 4 == 0) {
+    proj_dh_kernel<<<blocks_for(B * J * P / 4), 256, 0, st>>>(f->dy, prm + f->off_Q2, f->g1, f->dh,
+                                                             (int)J, P, B);
+  } else {
+    FCHK(gemm(f, (int)J, (int)P, 3, B, prm + f->off_Q2, 0, 1, J, f->dy, 3 * P, P, 1, f->dh, J * P, P, 1));
+    gelu_bwd_kernel<<<blocks_for(B * J * P), 256, 0, st>>>(f->dh, f->g1, f->dh, B * J * P);
+  }
   FCHK(cudaGetLastError());
   FCHK(weight_grad(f, f->dh, f->v[f->L], B, (int)J, (int)C, gr + f->off_Q1));
   channel_sum(f, f->dh, B, J, P, gr + f->off_q1b);

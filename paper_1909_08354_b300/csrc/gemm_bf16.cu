@@ -20,6 +20,11 @@ namespace sn {
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 32, PADK = 8, THREADS = 128;
+
+// the epilogue's activation: x Phi(x) with the error function
+__device__ __forceinline__ float gelu_erf(float x) {
+  return 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
+}
 constexpr int TILE = BM * BK;          // elements of one operand tile (BN * BK too)
 constexpr int PER = TILE / THREADS;    // elements per thread per operand tile
 constexpr int CST = BN + 4;            // row stride of the staged C tile (floats)
@@ -187,6 +192,7 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(GemmArgs g, int nsplit) {
     __syncthreads();
   }
   float* C = g.C + z * g.sCz + (long long)sp * g.sCsp;
+  float* C2 = g.C2 != nullptr ? g.C2 + z * g.sCz : nullptr;
   if constexpr (CVEC) {
     // stage the tile, then float4 rows (n contiguous, sCm a multiple of 4, C aligned)
     float* Cs = reinterpret_cast<float*>(smem);
@@ -208,6 +214,8 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(GemmArgs g, int nsplit) {
       const int gm = m0 + m, gn = n0 + n;
       if (gm >= g.M) continue;
       float* p = C + (long long)gm * g.sCm + gn;
+      float* p2 = C2 != nullptr ? C2 + (long long)gm * g.sCm + gn : nullptr;
+      const float bm = g.bias != nullptr ? g.bias[gm] : 0.f;
       const float4 a = *reinterpret_cast<const float4*>(&Cs[m * CST + n]);
       if (gn + 3 < g.N) {
         float4 v = make_float4(g.alpha * a.x, g.alpha * a.y, g.alpha * a.z, g.alpha * a.w);
@@ -215,11 +223,20 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(GemmArgs g, int nsplit) {
           const float4 c = *reinterpret_cast<const float4*>(p);
           v.x += g.beta * c.x; v.y += g.beta * c.y; v.z += g.beta * c.z; v.w += g.beta * c.w;
         }
+        if (g.bias != nullptr) { v.x += bm; v.y += bm; v.z += bm; v.w += bm; }
         *reinterpret_cast<float4*>(p) = v;
+        if (p2 != nullptr) {
+          if (g.act) v = make_float4(gelu_erf(v.x), gelu_erf(v.y), gelu_erf(v.z), gelu_erf(v.w));
+          *reinterpret_cast<float4*>(p2) = v;
+        }
       } else {
         const float av[4] = {a.x, a.y, a.z, a.w};
-        for (int j = 0; j < 4 && gn + j < g.N; ++j)
-          p[j] = (g.beta != 0.f) ? g.alpha * av[j] + g.beta * p[j] : g.alpha * av[j];
+        for (int j = 0; j < 4 && gn + j < g.N; ++j) {
+          float v = (g.beta != 0.f) ? g.alpha * av[j] + g.beta * p[j] : g.alpha * av[j];
+          if (g.bias != nullptr) v += bm;
+          p[j] = v;
+          if (p2 != nullptr) p2[j] = g.act ? gelu_erf(v) : v;
+        }
       }
     }
   } else {
@@ -296,6 +313,10 @@ cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
   if (!chunk4) { ma &= 1; mb &= 1; }
   const bool cvec = g.sCn == 1 && aligned16(g.C) && g.sCm % 4 == 0 && g.sCz % 4 == 0 &&
                     g.sCsp % 4 == 0;
+  // the epilogue runs in the staged-C path of a GEMM without split-K
+  if ((g.bias != nullptr || g.C2 != nullptr) &&
+      (!cvec || nsplit != 1 || (g.C2 != nullptr && !aligned16(g.C2))))
+    return cudaErrorInvalidValue;
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)zs);
   switch (ma) {
     case 0: return launch2<0>(g, mb, nsplit, cvec, grid, s);

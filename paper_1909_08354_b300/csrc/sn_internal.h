@@ -282,6 +282,12 @@ struct GemmArgs {
   long long sCz, sCm, sCn, sCsp;
   int M, N, K, Z, kchunk;
   float alpha, beta;
+  // optional epilogue (no split-K; rows of C contiguous and 16-byte aligned):
+  // C = alpha A B + beta C + bias[m], and C2 (the strides of C) = GELU of
+  // that (act) or a copy; NULL bias and C2 for none
+  const float* bias;
+  float* C2;
+  int act;
 };
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);
 // out[i] = sum_{j<count} part[j*stride + i] (+ beta * out[i]) for i < n
