@@ -734,6 +734,26 @@ def run_fluid(sn, torch, stream, n=256, L=40.0, steps=2000, dt=5e-4):
     return out
 
 
+def fno_forward_bytes(s, ci, C, m, layers, J):
+    """Algorithmic HBM bytes of one sample's forward in the fused-layer
+    schedule (FP32 activations, each kernel's inputs read and outputs written
+    once): the lift (a in, v out); per layer the DFT along x (v in, its 2m
+    modes out), along y and the mode mixing (the 2m-mode planes in and out),
+    the inverse along y (the planes of 2m modes out) and the fused layer
+    kernel (v and those planes in, z and v' out); the 64 -> J projection (v
+    in, its pre- and post-GELU outputs out) and the head (the hidden layer
+    and psi in, y and the output out)."""
+    P = s * s
+    f = 4.0
+    plane_modes = C * s * 2 * m * f      # a channel set of 2m modes along one axis
+    lift = (ci + C) * P * f
+    layer = (C * P * f + plane_modes) + 2 * plane_modes + plane_modes + \
+            (C * P * f + plane_modes + 2 * C * P * f)
+    proj = C * P * f + 2 * J * P * f
+    head = J * P * f + 2 * P * f + 3 * P * f + 2 * P * f
+    return lift + layers * layer + proj + head
+
+
 def run_fno(sn, torch, stream, iters=10):
     """Training throughput of the FNO surrogate at its full size (256^2, width 64,
     24x24 modes, 4 layers, projection 128, batch 16): forward + loss + backward + Adam."""
@@ -770,8 +790,13 @@ def run_fno(sn, torch, stream, iters=10):
     t_train = (time.perf_counter() - t0) / iters
     n = net.nparams
     net.close()
+    fb = fno_forward_bytes(s, c_in, 64, 24, 4, 128) * B
+    peak, peak_source = measured_peaks()
     return {"network": "FNO 256^2, width 64, 24x24 modes, 4 spectral layers, projection 128, "
                        "phase head", "params": n, "batch": B,
+            "roofline": {"bound": "hbm", "achieved": fb / t_fwd / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": fb / t_fwd / 1e9 / peak, "peak_source": peak_source,
+                         "bytes_per_forward": fb, "of": "the forward in the faster layer form"},
             "forward_samples_per_s": B / t_fwd, "train_samples_per_s": B / t_train,
             "train_step_ms": 1e3 * t_train,
             "forward_ms": {"gemm_layers": 1e3 * t_form[sn.SN_FNO_LAYER_GEMMS],
