@@ -481,7 +481,38 @@ def run_configs(sn, torch, stream, peak, main_value):
         t = time_grid_steps(sn, torch, stream, w, "c64", 200)
         out[f"nbody_256_alpha_{alpha:g}"] = {"value": w.cells / t, "unit": UNIT,
                                              "ms_per_step": 1e3 * t}
+    out["gaussian_128_observables_every_step"] = run_c1(sn, torch, stream)
     return out
+
+
+def run_c1(sn, torch, stream, steps=200):
+    """The 2D Gaussian of 128^2 (complex128, the plain FP64 step; and the same
+    state in complex64 on the fused step) for 200 steps with the observables
+    after every step: host wall time per step and observables call."""
+    w = W.centred_gaussian_2d()
+    row = {"workload": f"gaussian2d_128: 128^2, L=20, sigma=1.5, Newton G=1, g=0, dt={w.dt:g}, "
+                       f"{steps} steps, sn_observables after every step"}
+    for dtype, mode, name in (("c128", sn.SN_OBS_FP64, "complex128_fp64_observables"),
+                              ("c64", sn.SN_OBS_FP32, "complex64_fp32_observables")):
+        g = sn.Grid(w.n, w.L, dtype, stream=stream.cuda_stream)
+        try:
+            g.set_kernel(**kernel_kw(w.kernel))
+            if dtype == "c64":
+                g.set_obs_mode(mode)
+            g.set_state(w.psi0().astype(np.complex64 if dtype == "c64" else np.complex128))
+            for _ in range(5):
+                g.step(w.dt, 1)
+                g.observables()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                g.step(w.dt, 1)
+                o = g.observables()
+            t = (time.perf_counter() - t0) / steps
+            row[name] = {"ms_per_step_with_observables": 1e3 * t, "mass": o["mass"],
+                         "ms_per_step_alone": 1e3 * time_grid_steps(sn, torch, stream, w, dtype, 200)}
+        finally:
+            g.close()
+    return row
 
 
 def run_f2(sn, torch, stream, peak):
