@@ -783,7 +783,7 @@ sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
   float* prm = f->params;
   FCHK(cudaMemcpyAsync(f->a, in, (size_t)B * ci * P * sizeof(float), cudaMemcpyDeviceToDevice, st));
   // lift: one pass over the input on the CUDA cores (few input channels)
-  if (ci <= kLiftMaxIn && P % 4 == 0) {
+  if (ci <= kLiftMaxIn && P % 4 == 0 && (C * ci + C) * sizeof(float) <= 48 * 1024) {
     lift_kernel<<<blocks_for(B * P / 4), 256, (size_t)(C * ci + C) * sizeof(float), st>>>(
         f->a, prm + f->off_P, prm + f->off_pb, f->v[0], (int)ci, (int)C, P, B);
   } else {
@@ -812,7 +812,7 @@ sn_status sn_fno_forward(sn_fno f, const float* in, float* out, int B) {
   // g1 = Q1 v + bias and h = GELU(g1) in the GEMM's epilogue
   FCHK(gemm(f, (int)J, (int)P, (int)C, B, prm + f->off_Q1, 0, C, 1, f->v[f->L], C * P, P, 1, f->g1,
             J * P, P, 1, 1.f, 0.f, prm + f->off_q1b, f->h, 1));
-  if (P % 4 == 0) {
+  if (P % 4 == 0 && 3 * J * sizeof(float) <= 48 * 1024) {
     // the last 1x1 (three outputs) and the head in one pass over h
     proj_head_kernel<<<blocks_for(B * P / 4), 256, (size_t)3 * J * sizeof(float), st>>>(
         f->h, prm + f->off_Q2, prm + f->off_q2b, f->a, f->yh, f->out, (int)J, (int)ci, P, B);
