@@ -9,6 +9,7 @@
 // sub-step leaves unchanged, so the sub-step is exact.
 #include <cuda_runtime.h>
 
+#include "pdl.cuh"
 #include "sn_internal.h"
 
 namespace sn {
@@ -36,6 +37,8 @@ __device__ __forceinline__ double floored(double rho, double floor, int mode) {
 // Laplacians (real part: lap rho, imaginary part: lap sqrt rho)
 __global__ void prep_kernel(const double2* psi, double2* wa, double floor, int mode,
                             long long cells) {
+  pdl_allow_next();
+  pdl_wait_prev();
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const double rho = density(psi, c);
@@ -47,6 +50,8 @@ __global__ void prep_kernel(const double2* psi, double2* wa, double floor, int m
 __global__ void lap_mult_kernel(double2* w, long long n0, long long n1, long long n2,
                                 const double* k20, const double* k21, const double* k22,
                                 double scale) {
+  pdl_allow_next();
+  pdl_wait_prev();
   const long long cells = n0 * n1 * n2;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
@@ -62,6 +67,8 @@ __global__ void lap_mult_kernel(double2* w, long long n0, long long n1, long lon
 // beta = 0, gamma == NULL means gamma = 1/2 (GR)
 __global__ void source_kernel(const double2* psi, const double2* wlap, double2* w,
                               const double* gamma, const double* beta, long long cells) {
+  pdl_allow_next();
+  pdl_wait_prev();
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const double g = gamma ? gamma[c] : 0.5;
@@ -73,6 +80,8 @@ __global__ void source_kernel(const double2* psi, const double2* wlap, double2* 
 
 __global__ void phase_kernel(double2* psi, const double2* wphi, const double2* wlap,
                              const double* phi_c, FluidPhase p, long long cells) {
+  pdl_allow_next();
+  pdl_wait_prev();
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const double2 z = psi[c];
@@ -91,8 +100,8 @@ __global__ void phase_kernel(double2* psi, const double2* wphi, const double2* w
 
 cudaError_t launch_fluid_prep_f64(const double2* psi, double2* wa, double floor, int floor_mode,
                                   long long cells, cudaStream_t s) {
-  prep_kernel<<<blocks_for(cells), kThreads, 0, s>>>(psi, wa, floor, floor_mode, cells);
-  return cudaGetLastError();
+  return launch_pdl(prep_kernel, dim3(blocks_for(cells)), dim3(kThreads), 0, s, psi, wa, floor,
+                    floor_mode, cells);
 }
 
 cudaError_t launch_lap_mult_f64(double2* w, const int* n, int ndim, const double* const* k2,
@@ -102,22 +111,22 @@ cudaError_t launch_lap_mult_f64(double2* w, const int* n, int ndim, const double
   const double* a0 = ndim == 3 ? k2[0] : nullptr;
   const double* a1 = ndim == 3 ? k2[1] : k2[0];
   const double* a2 = ndim == 3 ? k2[2] : k2[1];
-  lap_mult_kernel<<<blocks_for(n0 * n1 * n2), kThreads, 0, s>>>(w, n0, n1, n2, a0, a1, a2, scale);
-  return cudaGetLastError();
+  return launch_pdl(lap_mult_kernel, dim3(blocks_for(n0 * n1 * n2)), dim3(kThreads), 0, s, w, n0, n1, n2,
+                    a0, a1, a2, scale);
 }
 
 cudaError_t launch_fluid_source_f64(const double2* psi, const double2* wlap, double2* w,
                                     const double* gamma, const double* beta, long long cells,
                                     cudaStream_t s) {
-  source_kernel<<<blocks_for(cells), kThreads, 0, s>>>(psi, wlap, w, gamma, beta, cells);
-  return cudaGetLastError();
+  return launch_pdl(source_kernel, dim3(blocks_for(cells)), dim3(kThreads), 0, s, psi, wlap, w, gamma,
+                    beta, cells);
 }
 
 cudaError_t launch_fluid_phase_f64(double2* psi, const double2* wphi, const double2* wlap,
                                    const double* phi_c, const FluidPhase& p, long long cells,
                                    cudaStream_t s) {
-  phase_kernel<<<blocks_for(cells), kThreads, 0, s>>>(psi, wphi, wlap, phi_c, p, cells);
-  return cudaGetLastError();
+  return launch_pdl(phase_kernel, dim3(blocks_for(cells)), dim3(kThreads), 0, s, psi, wphi, wlap, phi_c,
+                    p, cells);
 }
 
 }  // namespace sn

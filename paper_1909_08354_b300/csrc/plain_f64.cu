@@ -9,6 +9,7 @@
 // centroids, momentum) use the same FP64 axis FFTs and block reductions with a
 // fixed order, so repeated calls give bit-identical results.
 #include "sn_fft.cuh"
+#include "pdl.cuh"
 #include "sn_internal.h"
 
 using namespace snfft;
@@ -56,8 +57,10 @@ fft_f64_kernel(double2* data, long long outer, long long inner, const double2* t
     base = (size_t)o * N;
     stride = 1;
   }
+  pdl_allow_next();
   for (int k = tid; k < P::TWN; k += NT) tw_sm[k] = ldd(tw + k);
   __syncthreads();
+  pdl_wait_prev();  // the lines come from the previous kernel
   cx<double> v[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) {
@@ -87,8 +90,7 @@ cudaError_t launch_fft_lpb(double2* d, long long outer, long long inner, const d
   dim3 block(LPB * Plan<N>::T);
   dim3 grid = STRIDED ? dim3((unsigned)((inner + LPB - 1) / LPB), (unsigned)outer)
                       : dim3((unsigned)((outer + LPB - 1) / LPB));
-  kern<<<grid, block, smem, s>>>(d, outer, inner, tw);
-  return cudaGetLastError();
+  return launch_pdl(kern, grid, block, smem, s, d, outer, inner, tw);
 }
 
 // Lines per CTA: LinesF64::value, or LinesF64::few when that leaves fewer
@@ -130,6 +132,8 @@ inline unsigned ew_blocks(long long cells) {
 
 __global__ void mult_kinetic_kernel(double2* psi, Dims d, const double2* m0, const double2* m1,
                                     const double2* m2) {
+  pdl_allow_next();
+  pdl_wait_prev();
   const long long cells = d.n0 * d.n1 * d.n2;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
@@ -142,6 +146,8 @@ __global__ void mult_kinetic_kernel(double2* psi, Dims d, const double2* m0, con
 }
 
 __global__ void density_kernel(const double2* psi, double2* w, long long cells, bool accumulate) {
+  pdl_allow_next();
+  pdl_wait_prev();
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const cx<double> z = ldd(psi + c);
@@ -151,6 +157,8 @@ __global__ void density_kernel(const double2* psi, double2* w, long long cells, 
 
 __global__ void green_kernel(double2* w, Dims d, const double* k20, const double* k21,
                              const double* k22, double cN, double cY, double mu2, double cL) {
+  pdl_allow_next();
+  pdl_wait_prev();
   const long long cells = d.n0 * d.n1 * d.n2;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
@@ -163,6 +171,8 @@ __global__ void green_kernel(double2* w, Dims d, const double* k20, const double
 
 __global__ void phase_kernel(double2* psi, const double2* w, const double* vext, double h,
                              double gh, long long cells) {
+  pdl_allow_next();
+  pdl_wait_prev();
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
        c += (long long)gridDim.x * blockDim.x) {
     const cx<double> z = ldd(psi + c);
@@ -328,14 +338,14 @@ cudaError_t launch_mult_kinetic_f64(double2* psi, const int* n, int ndim, const 
   const double2* m0 = ndim == 3 ? m[0] : nullptr;
   const double2* m1 = ndim == 3 ? m[1] : m[0];
   const double2* m2 = ndim == 3 ? m[2] : m[1];
-  mult_kinetic_kernel<<<ew_blocks(d.n0 * d.n1 * d.n2), kEwThreads, 0, s>>>(psi, d, m0, m1, m2);
-  return cudaGetLastError();
+  return launch_pdl(mult_kinetic_kernel, dim3(ew_blocks(d.n0 * d.n1 * d.n2)), dim3(kEwThreads), 0, s,
+                    psi, d, m0, m1, m2);
 }
 
 cudaError_t launch_density_f64(const double2* psi, double2* w, long long cells, cudaStream_t s,
                                bool accumulate) {
-  density_kernel<<<ew_blocks(cells), kEwThreads, 0, s>>>(psi, w, cells, accumulate);
-  return cudaGetLastError();
+  return launch_pdl(density_kernel, dim3(ew_blocks(cells)), dim3(kEwThreads), 0, s, psi, w, cells,
+                    accumulate);
 }
 
 cudaError_t launch_green_f64(double2* w, const int* n, int ndim, const double* const* k2,
@@ -344,15 +354,14 @@ cudaError_t launch_green_f64(double2* w, const int* n, int ndim, const double* c
   const double* a0 = ndim == 3 ? k2[0] : nullptr;
   const double* a1 = ndim == 3 ? k2[1] : k2[0];
   const double* a2 = ndim == 3 ? k2[2] : k2[1];
-  green_kernel<<<ew_blocks(d.n0 * d.n1 * d.n2), kEwThreads, 0, s>>>(w, d, a0, a1, a2, cN, cY, mu2,
-                                                                    cL);
-  return cudaGetLastError();
+  return launch_pdl(green_kernel, dim3(ew_blocks(d.n0 * d.n1 * d.n2)), dim3(kEwThreads), 0, s, w, d, a0,
+                    a1, a2, cN, cY, mu2, cL);
 }
 
 cudaError_t launch_phase_f64(double2* psi, const double2* w, const double* vext, double h,
                              double gh, long long cells, cudaStream_t s) {
-  phase_kernel<<<ew_blocks(cells), kEwThreads, 0, s>>>(psi, w, vext, h, gh, cells);
-  return cudaGetLastError();
+  return launch_pdl(phase_kernel, dim3(ew_blocks(cells)), dim3(kEwThreads), 0, s, psi, w, vext, h, gh,
+                    cells);
 }
 
 cudaError_t launch_widen_f32_to_f64(const float2* in, double2* out, long long cells,

@@ -12,6 +12,7 @@
 
 #include "fft_plan.h"
 #include "sn.h"
+#include "pdl.cuh"
 #include "sn_internal.h"
 
 using namespace sn;
@@ -821,6 +822,7 @@ sn_status ensure_fluid_scratch(sn_grid g) {
 }
 
 sn_status step_fluid_f64(sn_grid g, double dt, int nsteps) {
+  const PdlOff plain_launches;  // see launch_pdl
   sn_status st = ensure_fluid_scratch(g);
   if (st != SN_OK) return st;
   double2* psi = reinterpret_cast<double2*>(g->psi);
