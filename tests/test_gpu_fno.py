@@ -48,6 +48,9 @@ SMALL = F.FnoShape(s=32, c_in=5, width=8, modes=4, layers=2, proj=8)
 # mode-mixing kernel at its production shared-memory size, and weight-gradient
 # GEMMs whose K (2 x 64^2 pixels) spans eight split-K chunks of 1024
 PROD = F.FnoShape(s=64, c_in=5, width=64, modes=24, layers=4, proj=128)
+# more input channels than the fused lift kernel holds in registers: the lift
+# as a GEMM and a bias pass
+WIDE_IN = F.FnoShape(s=16, c_in=18, width=8, modes=2, layers=1, proj=8)
 
 
 def problem(sh, seed=5, rscale=30.0):
@@ -83,8 +86,9 @@ FWD_TOL, GRAD_TOL = 2e-2, 1e-2
 
 
 @pytest.mark.parametrize("form", [sn.SN_FNO_LAYER_GEMMS, sn.SN_FNO_LAYER_UMMA], ids=["gemms", "tcgen05"])
-@pytest.mark.parametrize("sh,rscale,group_tol", [(SMALL, 30.0, 2e-2), (PROD, 10.0, 1e-2)],
-                         ids=["small", "production"])
+@pytest.mark.parametrize("sh,rscale,group_tol",
+                         [(SMALL, 30.0, 2e-2), (PROD, 10.0, 1e-2), (WIDE_IN, 30.0, 2e-2)],
+                         ids=["small", "production", "wide-input"])
 def test_forward_and_gradients_match_oracle(sh, rscale, group_tol, form):
     p, a, t = problem(sh, rscale=rscale)
     out_ref, cache = F.forward(p, a, sh)
