@@ -144,6 +144,29 @@ def test_expired_wait_reports_timeout_and_gpu_stays_usable():
     b.close()
 
 
+def test_one_instance_on_every_schedule():
+    """The degenerate batch: one instance (one size class, one graph branch),
+    each schedule against the single-grid path."""
+    w = W.random_small((64, 64), seed=700, L=12.0)
+    psi = w.psi0().astype(np.complex64)
+    ref = grid_run(psi, w.L, kw_of(w.kernel), 0.01, 5)
+    for sched in (sn.SN_BATCH_PERSISTENT, sn.SN_BATCH_CLASSES, sn.SN_BATCH_GRAPH):
+        b = sn.Batch([64], [w.L[0]])
+        try:
+            b.set_schedule(sched)
+            b.set_kernels([kw_of(w.kernel)])
+            b.set_state(0, psi)
+            b.step(0.01, 5)
+            b.sync()
+            out = b.get_state(0)
+        finally:
+            b.close()
+        if sched == sn.SN_BATCH_GRAPH:
+            assert np.array_equal(out, ref)
+        else:
+            assert O.rel_l2(out, ref) <= 5 * STEP_TOL, sched
+
+
 def test_parameter_scan_96_instances_on_the_graph_schedule():
     """The 96-instance scan workload on the graph schedule: 20 steps of every
     instance give sn_step's bits, and the mass of every instance is kept."""
