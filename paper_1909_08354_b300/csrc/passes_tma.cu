@@ -124,9 +124,15 @@ line_pass_tma_kernel(const __grid_constant__ TmaLineArgs a) {
     if constexpr (STRIDED) {
       const long long o = tau / tiles_i;
       const int i0 = (int)((tau - o * tiles_i) * kLpb);
-      tma::tma_store_3d(&a.map, i0, 0, (int)o, slots + s * TILE);
+      if constexpr (OP == LINE_KINETIC)  // psi: leave L2 to the half spectrum
+        tma::tma_store_3d_ef(&a.map, i0, 0, (int)o, slots + s * TILE, tma::policy_evict_first());
+      else
+        tma::tma_store_3d(&a.map, i0, 0, (int)o, slots + s * TILE);
     } else {
-      tma::tma_store_2d(&a.map, 0, (int)(tau * kLpb), slots + s * TILE);
+      if constexpr (OP == LINE_KINETIC)
+        tma::tma_store_2d_ef(&a.map, 0, (int)(tau * kLpb), slots + s * TILE, tma::policy_evict_first());
+      else
+        tma::tma_store_2d(&a.map, 0, (int)(tau * kLpb), slots + s * TILE);
     }
     tma::bulk_commit();
   };
@@ -455,8 +461,9 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
     tma::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
-      if constexpr (STRIDED) tma::tma_store_3d(&a.psi_map, i0, 0, (int)o, buf);
-      else tma::tma_store_2d(&a.psi_map, 0, (int)o, buf);
+      // psi leaves L2 first; the half spectrum a density pass writes stays
+      if constexpr (STRIDED) tma::tma_store_3d_ef(&a.psi_map, i0, 0, (int)o, buf, tma::policy_evict_first());
+      else tma::tma_store_2d_ef(&a.psi_map, 0, (int)o, buf, tma::policy_evict_first());
       tma::bulk_commit();
       const long long tau2 = tau + 2 * (long long)gridDim.x;
       if (tau2 < count) {

@@ -99,6 +99,31 @@ __device__ __forceinline__ void tma_store_3d(const void* map, int c0, int c1, in
       "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
       : "memory");
 }
+// L2 policy for data the next kernels do not read soon: psi written by a pass
+// (134 MB at 256^3, larger than L2) goes first, so that the half spectrum the
+// density pass writes beside it is still in L2 for the next pass.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+// the tile stores with an L2 cache policy
+__device__ __forceinline__ void tma_store_2d_ef(const void* map, int c0, int c1, const void* src,
+                                                uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group.L2::cache_hint"
+      " [%0, {%1, %2}], [%3], %4;\n" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(smem_u32(src)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_3d_ef(const void* map, int c0, int c1, int c2,
+                                                const void* src, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group.L2::cache_hint"
+      " [%0, {%1, %2, %3}], [%4], %5;\n" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src)), "l"(pol)
+      : "memory");
+}
 __device__ __forceinline__ void bulk_commit() {
   asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
 }
