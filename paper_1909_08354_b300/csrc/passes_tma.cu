@@ -288,6 +288,21 @@ constexpr size_t edge_smem_bytes() {
          (size_t)N * sizeof(float4) + 2 * sizeof(uint64_t);
 }
 
+// word of (line row, position pos) in a line-major float region of a tile (V
+// of contiguous tiles in P1, rho in P3): pos XOR 2 pi(row), pi a permutation
+// of the 16 lines.  The contiguous mapping puts R = 32 / T lines of T
+// consecutive positions in a warp, the strided one all 16 lines at two
+// positions; pi(row) = (row mod R) 16 / R + row / R keeps the lanes of a warp
+// on distinct banks in both (a plain pitch of N put the contiguous mapping's
+// lines on the same banks).
+template <int N>
+__device__ __forceinline__ int vw(int row, int pos) {
+  constexpr int T = Plan<N>::T, R = 32 / T;
+  static_assert(T == 8 || T == 16, "edge passes take 128- and 256-point lines");
+  const int pi = ((row % R) * (kLpb / R)) | (row / R);
+  return row * N + (pos ^ (pi << 1));
+}
+
 // word of (row k, line col) in a swizzled half-spectrum region
 __device__ __forceinline__ int rhw(int k, int col) {
   return k * kLpb + ((((col >> 1) ^ (k & 7)) << 1) | (col & 1));
@@ -302,7 +317,6 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
   constexpr unsigned PSI_BYTES = (unsigned)(TILE * sizeof(float2));
   constexpr unsigned RH_BYTES = (unsigned)(kLpb * H * sizeof(float2));
   constexpr size_t SLOT = edge_slot_bytes<N>();
-  constexpr int RLS = STRIDED ? N + 1 : N;  // row pitch (floats) of rho in P3
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   // the swizzled regions need 1024-byte alignment: the window is over-allocated
   // by 1 KB and its base rounded up
@@ -413,8 +427,8 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
             rf[p * kLpb + (lc ^ (p & 15))] = c[m].re;
             rf[p * kLpb + ((lc + HALF) ^ (p & 15))] = c[m].im;
           } else {
-            rf[lc * N + p] = c[m].re;
-            rf[(lc + HALF) * N + p] = c[m].im;
+            rf[vw<N>(lc, p)] = c[m].re;
+            rf[vw<N>(lc + HALF, p)] = c[m].im;
           }
         }
       }
@@ -439,7 +453,7 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
           v,
           [&](int m) {
             const int p = t + T * m;
-            return STRIDED ? rf[p * kLpb + (l ^ (p & 15))] : rf[l * N + p];
+            return STRIDED ? rf[p * kLpb + (l ^ (p & 15))] : rf[vw<N>(l, p)];
           },
           a.gh, vx, a.h, ustride, t, valid);
     }
@@ -479,13 +493,13 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
       // ---- rho = |psi|^2 and its R2C along the lines (packed lines lc, lc + 8)
       __syncthreads();  // the region is free
 #pragma unroll
-      for (int m = 0; m < E; ++m) rf[l * RLS + t + T * m] = cnorm2(v[m]);
+      for (int m = 0; m < E; ++m) rf[vw<N>(l, t + T * m)] = cnorm2(v[m]);
       __syncthreads();
       cx<float> c[E];
       if (pk) {
 #pragma unroll
         for (int m = 0; m < E; ++m)
-          c[m] = {rf[lc * RLS + tc + T * m], rf[(lc + HALF) * RLS + tc + T * m]};
+          c[m] = {rf[vw<N>(lc, tc + T * m)], rf[vw<N>(lc + HALF, tc + T * m)]};
       }
       __syncthreads();  // rho is in registers: the region becomes exchange space
       if (pk) tma::xform<N, -1, false, kLpb>(c, rh, tw_sm, lc, tc);
