@@ -303,6 +303,24 @@ __device__ __forceinline__ int vw(int row, int pos) {
   return row * N + (pos ^ (pi << 1));
 }
 
+// The words vw(row, t + T m), m = 0 … E - 1, of one thread (t < T): with
+// s = 2 pi(row) = T s_hi + s_lo (s_lo < T, s_hi < R), (t + T m) XOR s is
+// (t XOR s_lo) + T ((m mod R) XOR s_hi) + 32 (m / R), so the row's words are
+// R per-thread bases plus a constant per m: no swizzle arithmetic per access
+// once the loops over m are unrolled.
+template <int N>
+struct VRow {
+  static constexpr int T = Plan<N>::T, R = 32 / T;
+  int base[R];
+  __device__ __forceinline__ VRow(int row, int t) {
+    const int sw = vw<N>(row, 0) - row * N;  // 2 pi(row)
+    const int lo = row * N + (t ^ (sw % T));
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[r] = lo + T * (r ^ (sw / T));
+  }
+  __device__ __forceinline__ int operator[](int m) const { return base[m % R] + 32 * (m / R); }
+};
+
 // word of (row k, line col) in a swizzled half-spectrum region
 __device__ __forceinline__ int rhw(int k, int col) {
   return k * kLpb + ((((col >> 1) ^ (k & 7)) << 1) | (col & 1));
@@ -420,15 +438,19 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
       if (pk) tma::xform<N, +1, false, kLpb>(c, rh, tw_sm, lc, tc);
       __syncthreads();  // every exchange read is done: the region takes V
       if (pk) {
+        if constexpr (STRIDED) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-          const int p = tc + T * m;
-          if constexpr (STRIDED) {
+          for (int m = 0; m < E; ++m) {
+            const int p = tc + T * m;
             rf[p * kLpb + (lc ^ (p & 15))] = c[m].re;
             rf[p * kLpb + ((lc + HALF) ^ (p & 15))] = c[m].im;
-          } else {
-            rf[vw<N>(lc, p)] = c[m].re;
-            rf[vw<N>(lc + HALF, p)] = c[m].im;
+          }
+        } else {
+          const VRow<N> ra(lc, tc), rb(lc + HALF, tc);
+#pragma unroll
+          for (int m = 0; m < E; ++m) {
+            rf[ra[m]] = c[m].re;
+            rf[rb[m]] = c[m].im;
           }
         }
       }
@@ -449,11 +471,12 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
       if (a.vext != nullptr && valid)
         vx = a.vext + (STRIDED ? (size_t)o * N * a.inner + i0 + l : (size_t)(o + l) * N);
       const unsigned ustride = STRIDED ? (unsigned)a.inner : 1u;
+      const VRow<N> rv(l, t);
       tile::nonlinear_phase_at<E, T>(
           v,
           [&](int m) {
             const int p = t + T * m;
-            return STRIDED ? rf[p * kLpb + (l ^ (p & 15))] : rf[vw<N>(l, p)];
+            return STRIDED ? rf[p * kLpb + (l ^ (p & 15))] : rf[rv[m]];
           },
           a.gh, vx, a.h, ustride, t, valid);
     }
@@ -492,14 +515,17 @@ edge_pass_tma_kernel(const __grid_constant__ TmaEdgeArgs a) {
     if constexpr (EDGE == EDGE_DENSITY) {
       // ---- rho = |psi|^2 and its R2C along the lines (packed lines lc, lc + 8)
       __syncthreads();  // the region is free
+      {
+        const VRow<N> rw(l, t);
 #pragma unroll
-      for (int m = 0; m < E; ++m) rf[vw<N>(l, t + T * m)] = cnorm2(v[m]);
+        for (int m = 0; m < E; ++m) rf[rw[m]] = cnorm2(v[m]);
+      }
       __syncthreads();
       cx<float> c[E];
       if (pk) {
+        const VRow<N> ra(lc, tc), rb(lc + HALF, tc);
 #pragma unroll
-        for (int m = 0; m < E; ++m)
-          c[m] = {rf[vw<N>(lc, tc + T * m)], rf[vw<N>(lc + HALF, tc + T * m)]};
+        for (int m = 0; m < E; ++m) c[m] = {rf[ra[m]], rf[rb[m]]};
       }
       __syncthreads();  // rho is in registers: the region becomes exchange space
       if (pk) tma::xform<N, -1, false, kLpb>(c, rh, tw_sm, lc, tc);
