@@ -41,6 +41,7 @@ struct sn_fno_s {
   std::vector<ll> off_R, off_W, off_b;
   float *ExF = nullptr, *ExFw = nullptr, *EyA = nullptr, *EyB = nullptr;
   float *EyIre = nullptr, *EyIim = nullptr, *WxI = nullptr, *WxI1 = nullptr;
+  __nv_bfloat16* EyAB = nullptr;  // [EyA | EyB] rounded to BF16, 4m x 2s (dft_y_kernel)
   float *a = nullptr, *A1 = nullptr, *Uh = nullptr, *B1 = nullptr, *g1 = nullptr, *h = nullptr;
   float *out = nullptr, *dout = nullptr, *dv = nullptr, *dv2 = nullptr, *dz = nullptr, *dh = nullptr;
   float *yh = nullptr, *dy = nullptr;  // head channels (phi, dr, di) and their gradient
@@ -53,6 +54,7 @@ struct sn_fno_s {
   double* norms = nullptr;  // per sample (||out - t||^2, ||t||^2)
   double* chan_part = nullptr;  // channel-sum partials [max channels][kChanParts]
   int lastB = 0;
+  int sms = 1;  // the device's SM count (grids of the persistent kernels)
   ll work_floats = 0;
   std::vector<void*> allocs;
 };
@@ -409,6 +411,141 @@ __global__ void mass_kernel(const float2* psi, ll P, double* out) {
   if (threadIdx.x == 0) out[b] = red[0];
 }
 
+// ---- truncated DFT along y of whole planes --------------------------------------
+// V (4m x m) = [EyA | EyB] (4m x 2s) [A1re ; A1im] (2s x m) for every plane: the
+// two per-plane GEMMs of the y transform as one product with K = 2s.  The
+// 4m x 2s table, rounded to BF16 once (dfty_table_kernel), is copied into
+// shared memory once per CTA with 16-byte loads, each plane's A1 (s x 2m FP32) is read once, rounded to BF16 like the GEMM's
+// operands and stored [k][n]; the next plane's A1 is loaded into registers
+// while the current one is multiplied.  One warp per 16 rows of V, NT n-tiles
+// of 8 modes each (mma.sync m16n8k16, FP32 accumulation).  Row strides: the
+// table's 2s + 8 and the plane operand's dfty_ns(m) BF16 values, both an odd
+// multiple of 4 words modulo 8, which keeps the fragment loads on 32 banks.
+constexpr int kDftyMaxLoads = 16;  // float4 of a plane per thread: s / 16 <= 16
+
+__host__ __device__ constexpr int dfty_ns(int m) {
+  return ((((m + 7) / 8) * 4) % 8 == 4 ? ((m + 7) / 8) * 8 : ((m + 7) / 8) * 8 + 8);
+}
+inline size_t dfty_smem(int s, int m) {
+  return sizeof(__nv_bfloat16) * ((size_t)4 * m * (2 * s + 8) + (size_t)2 * s * dfty_ns(m));
+}
+
+__device__ __forceinline__ void mma_16x8x16_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                                 unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned bf16_pair(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+// [EyA | EyB] (4m rows of s + s) rounded to BF16 into one 4m x 2s table
+__global__ void dfty_table_kernel(const float* EyA, const float* EyB, __nv_bfloat16* T, int s,
+                                  int m) {
+  const ll n = (ll)4 * m * 2 * s;
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < n; i += (ll)gridDim.x * blockDim.x) {
+    const ll r = i / (2 * s), k = i - r * (2 * s);
+    T[i] = __float2bfloat16_rn(k < s ? EyA[r * s + k] : EyB[r * s + (k - s)]);
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(256) dft_y_kernel(const __nv_bfloat16* __restrict__ EyAB,
+                                                    const float* __restrict__ A1,
+                                                    float* __restrict__ V, int s, int m, ll planes,
+                                                    ll vstride) {
+  extern __shared__ __align__(16) unsigned char dfty_sm[];
+  const int KS = 2 * s + 8, NS = dfty_ns(m);
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(dfty_sm);  // [4m][KS]
+  __nv_bfloat16* Bs = As + (size_t)4 * m * KS;                      // [2s][NS]
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
+  {
+    // the table in 16-byte chunks of 8 values (s / 4 per row; rows of KS
+    // values keep them 16-byte aligned), eight loads in flight a thread
+    const int cpr = s / 4, nch = 4 * m * cpr;
+    const uint4* src = reinterpret_cast<const uint4*>(EyAB);
+    for (int i0 = tid; i0 < nch; i0 += 8 * nth) {
+      uint4 w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u * nth < nch) w[u] = src[i0 + u * nth];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * nth;
+        if (i < nch) {
+          const int r = i / cpr, c = i - r * cpr;
+          *reinterpret_cast<uint4*>(As + r * KS + 8 * c) = w[u];
+        }
+      }
+    }
+  }
+  const int nq = s * m / 2;  // float4 of one plane's A1
+  float4 pre[kDftyMaxLoads];
+  auto load = [&](ll pl) {
+    const float4* src = reinterpret_cast<const float4*>(A1 + pl * (ll)s * 2 * m);
+#pragma unroll
+    for (int i = 0; i < kDftyMaxLoads; ++i) {
+      const int q = tid + nth * i;
+      if (q < nq) pre[i] = src[q];
+    }
+  };
+  ll p = blockIdx.x;
+  if (p < planes) load(p);
+  for (; p < planes; p += gridDim.x) {
+    __syncthreads();  // the previous plane's fragment reads (and the table's writes) are done
+#pragma unroll
+    for (int i = 0; i < kDftyMaxLoads; ++i) {
+      const int q = tid + nth * i;
+      if (q < nq) {
+        const int e = 4 * q, y = e / (2 * m), c = e - y * (2 * m);
+        const int row = c < m ? y : s + y, col = c < m ? c : c - m;
+        uint2 w;
+        w.x = bf16_pair(__float2bfloat16_rn(pre[i].x), __float2bfloat16_rn(pre[i].y));
+        w.y = bf16_pair(__float2bfloat16_rn(pre[i].z), __float2bfloat16_rn(pre[i].w));
+        *reinterpret_cast<uint2*>(Bs + row * NS + col) = w;
+      }
+    }
+    __syncthreads();
+    if (p + gridDim.x < planes) load(p + gridDim.x);
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
+    const int r0 = warp * 16 + gid;
+    for (int kk = 0; kk < 2 * s; kk += 16) {
+      unsigned af[4];
+      af[0] = *reinterpret_cast<const unsigned*>(As + r0 * KS + kk + 2 * tig);
+      af[1] = *reinterpret_cast<const unsigned*>(As + (r0 + 8) * KS + kk + 2 * tig);
+      af[2] = *reinterpret_cast<const unsigned*>(As + r0 * KS + kk + 2 * tig + 8);
+      af[3] = *reinterpret_cast<const unsigned*>(As + (r0 + 8) * KS + kk + 2 * tig + 8);
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const __nv_bfloat16* b = Bs + (kk + 2 * tig) * NS + 8 * j + gid;
+        mma_16x8x16_bf16(acc[j], af, bf16_pair(b[0], b[NS]), bf16_pair(b[8 * NS], b[9 * NS]));
+      }
+    }
+    float* out = V + p * vstride;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int col = 8 * j + 2 * tig;
+      if (col < m) {
+        out[(ll)r0 * m + col] = acc[j][0];
+        out[(ll)(r0 + 8) * m + col] = acc[j][2];
+      }
+      if (col + 1 < m) {
+        out[(ll)r0 * m + col + 1] = acc[j][1];
+        out[(ll)(r0 + 8) * m + col + 1] = acc[j][3];
+      }
+    }
+  }
+}
+
 // ---- per-mode complex channel mixing ---------------------------------------
 // U[b][o](mode) = sum_i V[b][i](mode) R[mode][i][o], complex, with the planar
 // layout X[b][c][re/im][mode] of V and U and R[mode][i][o][re/im].  One block
@@ -533,6 +670,36 @@ cudaError_t weight_grad(sn_fno f, const float* dY, const float* X, int B, int M,
   return reduce_sum(f->work, (ll)B * nsplit, (ll)M * N, (ll)M * N, dW, 0.f, f->stream);
 }
 
+// the whole-plane y transform (dft_y_kernel) takes m a multiple of 4 up to 32
+// (one warp per 16 of the 4m rows, at most 4 n-tiles) and s a multiple of 16
+// up to 256 (a plane's A1 in at most 16 float4 a thread)
+bool dfty_supported(int s, int m) {
+  return m % 4 == 0 && m >= 4 && m <= 32 && s % 16 == 0 && s >= 16 && s <= 256 &&
+         dfty_smem(s, m) <= 200 * 1024;
+}
+
+template <int NT>
+cudaError_t launch_dft_y_t(sn_fno f, ll planes, float* V) {
+  const size_t smem = dfty_smem(f->s, f->m);
+  const int threads = 8 * f->m;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_y_kernel<NT>, threads, smem);
+  if (e != cudaSuccess) return e;
+  const ll grid = std::min<ll>(planes, (ll)std::max(1, std::min(per_sm, 8)) * f->sms);
+  dft_y_kernel<NT><<<(unsigned)grid, threads, smem, f->stream>>>(f->EyAB, f->A1, V, f->s, f->m,
+                                                                 planes, 2 * f->Nm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dft_y(sn_fno f, ll planes, float* V) {
+  switch ((f->m + 7) / 8) {
+    case 1: return launch_dft_y_t<1>(f, planes, V);
+    case 2: return launch_dft_y_t<2>(f, planes, V);
+    case 3: return launch_dft_y_t<3>(f, planes, V);
+    default: return launch_dft_y_t<4>(f, planes, V);
+  }
+}
+
 // modes V[B][C][2][Nm] = truncated forward DFT of planes X[B][C][s][s]; Ex: s x 2m
 cudaError_t dft_forward(sn_fno f, const float* X, int B, int Cn, const float* Ex, float* V) {
   const int s = f->s, m = f->m;
@@ -542,6 +709,7 @@ cudaError_t dft_forward(sn_fno f, const float* X, int B, int Cn, const float* Ex
                        2 * m, 1);
   if (e != cudaSuccess) return e;
   // along y, per plane: V (4m x m) = EyA (4m x s) A1re (s x m) + EyB (4m x s) A1im (s x m)
+  if (dfty_supported(s, m)) return launch_dft_y(f, planes, V);
   e = gemm(f, 4 * m, m, s, (int)planes, f->EyA, 0, s, 1, f->A1, (ll)s * 2 * m, 2 * m, 1, V,
            2 * f->Nm, m, 1);
   if (e != cudaSuccess) return e;
@@ -732,6 +900,25 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
                                     (int)sm_fwd) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(mode_mix_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sm_bwd) == cudaSuccess;
+  }
+  {
+    int dev = 0;
+    ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&f->sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+  }
+  if (dfty_supported(s, modes)) {
+    const int sm = (int)dfty_smem(s, modes);
+    const size_t tn = (size_t)4 * modes * 2 * s;  // BF16 values of the table
+    ok = ok && falloc(f, &f->EyAB, tn) == cudaSuccess;
+    if (ok) {
+      dfty_table_kernel<<<(unsigned)((tn + 255) / 256), 256, 0, f->stream>>>(f->EyA, f->EyB, f->EyAB, s,
+                                                                             modes);
+      ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(f->stream) == cudaSuccess;
+    }
+    ok = ok && cudaFuncSetAttribute(dft_y_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_y_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_y_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_y_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
   }
   if (!ok) return bail(ffail(SN_ENOMEM, "sn_fno_create: device allocation failed"));
   if (fno_layer_umma_supported(f->C, 2 * f->m, f->s)) f->layer_form = SN_FNO_LAYER_UMMA;
