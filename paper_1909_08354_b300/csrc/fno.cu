@@ -42,6 +42,7 @@ struct sn_fno_s {
   float *ExF = nullptr, *ExFw = nullptr, *EyA = nullptr, *EyB = nullptr;
   float *EyIre = nullptr, *EyIim = nullptr, *WxI = nullptr, *WxI1 = nullptr;
   __nv_bfloat16* EyAB = nullptr;  // [EyA | EyB] rounded to BF16, 4m x 2s (dft_y_kernel)
+  __nv_bfloat16* EyI = nullptr;   // [EyIre ; EyIim] rounded to BF16, 2s x 4m (idft_y_kernel)
   float *a = nullptr, *A1 = nullptr, *Uh = nullptr, *B1 = nullptr, *g1 = nullptr, *h = nullptr;
   float *out = nullptr, *dout = nullptr, *dv = nullptr, *dv2 = nullptr, *dz = nullptr, *dh = nullptr;
   float *yh = nullptr, *dy = nullptr;  // head channels (phi, dr, di) and their gradient
@@ -546,6 +547,122 @@ __global__ void __launch_bounds__(256) dft_y_kernel(const __nv_bfloat16* __restr
   }
 }
 
+// The inverse DFT along y of whole planes: B1 (s x 2m, [y][re q | im q]) =
+// [EyIre ; EyIim] (2s x 4m) U (4m x m) per plane, rows r < s giving the real
+// parts of row y = r and rows s + y the imaginary ones.  The same scheme as
+// dft_y_kernel: the 2s x 4m BF16 table resident in shared memory (row stride
+// 4m + 8), each plane's modes U (4m x m FP32) read once and rounded to BF16
+// ([k][n], stride dfty_ns(m)), the next plane's loaded while the current one is
+// multiplied; eight warps take the 2s / 16 row tiles in turn.
+constexpr int kIdftyThreads = 256, kIdftyMaxLoads = 4;  // m^2 / 4 float4 of U <= 4 a thread
+
+inline size_t idfty_smem(int s, int m) {
+  return sizeof(__nv_bfloat16) * ((size_t)2 * s * (4 * m + 8) + (size_t)4 * m * dfty_ns(m));
+}
+
+// [top ; bottom] (two row-major blocks of n values each) rounded to BF16
+__global__ void stack_bf16_kernel(const float* top, const float* bottom, __nv_bfloat16* T, ll n) {
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < 2 * n; i += (ll)gridDim.x * blockDim.x)
+    T[i] = __float2bfloat16_rn(i < n ? top[i] : bottom[i - n]);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kIdftyThreads) idft_y_kernel(const __nv_bfloat16* __restrict__ EyI,
+                                                               const float* __restrict__ U,
+                                                               float* __restrict__ B1, int s, int m,
+                                                               ll planes, ll ustride) {
+  extern __shared__ __align__(16) unsigned char idfty_sm[];
+  const int KS = 4 * m + 8, NS = dfty_ns(m);
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(idfty_sm);  // [2s][KS]
+  __nv_bfloat16* Bs = As + (size_t)2 * s * KS;                       // [4m][NS]
+  const int tid = threadIdx.x, nth = kIdftyThreads;
+  const int lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
+  {
+    // the table in 16-byte chunks (m / 2 per row of 4m values), eight loads
+    // in flight a thread
+    const int cpr = m / 2, nch = 2 * s * cpr;
+    const uint4* src = reinterpret_cast<const uint4*>(EyI);
+    for (int i0 = tid; i0 < nch; i0 += 8 * nth) {
+      uint4 w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u * nth < nch) w[u] = src[i0 + u * nth];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * nth;
+        if (i < nch) {
+          const int r = i / cpr, c = i - r * cpr;
+          *reinterpret_cast<uint4*>(As + r * KS + 8 * c) = w[u];
+        }
+      }
+    }
+  }
+  const int nq = m * m;  // float4 of one plane's U (4m x m)
+  float4 pre[kIdftyMaxLoads];
+  auto load = [&](ll pl) {
+    const float4* src = reinterpret_cast<const float4*>(U + pl * ustride);
+#pragma unroll
+    for (int i = 0; i < kIdftyMaxLoads; ++i) {
+      const int q = tid + nth * i;
+      if (q < nq) pre[i] = src[q];
+    }
+  };
+  ll p = blockIdx.x;
+  if (p < planes) load(p);
+  const int mtiles = 2 * s / 16;
+  for (; p < planes; p += gridDim.x) {
+    __syncthreads();  // the previous plane's fragment reads (and the table's writes) are done
+#pragma unroll
+    for (int i = 0; i < kIdftyMaxLoads; ++i) {
+      const int q = tid + nth * i;
+      if (q < nq) {
+        const int e = 4 * q, k = e / m, c = e - k * m;
+        uint2 w;
+        w.x = bf16_pair(__float2bfloat16_rn(pre[i].x), __float2bfloat16_rn(pre[i].y));
+        w.y = bf16_pair(__float2bfloat16_rn(pre[i].z), __float2bfloat16_rn(pre[i].w));
+        *reinterpret_cast<uint2*>(Bs + k * NS + c) = w;
+      }
+    }
+    __syncthreads();
+    if (p + gridDim.x < planes) load(p + gridDim.x);
+    float* out = B1 + p * (ll)s * 2 * m;
+    for (int mt = warp; mt < mtiles; mt += nth / 32) {
+      float acc[NT][4];
+#pragma unroll
+      for (int j = 0; j < NT; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
+      const int r0 = mt * 16 + gid;
+      for (int kk = 0; kk < 4 * m; kk += 16) {
+        unsigned af[4];
+        af[0] = *reinterpret_cast<const unsigned*>(As + r0 * KS + kk + 2 * tig);
+        af[1] = *reinterpret_cast<const unsigned*>(As + (r0 + 8) * KS + kk + 2 * tig);
+        af[2] = *reinterpret_cast<const unsigned*>(As + r0 * KS + kk + 2 * tig + 8);
+        af[3] = *reinterpret_cast<const unsigned*>(As + (r0 + 8) * KS + kk + 2 * tig + 8);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const __nv_bfloat16* b = Bs + (kk + 2 * tig) * NS + 8 * j + gid;
+          mma_16x8x16_bf16(acc[j], af, bf16_pair(b[0], b[NS]), bf16_pair(b[8 * NS], b[9 * NS]));
+        }
+      }
+      // rows r0 and r0 + 8 of the stacked product: (y, half) = (r mod s, r / s)
+      float* o0 = out + (ll)(r0 % s) * 2 * m + (r0 / s) * m;
+      float* o1 = out + (ll)((r0 + 8) % s) * 2 * m + ((r0 + 8) / s) * m;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int col = 8 * j + 2 * tig;
+        if (col + 1 < m) {
+          *reinterpret_cast<float2*>(o0 + col) = make_float2(acc[j][0], acc[j][1]);
+          *reinterpret_cast<float2*>(o1 + col) = make_float2(acc[j][2], acc[j][3]);
+        } else if (col < m) {
+          o0[col] = acc[j][0];
+          o1[col] = acc[j][2];
+        }
+      }
+    }
+  }
+}
+
 // ---- per-mode complex channel mixing ---------------------------------------
 // U[b][o](mode) = sum_i V[b][i](mode) R[mode][i][o], complex, with the planar
 // layout X[b][c][re/im][mode] of V and U and R[mode][i][o][re/im].  One block
@@ -700,6 +817,28 @@ cudaError_t launch_dft_y(sn_fno f, ll planes, float* V) {
   }
 }
 
+template <int NT>
+cudaError_t launch_idft_y_t(sn_fno f, const float* U, ll planes) {
+  const size_t smem = idfty_smem(f->s, f->m);
+  int per_sm = 0;
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, idft_y_kernel<NT>, kIdftyThreads, smem);
+  if (e != cudaSuccess) return e;
+  const ll grid = std::min<ll>(planes, (ll)std::max(1, std::min(per_sm, 8)) * f->sms);
+  idft_y_kernel<NT><<<(unsigned)grid, kIdftyThreads, smem, f->stream>>>(f->EyI, U, f->B1, f->s, f->m,
+                                                                        planes, 2 * f->Nm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_idft_y(sn_fno f, const float* U, ll planes) {
+  switch ((f->m + 7) / 8) {
+    case 1: return launch_idft_y_t<1>(f, U, planes);
+    case 2: return launch_idft_y_t<2>(f, U, planes);
+    case 3: return launch_idft_y_t<3>(f, U, planes);
+    default: return launch_idft_y_t<4>(f, U, planes);
+  }
+}
+
 // modes V[B][C][2][Nm] = truncated forward DFT of planes X[B][C][s][s]; Ex: s x 2m
 cudaError_t dft_forward(sn_fno f, const float* X, int B, int Cn, const float* Ex, float* V) {
   const int s = f->s, m = f->m;
@@ -723,6 +862,7 @@ cudaError_t dft_inverse_y(sn_fno f, const float* U, int B, int Cn) {
   const int s = f->s, m = f->m;
   const ll planes = (ll)B * Cn;
   // per plane: B1re (s x m) = EyIre (s x 4m) U (4m x m); B1im likewise; B1 is [y][re|im][q]
+  if (f->EyI != nullptr) return launch_idft_y(f, U, planes);
   cudaError_t e = gemm(f, s, m, 4 * m, (int)planes, f->EyIre, 0, 4 * m, 1, U, 2 * f->Nm, m, 1,
                        f->B1, (ll)s * 2 * m, 2 * m, 1);
   if (e != cudaSuccess) return e;
@@ -919,6 +1059,19 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
     ok = ok && cudaFuncSetAttribute(dft_y_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(dft_y_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(dft_y_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+  }
+  if (dfty_supported(s, modes) && idfty_smem(s, modes) <= 200 * 1024) {
+    const int sm = (int)idfty_smem(s, modes);
+    const ll n = (ll)s * 4 * modes;  // values of EyIre (and of EyIim)
+    ok = ok && falloc(f, &f->EyI, (size_t)(2 * n)) == cudaSuccess;
+    if (ok) {
+      stack_bf16_kernel<<<(unsigned)((2 * n + 255) / 256), 256, 0, f->stream>>>(f->EyIre, f->EyIim, f->EyI, n);
+      ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(f->stream) == cudaSuccess;
+    }
+    ok = ok && cudaFuncSetAttribute(idft_y_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(idft_y_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(idft_y_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(idft_y_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
   }
   if (!ok) return bail(ffail(SN_ENOMEM, "sn_fno_create: device allocation failed"));
   if (fno_layer_umma_supported(f->C, 2 * f->m, f->s)) f->layer_form = SN_FNO_LAYER_UMMA;
