@@ -835,8 +835,8 @@ def run_fno(sn, torch, stream, iters=10):
             "layer_form": "tcgen05" if best == sn.SN_FNO_LAYER_UMMA else "gemms",
             "gemm": "the layers' inverse DFT along x, 1x1 convolution, bias and GELU: one "
                     "tcgen05.mma kernel (BF16, FP32 accumulators in tensor memory) or mma.sync "
-                    "m16n8k16 BF16 GEMMs; the DFTs along y, forward and inverse: one mma.sync pass over the planes each "
-                    "(dft_y_kernel, idft_y_kernel); "
+                    "m16n8k16 BF16 GEMMs; the DFT along x and the DFTs along y, forward and inverse: one mma.sync "
+                    "streaming pass each (dft_x_kernel, dft_y_kernel, idft_y_kernel); "
                     "every other contraction: mma.sync BF16 GEMMs"}
 
 

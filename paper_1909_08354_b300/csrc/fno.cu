@@ -547,6 +547,70 @@ __global__ void __launch_bounds__(256) dft_y_kernel(const __nv_bfloat16* __restr
   }
 }
 
+// The truncated DFT along x of every row: A1 (rows x 2m) = X (rows x s) Ex
+// (s x 2m).  X is read once, straight into the A fragments (FP32 pairs
+// rounded to BF16 in registers, as the GEMM rounds its operands); Ex is
+// rounded to BF16 into shared memory once per CTA ([n][k], stride s + 8, an
+// odd multiple of 4 words modulo 8 for the fragment loads).  Each warp takes
+// 16 rows at a time with NT2 = 2m / 8 n-tiles (mma.sync m16n8k16, FP32
+// accumulation in the GEMM's k order).
+constexpr int kDftxThreads = 256;
+
+inline size_t dftx_smem(int s, int m) { return sizeof(__nv_bfloat16) * (size_t)2 * m * (s + 8); }
+
+template <int NT2>
+__global__ void __launch_bounds__(kDftxThreads) dft_x_kernel(const float* __restrict__ X,
+                                                             const float* __restrict__ Ex,
+                                                             float* __restrict__ A1, int s, int m,
+                                                             ll rows) {
+  extern __shared__ __align__(16) unsigned char dftx_sm[];
+  const int KS = s + 8, N2 = 2 * m;
+  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(dftx_sm);  // [2m][KS]
+  const int tid = threadIdx.x, nth = kDftxThreads;
+  const int lane = tid & 31, warp = tid >> 5, gid = lane >> 2, tig = lane & 3;
+  for (int i = tid; i < s * N2; i += nth) {
+    const int k = i / N2, n = i - k * N2;
+    Bs[n * KS + k] = __float2bfloat16_rn(Ex[i]);
+  }
+  __syncthreads();
+  const ll tiles = rows / 16;
+  const int wpb = nth / 32;
+  for (ll t = (ll)blockIdx.x * wpb + warp; t < tiles; t += (ll)gridDim.x * wpb) {
+    const float* x0 = X + (t * 16 + gid) * (ll)s + 2 * tig;  // row gid of the tile
+    const float* x1 = x0 + 8 * (ll)s;                         // row gid + 8
+    float acc[NT2][4];
+#pragma unroll
+    for (int j = 0; j < NT2; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
+#pragma unroll 4
+    for (int kk = 0; kk < s; kk += 16) {
+      const float2 a00 = __ldcs(reinterpret_cast<const float2*>(x0 + kk));
+      const float2 a10 = __ldcs(reinterpret_cast<const float2*>(x1 + kk));
+      const float2 a01 = __ldcs(reinterpret_cast<const float2*>(x0 + kk + 8));
+      const float2 a11 = __ldcs(reinterpret_cast<const float2*>(x1 + kk + 8));
+      const unsigned af[4] = {bf16_pair(__float2bfloat16_rn(a00.x), __float2bfloat16_rn(a00.y)),
+                              bf16_pair(__float2bfloat16_rn(a10.x), __float2bfloat16_rn(a10.y)),
+                              bf16_pair(__float2bfloat16_rn(a01.x), __float2bfloat16_rn(a01.y)),
+                              bf16_pair(__float2bfloat16_rn(a11.x), __float2bfloat16_rn(a11.y))};
+#pragma unroll
+      for (int j = 0; j < NT2; ++j) {
+        const __nv_bfloat16* b = Bs + (8 * j + gid) * KS + kk + 2 * tig;
+        mma_16x8x16_bf16(acc[j], af, *reinterpret_cast<const unsigned*>(b),
+                         *reinterpret_cast<const unsigned*>(b + 8));
+      }
+    }
+    float* o0 = A1 + (t * 16 + gid) * (ll)N2;
+    float* o1 = o0 + 8 * (ll)N2;
+#pragma unroll
+    for (int j = 0; j < NT2; ++j) {
+      const int col = 8 * j + 2 * tig;
+      *reinterpret_cast<float2*>(o0 + col) = make_float2(acc[j][0], acc[j][1]);
+      *reinterpret_cast<float2*>(o1 + col) = make_float2(acc[j][2], acc[j][3]);
+    }
+  }
+}
+
 // The inverse DFT along y of whole planes: B1 (s x 2m, [y][re q | im q]) =
 // [EyIre ; EyIim] (2s x 4m) U (4m x m) per plane, rows r < s giving the real
 // parts of row y = r and rows s + y the imaginary ones.  The same scheme as
@@ -817,6 +881,32 @@ cudaError_t launch_dft_y(sn_fno f, ll planes, float* V) {
   }
 }
 
+template <int NT2>
+cudaError_t launch_dft_x_t(sn_fno f, const float* X, const float* Ex, ll rows) {
+  const size_t smem = dftx_smem(f->s, f->m);
+  int per_sm = 0;
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_x_kernel<NT2>, kDftxThreads, smem);
+  if (e != cudaSuccess) return e;
+  const ll tiles = rows / 16, wpb = kDftxThreads / 32;
+  const ll grid = std::min<ll>((tiles + wpb - 1) / wpb, (ll)std::max(1, per_sm) * f->sms);
+  dft_x_kernel<NT2><<<(unsigned)grid, kDftxThreads, smem, f->stream>>>(X, Ex, f->A1, f->s, f->m, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dft_x(sn_fno f, const float* X, const float* Ex, ll rows) {
+  switch (f->m / 4) {
+    case 1: return launch_dft_x_t<1>(f, X, Ex, rows);
+    case 2: return launch_dft_x_t<2>(f, X, Ex, rows);
+    case 3: return launch_dft_x_t<3>(f, X, Ex, rows);
+    case 4: return launch_dft_x_t<4>(f, X, Ex, rows);
+    case 5: return launch_dft_x_t<5>(f, X, Ex, rows);
+    case 6: return launch_dft_x_t<6>(f, X, Ex, rows);
+    case 7: return launch_dft_x_t<7>(f, X, Ex, rows);
+    default: return launch_dft_x_t<8>(f, X, Ex, rows);
+  }
+}
+
 template <int NT>
 cudaError_t launch_idft_y_t(sn_fno f, const float* U, ll planes) {
   const size_t smem = idfty_smem(f->s, f->m);
@@ -844,8 +934,10 @@ cudaError_t dft_forward(sn_fno f, const float* X, int B, int Cn, const float* Ex
   const int s = f->s, m = f->m;
   const ll planes = (ll)B * Cn;
   // along x: A1 (planes*s x 2m) = X (planes*s x s) Ex (s x 2m)
-  cudaError_t e = gemm(f, (int)(planes * s), 2 * m, s, 1, X, 0, s, 1, Ex, 0, 2 * m, 1, f->A1, 0,
-                       2 * m, 1);
+  cudaError_t e = dfty_supported(s, m)
+                      ? launch_dft_x(f, X, Ex, planes * s)
+                      : gemm(f, (int)(planes * s), 2 * m, s, 1, X, 0, s, 1, Ex, 0, 2 * m, 1, f->A1,
+                             0, 2 * m, 1);
   if (e != cudaSuccess) return e;
   // along y, per plane: V (4m x m) = EyA (4m x s) A1re (s x m) + EyB (4m x s) A1im (s x m)
   if (dfty_supported(s, m)) return launch_dft_y(f, planes, V);
@@ -1059,6 +1151,17 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
     ok = ok && cudaFuncSetAttribute(dft_y_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(dft_y_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(dft_y_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+  }
+  if (dfty_supported(s, modes)) {
+    const int sm = (int)dftx_smem(s, modes);  // at most 2 x 32 x 264 BF16 values
+    ok = ok && cudaFuncSetAttribute(dft_x_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_x_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_x_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_x_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_x_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_x_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_x_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(dft_x_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
   }
   if (dfty_supported(s, modes) && idfty_smem(s, modes) <= 200 * 1024) {
     const int sm = (int)idfty_smem(s, modes);
