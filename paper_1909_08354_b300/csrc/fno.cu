@@ -734,9 +734,12 @@ __global__ void __launch_bounds__(kIdftyThreads) idft_y_kernel(const __nv_bfloat
 // operands, products accumulate in FP32.
 __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// The forward stages the mode's R, rounded, in shared memory beside V: each R
+// value serves all B samples, so it is loaded and rounded once.
 __global__ void mode_mix_kernel(const float* V, const float* R, float* U, int B, int C, ll Nm) {
   extern __shared__ float mm_sm[];
   float2* Vs = reinterpret_cast<float2*>(mm_sm);  // [B][C]
+  float2* Rs = Vs + B * C;                        // [C][C], rounded
   const ll mode = blockIdx.x;
   const ll is = 2 * Nm, bs = (ll)C * is;
   for (int e = threadIdx.x; e < B * C; e += blockDim.x) {
@@ -744,15 +747,19 @@ __global__ void mode_mix_kernel(const float* V, const float* R, float* U, int B,
     const float* v = V + b * bs + i * is + mode;
     Vs[e] = make_float2(bf(v[0]), bf(v[Nm]));
   }
-  __syncthreads();
   const float2* Rm = reinterpret_cast<const float2*>(R) + mode * (ll)C * C;
+  for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+    const float2 r = Rm[e];
+    Rs[e] = make_float2(bf(r.x), bf(r.y));
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < B * C; e += blockDim.x) {
     const int b = e / C, o = e % C;
     float ar = 0.f, ai = 0.f;
     for (int i = 0; i < C; ++i) {
       const float2 x = Vs[b * C + i];
-      const float2 r = Rm[i * C + o];
-      const float rr = bf(r.x), ri = bf(r.y);
+      const float2 r = Rs[i * C + o];
+      const float rr = r.x, ri = r.y;
       ar = fmaf(x.x, rr, fmaf(-x.y, ri, ar));
       ai = fmaf(x.x, ri, fmaf(x.y, rr, ai));
     }
@@ -976,7 +983,7 @@ cudaError_t dft_inverse(sn_fno f, const float* U, int B, int Cn, const float* Wx
 
 // U[b][o] = sum_i R[mode][i][o] V[b][i] per mode (complex), four real GEMMs
 cudaError_t mode_mix(sn_fno f, const float* V, const float* R, int B, float* U) {
-  const size_t sm = sizeof(float2) * (size_t)B * f->C;
+  const size_t sm = sizeof(float2) * ((size_t)B * f->C + (size_t)f->C * f->C);
   mode_mix_kernel<<<(unsigned)f->Nm, 256, sm, f->stream>>>(V, R, U, B, f->C, f->Nm);
   return cudaGetLastError();
 }
@@ -1125,7 +1132,7 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
   ok = ok && falloc(f, &f->work, f->work_floats) == cudaSuccess;
   {
     // per-mode mixing keeps V, GU (B x C) and R (C x C) of one mode in shared memory
-    const size_t sm_fwd = sizeof(float2) * (size_t)B * C;
+    const size_t sm_fwd = sizeof(float2) * ((size_t)B * C + (size_t)C * C);
     const size_t sm_bwd = sizeof(float2) * (2 * (size_t)B * C + (size_t)C * C);
     if (sm_bwd > 200 * 1024) return bail(ffail(SN_ENOTSUP, "sn_fno_create: batch_max * width too large"));
     ok = ok && cudaFuncSetAttribute(mode_mix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
