@@ -775,7 +775,8 @@ __global__ void mode_mix_bwd_kernel(const float* V, const float* R, const float*
   extern __shared__ float mm_sm[];
   float2* Vs = reinterpret_cast<float2*>(mm_sm);  // [B][C]
   float2* Gs = Vs + B * C;                         // [B][C]
-  float2* Rs = Gs + B * C;                         // [C][C]
+  float2* Rs = Gs + B * C;  // R transposed, [o][i] with row stride C + 1: the GV loop's lanes
+                            // (consecutive i) then read consecutive words
   const ll mode = blockIdx.x;
   const ll is = 2 * Nm, bs = (ll)C * is;
   for (int e = threadIdx.x; e < B * C; e += blockDim.x) {
@@ -788,7 +789,8 @@ __global__ void mode_mix_bwd_kernel(const float* V, const float* R, const float*
   const float2* Rm = reinterpret_cast<const float2*>(R) + mode * (ll)C * C;
   for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
     const float2 r = Rm[e];
-    Rs[e] = make_float2(bf(r.x), bf(r.y));
+    const int i = e / C, o = e % C;
+    Rs[o * (C + 1) + i] = make_float2(bf(r.x), bf(r.y));
   }
   __syncthreads();
   float2* GRm = reinterpret_cast<float2*>(GR) + mode * (ll)C * C;
@@ -806,7 +808,7 @@ __global__ void mode_mix_bwd_kernel(const float* V, const float* R, const float*
     const int b = e / C, i = e % C;
     float ar = 0.f, ai = 0.f;
     for (int o = 0; o < C; ++o) {
-      const float2 r = Rs[i * C + o], g = Gs[b * C + o];
+      const float2 r = Rs[o * (C + 1) + i], g = Gs[b * C + o];
       ar = fmaf(r.x, g.x, fmaf(r.y, g.y, ar));   // conj(r) g
       ai = fmaf(r.x, g.y, fmaf(-r.y, g.x, ai));
     }
@@ -991,7 +993,7 @@ cudaError_t mode_mix(sn_fno f, const float* V, const float* R, int B, float* U) 
 // backward of mode_mix: GR[mode][i][o] = sum_b conj(V_i) GU_o ; GV[b][i] = sum_o conj(R_io) GU_o
 cudaError_t mode_mix_bwd(sn_fno f, const float* V, const float* R, const float* GU, int B, float* GR,
                          float* GV) {
-  const size_t sm = sizeof(float2) * (2 * (size_t)B * f->C + (size_t)f->C * f->C);
+  const size_t sm = sizeof(float2) * (2 * (size_t)B * f->C + (size_t)f->C * (f->C + 1));
   mode_mix_bwd_kernel<<<(unsigned)f->Nm, 256, sm, f->stream>>>(V, R, GU, GR, GV, B, f->C, f->Nm);
   return cudaGetLastError();
 }
@@ -1133,7 +1135,7 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
   {
     // per-mode mixing keeps V, GU (B x C) and R (C x C) of one mode in shared memory
     const size_t sm_fwd = sizeof(float2) * ((size_t)B * C + (size_t)C * C);
-    const size_t sm_bwd = sizeof(float2) * (2 * (size_t)B * C + (size_t)C * C);
+    const size_t sm_bwd = sizeof(float2) * (2 * (size_t)B * C + (size_t)C * (C + 1));
     if (sm_bwd > 200 * 1024) return bail(ffail(SN_ENOTSUP, "sn_fno_create: batch_max * width too large"));
     ok = ok && cudaFuncSetAttribute(mode_mix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sm_fwd) == cudaSuccess;
