@@ -257,13 +257,40 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(GemmArgs g, int nsplit) {
   }
 }
 
-__global__ void reduce_sum_kernel(const float* part, long long count, long long stride, long long n,
-                                  float* out, float beta) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (long long j = 0; j < count; ++j) s += part[j * stride + i];
-    out[i] = (beta != 0.f) ? s + beta * out[i] : s;
+// out[i] = sum_j part[j stride + i] (+ beta out[i]).  A block takes 32
+// consecutive outputs (one per lane, coalesced) and splits j over its
+// kReduceSlices warps, slice w summing j = w, w + kReduceSlices, ... in eight
+// interleaved partial sums (eight loads in flight); the partial sums and then
+// the slices are added in a fixed order, so the result is the same on every
+// run.
+constexpr int kReduceSlices = 8;
+
+__global__ void __launch_bounds__(32 * kReduceSlices)
+reduce_sum_kernel(const float* part, long long count, long long stride, long long n, float* out,
+                  float beta) {
+  __shared__ float red[kReduceSlices][32];
+  const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  constexpr int S = kReduceSlices;
+  for (long long i0 = blockIdx.x * 32LL; i0 < n; i0 += gridDim.x * 32LL) {
+    const long long i = i0 + lane;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < n) {
+      long long j = sl;
+      for (; j + 7 * S < count; j += 8 * S) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] += part[(j + u * S) * stride + i];
+      }
+      for (; j < count; j += S) acc[0] += part[j * stride + i];
+    }
+    red[sl][lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    __syncthreads();
+    if (sl == 0 && i < n) {
+      float s = 0.f;
+#pragma unroll
+      for (int w = 0; w < S; ++w) s += red[w][lane];
+      out[i] = (beta != 0.f) ? s + beta * out[i] : s;
+    }
+    __syncthreads();
   }
 }
 
@@ -328,9 +355,9 @@ cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
 
 cudaError_t reduce_sum(const float* part, long long count, long long stride, long long n, float* out,
                        float beta, cudaStream_t s) {
-  const long long blocks = (n + 255) / 256;
-  reduce_sum_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(part, count, stride,
-                                                                                n, out, beta);
+  const long long blocks = (n + 31) / 32;
+  reduce_sum_kernel<<<(unsigned)(blocks < 8192 ? blocks : 8192), 32 * kReduceSlices, 0, s>>>(
+      part, count, stride, n, out, beta);
   return cudaGetLastError();
 }
 
