@@ -52,7 +52,8 @@ struct sn_fno_s {
   int* status = nullptr;
   float *GU = nullptr, *GV = nullptr, *work = nullptr;
   std::vector<float*> v, z, Vh;
-  double* norms = nullptr;  // per sample (||out - t||^2, ||t||^2)
+  double* norms = nullptr;  // per sample (||out - t||^2, ||t||^2), then the B gradient scales
+  double* loss_part = nullptr;  // per sample and chunk, the two partial sums
   double* chan_part = nullptr;  // channel-sum partials [max channels][kChanParts]
   int lastB = 0;
   int sms = 1;  // the device's SM count (grids of the persistent kernels)
@@ -310,11 +311,20 @@ __global__ void channel_final_kernel(const double* part, ll C, float* out) {
   out[c] = (float)s;
 }
 
-// per sample b: norms[2b] = ||out_b - t_b||^2, norms[2b+1] = ||t_b||^2 (one block per sample)
-__global__ void loss_norms_kernel(const float* out, const float* t, ll n_per, double* norms) {
+// per sample b: norms[2b] = ||out_b - t_b||^2, norms[2b+1] = ||t_b||^2, in
+// FP64.  kLossParts blocks per sample each sum one contiguous chunk (per
+// thread, then a tree over the block) into part[b][j]; loss_final_kernel adds
+// the parts in order and stores the gradient's scale 1 / (B ||out_b - t_b||
+// ||t_b||) (0 where a norm is 0) after the 2B norms.
+constexpr int kLossParts = 64;
+
+__global__ void loss_parts_kernel(const float* out, const float* t, ll n_per, double* part) {
   const ll b = blockIdx.x;
+  const int j = blockIdx.y;
+  const ll span = (n_per + kLossParts - 1) / kLossParts;
+  const ll i0 = j * span, i1 = min(n_per, i0 + span);
   double d2 = 0.0, t2 = 0.0;
-  for (ll i = threadIdx.x; i < n_per; i += blockDim.x) {
+  for (ll i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const double o = out[b * n_per + i], tt = t[b * n_per + i];
     d2 += (o - tt) * (o - tt);
     t2 += tt * tt;
@@ -331,19 +341,32 @@ __global__ void loss_norms_kernel(const float* out, const float* t, ll n_per, do
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    norms[2 * b] = r1[0];
-    norms[2 * b + 1] = r2[0];
+    part[2 * (b * kLossParts + j)] = r1[0];
+    part[2 * (b * kLossParts + j) + 1] = r2[0];
   }
 }
 
-// dout = (out - t) / (B ||out_b - t_b|| ||t_b||)
+__global__ void loss_final_kernel(const double* part, ll B, double* norms) {
+  const ll b = blockIdx.x * (ll)blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double d2 = 0.0, t2 = 0.0;
+  for (int j = 0; j < kLossParts; ++j) {
+    d2 += part[2 * (b * kLossParts + j)];
+    t2 += part[2 * (b * kLossParts + j) + 1];
+  }
+  norms[2 * b] = d2;
+  norms[2 * b + 1] = t2;
+  const double den = (double)B * sqrt(d2) * sqrt(t2);
+  norms[2 * B + b] = den > 0.0 ? 1.0 / den : 0.0;
+}
+
+// dout = (out - t) / (B ||out_b - t_b|| ||t_b||), the scale taken per sample
 __global__ void loss_grad_kernel(const float* out, const float* t, const double* norms, ll n_per,
                                  ll B, float* dout) {
   for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < B * n_per;
        i += (ll)gridDim.x * blockDim.x) {
     const ll b = i / n_per;
-    const double den = (double)B * sqrt(norms[2 * b]) * sqrt(norms[2 * b + 1]);
-    dout[i] = den > 0.0 ? (float)((out[i] - t[i]) / den) : 0.f;
+    dout[i] = (float)(((double)out[i] - (double)t[i]) * norms[2 * B + b]);
   }
 }
 
@@ -1126,7 +1149,8 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
   ok = ok && falloc(f, &f->dv, plane) == cudaSuccess;
   ok = ok && falloc(f, &f->dv2, plane) == cudaSuccess;
   ok = ok && falloc(f, &f->dz, plane) == cudaSuccess;
-  ok = ok && falloc(f, &f->norms, 2 * B) == cudaSuccess;
+  ok = ok && falloc(f, &f->norms, 3 * B) == cudaSuccess;
+  ok = ok && falloc(f, &f->loss_part, 2 * B * kLossParts) == cudaSuccess;
   ok = ok && falloc(f, &f->chan_part, kChanParts * (size_t)std::max<ll>(proj, width)) == cudaSuccess;
   const ll nsplit = (P + kWgChunk - 1) / kWgChunk;
   const ll mn = std::max<ll>((ll)proj * C, std::max<ll>(C * C, C * (ll)c_in));
@@ -1284,7 +1308,9 @@ sn_status sn_fno_loss(sn_fno f, const float* target, int B, double* loss) {
   if (!f || !target || !loss) return ffail(SN_EINVAL, "sn_fno_loss: NULL argument");
   if (B != f->lastB) return ffail(SN_EINVAL, "sn_fno_loss: batch differs from the last forward");
   const ll n_per = 2 * f->P;
-  loss_norms_kernel<<<B, 256, 0, f->stream>>>(f->out, target, n_per, f->norms);
+  loss_parts_kernel<<<dim3((unsigned)B, kLossParts), 256, 0, f->stream>>>(f->out, target, n_per,
+                                                                           f->loss_part);
+  loss_final_kernel<<<(unsigned)((B + 127) / 128), 128, 0, f->stream>>>(f->loss_part, B, f->norms);
   loss_grad_kernel<<<blocks_for(B * n_per), 256, 0, f->stream>>>(f->out, target, f->norms, n_per, B, f->dout);
   FCHK(cudaGetLastError());
   std::vector<double> nr(2 * B);
