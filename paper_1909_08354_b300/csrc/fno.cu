@@ -1,6 +1,10 @@
 // Fourier-neural-operator surrogate of the split-step solver: forward,
-// backward, loss and Adam, every contraction on the BF16 tensor-core GEMM
-// (FP32 accumulation) and every pointwise op in its own small kernel.
+// backward, loss and Adam.  Every contraction runs on BF16 tensor cores with
+// FP32 accumulation: the truncated DFTs in streaming passes of their own
+// (dft_x_kernel, dft_y_kernel, idft_y_kernel), the spectral layers' inverse
+// DFT along x with the 1x1 convolution in the tcgen05 layer kernel, the rest
+// on the batched GEMM; pointwise work is fused into those kernels or runs in
+// small kernels of its own.
 //
 // Network (channels C, grid s x s, kept modes ky in {0..m-1} u {s-m..s-1},
 // kx in {0..m-1}, Nm = 2m * m modes):
