@@ -443,19 +443,24 @@ __global__ void mass_kernel(const float2* psi, ll P, double* out) {
 // V (4m x m) = [EyA | EyB] (4m x 2s) [A1re ; A1im] (2s x m) for every plane: the
 // two per-plane GEMMs of the y transform as one product with K = 2s.  The
 // 4m x 2s table, rounded to BF16 once (dfty_table_kernel), is copied into
-// shared memory once per CTA with 16-byte loads, each plane's A1 (s x 2m FP32) is read once, rounded to BF16 like the GEMM's
-// operands and stored [k][n]; the next plane's A1 is loaded into registers
-// while the current one is multiplied.  One warp per 16 rows of V, NT n-tiles
-// of 8 modes each (mma.sync m16n8k16, FP32 accumulation).  Row strides: the
-// table's 2s + 8 and the plane operand's dfty_ns(m) BF16 values, both an odd
-// multiple of 4 words modulo 8, which keeps the fragment loads on 32 banks.
-constexpr int kDftyMaxLoads = 16;  // float4 of a plane per thread: s / 16 <= 16
+// shared memory once per CTA with 16-byte loads; each plane's A1 (s x 2m
+// FP32) is read once, rounded to BF16 like the GEMM's operands and stored
+// [k][n]; the next plane's A1 is loaded into registers while the current one
+// is multiplied.  Two groups of m / 4 warps, one warp per 16 rows of V in each,
+// take the two halves of K (the EyA and the EyB products); the second group's
+// sums go through shared memory to the first, which adds them and stores V.
+// NT n-tiles of 8 modes each (mma.sync m16n8k16, FP32 accumulation).  Row
+// strides: the table's 2s + 8 and the plane operand's dfty_ns(m) BF16 values,
+// both an odd multiple of 4 words modulo 8, which keeps the fragment loads on
+// 32 banks.
+constexpr int kDftyMaxLoads = 8;  // float4 of a plane per thread: s / 32 <= 8
 
 __host__ __device__ constexpr int dfty_ns(int m) {
   return ((((m + 7) / 8) * 4) % 8 == 4 ? ((m + 7) / 8) * 8 : ((m + 7) / 8) * 8 + 8);
 }
 inline size_t dfty_smem(int s, int m) {
-  return sizeof(__nv_bfloat16) * ((size_t)4 * m * (2 * s + 8) + (size_t)2 * s * dfty_ns(m));
+  return sizeof(__nv_bfloat16) * ((size_t)4 * m * (2 * s + 8) + (size_t)2 * s * dfty_ns(m)) +
+         sizeof(float) * (size_t)(m / 4) * 32 * 4 * ((m + 7) / 8);  // the second group's sums
 }
 
 __device__ __forceinline__ void mma_16x8x16_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0,
@@ -482,7 +487,7 @@ __global__ void dfty_table_kernel(const float* EyA, const float* EyB, __nv_bfloa
 }
 
 template <int NT>
-__global__ void __launch_bounds__(256) dft_y_kernel(const __nv_bfloat16* __restrict__ EyAB,
+__global__ void __launch_bounds__(512) dft_y_kernel(const __nv_bfloat16* __restrict__ EyAB,
                                                     const float* __restrict__ A1,
                                                     float* __restrict__ V, int s, int m, ll planes,
                                                     ll vstride) {
@@ -545,8 +550,10 @@ __global__ void __launch_bounds__(256) dft_y_kernel(const __nv_bfloat16* __restr
     for (int j = 0; j < NT; ++j)
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
-    const int r0 = warp * 16 + gid;
-    for (int kk = 0; kk < 2 * s; kk += 16) {
+    const int nwm = m / 4;                            // warps per half of K
+    const int kh = warp / nwm, mt = warp - kh * nwm;  // half of K, row tile
+    const int r0 = mt * 16 + gid;
+    for (int kk = kh * s; kk < kh * s + s; kk += 16) {
       unsigned af[4];
       af[0] = *reinterpret_cast<const unsigned*>(As + r0 * KS + kk + 2 * tig);
       af[1] = *reinterpret_cast<const unsigned*>(As + (r0 + 8) * KS + kk + 2 * tig);
@@ -558,6 +565,21 @@ __global__ void __launch_bounds__(256) dft_y_kernel(const __nv_bfloat16* __restr
         mma_16x8x16_bf16(acc[j], af, bf16_pair(b[0], b[NS]), bf16_pair(b[8 * NS], b[9 * NS]));
       }
     }
+    // the EyB half's sums to the EyA half (the next plane's writes of Bs come
+    // after the barrier at the top of the loop, so red is free again by then)
+    float* red = reinterpret_cast<float*>(Bs + (size_t)2 * s * NS) + (size_t)(mt * 32 + lane) * 4 * NT;
+    if (kh == 1) {
+#pragma unroll
+      for (int j = 0; j < NT; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) red[4 * j + r] = acc[j][r];
+    }
+    __syncthreads();
+    if (kh == 1) continue;
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[j][r] += red[4 * j + r];
     float* out = V + p * vstride;
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
@@ -898,7 +920,7 @@ bool dfty_supported(int s, int m) {
 template <int NT>
 cudaError_t launch_dft_y_t(sn_fno f, ll planes, float* V) {
   const size_t smem = dfty_smem(f->s, f->m);
-  const int threads = 8 * f->m;
+  const int threads = 16 * f->m;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_y_kernel<NT>, threads, smem);
   if (e != cudaSuccess) return e;
