@@ -666,8 +666,8 @@ __global__ void __launch_bounds__(kDftxThreads) dft_x_kernel(const float* __rest
 // dft_y_kernel: the 2s x 4m BF16 table resident in shared memory (row stride
 // 4m + 8), each plane's modes U (4m x m FP32) read once and rounded to BF16
 // ([k][n], stride dfty_ns(m)), the next plane's loaded while the current one is
-// multiplied; eight warps take the 2s / 16 row tiles in turn.
-constexpr int kIdftyThreads = 256, kIdftyMaxLoads = 4;  // m^2 / 4 float4 of U <= 4 a thread
+// multiplied; sixteen warps take the 2s / 16 row tiles in turn.
+constexpr int kIdftyThreads = 512, kIdftyMaxLoads = 2;  // m^2 float4 of U <= 2 a thread
 
 inline size_t idfty_smem(int s, int m) {
   return sizeof(__nv_bfloat16) * ((size_t)2 * s * (4 * m + 8) + (size_t)4 * m * dfty_ns(m));
@@ -680,7 +680,7 @@ __global__ void stack_bf16_kernel(const float* top, const float* bottom, __nv_bf
 }
 
 template <int NT>
-__global__ void __launch_bounds__(kIdftyThreads) idft_y_kernel(const __nv_bfloat16* __restrict__ EyI,
+__global__ void __launch_bounds__(kIdftyThreads, 1) idft_y_kernel(const __nv_bfloat16* __restrict__ EyI,
                                                                const float* __restrict__ U,
                                                                float* __restrict__ B1, int s, int m,
                                                                ll planes, ll ustride) {
