@@ -818,6 +818,70 @@ __global__ void mode_mix_kernel(const float* V, const float* R, float* U, int B,
   }
 }
 
+// The same mixing for kMixModes consecutive modes per block: V and U of all of
+// them staged in shared memory, so that the global reads and writes are runs
+// of kMixModes modes (32 bytes) instead of one word per sector; R staged one
+// mode at a time.  Each output is summed over i in the same order with the
+// same operations as mode_mix_kernel, so the results are the same bits.
+constexpr int kMixModes = 8, kMixThreads = 512;
+
+inline size_t mode_mix8_smem(ll B, ll C) {
+  return sizeof(float2) * ((size_t)2 * kMixModes * B * C + (size_t)C * C);
+}
+
+__global__ void __launch_bounds__(kMixThreads) mode_mix8_kernel(const float* V, const float* R,
+                                                                float* U, int B, int C, ll Nm) {
+  extern __shared__ float mm_sm[];
+  const int BC = B * C;
+  float2* Vs = reinterpret_cast<float2*>(mm_sm);  // [kMixModes][B][C]
+  float2* Us = Vs + kMixModes * BC;               // [kMixModes][B][C]
+  float2* Rs = Us + kMixModes * BC;               // [C][C], rounded
+  const ll mode0 = blockIdx.x * (ll)kMixModes;
+  const int nm = (int)min((ll)kMixModes, Nm - mode0);
+  const ll is = 2 * Nm, bs = (ll)C * is;
+  for (int e = threadIdx.x; e < BC * kMixModes; e += blockDim.x) {
+    const int bi = e / kMixModes, q = e - bi * kMixModes;
+    if (q < nm) {
+      const int b = bi / C, i = bi - b * C;
+      const float* v = V + b * bs + i * is + mode0 + q;
+      Vs[q * BC + bi] = make_float2(bf(v[0]), bf(v[Nm]));
+    }
+  }
+  for (int q = 0; q < nm; ++q) {
+    __syncthreads();  // the previous mode's reads of Rs are done (and Vs is written)
+    const float2* Rm = reinterpret_cast<const float2*>(R) + (mode0 + q) * (ll)C * C;
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+      const float2 r = Rm[e];
+      Rs[e] = make_float2(bf(r.x), bf(r.y));
+    }
+    __syncthreads();
+    const float2* Vq = Vs + q * BC;
+    for (int e = threadIdx.x; e < BC; e += blockDim.x) {
+      const int b = e / C, o = e - b * C;
+      float ar = 0.f, ai = 0.f;
+      for (int i = 0; i < C; ++i) {
+        const float2 x = Vq[b * C + i];
+        const float2 r = Rs[i * C + o];
+        const float rr = r.x, ri = r.y;
+        ar = fmaf(x.x, rr, fmaf(-x.y, ri, ar));
+        ai = fmaf(x.x, ri, fmaf(x.y, rr, ai));
+      }
+      Us[q * BC + e] = make_float2(ar, ai);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < BC * kMixModes; e += blockDim.x) {
+    const int bo = e / kMixModes, q = e - bo * kMixModes;
+    if (q < nm) {
+      const int b = bo / C, o = bo - b * C;
+      float* u = U + b * bs + o * is + mode0 + q;
+      const float2 w = Us[q * BC + bo];
+      u[0] = w.x;
+      u[Nm] = w.y;
+    }
+  }
+}
+
 // GR[mode][i][o] = sum_b conj(V[b][i]) GU[b][o];  GV[b][i] = sum_o conj(R[i][o]) GU[b][o]
 __global__ void mode_mix_bwd_kernel(const float* V, const float* R, const float* GU, float* GR,
                                     float* GV, int B, int C, ll Nm) {
@@ -1034,6 +1098,11 @@ cudaError_t dft_inverse(sn_fno f, const float* U, int B, int Cn, const float* Wx
 
 // U[b][o] = sum_i R[mode][i][o] V[b][i] per mode (complex), four real GEMMs
 cudaError_t mode_mix(sn_fno f, const float* V, const float* R, int B, float* U) {
+  if (mode_mix8_smem(f->Bmax, f->C) <= 200 * 1024) {
+    mode_mix8_kernel<<<(unsigned)((f->Nm + kMixModes - 1) / kMixModes), kMixThreads,
+                       mode_mix8_smem(B, f->C), f->stream>>>(V, R, U, B, f->C, f->Nm);
+    return cudaGetLastError();
+  }
   const size_t sm = sizeof(float2) * ((size_t)B * f->C + (size_t)f->C * f->C);
   mode_mix_kernel<<<(unsigned)f->Nm, 256, sm, f->stream>>>(V, R, U, B, f->C, f->Nm);
   return cudaGetLastError();
@@ -1189,6 +1258,9 @@ sn_status sn_fno_create(sn_fno* out, int s, int c_in, int width, int modes, int 
     if (sm_bwd > 200 * 1024) return bail(ffail(SN_ENOTSUP, "sn_fno_create: batch_max * width too large"));
     ok = ok && cudaFuncSetAttribute(mode_mix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sm_fwd) == cudaSuccess;
+    if (mode_mix8_smem(B, C) <= 200 * 1024)
+      ok = ok && cudaFuncSetAttribute(mode_mix8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)mode_mix8_smem(B, C)) == cudaSuccess;
     ok = ok && cudaFuncSetAttribute(mode_mix_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sm_bwd) == cudaSuccess;
   }
